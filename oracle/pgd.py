@@ -1,0 +1,245 @@
+"""Projection, PGD, rounding/check and annealing with ERWA (TEST INFRASTRUCTURE ONLY).
+
+Follows, in the paper's order:
+  * Eq. pg1 / pg2 (Methods, "Projected Gradient Descent"): a gradient step
+    then proj_D.  The step is taken in coordinates where the reals are divided
+    by the instance length scale S (the paper's instances live in [0, 1]), so
+    the b-step is eta * S^2 * dC/db; uniform scaling leaves the Euclidean
+    projection of the reals unchanged.
+  * Def. Projection / Prop. QP: D = [-1, 1]^n x (box of the reals) x (unit
+    atomic constraints).  Single-variable unit atoms tighten the box (exact
+    clamp).  Multi-variable unit atoms are half-spaces; the projection onto
+    box n half-spaces uses Dykstra's alternating projections (Boyle & Dykstra
+    1986) with a fixed number of sweeps, half-spaces in constraint order and
+    the box last in each sweep -- the paper names no QP method, so this is a
+    documented reading, exact only in the limit.
+  * Eq. grad_map: g = ((a, b) - proj(...)) / eta, measured in the scaled
+    coordinates, and the epsilon-critical stopping rule ||g||^2 <= eps^2
+    (Eq. critical), applied per restart.
+  * Alg. 1 rounding x = sgn(a) with x_i = TRUE (-1) iff a_i < 0, y = b, and the
+    exact check of every constraint (Thm. Soundness).
+  * Alg. 2: per sigma stage, PGD to a critical point, round, u_c = [c violated],
+    h_c <- rho h_c + u_c, and every tau stages w_c <- w_c gamma^h_c, h_c <- 1;
+    SAT when #Unsat = 0.  rho = 0.5, gamma = 2, tau = 1 (Methods).
+
+Pins (tests/test_oracle_pgd.py): projection idempotent and non-expansive;
+Dykstra against an exact active-set enumeration of the QP on small blocks;
+the descent lemma with eta = 1/L (Lemma descent, Prop. Lipschitz); exact check
+against planted assignments and single-literal flips; Fig. 2's two minima;
+the vectorised kind evaluation against the scalar definition.
+The annealing trajectory itself is parity unpinned (the paper gives no
+trajectory values for a known step size).
+"""
+from dataclasses import dataclass, field
+from fractions import Fraction
+
+import numpy as np
+
+from . import objective as OBJ
+from . import semantics as S
+
+
+@dataclass
+class Config:
+    eta: float = 0.01
+    eps: float = 1e-2
+    t_max: int = 200
+    rho: float = 0.5
+    gamma: float = 2.0
+    tau: int = 1
+    sweeps: int = 20
+    policy: int = OBJ.PROJECT
+    inv_sigma: list = field(default_factory=lambda: [0.1 * t for t in range(1, 21)])  # times 1/S
+
+
+# ---------------------------------------------------------------------------
+# the feasible set D
+# ---------------------------------------------------------------------------
+class Domain:
+    """Box [lo, hi] of the reals tightened by unit atoms, plus half-spaces q.y <= q0."""
+
+    def __init__(self, inst, policy=OBJ.PROJECT):
+        self.lo = np.array(inst.lo, np.float64)
+        self.hi = np.array(inst.hi, np.float64)
+        self.halfspaces = []  # (vars, coefs float64, q0 float64)
+        if policy != OBJ.PROJECT:
+            return
+        for c in range(inst.n_cons):
+            if not OBJ.is_unit_atomic(inst, c):
+                continue
+            l = int(inst.lits(c)[0])
+            var, coef, q0, rel = inst.atom((l >> 1) - inst.n_bool)
+            coef, q0, strict = S.normalized_atom(coef, q0, rel)
+            if l & 1:  # not (q.y <= q0)  ->  -q.y <= -q0 (closure of the open half-space)
+                coef, q0 = [-c_ for c_ in coef], -q0
+            if len(var) == 1:
+                j, qj = int(var[0]), coef[0]
+                bound = float(Fraction(q0, qj))
+                if qj > 0:
+                    self.hi[j] = min(self.hi[j], bound)
+                else:
+                    self.lo[j] = max(self.lo[j], bound)
+            else:
+                self.halfspaces.append((np.asarray(var, np.int64), np.asarray(coef, np.float64), float(q0)))
+
+    def project_b(self, bp, sweeps):
+        """proj onto box n half-spaces of points bp [m][R] (Dykstra; exact clamp if no half-space)."""
+        x = np.clip(bp, self.lo[:, None], self.hi[:, None])
+        if not self.halfspaces:
+            return x
+        J = np.unique(np.concatenate([h[0] for h in self.halfspaces]))
+        x[J] = bp[J]
+        R = bp.shape[1]
+        p_box = np.zeros((len(J), R))
+        t_h = [np.zeros(R) for _ in self.halfspaces]
+        for _ in range(sweeps):
+            for k, (var, q, q0) in enumerate(self.halfspaces):
+                yv = x[var] + t_h[k][None, :] * q[:, None]
+                viol = (q[:, None] * yv).sum(0) - q0
+                t_h[k] = np.maximum(viol, 0.0) / float((q * q).sum())
+                x[var] = yv - t_h[k][None, :] * q[:, None]
+            yv = x[J] + p_box
+            xn = np.clip(yv, self.lo[J][:, None], self.hi[J][:, None])
+            p_box = yv - xn
+            x[J] = xn
+        return x
+
+
+def pgd_step(a, b, ga, gb, eta, scale, dom, sweeps):
+    """One PGD step (Eq. pg1, pg2) and ||g||^2 (Eq. grad_map, scaled coordinates)."""
+    a_new = np.clip(a - eta * ga, -1.0, 1.0)
+    b_new = dom.project_b(b - eta * scale * scale * gb, sweeps)
+    gn2 = (((a - a_new) / eta) ** 2).sum(0) + (((b - b_new) / (scale * eta)) ** 2).sum(0)
+    return a_new, b_new, gn2
+
+
+# ---------------------------------------------------------------------------
+# rounding and the exact check
+# ---------------------------------------------------------------------------
+def kind_value_vec(kind, param, T):
+    """semantics.kind_value over restarts: T is a bool array [L][R]."""
+    if kind == S.OR:
+        return T.any(0)
+    if kind == S.XOR:
+        return T.sum(0) % 2 == 1
+    if kind == S.CARD_LE:
+        return T.sum(0) <= param
+    if kind == S.NAE:
+        return T.any(0) & ~T.all(0)
+    if kind == S.MUX:
+        idx = sum((T[i].astype(np.int64) << i) for i in range(param))
+        return np.take_along_axis(T[param:], idx[None, :], 0)[0]
+    if kind == S.NEQ_OR:
+        P = param
+        r = np.zeros(T.shape[1], bool)
+        for i in range(P):
+            r |= T[2 * i] != T[2 * i + 1]
+        return r | T[2 * P:].any(0)
+    raise ValueError(kind)
+
+
+def atom_truth_exact(inst, i, y):
+    """Exact truth of atom i at each restart's reals y [m][R] (float values).
+
+    A float64 evaluation decides the sign when it is far from zero relative to
+    a bound on its rounding error; otherwise the sign is computed in Fractions.
+    """
+    var, coef, q0, rel = inst.atom(i)
+    yv = np.asarray(y, np.float64)[np.asarray(var, np.int64)]
+    q = np.asarray(coef, np.float64)[:, None]
+    s = (q * yv).sum(0) - float(q0)
+    mag = (np.abs(q * yv)).sum(0) + abs(float(q0))
+    unsure = np.abs(s) <= 1e-12 * mag
+    for r in np.nonzero(unsure)[0]:
+        s[r] = float(sum(Fraction(int(c)) * Fraction(float(v)) for c, v in zip(coef, yv[:, r]))
+                     - Fraction(int(q0)))
+    if rel == S.LE:
+        return s <= 0
+    if rel == S.LT:
+        return s < 0
+    if rel == S.GE:
+        return s >= 0
+    return s > 0
+
+
+def round_check(inst, a, b, constraints=None):
+    """x = sgn(a) (TRUE iff a < 0), y = b; returns (x int8 [n][R], violated bool [C][R])."""
+    a = np.asarray(a)
+    R = a.shape[1] if a.ndim == 2 else np.asarray(b).shape[1]
+    x = np.where(a < 0, -1, 1).astype(np.int8)
+    cons = range(inst.n_cons) if constraints is None else constraints
+    viol = np.zeros((inst.n_cons, R), bool)
+    atom_cache = {}
+    for c in cons:
+        ls = inst.lits(c)
+        T = np.empty((len(ls), R), bool)
+        for t, l in enumerate(ls):
+            vid, neg = int(l) >> 1, bool(int(l) & 1)
+            if vid < inst.n_bool:
+                val = x[vid] == -1
+            else:
+                val = atom_cache.get(vid)
+                if val is None:
+                    val = atom_cache[vid] = atom_truth_exact(inst, vid - inst.n_bool, b)
+            T[t] = val != neg
+        viol[c] = ~kind_value_vec(int(inst.con_kind[c]), int(inst.con_param[c]), T)
+    return x, viol
+
+
+def erwa(w, h, u, t, rho, gamma, tau):
+    """Alg. 2's history and weight update for stage index t (1-based); returns (w, h, #Unsat)."""
+    h = rho * h + u
+    n_unsat = u.sum(0)
+    if t % tau == 0:
+        w = w * np.power(gamma, h)
+        h = np.ones_like(h)
+    return w, h, n_unsat
+
+
+# ---------------------------------------------------------------------------
+# one annealing stage and the full Alg. 2 loop
+# ---------------------------------------------------------------------------
+def run_stage(inst, a, b, w, h, sigma, t, cfg: Config, dom=None, diagrams=None, iters=None):
+    """PGD at fixed sigma (Alg. 1's while loop, per restart) then rounding, check and ERWA.
+
+    Returns (a, b, w, h, n_unsat [R], iterations_run [R], obj_last [R]).
+    """
+    dom = dom or Domain(inst, cfg.policy)
+    diagrams = diagrams or OBJ.Diagrams(inst)
+    a = np.array(a, np.float64)
+    b = np.array(b, np.float64)
+    R = w.shape[1]
+    active = np.ones(R, bool)
+    its = np.zeros(R, np.int64)
+    obj = np.zeros(R)
+    for _ in range(cfg.t_max if iters is None else iters):
+        obj, _, ga, gb = OBJ.evaluate(inst, a, b, w, sigma, cfg.policy, diagrams)
+        a_new, b_new, gn2 = pgd_step(a, b, ga, gb, cfg.eta, inst.scale, dom, cfg.sweeps)
+        a[:, active] = a_new[:, active]
+        b[:, active] = b_new[:, active]
+        its += active
+        active &= ~(gn2 <= cfg.eps * cfg.eps)
+        if not active.any():
+            break
+    _, viol = round_check(inst, a, b)
+    w, h, n_unsat = erwa(w, h, viol.astype(np.float64), t, cfg.rho, cfg.gamma, cfg.tau)
+    return a, b, w, h, n_unsat, its, obj
+
+
+def anneal(inst, a, b, cfg: Config, stages=None):
+    """Alg. 2 over the sigma schedule for R restarts; returns per-restart first SAT stage (0 = none)."""
+    R = a.shape[1]
+    w = np.ones((inst.n_cons, R))
+    h = np.zeros((inst.n_cons, R))
+    dom = Domain(inst, cfg.policy)
+    diagrams = OBJ.Diagrams(inst)
+    sat_stage = np.zeros(R, np.int64)
+    sched = cfg.inv_sigma if stages is None else cfg.inv_sigma[:stages]
+    for t, inv in enumerate(sched, start=1):
+        sigma = inst.scale / inv
+        a, b, w, h, n_unsat, _, _ = run_stage(inst, a, b, w, h, sigma, t, cfg, dom, diagrams)
+        newly = (n_unsat == 0) & (sat_stage == 0)
+        sat_stage[newly] = t
+        if (sat_stage > 0).all():
+            break
+    return sat_stage, a, b

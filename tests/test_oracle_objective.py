@@ -1,0 +1,146 @@
+"""Pins for the oracle's relaxation, objective and gradient (no GPU)."""
+import math
+
+import numpy as np
+import pytest
+from scipy.special import ndtr
+
+from oracle import objective as OBJ, relax
+from workloads import instances as W
+
+
+def small_instance(seed=3):
+    return W.tiny_random(seed, n_bool=8, n_real=4, n_cons=25)
+
+
+def test_atom_probability_is_gaussian_cdf():
+    """Eq. sampling: P[q.Y <= q0], Y ~ N(b, sigma^2 I) = Phi(-z / (sigma ||q||))."""
+    B = W._Builder(0, 3)
+    B.atom([0, 2], [3, -4], 7, W.LE)
+    B.con(W.OR, [W.lit(0)])
+    inst = B.freeze("t", np.zeros(3), np.ones(3), [], np.zeros(3), 1.0)
+    rng = np.random.default_rng(0)
+    b = rng.uniform(-3, 3, (3, 50))
+    for sigma in (0.3, 1.0, 4.0):
+        p, _ = relax.atom_terms(inst, 0, b, sigma)
+        z = 3 * b[0] - 4 * b[2] - 7
+        np.testing.assert_allclose(p, ndtr(-z / (sigma * 5.0)), rtol=1e-12, atol=1e-300)
+
+
+def test_atom_probability_monte_carlo():
+    B = W._Builder(0, 2)
+    B.atom([0, 1], [2, 1], 3, W.GE)
+    B.con(W.OR, [W.lit(0)])
+    inst = B.freeze("t", np.zeros(2), np.ones(2), [], np.zeros(2), 1.0)
+    b = np.array([[1.2], [0.4]])
+    sigma = 0.7
+    p, _ = relax.atom_terms(inst, 0, b, sigma)
+    rng = np.random.default_rng(1)
+    N = 1_000_000
+    y = b[:, 0][:, None] + sigma * rng.standard_normal((2, N))
+    est = ((2 * y[0] + y[1]) >= 3).mean()
+    assert abs(est - p[0]) < 4 * math.sqrt(p[0] * (1 - p[0]) / N)
+
+
+def test_atom_derivative_finite_difference():
+    """dd/db_j (Prop. Lipschitz proof form) against central differences of d = 1 - 2p."""
+    inst = small_instance()
+    rng = np.random.default_rng(2)
+    b = rng.uniform(0, 100, (inst.n_real, 3))
+    for i in range(min(inst.n_atoms, 12)):
+        for sigma in (5.0, 30.0):
+            _, terms = relax.atom_terms(inst, i, b, sigma)
+            for j, g in terms:
+                h = 1e-4
+                bp, bm = b.copy(), b.copy()
+                bp[j] += h
+                bm[j] -= h
+                fd = (relax.atom_d(inst, i, bp, sigma) - relax.atom_d(inst, i, bm, sigma)) / (2 * h)
+                np.testing.assert_allclose(g, fd, rtol=1e-6, atol=1e-10)
+
+
+def test_sigma_zero_is_the_indicator():
+    B = W._Builder(0, 1)
+    B.atom([0], [1], 2, W.LE)
+    B.atom([0], [1], 2, W.LT)
+    B.con(W.OR, [W.lit(0)])
+    inst = B.freeze("t", np.zeros(1), np.ones(1), [], np.zeros(1), 1.0)
+    b = np.array([[1.0, 2.0, 3.0]])
+    p_le, t_le = relax.atom_terms(inst, 0, b, 0.0)
+    p_lt, _ = relax.atom_terms(inst, 1, b, 0.0)
+    assert list(p_le) == [1.0, 1.0, 0.0] and list(p_lt) == [1.0, 0.0, 0.0]
+    assert all((g == 0).all() for _, g in t_le)
+
+
+def test_gradient_central_differences():
+    inst = small_instance()
+    R = 3
+    a, b = W.initial_point(inst, R, seed=4)
+    a = a.astype(np.float64) * 0.9
+    b = b.astype(np.float64)
+    w = np.random.default_rng(5).uniform(0.5, 2.0, (inst.n_cons, R))
+    sigma = 20.0
+    obj, _, ga, gb = OBJ.evaluate(inst, a, b, w, sigma)
+    h = 1e-6
+    for i in range(inst.n_bool):
+        ap, am = a.copy(), a.copy()
+        ap[i] += h
+        am[i] -= h
+        fd = (OBJ.evaluate(inst, ap, b, w, sigma, with_grad=False)[0] -
+              OBJ.evaluate(inst, am, b, w, sigma, with_grad=False)[0]) / (2 * h)
+        np.testing.assert_allclose(ga[i], fd, rtol=1e-6, atol=1e-8)
+    for j in range(inst.n_real):
+        hb = 1e-5
+        bp, bm = b.copy(), b.copy()
+        bp[j] += hb
+        bm[j] -= hb
+        fd = (OBJ.evaluate(inst, a, bp, w, sigma, with_grad=False)[0] -
+              OBJ.evaluate(inst, a, bm, w, sigma, with_grad=False)[0]) / (2 * hb)
+        np.testing.assert_allclose(gb[j], fd, rtol=1e-5, atol=1e-9)
+
+
+def test_multilinear_identity():
+    """Lemma expectation: C is affine in each a_i, so C(a_i=1) - C(a_i=-1) = 2 dC/da_i."""
+    inst = small_instance(9)
+    R = 2
+    a, b = W.initial_point(inst, R, seed=1)
+    a = a.astype(np.float64)
+    b = b.astype(np.float64)
+    w = np.ones((inst.n_cons, R))
+    _, _, ga, _ = OBJ.evaluate(inst, a, b, w, 15.0)
+    for i in range(inst.n_bool):
+        ap, am = a.copy(), a.copy()
+        ap[i], am[i] = 1.0, -1.0
+        diff = OBJ.evaluate(inst, ap, b, w, 15.0, with_grad=False)[0] - \
+            OBJ.evaluate(inst, am, b, w, 15.0, with_grad=False)[0]
+        np.testing.assert_allclose(diff, 2 * ga[i], atol=1e-12)
+
+
+@pytest.mark.parametrize("make", [lambda: W.tiny_random(1001), lambda: W.jobshop(1002, 8, 4),
+                                  lambda: W.placement2d(1003, 12), lambda: W.large_scheduling(1005, 16, 20, 6, 3, 5)])
+def test_soundness_at_planted_vertex(make):
+    """Thm. Soundness / Cor. cop=wfe at sigma = 0: every COP is 1 and C = -sum w at a model."""
+    inst = make()
+    a = inst.planted_x.astype(np.float64)[:, None]
+    b = inst.planted_y[:, None]
+    w = np.ones((inst.n_cons, 1))
+    obj, cops, _, _ = OBJ.evaluate(inst, a, b, w, 0.0, policy=OBJ.SOFT)
+    assert np.all(cops == 1.0)
+    assert obj[0] == -inst.n_cons
+
+
+def test_optimality_sigma_zero_affine():
+    """Thm. optimality: at sigma = 0, C is multilinear in a (no interior optimum): the
+    second difference along each coordinate vanishes."""
+    inst = small_instance(4)
+    a, b = W.initial_point(inst, 2, seed=8)
+    a = a.astype(np.float64) * 0.5
+    b = b.astype(np.float64)
+    w = np.ones((inst.n_cons, 2))
+    for i in range(inst.n_bool):
+        vals = []
+        for t in (-0.2, 0.0, 0.2):
+            ap = a.copy()
+            ap[i] += t
+            vals.append(OBJ.evaluate(inst, ap, b, w, 0.0, with_grad=False)[0])
+        np.testing.assert_allclose(vals[0] - 2 * vals[1] + vals[2], 0.0, atol=1e-12)

@@ -1,0 +1,192 @@
+"""Pins for the oracle's projection, PGD step, exact check and ERWA (no GPU)."""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+from oracle import objective as OBJ, pgd, semantics as S
+from workloads import instances as W
+
+
+def exact_projection(y, lo, hi, A, c):
+    """argmin ||x - y||^2 s.t. lo <= x <= hi, A x <= c, by enumerating active sets (KKT)."""
+    n = len(y)
+    rows = []
+    for i in range(n):
+        e = np.zeros(n)
+        e[i] = 1
+        rows.append((e, hi[i]))
+        rows.append((-e, -lo[i]))
+    for k in range(len(c)):
+        rows.append((A[k], c[k]))
+    best, best_d = None, np.inf
+    for r in range(0, n + 1):
+        for act in itertools.combinations(range(len(rows)), r):
+            G = np.array([rows[k][0] for k in act]).reshape(r, n)
+            h = np.array([rows[k][1] for k in act])
+            if r:
+                M = G @ G.T
+                if abs(np.linalg.det(M)) < 1e-12:
+                    continue
+                lam = np.linalg.solve(M, G @ y - h)
+                if (lam < -1e-12).any():
+                    continue
+                x = y - G.T @ lam
+            else:
+                x = y.copy()
+            ok = all(rows[k][0] @ x <= rows[k][1] + 1e-9 for k in range(len(rows)))
+            if ok and np.linalg.norm(x - y) < best_d:
+                best, best_d = x, np.linalg.norm(x - y)
+    return best
+
+
+def halfspace_instance(rng, n_real=3, n_half=3):
+    B = W._Builder(0, n_real)
+    A, c = [], []
+    for _ in range(n_half):
+        var = rng.choice(n_real, 2, replace=False)
+        coef = rng.integers(1, 4, 2) * rng.choice([-1, 1], 2)
+        q0 = int(rng.integers(-3, 4))
+        B.con(W.OR, [W.lit(B.atom(var, coef, q0, W.LE))])
+        row = np.zeros(n_real)
+        row[var] = coef
+        A.append(row)
+        c.append(q0)
+    lo, hi = np.full(n_real, -4.0), np.full(n_real, 4.0)
+    return B.freeze("h", lo, hi, [], np.zeros(n_real), 1.0), lo, hi, np.array(A), np.array(c, float)
+
+
+def test_dykstra_matches_exact_qp():
+    rng = np.random.default_rng(0)
+    checked = 0
+    for _ in range(40):
+        inst, lo, hi, A, c = halfspace_instance(rng)
+        dom = pgd.Domain(inst)
+        assert len(dom.halfspaces) == 3
+        y = rng.uniform(-6, 6, inst.n_real)
+        x_ex = exact_projection(y, lo, hi, A, c)
+        if x_ex is None:  # empty feasible set
+            continue
+        x = dom.project_b(y[:, None], sweeps=3000)[:, 0]
+        np.testing.assert_allclose(x, x_ex, atol=1e-7)
+        checked += 1
+    assert checked > 20
+
+
+def test_projection_idempotent_and_nonexpansive():
+    rng = np.random.default_rng(1)
+    inst, lo, hi, A, c = halfspace_instance(rng, 4, 3)
+    dom = pgd.Domain(inst)
+    y = rng.uniform(-8, 8, (4, 50))
+    x = dom.project_b(y, 3000)
+    if exact_projection(y[:, 0], lo, hi, A, c) is None:
+        pytest.skip("empty feasible set for this draw")
+    np.testing.assert_allclose(dom.project_b(x, 3000), x, atol=1e-7)
+    d_in = np.linalg.norm(y[:, :25] - y[:, 25:], axis=0)
+    d_out = np.linalg.norm(x[:, :25] - x[:, 25:], axis=0)
+    assert (d_out <= d_in + 1e-7).all()
+
+
+def test_single_variable_unit_atoms_tighten_the_box():
+    B = W._Builder(0, 2)
+    B.con(W.OR, [W.lit(B.atom([0], [3], 7, W.LE))])  # y0 <= 7/3
+    B.con(W.OR, [W.lit(B.atom([1], [2], 1, W.GE))])  # y1 >= 1/2
+    B.con(W.OR, [W.lit(B.atom([1], [1], 5, W.GT), True)])  # not (y1 > 5): y1 <= 5
+    inst = B.freeze("u", np.array([-10.0, -10.0]), np.array([10.0, 10.0]), [], np.zeros(2), 1.0)
+    dom = pgd.Domain(inst)
+    assert dom.hi[0] == 7 / 3 and dom.lo[1] == 0.5 and dom.hi[1] == 5.0
+    assert OBJ.objective_constraints(inst, OBJ.PROJECT) == []
+    assert OBJ.objective_constraints(inst, OBJ.SOFT) == [0, 1, 2]
+
+
+def test_descent_lemma():
+    """Lemma descent with eta = 1/L, L from Prop. Lipschitz (scale 1, box only)."""
+    inst = W.tiny_random(21, n_bool=6, n_real=4, n_cons=12)
+    inst.scale = 1.0
+    R = 4
+    a, b = W.initial_point(inst, R, seed=3)
+    a, b = a.astype(np.float64), b.astype(np.float64)
+    w = np.ones((inst.n_cons, R))
+    sigma = 30.0
+    n, m = inst.n_bool, inst.n_real
+    alpha = float(inst.n_cons)
+    beta = max(1, max(sum(1 for l in inst.lits(c) if (l >> 1) >= n and j in inst.atom((l >> 1) - n)[0])
+                      for c in range(inst.n_cons) for j in range(m)))
+    gam = math.sqrt(2) * beta / (math.sqrt(math.pi) * sigma)
+    rho = alpha * math.sqrt(n + m) * max(1.0, gam)
+    L = math.sqrt(n + m * gam * gam) * rho
+    eta = 1.0 / L
+    dom = pgd.Domain(inst)
+    for _ in range(5):
+        obj, _, ga, gb = OBJ.evaluate(inst, a, b, w, sigma)
+        a2, b2, gn2 = pgd.pgd_step(a, b, ga, gb, eta, 1.0, dom, 20)
+        obj2 = OBJ.evaluate(inst, a2, b2, w, sigma, with_grad=False)[0]
+        assert (obj2 - obj <= -eta / 2 * gn2 + 1e-12).all()
+        a, b = a2, b2
+
+
+@pytest.mark.parametrize("make", [lambda: W.tiny_random(1001), lambda: W.jobshop(1002, 8, 4),
+                                  lambda: W.placement2d(1003, 12), lambda: W.placement2d(1003, 12, selectors=False),
+                                  lambda: W.large_scheduling(1005, 16, 20, 6, 3, 5)])
+def test_exact_check_planted_and_flip(make):
+    inst = make()
+    a = inst.planted_x.astype(np.float64)[:, None] * 0.5
+    b = inst.planted_y[:, None]
+    x, viol = pgd.round_check(inst, a, b)
+    assert not viol.any()
+    assert (x[:, 0] == inst.planted_x).all()
+    # the scalar definition agrees
+    assert S.unsat_constraints(inst, inst.planted_x, inst.planted_y) == []
+    # flipping every Boolean still leaves unit atom constraints intact, but violates some clause
+    if inst.n_bool:
+        _, viol2 = pgd.round_check(inst, -a, b)
+        assert viol2.any()
+
+
+def test_exact_check_boundary():
+    """An atom exactly on its boundary: y0 - y1 <= -3 at y = (1, 4) holds; LT does not."""
+    B = W._Builder(0, 2)
+    B.con(W.OR, [W.lit(B.atom([0, 1], [1, -1], -3, W.LE))])
+    B.con(W.OR, [W.lit(B.atom([0, 1], [1, -1], -3, W.LT))])
+    inst = B.freeze("b", np.zeros(2), np.ones(2) * 9, [], np.zeros(2), 1.0)
+    y = np.array([[1.0, 1.0 + 2.0 ** -40], [4.0, 4.0]])
+    _, viol = pgd.round_check(inst, np.zeros((0, 2)), y)
+    assert list(viol[0]) == [False, True] and list(viol[1]) == [True, True]
+
+
+def test_kind_value_vec_matches_definition():
+    rng = np.random.default_rng(4)
+    for kind, L, param in [(S.OR, 4, 0), (S.XOR, 5, 0), (S.CARD_LE, 5, 2), (S.NAE, 3, 0),
+                           (S.MUX, 6, 2), (S.MUX, 3, 1), (S.NEQ_OR, 7, 3)]:
+        T = rng.random((L, 200)) < 0.5
+        v = pgd.kind_value_vec(kind, param, T)
+        for r in range(200):
+            assert v[r] == S.kind_value(kind, param, list(T[:, r]))
+
+
+def test_erwa_two_stages():
+    """Alg. 2 with rho = 0.5, gamma = 2, tau = 1: h0 = 0, u = 1 -> w = 2, h = 1;
+    then u = 0 -> h = 0.5 -> w = 2 * sqrt(2), h = 1."""
+    w, h = np.ones((1, 1)), np.zeros((1, 1))
+    w, h, n = pgd.erwa(w, h, np.ones((1, 1)), 1, 0.5, 2.0, 1)
+    assert w[0, 0] == 2.0 and h[0, 0] == 1.0 and n[0] == 1
+    w, h, n = pgd.erwa(w, h, np.zeros((1, 1)), 2, 0.5, 2.0, 1)
+    assert abs(w[0, 0] - 2 * math.sqrt(2)) < 1e-15 and h[0, 0] == 1.0 and n[0] == 0
+    # tau = 2: no weight update at odd stages
+    w, h, n = pgd.erwa(np.ones((1, 1)), np.zeros((1, 1)), np.ones((1, 1)), 1, 0.5, 2.0, 2)
+    assert w[0, 0] == 1.0 and h[0, 0] == 1.0
+
+
+def test_fig2_toy_annealing_reaches_global_minimum():
+    """Fig. 2: annealing 1/sigma upwards from a point between the minima ends at x = -1, y > 0."""
+    B = W._Builder(1, 1)
+    A = B.atom([0], [1], 0, W.GT)
+    B.con(W.XOR, [W.lit(0, True), W.lit(A)])
+    B.con(W.CARD_LE, [W.lit(0, True), W.lit(A, True)], param=0)
+    inst = B.freeze("fig2", np.array([-1.0]), np.array([1.0]), [-1], np.array([0.5]), 1.0)
+    cfg = pgd.Config(eta=0.05, t_max=200)
+    a = np.array([[0.3]])
+    b = np.array([[-0.2]])
+    sat, a_end, b_end = pgd.anneal(inst, a, b, cfg)
+    assert sat[0] > 0 and a_end[0, 0] < 0 and b_end[0, 0] > 0

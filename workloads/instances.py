@@ -1,0 +1,454 @@
+"""Seeded synthetic SMT(LRA) instances shaped like the paper's workloads.
+
+This module only *generates* inputs: constraint sets over Boolean variables and
+linear atoms, planted satisfying assignments, and seeded initial points. It
+holds none of the method's arithmetic (no COP, no gradient, no projection), so
+that both the FP64 oracle and the CUDA path can consume exactly the same inputs.
+
+Conventions (shared by every consumer):
+  * Boolean variables have ids 0..n_bool-1; an atom with index i has id n_bool+i.
+  * A literal is ``2*id + neg``.  A literal is true when its variable/atom is
+    true and neg == 0, or when it is false and neg == 1.
+  * A Boolean value x is +-1 with -1 meaning TRUE (the paper's convention, Cor. 1).
+  * An atom is ``sum_j coef_j * y_j  rel  q0`` with integer coefficients and
+    rel in {LE, LT, GE, GT}.
+  * Constraint kinds (the Boolean function of the literal truth values):
+      OR      at least one literal true
+      XOR     an odd number of literals true
+      CARD_LE at most ``param`` literals true
+      NAE     not all literals equal (at least one true and one false)
+      MUX     ``param`` = b selectors, then 2**b data literals; value is the
+              data literal indexed by sum_i 2**i [selector i true]
+      NEQ_OR  ``param`` = P pairs; true if some pair (l_2t, l_2t+1) differs
+              or one of the remaining literals is true
+  * A constraint never names the same variable or atom twice.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from fractions import Fraction
+
+import numpy as np
+
+# constraint kinds
+OR, XOR, CARD_LE, NAE, MUX, NEQ_OR = 0, 1, 2, 3, 4, 5
+KIND_NAMES = {OR: "OR", XOR: "XOR", CARD_LE: "CARD_LE", NAE: "NAE", MUX: "MUX", NEQ_OR: "NEQ_OR"}
+# atom relations
+LE, LT, GE, GT = 0, 1, 2, 3
+
+
+@dataclass
+class Instance:
+    name: str
+    n_bool: int
+    n_real: int
+    # box bounds on the reals (may be +-inf)
+    lo: np.ndarray
+    hi: np.ndarray
+    # atoms, CSR
+    atom_ptr: np.ndarray  # int64 [k+1]
+    atom_var: np.ndarray  # int32 [nnz]
+    atom_coef: np.ndarray  # int64 [nnz]
+    atom_q0: np.ndarray  # int64 [k]
+    atom_rel: np.ndarray  # int8 [k]
+    # constraints, CSR over literals
+    con_kind: np.ndarray  # int8 [C]
+    con_param: np.ndarray  # int32 [C]
+    con_ptr: np.ndarray  # int64 [C+1]
+    con_lits: np.ndarray  # int32 [L]
+    # a planted satisfying assignment (x in {-1,+1}, y exact as Fractions via float64)
+    planted_x: np.ndarray  # int8 [n]
+    planted_y: np.ndarray  # float64 [m] (integers or dyadic values: exact)
+    # length scale of the reals (used to scale the sigma schedule and the b-step)
+    scale: float = 1.0
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_atoms(self) -> int:
+        return len(self.atom_q0)
+
+    @property
+    def n_cons(self) -> int:
+        return len(self.con_kind)
+
+    def lits(self, c: int) -> np.ndarray:
+        return self.con_lits[self.con_ptr[c]:self.con_ptr[c + 1]]
+
+    def atom(self, i: int):
+        s, e = self.atom_ptr[i], self.atom_ptr[i + 1]
+        return self.atom_var[s:e], self.atom_coef[s:e], int(self.atom_q0[i]), int(self.atom_rel[i])
+
+
+class _Builder:
+    """Accumulates atoms and constraints, then freezes them into an Instance."""
+
+    def __init__(self, n_bool: int, n_real: int):
+        self.n_bool, self.n_real = n_bool, n_real
+        self.atom_var, self.atom_coef, self.atom_ptr = [], [], [0]
+        self.atom_q0, self.atom_rel = [], []
+        self.kind, self.param, self.lits, self.ptr = [], [], [], [0]
+
+    def atom(self, var, coef, q0, rel=LE) -> int:
+        var = [int(v) for v in var]
+        assert len(set(var)) == len(var) and len(var) > 0
+        self.atom_var += var
+        self.atom_coef += [int(c) for c in coef]
+        self.atom_ptr.append(len(self.atom_var))
+        self.atom_q0.append(int(q0))
+        self.atom_rel.append(int(rel))
+        return self.n_bool + len(self.atom_q0) - 1  # the atom's id
+
+    def con(self, kind, lits, param=0):
+        ids = [l >> 1 for l in lits]
+        assert len(set(ids)) == len(ids), "a constraint may not repeat a variable"
+        self.kind.append(kind)
+        self.param.append(int(param))
+        self.lits += [int(l) for l in lits]
+        self.ptr.append(len(self.lits))
+
+    def freeze(self, name, lo, hi, px, py, scale, **meta) -> Instance:
+        return Instance(
+            name=name, n_bool=self.n_bool, n_real=self.n_real,
+            lo=np.asarray(lo, np.float64), hi=np.asarray(hi, np.float64),
+            atom_ptr=np.asarray(self.atom_ptr, np.int64),
+            atom_var=np.asarray(self.atom_var, np.int32),
+            atom_coef=np.asarray(self.atom_coef, np.int64),
+            atom_q0=np.asarray(self.atom_q0, np.int64),
+            atom_rel=np.asarray(self.atom_rel, np.int8),
+            con_kind=np.asarray(self.kind, np.int8),
+            con_param=np.asarray(self.param, np.int32),
+            con_ptr=np.asarray(self.ptr, np.int64),
+            con_lits=np.asarray(self.lits, np.int32),
+            planted_x=np.asarray(px, np.int8), planted_y=np.asarray(py, np.float64),
+            scale=float(scale), meta=meta)
+
+
+def lit(var_id: int, neg: bool = False) -> int:
+    return 2 * int(var_id) + int(bool(neg))
+
+
+def _ceil_dot(coef, yvals) -> int:
+    """ceil(sum coef*y) computed exactly (y are float64, hence dyadic rationals)."""
+    s = sum(Fraction(int(c)) * Fraction(float(v)) for c, v in zip(coef, yvals))
+    return math.ceil(s)
+
+
+# ---------------------------------------------------------------------------
+# Tiny random SMT(LRA): 20 Booleans, 10 reals in [0,100], 200 clauses of 3 literals
+# ---------------------------------------------------------------------------
+def tiny_random(seed: int = 1001, n_bool=20, n_real=10, n_cons=200, width=3) -> Instance:
+    rng = np.random.default_rng(seed)
+    px = rng.choice(np.array([-1, 1], np.int8), n_bool)
+    py = rng.uniform(0.0, 100.0, n_real)
+    B = _Builder(n_bool, n_real)
+    for _ in range(n_cons):
+        lits, truth = [], []
+        used_bool = set()
+        for _t in range(width):
+            if rng.random() < 0.5:
+                v = int(rng.integers(n_bool))
+                while v in used_bool:
+                    v = int(rng.integers(n_bool))
+                used_bool.add(v)
+                neg = bool(rng.integers(2))
+                lits.append(lit(v, neg))
+                truth.append((px[v] == -1) != neg)
+            else:
+                nnz = int(rng.integers(2, 5))
+                var = rng.choice(n_real, nnz, replace=False)
+                coef = rng.integers(1, 11, nnz) * rng.choice([-1, 1], nnz)
+                q0 = _ceil_dot(coef, py[var])  # the atom holds at the plant
+                aid = B.atom(var, coef, q0, LE)
+                neg = bool(rng.integers(2))
+                lits.append(lit(aid, neg))
+                truth.append(not neg)
+        if not any(truth):  # make the plant satisfy the clause
+            lits[0] ^= 1
+        B.con(OR, lits)
+    return B.freeze("tiny_random", np.zeros(n_real), np.full(n_real, 100.0), px, py, 100.0,
+                    seed=seed)
+
+
+# ---------------------------------------------------------------------------
+# Job-shop scheduling with Boolean order selectors
+# ---------------------------------------------------------------------------
+def _jobshop_into(B: _Builder, rng, n_jobs, n_mach, dur_max, bool_base, real_base, px, py):
+    """Adds one job-shop instance to builder B.  Returns (horizon, n_bool_used, n_real_used)."""
+    order = [rng.permutation(n_mach) for _ in range(n_jobs)]
+    dur = rng.integers(1, dur_max + 1, (n_jobs, n_mach))
+    sidx = lambda j, k: real_base + j * n_mach + k  # real var of the k-th operation of job j
+    # planted schedule by greedy list scheduling (operation rank major, jobs in random order)
+    start = np.zeros((n_jobs, n_mach), np.int64)
+    job_ready = np.zeros(n_jobs, np.int64)
+    mach_ready = np.zeros(n_mach, np.int64)
+    for k in range(n_mach):
+        for j in rng.permutation(n_jobs):
+            mch = order[j][k]
+            s = max(job_ready[j], mach_ready[mch])
+            start[j, k] = s
+            job_ready[j] = mach_ready[mch] = s + dur[j, k]
+    H = int(math.ceil(1.2 * int(job_ready.max())))
+    for j in range(n_jobs):
+        for k in range(n_mach):
+            py[sidx(j, k)] = float(start[j, k])
+    # unit atoms: 0 <= s and s + d <= H
+    for j in range(n_jobs):
+        for k in range(n_mach):
+            a0 = B.atom([sidx(j, k)], [-1], 0, LE)
+            B.con(OR, [lit(a0)])
+            a1 = B.atom([sidx(j, k)], [1], H - int(dur[j, k]), LE)
+            B.con(OR, [lit(a1)])
+    # precedence along each job: s_k + d_k <= s_{k+1}
+    for j in range(n_jobs):
+        for k in range(n_mach - 1):
+            a = B.atom([sidx(j, k), sidx(j, k + 1)], [1, -1], -int(dur[j, k]), LE)
+            B.con(OR, [lit(a)])
+    # same-machine pairs with an order selector o: o -> (i before j), not o -> (j before i)
+    ops_on = [[] for _ in range(n_mach)]
+    for j in range(n_jobs):
+        for k in range(n_mach):
+            ops_on[order[j][k]].append((j, k))
+    nb = 0
+    for mch in range(n_mach):
+        ops = ops_on[mch]
+        for u in range(len(ops)):
+            for v in range(u + 1, len(ops)):
+                (ji, ki), (jj, kj) = ops[u], ops[v]
+                o = bool_base + nb
+                nb += 1
+                si, sj = sidx(ji, ki), sidx(jj, kj)
+                di, dj = int(dur[ji, ki]), int(dur[jj, kj])
+                a_ij = B.atom([si, sj], [1, -1], -di, LE)  # s_i + d_i <= s_j
+                a_ji = B.atom([sj, si], [1, -1], -dj, LE)  # s_j + d_j <= s_i
+                B.con(OR, [lit(o, True), lit(a_ij)])
+                B.con(OR, [lit(o, False), lit(a_ji)])
+                px[o] = -1 if start[ji, ki] < start[jj, kj] else 1
+    return H, nb, n_jobs * n_mach
+
+
+def jobshop(seed: int = 1002, n_jobs=40, n_mach=10, dur_max=20) -> Instance:
+    rng = np.random.default_rng(seed)
+    n_bool = n_mach * n_jobs * (n_jobs - 1) // 2
+    n_real = n_jobs * n_mach
+    B = _Builder(n_bool, n_real)
+    px = np.ones(n_bool, np.int8)
+    py = np.zeros(n_real)
+    H, nb, nr = _jobshop_into(B, rng, n_jobs, n_mach, dur_max, 0, 0, px, py)
+    assert nb == n_bool and nr == n_real
+    lo = np.zeros(n_real)
+    hi = np.full(n_real, float(H))
+    return B.freeze("jobshop", lo, hi, px, py, float(dur_max), seed=seed, horizon=H,
+                    n_jobs=n_jobs, n_mach=n_mach)
+
+
+def uneven_batch(seed: int = 1004, n_inst=64, jobs=(5, 60), machines=(3, 15), dur_max=20):
+    """A list of job-shop instances of very different sizes (one per batch member)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for t in range(n_inst):
+        nj = int(rng.integers(jobs[0], jobs[1] + 1))
+        nm = int(rng.integers(machines[0], machines[1] + 1))
+        out.append(jobshop(seed * 1000 + t, nj, nm, dur_max))
+    return out
+
+
+# ---------------------------------------------------------------------------
+# 2D placement with Boolean selectors
+# ---------------------------------------------------------------------------
+def placement2d(seed: int = 1003, n_rect=400, dim_max=30, selectors=True) -> Instance:
+    redraws = 0
+    while True:
+        rng = np.random.default_rng(seed + 7919 * redraws)
+        w = rng.integers(1, dim_max + 1, n_rect)
+        h = rng.integers(1, dim_max + 1, n_rect)
+        L = int(math.ceil(math.sqrt(1.3 * float((w * h).sum()))))
+        # shelf packing plant: tallest first, left to right, shelves upwards
+        order = np.argsort(-h, kind="stable")
+        X = np.zeros(n_rect, np.int64)
+        Y = np.zeros(n_rect, np.int64)
+        cx, cy, shelf_h, ok = 0, 0, 0, True
+        for i in order:
+            if cx + w[i] > L:
+                cy += shelf_h
+                cx, shelf_h = 0, 0
+            X[i], Y[i] = cx, cy
+            cx += w[i]
+            shelf_h = max(shelf_h, int(h[i]))
+            if cy + h[i] > L:
+                ok = False
+                break
+        if ok:
+            break
+        redraws += 1
+    n_real = 2 * n_rect
+    n_pairs = n_rect * (n_rect - 1) // 2
+    n_bool = 2 * n_pairs if selectors else 0
+    B = _Builder(n_bool, n_real)
+    xv = lambda i: 2 * i
+    yv = lambda i: 2 * i + 1
+    py = np.zeros(n_real)
+    for i in range(n_rect):
+        py[xv(i)], py[yv(i)] = float(X[i]), float(Y[i])
+    px = np.ones(n_bool, np.int8)
+    # feasibility: 0 <= x <= L - w, 0 <= y <= L - h  (unit atoms)
+    for i in range(n_rect):
+        for v, size in ((xv(i), w[i]), (yv(i), h[i])):
+            B.con(OR, [lit(B.atom([v], [-1], 0, LE))])
+            B.con(OR, [lit(B.atom([v], [1], L - int(size), LE))])
+    p = 0
+    for i in range(n_rect):
+        for j in range(i + 1, n_rect):
+            A1 = B.atom([xv(i), xv(j)], [1, -1], -int(w[i]), LE)  # x_i + w_i <= x_j
+            A2 = B.atom([xv(j), xv(i)], [1, -1], -int(w[j]), LE)  # x_j + w_j <= x_i
+            A3 = B.atom([yv(i), yv(j)], [1, -1], -int(h[i]), LE)  # y_i + h_i <= y_j
+            A4 = B.atom([yv(j), yv(i)], [1, -1], -int(h[j]), LE)  # y_j + h_j <= y_i
+            holds = [X[i] + w[i] <= X[j], X[j] + w[j] <= X[i], Y[i] + h[i] <= Y[j], Y[j] + h[j] <= Y[i]]
+            if selectors:
+                u, v = 2 * p, 2 * p + 1
+                # ITE(u, ITE(v, A1, A2), ITE(v, A3, A4)) as a MUX with index [u] + 2[v]:
+                #   idx 0 (u F, v F) -> A4, 1 (u T, v F) -> A2, 2 (u F, v T) -> A3, 3 (u T, v T) -> A1
+                B.con(MUX, [lit(u), lit(v), lit(A4), lit(A2), lit(A3), lit(A1)], param=2)
+                k = int(np.argmax(holds))  # which disjunct the plant uses
+                uT, vT = {0: (True, True), 1: (True, False), 2: (False, True), 3: (False, False)}[k]
+                px[u] = -1 if uT else 1
+                px[v] = -1 if vT else 1
+            else:
+                B.con(OR, [lit(A1), lit(A2), lit(A3), lit(A4)])
+            p += 1
+    lo = np.zeros(n_real)
+    hi = np.full(n_real, float(L))
+    return B.freeze("placement2d" + ("" if selectors else "_nosel"), lo, hi, px, py, float(dim_max),
+                    seed=seed, redraws=redraws, die=L)
+
+
+# ---------------------------------------------------------------------------
+# Large continuous-time scheduling (worker-index bits, pairwise non-overlap)
+# ---------------------------------------------------------------------------
+def large_scheduling(seed: int = 1005, n_workers=256, n_jobs=1111, dur_max=20,
+                     n_late=72, late_max=10, chain_max=3) -> Instance:
+    """The paper's scheduling encoding at ~10k variables / ~0.7M constraints.
+
+    Per job j: worker-index bits x_{i,j} (log2 n_workers of them) and a start time y_j.
+    Constraints: per-pair non-overlap  OR_i (x_{i,j} xor x_{i,j'}) OR (y_j - y_j' >= t_j')
+    OR (y_j' - y_j >= t_j); precedence y_j >= y_j' + t_j' inside short job chains;
+    release/deadline unit atoms 0 <= y_j, y_j + t_j <= T; and, for each of ``n_late``
+    workers that start late at d_w, per job: (X_j != w) OR (y_j >= d_w).
+    """
+    rng = np.random.default_rng(seed)
+    bits = int(round(math.log2(n_workers)))
+    assert 1 << bits == n_workers
+    n_bool = bits * n_jobs
+    n_real = n_jobs
+    t = rng.integers(1, dur_max + 1, n_jobs)
+    d = np.zeros(n_workers, np.int64)
+    late = rng.choice(n_workers, n_late, replace=False)
+    d[late] = rng.integers(1, late_max + 1, n_late)
+    # precedence: jobs form chains of 1..chain_max consecutive jobs
+    pred = -np.ones(n_jobs, np.int64)
+    j = 0
+    while j < n_jobs:
+        ln = int(rng.integers(1, chain_max + 1))
+        for q in range(j + 1, min(j + ln, n_jobs)):
+            pred[q] = q - 1
+        j += ln
+    # planted greedy schedule: each job to the worker where it can start earliest
+    free = d.copy()
+    Y = np.zeros(n_jobs, np.int64)
+    W = np.zeros(n_jobs, np.int64)
+    for j in range(n_jobs):
+        ready = 0 if pred[j] < 0 else Y[pred[j]] + t[pred[j]]
+        st = np.maximum(free, ready)
+        w = int(np.argmin(st))
+        Y[j], W[j] = st[w], w
+        free[w] = st[w] + t[j]
+    T = int(math.ceil(1.2 * int((Y + t).max())))
+    xb = lambda i, j: j * bits + i  # Boolean id of bit i of job j
+    B = _Builder(n_bool, n_real)
+    px = np.ones(n_bool, np.int8)
+    for j in range(n_jobs):
+        for i in range(bits):
+            px[xb(i, j)] = -1 if (W[j] >> i) & 1 else 1
+    py = Y.astype(np.float64)
+    # non-overlap for every pair
+    for j in range(n_jobs):
+        for k in range(j + 1, n_jobs):
+            A1 = B.atom([k, j], [1, -1], -int(t[k]), LE)  # y_j - y_k >= t_k
+            A2 = B.atom([j, k], [1, -1], -int(t[j]), LE)  # y_k - y_j >= t_j
+            lits = []
+            for i in range(bits):
+                lits += [lit(xb(i, j)), lit(xb(i, k))]
+            B.con(NEQ_OR, lits + [lit(A1), lit(A2)], param=bits)
+    # precedence
+    for j in range(n_jobs):
+        if pred[j] >= 0:
+            B.con(OR, [lit(B.atom([int(pred[j]), j], [1, -1], -int(t[pred[j]]), LE))])
+    # release / deadline
+    for j in range(n_jobs):
+        B.con(OR, [lit(B.atom([j], [-1], 0, LE))])
+        B.con(OR, [lit(B.atom([j], [1], T - int(t[j]), LE))])
+    # late workers: (X_j != w) OR (y_j >= d_w)
+    for w in late:
+        for j in range(n_jobs):
+            lits = [lit(xb(i, j), neg=bool((int(w) >> i) & 1)) for i in range(bits)]
+            lits.append(lit(B.atom([j], [-1], -int(d[w]), LE)))
+            B.con(OR, lits)
+    lo = np.zeros(n_real)
+    hi = np.full(n_real, float(T))
+    return B.freeze("large_scheduling", lo, hi, px, py, float(dur_max), seed=seed, horizon=T,
+                    n_workers=n_workers, n_jobs=n_jobs, n_late=n_late)
+
+
+def concat(instances, name="batch") -> Instance:
+    """Block-diagonal union of instances (disjoint variables), for batched solving.
+
+    meta['bool_base'], meta['real_base'], meta['con_base'] give each member's offsets.
+    """
+    n_bool = sum(I.n_bool for I in instances)
+    n_real = sum(I.n_real for I in instances)
+    B = _Builder(n_bool, n_real)
+    bb, rb, cb = [0], [0], [0]
+    for I in instances:
+        boff, roff, aoff_new = bb[-1], rb[-1], None
+        atom_map = {}
+        for i in range(I.n_atoms):
+            var, coef, q0, rel = I.atom(i)
+            atom_map[I.n_bool + i] = B.atom(var + roff, coef, q0, rel)
+        for c in range(I.n_cons):
+            ls = []
+            for l in I.lits(c):
+                vid, neg = int(l) >> 1, int(l) & 1
+                nid = vid + boff if vid < I.n_bool else atom_map[vid]
+                ls.append(2 * nid + neg)
+            B.con(int(I.con_kind[c]), ls, int(I.con_param[c]))
+        bb.append(boff + I.n_bool)
+        rb.append(roff + I.n_real)
+        cb.append(cb[-1] + I.n_cons)
+    return B.freeze(name, np.concatenate([I.lo for I in instances]),
+                    np.concatenate([I.hi for I in instances]),
+                    np.concatenate([I.planted_x for I in instances]),
+                    np.concatenate([I.planted_y for I in instances]),
+                    max(I.scale for I in instances),
+                    bool_base=bb, real_base=rb, con_base=cb, members=len(instances))
+
+
+# ---------------------------------------------------------------------------
+# Seeded initial points (restart-minor layout [var][R], float32)
+# ---------------------------------------------------------------------------
+def initial_point(inst: Instance, R: int, seed: int = 7):
+    """a ~ U(-1,1); b_j ~ U(lo_j, hi_j) (U(0, scale) where a bound is infinite)."""
+    rng = np.random.default_rng(seed)
+    a = rng.uniform(-1.0, 1.0, (inst.n_bool, R)).astype(np.float32)
+    lo = np.where(np.isfinite(inst.lo), inst.lo, 0.0)
+    hi = np.where(np.isfinite(inst.hi), inst.hi, lo + inst.scale)
+    b = (lo[:, None] + (hi - lo)[:, None] * rng.random((inst.n_real, R))).astype(np.float32)
+    return a, b
+
+
+CONFIGS = {
+    "tiny_random": dict(make=lambda: tiny_random(1001), R=64),
+    "jobshop": dict(make=lambda: jobshop(1002), R=256),
+    "placement2d": dict(make=lambda: placement2d(1003), R=1024),
+    "uneven_batch": dict(make=lambda: concat(uneven_batch(1004), "uneven_batch"), R=32),
+    "large_scheduling": dict(make=lambda: large_scheduling(1005), R=512),
+}
