@@ -139,27 +139,8 @@ def kind_value_vec(kind, param, T):
 
 
 def atom_truth_exact(inst, i, y):
-    """Exact truth of atom i at each restart's reals y [m][R] (float values).
-
-    A float64 evaluation decides the sign when it is far from zero relative to
-    a bound on its rounding error; otherwise the sign is computed in Fractions.
-    """
-    var, coef, q0, rel = inst.atom(i)
-    yv = np.asarray(y, np.float64)[np.asarray(var, np.int64)]
-    q = np.asarray(coef, np.float64)[:, None]
-    s = (q * yv).sum(0) - float(q0)
-    mag = (np.abs(q * yv)).sum(0) + abs(float(q0))
-    unsure = np.abs(s) <= 1e-12 * mag
-    for r in np.nonzero(unsure)[0]:
-        s[r] = float(sum(Fraction(int(c)) * Fraction(float(v)) for c, v in zip(coef, yv[:, r]))
-                     - Fraction(int(q0)))
-    if rel == S.LE:
-        return s <= 0
-    if rel == S.LT:
-        return s < 0
-    if rel == S.GE:
-        return s >= 0
-    return s > 0
+    """Exact truth of atom i at each restart's reals y [m][R]."""
+    return S.atom_truth_batch(inst, i, y)
 
 
 def round_check(inst, a, b, constraints=None):

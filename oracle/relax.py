@@ -12,7 +12,7 @@
   "Smoothness"); the printed formula in Suppl. Note "Expectation" has a garbled
   exponent denominator.  GE/GT atoms are negated into LE/LT form first.
   sigma = 0 is the unsmoothed indicator (Thm. expectation, sigma^2 = 0 case):
-  p = [z <= 0] (or [z < 0] for a strict atom) and dd/db = 0.
+  p = [z <= 0] (or [z < 0] for a strict atom), decided exactly, and dd/db = 0.
   p is evaluated with erfc rather than 1 - erf so that tails keep their
   relative accuracy (mathematically identical).
 
@@ -44,8 +44,8 @@ def atom_terms(inst, i, b, sigma):
     coef, q0, strict = S.normalized_atom(coef, q0, rel)
     q = np.asarray(coef, np.float64)
     z = sum(q[t] * np.asarray(b[int(var[t])], np.float64) for t in range(len(q))) - float(q0)
-    if sigma == 0.0:
-        p = (z < 0).astype(np.float64) if strict else (z <= 0).astype(np.float64)
+    if sigma == 0.0:  # the indicator itself, decided exactly
+        p = S.atom_truth_batch(inst, i, b).astype(np.float64)
         return p, [(int(var[t]), np.zeros_like(z)) for t in range(len(q))]
     s = sigma * math.sqrt(float((q * q).sum()))
     u = z / (SQRT2 * s)

@@ -12,6 +12,8 @@ arithmetic (Python Fractions), the textbook meaning of the relation.
 """
 from fractions import Fraction
 
+import numpy as np
+
 OR, XOR, CARD_LE, NAE, MUX, NEQ_OR = 0, 1, 2, 3, 4, 5
 LE, LT, GE, GT = 0, 1, 2, 3
 
@@ -76,3 +78,27 @@ def constraint_holds(inst, c, x, y) -> bool:
 def unsat_constraints(inst, x, y):
     """Indices of the constraints violated by (x, y), all decided exactly."""
     return [c for c in range(inst.n_cons) if not constraint_holds(inst, c, x, y)]
+
+
+def atom_truth_batch(inst, i, y):
+    """Exact truth of atom i at each column of reals y [m][R] (float values).
+
+    A float64 evaluation decides the sign when it is far from zero relative to
+    a bound on its rounding error; otherwise the sign is computed in Fractions.
+    """
+    var, coef, q0, rel = inst.atom(i)
+    yv = np.asarray(y, np.float64)[np.asarray(var, np.int64)]
+    q = np.asarray(coef, np.float64)[:, None]
+    s = (q * yv).sum(0) - float(q0)
+    mag = (np.abs(q * yv)).sum(0) + abs(float(q0))
+    unsure = np.abs(s) <= 1e-12 * mag
+    for r in np.nonzero(unsure)[0]:
+        fr = sum(Fraction(int(c)) * Fraction(float(v)) for c, v in zip(coef, yv[:, r])) - Fraction(int(q0))
+        s[r] = float((fr > 0) - (fr < 0))  # the exact sign
+    if rel == LE:
+        return s <= 0
+    if rel == LT:
+        return s < 0
+    if rel == GE:
+        return s >= 0
+    return s > 0

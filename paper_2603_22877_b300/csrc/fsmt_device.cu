@@ -1,0 +1,966 @@
+// Device side of the C ABI: upload, the relaxed-objective kernels (fused and
+// plain forms), the PGD step with projection, rounding + exact check + ERWA, and
+// one annealing stage replayed from a CUDA graph.  sm_103a.
+//
+// Layout: restart-minor.  Lane l of a warp works on restart 32*t + l of restart
+// tile t, so every per-restart access of a warp is one contiguous 128-byte line,
+// while the diagram structure a warp reads is the same for all its lanes.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "fsmt_internal.h"
+
+namespace fsmt {
+
+namespace {
+
+constexpr float kTwoOverSqrtPi = 1.1283791670955126f;
+constexpr float kInvSqrt2 = 0.70710678118654752f;
+constexpr int kFusedThreads = 256;  // 8 warps
+constexpr int kSmemBudget = 112 * 1024;
+constexpr int kMaxObjSmemR = 4096;
+
+// stage parameter slots (device float[16])
+enum { P_SIGMA = 0, P_ETA, P_BSCALE, P_EPS, P_RHO, P_GAMMA, P_UPDATE_W, P_SWEEPS };
+
+fsmt_status cuda_fail(cudaError_t e, const char* what) {
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return FSMT_ECUDA;
+}
+
+#define FSMT_CUDA(call, what)                      \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+inline size_t fused_warp_bytes(int vcap) { return (size_t)vcap * 8 + (size_t)(3 * vcap + 2) * 32 * 4; }
+
+struct FusedShape {
+  int warps;
+  int vcap;
+  size_t smem;
+};
+
+FusedShape fused_shape(const Compiled& C, int R) {
+  FusedShape f;
+  f.vcap = std::max(1, C.max_nodes);
+  size_t wb = fused_warp_bytes(f.vcap);
+  int w = (int)std::min<size_t>(kFusedThreads / 32, std::max<size_t>(1, kSmemBudget / wb));
+  f.warps = w;
+  f.smem = wb * w + (R <= kMaxObjSmemR ? (size_t)R * 4 : 0);
+  return f;
+}
+
+// ------------------------------------------------------- literal probability --
+// p = P[variable TRUE]; gz = dd/dz for atoms (0 for Booleans).  Eq. rounding and
+// Eq. sampling; sigma = 0 decides the atom exactly.
+__device__ __forceinline__ void literal_prob(const DevView& d, int lab, int R, int r, bool ok, float s_inv,
+                                             const float* __restrict__ a, const float* __restrict__ b, float& p,
+                                             float& gz) {
+  if (lab < d.n_bool) {
+    float av = ok ? __ldg(a + (size_t)lab * R + r) : 0.f;
+    p = 0.5f * (1.f - av);
+    gz = 0.f;
+    return;
+  }
+  const int i = lab - d.n_bool;
+  const int k0 = __ldg(d.atom_ptr + i), k1 = __ldg(d.atom_ptr + i + 1);
+  if (s_inv > 0.f) {
+    float z = -__ldg(d.atom_q0f + i);
+    for (int k = k0; k < k1; ++k) {
+      float bv = ok ? __ldg(b + (size_t)__ldg(d.atom_var + k) * R + r) : 0.f;
+      z = fmaf(__ldg(d.atom_coef + k), bv, z);
+    }
+    const float si = __ldg(d.atom_inv_norm + i) * s_inv;  // 1 / (sqrt(2) sigma ||q||)
+    const float u = z * si;
+    p = 0.5f * erfcf(u);
+    gz = kTwoOverSqrtPi * __expf(-u * u) * si;
+  } else {
+    Fixed320 acc;
+    acc.clear();
+    for (int k = k0; k < k1; ++k) {
+      float bv = ok ? __ldg(b + (size_t)__ldg(d.atom_var + k) * R + r) : 0.f;
+      uint32_t m;
+      int e;
+      bool neg;
+      float_parts(bv, m, e, neg);
+      if (m == 0) continue;
+      float c = __ldg(d.atom_coef + k);
+      bool cneg = c < 0.f;
+      acc.add((uint64_t)(cneg ? -c : c) * (uint64_t)m, e + 149, neg != cneg);
+    }
+    double q0 = __ldg(d.atom_q0d + i);
+    if (q0 != 0.0) acc.add((uint64_t)fabs(q0), 149, q0 > 0.0);
+    const int sg = acc.sign();
+    const bool truth = __ldg(d.atom_strict + i) ? sg < 0 : sg <= 0;
+    p = truth ? 1.f : 0.f;
+    gz = 0.f;
+  }
+}
+
+__device__ __forceinline__ bool literal_truth_exact(const DevView& d, int lab, int R, int r,
+                                                    const float* __restrict__ a, const float* __restrict__ b) {
+  if (lab < d.n_bool) return __ldg(a + (size_t)lab * R + r) < 0.f;
+  float p, gz;
+  literal_prob(d, lab, R, r, true, 0.f, a, b, p, gz);
+  return p > 0.5f;
+}
+
+__device__ __forceinline__ void scatter_grad(const DevView& d, int lab, int R, int r, float g, float gz,
+                                             float* __restrict__ grad_a, float* __restrict__ grad_b) {
+  if (lab < d.n_bool) {
+    atomicAdd(grad_a + (size_t)lab * R + r, g);
+  } else {
+    const int i = lab - d.n_bool;
+    const float gg = g * gz;
+    if (gg != 0.f) {
+      const int k0 = __ldg(d.atom_ptr + i), k1 = __ldg(d.atom_ptr + i + 1);
+      for (int k = k0; k < k1; ++k)
+        atomicAdd(grad_b + (size_t)__ldg(d.atom_var + k) * R + r, gg * __ldg(d.atom_coef + k));
+    }
+  }
+}
+
+__device__ __forceinline__ float load_param(const float* prm, int slot, float fallback) {
+  return prm ? prm[slot] : fallback;
+}
+
+// ---------------------------------------------------------- fused kernel --
+// One warp per constraint of C_sigma (grid-stride), looping over restart tiles;
+// the constraint's nodes are staged once in the warp's shared memory and reused
+// for every tile.  Per lane: Alg. 3 (top-down messages m_td), then, if ADJ,
+// Alg. 4 (bottom-up messages m_bu written over m_td in reverse topological
+// order, so one array serves both) with the gradient scattered by atomics.
+template <bool ADJ>
+__global__ void __launch_bounds__(kFusedThreads) k_fused(DevView d, int R, float sigma, const float* prm, int vcap,
+                                                         const float* __restrict__ w, const float* __restrict__ a,
+                                                         const float* __restrict__ b, float* __restrict__ grad_a,
+                                                         float* __restrict__ grad_b, float* __restrict__ obj,
+                                                         float* __restrict__ cop, const int* ctl) {
+  if (ctl && ctl[0] == 0) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
+  const size_t wb = (size_t)vcap * 8 + (size_t)(3 * vcap + 2) * 128;
+  uint2* snode = reinterpret_cast<uint2*>(smem + warp * wb);
+  float* sp = reinterpret_cast<float*>(snode + vcap);
+  float* sg = sp + vcap * 32;
+  float* sm = sg + vcap * 32;
+  float* obj_s = (R <= kMaxObjSmemR) ? reinterpret_cast<float*>(smem + W * wb) : nullptr;
+  if (obj_s) {
+    for (int r = threadIdx.x; r < R; r += blockDim.x) obj_s[r] = 0.f;
+    __syncthreads();
+  }
+  sigma = load_param(prm, P_SIGMA, sigma);
+  const float s_inv = sigma > 0.f ? kInvSqrt2 / sigma : 0.f;
+  const int n_tiles = (R + 31) >> 5;
+  for (int s = blockIdx.x * W + warp; s < d.n_obj; s += gridDim.x * W) {
+    const int nb = __ldg(d.con_ptr + s);
+    const int V = __ldg(d.con_ptr + s + 1) - nb;
+    const int cid = __ldg(d.con_id + s);
+    const int root = __ldg(d.con_root + s);
+    for (int i = lane; i < V; i += 32) snode[i] = d.nodes[nb + i];
+    __syncwarp();
+    for (int t = 0; t < n_tiles; ++t) {
+      const int r = t * 32 + lane;
+      const bool ok = r < R;
+      for (int v = 0; v < V + 2; ++v) sm[v * 32 + lane] = 0.f;
+      sm[root * 32 + lane] = 1.f;
+      for (int v = 0; v < V; ++v) {  // Alg. 3, topological order
+        const uint2 nd = snode[v];
+        const int hi = nd.y & 0xffff, lo = nd.y >> 16;
+        float p, gz;
+        literal_prob(d, (int)nd.x, R, r, ok, s_inv, a, b, p, gz);
+        sp[v * 32 + lane] = p;
+        if (ADJ) sg[v * 32 + lane] = gz;
+        const float mv = sm[v * 32 + lane];
+        sm[hi * 32 + lane] = fmaf(p, mv, sm[hi * 32 + lane]);
+        sm[lo * 32 + lane] = fmaf(1.f - p, mv, sm[lo * 32 + lane]);
+      }
+      const float cp = sm[V * 32 + lane];
+      const float wc = ok ? __ldg(w + (size_t)cid * R + r) : 0.f;
+      if (ok) {
+        if (cop) cop[(size_t)cid * R + r] = cp;
+        const float contrib = wc * (1.f - 2.f * cp);
+        if (obj) {
+          if (obj_s)
+            atomicAdd(obj_s + r, contrib);
+          else
+            atomicAdd(obj + r, contrib);
+        }
+      }
+      if (ADJ) {  // Alg. 4, reverse topological order
+        sm[V * 32 + lane] = 1.f;
+        sm[(V + 1) * 32 + lane] = 0.f;
+        for (int v = V - 1; v >= 0; --v) {
+          const uint2 nd = snode[v];
+          const int hi = nd.y & 0xffff, lo = nd.y >> 16;
+          const float mh = sm[hi * 32 + lane], ml = sm[lo * 32 + lane];
+          const float p = sp[v * 32 + lane];
+          const float td = sm[v * 32 + lane];
+          const float diff = mh - ml;
+          sm[v * 32 + lane] = fmaf(p, diff, ml);
+          if (ok) scatter_grad(d, (int)nd.x, R, r, wc * td * diff, sg[v * 32 + lane], grad_a, grad_b);
+        }
+      }
+    }
+    __syncwarp();
+  }
+  if (obj_s && obj) {
+    __syncthreads();
+    for (int r = threadIdx.x; r < R; r += blockDim.x)
+      if (obj_s[r] != 0.f) atomicAdd(obj + r, obj_s[r]);
+  }
+}
+
+// ------------------------------------------------------------ plain form --
+// Separate kernels; every node's message lives in global memory (work) between
+// the passes: work = m [(n_obj_nodes + 2 n_obj) x R] | p_atom [K x R] | gz [K x R].
+__global__ void k_atoms_plain(DevView d, int R, float sigma, const float* __restrict__ b, float* __restrict__ p_atom,
+                              float* __restrict__ gz_atom) {
+  const int r = blockIdx.x * 32 + threadIdx.x;
+  const bool ok = r < R;
+  const float s_inv = sigma > 0.f ? kInvSqrt2 / sigma : 0.f;
+  for (int i = blockIdx.y * blockDim.y + threadIdx.y; i < d.n_atoms; i += gridDim.y * blockDim.y) {
+    float p, gz;
+    literal_prob(d, d.n_bool + i, R, r, ok, s_inv, nullptr, b, p, gz);
+    if (ok) {
+      p_atom[(size_t)i * R + r] = p;
+      gz_atom[(size_t)i * R + r] = gz;
+    }
+  }
+}
+
+__device__ __forceinline__ float plain_prob(const DevView& d, int lab, int R, int r, bool ok, const float* a,
+                                            const float* p_atom) {
+  if (!ok) return 0.f;
+  if (lab < d.n_bool) return 0.5f * (1.f - a[(size_t)lab * R + r]);
+  return p_atom[(size_t)(lab - d.n_bool) * R + r];
+}
+
+__global__ void k_fwd_plain(DevView d, int R, const float* __restrict__ w, const float* __restrict__ a,
+                            const float* __restrict__ p_atom, float* __restrict__ m, float* __restrict__ cop,
+                            float* __restrict__ obj) {
+  const int lane = threadIdx.x & 31;
+  const int W = blockDim.x >> 5;
+  const int n_tiles = (R + 31) >> 5;
+  for (int s = blockIdx.x * W + (threadIdx.x >> 5); s < d.n_obj; s += gridDim.x * W) {
+    const int nb = d.con_ptr[s];
+    const int V = d.con_ptr[s + 1] - nb;
+    const int cid = d.con_id[s];
+    float* ms = m + (size_t)(nb + 2 * s) * R;
+    for (int t = 0; t < n_tiles; ++t) {
+      const int r = t * 32 + lane;
+      const bool ok = r < R;
+      if (!ok) continue;
+      for (int v = 0; v < V + 2; ++v) ms[(size_t)v * R + r] = 0.f;
+      ms[(size_t)d.con_root[s] * R + r] = 1.f;
+      for (int v = 0; v < V; ++v) {
+        const uint2 nd = d.nodes[nb + v];
+        const int hi = nd.y & 0xffff, lo = nd.y >> 16;
+        const float p = plain_prob(d, (int)nd.x, R, r, ok, a, p_atom);
+        const float mv = ms[(size_t)v * R + r];
+        ms[(size_t)hi * R + r] += p * mv;
+        ms[(size_t)lo * R + r] += (1.f - p) * mv;
+      }
+      const float cp = ms[(size_t)V * R + r];
+      if (cop) cop[(size_t)cid * R + r] = cp;
+      if (obj) atomicAdd(obj + r, w[(size_t)cid * R + r] * (1.f - 2.f * cp));
+    }
+  }
+}
+
+__global__ void k_adj_plain(DevView d, int R, const float* __restrict__ w, const float* __restrict__ a,
+                            const float* __restrict__ p_atom, const float* __restrict__ gz_atom,
+                            float* __restrict__ m, float* __restrict__ grad_a, float* __restrict__ grad_b) {
+  const int lane = threadIdx.x & 31;
+  const int W = blockDim.x >> 5;
+  const int n_tiles = (R + 31) >> 5;
+  for (int s = blockIdx.x * W + (threadIdx.x >> 5); s < d.n_obj; s += gridDim.x * W) {
+    const int nb = d.con_ptr[s];
+    const int V = d.con_ptr[s + 1] - nb;
+    const int cid = d.con_id[s];
+    float* ms = m + (size_t)(nb + 2 * s) * R;
+    for (int t = 0; t < n_tiles; ++t) {
+      const int r = t * 32 + lane;
+      if (r >= R) continue;
+      const float wc = w[(size_t)cid * R + r];
+      ms[(size_t)V * R + r] = 1.f;
+      ms[(size_t)(V + 1) * R + r] = 0.f;
+      for (int v = V - 1; v >= 0; --v) {
+        const uint2 nd = d.nodes[nb + v];
+        const int hi = nd.y & 0xffff, lo = nd.y >> 16;
+        const float p = plain_prob(d, (int)nd.x, R, r, true, a, p_atom);
+        const float mh = ms[(size_t)hi * R + r], ml = ms[(size_t)lo * R + r];
+        const float td = ms[(size_t)v * R + r];
+        const float diff = mh - ml;
+        ms[(size_t)v * R + r] = p * mh + (1.f - p) * ml;
+        const int lab = (int)nd.x;
+        const float gz = lab < d.n_bool ? 0.f : gz_atom[(size_t)(lab - d.n_bool) * R + r];
+        scatter_grad(d, lab, R, r, wc * td * diff, gz, grad_a, grad_b);
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------- PGD step --
+// Eq. pg1 / pg2 with the b-step scaled by b_scale^2, projection onto D, and the
+// per-restart ||g||^2 of Eq. grad_map.  Block = 32 restarts x 8 row groups.
+__device__ __forceinline__ void reduce_rows_add(float part, float* gn2, int r, bool ok) {
+  __shared__ float red[8][33];
+  red[threadIdx.y][threadIdx.x] = part;
+  __syncthreads();
+  if (threadIdx.y == 0) {
+    float s = 0.f;
+    for (int y = 0; y < (int)blockDim.y; ++y) s += red[y][threadIdx.x];
+    if (ok && s != 0.f) atomicAdd(gn2 + r, s);
+  }
+}
+
+__global__ void k_pgd_bool(DevView d, int R, float eta, const float* prm, float* __restrict__ a,
+                           float* __restrict__ ga, float* __restrict__ gn2, const uint8_t* __restrict__ active,
+                           int clear_grad, const int* ctl) {
+  if (ctl && ctl[0] == 0) return;
+  eta = load_param(prm, P_ETA, eta);
+  const int r = blockIdx.x * 32 + threadIdx.x;
+  const bool ok = r < R;
+  const bool act = ok && (!active || active[r]);
+  float part = 0.f;
+  if (ok) {
+    for (int i = blockIdx.y * blockDim.y + threadIdx.y; i < d.n_bool; i += gridDim.y * blockDim.y) {
+      const size_t k = (size_t)i * R + r;
+      const float av = a[k];
+      const float g = ga[k];
+      const float an = fminf(fmaxf(av - eta * g, -1.f), 1.f);
+      const float q = (av - an) / eta;
+      part = fmaf(q, q, part);
+      if (act) a[k] = an;
+      if (clear_grad) ga[k] = 0.f;
+    }
+  }
+  reduce_rows_add(part, gn2, r, ok);
+}
+
+__global__ void k_pgd_free(DevView d, int R, float eta, float bscale, const float* prm, float* __restrict__ b,
+                           float* __restrict__ gb, float* __restrict__ gn2, const uint8_t* __restrict__ active,
+                           int clear_grad, const int* ctl) {
+  if (ctl && ctl[0] == 0) return;
+  eta = load_param(prm, P_ETA, eta);
+  bscale = load_param(prm, P_BSCALE, bscale);
+  const float step = eta * bscale * bscale, inv = 1.f / (bscale * eta);
+  const int r = blockIdx.x * 32 + threadIdx.x;
+  const bool ok = r < R;
+  const bool act = ok && (!active || active[r]);
+  float part = 0.f;
+  if (ok) {
+    for (int t = blockIdx.y * blockDim.y + threadIdx.y; t < d.n_free; t += gridDim.y * blockDim.y) {
+      const int j = d.free_var[t];
+      const size_t k = (size_t)j * R + r;
+      const float bv = b[k];
+      const float bn = fminf(fmaxf(bv - step * gb[k], d.lo[j]), d.hi[j]);
+      const float q = (bv - bn) * inv;
+      part = fmaf(q, q, part);
+      if (act) b[k] = bn;
+      if (clear_grad) gb[k] = 0.f;
+    }
+  }
+  reduce_rows_add(part, gn2, r, ok);
+}
+
+// Dykstra's alternating projections on one block of coupled reals, one thread
+// per (block, restart); the block's reals and the half-space increments stay in
+// thread-local arrays.  Per sweep: every half-space in constraint order, then the box.
+__global__ void k_pgd_comp(DevView d, int R, float eta, float bscale, int sweeps, const float* prm,
+                           float* __restrict__ b, float* __restrict__ gb, float* __restrict__ gn2,
+                           const uint8_t* __restrict__ active, int clear_grad, const int* ctl) {
+  if (ctl && ctl[0] == 0) return;
+  eta = load_param(prm, P_ETA, eta);
+  bscale = load_param(prm, P_BSCALE, bscale);
+  if (prm) sweeps = (int)prm[P_SWEEPS];
+  const float step = eta * bscale * bscale, inv = 1.f / (bscale * eta);
+  const int r = blockIdx.x * 32 + threadIdx.x;
+  const bool ok = r < R;
+  const bool act = ok && (!active || active[r]);
+  float part = 0.f;
+  if (ok) {
+    for (int c = blockIdx.y * blockDim.y + threadIdx.y; c < d.n_comp; c += gridDim.y * blockDim.y) {
+      float x[kMaxCompVars], old[kMaxCompVars], pbox[kMaxCompVars], th[kMaxCompHalfspaces];
+      const int v0 = d.comp_var_ptr[c], nv = d.comp_var_ptr[c + 1] - v0;
+      const int h0 = d.comp_hs_ptr[c], nh = d.comp_hs_ptr[c + 1] - h0;
+      for (int t = 0; t < nv; ++t) {
+        const size_t k = (size_t)d.comp_var[v0 + t] * R + r;
+        old[t] = b[k];
+        x[t] = old[t] - step * gb[k];
+        pbox[t] = 0.f;
+        if (clear_grad) gb[k] = 0.f;
+      }
+      for (int q = 0; q < nh; ++q) th[q] = 0.f;
+      for (int sw = 0; sw < sweeps; ++sw) {
+        for (int q = 0; q < nh; ++q) {
+          const int e0 = d.hs_ptr[h0 + q], e1 = d.hs_ptr[h0 + q + 1];
+          float dot = -d.hs_q0[h0 + q];
+          for (int e = e0; e < e1; ++e) {
+            const float cf = d.hs_coef[e];
+            dot = fmaf(cf, x[d.hs_lvar[e]] + th[q] * cf, dot);
+          }
+          const float tn = fmaxf(dot, 0.f) * d.hs_inv_qq[h0 + q];
+          const float delta = th[q] - tn;
+          for (int e = e0; e < e1; ++e) x[d.hs_lvar[e]] = fmaf(delta, d.hs_coef[e], x[d.hs_lvar[e]]);
+          th[q] = tn;
+        }
+        for (int t = 0; t < nv; ++t) {
+          const int j = d.comp_var[v0 + t];
+          const float yv = x[t] + pbox[t];
+          const float xn = fminf(fmaxf(yv, d.lo[j]), d.hi[j]);
+          pbox[t] = yv - xn;
+          x[t] = xn;
+        }
+      }
+      if (sweeps == 0)
+        for (int t = 0; t < nv; ++t) {
+          const int j = d.comp_var[v0 + t];
+          x[t] = fminf(fmaxf(x[t], d.lo[j]), d.hi[j]);
+        }
+      for (int t = 0; t < nv; ++t) {
+        const float q = (old[t] - x[t]) * inv;
+        part = fmaf(q, q, part);
+        if (act) b[(size_t)d.comp_var[v0 + t] * R + r] = x[t];
+      }
+    }
+  }
+  reduce_rows_add(part, gn2, r, ok);
+}
+
+// ------------------------------------------------------- stage bookkeeping --
+__global__ void k_set_params(float* prm, float sigma, float eta, float bscale, float eps, float rho, float gamma,
+                             float update_w, float sweeps) {
+  prm[P_SIGMA] = sigma;
+  prm[P_ETA] = eta;
+  prm[P_BSCALE] = bscale;
+  prm[P_EPS] = eps;
+  prm[P_RHO] = rho;
+  prm[P_GAMMA] = gamma;
+  prm[P_UPDATE_W] = update_w;
+  prm[P_SWEEPS] = sweeps;
+}
+
+__global__ void k_stage_begin(int R, uint8_t* active, int* iters, int* ctl) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < R; r += gridDim.x * blockDim.x) {
+    active[r] = 1;
+    iters[r] = 0;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctl[0] = R;
+    ctl[1] = 0;
+  }
+}
+
+__global__ void k_iter_begin(int R, float* obj, float* gn2, const int* ctl) {
+  if (ctl[0] == 0) return;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < R; r += gridDim.x * blockDim.x) {
+    obj[r] = 0.f;
+    gn2[r] = 0.f;
+  }
+}
+
+// Eq. critical per restart: the iteration just run is counted, and a restart
+// whose ||g||^2 <= eps^2 stops.  One block; ctl[0] = restarts still iterating.
+__global__ void k_converge(int R, const float* prm, const float* gn2, uint8_t* active, int* iters, int* ctl) {
+  if (ctl[0] == 0) return;
+  __syncthreads();
+  const float eps = prm[P_EPS];
+  const float eps2 = eps * eps;
+  int cnt = 0;
+  for (int r = threadIdx.x; r < R; r += blockDim.x) {
+    if (!active[r]) continue;
+    iters[r] += 1;
+    const float g = gn2[r];
+    if (isnan(g)) {
+      active[r] = 0;
+      atomicOr(ctl + 1, 1);
+    } else if (g <= eps2) {
+      active[r] = 0;
+    } else {
+      ++cnt;
+    }
+  }
+  __shared__ int red[32];
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = cnt;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int s = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+    ctl[0] = s;
+  }
+}
+
+// --------------------------------------------------- round + check + ERWA --
+// Alg. 1 rounding and an exact walk of every constraint's diagram per restart;
+// Alg. 2's u_c, h_c, #Unsat and weight update.  One warp per constraint.
+__global__ void k_round_check(DevView d, int R, const float* __restrict__ a, const float* __restrict__ b,
+                              uint8_t* __restrict__ viol, int* __restrict__ n_unsat, float* __restrict__ w,
+                              float* __restrict__ h, float rho, float gamma, int update_w, const float* prm) {
+  extern __shared__ int cnt_s[];
+  for (int r = threadIdx.x; r < R; r += blockDim.x) cnt_s[r] = 0;
+  __syncthreads();
+  if (prm) {
+    rho = prm[P_RHO];
+    gamma = prm[P_GAMMA];
+    update_w = prm[P_UPDATE_W] != 0.f;
+  }
+  const float lg = log2f(gamma);
+  const int lane = threadIdx.x & 31, W = blockDim.x >> 5;
+  const int n_tiles = (R + 31) >> 5;
+  for (int s = blockIdx.x * W + (threadIdx.x >> 5); s < d.n_cons; s += gridDim.x * W) {
+    const int nb = __ldg(d.con_ptr + s);
+    const int V = __ldg(d.con_ptr + s + 1) - nb;
+    const int cid = __ldg(d.con_id + s);
+    const int root = __ldg(d.con_root + s);
+    for (int t = 0; t < n_tiles; ++t) {
+      const int r = t * 32 + lane;
+      if (r >= R) continue;
+      int v = root;
+      while (v < V) {
+        const uint2 nd = d.nodes[nb + v];
+        v = literal_truth_exact(d, (int)nd.x, R, r, a, b) ? (int)(nd.y & 0xffff) : (int)(nd.y >> 16);
+      }
+      const int u = v != V ? 1 : 0;
+      if (viol) viol[(size_t)cid * R + r] = (uint8_t)u;
+      if (u) atomicAdd(cnt_s + r, 1);
+      if (h) {
+        const size_t k = (size_t)cid * R + r;
+        float hh = fmaf(rho, h[k], (float)u);
+        if (update_w) {
+          w[k] = w[k] * exp2f(hh * lg);
+          hh = 1.f;
+        }
+        h[k] = hh;
+      }
+    }
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < R; r += blockDim.x)
+    if (cnt_s[r]) atomicAdd(n_unsat + r, cnt_s[r]);
+}
+
+__global__ void k_sign(int n, int R, const float* __restrict__ a, int8_t* __restrict__ x) {
+  const size_t N = (size_t)n * R;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < N; k += (size_t)gridDim.x * blockDim.x)
+    x[k] = a[k] < 0.f ? (int8_t)-1 : (int8_t)1;
+}
+
+// ---------------------------------------------------------------- helpers --
+int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 148;
+  }
+  return n;
+}
+
+fsmt_status check_ready(const fsmt_compiled* c, int R) {
+  if (!c) {
+    set_error("compiled is NULL");
+    return FSMT_EINVAL;
+  }
+  if (!c->c.uploaded) {
+    set_error("fsmt_upload has not been called");
+    return FSMT_ESTATE;
+  }
+  if (R < 1) {
+    set_error("R must be >= 1");
+    return FSMT_EINVAL;
+  }
+  return FSMT_OK;
+}
+
+fsmt_status launch_fused(const Compiled& C, bool adj, int R, float sigma, const float* prm, const float* w,
+                         const float* a, const float* b, float* ga, float* gb, float* obj, float* cop, const int* ctl,
+                         cudaStream_t st) {
+  if (C.n_obj == 0) return FSMT_OK;
+  FusedShape f = fused_shape(C, R);
+  if (fused_warp_bytes(f.vcap) + (size_t)R * 4 > 220 * 1024) {
+    set_error("a diagram is too large for the fused kernel; use the plain form");
+    return FSMT_EINVAL;
+  }
+  const int threads = f.warps * 32;
+  int per_sm = 1;
+  if (adj)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<true>, threads, f.smem);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<false>, threads, f.smem);
+  per_sm = std::max(per_sm, 1);
+  const long need = (C.n_obj + f.warps - 1) / f.warps;
+  const int blocks = (int)std::max<long>(1, std::min<long>(need, (long)sm_count() * per_sm));
+  if (adj)
+    k_fused<true><<<blocks, threads, f.smem, st>>>(C.view, R, sigma, prm, f.vcap, w, a, b, ga, gb, obj, cop, ctl);
+  else
+    k_fused<false><<<blocks, threads, f.smem, st>>>(C.view, R, sigma, prm, f.vcap, w, a, b, ga, gb, obj, cop, ctl);
+  FSMT_CUDA(cudaGetLastError(), "fused kernel launch");
+  return FSMT_OK;
+}
+
+fsmt_status launch_pgd(const Compiled& C, int R, float eta, float bscale, int sweeps, const float* prm, float* a,
+                       float* b, float* ga, float* gb, float* gn2, const uint8_t* active, int clear, const int* ctl,
+                       cudaStream_t st) {
+  const int tiles = (R + 31) / 32;
+  const dim3 blk(32, 8);
+  // enough blocks to fill the GPU a few times; each thread strides over rows
+  auto rows = [&](long n) {
+    const long cap = std::max<long>(1, 4L * sm_count() * 8 / tiles);
+    return (int)std::max<long>(1, std::min<long>(std::min<long>((n + 7) / 8, cap), 65535L));
+  };
+  if (C.n_bool > 0)
+    k_pgd_bool<<<dim3(tiles, rows(C.n_bool)), blk, 0, st>>>(C.view, R, eta, prm, a, ga, gn2, active, clear, ctl);
+  if (!C.free_var.empty())
+    k_pgd_free<<<dim3(tiles, rows((long)C.free_var.size())), blk, 0, st>>>(C.view, R, eta, bscale, prm, b, gb, gn2,
+                                                                           active, clear, ctl);
+  const int ncomp = (int)C.comp_var_ptr.size() - 1;
+  if (ncomp > 0)
+    k_pgd_comp<<<dim3(tiles, rows(ncomp)), blk, 0, st>>>(C.view, R, eta, bscale, sweeps, prm, b, gb, gn2, active,
+                                                         clear, ctl);
+  FSMT_CUDA(cudaGetLastError(), "pgd kernel launch");
+  return FSMT_OK;
+}
+
+fsmt_status launch_round_check(const Compiled& C, int R, const float* a, const float* b, uint8_t* viol, int* n_unsat,
+                               float* w, float* h, float rho, float gamma, int update_w, const float* prm,
+                               cudaStream_t st) {
+  FSMT_CUDA(cudaMemsetAsync(n_unsat, 0, sizeof(int) * (size_t)R, st), "memset n_unsat");
+  if (C.n_cons == 0) return FSMT_OK;
+  const int threads = 256;
+  const size_t smem = (size_t)R * sizeof(int);
+  if (smem > 200 * 1024) {
+    set_error("R too large for round_check");
+    return FSMT_EINVAL;
+  }
+  const int blocks = (int)std::max<long>(1, std::min<long>((C.n_cons + 7) / 8, (long)sm_count() * 4));
+  k_round_check<<<blocks, threads, smem, st>>>(C.view, R, a, b, viol, n_unsat, w, h, rho, gamma, update_w, prm);
+  FSMT_CUDA(cudaGetLastError(), "round_check launch");
+  return FSMT_OK;
+}
+
+template <typename T>
+size_t push_array(std::vector<unsigned char>& blob, const std::vector<T>& v) {
+  size_t off = (blob.size() + 255) & ~size_t(255);
+  blob.resize(off + std::max<size_t>(v.size() * sizeof(T), 1));
+  if (!v.empty()) std::memcpy(blob.data() + off, v.data(), v.size() * sizeof(T));
+  return off;
+}
+
+}  // namespace
+
+}  // namespace fsmt
+
+using namespace fsmt;
+
+int fsmt_fused_limit_ok(const fsmt::Compiled& C) {
+  return fused_warp_bytes(std::max(1, C.max_nodes)) <= 200 * 1024 ? 1 : 0;
+}
+
+extern "C" {
+
+fsmt_status fsmt_upload(fsmt_compiled* cc, void* stream) {
+  if (!cc) {
+    set_error("compiled is NULL");
+    return FSMT_EINVAL;
+  }
+  Compiled& C = cc->c;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<unsigned char> blob;
+  std::vector<uint2> nodes(C.node_label.size());
+  for (size_t i = 0; i < nodes.size(); ++i) nodes[i] = make_uint2(C.node_label[i], C.node_hilo[i]);
+  const size_t o_con_ptr = push_array(blob, C.con_ptr), o_con_id = push_array(blob, C.con_id),
+               o_con_root = push_array(blob, C.con_root), o_nodes = push_array(blob, nodes),
+               o_aptr = push_array(blob, C.atom_ptr), o_avar = push_array(blob, C.atom_var),
+               o_acoef = push_array(blob, C.atom_coef), o_aq0f = push_array(blob, C.atom_q0f),
+               o_aq0d = push_array(blob, C.atom_q0d), o_ainv = push_array(blob, C.atom_inv_norm),
+               o_astr = push_array(blob, C.atom_strict), o_lo = push_array(blob, C.lo), o_hi = push_array(blob, C.hi),
+               o_free = push_array(blob, C.free_var), o_cvp = push_array(blob, C.comp_var_ptr),
+               o_cv = push_array(blob, C.comp_var), o_chp = push_array(blob, C.comp_hs_ptr),
+               o_hsp = push_array(blob, C.hs_ptr), o_hsl = push_array(blob, C.hs_lvar),
+               o_hsc = push_array(blob, C.hs_coef), o_hsq = push_array(blob, C.hs_q0),
+               o_hsi = push_array(blob, C.hs_inv_qq);
+  if (C.dev_block) {
+    cudaFree(C.dev_block);
+    C.dev_block = nullptr;
+  }
+  cudaError_t e = cudaMalloc(&C.dev_block, blob.size());
+  if (e != cudaSuccess) {
+    set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? FSMT_ENOMEM : FSMT_ECUDA;
+  }
+  FSMT_CUDA(cudaMemcpyAsync(C.dev_block, blob.data(), blob.size(), cudaMemcpyHostToDevice, st), "upload copy");
+  FSMT_CUDA(cudaStreamSynchronize(st), "upload sync");
+  unsigned char* base = (unsigned char*)C.dev_block;
+  DevView& v = C.view;
+  v.n_bool = C.n_bool;
+  v.n_real = C.n_real;
+  v.n_atoms = C.n_atoms;
+  v.n_cons = C.n_cons;
+  v.n_obj = C.n_obj;
+  v.con_ptr = (const int32_t*)(base + o_con_ptr);
+  v.con_id = (const int32_t*)(base + o_con_id);
+  v.con_root = (const uint8_t*)(base + o_con_root);
+  v.nodes = (const uint2*)(base + o_nodes);
+  v.atom_ptr = (const int32_t*)(base + o_aptr);
+  v.atom_var = (const int32_t*)(base + o_avar);
+  v.atom_coef = (const float*)(base + o_acoef);
+  v.atom_q0f = (const float*)(base + o_aq0f);
+  v.atom_q0d = (const double*)(base + o_aq0d);
+  v.atom_inv_norm = (const float*)(base + o_ainv);
+  v.atom_strict = (const uint8_t*)(base + o_astr);
+  v.lo = (const float*)(base + o_lo);
+  v.hi = (const float*)(base + o_hi);
+  v.n_free = (int32_t)C.free_var.size();
+  v.free_var = (const int32_t*)(base + o_free);
+  v.n_comp = (int32_t)C.comp_var_ptr.size() - 1;
+  v.comp_var_ptr = (const int32_t*)(base + o_cvp);
+  v.comp_var = (const int32_t*)(base + o_cv);
+  v.comp_hs_ptr = (const int32_t*)(base + o_chp);
+  v.hs_ptr = (const int32_t*)(base + o_hsp);
+  v.hs_lvar = (const int32_t*)(base + o_hsl);
+  v.hs_coef = (const float*)(base + o_hsc);
+  v.hs_q0 = (const float*)(base + o_hsq);
+  v.hs_inv_qq = (const float*)(base + o_hsi);
+  FSMT_CUDA(cudaFuncSetAttribute(k_fused<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024),
+            "smem attribute");
+  FSMT_CUDA(cudaFuncSetAttribute(k_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024),
+            "smem attribute");
+  FSMT_CUDA(cudaFuncSetAttribute(k_round_check, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024),
+            "smem attribute");
+  cudaGetDevice(&C.device);
+  C.uploaded = true;
+  return FSMT_OK;
+}
+
+void fsmt_free_compiled(fsmt_compiled* cc) {
+  if (!cc) return;
+  if (cc->c.graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)cc->c.graph_exec);
+  if (cc->c.dev_block) cudaFree(cc->c.dev_block);
+  delete cc;
+}
+
+fsmt_status fsmt_forward(const fsmt_compiled* c, int32_t R, float sigma, const float* w, const float* a,
+                         const float* b, float* cop, float* obj, void* stream) {
+  fsmt_status s = check_ready(c, R);
+  if (s != FSMT_OK) return s;
+  if (!(sigma >= 0.f) || !w || (c->c.n_bool && !a) || (c->c.n_real && !b)) {
+    set_error("invalid sigma or NULL input");
+    return FSMT_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  if (obj) FSMT_CUDA(cudaMemsetAsync(obj, 0, sizeof(float) * (size_t)R, st), "memset obj");
+  return launch_fused(c->c, false, R, sigma, nullptr, w, a, b, nullptr, nullptr, obj, cop, nullptr, st);
+}
+
+fsmt_status fsmt_adjoint(const fsmt_compiled* c, int32_t R, float sigma, const float* w, const float* a,
+                         const float* b, float* grad_a, float* grad_b, float* obj, float* cop, void* stream) {
+  fsmt_status s = check_ready(c, R);
+  if (s != FSMT_OK) return s;
+  const Compiled& C = c->c;
+  if (!(sigma >= 0.f) || !w || (C.n_bool && (!a || !grad_a)) || (C.n_real && (!b || !grad_b))) {
+    set_error("invalid sigma or NULL argument");
+    return FSMT_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  if (C.n_bool) FSMT_CUDA(cudaMemsetAsync(grad_a, 0, sizeof(float) * (size_t)C.n_bool * R, st), "memset grad_a");
+  if (C.n_real) FSMT_CUDA(cudaMemsetAsync(grad_b, 0, sizeof(float) * (size_t)C.n_real * R, st), "memset grad_b");
+  if (obj) FSMT_CUDA(cudaMemsetAsync(obj, 0, sizeof(float) * (size_t)R, st), "memset obj");
+  return launch_fused(C, true, R, sigma, nullptr, w, a, b, grad_a, grad_b, obj, cop, nullptr, st);
+}
+
+fsmt_status fsmt_plain_work_floats(const fsmt_compiled* c, int32_t R, int64_t* n_floats) {
+  if (!c || !n_floats || R < 1) {
+    set_error("invalid argument");
+    return FSMT_EINVAL;
+  }
+  const Compiled& C = c->c;
+  *n_floats = ((int64_t)C.n_obj_nodes + 2LL * C.n_obj + 2LL * C.n_atoms) * R;
+  return FSMT_OK;
+}
+
+fsmt_status fsmt_forward_plain(const fsmt_compiled* c, int32_t R, float sigma, const float* w, const float* a,
+                               const float* b, float* work, float* cop, float* obj, void* stream) {
+  fsmt_status s = check_ready(c, R);
+  if (s != FSMT_OK) return s;
+  const Compiled& C = c->c;
+  if (!(sigma >= 0.f) || !w || !work || (C.n_bool && !a) || (C.n_real && !b)) {
+    set_error("invalid sigma or NULL argument");
+    return FSMT_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  float* m = work;
+  float* p_atom = work + ((size_t)C.n_obj_nodes + 2 * (size_t)C.n_obj) * R;
+  float* gz_atom = p_atom + (size_t)C.n_atoms * R;
+  const int tiles = (R + 31) / 32;
+  if (C.n_atoms > 0) {
+    k_atoms_plain<<<dim3(tiles, (unsigned)std::min<long>((C.n_atoms + 7) / 8, 4096)), dim3(32, 8), 0, st>>>(
+        C.view, R, sigma, b, p_atom, gz_atom);
+    FSMT_CUDA(cudaGetLastError(), "atoms kernel launch");
+  }
+  if (obj) FSMT_CUDA(cudaMemsetAsync(obj, 0, sizeof(float) * (size_t)R, st), "memset obj");
+  if (C.n_obj > 0) {
+    const int blocks = (int)std::max<long>(1, std::min<long>((C.n_obj + 7) / 8, (long)sm_count() * 8));
+    k_fwd_plain<<<blocks, 256, 0, st>>>(C.view, R, w, a, p_atom, m, cop, obj);
+    FSMT_CUDA(cudaGetLastError(), "plain forward launch");
+  }
+  return FSMT_OK;
+}
+
+fsmt_status fsmt_adjoint_plain(const fsmt_compiled* c, int32_t R, float sigma, const float* w, const float* a,
+                               const float* b, float* work, float* grad_a, float* grad_b, void* stream) {
+  (void)sigma;
+  (void)b;
+  fsmt_status s = check_ready(c, R);
+  if (s != FSMT_OK) return s;
+  const Compiled& C = c->c;
+  if (!w || !work || (C.n_bool && (!a || !grad_a)) || (C.n_real && !grad_b)) {
+    set_error("NULL argument");
+    return FSMT_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  float* m = work;
+  float* p_atom = work + ((size_t)C.n_obj_nodes + 2 * (size_t)C.n_obj) * R;
+  float* gz_atom = p_atom + (size_t)C.n_atoms * R;
+  if (C.n_bool) FSMT_CUDA(cudaMemsetAsync(grad_a, 0, sizeof(float) * (size_t)C.n_bool * R, st), "memset grad_a");
+  if (C.n_real) FSMT_CUDA(cudaMemsetAsync(grad_b, 0, sizeof(float) * (size_t)C.n_real * R, st), "memset grad_b");
+  if (C.n_obj > 0) {
+    const int blocks = (int)std::max<long>(1, std::min<long>((C.n_obj + 7) / 8, (long)sm_count() * 8));
+    k_adj_plain<<<blocks, 256, 0, st>>>(C.view, R, w, a, p_atom, gz_atom, m, grad_a, grad_b);
+    FSMT_CUDA(cudaGetLastError(), "plain adjoint launch");
+  }
+  return FSMT_OK;
+}
+
+fsmt_status fsmt_pgd_step(const fsmt_compiled* c, int32_t R, float eta, float b_scale, int32_t sweeps, float* a,
+                          float* b, const float* grad_a, const float* grad_b, float* gnorm2, const uint8_t* active,
+                          void* stream) {
+  fsmt_status s = check_ready(c, R);
+  if (s != FSMT_OK) return s;
+  const Compiled& C = c->c;
+  if (!(eta > 0.f) || !(b_scale > 0.f) || sweeps < 0 || !gnorm2 || (C.n_bool && (!a || !grad_a)) ||
+      (C.n_real && (!b || !grad_b))) {
+    set_error("invalid step parameters or NULL argument");
+    return FSMT_EINVAL;
+  }
+  return launch_pgd(C, R, eta, b_scale, sweeps, nullptr, a, b, const_cast<float*>(grad_a), const_cast<float*>(grad_b),
+                    gnorm2, active, 0, nullptr, (cudaStream_t)stream);
+}
+
+fsmt_status fsmt_round_check(const fsmt_compiled* c, int32_t R, const float* a, const float* b, int8_t* x,
+                             uint8_t* violated, int32_t* n_unsat, float* w, float* h, float rho, float gamma,
+                             int32_t update_w, void* stream) {
+  fsmt_status s = check_ready(c, R);
+  if (s != FSMT_OK) return s;
+  const Compiled& C = c->c;
+  if (!n_unsat || (C.n_bool && !a) || (C.n_real && !b) || ((w == nullptr) != (h == nullptr)) ||
+      (h && !(gamma > 0.f))) {
+    set_error("NULL argument or invalid ERWA parameters");
+    return FSMT_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  if (x && C.n_bool) {
+    k_sign<<<std::min<long>(((long)C.n_bool * R + 255) / 256, 65535L), 256, 0, st>>>(C.n_bool, R, a, x);
+    FSMT_CUDA(cudaGetLastError(), "sign launch");
+  }
+  return launch_round_check(C, R, a, b, violated, n_unsat, w, h, rho, gamma, update_w, nullptr, st);
+}
+
+static fsmt_status enqueue_stage(const Compiled& C, int t_max, fsmt_state* s, cudaStream_t st) {
+  const int R = s->R;
+  k_stage_begin<<<(R + 255) / 256, 256, 0, st>>>(R, s->active, s->iters, s->ctl);
+  FSMT_CUDA(cudaGetLastError(), "stage begin");
+  for (int it = 0; it < t_max; ++it) {
+    k_iter_begin<<<(R + 255) / 256, 256, 0, st>>>(R, s->obj, s->gnorm2, s->ctl);
+    fsmt_status e = launch_fused(C, true, R, 0.f, s->params, s->w, s->a, s->b, s->grad_a, s->grad_b, s->obj, nullptr,
+                                 s->ctl, st);
+    if (e != FSMT_OK) return e;
+    e = launch_pgd(C, R, 1.f, 1.f, 0, s->params, s->a, s->b, s->grad_a, s->grad_b, s->gnorm2, s->active, 1, s->ctl, st);
+    if (e != FSMT_OK) return e;
+    k_converge<<<1, 1024, 0, st>>>(R, s->params, s->gnorm2, s->active, s->iters, s->ctl);
+    FSMT_CUDA(cudaGetLastError(), "converge");
+  }
+  return launch_round_check(C, R, s->a, s->b, nullptr, s->n_unsat, s->w, s->h, 0.f, 2.f, 0, s->params, st);
+}
+
+fsmt_status fsmt_solve_stage(fsmt_compiled* cc, const fsmt_stage_config* cfg, fsmt_state* s, void* stream) {
+  if (!cfg || !s) {
+    set_error("NULL argument");
+    return FSMT_EINVAL;
+  }
+  fsmt_status e = check_ready(cc, s->R);
+  if (e != FSMT_OK) return e;
+  Compiled& C = cc->c;
+  if (!(cfg->sigma >= 0.f) || !(cfg->eta > 0.f) || !(cfg->b_scale > 0.f) || cfg->t_max < 0 || cfg->sweeps < 0 ||
+      !(cfg->gamma > 0.f) || !s->w || !s->h || !s->obj || !s->gnorm2 || !s->active || !s->iters || !s->n_unsat ||
+      !s->ctl || !s->params || (C.n_bool && (!s->a || !s->grad_a)) || (C.n_real && (!s->b || !s->grad_b))) {
+    set_error("invalid stage configuration or NULL state buffer");
+    return FSMT_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  k_set_params<<<1, 1, 0, st>>>(s->params, cfg->sigma, cfg->eta, cfg->b_scale, cfg->eps, cfg->rho, cfg->gamma,
+                                (float)cfg->update_w, (float)cfg->sweeps);
+  FSMT_CUDA(cudaGetLastError(), "set params");
+  if (!cfg->use_graph) return enqueue_stage(C, cfg->t_max, s, st);
+  // one graph per (buffer set, R, t_max)
+  uint64_t key = 1469598103934665603ull;
+  auto mix = [&](uint64_t v) { key = (key ^ v) * 1099511628211ull; };
+  const void* ptrs[] = {s->a, s->b, s->w, s->h, s->grad_a, s->grad_b, s->obj, s->gnorm2, s->active, s->iters,
+                        s->n_unsat, s->ctl, s->params};
+  for (const void* p : ptrs) mix((uint64_t)(uintptr_t)p);
+  mix((uint64_t)s->R);
+  mix((uint64_t)cfg->t_max);
+  if (!C.graph_exec || C.graph_key != key) {
+    if (C.graph_exec) {
+      cudaGraphExecDestroy((cudaGraphExec_t)C.graph_exec);
+      C.graph_exec = nullptr;
+    }
+    cudaGraph_t g;
+    FSMT_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture");
+    fsmt_status q = enqueue_stage(C, cfg->t_max, s, st);
+    cudaError_t ce = cudaStreamEndCapture(st, &g);
+    if (q != FSMT_OK) return q;
+    if (ce != cudaSuccess) return cuda_fail(ce, "end capture");
+    cudaGraphExec_t ex;
+    ce = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) return cuda_fail(ce, "graph instantiate");
+    C.graph_exec = ex;
+    C.graph_key = key;
+  }
+  FSMT_CUDA(cudaGraphLaunch((cudaGraphExec_t)C.graph_exec, st), "graph launch");
+  return FSMT_OK;
+}
+
+fsmt_status fsmt_solve_stage_host(fsmt_compiled* cc, const fsmt_stage_config* cfg, fsmt_state* s,
+                                  const float* a_host, const float* b_host, int32_t* n_unsat_host, float* obj_host,
+                                  void* stream) {
+  if (!cc || !cfg || !s) {
+    set_error("NULL argument");
+    return FSMT_EINVAL;
+  }
+  const Compiled& C = cc->c;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t R = (size_t)s->R;
+  if (C.n_bool && a_host)
+    FSMT_CUDA(cudaMemcpyAsync(s->a, a_host, sizeof(float) * C.n_bool * R, cudaMemcpyHostToDevice, st), "copy a");
+  if (C.n_real && b_host)
+    FSMT_CUDA(cudaMemcpyAsync(s->b, b_host, sizeof(float) * C.n_real * R, cudaMemcpyHostToDevice, st), "copy b");
+  fsmt_status e = fsmt_solve_stage(cc, cfg, s, stream);
+  if (e != FSMT_OK) return e;
+  if (n_unsat_host)
+    FSMT_CUDA(cudaMemcpyAsync(n_unsat_host, s->n_unsat, sizeof(int32_t) * R, cudaMemcpyDeviceToHost, st), "copy n_unsat");
+  if (obj_host) FSMT_CUDA(cudaMemcpyAsync(obj_host, s->obj, sizeof(float) * R, cudaMemcpyDeviceToHost, st), "copy obj");
+  FSMT_CUDA(cudaStreamSynchronize(st), "stage sync");
+  return FSMT_OK;
+}
+
+}  // extern "C"

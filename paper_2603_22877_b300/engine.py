@@ -1,0 +1,341 @@
+"""Python front end of the C ABI: problem building, device calls on torch tensors,
+the autograd bridge, and the annealing driver of Alg. 2.
+
+Only argument marshalling and host-side orchestration live here; every
+numerical step of the hot path runs in libfsmt.so.  PyTorch provides device
+memory and streams.
+"""
+import ctypes as C
+import time
+
+import numpy as np
+
+from . import _lib as L
+
+
+def _np_ptr(a):
+    return C.c_void_p(a.ctypes.data) if a is not None and a.size else C.c_void_p(0)
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _dptr(t, dtype=None, shape=None, name="tensor"):
+    """Device pointer of a contiguous CUDA tensor (or NULL for None)."""
+    if t is None:
+        return C.c_void_p(0)
+    import torch
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return C.c_void_p(t.data_ptr())
+
+
+class Problem:
+    """An fsmt_problem (constraint set C of Alg. 1)."""
+
+    def __init__(self, n_bool, n_real):
+        self.n_bool, self.n_real = int(n_bool), int(n_real)
+        h = C.c_void_p()
+        L.call("fsmt_problem_create", self.n_bool, self.n_real, C.byref(h))
+        self.h = h
+        self.n_atoms = 0
+        self.n_cons = 0
+
+    def __del__(self):
+        if getattr(self, "h", None) and L._lib is not None:
+            L._lib.fsmt_free_problem(self.h)
+            self.h = None
+
+    def set_bounds(self, lo, hi):
+        for j in range(self.n_real):
+            L.call("fsmt_set_real_bounds", self.h, j, float(lo[j]), float(hi[j]))
+
+    def add_atoms(self, ptr, var, coef, q0, rel):
+        ptr = np.ascontiguousarray(ptr, np.int64)
+        var = np.ascontiguousarray(var, np.int32)
+        coef = np.ascontiguousarray(coef, np.int64)
+        q0 = np.ascontiguousarray(q0, np.int64)
+        rel = np.ascontiguousarray(rel, np.int8)
+        n = len(q0)
+        L.call("fsmt_add_atoms", self.h, n, _np_ptr(ptr), _np_ptr(var), _np_ptr(coef), _np_ptr(q0), _np_ptr(rel))
+        self.n_atoms += n
+
+    def add_constraints(self, kind, param, ptr, lits):
+        kind = np.ascontiguousarray(kind, np.int8)
+        param = np.ascontiguousarray(param, np.int32)
+        ptr = np.ascontiguousarray(ptr, np.int64)
+        lits = np.ascontiguousarray(lits, np.int32)
+        n = len(kind)
+        L.call("fsmt_add_constraints", self.h, n, _np_ptr(kind), _np_ptr(param), _np_ptr(ptr), _np_ptr(lits))
+        self.n_cons += n
+
+    @classmethod
+    def from_instance(cls, inst):
+        """Builds the problem from an object with the fields of a generated instance."""
+        P = cls(inst.n_bool, inst.n_real)
+        P.set_bounds(inst.lo, inst.hi)
+        P.add_atoms(inst.atom_ptr, inst.atom_var, inst.atom_coef, inst.atom_q0, inst.atom_rel)
+        P.add_constraints(inst.con_kind, inst.con_param, inst.con_ptr, inst.con_lits)
+        return P
+
+    def verify_exact(self, x, y):
+        """Exact check of a rounded assignment (x in +-1, y reals).  Returns (sat, first_violated)."""
+        x = np.ascontiguousarray(x, np.int8)
+        y = np.ascontiguousarray(y, np.float64)
+        sat, first = C.c_int32(), C.c_int32()
+        L.call("fsmt_verify_exact", self.h, _np_ptr(x), _np_ptr(y), C.byref(sat), C.byref(first))
+        return bool(sat.value), int(first.value)
+
+    def compile(self, policy=L.UNIT_PROJECT):
+        return Compiled(self, policy)
+
+
+class Compiled:
+    """An fsmt_compiled: flattened xBDDs, atoms and projection data."""
+
+    def __init__(self, problem, policy=L.UNIT_PROJECT):
+        h = C.c_void_p()
+        L.call("fsmt_compile", problem.h, int(policy), C.byref(h))
+        self.h = h
+        info = L.Info()
+        L.call("fsmt_compiled_info", self.h, C.byref(info))
+        self.info = {k: getattr(info, k) for k, _ in L.Info._fields_}
+        self.n_bool, self.n_real, self.n_cons = info.n_bool, info.n_real, info.n_cons
+        self.uploaded = False
+        self._work = None
+
+    def __del__(self):
+        if getattr(self, "h", None) and L._lib is not None:
+            L._lib.fsmt_free_compiled(self.h)
+            self.h = None
+
+    def diagrams(self):
+        """Host copy of the flattened diagrams: dict of numpy arrays."""
+        nc, nn = self.info["n_cons"], self.info["n_nodes"]
+        out = dict(con_ptr=np.zeros(nc + 1, np.int32), con_id=np.zeros(nc, np.int32),
+                   con_root=np.zeros(nc, np.uint8), label=np.zeros(nn, np.int32),
+                   hi=np.zeros(nn, np.uint16), lo=np.zeros(nn, np.uint16))
+        L.call("fsmt_get_diagrams", self.h, *[_np_ptr(out[k]) for k in
+                                              ("con_ptr", "con_id", "con_root", "label", "hi", "lo")])
+        return out
+
+    def bounds(self):
+        lo = np.zeros(self.n_real, np.float32)
+        hi = np.zeros(self.n_real, np.float32)
+        L.call("fsmt_get_bounds", self.h, _np_ptr(lo), _np_ptr(hi))
+        return lo, hi
+
+    def upload(self, stream=None):
+        L.call("fsmt_upload", self.h, _stream(stream))
+        self.uploaded = True
+        return self
+
+    # ------------------------------------------------------ device calls --
+    def _shapes(self, R):
+        return (self.n_bool, R), (self.n_real, R), (self.n_cons, R)
+
+    def forward(self, R, sigma, w, a, b, cop=None, obj=None, stream=None):
+        import torch
+        sa, sb, sw = self._shapes(R)
+        L.call("fsmt_forward", self.h, int(R), float(sigma), _dptr(w, torch.float32, sw, "w"),
+               _dptr(a, torch.float32, sa, "a"), _dptr(b, torch.float32, sb, "b"),
+               _dptr(cop, torch.float32, sw, "cop"), _dptr(obj, torch.float32, (R,), "obj"), _stream(stream))
+
+    def adjoint(self, R, sigma, w, a, b, grad_a, grad_b, obj=None, cop=None, stream=None):
+        import torch
+        sa, sb, sw = self._shapes(R)
+        L.call("fsmt_adjoint", self.h, int(R), float(sigma), _dptr(w, torch.float32, sw, "w"),
+               _dptr(a, torch.float32, sa, "a"), _dptr(b, torch.float32, sb, "b"),
+               _dptr(grad_a, torch.float32, sa, "grad_a"), _dptr(grad_b, torch.float32, sb, "grad_b"),
+               _dptr(obj, torch.float32, (R,), "obj"), _dptr(cop, torch.float32, sw, "cop"), _stream(stream))
+
+    def plain_work(self, R):
+        n = C.c_int64()
+        L.call("fsmt_plain_work_floats", self.h, int(R), C.byref(n))
+        return int(n.value)
+
+    def forward_plain(self, R, sigma, w, a, b, work, cop=None, obj=None, stream=None):
+        import torch
+        sa, sb, sw = self._shapes(R)
+        L.call("fsmt_forward_plain", self.h, int(R), float(sigma), _dptr(w, torch.float32, sw, "w"),
+               _dptr(a, torch.float32, sa, "a"), _dptr(b, torch.float32, sb, "b"),
+               _dptr(work, torch.float32, None, "work"), _dptr(cop, torch.float32, sw, "cop"),
+               _dptr(obj, torch.float32, (R,), "obj"), _stream(stream))
+
+    def adjoint_plain(self, R, sigma, w, a, b, work, grad_a, grad_b, stream=None):
+        import torch
+        sa, sb, sw = self._shapes(R)
+        L.call("fsmt_adjoint_plain", self.h, int(R), float(sigma), _dptr(w, torch.float32, sw, "w"),
+               _dptr(a, torch.float32, sa, "a"), _dptr(b, torch.float32, sb, "b"),
+               _dptr(work, torch.float32, None, "work"), _dptr(grad_a, torch.float32, sa, "grad_a"),
+               _dptr(grad_b, torch.float32, sb, "grad_b"), _stream(stream))
+
+    def pgd_step(self, R, eta, b_scale, sweeps, a, b, grad_a, grad_b, gnorm2, active=None, stream=None):
+        import torch
+        sa, sb, _ = self._shapes(R)
+        L.call("fsmt_pgd_step", self.h, int(R), float(eta), float(b_scale), int(sweeps),
+               _dptr(a, torch.float32, sa, "a"), _dptr(b, torch.float32, sb, "b"),
+               _dptr(grad_a, torch.float32, sa, "grad_a"), _dptr(grad_b, torch.float32, sb, "grad_b"),
+               _dptr(gnorm2, torch.float32, (R,), "gnorm2"), _dptr(active, torch.uint8, (R,), "active"),
+               _stream(stream))
+
+    def round_check(self, R, a, b, n_unsat, x=None, violated=None, w=None, h=None, rho=0.5, gamma=2.0,
+                    update_w=True, stream=None):
+        import torch
+        sa, sb, sw = self._shapes(R)
+        L.call("fsmt_round_check", self.h, int(R), _dptr(a, torch.float32, sa, "a"),
+               _dptr(b, torch.float32, sb, "b"), _dptr(x, torch.int8, sa, "x"),
+               _dptr(violated, torch.uint8, sw, "violated"), _dptr(n_unsat, torch.int32, (R,), "n_unsat"),
+               _dptr(w, torch.float32, sw, "w"), _dptr(h, torch.float32, sw, "h"), float(rho), float(gamma),
+               int(bool(update_w)), _stream(stream))
+
+
+def relaxed_objective(compiled, sigma, w, a, b, plain=False):
+    """C_sigma per restart as a differentiable torch function of (a, b)."""
+    return RelaxedObjective.apply(a, b, compiled, w, float(sigma), bool(plain))
+
+
+def _autograd_function():
+    import torch
+
+    class _RelaxedObjective(torch.autograd.Function):
+        """forward: C_sigma(a, b) per restart ([R]); backward: the adjoint sweep.
+
+        Fused form: one kernel computes C and its gradient in forward (the
+        gradient is kept for backward).  Plain form: the forward kernel stores the
+        top-down messages in a work buffer and backward runs the adjoint kernel.
+        """
+
+        @staticmethod
+        def forward(ctx, a, b, compiled, w, sigma, plain):
+            R = w.shape[1]
+            obj = torch.empty(R, device=w.device, dtype=torch.float32)
+            ga = torch.empty_like(a)
+            gb = torch.empty_like(b)
+            a_c, b_c = a.detach().contiguous(), b.detach().contiguous()
+            if plain:
+                work = torch.empty(compiled.plain_work(R), device=w.device, dtype=torch.float32)
+                compiled.forward_plain(R, sigma, w, a_c, b_c, work, obj=obj)
+                ctx.save_for_backward(a_c, b_c, w, work)
+            else:
+                compiled.adjoint(R, sigma, w, a_c, b_c, ga, gb, obj=obj)
+                ctx.save_for_backward(ga, gb)
+            ctx.compiled, ctx.sigma, ctx.plain, ctx.R = compiled, sigma, plain, R
+            return obj
+
+        @staticmethod
+        def backward(ctx, g):
+            if ctx.plain:
+                a, b, w, work = ctx.saved_tensors
+                ga = torch.empty_like(a)
+                gb = torch.empty_like(b)
+                ctx.compiled.adjoint_plain(ctx.R, ctx.sigma, w, a, b, work, ga, gb)
+            else:
+                ga, gb = ctx.saved_tensors
+            g = g.reshape(1, -1)
+            return ga * g, gb * g, None, None, None, None
+
+    return _RelaxedObjective
+
+
+class _Lazy:
+    def __init__(self):
+        self.fn = None
+
+    def apply(self, *args):
+        if self.fn is None:
+            self.fn = _autograd_function()
+        return self.fn.apply(*args)
+
+
+RelaxedObjective = _Lazy()
+
+
+class Solver:
+    """Alg. 2 (annealing + ERWA) over R restarts with device-resident state.
+
+    Each sigma stage is one fsmt_solve_stage call (a CUDA graph when use_graph);
+    restarts whose check reports #Unsat = 0 are re-verified exactly on the host
+    before SAT is reported.
+    """
+
+    def __init__(self, problem, compiled, R, eta, b_scale, eps=1e-2, t_max=200, sweeps=20, rho=0.5, gamma=2.0,
+                 tau=1, use_graph=True, device="cuda"):
+        import torch
+        self.problem, self.comp, self.R = problem, compiled, int(R)
+        if not compiled.uploaded:
+            compiled.upload()
+        n, m, nc = compiled.n_bool, compiled.n_real, compiled.n_cons
+        f32 = dict(device=device, dtype=torch.float32)
+        self.a = torch.zeros((n, R), **f32)
+        self.b = torch.zeros((m, R), **f32)
+        self.w = torch.ones((nc, R), **f32)
+        self.h = torch.zeros((nc, R), **f32)
+        self.grad_a = torch.zeros((n, R), **f32)
+        self.grad_b = torch.zeros((m, R), **f32)
+        self.obj = torch.zeros(R, **f32)
+        self.gnorm2 = torch.zeros(R, **f32)
+        self.active = torch.zeros(R, device=device, dtype=torch.uint8)
+        self.iters = torch.zeros(R, device=device, dtype=torch.int32)
+        self.n_unsat = torch.zeros(R, device=device, dtype=torch.int32)
+        self.ctl = torch.zeros(4, device=device, dtype=torch.int32)
+        self.params = torch.zeros(16, **f32)
+        self.eta, self.b_scale, self.eps, self.t_max, self.sweeps = eta, b_scale, eps, t_max, sweeps
+        self.rho, self.gamma, self.tau, self.use_graph = rho, gamma, tau, use_graph
+        self._state = L.State(self.R, *[C.c_void_p(t.data_ptr()) for t in (
+            self.a, self.b, self.w, self.h, self.grad_a, self.grad_b, self.obj, self.gnorm2, self.active,
+            self.iters, self.n_unsat, self.ctl, self.params)])
+
+    def reset(self, a0, b0):
+        """Loads initial points ([n][R], [m][R] float32, host or device) and resets weights."""
+        import torch
+        self.a.copy_(torch.as_tensor(a0))
+        self.b.copy_(torch.as_tensor(b0))
+        self.w.fill_(1.0)
+        self.h.zero_()
+
+    def config(self, sigma, t):
+        return L.StageConfig(float(sigma), float(self.eta), float(self.b_scale), float(self.eps), int(self.t_max),
+                             int(self.sweeps), float(self.rho), float(self.gamma), int(t % self.tau == 0),
+                             int(bool(self.use_graph)))
+
+    def stage(self, sigma, t, stream=None):
+        cfg = self.config(sigma, t)
+        L.call("fsmt_solve_stage", self.comp.h, C.byref(cfg), C.byref(self._state), _stream(stream))
+
+    def stage_host(self, sigma, t, a_host, b_host, n_unsat_host, obj_host, stream=None):
+        """The same stage with host input/output buffers (copies inside the call)."""
+        cfg = self.config(sigma, t)
+        L.call("fsmt_solve_stage_host", self.comp.h, C.byref(cfg), C.byref(self._state), _np_ptr(a_host),
+               _np_ptr(b_host), _np_ptr(n_unsat_host), _np_ptr(obj_host), _stream(stream))
+
+    def verify_restart(self, r):
+        x = np.where(self.a[:, r].cpu().numpy() < 0, -1, 1).astype(np.int8)
+        y = self.b[:, r].cpu().numpy().astype(np.float64)
+        sat, _ = self.problem.verify_exact(x, y)
+        return sat, x, y
+
+    def anneal(self, schedule, time_limit=None):
+        """Runs the sigma schedule; returns dict with the first exactly verified SAT restart (or None)."""
+        import torch
+        t0 = time.perf_counter()
+        for t, sigma in enumerate(schedule, start=1):
+            self.stage(sigma, t)
+            cand = torch.nonzero(self.n_unsat == 0).flatten().tolist()
+            for r in cand:
+                sat, x, y = self.verify_restart(r)
+                if sat:
+                    return dict(sat=True, restart=r, stage=t, seconds=time.perf_counter() - t0, x=x, y=y)
+            if time_limit is not None and time.perf_counter() - t0 > time_limit:
+                break
+        torch.cuda.synchronize()
+        return dict(sat=False, restart=None, stage=None, seconds=time.perf_counter() - t0)

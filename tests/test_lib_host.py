@@ -1,0 +1,184 @@
+"""The C-ABI library on the host (no GPU): loading, exported symbols, the xBDD
+compiler against the oracle's diagrams, projection bounds, the exact verifier
+and argument validation."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import bdd, objective as OBJ, pgd, semantics as S
+from paper_2603_22877_b300 import _lib as L
+from paper_2603_22877_b300 import build as B
+from paper_2603_22877_b300.engine import Problem
+from workloads import instances as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    B.build()
+    return L.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    hdr = open(os.path.join(ROOT, "include", "fsmt.h")).read()
+    declared = set(re.findall(r"\b(fsmt_[a-z_0-9]+)\s*\(", hdr))
+    assert len(declared) >= 20
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert set(L.PROTOTYPES) == declared
+
+
+SMALL = {
+    "tiny_random": lambda: W.tiny_random(1001),
+    "jobshop": lambda: W.jobshop(1002, 8, 4),
+    "placement2d": lambda: W.placement2d(1003, 14),
+    "placement2d_nosel": lambda: W.placement2d(1003, 10, selectors=False),
+    "large_scheduling": lambda: W.large_scheduling(1005, 16, 24, 6, 3, 5),
+    "uneven_batch": lambda: W.concat(W.uneven_batch(1004, 3, (3, 6), (2, 4)), "b"),
+}
+
+
+@pytest.mark.parametrize("name", list(SMALL))
+def test_compiler_matches_oracle_diagrams(name):
+    inst = SMALL[name]()
+    P = Problem.from_instance(inst)
+    for policy in (L.UNIT_PROJECT, L.UNIT_SOFT):
+        comp = P.compile(policy)
+        D = comp.diagrams()
+        obj_cons = OBJ.objective_constraints(inst, policy)
+        assert comp.info["n_obj_cons"] == len(obj_cons)
+        assert list(D["con_id"][:len(obj_cons)]) == obj_cons
+        assert sorted(D["con_id"]) == list(range(inst.n_cons))
+        total = 0
+        for s in range(inst.n_cons):
+            c = int(D["con_id"][s])
+            ref = bdd.constraint_diagram(inst, c)
+            b0, b1 = D["con_ptr"][s], D["con_ptr"][s + 1]
+            V = b1 - b0
+            assert V == len(ref[0]), (name, c)  # canonical ROBDD for the same order
+            total += V
+            mine = (list(D["label"][b0:b1]), list(D["hi"][b0:b1]), list(D["lo"][b0:b1]),
+                    int(D["con_root"][s]))
+            ids = sorted({int(l) >> 1 for l in inst.lits(c)})
+            rng = np.random.default_rng(c)
+            for _ in range(8):
+                vals = {i: bool(rng.integers(2)) for i in ids}
+                assert bdd.evaluate(mine, vals.__getitem__) == bdd.evaluate(ref, vals.__getitem__)
+        assert total == comp.info["n_nodes"]
+
+
+def test_all_kinds_random_constraints():
+    rng = np.random.default_rng(3)
+    Bd = W._Builder(30, 2)
+    for _ in range(200):
+        kind = int(rng.integers(6))
+        if kind == W.MUX:
+            b = int(rng.integers(1, 3))
+            L_, param = b + (1 << b), b
+        elif kind == W.NEQ_OR:
+            P_ = int(rng.integers(0, 4))
+            L_, param = 2 * P_ + int(rng.integers(0, 3)), P_
+        else:
+            L_ = int(rng.integers(0, 9))
+            param = int(rng.integers(0, L_ + 2)) if kind == W.CARD_LE else 0
+        ids = rng.choice(30, L_, replace=False)
+        Bd.con(kind, [2 * int(i) + int(rng.integers(2)) for i in ids], param)
+    inst = Bd.freeze("k", np.zeros(2), np.ones(2), np.ones(30), np.zeros(2), 1.0)
+    comp = Problem.from_instance(inst).compile()
+    D = comp.diagrams()
+    for s in range(inst.n_cons):
+        c = int(D["con_id"][s])
+        b0, b1 = D["con_ptr"][s], D["con_ptr"][s + 1]
+        mine = (list(D["label"][b0:b1]), list(D["hi"][b0:b1]), list(D["lo"][b0:b1]), int(D["con_root"][s]))
+        ref = bdd.constraint_diagram(inst, c)
+        assert b1 - b0 == len(ref[0])
+        ls = inst.lits(c)
+        ids = [int(l) >> 1 for l in ls]
+        for mask in range(1 << len(ids)) if len(ids) <= 6 else rng.integers(0, 1 << len(ids), 40):
+            vals = {i: bool((int(mask) >> k) & 1) for k, i in enumerate(ids)}
+            t = [vals[int(l) >> 1] != bool(int(l) & 1) for l in ls]
+            assert bdd.evaluate(mine, vals.__getitem__) == S.kind_value(int(inst.con_kind[c]),
+                                                                        int(inst.con_param[c]), t)
+
+
+def test_bounds_rounded_inward_and_match_oracle():
+    inst = W.jobshop(1002, 8, 4)
+    comp = Problem.from_instance(inst).compile()
+    lo, hi = comp.bounds()
+    dom = pgd.Domain(inst)
+    np.testing.assert_allclose(lo, dom.lo, rtol=1e-7)
+    np.testing.assert_allclose(hi, dom.hi, rtol=1e-7)
+    assert (lo.astype(np.float64) >= dom.lo).all() and (hi.astype(np.float64) <= dom.hi).all()
+    assert comp.info["n_halfspaces"] == len(dom.halfspaces)
+    # fractional bound: 3 y <= 7 -> hi = largest float <= 7/3
+    Bd = W._Builder(0, 1)
+    Bd.con(W.OR, [W.lit(Bd.atom([0], [3], 7, W.LE))])
+    Bd.con(W.OR, [W.lit(Bd.atom([0], [-3], -1, W.LT))])  # -3y < -1 -> y > 1/3
+    inst2 = Bd.freeze("f", np.array([-5.0]), np.array([5.0]), [], np.zeros(1), 1.0)
+    lo2, hi2 = Problem.from_instance(inst2).compile().bounds()
+    assert float(hi2[0]) * 3 <= 7 and float(np.nextafter(hi2[0], np.float32(9))) * 3 > 7
+    assert float(lo2[0]) * -3 < -1 and float(np.nextafter(lo2[0], np.float32(-9))) * -3 >= -1
+
+
+@pytest.mark.parametrize("name", list(SMALL))
+def test_verify_exact_matches_oracle(name):
+    inst = SMALL[name]()
+    P = Problem.from_instance(inst)
+    sat, first = P.verify_exact(inst.planted_x, inst.planted_y)
+    assert sat and first == -1
+    rng = np.random.default_rng(1)
+    for _ in range(6):
+        x = inst.planted_x.copy()
+        flip = rng.random(inst.n_bool) < 0.1
+        x[flip] *= -1
+        y = inst.planted_y + rng.normal(0, 2.0, inst.n_real) * (rng.random(inst.n_real) < 0.3)
+        sat, first = P.verify_exact(x, y)
+        bad = S.unsat_constraints(inst, x, y)
+        assert sat == (not bad)
+        assert first == (bad[0] if bad else -1)
+
+
+def test_verify_exact_boundary_and_tiny_values():
+    Bd = W._Builder(0, 2)
+    Bd.con(W.OR, [W.lit(Bd.atom([0, 1], [3, -7], 0, W.LE))])
+    Bd.con(W.OR, [W.lit(Bd.atom([0, 1], [3, -7], 0, W.LT))])
+    inst = Bd.freeze("e", np.zeros(2), np.ones(2), [], np.zeros(2), 1.0)
+    P = Problem.from_instance(inst)
+    y = np.array([7.0 * 2.0 ** -1060, 3.0 * 2.0 ** -1060])  # 3*7e - 7*3e = 0 exactly, subnormal scale
+    assert P.verify_exact(np.zeros(0, np.int8), y) == (False, 1)
+    y2 = np.array([7.0 * 2.0 ** -1060, np.nextafter(3.0 * 2.0 ** -1060, 1.0)])
+    assert P.verify_exact(np.zeros(0, np.int8), y2) == (True, -1)
+
+
+def test_argument_validation():
+    P = Problem(3, 2)
+    bad = [
+        lambda: P.add_atoms([0, 2], [0, 0], [1, 1], [0], [0]),   # repeated variable
+        lambda: P.add_atoms([0, 1], [0], [0], [0], [0]),         # zero coefficient
+        lambda: P.add_atoms([0, 1], [5], [1], [0], [0]),         # variable out of range
+        lambda: P.add_atoms([0, 1], [0], [1 << 24], [0], [0]),   # coefficient too large
+        lambda: P.add_atoms([0, 1], [0], [1], [1 << 53], [0]),   # q0 too large
+        lambda: P.add_atoms([0, 1], [0], [1], [0], [7]),         # relation
+        lambda: P.add_constraints([0], [0], [0, 2], [0, 1]),     # same variable twice
+        lambda: P.add_constraints([4], [2], [0, 3], [0, 2, 4]),  # MUX arity
+        lambda: P.add_constraints([9], [0], [0, 1], [0]),        # kind
+        lambda: P.add_constraints([0], [0], [0, 1], [100]),      # unknown id
+    ]
+    for f in bad:
+        with pytest.raises(L.FsmtError) as e:
+            f()
+        assert e.value.status == L.EINVAL
+    assert P.n_cons == 0
+    with pytest.raises(L.FsmtError):
+        P.verify_exact(np.array([0, 1, 1], np.int8), np.zeros(2))
+
+
+def test_device_calls_need_upload():
+    inst = W.tiny_random(5, n_bool=4, n_real=4, n_cons=5)
+    comp = Problem.from_instance(inst).compile()
+    st = L.load().fsmt_forward(comp.h, 4, C.c_float(1.0), None, None, None, None, None, None)
+    assert st == L.ESTATE
