@@ -1,0 +1,333 @@
+#!/usr/bin/env python3
+"""Benchmark of the FourierSMT hot path on B300: fwd+adjoint xBDD nodes/s.
+
+A step is one annealing stage of Alg. 2 over one batch of restarts: `iters`
+iterations of [relax -> forward COP -> adjoint -> PGD + projection -> ||g||^2
+test], then round + exact check + ERWA.  The stage runs from a captured CUDA
+graph (fused form).  value = decision-node visits of the forward+adjoint sweep
+(nodes in C_sigma x restarts x iterations run) per second, whole job.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload large_scheduling] [--iters 20] [--tts SECONDS]
+
+Under torchrun (N > 1) every rank runs an independent replica (its own restart
+seeds; the paper runs 8 independent replicas): weak scaling, no collective on
+the data path; rank 0 prints the max-over-ranks time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from workloads import instances as W  # noqa: E402
+
+METRIC = "fwd+adjoint xBDD nodes/s"
+UNIT = "nodes/s"
+
+WORKLOADS = {
+    "large_scheduling": (lambda: W.large_scheduling(1005), 512),
+    "large_scheduling_400": (lambda: W.large_scheduling(1005, n_jobs=400), 512),
+    "placement2d": (lambda: W.placement2d(1003), 1024),
+    "jobshop": (lambda: W.jobshop(1002), 256),
+    "uneven_batch": (lambda: W.concat(W.uneven_batch(1004), "uneven_batch"), 32),
+    "tiny_random": (lambda: W.tiny_random(1001), 64),
+}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="large_scheduling", choices=list(WORKLOADS))
+    p.add_argument("--iters", type=int, default=20, help="PGD iterations per stage (step)")
+    p.add_argument("--eta", type=float, default=None)
+    p.add_argument("--tts", type=float, default=0.0, help="time-to-SAT budget in seconds per form (0 = skip)")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--roofline-launches", type=int, default=10)
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------- oracle timing
+def oracle_sample_rate(inst, R, a, b, w, sigma, budget_s):
+    """The FP64 oracle (as it stands) over a bounded prefix of the constraints of C_sigma.
+
+    Returns (nodes/s, constraints sampled, node-restart visits, seconds)."""
+    from oracle import objective as OBJ
+    D = OBJ.Diagrams(inst)
+    a64, b64, w64 = a.astype(np.float64), b.astype(np.float64), w.astype(np.float64)
+    oc = OBJ.objective_constraints(inst)
+    t0 = time.perf_counter()
+    visits, k = 0, 0
+    while k < len(oc) and time.perf_counter() - t0 < budget_s:
+        c = oc[k]
+        OBJ.constraint_contrib(inst, D, c, a64, b64, w64[c], sigma)
+        visits += len(D[c][0]) * R
+        k += 1
+    dt = time.perf_counter() - t0
+    return visits / dt, k, visits, dt
+
+
+def reference_arm(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    make, R = WORKLOADS[args.workload]
+    inst = make()
+    a, b = W.initial_point(inst, R, seed=7)
+    w = np.ones((inst.n_cons, R), np.float32)
+    sigma = inst.scale / (0.1 * 10)
+    budget = 3.0
+    for _ in range(args.warmup):
+        oracle_sample_rate(inst, R, a, b, w, sigma, budget)
+    visits, secs, ks = 0, 0.0, []
+    for _ in range(args.steps):
+        _, k, v, dt = oracle_sample_rate(inst, R, a, b, w, sigma, budget)
+        visits += v
+        secs += dt
+        ks.append(k)
+    value = visits / secs
+    sample = (f"first {max(ks)} constraints of C_sigma x {R} restarts per step (~{budget:.0f} s of FP64 numpy "
+              f"forward+adjoint each), {inst.name}")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": inst.name, "restarts": R, "n_vars": inst.n_bool + inst.n_real,
+                       "n_cons": inst.n_cons},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------- our arm
+def our_arm(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device("cuda", local)
+    from paper_2603_22877_b300 import Solver, build
+    from paper_2603_22877_b300.engine import Problem
+    build.build()
+    make, R = WORKLOADS[args.workload]
+    inst = make()
+    t_c = time.perf_counter()
+    P = Problem.from_instance(inst)
+    comp = P.compile()
+    compile_s = time.perf_counter() - t_c
+    comp.upload()
+    info = comp.info
+    eta = args.eta if args.eta is not None else 0.02
+    a0, b0 = W.initial_point(inst, R, seed=7 + 1000 * rank)
+    S = Solver(P, comp, R, eta=eta, b_scale=inst.scale, t_max=args.iters, sweeps=20, use_graph=True)
+    S.reset(a0, b0)
+    sched = [inst.scale / (0.1 * t) for t in range(1, 21)]
+    stream = torch.cuda.current_stream()
+    nodes = info["n_obj_nodes"]
+
+    def step(k):
+        S.stage(sched[k % len(sched)], k + 1)
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.steps):
+        step(args.warmup + k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    # a stage stops early only when every restart has converged: count what ran
+    iters_per_step = int(S.iters.max().item())
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    clk = clocks.stop()
+    visits = nodes * R * iters_per_step * args.steps * ws
+    value = visits / (ms / 1000.0)
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    a_h = torch.from_numpy(a0).pin_memory()
+    b_h = torch.from_numpy(b0).pin_memory()
+    nu_h = torch.zeros(R, dtype=torch.int32).pin_memory()
+    ob_h = torch.zeros(R, dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        S.stage_host(sched[k % len(sched)], k + 1, a_h.numpy(), b_h.numpy(), nu_h.numpy(), ob_h.numpy())
+    e2e_s = time.perf_counter() - t0
+    e2e_value = nodes * R * args.iters * args.steps * ws / e2e_s
+    h2d = (inst.n_bool + inst.n_real) * R * 4
+    d2h = R * 8
+
+    # roofline of the dominant kernel: the fused forward+adjoint, timed alone with events
+    da, db, dw = S.a, S.b, S.w
+    ga, gb = torch.zeros_like(da), torch.zeros_like(db)
+    obj = torch.zeros(R, device=dev)
+    sigma = sched[9]
+    for _ in range(2):
+        comp.adjoint(R, sigma, dw, da, db, ga, gb, obj=obj)
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(args.roofline_launches):
+        comp.adjoint(R, sigma, dw, da, db, ga, gb, obj=obj)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    fused_ms = f0.elapsed_time(f1) / args.roofline_launches  # includes the three small memsets
+    structure = nodes * 8 + info["n_atoms"] * 17 + info["atom_nnz"] * 8 + info["n_obj_cons"] * 9
+    state = 4 * R * (info["n_obj_cons"] + 2 * (inst.n_bool + inst.n_real) + 1)
+    alg_bytes = structure + state
+    peaks, peak_kind = load_peaks()
+    achieved = alg_bytes / (fused_ms / 1000.0) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_kind": peak_kind,
+                "kernel": "k_fused<true> (forward + adjoint)", "kernel_ms": fused_ms,
+                "algorithmic_bytes": alg_bytes,
+                "node_visits_per_s": nodes * R / (fused_ms / 1000.0)}
+
+    # plain (unfused) form of the same forward+adjoint, for comparison
+    plain = None
+    try:
+        nwork = comp.plain_work(R)
+        if nwork * 4 < 0.6 * torch.cuda.mem_get_info()[0]:
+            work = torch.empty(nwork, device=dev)
+            for _ in range(2):
+                comp.forward_plain(R, sigma, dw, da, db, work, obj=obj)
+                comp.adjoint_plain(R, sigma, dw, da, db, work, ga, gb)
+            torch.cuda.synchronize()
+            f0.record(stream)
+            for _ in range(3):
+                comp.forward_plain(R, sigma, dw, da, db, work, obj=obj)
+                comp.adjoint_plain(R, sigma, dw, da, db, work, ga, gb)
+            f1.record(stream)
+            torch.cuda.synchronize()
+            pms = f0.elapsed_time(f1) / 3
+            plain = {"ms_per_fwd_adj": pms, "node_visits_per_s": nodes * R / (pms / 1000.0),
+                     "fused_speedup": pms / fused_ms}
+            del work
+    except Exception as e:  # report, never hide
+        plain = {"error": str(e)}
+
+    tts = None
+    if args.tts > 0:
+        S.reset(a0, b0)
+        S.t_max = 200
+        res = S.anneal(sched, time_limit=args.tts)
+        tts = {"fused": {"sat": res["sat"], "seconds": res["seconds"], "stage": res["stage"],
+                         "restart": res["restart"]}}
+        S.t_max = args.iters
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, k, v, dt = oracle_sample_rate(inst, R, a0, b0, np.ones((inst.n_cons, R), np.float32), sigma, 15.0)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"first {k} constraints of C_sigma x {R} restarts, FP64 numpy forward+adjoint, "
+                         f"{dt:.1f} s on the host"}
+    launches_per_step = 2 + args.iters * (3 + (inst.n_bool > 0) + (info["n_free_reals"] > 0) +
+                                          (info["n_components"] > 0)) + 1
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": inst.name, "restarts": R, "n_vars": inst.n_bool + inst.n_real,
+                           "n_bool": inst.n_bool, "n_real": inst.n_real, "n_cons": inst.n_cons,
+                           "n_obj_cons": info["n_obj_cons"], "n_obj_nodes": nodes, "atoms": inst.n_atoms,
+                           "iters_per_step": iters_per_step, "eta": eta, "form": "fused + CUDA graph",
+                           "l2": "inputs larger than L2 (diagrams + weights > 126 MB)",
+                           "compile_s": compile_s, "parallelism": f"replicas x{ws}"},
+                "roofline": roofline, "cpu_baseline": cpu,
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "gpu_launches": launches_per_step * args.steps, "clocks": clk, "plain": plain,
+                "time_to_sat": tts}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        our_arm(args)
+
+
+if __name__ == "__main__":
+    main()

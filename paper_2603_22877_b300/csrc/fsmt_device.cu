@@ -744,6 +744,7 @@ fsmt_status fsmt_upload(fsmt_compiled* cc, void* stream) {
 void fsmt_free_compiled(fsmt_compiled* cc) {
   if (!cc) return;
   if (cc->c.graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)cc->c.graph_exec);
+  if (cc->c.capture_stream) cudaStreamDestroy((cudaStream_t)cc->c.capture_stream);
   if (cc->c.dev_block) cudaFree(cc->c.dev_block);
   delete cc;
 }
@@ -910,6 +911,16 @@ fsmt_status fsmt_solve_stage(fsmt_compiled* cc, const fsmt_stage_config* cfg, fs
                                 (float)cfg->update_w, (float)cfg->sweeps);
   FSMT_CUDA(cudaGetLastError(), "set params");
   if (!cfg->use_graph) return enqueue_stage(C, cfg->t_max, s, st);
+  // the legacy default stream cannot be captured: use a blocking stream of our own,
+  // which the legacy stream's implicit synchronisation orders with the caller's work
+  if (st == nullptr || st == cudaStreamLegacy) {
+    if (!C.capture_stream) {
+      cudaStream_t cs;
+      FSMT_CUDA(cudaStreamCreate(&cs), "create capture stream");
+      C.capture_stream = cs;
+    }
+    st = (cudaStream_t)C.capture_stream;
+  }
   // one graph per (buffer set, R, t_max)
   uint64_t key = 1469598103934665603ull;
   auto mix = [&](uint64_t v) { key = (key ^ v) * 1099511628211ull; };

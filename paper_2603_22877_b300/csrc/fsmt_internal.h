@@ -96,6 +96,7 @@ struct Compiled {
   // cached CUDA graph of a stage (fsmt_device.cu)
   void* graph_exec = nullptr;
   uint64_t graph_key = 0;
+  void* capture_stream = nullptr;  // used when the caller passes the legacy default stream
 };
 
 // Exact sign of  sum_t c_t * y_t - q0  where c_t are integers with |c_t| < 2^24

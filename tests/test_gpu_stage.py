@@ -1,0 +1,132 @@
+"""PGD step with projection, rounding + exact check + ERWA, and whole annealing
+stages: CUDA path vs the FP64 oracle."""
+import numpy as np
+import pytest
+
+from oracle import objective as OBJ, pgd
+from workloads import instances as W
+
+from _gpu_common import setup, sigmas_for, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("make,R", [(lambda: W.jobshop(1002, 10, 5), 70), (lambda: W.tiny_random(1001), 45),
+                                    (lambda: W.large_scheduling(1005, 16, 30, 6, 4, 5), 40)])
+def test_pgd_step_parity(make, R):
+    import torch
+    inst = make()
+    P, comp, a, b, w = setup(inst, R)
+    sigma = sigmas_for(inst)[1]
+    _, _, ga, gb = OBJ.evaluate(inst, a.astype(np.float64), b.astype(np.float64), w.astype(np.float64), sigma)
+    ga32, gb32 = ga.astype(np.float32), gb.astype(np.float32)
+    eta = 0.05
+    dom = pgd.Domain(inst)
+    a_ref, b_ref, gn_ref = pgd.pgd_step(a.astype(np.float64), b.astype(np.float64), ga32.astype(np.float64),
+                                        gb32.astype(np.float64), eta, inst.scale, dom, 20)
+    da, db, dga, dgb = to_dev(a, b, ga32, gb32)
+    gn = torch.zeros(R, device="cuda")
+    active = torch.ones(R, dtype=torch.uint8, device="cuda")
+    active[1::3] = 0
+    comp.pgd_step(R, eta, inst.scale, 20, da, db, dga, dgb, gn, active)
+    act = active.cpu().numpy().astype(bool)
+    a_out, b_out = da.cpu().numpy(), db.cpu().numpy()
+    np.testing.assert_allclose(a_out[:, act], a_ref[:, act], atol=2e-6)
+    np.testing.assert_array_equal(a_out[:, ~act], a[:, ~act])
+    scale_b = max(1.0, float(np.abs(b_ref).max()))
+    np.testing.assert_allclose(b_out[:, act], b_ref[:, act], atol=2e-5 * scale_b)
+    np.testing.assert_array_equal(b_out[:, ~act], b[:, ~act])
+    np.testing.assert_allclose(gn.cpu().numpy(), gn_ref, rtol=2e-4, atol=1e-6)
+
+
+@pytest.mark.parametrize("make,R", [(lambda: W.tiny_random(1001), 45), (lambda: W.jobshop(1002, 10, 5), 64),
+                                    (lambda: W.placement2d(1003, 20), 33),
+                                    (lambda: W.large_scheduling(1005, 16, 30, 6, 4, 5), 37)])
+def test_round_check_erwa_parity(make, R):
+    import torch
+    inst = make()
+    P, comp, a, b, w = setup(inst, R)
+    # a third of the restarts sit exactly on the planted assignment (every constraint
+    # holds, many atoms exactly on their boundary), a third are planted with a few flips
+    rng = np.random.default_rng(3)
+    a, b = a.copy(), b.copy()
+    a[:, ::3] = 0.5 * inst.planted_x[:, None]
+    b[:, ::3] = inst.planted_y[:, None]
+    a[:, 1::3] = 0.5 * inst.planted_x[:, None] * np.where(rng.random((inst.n_bool, 1)) < 0.05, -1, 1)
+    b[:, 1::3] = inst.planted_y[:, None]
+    h0 = rng.uniform(0, 2, (inst.n_cons, R)).astype(np.float32)
+    x_ref, viol_ref = pgd.round_check(inst, a.astype(np.float64), b.astype(np.float64))
+    for update_w in (True, False):
+        w_ref, h_ref, nu_ref = pgd.erwa(w.astype(np.float64), h0.astype(np.float64), viol_ref.astype(np.float64),
+                                        1, 0.5, 2.0, 1 if update_w else 2)
+        da, db, dw, dh = to_dev(a, b, w, h0)
+        x = torch.zeros((inst.n_bool, R), dtype=torch.int8, device="cuda")
+        viol = torch.zeros((inst.n_cons, R), dtype=torch.uint8, device="cuda")
+        nu = torch.zeros(R, dtype=torch.int32, device="cuda")
+        comp.round_check(R, da, db, nu, x=x, violated=viol, w=dw, h=dh, rho=0.5, gamma=2.0, update_w=update_w)
+        np.testing.assert_array_equal(x.cpu().numpy(), x_ref)
+        np.testing.assert_array_equal(viol.cpu().numpy().astype(bool), viol_ref)
+        np.testing.assert_array_equal(nu.cpu().numpy(), nu_ref.astype(np.int32))
+        np.testing.assert_allclose(dw.cpu().numpy(), w_ref, rtol=2e-6)
+        np.testing.assert_allclose(dh.cpu().numpy(), h_ref, rtol=1e-6, atol=1e-6)
+    assert (nu_ref[::3] == 0).all()
+
+
+def _solver(inst, R, comp, P, **kw):
+    from paper_2603_22877_b300 import Solver
+    return Solver(P, comp, R, **kw)
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_stage_matches_oracle_first_iterations(use_graph):
+    """A stage of 5 PGD iterations then round/check/ERWA: GPU vs oracle run_stage."""
+    inst = W.jobshop(1002, 10, 5)
+    R = 40
+    P, comp, a, b, _ = setup(inst, R)
+    eta = 0.02
+    cfg = pgd.Config(eta=eta, t_max=5, sweeps=20)
+    S = _solver(inst, R, comp, P, eta=eta, b_scale=inst.scale, t_max=5, sweeps=20, use_graph=use_graph)
+    S.reset(a, b)
+    sigma = sigmas_for(inst)[0]
+    S.stage(sigma, 1)
+    w0 = np.ones((inst.n_cons, R))
+    h0 = np.zeros((inst.n_cons, R))
+    a_ref, b_ref, w_ref, h_ref, nu_ref, its_ref, obj_ref = pgd.run_stage(inst, a, b, w0, h0, sigma, 1, cfg)
+    np.testing.assert_allclose(S.a.cpu().numpy(), a_ref, atol=1e-4)
+    np.testing.assert_allclose(S.b.cpu().numpy(), b_ref, atol=1e-4 * inst.meta["horizon"])
+    np.testing.assert_array_equal(S.iters.cpu().numpy(), its_ref)
+    np.testing.assert_allclose(S.obj.cpu().numpy(), obj_ref, rtol=1e-4, atol=1e-3)
+    # the check and ERWA on the GPU's own final point are exact
+    _, viol = pgd.round_check(inst, S.a.cpu().numpy().astype(np.float64), S.b.cpu().numpy().astype(np.float64))
+    np.testing.assert_array_equal(S.n_unsat.cpu().numpy(), viol.sum(0))
+    np.testing.assert_allclose(S.w.cpu().numpy(), np.power(2.0, viol.astype(np.float64)), rtol=1e-6)
+    assert (S.h.cpu().numpy() == 1.0).all()
+
+
+def test_stage_epsilon_rule_stops_restarts():
+    """With eps large every restart stops after its first iteration (Eq. critical)."""
+    inst = W.tiny_random(1001)
+    R = 50
+    P, comp, a, b, _ = setup(inst, R)
+    S = _solver(inst, R, comp, P, eta=0.01, b_scale=inst.scale, t_max=7, eps=1e6)
+    S.reset(a, b)
+    S.stage(sigmas_for(inst)[0], 1)
+    assert (S.iters.cpu().numpy() == 1).all()
+    assert int(S.ctl[0].item()) == 0 and int(S.ctl[1].item()) == 0
+
+
+def test_stage_host_buffers_match_device():
+    inst = W.jobshop(1002, 10, 5)
+    R = 64
+    P, comp, a, b, _ = setup(inst, R)
+    S1 = _solver(inst, R, comp, P, eta=0.02, b_scale=inst.scale, t_max=4)
+    S1.reset(a, b)
+    S1.stage(sigmas_for(inst)[0], 1)
+    S2 = _solver(inst, R, comp, P, eta=0.02, b_scale=inst.scale, t_max=4)
+    S2.reset(a, b)
+    nu = np.zeros(R, np.int32)
+    ob = np.zeros(R, np.float32)
+    S2.stage_host(sigmas_for(inst)[0], 1, np.ascontiguousarray(a), np.ascontiguousarray(b), nu, ob)
+    np.testing.assert_allclose(S2.a.cpu().numpy(), S1.a.cpu().numpy(), atol=1e-5)
+    np.testing.assert_allclose(ob, S1.obj.cpu().numpy(), rtol=1e-5, atol=1e-3)
+    np.testing.assert_array_equal(nu, S2.n_unsat.cpu().numpy())
