@@ -203,18 +203,31 @@ fsmt_status fsmt_adjoint_plain(const fsmt_compiled* c, int32_t R, float sigma, c
                                const float* b, float* work, float* grad_a, float* grad_b, void* stream);
 
 /* ------------------------------------------------------------ PGD step --
- * Eq. pg1 / pg2 and Eq. grad_map, in coordinates where the reals are divided by
- * b_scale (> 0): a' = a - eta grad_a, b' = b - eta b_scale^2 grad_b,
- * (a, b) <- proj_D(a', b') with D = [-1,1]^n x box x half-spaces (clamps; Dykstra's
- * alternating projections with `sweeps` sweeps per block of coupled reals,
- * half-spaces in constraint order then the box), and
- * gnorm2[r] += sum ((a - a_new)/eta)^2 + sum ((b - b_new)/(b_scale eta))^2.
+ * fsmt_weight_sum: wsum[r] = sum over the constraints of C_sigma of w[c][r]
+ * (device w[n_cons][R] in, device wsum[R] overwritten) -- alpha of Prop.
+ * Lipschitz per restart.  Errors as above.
+ *
+ * fsmt_pgd_step: Eq. pg1 / pg2 and Eq. grad_map, in coordinates where the reals
+ * are divided by b_scale (> 0).  Step of restart r: eta_r = eta, or, when wsum
+ * is given, eta_r = eta * n_obj / wsum[r] (Thm. max_step takes eta = 1/L with L
+ * proportional to the total weight; the ERWA weights grow every stage).
+ * a' = a - eta_r grad_a, b' = b - eta_r b_scale^2 grad_b,
+ * (a, b) <- proj_D(a', b') with D = [-1,1]^n x box x half-spaces: clamps, and for
+ * each block of reals coupled by half-spaces, `sweeps` sweeps of Dykstra's
+ * alternating projections (half-spaces in constraint order, then the box)
+ * followed by up to `polish` passes that project each half-space q.y <= q0 with
+ * q.y > q0 - m onto q.y <= q0 - m, m = 2^-16 (|q0| + sum |q_j y_j|), then clamp
+ * the box, until a pass moves nothing (so the result lies in D exactly once the
+ * passes settle); then
+ * gnorm2[r] += sum ((a - a_new)/eta_r)^2 + sum ((b - b_new)/(b_scale eta_r))^2.
  * a, b (device, [n][R], [m][R]) are updated in place for restarts with
  * active[r] != 0 (active may be NULL = all); gnorm2[R] (device) is accumulated,
- * so the caller zeroes it first.  eta > 0, sweeps >= 0.  Errors as above. */
+ * so the caller zeroes it first.  eta > 0, sweeps >= 0, polish >= 0; wsum (device
+ * [R]) may be NULL.  Errors as above. */
+fsmt_status fsmt_weight_sum(const fsmt_compiled* c, int32_t R, const float* w, float* wsum, void* stream);
 fsmt_status fsmt_pgd_step(const fsmt_compiled* c, int32_t R, float eta, float b_scale, int32_t sweeps,
-                          float* a, float* b, const float* grad_a, const float* grad_b, float* gnorm2,
-                          const uint8_t* active, void* stream);
+                          int32_t polish, float* a, float* b, const float* grad_a, const float* grad_b,
+                          const float* wsum, float* gnorm2, const uint8_t* active, void* stream);
 
 /* ------------------------------------------------------- round + check --
  * Alg. 1's rounding x = sgn(a) (x_i = TRUE = -1 iff a_i < 0), y = b, and an exact
@@ -229,7 +242,8 @@ fsmt_status fsmt_round_check(const fsmt_compiled* c, int32_t R, const float* a, 
                              int32_t update_w, void* stream);
 
 /* ------------------------------------------------------- one sigma stage --
- * One stage of Alg. 2 for all restarts: up to t_max iterations of
+ * One stage of Alg. 2 for all restarts: wsum from fsmt_weight_sum, then up to
+ * t_max iterations of
  * [fused forward + adjoint -> PGD step + projection -> ||g||^2 test] with the
  * epsilon rule of Eq. critical applied per restart (an iteration's update is
  * applied, then a restart with ||g||^2 <= eps^2 stops for the rest of the
@@ -255,6 +269,7 @@ typedef struct {
   int32_t* n_unsat;/* [R] */
   int32_t* ctl;    /* [4] */
   float* params;   /* [16] */
+  float* wsum;     /* [R] total weight of C_sigma per restart, computed at stage start */
 } fsmt_state;
 
 typedef struct {
@@ -263,6 +278,8 @@ typedef struct {
   float rho, gamma;
   int32_t update_w;
   int32_t use_graph;
+  int32_t polish;        /* feasibility passes after Dykstra (see fsmt_pgd_step) */
+  int32_t normalize_eta; /* 1: eta_r = eta * n_obj / wsum[r] */
 } fsmt_stage_config;
 
 fsmt_status fsmt_solve_stage(fsmt_compiled* c, const fsmt_stage_config* cfg, fsmt_state* s, void* stream);

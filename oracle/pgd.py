@@ -11,8 +11,12 @@ Follows, in the paper's order:
     clamp).  Multi-variable unit atoms are half-spaces; the projection onto
     box n half-spaces uses Dykstra's alternating projections (Boyle & Dykstra
     1986) with a fixed number of sweeps, half-spaces in constraint order and
-    the box last in each sweep -- the paper names no QP method, so this is a
-    documented reading, exact only in the limit.
+    the box last in each sweep, followed by a short feasibility polish so that
+    the point lies in D exactly -- the paper names no QP method, so this is a
+    documented reading (the projection it approximates is exact in the limit).
+  * Step size: Thm. max_step takes eta = 1/L with L proportional to the total
+    weight alpha (Prop. Lipschitz); with ERWA growing the weights, the step is
+    eta_r = eta |C_sigma| / alpha_r per restart (a documented reading).
   * Eq. grad_map: g = ((a, b) - proj(...)) / eta, measured in the scaled
     coordinates, and the epsilon-critical stopping rule ||g||^2 <= eps^2
     (Eq. critical), applied per restart.
@@ -48,8 +52,26 @@ class Config:
     gamma: float = 2.0
     tau: int = 1
     sweeps: int = 20
+    polish: int = 8
+    normalize_eta: bool = True
     policy: int = OBJ.PROJECT
     inv_sigma: list = field(default_factory=lambda: [0.1 * t for t in range(1, 21)])  # times 1/S
+
+
+POLISH_MARGIN = 2.0 ** -16
+
+
+def step_sizes(inst, w, cfg, policy=None):
+    """Per-restart step size.  With normalize_eta, eta_r = eta |C_sigma| / sum_c w_c[r]:
+    Thm. max_step takes eta = 1/L with L proportional to alpha = sum_c w_c (Prop.
+    Lipschitz), so the step shrinks as ERWA grows the weights."""
+    R = w.shape[1]
+    if not cfg.normalize_eta:
+        return np.full(R, cfg.eta)
+    oc = OBJ.objective_constraints(inst, cfg.policy if policy is None else policy)
+    if not oc:
+        return np.full(R, cfg.eta)
+    return cfg.eta * len(oc) / w[oc].sum(0)
 
 
 # ---------------------------------------------------------------------------
@@ -82,8 +104,15 @@ class Domain:
             else:
                 self.halfspaces.append((np.asarray(var, np.int64), np.asarray(coef, np.float64), float(q0)))
 
-    def project_b(self, bp, sweeps):
-        """proj onto box n half-spaces of points bp [m][R] (Dykstra; exact clamp if no half-space)."""
+    def project_b(self, bp, sweeps, polish=8):
+        """proj onto box n half-spaces of points bp [m][R] (Dykstra; exact clamp if no half-space).
+
+        After the Dykstra sweeps, up to `polish` passes make the point feasible:
+        each half-space q.y <= q0 whose value is above -margin is projected onto
+        q.y <= q0 - margin (margin = 2^-16 (|q0| + sum |q_j y_j|), far above the
+        rounding error of evaluating q.y), then the box is clamped; a restart stops
+        when a pass moves nothing.  The result satisfies every half-space exactly
+        whenever the passes settle."""
         x = np.clip(bp, self.lo[:, None], self.hi[:, None])
         if not self.halfspaces:
             return x
@@ -102,13 +131,29 @@ class Domain:
             xn = np.clip(yv, self.lo[J][:, None], self.hi[J][:, None])
             p_box = yv - xn
             x[J] = xn
+        for _ in range(polish):
+            moved = np.zeros(R, bool)
+            for var, q, q0 in self.halfspaces:
+                xv = x[var]
+                v = (q[:, None] * xv).sum(0) - q0
+                margin = POLISH_MARGIN * (abs(q0) + (np.abs(q[:, None] * xv)).sum(0))
+                need = v > -margin
+                step = np.where(need, (v + margin) / float((q * q).sum()), 0.0)
+                x[var] = xv - step[None, :] * q[:, None]
+                moved |= need
+            x[J] = np.clip(x[J], self.lo[J][:, None], self.hi[J][:, None])
+            if not moved.any():
+                break
         return x
 
 
-def pgd_step(a, b, ga, gb, eta, scale, dom, sweeps):
-    """One PGD step (Eq. pg1, pg2) and ||g||^2 (Eq. grad_map, scaled coordinates)."""
+def pgd_step(a, b, ga, gb, eta, scale, dom, sweeps, polish=8):
+    """One PGD step (Eq. pg1, pg2) and ||g||^2 (Eq. grad_map, scaled coordinates).
+
+    eta is a scalar or one step size per restart ([R])."""
+    eta = np.asarray(eta, np.float64)
     a_new = np.clip(a - eta * ga, -1.0, 1.0)
-    b_new = dom.project_b(b - eta * scale * scale * gb, sweeps)
+    b_new = dom.project_b(b - eta * scale * scale * gb, sweeps, polish)
     gn2 = (((a - a_new) / eta) ** 2).sum(0) + (((b - b_new) / (scale * eta)) ** 2).sum(0)
     return a_new, b_new, gn2
 
@@ -193,9 +238,10 @@ def run_stage(inst, a, b, w, h, sigma, t, cfg: Config, dom=None, diagrams=None, 
     active = np.ones(R, bool)
     its = np.zeros(R, np.int64)
     obj = np.zeros(R)
+    etas = step_sizes(inst, w, cfg)
     for _ in range(cfg.t_max if iters is None else iters):
         obj, _, ga, gb = OBJ.evaluate(inst, a, b, w, sigma, cfg.policy, diagrams)
-        a_new, b_new, gn2 = pgd_step(a, b, ga, gb, cfg.eta, inst.scale, dom, cfg.sweeps)
+        a_new, b_new, gn2 = pgd_step(a, b, ga, gb, etas, inst.scale, dom, cfg.sweeps, cfg.polish)
         a[:, active] = a_new[:, active]
         b[:, active] = b_new[:, active]
         its += active

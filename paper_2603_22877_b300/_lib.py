@@ -40,7 +40,8 @@ class State(C.Structure):
 class StageConfig(C.Structure):
     _fields_ = [("sigma", C.c_float), ("eta", C.c_float), ("b_scale", C.c_float), ("eps", C.c_float),
                 ("t_max", C.c_int32), ("sweeps", C.c_int32), ("rho", C.c_float), ("gamma", C.c_float),
-                ("update_w", C.c_int32), ("use_graph", C.c_int32)]
+                ("update_w", C.c_int32), ("use_graph", C.c_int32), ("polish", C.c_int32),
+                ("normalize_eta", C.c_int32)]
 
 
 P = C.c_void_p
@@ -66,7 +67,8 @@ PROTOTYPES = {
     "fsmt_plain_work_floats": [P, i32, C.POINTER(i64)],
     "fsmt_forward_plain": [P, i32, f32, P, P, P, P, P, P, P],
     "fsmt_adjoint_plain": [P, i32, f32, P, P, P, P, P, P, P],
-    "fsmt_pgd_step": [P, i32, f32, f32, i32, P, P, P, P, P, P, P],
+    "fsmt_weight_sum": [P, i32, P, P, P],
+    "fsmt_pgd_step": [P, i32, f32, f32, i32, i32, P, P, P, P, P, P, P, P],
     "fsmt_round_check": [P, i32, P, P, P, P, P, P, P, f32, f32, i32, P],
     "fsmt_solve_stage": [P, C.POINTER(StageConfig), C.POINTER(State), P],
     "fsmt_solve_stage_host": [P, C.POINTER(StageConfig), C.POINTER(State), P, P, P, P, P],

@@ -24,7 +24,8 @@ constexpr int kSmemBudget = 112 * 1024;
 constexpr int kMaxObjSmemR = 4096;
 
 // stage parameter slots (device float[16])
-enum { P_SIGMA = 0, P_ETA, P_BSCALE, P_EPS, P_RHO, P_GAMMA, P_UPDATE_W, P_SWEEPS };
+enum { P_SIGMA = 0, P_ETA, P_BSCALE, P_EPS, P_RHO, P_GAMMA, P_UPDATE_W, P_SWEEPS, P_POLISH, P_NORM };
+constexpr float kPolishMargin = 1.52587890625e-05f;  // 2^-16
 
 fsmt_status cuda_fail(cudaError_t e, const char* what) {
   set_error(std::string(what) + ": " + cudaGetErrorString(e));
@@ -309,6 +310,9 @@ __global__ void k_adj_plain(DevView d, int R, const float* __restrict__ w, const
 // ------------------------------------------------------------- PGD step --
 // Eq. pg1 / pg2 with the b-step scaled by b_scale^2, projection onto D, and the
 // per-restart ||g||^2 of Eq. grad_map.  Block = 32 restarts x 8 row groups.
+// With wsum (per-restart total weight of C_sigma) the step of restart r is
+// eta * n_obj / wsum[r] (Thm. max_step: eta = 1/L with L proportional to the
+// total weight, Prop. Lipschitz).
 __device__ __forceinline__ void reduce_rows_add(float part, float* gn2, int r, bool ok) {
   __shared__ float red[8][33];
   red[threadIdx.y][threadIdx.x] = part;
@@ -320,14 +324,26 @@ __device__ __forceinline__ void reduce_rows_add(float part, float* gn2, int r, b
   }
 }
 
-__global__ void k_pgd_bool(DevView d, int R, float eta, const float* prm, float* __restrict__ a,
-                           float* __restrict__ ga, float* __restrict__ gn2, const uint8_t* __restrict__ active,
-                           int clear_grad, const int* ctl) {
-  if (ctl && ctl[0] == 0) return;
+__device__ __forceinline__ float restart_eta(const DevView& d, float eta, const float* prm, const float* wsum,
+                                             int r, bool ok) {
   eta = load_param(prm, P_ETA, eta);
+  if (prm && prm[P_NORM] == 0.f) wsum = nullptr;
+  if (wsum && ok && d.n_obj > 0) {
+    const float ws = wsum[r];
+    if (ws > 0.f) eta *= (float)d.n_obj / ws;
+  }
+  return eta;
+}
+
+__global__ void k_pgd_bool(DevView d, int R, float eta, const float* prm, const float* __restrict__ wsum,
+                           float* __restrict__ a, float* __restrict__ ga, float* __restrict__ gn2,
+                           const uint8_t* __restrict__ active, int clear_grad, const int* ctl) {
+  if (ctl && ctl[0] == 0) return;
   const int r = blockIdx.x * 32 + threadIdx.x;
   const bool ok = r < R;
   const bool act = ok && (!active || active[r]);
+  eta = restart_eta(d, eta, prm, wsum, r, ok);
+  const float inv = 1.f / eta;
   float part = 0.f;
   if (ok) {
     for (int i = blockIdx.y * blockDim.y + threadIdx.y; i < d.n_bool; i += gridDim.y * blockDim.y) {
@@ -335,7 +351,7 @@ __global__ void k_pgd_bool(DevView d, int R, float eta, const float* prm, float*
       const float av = a[k];
       const float g = ga[k];
       const float an = fminf(fmaxf(av - eta * g, -1.f), 1.f);
-      const float q = (av - an) / eta;
+      const float q = (av - an) * inv;
       part = fmaf(q, q, part);
       if (act) a[k] = an;
       if (clear_grad) ga[k] = 0.f;
@@ -344,16 +360,17 @@ __global__ void k_pgd_bool(DevView d, int R, float eta, const float* prm, float*
   reduce_rows_add(part, gn2, r, ok);
 }
 
-__global__ void k_pgd_free(DevView d, int R, float eta, float bscale, const float* prm, float* __restrict__ b,
-                           float* __restrict__ gb, float* __restrict__ gn2, const uint8_t* __restrict__ active,
-                           int clear_grad, const int* ctl) {
+__global__ void k_pgd_free(DevView d, int R, float eta, float bscale, const float* prm,
+                           const float* __restrict__ wsum, float* __restrict__ b, float* __restrict__ gb,
+                           float* __restrict__ gn2, const uint8_t* __restrict__ active, int clear_grad,
+                           const int* ctl) {
   if (ctl && ctl[0] == 0) return;
-  eta = load_param(prm, P_ETA, eta);
-  bscale = load_param(prm, P_BSCALE, bscale);
-  const float step = eta * bscale * bscale, inv = 1.f / (bscale * eta);
   const int r = blockIdx.x * 32 + threadIdx.x;
   const bool ok = r < R;
   const bool act = ok && (!active || active[r]);
+  eta = restart_eta(d, eta, prm, wsum, r, ok);
+  bscale = load_param(prm, P_BSCALE, bscale);
+  const float step = eta * bscale * bscale, inv = 1.f / (bscale * eta);
   float part = 0.f;
   if (ok) {
     for (int t = blockIdx.y * blockDim.y + threadIdx.y; t < d.n_free; t += gridDim.y * blockDim.y) {
@@ -372,18 +389,27 @@ __global__ void k_pgd_free(DevView d, int R, float eta, float bscale, const floa
 
 // Dykstra's alternating projections on one block of coupled reals, one thread
 // per (block, restart); the block's reals and the half-space increments stay in
-// thread-local arrays.  Per sweep: every half-space in constraint order, then the box.
-__global__ void k_pgd_comp(DevView d, int R, float eta, float bscale, int sweeps, const float* prm,
-                           float* __restrict__ b, float* __restrict__ gb, float* __restrict__ gn2,
-                           const uint8_t* __restrict__ active, int clear_grad, const int* ctl) {
+// thread-local arrays.  Per sweep: every half-space in constraint order, then
+// the box.  Then up to `polish` passes: each half-space q.y <= q0 whose value is
+// above -margin, margin = 2^-16 (|q0| + sum |q_j y_j|) (far above the FP32
+// rounding of q.y), is projected onto q.y <= q0 - margin, then the box is
+// clamped; the thread stops at the first pass that moves nothing, so the point
+// it returns satisfies every half-space exactly whenever the passes settle.
+__global__ void k_pgd_comp(DevView d, int R, float eta, float bscale, int sweeps, int polish, const float* prm,
+                           const float* __restrict__ wsum, float* __restrict__ b, float* __restrict__ gb,
+                           float* __restrict__ gn2, const uint8_t* __restrict__ active, int clear_grad,
+                           const int* ctl) {
   if (ctl && ctl[0] == 0) return;
-  eta = load_param(prm, P_ETA, eta);
-  bscale = load_param(prm, P_BSCALE, bscale);
-  if (prm) sweeps = (int)prm[P_SWEEPS];
-  const float step = eta * bscale * bscale, inv = 1.f / (bscale * eta);
   const int r = blockIdx.x * 32 + threadIdx.x;
   const bool ok = r < R;
   const bool act = ok && (!active || active[r]);
+  eta = restart_eta(d, eta, prm, wsum, r, ok);
+  bscale = load_param(prm, P_BSCALE, bscale);
+  if (prm) {
+    sweeps = (int)prm[P_SWEEPS];
+    polish = (int)prm[P_POLISH];
+  }
+  const float step = eta * bscale * bscale, inv = 1.f / (bscale * eta);
   float part = 0.f;
   if (ok) {
     for (int c = blockIdx.y * blockDim.y + threadIdx.y; c < d.n_comp; c += gridDim.y * blockDim.y) {
@@ -424,6 +450,30 @@ __global__ void k_pgd_comp(DevView d, int R, float eta, float bscale, int sweeps
           const int j = d.comp_var[v0 + t];
           x[t] = fminf(fmaxf(x[t], d.lo[j]), d.hi[j]);
         }
+      for (int pass = 0; pass < polish; ++pass) {
+        bool moved = false;
+        for (int q = 0; q < nh; ++q) {
+          const int e0 = d.hs_ptr[h0 + q], e1 = d.hs_ptr[h0 + q + 1];
+          const float q0 = d.hs_q0[h0 + q];
+          float v = -q0, mag = fabsf(q0);
+          for (int e = e0; e < e1; ++e) {
+            const float term = d.hs_coef[e] * x[d.hs_lvar[e]];
+            v += term;
+            mag += fabsf(term);
+          }
+          const float margin = kPolishMargin * mag;
+          if (v > -margin) {
+            const float tq = (v + margin) * d.hs_inv_qq[h0 + q];
+            for (int e = e0; e < e1; ++e) x[d.hs_lvar[e]] = fmaf(-tq, d.hs_coef[e], x[d.hs_lvar[e]]);
+            moved = true;
+          }
+        }
+        for (int t = 0; t < nv; ++t) {
+          const int j = d.comp_var[v0 + t];
+          x[t] = fminf(fmaxf(x[t], d.lo[j]), d.hi[j]);
+        }
+        if (!moved) break;
+      }
       for (int t = 0; t < nv; ++t) {
         const float q = (old[t] - x[t]) * inv;
         part = fmaf(q, q, part);
@@ -434,9 +484,20 @@ __global__ void k_pgd_comp(DevView d, int R, float eta, float bscale, int sweeps
   reduce_rows_add(part, gn2, r, ok);
 }
 
+// wsum[r] += sum over the constraints of C_sigma of w[c][r] (caller zeroes wsum).
+__global__ void k_weight_sum(DevView d, int R, const float* __restrict__ w, float* __restrict__ wsum) {
+  const int r = blockIdx.x * 32 + threadIdx.x;
+  const bool ok = r < R;
+  float part = 0.f;
+  if (ok)
+    for (int s = blockIdx.y * blockDim.y + threadIdx.y; s < d.n_obj; s += gridDim.y * blockDim.y)
+      part += w[(size_t)d.con_id[s] * R + r];
+  reduce_rows_add(part, wsum, r, ok);
+}
+
 // ------------------------------------------------------- stage bookkeeping --
 __global__ void k_set_params(float* prm, float sigma, float eta, float bscale, float eps, float rho, float gamma,
-                             float update_w, float sweeps) {
+                             float update_w, float sweeps, float polish, float norm) {
   prm[P_SIGMA] = sigma;
   prm[P_ETA] = eta;
   prm[P_BSCALE] = bscale;
@@ -445,6 +506,8 @@ __global__ void k_set_params(float* prm, float sigma, float eta, float bscale, f
   prm[P_GAMMA] = gamma;
   prm[P_UPDATE_W] = update_w;
   prm[P_SWEEPS] = sweeps;
+  prm[P_POLISH] = polish;
+  prm[P_NORM] = norm;
 }
 
 __global__ void k_stage_begin(int R, uint8_t* active, int* iters, int* ctl) {
@@ -607,9 +670,9 @@ fsmt_status launch_fused(const Compiled& C, bool adj, int R, float sigma, const 
   return FSMT_OK;
 }
 
-fsmt_status launch_pgd(const Compiled& C, int R, float eta, float bscale, int sweeps, const float* prm, float* a,
-                       float* b, float* ga, float* gb, float* gn2, const uint8_t* active, int clear, const int* ctl,
-                       cudaStream_t st) {
+fsmt_status launch_pgd(const Compiled& C, int R, float eta, float bscale, int sweeps, int polish, const float* prm,
+                       const float* wsum, float* a, float* b, float* ga, float* gb, float* gn2,
+                       const uint8_t* active, int clear, const int* ctl, cudaStream_t st) {
   const int tiles = (R + 31) / 32;
   const dim3 blk(32, 8);
   // enough blocks to fill the GPU a few times; each thread strides over rows
@@ -618,15 +681,27 @@ fsmt_status launch_pgd(const Compiled& C, int R, float eta, float bscale, int sw
     return (int)std::max<long>(1, std::min<long>(std::min<long>((n + 7) / 8, cap), 65535L));
   };
   if (C.n_bool > 0)
-    k_pgd_bool<<<dim3(tiles, rows(C.n_bool)), blk, 0, st>>>(C.view, R, eta, prm, a, ga, gn2, active, clear, ctl);
+    k_pgd_bool<<<dim3(tiles, rows(C.n_bool)), blk, 0, st>>>(C.view, R, eta, prm, wsum, a, ga, gn2, active, clear,
+                                                            ctl);
   if (!C.free_var.empty())
-    k_pgd_free<<<dim3(tiles, rows((long)C.free_var.size())), blk, 0, st>>>(C.view, R, eta, bscale, prm, b, gb, gn2,
-                                                                           active, clear, ctl);
+    k_pgd_free<<<dim3(tiles, rows((long)C.free_var.size())), blk, 0, st>>>(C.view, R, eta, bscale, prm, wsum, b, gb,
+                                                                           gn2, active, clear, ctl);
   const int ncomp = (int)C.comp_var_ptr.size() - 1;
   if (ncomp > 0)
-    k_pgd_comp<<<dim3(tiles, rows(ncomp)), blk, 0, st>>>(C.view, R, eta, bscale, sweeps, prm, b, gb, gn2, active,
-                                                         clear, ctl);
+    k_pgd_comp<<<dim3(tiles, rows(ncomp)), blk, 0, st>>>(C.view, R, eta, bscale, sweeps, polish, prm, wsum, b, gb,
+                                                         gn2, active, clear, ctl);
   FSMT_CUDA(cudaGetLastError(), "pgd kernel launch");
+  return FSMT_OK;
+}
+
+fsmt_status launch_weight_sum(const Compiled& C, int R, const float* w, float* wsum, cudaStream_t st) {
+  FSMT_CUDA(cudaMemsetAsync(wsum, 0, sizeof(float) * (size_t)R, st), "memset wsum");
+  if (C.n_obj == 0) return FSMT_OK;
+  const int tiles = (R + 31) / 32;
+  const long cap = std::max<long>(1, 4L * sm_count() * 8 / tiles);
+  const int gy = (int)std::max<long>(1, std::min<long>(std::min<long>((C.n_obj + 7) / 8, cap), 65535L));
+  k_weight_sum<<<dim3(tiles, gy), dim3(32, 8), 0, st>>>(C.view, R, w, wsum);
+  FSMT_CUDA(cudaGetLastError(), "weight sum launch");
   return FSMT_OK;
 }
 
@@ -841,18 +916,29 @@ fsmt_status fsmt_adjoint_plain(const fsmt_compiled* c, int32_t R, float sigma, c
   return FSMT_OK;
 }
 
-fsmt_status fsmt_pgd_step(const fsmt_compiled* c, int32_t R, float eta, float b_scale, int32_t sweeps, float* a,
-                          float* b, const float* grad_a, const float* grad_b, float* gnorm2, const uint8_t* active,
-                          void* stream) {
+fsmt_status fsmt_weight_sum(const fsmt_compiled* c, int32_t R, const float* w, float* wsum, void* stream) {
+  fsmt_status s = check_ready(c, R);
+  if (s != FSMT_OK) return s;
+  if (!w || !wsum) {
+    set_error("NULL argument");
+    return FSMT_EINVAL;
+  }
+  return launch_weight_sum(c->c, R, w, wsum, (cudaStream_t)stream);
+}
+
+fsmt_status fsmt_pgd_step(const fsmt_compiled* c, int32_t R, float eta, float b_scale, int32_t sweeps, int32_t polish,
+                          float* a, float* b, const float* grad_a, const float* grad_b, const float* wsum,
+                          float* gnorm2, const uint8_t* active, void* stream) {
   fsmt_status s = check_ready(c, R);
   if (s != FSMT_OK) return s;
   const Compiled& C = c->c;
-  if (!(eta > 0.f) || !(b_scale > 0.f) || sweeps < 0 || !gnorm2 || (C.n_bool && (!a || !grad_a)) ||
+  if (!(eta > 0.f) || !(b_scale > 0.f) || sweeps < 0 || polish < 0 || !gnorm2 || (C.n_bool && (!a || !grad_a)) ||
       (C.n_real && (!b || !grad_b))) {
     set_error("invalid step parameters or NULL argument");
     return FSMT_EINVAL;
   }
-  return launch_pgd(C, R, eta, b_scale, sweeps, nullptr, a, b, const_cast<float*>(grad_a), const_cast<float*>(grad_b),
+  return launch_pgd(C, R, eta, b_scale, sweeps, polish, nullptr, wsum, a, b, const_cast<float*>(grad_a),
+                    const_cast<float*>(grad_b),
                     gnorm2, active, 0, nullptr, (cudaStream_t)stream);
 }
 
@@ -879,12 +965,15 @@ static fsmt_status enqueue_stage(const Compiled& C, int t_max, fsmt_state* s, cu
   const int R = s->R;
   k_stage_begin<<<(R + 255) / 256, 256, 0, st>>>(R, s->active, s->iters, s->ctl);
   FSMT_CUDA(cudaGetLastError(), "stage begin");
+  fsmt_status ws = launch_weight_sum(C, R, s->w, s->wsum, st);
+  if (ws != FSMT_OK) return ws;
   for (int it = 0; it < t_max; ++it) {
     k_iter_begin<<<(R + 255) / 256, 256, 0, st>>>(R, s->obj, s->gnorm2, s->ctl);
     fsmt_status e = launch_fused(C, true, R, 0.f, s->params, s->w, s->a, s->b, s->grad_a, s->grad_b, s->obj, nullptr,
                                  s->ctl, st);
     if (e != FSMT_OK) return e;
-    e = launch_pgd(C, R, 1.f, 1.f, 0, s->params, s->a, s->b, s->grad_a, s->grad_b, s->gnorm2, s->active, 1, s->ctl, st);
+    e = launch_pgd(C, R, 1.f, 1.f, 0, 0, s->params, s->wsum, s->a, s->b, s->grad_a, s->grad_b, s->gnorm2, s->active, 1,
+                   s->ctl, st);
     if (e != FSMT_OK) return e;
     k_converge<<<1, 1024, 0, st>>>(R, s->params, s->gnorm2, s->active, s->iters, s->ctl);
     FSMT_CUDA(cudaGetLastError(), "converge");
@@ -901,14 +990,15 @@ fsmt_status fsmt_solve_stage(fsmt_compiled* cc, const fsmt_stage_config* cfg, fs
   if (e != FSMT_OK) return e;
   Compiled& C = cc->c;
   if (!(cfg->sigma >= 0.f) || !(cfg->eta > 0.f) || !(cfg->b_scale > 0.f) || cfg->t_max < 0 || cfg->sweeps < 0 ||
-      !(cfg->gamma > 0.f) || !s->w || !s->h || !s->obj || !s->gnorm2 || !s->active || !s->iters || !s->n_unsat ||
+      cfg->polish < 0 || !(cfg->gamma > 0.f) || !s->w || !s->h || !s->wsum || !s->obj || !s->gnorm2 || !s->active || !s->iters || !s->n_unsat ||
       !s->ctl || !s->params || (C.n_bool && (!s->a || !s->grad_a)) || (C.n_real && (!s->b || !s->grad_b))) {
     set_error("invalid stage configuration or NULL state buffer");
     return FSMT_EINVAL;
   }
   cudaStream_t st = (cudaStream_t)stream;
   k_set_params<<<1, 1, 0, st>>>(s->params, cfg->sigma, cfg->eta, cfg->b_scale, cfg->eps, cfg->rho, cfg->gamma,
-                                (float)cfg->update_w, (float)cfg->sweeps);
+                                (float)cfg->update_w, (float)cfg->sweeps, (float)cfg->polish,
+                                (float)cfg->normalize_eta);
   FSMT_CUDA(cudaGetLastError(), "set params");
   if (!cfg->use_graph) return enqueue_stage(C, cfg->t_max, s, st);
   // the legacy default stream cannot be captured: use a blocking stream of our own,
@@ -925,7 +1015,7 @@ fsmt_status fsmt_solve_stage(fsmt_compiled* cc, const fsmt_stage_config* cfg, fs
   uint64_t key = 1469598103934665603ull;
   auto mix = [&](uint64_t v) { key = (key ^ v) * 1099511628211ull; };
   const void* ptrs[] = {s->a, s->b, s->w, s->h, s->grad_a, s->grad_b, s->obj, s->gnorm2, s->active, s->iters,
-                        s->n_unsat, s->ctl, s->params};
+                        s->n_unsat, s->ctl, s->params, s->wsum};
   for (const void* p : ptrs) mix((uint64_t)(uintptr_t)p);
   mix((uint64_t)s->R);
   mix((uint64_t)cfg->t_max);

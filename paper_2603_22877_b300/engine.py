@@ -179,14 +179,20 @@ class Compiled:
                _dptr(work, torch.float32, None, "work"), _dptr(grad_a, torch.float32, sa, "grad_a"),
                _dptr(grad_b, torch.float32, sb, "grad_b"), _stream(stream))
 
-    def pgd_step(self, R, eta, b_scale, sweeps, a, b, grad_a, grad_b, gnorm2, active=None, stream=None):
+    def weight_sum(self, R, w, wsum, stream=None):
+        import torch
+        L.call("fsmt_weight_sum", self.h, int(R), _dptr(w, torch.float32, (self.n_cons, R), "w"),
+               _dptr(wsum, torch.float32, (R,), "wsum"), _stream(stream))
+
+    def pgd_step(self, R, eta, b_scale, sweeps, a, b, grad_a, grad_b, gnorm2, active=None, wsum=None, polish=8,
+                 stream=None):
         import torch
         sa, sb, _ = self._shapes(R)
-        L.call("fsmt_pgd_step", self.h, int(R), float(eta), float(b_scale), int(sweeps),
+        L.call("fsmt_pgd_step", self.h, int(R), float(eta), float(b_scale), int(sweeps), int(polish),
                _dptr(a, torch.float32, sa, "a"), _dptr(b, torch.float32, sb, "b"),
                _dptr(grad_a, torch.float32, sa, "grad_a"), _dptr(grad_b, torch.float32, sb, "grad_b"),
-               _dptr(gnorm2, torch.float32, (R,), "gnorm2"), _dptr(active, torch.uint8, (R,), "active"),
-               _stream(stream))
+               _dptr(wsum, torch.float32, (R,), "wsum"), _dptr(gnorm2, torch.float32, (R,), "gnorm2"),
+               _dptr(active, torch.uint8, (R,), "active"), _stream(stream))
 
     def round_check(self, R, a, b, n_unsat, x=None, violated=None, w=None, h=None, rho=0.5, gamma=2.0,
                     update_w=True, stream=None):
@@ -269,7 +275,7 @@ class Solver:
     """
 
     def __init__(self, problem, compiled, R, eta, b_scale, eps=1e-2, t_max=200, sweeps=20, rho=0.5, gamma=2.0,
-                 tau=1, use_graph=True, device="cuda"):
+                 tau=1, use_graph=True, polish=8, normalize_eta=True, device="cuda"):
         import torch
         self.problem, self.comp, self.R = problem, compiled, int(R)
         if not compiled.uploaded:
@@ -289,11 +295,13 @@ class Solver:
         self.n_unsat = torch.zeros(R, device=device, dtype=torch.int32)
         self.ctl = torch.zeros(4, device=device, dtype=torch.int32)
         self.params = torch.zeros(16, **f32)
+        self.wsum = torch.zeros(R, **f32)
+        self.polish, self.normalize_eta = polish, normalize_eta
         self.eta, self.b_scale, self.eps, self.t_max, self.sweeps = eta, b_scale, eps, t_max, sweeps
         self.rho, self.gamma, self.tau, self.use_graph = rho, gamma, tau, use_graph
         self._state = L.State(self.R, *[C.c_void_p(t.data_ptr()) for t in (
             self.a, self.b, self.w, self.h, self.grad_a, self.grad_b, self.obj, self.gnorm2, self.active,
-            self.iters, self.n_unsat, self.ctl, self.params)])
+            self.iters, self.n_unsat, self.ctl, self.params, self.wsum)])
 
     def reset(self, a0, b0):
         """Loads initial points ([n][R], [m][R] float32, host or device) and resets weights."""
@@ -306,7 +314,7 @@ class Solver:
     def config(self, sigma, t):
         return L.StageConfig(float(sigma), float(self.eta), float(self.b_scale), float(self.eps), int(self.t_max),
                              int(self.sweeps), float(self.rho), float(self.gamma), int(t % self.tau == 0),
-                             int(bool(self.use_graph)))
+                             int(bool(self.use_graph)), int(self.polish), int(bool(self.normalize_eta)))
 
     def stage(self, sigma, t, stream=None):
         cfg = self.config(sigma, t)

@@ -22,13 +22,19 @@ def test_pgd_step_parity(make, R):
     ga32, gb32 = ga.astype(np.float32), gb.astype(np.float32)
     eta = 0.05
     dom = pgd.Domain(inst)
+    # per-restart step normalised by the total weight of C_sigma (oracle: pgd.step_sizes)
+    etas = pgd.step_sizes(inst, w.astype(np.float64), pgd.Config(eta=eta))
     a_ref, b_ref, gn_ref = pgd.pgd_step(a.astype(np.float64), b.astype(np.float64), ga32.astype(np.float64),
-                                        gb32.astype(np.float64), eta, inst.scale, dom, 20)
-    da, db, dga, dgb = to_dev(a, b, ga32, gb32)
+                                        gb32.astype(np.float64), etas, inst.scale, dom, 20, 8)
+    da, db, dga, dgb, dw = to_dev(a, b, ga32, gb32, w)
     gn = torch.zeros(R, device="cuda")
+    wsum = torch.zeros(R, device="cuda")
+    comp.weight_sum(R, dw, wsum)
+    oc = OBJ.objective_constraints(inst)
+    np.testing.assert_allclose(wsum.cpu().numpy(), w[oc].astype(np.float64).sum(0), rtol=1e-5)
     active = torch.ones(R, dtype=torch.uint8, device="cuda")
     active[1::3] = 0
-    comp.pgd_step(R, eta, inst.scale, 20, da, db, dga, dgb, gn, active)
+    comp.pgd_step(R, eta, inst.scale, 20, da, db, dga, dgb, gn, active, wsum=wsum, polish=8)
     act = active.cpu().numpy().astype(bool)
     a_out, b_out = da.cpu().numpy(), db.cpu().numpy()
     np.testing.assert_allclose(a_out[:, act], a_ref[:, act], atol=2e-6)
@@ -37,6 +43,29 @@ def test_pgd_step_parity(make, R):
     np.testing.assert_allclose(b_out[:, act], b_ref[:, act], atol=2e-5 * scale_b)
     np.testing.assert_array_equal(b_out[:, ~act], b[:, ~act])
     np.testing.assert_allclose(gn.cpu().numpy(), gn_ref, rtol=2e-4, atol=1e-6)
+
+
+@pytest.mark.parametrize("make", [lambda: W.jobshop(1002, 10, 5), lambda: W.large_scheduling(1005, 16, 40, 6, 4, 5)])
+def test_projection_lands_in_D_exactly(make):
+    """From points near a feasible one (a PGD step's regime), the projection with
+    the feasibility polish satisfies every projected unit atom exactly, on the GPU
+    and in the oracle, and the two agree."""
+    import torch
+    inst = make()
+    R = 64
+    P, comp, a, b, w = setup(inst, R)
+    rng = np.random.default_rng(2)
+    b = (inst.planted_y[:, None] + rng.normal(0, 3.0, (inst.n_real, R))).astype(np.float32)
+    zero_a, zero_b = np.zeros_like(a), np.zeros_like(b)
+    da, db, dga, dgb = to_dev(a, b, zero_a, zero_b)
+    gn = torch.zeros(R, device="cuda")
+    comp.pgd_step(R, 0.05, inst.scale, 20, da, db, dga, dgb, gn, polish=8)
+    b_out = db.cpu().numpy().astype(np.float64)
+    unit = [c for c in range(inst.n_cons) if OBJ.is_unit_atomic(inst, c)]
+    _, viol = pgd.round_check(inst, a.astype(np.float64), b_out, constraints=unit)
+    assert not viol[unit].any()
+    b_ref = pgd.Domain(inst).project_b(b.astype(np.float64), 20, 8)
+    np.testing.assert_allclose(b_out, b_ref, atol=1e-3)
 
 
 @pytest.mark.parametrize("make,R", [(lambda: W.tiny_random(1001), 45), (lambda: W.jobshop(1002, 10, 5), 64),
@@ -84,7 +113,7 @@ def test_stage_matches_oracle_first_iterations(use_graph):
     R = 40
     P, comp, a, b, _ = setup(inst, R)
     eta = 0.02
-    cfg = pgd.Config(eta=eta, t_max=5, sweeps=20)
+    cfg = pgd.Config(eta=eta, t_max=5, sweeps=20, polish=8)
     S = _solver(inst, R, comp, P, eta=eta, b_scale=inst.scale, t_max=5, sweeps=20, use_graph=use_graph)
     S.reset(a, b)
     sigma = sigmas_for(inst)[0]
@@ -130,3 +159,19 @@ def test_stage_host_buffers_match_device():
     np.testing.assert_allclose(S2.a.cpu().numpy(), S1.a.cpu().numpy(), atol=1e-5)
     np.testing.assert_allclose(ob, S1.obj.cpu().numpy(), rtol=1e-5, atol=1e-3)
     np.testing.assert_array_equal(nu, S2.n_unsat.cpu().numpy())
+
+
+def test_anneal_finds_exactly_verified_sat():
+    """Alg. 2 on a small instance of the scheduling family: some restart reaches
+    #Unsat = 0, and both the library's exact verifier and the oracle's exact
+    check confirm the assignment."""
+    from oracle import semantics as Sm
+    inst = W.large_scheduling(1005, 16, 30, 6, 4, 5)
+    R = 64
+    P, comp, a, b, _ = setup(inst, R)
+    S = _solver(inst, R, comp, P, eta=0.05, b_scale=inst.scale, t_max=50)
+    S.reset(a, b)
+    sched = [inst.scale / (0.1 * t) for t in range(1, 21)]
+    res = S.anneal(sched)
+    assert res["sat"], res
+    assert Sm.unsat_constraints(inst, res["x"], res["y"]) == []

@@ -1,6 +1,7 @@
 """Pins for the oracle's projection, PGD step, exact check and ERWA (no GPU)."""
 import itertools
 import math
+from fractions import Fraction
 
 import numpy as np
 import pytest
@@ -59,7 +60,7 @@ def halfspace_instance(rng, n_real=3, n_half=3):
 
 def test_dykstra_matches_exact_qp():
     rng = np.random.default_rng(0)
-    checked = 0
+    checked = polished = 0
     for _ in range(40):
         inst, lo, hi, A, c = halfspace_instance(rng)
         dom = pgd.Domain(inst)
@@ -68,10 +69,38 @@ def test_dykstra_matches_exact_qp():
         x_ex = exact_projection(y, lo, hi, A, c)
         if x_ex is None:  # empty feasible set
             continue
-        x = dom.project_b(y[:, None], sweeps=3000)[:, 0]
+        x = dom.project_b(y[:, None], sweeps=3000, polish=0)[:, 0]
         np.testing.assert_allclose(x, x_ex, atol=1e-7)
+        # where the polish lands in D exactly, it stays within the margin scale of the projection
+        xp = dom.project_b(y[:, None], sweeps=20, polish=8)[:, 0]
+        feasible = all(sum(Fraction(float(A[k, j])) * Fraction(float(xp[j])) for j in range(len(xp)))
+                       <= Fraction(float(c[k])) for k in range(len(c)))
+        assert (xp >= lo).all() and (xp <= hi).all()
+        if feasible:
+            assert np.abs(xp - x_ex).max() <= 1e-2
+            polished += 1
         checked += 1
-    assert checked > 20
+    assert checked > 20 and polished >= checked // 2
+
+
+def test_polish_makes_precedence_chains_exactly_feasible():
+    """Job-shop precedence chains with box bounds (the workloads' unit atoms): from
+    points near a feasible one (the regime of a PGD step), the projected point
+    satisfies every unit atom exactly; without the polish, Dykstra's does not."""
+    inst = W.jobshop(1002, 8, 6)
+    dom = pgd.Domain(inst)
+    assert len(dom.halfspaces) == 8 * 5
+    rng = np.random.default_rng(5)
+    unit = [c for c in range(inst.n_cons) if OBJ.is_unit_atomic(inst, c)]
+    for noise in (0.5, 2.0, 10.0):
+        y = inst.planted_y[:, None] + rng.normal(0, noise, (inst.n_real, 64))
+        x = dom.project_b(y, sweeps=20, polish=8)
+        _, viol = pgd.round_check(inst, np.zeros((inst.n_bool, 64)), x, constraints=unit)
+        assert not viol[unit].any()
+        x0 = dom.project_b(y, sweeps=20, polish=0)
+        _, viol0 = pgd.round_check(inst, np.zeros((inst.n_bool, 64)), x0, constraints=unit)
+        assert viol0[unit].any()
+        assert np.abs(x - x0).max() <= 0.05  # the polish moves the point by the margin scale
 
 
 def test_projection_idempotent_and_nonexpansive():
@@ -79,10 +108,10 @@ def test_projection_idempotent_and_nonexpansive():
     inst, lo, hi, A, c = halfspace_instance(rng, 4, 3)
     dom = pgd.Domain(inst)
     y = rng.uniform(-8, 8, (4, 50))
-    x = dom.project_b(y, 3000)
+    x = dom.project_b(y, 3000, polish=0)
     if exact_projection(y[:, 0], lo, hi, A, c) is None:
         pytest.skip("empty feasible set for this draw")
-    np.testing.assert_allclose(dom.project_b(x, 3000), x, atol=1e-7)
+    np.testing.assert_allclose(dom.project_b(x, 3000, polish=0), x, atol=1e-7)
     d_in = np.linalg.norm(y[:, :25] - y[:, 25:], axis=0)
     d_out = np.linalg.norm(x[:, :25] - x[:, 25:], axis=0)
     assert (d_out <= d_in + 1e-7).all()
