@@ -216,8 +216,9 @@ fsmt_status fsmt_adjoint_plain(const fsmt_compiled* c, int32_t R, float sigma, c
  * each block of reals coupled by half-spaces, `sweeps` sweeps of Dykstra's
  * alternating projections (half-spaces in constraint order, then the box)
  * followed by up to `polish` passes that project each half-space q.y <= q0 with
- * q.y > q0 - m onto q.y <= q0 - m, m = 2^-16 (|q0| + sum |q_j y_j|), then clamp
- * the box, until a pass moves nothing (so the result lies in D exactly once the
+ * q.y > q0 - m onto q.y <= q0 - 2m, m = 2^-16 (|q0| + sum |q_j y_j|), moving only
+ * reals not pinned at the bound the step would cross, then clamp the box, until
+ * a pass moves nothing (so the result lies in D exactly once the
  * passes settle); then
  * gnorm2[r] += sum ((a - a_new)/eta_r)^2 + sum ((b - b_new)/(b_scale eta_r))^2.
  * a, b (device, [n][R], [m][R]) are updated in place for restarts with

@@ -52,7 +52,7 @@ class Config:
     gamma: float = 2.0
     tau: int = 1
     sweeps: int = 20
-    polish: int = 8
+    polish: int = 32
     normalize_eta: bool = True
     policy: int = OBJ.PROJECT
     inv_sigma: list = field(default_factory=lambda: [0.1 * t for t in range(1, 21)])  # times 1/S
@@ -104,14 +104,15 @@ class Domain:
             else:
                 self.halfspaces.append((np.asarray(var, np.int64), np.asarray(coef, np.float64), float(q0)))
 
-    def project_b(self, bp, sweeps, polish=8):
+    def project_b(self, bp, sweeps, polish=32):
         """proj onto box n half-spaces of points bp [m][R] (Dykstra; exact clamp if no half-space).
 
         After the Dykstra sweeps, up to `polish` passes make the point feasible:
-        each half-space q.y <= q0 whose value is above -margin is projected onto
-        q.y <= q0 - margin (margin = 2^-16 (|q0| + sum |q_j y_j|), far above the
-        rounding error of evaluating q.y), then the box is clamped; a restart stops
-        when a pass moves nothing.  The result satisfies every half-space exactly
+        each half-space q.y <= q0 whose value is above -margin (margin = 2^-16
+        (|q0| + sum |q_j y_j|), far above the rounding error of evaluating q.y) is
+        projected onto q.y <= q0 - 2 margin along the reals that are not pinned
+        at the bound the step would cross, then the box is clamped; a restart
+        stops when a pass moves nothing.  The result satisfies every half-space exactly
         whenever the passes settle."""
         x = np.clip(bp, self.lo[:, None], self.hi[:, None])
         if not self.halfspaces:
@@ -138,8 +139,13 @@ class Domain:
                 v = (q[:, None] * xv).sum(0) - q0
                 margin = POLISH_MARGIN * (abs(q0) + (np.abs(q[:, None] * xv)).sum(0))
                 need = v > -margin
-                step = np.where(need, (v + margin) / float((q * q).sum()), 0.0)
-                x[var] = xv - step[None, :] * q[:, None]
+                # the step moves y_j by -t q_j; a real on the bound it would cross stays put
+                lo, hi = self.lo[var][:, None], self.hi[var][:, None]
+                free = ~(((q[:, None] > 0) & (xv <= lo)) | ((q[:, None] < 0) & (xv >= hi)))
+                qq = ((q * q)[:, None] * free).sum(0)
+                need &= qq > 0
+                step = np.where(need, (v + 2.0 * margin) / np.where(qq > 0, qq, 1.0), 0.0)
+                x[var] = xv - step[None, :] * q[:, None] * free
                 moved |= need
             x[J] = np.clip(x[J], self.lo[J][:, None], self.hi[J][:, None])
             if not moved.any():
@@ -147,7 +153,7 @@ class Domain:
         return x
 
 
-def pgd_step(a, b, ga, gb, eta, scale, dom, sweeps, polish=8):
+def pgd_step(a, b, ga, gb, eta, scale, dom, sweeps, polish=32):
     """One PGD step (Eq. pg1, pg2) and ||g||^2 (Eq. grad_map, scaled coordinates).
 
     eta is a scalar or one step size per restart ([R])."""

@@ -34,7 +34,7 @@ class State(C.Structure):
     _fields_ = [("R", C.c_int32), ("a", C.c_void_p), ("b", C.c_void_p), ("w", C.c_void_p), ("h", C.c_void_p),
                 ("grad_a", C.c_void_p), ("grad_b", C.c_void_p), ("obj", C.c_void_p), ("gnorm2", C.c_void_p),
                 ("active", C.c_void_p), ("iters", C.c_void_p), ("n_unsat", C.c_void_p), ("ctl", C.c_void_p),
-                ("params", C.c_void_p)]
+                ("params", C.c_void_p), ("wsum", C.c_void_p)]
 
 
 class StageConfig(C.Structure):

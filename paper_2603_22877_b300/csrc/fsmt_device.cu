@@ -392,9 +392,10 @@ __global__ void k_pgd_free(DevView d, int R, float eta, float bscale, const floa
 // thread-local arrays.  Per sweep: every half-space in constraint order, then
 // the box.  Then up to `polish` passes: each half-space q.y <= q0 whose value is
 // above -margin, margin = 2^-16 (|q0| + sum |q_j y_j|) (far above the FP32
-// rounding of q.y), is projected onto q.y <= q0 - margin, then the box is
-// clamped; the thread stops at the first pass that moves nothing, so the point
-// it returns satisfies every half-space exactly whenever the passes settle.
+// rounding of q.y), is projected onto q.y <= q0 - 2 margin along the reals not
+// pinned at the bound the step would cross, then the box is clamped; the thread
+// stops at the first pass that moves nothing, so the point it returns satisfies
+// every half-space exactly whenever the passes settle.
 __global__ void k_pgd_comp(DevView d, int R, float eta, float bscale, int sweeps, int polish, const float* prm,
                            const float* __restrict__ wsum, float* __restrict__ b, float* __restrict__ gb,
                            float* __restrict__ gn2, const uint8_t* __restrict__ active, int clear_grad,
@@ -463,9 +464,24 @@ __global__ void k_pgd_comp(DevView d, int R, float eta, float bscale, int sweeps
           }
           const float margin = kPolishMargin * mag;
           if (v > -margin) {
-            const float tq = (v + margin) * d.hs_inv_qq[h0 + q];
-            for (int e = e0; e < e1; ++e) x[d.hs_lvar[e]] = fmaf(-tq, d.hs_coef[e], x[d.hs_lvar[e]]);
-            moved = true;
+            // move along the reals that are not pinned at the bound the step would cross
+            float qq = 0.f;
+            for (int e = e0; e < e1; ++e) {
+              const float cf = d.hs_coef[e];
+              const int t = d.hs_lvar[e], j = d.comp_var[v0 + t];
+              const bool pinned = (cf > 0.f && x[t] <= d.lo[j]) || (cf < 0.f && x[t] >= d.hi[j]);
+              if (!pinned) qq = fmaf(cf, cf, qq);
+            }
+            if (qq > 0.f) {
+              const float tq = (v + 2.f * margin) / qq;
+              for (int e = e0; e < e1; ++e) {
+                const float cf = d.hs_coef[e];
+                const int t = d.hs_lvar[e], j = d.comp_var[v0 + t];
+                const bool pinned = (cf > 0.f && x[t] <= d.lo[j]) || (cf < 0.f && x[t] >= d.hi[j]);
+                if (!pinned) x[t] = fmaf(-tq, cf, x[t]);
+              }
+              moved = true;
+            }
           }
         }
         for (int t = 0; t < nv; ++t) {

@@ -184,7 +184,7 @@ class Compiled:
         L.call("fsmt_weight_sum", self.h, int(R), _dptr(w, torch.float32, (self.n_cons, R), "w"),
                _dptr(wsum, torch.float32, (R,), "wsum"), _stream(stream))
 
-    def pgd_step(self, R, eta, b_scale, sweeps, a, b, grad_a, grad_b, gnorm2, active=None, wsum=None, polish=8,
+    def pgd_step(self, R, eta, b_scale, sweeps, a, b, grad_a, grad_b, gnorm2, active=None, wsum=None, polish=32,
                  stream=None):
         import torch
         sa, sb, _ = self._shapes(R)
@@ -275,7 +275,7 @@ class Solver:
     """
 
     def __init__(self, problem, compiled, R, eta, b_scale, eps=1e-2, t_max=200, sweeps=20, rho=0.5, gamma=2.0,
-                 tau=1, use_graph=True, polish=8, normalize_eta=True, device="cuda"):
+                 tau=1, use_graph=True, polish=32, normalize_eta=True, device="cuda"):
         import torch
         self.problem, self.comp, self.R = problem, compiled, int(R)
         if not compiled.uploaded:

@@ -25,7 +25,7 @@ def test_pgd_step_parity(make, R):
     # per-restart step normalised by the total weight of C_sigma (oracle: pgd.step_sizes)
     etas = pgd.step_sizes(inst, w.astype(np.float64), pgd.Config(eta=eta))
     a_ref, b_ref, gn_ref = pgd.pgd_step(a.astype(np.float64), b.astype(np.float64), ga32.astype(np.float64),
-                                        gb32.astype(np.float64), etas, inst.scale, dom, 20, 8)
+                                        gb32.astype(np.float64), etas, inst.scale, dom, 20, 32)
     da, db, dga, dgb, dw = to_dev(a, b, ga32, gb32, w)
     gn = torch.zeros(R, device="cuda")
     wsum = torch.zeros(R, device="cuda")
@@ -34,7 +34,7 @@ def test_pgd_step_parity(make, R):
     np.testing.assert_allclose(wsum.cpu().numpy(), w[oc].astype(np.float64).sum(0), rtol=1e-5)
     active = torch.ones(R, dtype=torch.uint8, device="cuda")
     active[1::3] = 0
-    comp.pgd_step(R, eta, inst.scale, 20, da, db, dga, dgb, gn, active, wsum=wsum, polish=8)
+    comp.pgd_step(R, eta, inst.scale, 20, da, db, dga, dgb, gn, active, wsum=wsum, polish=32)
     act = active.cpu().numpy().astype(bool)
     a_out, b_out = da.cpu().numpy(), db.cpu().numpy()
     np.testing.assert_allclose(a_out[:, act], a_ref[:, act], atol=2e-6)
@@ -59,12 +59,12 @@ def test_projection_lands_in_D_exactly(make):
     zero_a, zero_b = np.zeros_like(a), np.zeros_like(b)
     da, db, dga, dgb = to_dev(a, b, zero_a, zero_b)
     gn = torch.zeros(R, device="cuda")
-    comp.pgd_step(R, 0.05, inst.scale, 20, da, db, dga, dgb, gn, polish=8)
+    comp.pgd_step(R, 0.05, inst.scale, 20, da, db, dga, dgb, gn, polish=32)
     b_out = db.cpu().numpy().astype(np.float64)
     unit = [c for c in range(inst.n_cons) if OBJ.is_unit_atomic(inst, c)]
     _, viol = pgd.round_check(inst, a.astype(np.float64), b_out, constraints=unit)
     assert not viol[unit].any()
-    b_ref = pgd.Domain(inst).project_b(b.astype(np.float64), 20, 8)
+    b_ref = pgd.Domain(inst).project_b(b.astype(np.float64), 20, 32)
     np.testing.assert_allclose(b_out, b_ref, atol=1e-3)
 
 
@@ -113,7 +113,7 @@ def test_stage_matches_oracle_first_iterations(use_graph):
     R = 40
     P, comp, a, b, _ = setup(inst, R)
     eta = 0.02
-    cfg = pgd.Config(eta=eta, t_max=5, sweeps=20, polish=8)
+    cfg = pgd.Config(eta=eta, t_max=5, sweeps=20, polish=32)
     S = _solver(inst, R, comp, P, eta=eta, b_scale=inst.scale, t_max=5, sweeps=20, use_graph=use_graph)
     S.reset(a, b)
     sigma = sigmas_for(inst)[0]

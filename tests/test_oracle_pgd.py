@@ -72,7 +72,7 @@ def test_dykstra_matches_exact_qp():
         x = dom.project_b(y[:, None], sweeps=3000, polish=0)[:, 0]
         np.testing.assert_allclose(x, x_ex, atol=1e-7)
         # where the polish lands in D exactly, it stays within the margin scale of the projection
-        xp = dom.project_b(y[:, None], sweeps=20, polish=8)[:, 0]
+        xp = dom.project_b(y[:, None], sweeps=3000, polish=32)[:, 0]
         feasible = all(sum(Fraction(float(A[k, j])) * Fraction(float(xp[j])) for j in range(len(xp)))
                        <= Fraction(float(c[k])) for k in range(len(c)))
         assert (xp >= lo).all() and (xp <= hi).all()
@@ -94,7 +94,7 @@ def test_polish_makes_precedence_chains_exactly_feasible():
     unit = [c for c in range(inst.n_cons) if OBJ.is_unit_atomic(inst, c)]
     for noise in (0.5, 2.0, 10.0):
         y = inst.planted_y[:, None] + rng.normal(0, noise, (inst.n_real, 64))
-        x = dom.project_b(y, sweeps=20, polish=8)
+        x = dom.project_b(y, sweeps=20, polish=32)
         _, viol = pgd.round_check(inst, np.zeros((inst.n_bool, 64)), x, constraints=unit)
         assert not viol[unit].any()
         x0 = dom.project_b(y, sweeps=20, polish=0)
