@@ -76,7 +76,7 @@ typedef struct {
   int32_t n_free_reals;  /* reals with a box constraint only */
   int64_t atom_nnz;      /* nonzero coefficients over all atoms */
   int32_t fused_ok;      /* 1 if the fused kernels accept this instance */
-  int32_t reserved;
+  int32_t n_chunks;      /* chunks of the chunked forward/adjoint kernel (0: warp-per-constraint kernel) */
 } fsmt_info;
 
 /* ---------------------------------------------------------------- problem --

@@ -22,6 +22,10 @@ constexpr float kInvSqrt2 = 0.70710678118654752f;
 constexpr int kFusedThreads = 256;  // 8 warps
 constexpr int kSmemBudget = 112 * 1024;
 constexpr int kMaxObjSmemR = 4096;
+constexpr int kChunkThreads = 512;  // 16 warps
+constexpr size_t kChunkFixedBytes = (size_t)kChunkMaxNodes * 8 + (size_t)kChunkMaxCons * 16 + (size_t)kChunkMaxSlots * 4 +
+                                    (size_t)kChunkMaxSlots * 32 * 4 * 3;
+constexpr size_t kSmemMax = 227 * 1024;
 
 // stage parameter slots (device float[16])
 enum { P_SIGMA = 0, P_ETA, P_BSCALE, P_EPS, P_RHO, P_GAMMA, P_UPDATE_W, P_SWEEPS, P_POLISH, P_NORM };
@@ -209,6 +213,120 @@ __global__ void __launch_bounds__(kFusedThreads) k_fused(DevView d, int R, float
       }
     }
     __syncwarp();
+  }
+  if (obj_s && obj) {
+    __syncthreads();
+    for (int r = threadIdx.x; r < R; r += blockDim.x)
+      if (obj_s[r] != 0.f) atomicAdd(obj + r, obj_s[r]);
+  }
+}
+
+// -------------------------------------------------------- chunked kernel --
+// One CTA per chunk of constraints of C_sigma (grid-stride over chunks), looping
+// over restart tiles.  Per tile: (1) every slot -- a Boolean or an atom used by
+// the chunk -- gets its TRUE-probability p (and dd/dz for atoms) once, lane =
+// restart; (2) each warp runs Alg. 3 and Alg. 4 on its constraints with p read
+// from shared memory and m_td / m_bu in the warp's shared array, adding
+// w_c * m_td[v] (m_bu[hi] - m_bu[lo]) into the slot's shared accumulator;
+// (3) each slot's accumulated derivative goes to the global gradient once.
+template <bool ADJ>
+__global__ void __launch_bounds__(kChunkThreads, 1)
+    k_chunked(DevView d, int R, float sigma, const float* prm, int vcap, const float* __restrict__ w,
+              const float* __restrict__ a, const float* __restrict__ b, float* __restrict__ grad_a,
+              float* __restrict__ grad_b, float* __restrict__ obj, float* __restrict__ cop, const int* ctl) {
+  if (ctl && ctl[0] == 0) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
+  uint2* s_node = reinterpret_cast<uint2*>(smem);
+  int4* s_con = reinterpret_cast<int4*>(s_node + kChunkMaxNodes);
+  int* s_lab = reinterpret_cast<int*>(s_con + kChunkMaxCons);
+  float* s_p = reinterpret_cast<float*>(s_lab + kChunkMaxSlots);
+  float* s_gz = s_p + kChunkMaxSlots * 32;
+  float* s_g = s_gz + kChunkMaxSlots * 32;
+  float* s_mw = s_g + kChunkMaxSlots * 32;
+  float* s_m = s_mw + warp * (vcap + 2) * 32;
+  float* obj_s = (R <= kMaxObjSmemR) ? s_mw + W * (vcap + 2) * 32 : nullptr;
+  if (obj_s)
+    for (int r = threadIdx.x; r < R; r += blockDim.x) obj_s[r] = 0.f;
+  sigma = load_param(prm, P_SIGMA, sigma);
+  const float s_inv = sigma > 0.f ? kInvSqrt2 / sigma : 0.f;
+  const int n_tiles = (R + 31) >> 5;
+  for (int q = blockIdx.x; q < d.n_chunks; q += gridDim.x) {
+    const int c0 = __ldg(d.chunk_con_ptr + q), nc = __ldg(d.chunk_con_ptr + q + 1) - c0;
+    const int n0 = __ldg(d.chunk_node_ptr + q), nn = __ldg(d.chunk_node_ptr + q + 1) - n0;
+    const int l0 = __ldg(d.chunk_slot_ptr + q), ns = __ldg(d.chunk_slot_ptr + q + 1) - l0;
+    __syncthreads();  // the previous chunk is done with shared memory
+    for (int i = threadIdx.x; i < nn; i += blockDim.x) s_node[i] = d.cnodes[n0 + i];
+    for (int i = threadIdx.x; i < nc; i += blockDim.x) s_con[i] = d.ccon[c0 + i];
+    for (int i = threadIdx.x; i < ns; i += blockDim.x) s_lab[i] = __ldg(d.slot_label + l0 + i);
+    __syncthreads();
+    for (int t = 0; t < n_tiles; ++t) {
+      const int r = t * 32 + lane;
+      const bool ok = r < R;
+      // (1) slot probabilities (Eq. rounding / Eq. sampling), once per slot
+      for (int i = warp; i < ns; i += W) {
+        float p, gz;
+        literal_prob(d, s_lab[i], R, r, ok, s_inv, a, b, p, gz);
+        s_p[i * 32 + lane] = p;
+        if (ADJ) {
+          s_gz[i * 32 + lane] = gz;
+          s_g[i * 32 + lane] = 0.f;
+        }
+      }
+      __syncthreads();
+      // (2) Alg. 3 then Alg. 4 per constraint, one warp per constraint
+      for (int k = warp; k < nc; k += W) {
+        const int4 cn = s_con[k];
+        const uint2* nd = s_node + cn.x;
+        const int V = cn.y;
+        for (int v = 0; v < V + 2; ++v) s_m[v * 32 + lane] = 0.f;
+        s_m[cn.z * 32 + lane] = 1.f;
+        for (int v = 0; v < V; ++v) {
+          const uint2 e = nd[v];
+          const int hi = (int)(e.y & 0xffffu) * 32 + lane, lo = (int)(e.y >> 16) * 32 + lane;
+          const float p = s_p[e.x * 32 + lane];
+          const float mv = s_m[v * 32 + lane];
+          s_m[hi] = fmaf(p, mv, s_m[hi]);
+          s_m[lo] = fmaf(1.f - p, mv, s_m[lo]);
+        }
+        const float cp = s_m[V * 32 + lane];
+        const float wc = ok ? __ldg(w + (size_t)cn.w * R + r) : 0.f;
+        if (ok) {
+          if (cop) cop[(size_t)cn.w * R + r] = cp;
+          if (obj) {
+            const float contrib = wc * (1.f - 2.f * cp);
+            if (obj_s)
+              atomicAdd(obj_s + r, contrib);
+            else
+              atomicAdd(obj + r, contrib);
+          }
+        }
+        if (ADJ) {
+          s_m[V * 32 + lane] = 1.f;
+          s_m[(V + 1) * 32 + lane] = 0.f;
+          for (int v = V - 1; v >= 0; --v) {
+            const uint2 e = nd[v];
+            const float mh = s_m[(e.y & 0xffffu) * 32 + lane], ml = s_m[(e.y >> 16) * 32 + lane];
+            const float p = s_p[e.x * 32 + lane];
+            const float td = s_m[v * 32 + lane];
+            const float diff = mh - ml;
+            s_m[v * 32 + lane] = fmaf(p, diff, ml);
+            const float g = wc * td * diff;
+            if (g != 0.f) atomicAdd(s_g + e.x * 32 + lane, g);
+          }
+        }
+      }
+      __syncthreads();
+      // (3) one global update per slot
+      if (ADJ) {
+        if (ok)
+          for (int i = warp; i < ns; i += W) {
+            const float g = s_g[i * 32 + lane];
+            if (g != 0.f) scatter_grad(d, s_lab[i], R, r, g, s_gz[i * 32 + lane], grad_a, grad_b);
+          }
+        __syncthreads();
+      }
+    }
   }
   if (obj_s && obj) {
     __syncthreads();
@@ -660,7 +778,7 @@ fsmt_status check_ready(const fsmt_compiled* c, int R) {
   return FSMT_OK;
 }
 
-fsmt_status launch_fused(const Compiled& C, bool adj, int R, float sigma, const float* prm, const float* w,
+fsmt_status launch_fused_warp(const Compiled& C, bool adj, int R, float sigma, const float* prm, const float* w,
                          const float* a, const float* b, float* ga, float* gb, float* obj, float* cop, const int* ctl,
                          cudaStream_t st) {
   if (C.n_obj == 0) return FSMT_OK;
@@ -684,6 +802,34 @@ fsmt_status launch_fused(const Compiled& C, bool adj, int R, float sigma, const 
     k_fused<false><<<blocks, threads, f.smem, st>>>(C.view, R, sigma, prm, f.vcap, w, a, b, ga, gb, obj, cop, ctl);
   FSMT_CUDA(cudaGetLastError(), "fused kernel launch");
   return FSMT_OK;
+}
+
+// warps of the chunked kernel for this instance (0 if it cannot run it)
+int chunk_warps(const Compiled& C, int R) {
+  if (!C.chunked_ok) return 0;
+  const size_t per_warp = (size_t)(std::max(1, C.max_nodes) + 2) * 32 * 4;
+  const size_t fixed = kChunkFixedBytes + (R <= kMaxObjSmemR ? (size_t)R * 4 : 0);
+  if (fixed + 4 * per_warp > kSmemMax) return 0;
+  return (int)std::min<size_t>(kChunkThreads / 32, (kSmemMax - fixed) / per_warp);
+}
+
+fsmt_status launch_fused(const Compiled& C, bool adj, int R, float sigma, const float* prm, const float* w,
+                         const float* a, const float* b, float* ga, float* gb, float* obj, float* cop, const int* ctl,
+                         cudaStream_t st) {
+  if (C.n_obj == 0) return FSMT_OK;
+  const int cw = chunk_warps(C, R);
+  if (cw > 0) {
+    const int vcap = std::max(1, C.max_nodes);
+    const size_t smem = kChunkFixedBytes + (size_t)cw * (vcap + 2) * 32 * 4 + (R <= kMaxObjSmemR ? (size_t)R * 4 : 0);
+    const int blocks = std::max(1, std::min(C.n_chunks, sm_count()));
+    if (adj)
+      k_chunked<true><<<blocks, cw * 32, smem, st>>>(C.view, R, sigma, prm, vcap, w, a, b, ga, gb, obj, cop, ctl);
+    else
+      k_chunked<false><<<blocks, cw * 32, smem, st>>>(C.view, R, sigma, prm, vcap, w, a, b, ga, gb, obj, cop, ctl);
+    FSMT_CUDA(cudaGetLastError(), "chunked kernel launch");
+    return FSMT_OK;
+  }
+  return launch_fused_warp(C, adj, R, sigma, prm, w, a, b, ga, gb, obj, cop, ctl, st);
 }
 
 fsmt_status launch_pgd(const Compiled& C, int R, float eta, float bscale, int sweeps, int polish, const float* prm,
@@ -779,6 +925,11 @@ fsmt_status fsmt_upload(fsmt_compiled* cc, void* stream) {
                o_hsp = push_array(blob, C.hs_ptr), o_hsl = push_array(blob, C.hs_lvar),
                o_hsc = push_array(blob, C.hs_coef), o_hsq = push_array(blob, C.hs_q0),
                o_hsi = push_array(blob, C.hs_inv_qq);
+  std::vector<uint2> cnodes(C.cnode_slot.size());
+  for (size_t i = 0; i < cnodes.size(); ++i) cnodes[i] = make_uint2(C.cnode_slot[i], C.cnode_hilo[i]);
+  const size_t o_ccp = push_array(blob, C.chunk_con_ptr), o_ccon = push_array(blob, C.ccon),
+               o_cnp = push_array(blob, C.chunk_node_ptr), o_cnodes = push_array(blob, cnodes),
+               o_csp = push_array(blob, C.chunk_slot_ptr), o_slab = push_array(blob, C.slot_label);
   if (C.dev_block) {
     cudaFree(C.dev_block);
     C.dev_block = nullptr;
@@ -821,11 +972,22 @@ fsmt_status fsmt_upload(fsmt_compiled* cc, void* stream) {
   v.hs_coef = (const float*)(base + o_hsc);
   v.hs_q0 = (const float*)(base + o_hsq);
   v.hs_inv_qq = (const float*)(base + o_hsi);
+  v.n_chunks = C.n_chunks;
+  v.chunk_con_ptr = (const int32_t*)(base + o_ccp);
+  v.ccon = (const int4*)(base + o_ccon);
+  v.chunk_node_ptr = (const int32_t*)(base + o_cnp);
+  v.cnodes = (const uint2*)(base + o_cnodes);
+  v.chunk_slot_ptr = (const int32_t*)(base + o_csp);
+  v.slot_label = (const int32_t*)(base + o_slab);
   FSMT_CUDA(cudaFuncSetAttribute(k_fused<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024),
             "smem attribute");
   FSMT_CUDA(cudaFuncSetAttribute(k_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024),
             "smem attribute");
   FSMT_CUDA(cudaFuncSetAttribute(k_round_check, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024),
+            "smem attribute");
+  FSMT_CUDA(cudaFuncSetAttribute(k_chunked<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024),
+            "smem attribute");
+  FSMT_CUDA(cudaFuncSetAttribute(k_chunked<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024),
             "smem attribute");
   cudaGetDevice(&C.device);
   C.uploaded = true;

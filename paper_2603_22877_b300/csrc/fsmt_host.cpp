@@ -209,6 +209,104 @@ static bool build_diagram(int kind, int param, const int32_t* lits, int L, Diagr
   return true;
 }
 
+// ------------------------------------------------------ chunked schedule ----
+// Groups the constraints of C_sigma into chunks for the chunked kernel.  The
+// constraints are first ordered for locality -- by the smallest and the largest
+// id of the variables they touch (Booleans by id, reals after them), coarsely
+// then finely -- so that a chunk's constraints share variables.  A chunk then
+// takes constraints in that order until it would exceed kChunkMaxCons
+// constraints, kChunkMaxNodes nodes or kChunkMaxSlots distinct variables/atoms
+// ("slots").  Every node's label is rewritten to its chunk-local slot.  Returns
+// false if a single constraint does not fit a chunk (the warp-per-constraint
+// kernel then serves the instance).
+static bool build_chunks(const Problem& P, Compiled& C) {
+  const int n_obj = C.n_obj;
+  C.chunk_con_ptr.assign(1, 0);
+  C.chunk_node_ptr.assign(1, 0);
+  C.chunk_slot_ptr.assign(1, 0);
+  C.slot_label.clear();
+  C.ccon.clear();
+  C.cnode_slot.clear();
+  C.cnode_hilo.clear();
+  C.n_chunks = 0;
+  if (n_obj == 0) return true;
+  struct Key {
+    int64_t k0, k1, k2, k3;
+    int s;
+  };
+  std::vector<Key> keys(n_obj);
+  for (int s = 0; s < n_obj; ++s) {
+    int64_t lo = INT64_MAX, hi = -1;
+    for (int v = C.con_ptr[s]; v < C.con_ptr[s + 1]; ++v) {
+      const int lab = (int)C.node_label[v];
+      if (lab < C.n_bool) {
+        lo = std::min<int64_t>(lo, lab);
+        hi = std::max<int64_t>(hi, lab);
+      } else {
+        const int i = lab - C.n_bool;
+        for (int64_t t = P.atom_ptr[i]; t < P.atom_ptr[i + 1]; ++t) {
+          const int64_t id = (int64_t)C.n_bool + P.atom_var[t];
+          lo = std::min(lo, id);
+          hi = std::max(hi, id);
+        }
+      }
+    }
+    if (hi < 0) lo = hi = 0;
+    keys[s] = {lo >> 6, hi >> 3, hi, lo, s};
+  }
+  std::sort(keys.begin(), keys.end(), [](const Key& x, const Key& y) {
+    if (x.k0 != y.k0) return x.k0 < y.k0;
+    if (x.k1 != y.k1) return x.k1 < y.k1;
+    if (x.k2 != y.k2) return x.k2 < y.k2;
+    if (x.k3 != y.k3) return x.k3 < y.k3;
+    return x.s < y.s;
+  });
+  std::unordered_map<int, int> slot_of;
+  int chunk_cons = 0, chunk_nodes = 0;
+  auto close_chunk = [&]() {
+    C.chunk_con_ptr.push_back((int32_t)(C.ccon.size() / 4));
+    C.chunk_node_ptr.push_back((int32_t)C.cnode_slot.size());
+    C.chunk_slot_ptr.push_back((int32_t)C.slot_label.size());
+    ++C.n_chunks;
+    slot_of.clear();
+    chunk_cons = chunk_nodes = 0;
+  };
+  for (const Key& k : keys) {
+    const int s = k.s;
+    const int b = C.con_ptr[s], V = C.con_ptr[s + 1] - b;
+    int new_slots = 0;
+    for (int v = b; v < b + V; ++v)
+      if (!slot_of.count((int)C.node_label[v])) ++new_slots;  // may count a repeat twice: conservative
+    if (chunk_cons > 0 && (chunk_cons + 1 > kChunkMaxCons || chunk_nodes + V > kChunkMaxNodes ||
+                           (int)slot_of.size() + new_slots > kChunkMaxSlots))
+      close_chunk();
+    if (V > kChunkMaxNodes) return false;
+    C.ccon.push_back(chunk_nodes);
+    C.ccon.push_back(V);
+    C.ccon.push_back(C.con_root[s]);
+    C.ccon.push_back(C.con_id[s]);
+    for (int v = b; v < b + V; ++v) {
+      const int lab = (int)C.node_label[v];
+      auto it = slot_of.find(lab);
+      int slot;
+      if (it == slot_of.end()) {
+        slot = (int)slot_of.size();
+        slot_of.emplace(lab, slot);
+        C.slot_label.push_back(lab);
+      } else {
+        slot = it->second;
+      }
+      C.cnode_slot.push_back((uint32_t)slot);
+      C.cnode_hilo.push_back(C.node_hilo[v]);
+    }
+    if ((int)slot_of.size() > kChunkMaxSlots) return false;
+    ++chunk_cons;
+    chunk_nodes += V;
+  }
+  if (chunk_cons > 0) close_chunk();
+  return true;
+}
+
 // ------------------------------------------------- FP32 bound rounding ------
 // Largest (upper) or smallest (lower) float f with  f * c <= d  (f * c < d when
 // strict), c a nonzero integer below 2^24 in magnitude and d an integer below
@@ -294,6 +392,7 @@ static fsmt_status compile(const Problem& P, int policy, Compiled& C) {
   }
   if (C.n_obj == 0) C.n_obj_nodes = 0;
   C.con_ptr[n_cons] = (int32_t)total;
+  C.chunked_ok = build_chunks(P, C);
   // atoms, normalised to  q.y - q0 (<= | <) 0
   const int K = C.n_atoms;
   C.atom_ptr.assign(K + 1, 0);
@@ -737,6 +836,7 @@ fsmt_status fsmt_compiled_info(const fsmt_compiled* c, fsmt_info* out) {
   out->n_free_reals = (int32_t)C.free_var.size();
   out->atom_nnz = (int64_t)C.atom_var.size();
   out->fused_ok = fsmt_fused_limit_ok(C);
+  out->n_chunks = C.chunked_ok ? C.n_chunks : 0;
   return FSMT_OK;
 }
 

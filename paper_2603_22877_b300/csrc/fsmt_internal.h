@@ -21,6 +21,10 @@ namespace fsmt {
 constexpr int kMaxNodesPerDiagram = 65533;  // hi/lo are 16-bit and V, V+1 are the terminals
 constexpr int kMaxCompVars = 32;            // reals per block coupled by half-spaces
 constexpr int kMaxCompHalfspaces = 64;      // half-spaces per block
+// chunks of the chunked forward/adjoint kernel
+constexpr int kChunkMaxCons = 64;    // constraints per chunk
+constexpr int kChunkMaxNodes = 2048; // decision nodes per chunk
+constexpr int kChunkMaxSlots = 256;  // distinct variables / atoms per chunk
 
 void set_error(const std::string& msg);
 
@@ -69,6 +73,14 @@ struct DevView {
   const float* hs_coef;
   const float* hs_q0;
   const float* hs_inv_qq;       // 1 / ||q||^2
+  // chunked schedule of the constraints of C_sigma
+  int32_t n_chunks;
+  const int32_t* chunk_con_ptr;   // [n_chunks + 1] into ccon
+  const int4* ccon;               // {node offset in chunk, V, root, constraint id}
+  const int32_t* chunk_node_ptr;  // [n_chunks + 1] into cnodes
+  const uint2* cnodes;            // {slot, hi | lo << 16}
+  const int32_t* chunk_slot_ptr;  // [n_chunks + 1] into slot_label
+  const int32_t* slot_label;      // variable id (< n_bool) or n_bool + atom index
 };
 
 // Host-side compiled form (arrays mirror DevView).
@@ -88,6 +100,12 @@ struct Compiled {
   std::vector<int32_t> free_var;
   std::vector<int32_t> comp_var_ptr{0}, comp_var, comp_hs_ptr{0}, hs_ptr{0}, hs_lvar;
   std::vector<float> hs_coef, hs_q0, hs_inv_qq;
+  // chunked schedule of C_sigma (see build_chunks in fsmt_host.cpp)
+  bool chunked_ok = false;
+  int32_t n_chunks = 0;
+  std::vector<int32_t> chunk_con_ptr{0}, chunk_node_ptr{0}, chunk_slot_ptr{0}, slot_label;
+  std::vector<int32_t> ccon;  // 4 ints per constraint
+  std::vector<uint32_t> cnode_slot, cnode_hilo;
   // device side
   void* dev_block = nullptr;  // one allocation holding every device array
   DevView view{};
