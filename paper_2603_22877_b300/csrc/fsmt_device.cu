@@ -23,8 +23,11 @@ constexpr int kFusedThreads = 256;  // 8 warps
 constexpr int kSmemBudget = 112 * 1024;
 constexpr int kMaxObjSmemR = 4096;
 constexpr int kChunkThreads = 512;  // 16 warps
-constexpr size_t kChunkFixedBytes = (size_t)kChunkMaxNodes * 8 + (size_t)kChunkMaxCons * 16 + (size_t)kChunkMaxSlots * 4 +
-                                    (size_t)kChunkMaxSlots * 32 * 4 * 3;
+// shared memory of the chunked kernel without the per-warp message arrays
+inline size_t chunk_fixed_bytes(int rpl) {
+  return (size_t)kChunkMaxNodes * 8 + (size_t)kChunkMaxCons * 16 + (size_t)kChunkMaxSlots * 4 +
+         (size_t)kChunkMaxSlots * 32 * 4 * rpl * 2;
+}
 constexpr size_t kSmemMax = 227 * 1024;
 
 // stage parameter slots (device float[16])
@@ -223,34 +226,56 @@ __global__ void __launch_bounds__(kFusedThreads) k_fused(DevView d, int R, float
 
 // -------------------------------------------------------- chunked kernel --
 // One CTA per chunk of constraints of C_sigma (grid-stride over chunks), looping
-// over restart tiles.  Per tile: (1) every slot -- a Boolean or an atom used by
-// the chunk -- gets its TRUE-probability p (and dd/dz for atoms) once, lane =
-// restart; (2) each warp runs Alg. 3 and Alg. 4 on its constraints with p read
-// from shared memory and m_td / m_bu in the warp's shared array, adding
-// w_c * m_td[v] (m_bu[hi] - m_bu[lo]) into the slot's shared accumulator;
-// (3) each slot's accumulated derivative goes to the global gradient once.
-template <bool ADJ>
+// over restart tiles of 32*RPL restarts; each lane carries RPL restarts (lane,
+// lane+32, ...), so every shared-memory operand is an RPL-wide vector and every
+// global access of a warp is a contiguous 128-byte line.  Per tile:
+//  (1) every slot -- a Boolean or an atom used by the chunk -- gets its
+//      TRUE-probability p once (Eq. rounding / Eq. sampling);
+//  (2) each warp runs Alg. 3 then Alg. 4 on its constraints with p from shared
+//      memory.  Only decision nodes are stored: pushes into a terminal are
+//      skipped in the forward pass and the terminals read as 1 (TRUE) / 0
+//      (FALSE) in the backward pass; COP_c = m_bu[root] (Lemma backward).  The
+//      backward pass adds w_c m_td[v] (m_bu[hi] - m_bu[lo]) into the slot's
+//      shared accumulator;
+//  (3) each slot's accumulated derivative reaches the global gradient once (for
+//      atoms through dd/db_j, recomputed here).
+template <int RPL>
+struct __align__(4 * RPL) Pack {
+  float v[RPL];
+};
+
+__device__ __forceinline__ float atom_dd_dz(const DevView& d, int i, int R, int r, float s_inv,
+                                           const float* __restrict__ b) {
+  if (s_inv <= 0.f) return 0.f;
+  const int k0 = __ldg(d.atom_ptr + i), k1 = __ldg(d.atom_ptr + i + 1);
+  float z = -__ldg(d.atom_q0f + i);
+  for (int k = k0; k < k1; ++k) z = fmaf(__ldg(d.atom_coef + k), __ldg(b + (size_t)__ldg(d.atom_var + k) * R + r), z);
+  const float si = __ldg(d.atom_inv_norm + i) * s_inv;
+  const float u = z * si;
+  return kTwoOverSqrtPi * __expf(-u * u) * si;
+}
+
+template <bool ADJ, int RPL>
 __global__ void __launch_bounds__(kChunkThreads, 1)
     k_chunked(DevView d, int R, float sigma, const float* prm, int vcap, const float* __restrict__ w,
               const float* __restrict__ a, const float* __restrict__ b, float* __restrict__ grad_a,
               float* __restrict__ grad_b, float* __restrict__ obj, float* __restrict__ cop, const int* ctl) {
+  using PK = Pack<RPL>;
   if (ctl && ctl[0] == 0) return;
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
   uint2* s_node = reinterpret_cast<uint2*>(smem);
   int4* s_con = reinterpret_cast<int4*>(s_node + kChunkMaxNodes);
   int* s_lab = reinterpret_cast<int*>(s_con + kChunkMaxCons);
-  float* s_p = reinterpret_cast<float*>(s_lab + kChunkMaxSlots);
-  float* s_gz = s_p + kChunkMaxSlots * 32;
-  float* s_g = s_gz + kChunkMaxSlots * 32;
-  float* s_mw = s_g + kChunkMaxSlots * 32;
-  float* s_m = s_mw + warp * (vcap + 2) * 32;
-  float* obj_s = (R <= kMaxObjSmemR) ? s_mw + W * (vcap + 2) * 32 : nullptr;
+  PK* s_p = reinterpret_cast<PK*>(s_lab + kChunkMaxSlots);
+  PK* s_g = s_p + kChunkMaxSlots * 32;
+  PK* s_m = s_g + kChunkMaxSlots * 32 + warp * vcap * 32;
+  float* obj_s = (R <= kMaxObjSmemR) ? reinterpret_cast<float*>(s_g + kChunkMaxSlots * 32 + W * vcap * 32) : nullptr;
   if (obj_s)
     for (int r = threadIdx.x; r < R; r += blockDim.x) obj_s[r] = 0.f;
   sigma = load_param(prm, P_SIGMA, sigma);
   const float s_inv = sigma > 0.f ? kInvSqrt2 / sigma : 0.f;
-  const int n_tiles = (R + 31) >> 5;
+  const int n_tiles = (R + 32 * RPL - 1) / (32 * RPL);
   for (int q = blockIdx.x; q < d.n_chunks; q += gridDim.x) {
     const int c0 = __ldg(d.chunk_con_ptr + q), nc = __ldg(d.chunk_con_ptr + q + 1) - c0;
     const int n0 = __ldg(d.chunk_node_ptr + q), nn = __ldg(d.chunk_node_ptr + q + 1) - n0;
@@ -261,69 +286,136 @@ __global__ void __launch_bounds__(kChunkThreads, 1)
     for (int i = threadIdx.x; i < ns; i += blockDim.x) s_lab[i] = __ldg(d.slot_label + l0 + i);
     __syncthreads();
     for (int t = 0; t < n_tiles; ++t) {
-      const int r = t * 32 + lane;
-      const bool ok = r < R;
-      // (1) slot probabilities (Eq. rounding / Eq. sampling), once per slot
+      int rr[RPL];
+      bool ok[RPL];
+#pragma unroll
+      for (int k = 0; k < RPL; ++k) {
+        rr[k] = (t * RPL + k) * 32 + lane;
+        ok[k] = rr[k] < R;
+      }
+      // (1) slot probabilities, once per slot and restart
       for (int i = warp; i < ns; i += W) {
-        float p, gz;
-        literal_prob(d, s_lab[i], R, r, ok, s_inv, a, b, p, gz);
-        s_p[i * 32 + lane] = p;
-        if (ADJ) {
-          s_gz[i * 32 + lane] = gz;
-          s_g[i * 32 + lane] = 0.f;
+        PK pp, zz;
+#pragma unroll
+        for (int k = 0; k < RPL; ++k) {
+          float gz;
+          literal_prob(d, s_lab[i], R, rr[k], ok[k], s_inv, a, b, pp.v[k], gz);
+          zz.v[k] = 0.f;
         }
+        s_p[i * 32 + lane] = pp;
+        if (ADJ) s_g[i * 32 + lane] = zz;
       }
       __syncthreads();
-      // (2) Alg. 3 then Alg. 4 per constraint, one warp per constraint
-      for (int k = warp; k < nc; k += W) {
-        const int4 cn = s_con[k];
+      // (2) Alg. 3 and Alg. 4, one warp per constraint
+      for (int c = warp; c < nc; c += W) {
+        const int4 cn = s_con[c];
         const uint2* nd = s_node + cn.x;
         const int V = cn.y;
-        for (int v = 0; v < V + 2; ++v) s_m[v * 32 + lane] = 0.f;
-        s_m[cn.z * 32 + lane] = 1.f;
-        for (int v = 0; v < V; ++v) {
-          const uint2 e = nd[v];
-          const int hi = (int)(e.y & 0xffffu) * 32 + lane, lo = (int)(e.y >> 16) * 32 + lane;
-          const float p = s_p[e.x * 32 + lane];
-          const float mv = s_m[v * 32 + lane];
-          s_m[hi] = fmaf(p, mv, s_m[hi]);
-          s_m[lo] = fmaf(1.f - p, mv, s_m[lo]);
-        }
-        const float cp = s_m[V * 32 + lane];
-        const float wc = ok ? __ldg(w + (size_t)cn.w * R + r) : 0.f;
-        if (ok) {
-          if (cop) cop[(size_t)cn.w * R + r] = cp;
-          if (obj) {
-            const float contrib = wc * (1.f - 2.f * cp);
-            if (obj_s)
-              atomicAdd(obj_s + r, contrib);
-            else
-              atomicAdd(obj + r, contrib);
+        PK wc;
+#pragma unroll
+        for (int k = 0; k < RPL; ++k) wc.v[k] = ok[k] ? __ldg(w + (size_t)cn.w * R + rr[k]) : 0.f;
+        if (ADJ) {
+          for (int v = 0; v < V; ++v) {
+            PK z;
+#pragma unroll
+            for (int k = 0; k < RPL; ++k) z.v[k] = 0.f;
+            s_m[v * 32 + lane] = z;
+          }
+          if (V > 0) {
+            PK one;
+#pragma unroll
+            for (int k = 0; k < RPL; ++k) one.v[k] = 1.f;
+            s_m[lane] = one;  // the root is node 0
+          }
+          for (int v = 0; v < V; ++v) {  // Alg. 3, topological order, decision nodes only
+            const uint2 e = nd[v];
+            const int hi = (int)(e.y & 0xffffu), lo = (int)(e.y >> 16);
+            const PK p = s_p[e.x * 32 + lane];
+            const PK mv = s_m[v * 32 + lane];
+            if (hi < V) {
+              PK mh = s_m[hi * 32 + lane];
+#pragma unroll
+              for (int k = 0; k < RPL; ++k) mh.v[k] = fmaf(p.v[k], mv.v[k], mh.v[k]);
+              s_m[hi * 32 + lane] = mh;
+            }
+            if (lo < V) {
+              PK ml = s_m[lo * 32 + lane];
+#pragma unroll
+              for (int k = 0; k < RPL; ++k) ml.v[k] = fmaf(1.f - p.v[k], mv.v[k], ml.v[k]);
+              s_m[lo * 32 + lane] = ml;
+            }
           }
         }
-        if (ADJ) {
-          s_m[V * 32 + lane] = 1.f;
-          s_m[(V + 1) * 32 + lane] = 0.f;
-          for (int v = V - 1; v >= 0; --v) {
-            const uint2 e = nd[v];
-            const float mh = s_m[(e.y & 0xffffu) * 32 + lane], ml = s_m[(e.y >> 16) * 32 + lane];
-            const float p = s_p[e.x * 32 + lane];
-            const float td = s_m[v * 32 + lane];
-            const float diff = mh - ml;
-            s_m[v * 32 + lane] = fmaf(p, diff, ml);
-            const float g = wc * td * diff;
-            if (g != 0.f) atomicAdd(s_g + e.x * 32 + lane, g);
+        PK root_bu;  // COP_c = m_bu[root]
+#pragma unroll
+        for (int k = 0; k < RPL; ++k) root_bu.v[k] = (V == 0 && cn.z == 0) ? 1.f : 0.f;
+        for (int v = V - 1; v >= 0; --v) {  // Alg. 4, reverse topological order
+          const uint2 e = nd[v];
+          const int hi = (int)(e.y & 0xffffu), lo = (int)(e.y >> 16);
+          const PK p = s_p[e.x * 32 + lane];
+          PK mh, ml, nb, gg;
+          if (hi < V) {
+            mh = s_m[hi * 32 + lane];
+          } else {
+#pragma unroll
+            for (int k = 0; k < RPL; ++k) mh.v[k] = hi == V ? 1.f : 0.f;
+          }
+          if (lo < V) {
+            ml = s_m[lo * 32 + lane];
+          } else {
+#pragma unroll
+            for (int k = 0; k < RPL; ++k) ml.v[k] = lo == V ? 1.f : 0.f;
+          }
+          bool any = false;
+          if (ADJ) {
+            const PK td = s_m[v * 32 + lane];
+#pragma unroll
+            for (int k = 0; k < RPL; ++k) {
+              const float diff = mh.v[k] - ml.v[k];
+              nb.v[k] = fmaf(p.v[k], diff, ml.v[k]);
+              gg.v[k] = wc.v[k] * td.v[k] * diff;
+              any |= gg.v[k] != 0.f;
+            }
+          } else {
+#pragma unroll
+            for (int k = 0; k < RPL; ++k) nb.v[k] = fmaf(p.v[k], mh.v[k] - ml.v[k], ml.v[k]);
+          }
+          s_m[v * 32 + lane] = nb;
+          if (v == 0) root_bu = nb;
+          if (ADJ && any) {
+            float* gs = s_g[e.x * 32 + lane].v;
+#pragma unroll
+            for (int k = 0; k < RPL; ++k)
+              if (gg.v[k] != 0.f) atomicAdd(gs + k, gg.v[k]);
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < RPL; ++k) {
+          if (!ok[k]) continue;
+          const float cp = root_bu.v[k];
+          if (cop) cop[(size_t)cn.w * R + rr[k]] = cp;
+          if (obj) {
+            const float contrib = wc.v[k] * (1.f - 2.f * cp);
+            if (obj_s)
+              atomicAdd(obj_s + rr[k], contrib);
+            else
+              atomicAdd(obj + rr[k], contrib);
           }
         }
       }
       __syncthreads();
-      // (3) one global update per slot
+      // (3) one global update per slot and restart
       if (ADJ) {
-        if (ok)
-          for (int i = warp; i < ns; i += W) {
-            const float g = s_g[i * 32 + lane];
-            if (g != 0.f) scatter_grad(d, s_lab[i], R, r, g, s_gz[i * 32 + lane], grad_a, grad_b);
+        for (int i = warp; i < ns; i += W) {
+          const PK g = s_g[i * 32 + lane];
+          const int lab = s_lab[i];
+#pragma unroll
+          for (int k = 0; k < RPL; ++k) {
+            if (!ok[k] || g.v[k] == 0.f) continue;
+            const float gz = lab < d.n_bool ? 0.f : atom_dd_dz(d, lab - d.n_bool, R, rr[k], s_inv, b);
+            scatter_grad(d, lab, R, rr[k], g.v[k], gz, grad_a, grad_b);
           }
+        }
         __syncthreads();
       }
     }
@@ -804,28 +896,43 @@ fsmt_status launch_fused_warp(const Compiled& C, bool adj, int R, float sigma, c
   return FSMT_OK;
 }
 
-// warps of the chunked kernel for this instance (0 if it cannot run it)
-int chunk_warps(const Compiled& C, int R) {
-  if (!C.chunked_ok) return 0;
-  const size_t per_warp = (size_t)(std::max(1, C.max_nodes) + 2) * 32 * 4;
-  const size_t fixed = kChunkFixedBytes + (R <= kMaxObjSmemR ? (size_t)R * 4 : 0);
-  if (fixed + 4 * per_warp > kSmemMax) return 0;
-  return (int)std::min<size_t>(kChunkThreads / 32, (kSmemMax - fixed) / per_warp);
+// restarts per lane and warps of the chunked kernel for this instance (warps 0: it cannot run it)
+struct ChunkShape {
+  int rpl, warps;
+  size_t smem;
+};
+ChunkShape chunk_shape(const Compiled& C, int R) {
+  ChunkShape s{R > 32 ? 2 : 1, 0, 0};
+  if (!C.chunked_ok) return s;
+  const int vcap = std::max(1, C.max_nodes);
+  const size_t per_warp = (size_t)vcap * 32 * 4 * s.rpl;
+  const size_t fixed = chunk_fixed_bytes(s.rpl) + (R <= kMaxObjSmemR ? (size_t)R * 4 : 0);
+  if (fixed + 4 * per_warp > kSmemMax) return s;
+  s.warps = (int)std::min<size_t>(kChunkThreads / 32, (kSmemMax - fixed) / per_warp);
+  s.smem = fixed + (size_t)s.warps * per_warp;
+  return s;
 }
 
 fsmt_status launch_fused(const Compiled& C, bool adj, int R, float sigma, const float* prm, const float* w,
                          const float* a, const float* b, float* ga, float* gb, float* obj, float* cop, const int* ctl,
                          cudaStream_t st) {
   if (C.n_obj == 0) return FSMT_OK;
-  const int cw = chunk_warps(C, R);
-  if (cw > 0) {
+  const ChunkShape cs = chunk_shape(C, R);
+  if (cs.warps > 0) {
     const int vcap = std::max(1, C.max_nodes);
-    const size_t smem = kChunkFixedBytes + (size_t)cw * (vcap + 2) * 32 * 4 + (R <= kMaxObjSmemR ? (size_t)R * 4 : 0);
     const int blocks = std::max(1, std::min(C.n_chunks, sm_count()));
-    if (adj)
-      k_chunked<true><<<blocks, cw * 32, smem, st>>>(C.view, R, sigma, prm, vcap, w, a, b, ga, gb, obj, cop, ctl);
-    else
-      k_chunked<false><<<blocks, cw * 32, smem, st>>>(C.view, R, sigma, prm, vcap, w, a, b, ga, gb, obj, cop, ctl);
+    const dim3 g(blocks), t(cs.warps * 32);
+    if (cs.rpl == 2) {
+      if (adj)
+        k_chunked<true, 2><<<g, t, cs.smem, st>>>(C.view, R, sigma, prm, vcap, w, a, b, ga, gb, obj, cop, ctl);
+      else
+        k_chunked<false, 2><<<g, t, cs.smem, st>>>(C.view, R, sigma, prm, vcap, w, a, b, ga, gb, obj, cop, ctl);
+    } else {
+      if (adj)
+        k_chunked<true, 1><<<g, t, cs.smem, st>>>(C.view, R, sigma, prm, vcap, w, a, b, ga, gb, obj, cop, ctl);
+      else
+        k_chunked<false, 1><<<g, t, cs.smem, st>>>(C.view, R, sigma, prm, vcap, w, a, b, ga, gb, obj, cop, ctl);
+    }
     FSMT_CUDA(cudaGetLastError(), "chunked kernel launch");
     return FSMT_OK;
   }
@@ -985,9 +1092,13 @@ fsmt_status fsmt_upload(fsmt_compiled* cc, void* stream) {
             "smem attribute");
   FSMT_CUDA(cudaFuncSetAttribute(k_round_check, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024),
             "smem attribute");
-  FSMT_CUDA(cudaFuncSetAttribute(k_chunked<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024),
+  FSMT_CUDA(cudaFuncSetAttribute(k_chunked<true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024),
             "smem attribute");
-  FSMT_CUDA(cudaFuncSetAttribute(k_chunked<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024),
+  FSMT_CUDA(cudaFuncSetAttribute(k_chunked<false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024),
+            "smem attribute");
+  FSMT_CUDA(cudaFuncSetAttribute(k_chunked<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024),
+            "smem attribute");
+  FSMT_CUDA(cudaFuncSetAttribute(k_chunked<false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024),
             "smem attribute");
   cudaGetDevice(&C.device);
   C.uploaded = true;

@@ -24,7 +24,7 @@ constexpr int kMaxCompHalfspaces = 64;      // half-spaces per block
 // chunks of the chunked forward/adjoint kernel
 constexpr int kChunkMaxCons = 64;    // constraints per chunk
 constexpr int kChunkMaxNodes = 2048; // decision nodes per chunk
-constexpr int kChunkMaxSlots = 256;  // distinct variables / atoms per chunk
+constexpr int kChunkMaxSlots = 192;  // distinct variables / atoms per chunk
 
 void set_error(const std::string& msg);
 

@@ -1,0 +1,74 @@
+"""Edge cases of the CUDA path against the oracle: constant diagrams, a diagram
+too large for a chunk (served by the warp-per-constraint kernel), wide atoms,
+ragged restart counts, sigma = 0 and an objective with no constraints."""
+import numpy as np
+import pytest
+
+from oracle import objective as OBJ
+from workloads import instances as W
+
+from _gpu_common import COP_TOL, assert_grad_close, gpu_adjoint, setup
+
+pytestmark = pytest.mark.gpu
+
+
+def mixed_instance(big=False, seed=0):
+    rng = np.random.default_rng(seed)
+    n_bool, n_real = 240, 30
+    B = W._Builder(n_bool, n_real)
+    py = rng.uniform(0, 10, n_real)
+    atoms = []
+    for _ in range(40):
+        nnz = int(rng.integers(1, 21))
+        var = rng.choice(n_real, nnz, replace=False)
+        coef = rng.integers(1, 6, nnz) * rng.choice([-1, 1], nnz)
+        atoms.append(B.atom(var, coef, int(np.ceil(float(coef @ py[var]))), W.LE))
+    B.con(W.OR, [])                                       # constant FALSE
+    B.con(W.CARD_LE, [W.lit(0), W.lit(1)], param=5)       # constant TRUE
+    B.con(W.OR, [W.lit(2, True)])                         # a single literal
+    for _ in range(60):
+        kind = int(rng.choice([W.OR, W.XOR, W.CARD_LE, W.NAE, W.NEQ_OR]))
+        L = int(rng.integers(2, 9))
+        ids = list(rng.choice(n_bool, L, replace=False)) + list(rng.choice(atoms, 2, replace=False))
+        lits = [2 * int(i) + int(rng.integers(2)) for i in ids]
+        param = int(rng.integers(0, len(lits))) if kind == W.CARD_LE else (2 if kind == W.NEQ_OR else 0)
+        B.con(kind, lits, param)
+    if big:  # 200 distinct literals: more slots than a chunk holds
+        B.con(W.XOR, [2 * i + (i % 2) for i in range(200)])
+        B.con(W.CARD_LE, [2 * i for i in range(30, 60)] + [2 * atoms[0]], param=6)
+    return B.freeze("mixed", np.zeros(n_real), np.full(n_real, 10.0), np.ones(n_bool, np.int8), py, 10.0)
+
+
+@pytest.mark.parametrize("big", [False, True])
+@pytest.mark.parametrize("R", [1, 33, 65])
+def test_mixed_kinds_against_oracle(big, R):
+    inst = mixed_instance(big)
+    P, comp, a, b, w = setup(inst, R)
+    if big:
+        assert comp.info["n_chunks"] == 0  # the warp-per-constraint kernel serves this instance
+    else:
+        assert comp.info["n_chunks"] > 0
+    D = OBJ.Diagrams(inst)
+    oc = OBJ.objective_constraints(inst)
+    for sigma in (0.0, 0.7, 5.0):
+        obj_ref, cop_ref, ga_ref, gb_ref = OBJ.evaluate(inst, a.astype(np.float64), b.astype(np.float64),
+                                                        w.astype(np.float64), sigma, diagrams=D)
+        obj, cop, ga, gb = gpu_adjoint(comp, R, np.float32(sigma), a, b, w)
+        assert np.abs(cop[oc] - cop_ref[oc]).max() <= COP_TOL
+        assert cop[0].max() == 0.0 and cop[1].min() == 1.0
+        np.testing.assert_allclose(obj, obj_ref, rtol=1e-5, atol=1e-4)
+        assert_grad_close(ga, ga_ref, f"grad_a sigma={sigma}")
+        assert_grad_close(gb, gb_ref, f"grad_b sigma={sigma}")
+
+
+def test_objective_without_constraints():
+    """Every constraint is a unit atom handled by the projection: C = 0, gradients 0."""
+    B = W._Builder(3, 2)
+    B.con(W.OR, [W.lit(B.atom([0], [1], 5, W.LE))])
+    B.con(W.OR, [W.lit(B.atom([0, 1], [1, -1], -1, W.LE))])
+    inst = B.freeze("units", np.zeros(2), np.full(2, 9.0), np.ones(3, np.int8), np.array([1.0, 3.0]), 1.0)
+    R = 40
+    P, comp, a, b, w = setup(inst, R)
+    assert comp.info["n_obj_cons"] == 0
+    obj, cop, ga, gb = gpu_adjoint(comp, R, 1.0, a, b, w)
+    assert (obj == 0).all() and (ga == 0).all() and (gb == 0).all()
