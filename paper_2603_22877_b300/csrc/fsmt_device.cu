@@ -227,32 +227,45 @@ __global__ void __launch_bounds__(kFusedThreads) k_fused(DevView d, int R, float
 // -------------------------------------------------------- chunked kernel --
 // One CTA per chunk of constraints of C_sigma (grid-stride over chunks), looping
 // over restart tiles of 32*RPL restarts; each lane carries RPL restarts (lane,
-// lane+32, ...), so every shared-memory operand is an RPL-wide vector and every
-// global access of a warp is a contiguous 128-byte line.  Per tile:
+// lane+32, ...), so every global access of a warp is a contiguous 128-byte line.
+// Per tile:
 //  (1) every slot -- a Boolean or an atom used by the chunk -- gets its
 //      TRUE-probability p once (Eq. rounding / Eq. sampling);
-//  (2) each warp runs Alg. 3 then Alg. 4 on its constraints with p from shared
-//      memory.  Only decision nodes are stored: pushes into a terminal are
-//      skipped in the forward pass and the terminals read as 1 (TRUE) / 0
-//      (FALSE) in the backward pass; COP_c = m_bu[root] (Lemma backward).  The
-//      backward pass adds w_c m_td[v] (m_bu[hi] - m_bu[lo]) into the slot's
+//  (2) each warp runs Alg. 3 then Alg. 4 on its constraints, with p read from
+//      shared memory and the messages in the warp's rows: one row per decision
+//      node plus two fixed rows for the terminals (the compiler points terminal
+//      children there), so the passes have no branches -- the forward pass may
+//      push into the terminal rows, which are then set to 1 (TRUE) and 0 (FALSE)
+//      for the backward pass; COP_c = m_bu[root] (Lemma backward).  The
+//      backward pass adds w_c m_td[v] (m_bu[hi] - m_bu[lo]) to the slot's
 //      shared accumulator;
 //  (3) each slot's accumulated derivative reaches the global gradient once (for
-//      atoms through dd/db_j, recomputed here).
+//      atoms through dd/db_j).
 template <int RPL>
 struct __align__(4 * RPL) Pack {
   float v[RPL];
 };
 
-__device__ __forceinline__ float atom_dd_dz(const DevView& d, int i, int R, int r, float s_inv,
-                                           const float* __restrict__ b) {
-  if (s_inv <= 0.f) return 0.f;
+// erfc(x)/2 for the atom probability, by Abramowitz & Stegun 7.1.26 (Hastings):
+// erf(x) = 1 - (a1 t + ... + a5 t^5) e^{-x^2} + e(x), t = 1/(1 + 0.3275911 x),
+// |e(x)| <= 1.5e-7 for x >= 0; erfc(-x) = 2 - erfc(x).  `ex` is e^{-x^2}.
+__device__ __forceinline__ float half_erfc_as(float x, float ex) {
+  const float ax = fabsf(x);
+  const float t = __frcp_rn(fmaf(0.3275911f, ax, 1.f));
+  float poly = fmaf(t, 1.061405429f, -1.453152027f);
+  poly = fmaf(t, poly, 1.421413741f);
+  poly = fmaf(t, poly, -0.284496736f);
+  poly = fmaf(t, poly, 0.254829592f);
+  const float h = 0.5f * t * poly * ex;  // erfc(|x|) / 2
+  return x >= 0.f ? h : 1.f - h;
+}
+
+// z = q.b - q0 of atom i at restart r (normalised form)
+__device__ __forceinline__ float atom_z(const DevView& d, int i, int R, int r, const float* __restrict__ b) {
   const int k0 = __ldg(d.atom_ptr + i), k1 = __ldg(d.atom_ptr + i + 1);
   float z = -__ldg(d.atom_q0f + i);
   for (int k = k0; k < k1; ++k) z = fmaf(__ldg(d.atom_coef + k), __ldg(b + (size_t)__ldg(d.atom_var + k) * R + r), z);
-  const float si = __ldg(d.atom_inv_norm + i) * s_inv;
-  const float u = z * si;
-  return kTwoOverSqrtPi * __expf(-u * u) * si;
+  return z;
 }
 
 template <bool ADJ, int RPL>
@@ -264,13 +277,16 @@ __global__ void __launch_bounds__(kChunkThreads, 1)
   if (ctl && ctl[0] == 0) return;
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
+  const int rows = vcap + 2;  // decision nodes, then TRUE (vcap) and FALSE (vcap + 1)
   uint2* s_node = reinterpret_cast<uint2*>(smem);
   int4* s_con = reinterpret_cast<int4*>(s_node + kChunkMaxNodes);
   int* s_lab = reinterpret_cast<int*>(s_con + kChunkMaxCons);
   PK* s_p = reinterpret_cast<PK*>(s_lab + kChunkMaxSlots);
-  PK* s_g = s_p + kChunkMaxSlots * 32;
-  PK* s_m = s_g + kChunkMaxSlots * 32 + warp * vcap * 32;
-  float* obj_s = (R <= kMaxObjSmemR) ? reinterpret_cast<float*>(s_g + kChunkMaxSlots * 32 + W * vcap * 32) : nullptr;
+  float* s_g = reinterpret_cast<float*>(s_p + kChunkMaxSlots * 32);  // [RPL][slots][32]
+  PK* s_m = reinterpret_cast<PK*>(s_g + RPL * kChunkMaxSlots * 32) + warp * rows * 32 + lane;
+  float* obj_s = (R <= kMaxObjSmemR)
+                     ? reinterpret_cast<float*>(reinterpret_cast<PK*>(s_g + RPL * kChunkMaxSlots * 32) + W * rows * 32)
+                     : nullptr;
   if (obj_s)
     for (int r = threadIdx.x; r < R; r += blockDim.x) obj_s[r] = 0.f;
   sigma = load_param(prm, P_SIGMA, sigma);
@@ -295,15 +311,30 @@ __global__ void __launch_bounds__(kChunkThreads, 1)
       }
       // (1) slot probabilities, once per slot and restart
       for (int i = warp; i < ns; i += W) {
-        PK pp, zz;
+        const int lab = s_lab[i];
+        PK pp;
+        if (lab < d.n_bool) {
 #pragma unroll
-        for (int k = 0; k < RPL; ++k) {
-          float gz;
-          literal_prob(d, s_lab[i], R, rr[k], ok[k], s_inv, a, b, pp.v[k], gz);
-          zz.v[k] = 0.f;
+          for (int k = 0; k < RPL; ++k) pp.v[k] = ok[k] ? 0.5f * (1.f - __ldg(a + (size_t)lab * R + rr[k])) : 0.f;
+        } else if (s_inv > 0.f) {
+          const int ia = lab - d.n_bool;
+          const float si = __ldg(d.atom_inv_norm + ia) * s_inv;
+#pragma unroll
+          for (int k = 0; k < RPL; ++k) {
+            const float u = ok[k] ? atom_z(d, ia, R, rr[k], b) * si : 0.f;
+            pp.v[k] = half_erfc_as(u, __expf(-u * u));
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < RPL; ++k) {
+            float gz;
+            literal_prob(d, lab, R, rr[k], ok[k], 0.f, a, b, pp.v[k], gz);
+          }
         }
         s_p[i * 32 + lane] = pp;
-        if (ADJ) s_g[i * 32 + lane] = zz;
+        if (ADJ)
+#pragma unroll
+          for (int k = 0; k < RPL; ++k) s_g[(k * kChunkMaxSlots + i) * 32 + lane] = 0.f;
       }
       __syncthreads();
       // (2) Alg. 3 and Alg. 4, one warp per constraint
@@ -314,88 +345,61 @@ __global__ void __launch_bounds__(kChunkThreads, 1)
         PK wc;
 #pragma unroll
         for (int k = 0; k < RPL; ++k) wc.v[k] = ok[k] ? __ldg(w + (size_t)cn.w * R + rr[k]) : 0.f;
-        if (ADJ) {
-          for (int v = 0; v < V; ++v) {
-            PK z;
+        PK zero, one;
 #pragma unroll
-            for (int k = 0; k < RPL; ++k) z.v[k] = 0.f;
-            s_m[v * 32 + lane] = z;
-          }
-          if (V > 0) {
-            PK one;
-#pragma unroll
-            for (int k = 0; k < RPL; ++k) one.v[k] = 1.f;
-            s_m[lane] = one;  // the root is node 0
-          }
-          for (int v = 0; v < V; ++v) {  // Alg. 3, topological order, decision nodes only
+        for (int k = 0; k < RPL; ++k) {
+          zero.v[k] = 0.f;
+          one.v[k] = 1.f;
+        }
+        if (ADJ && V > 0) {
+          s_m[0] = one;  // the root is node 0
+          for (int v = 1; v < V; ++v) s_m[v * 32] = zero;
+          for (int v = 0; v < V; ++v) {  // Alg. 3, topological order
             const uint2 e = nd[v];
-            const int hi = (int)(e.y & 0xffffu), lo = (int)(e.y >> 16);
+            const int hi = (int)(e.y & 0xffffu) * 32, lo = (int)(e.y >> 16) * 32;
             const PK p = s_p[e.x * 32 + lane];
-            const PK mv = s_m[v * 32 + lane];
-            if (hi < V) {
-              PK mh = s_m[hi * 32 + lane];
+            const PK mv = s_m[v * 32];
+            PK mh = s_m[hi], ml = s_m[lo];
 #pragma unroll
-              for (int k = 0; k < RPL; ++k) mh.v[k] = fmaf(p.v[k], mv.v[k], mh.v[k]);
-              s_m[hi * 32 + lane] = mh;
+            for (int k = 0; k < RPL; ++k) {
+              mh.v[k] = fmaf(p.v[k], mv.v[k], mh.v[k]);
+              ml.v[k] = fmaf(-p.v[k], mv.v[k], ml.v[k] + mv.v[k]);
             }
-            if (lo < V) {
-              PK ml = s_m[lo * 32 + lane];
-#pragma unroll
-              for (int k = 0; k < RPL; ++k) ml.v[k] = fmaf(1.f - p.v[k], mv.v[k], ml.v[k]);
-              s_m[lo * 32 + lane] = ml;
-            }
+            s_m[hi] = mh;
+            s_m[lo] = ml;
           }
         }
-        PK root_bu;  // COP_c = m_bu[root]
-#pragma unroll
-        for (int k = 0; k < RPL; ++k) root_bu.v[k] = (V == 0 && cn.z == 0) ? 1.f : 0.f;
+        s_m[vcap * 32] = one;
+        s_m[(vcap + 1) * 32] = zero;
         for (int v = V - 1; v >= 0; --v) {  // Alg. 4, reverse topological order
           const uint2 e = nd[v];
-          const int hi = (int)(e.y & 0xffffu), lo = (int)(e.y >> 16);
+          const PK mh = s_m[(int)(e.y & 0xffffu) * 32], ml = s_m[(int)(e.y >> 16) * 32];
           const PK p = s_p[e.x * 32 + lane];
-          PK mh, ml, nb, gg;
-          if (hi < V) {
-            mh = s_m[hi * 32 + lane];
-          } else {
-#pragma unroll
-            for (int k = 0; k < RPL; ++k) mh.v[k] = hi == V ? 1.f : 0.f;
-          }
-          if (lo < V) {
-            ml = s_m[lo * 32 + lane];
-          } else {
-#pragma unroll
-            for (int k = 0; k < RPL; ++k) ml.v[k] = lo == V ? 1.f : 0.f;
-          }
-          bool any = false;
+          PK nb;
           if (ADJ) {
-            const PK td = s_m[v * 32 + lane];
+            const PK td = s_m[v * 32];
+            float* gs = s_g + e.x * 32 + lane;
 #pragma unroll
             for (int k = 0; k < RPL; ++k) {
               const float diff = mh.v[k] - ml.v[k];
               nb.v[k] = fmaf(p.v[k], diff, ml.v[k]);
-              gg.v[k] = wc.v[k] * td.v[k] * diff;
-              any |= gg.v[k] != 0.f;
+              const float g = wc.v[k] * td.v[k] * diff;
+              if (g != 0.f) atomicAdd(gs + k * kChunkMaxSlots * 32, g);
             }
           } else {
 #pragma unroll
             for (int k = 0; k < RPL; ++k) nb.v[k] = fmaf(p.v[k], mh.v[k] - ml.v[k], ml.v[k]);
           }
-          s_m[v * 32 + lane] = nb;
-          if (v == 0) root_bu = nb;
-          if (ADJ && any) {
-            float* gs = s_g[e.x * 32 + lane].v;
-#pragma unroll
-            for (int k = 0; k < RPL; ++k)
-              if (gg.v[k] != 0.f) atomicAdd(gs + k, gg.v[k]);
-          }
+          s_m[v * 32] = nb;
         }
+        // COP = m_bu[root]; a constant diagram's root is a terminal row
+        const PK cp = V > 0 ? s_m[0] : s_m[(cn.z == 0 ? vcap : vcap + 1) * 32];
 #pragma unroll
         for (int k = 0; k < RPL; ++k) {
           if (!ok[k]) continue;
-          const float cp = root_bu.v[k];
-          if (cop) cop[(size_t)cn.w * R + rr[k]] = cp;
+          if (cop) cop[(size_t)cn.w * R + rr[k]] = cp.v[k];
           if (obj) {
-            const float contrib = wc.v[k] * (1.f - 2.f * cp);
+            const float contrib = wc.v[k] * (1.f - 2.f * cp.v[k]);
             if (obj_s)
               atomicAdd(obj_s + rr[k], contrib);
             else
@@ -407,13 +411,22 @@ __global__ void __launch_bounds__(kChunkThreads, 1)
       // (3) one global update per slot and restart
       if (ADJ) {
         for (int i = warp; i < ns; i += W) {
-          const PK g = s_g[i * 32 + lane];
           const int lab = s_lab[i];
 #pragma unroll
           for (int k = 0; k < RPL; ++k) {
-            if (!ok[k] || g.v[k] == 0.f) continue;
-            const float gz = lab < d.n_bool ? 0.f : atom_dd_dz(d, lab - d.n_bool, R, rr[k], s_inv, b);
-            scatter_grad(d, lab, R, rr[k], g.v[k], gz, grad_a, grad_b);
+            const float g = s_g[(k * kChunkMaxSlots + i) * 32 + lane];
+            if (!ok[k] || g == 0.f) continue;
+            if (lab < d.n_bool) {
+              atomicAdd(grad_a + (size_t)lab * R + rr[k], g);
+            } else if (s_inv > 0.f) {
+              const int ia = lab - d.n_bool;
+              const float si = __ldg(d.atom_inv_norm + ia) * s_inv;
+              const float u = atom_z(d, ia, R, rr[k], b) * si;
+              const float gg = g * kTwoOverSqrtPi * __expf(-u * u) * si;  // dC/dz
+              const int k0 = __ldg(d.atom_ptr + ia), k1 = __ldg(d.atom_ptr + ia + 1);
+              for (int j = k0; j < k1; ++j)
+                atomicAdd(grad_b + (size_t)__ldg(d.atom_var + j) * R + rr[k], gg * __ldg(d.atom_coef + j));
+            }
           }
         }
         __syncthreads();
@@ -905,7 +918,7 @@ ChunkShape chunk_shape(const Compiled& C, int R) {
   ChunkShape s{R > 32 ? 2 : 1, 0, 0};
   if (!C.chunked_ok) return s;
   const int vcap = std::max(1, C.max_nodes);
-  const size_t per_warp = (size_t)vcap * 32 * 4 * s.rpl;
+  const size_t per_warp = (size_t)(vcap + 2) * 32 * 4 * s.rpl;
   const size_t fixed = chunk_fixed_bytes(s.rpl) + (R <= kMaxObjSmemR ? (size_t)R * 4 : 0);
   if (fixed + 4 * per_warp > kSmemMax) return s;
   s.warps = (int)std::min<size_t>(kChunkThreads / 32, (kSmemMax - fixed) / per_warp);

@@ -216,7 +216,9 @@ static bool build_diagram(int kind, int param, const int32_t* lits, int L, Diagr
 // then finely -- so that a chunk's constraints share variables.  A chunk then
 // takes constraints in that order until it would exceed kChunkMaxCons
 // constraints, kChunkMaxNodes nodes or kChunkMaxSlots distinct variables/atoms
-// ("slots").  Every node's label is rewritten to its chunk-local slot.  Returns
+// ("slots").  Every node's label is rewritten to its chunk-local slot, and a
+// child that is a terminal to the fixed row max_nodes (TRUE) or max_nodes + 1
+// (FALSE).  Returns
 // false if a single constraint does not fit a chunk (the warp-per-constraint
 // kernel then serves the instance).
 static bool build_chunks(const Problem& P, Compiled& C) {
@@ -263,6 +265,7 @@ static bool build_chunks(const Problem& P, Compiled& C) {
   });
   std::unordered_map<int, int> slot_of;
   int chunk_cons = 0, chunk_nodes = 0;
+  const int tnode = std::max(1, C.max_nodes);  // row of the TRUE terminal in the kernel's message array
   auto close_chunk = [&]() {
     C.chunk_con_ptr.push_back((int32_t)(C.ccon.size() / 4));
     C.chunk_node_ptr.push_back((int32_t)C.cnode_slot.size());
@@ -297,7 +300,12 @@ static bool build_chunks(const Problem& P, Compiled& C) {
         slot = it->second;
       }
       C.cnode_slot.push_back((uint32_t)slot);
-      C.cnode_hilo.push_back(C.node_hilo[v]);
+      // children: decision nodes keep their index; the TRUE / FALSE terminals become
+      // the fixed rows tnode / tnode + 1 after the largest diagram's nodes
+      auto child = [&](uint32_t x) {
+        return x < (uint32_t)V ? x : (x == (uint32_t)V ? (uint32_t)tnode : (uint32_t)tnode + 1);
+      };
+      C.cnode_hilo.push_back(child(C.node_hilo[v] & 0xffffu) | (child(C.node_hilo[v] >> 16) << 16));
     }
     if ((int)slot_of.size() > kChunkMaxSlots) return false;
     ++chunk_cons;

@@ -72,3 +72,26 @@ def test_objective_without_constraints():
     assert comp.info["n_obj_cons"] == 0
     obj, cop, ga, gb = gpu_adjoint(comp, R, 1.0, a, b, w)
     assert (obj == 0).all() and (ga == 0).all() and (gb == 0).all()
+
+
+def test_atom_probability_within_published_erfc_bound():
+    """The kernel's atom probability p = erfc(u)/2 uses Abramowitz & Stegun 7.1.26,
+    whose absolute error is at most 1.5e-7; with FP32 rounding the COP of a
+    one-atom constraint stays within 5e-7 of the exact Gaussian CDF over u in [-6, 6]."""
+    from scipy.special import erfc
+    B = W._Builder(0, 1)
+    B.con(W.OR, [W.lit(B.atom([0], [1], 0, W.LE))])
+    inst = B.freeze("erfc", np.array([-100.0]), np.array([100.0]), [], np.zeros(1), 1.0)
+    R = 1024
+    P, comp, _, _, _ = setup(inst, R, policy=OBJ.SOFT)
+    sigma = 1.0
+    u = np.linspace(-6, 6, R)
+    b = (u * np.sqrt(2.0) * sigma).astype(np.float32)[None, :]  # z = b, ||q|| = 1
+    w = np.ones((1, R), np.float32)
+    _, cop, _, gb = gpu_adjoint(comp, R, sigma, np.zeros((0, R), np.float32), b, w)
+    uu = b[0].astype(np.float64) / (np.sqrt(2.0) * sigma)
+    ref = 0.5 * erfc(uu)
+    assert np.abs(cop[0] - ref).max() <= 5e-7
+    # and the derivative is the exact one: dC/db = -2 dp/db = (2/sqrt(pi)) e^{-u^2} / (sqrt(2) sigma)
+    dref = 2.0 / np.sqrt(np.pi) * np.exp(-uu * uu) / (np.sqrt(2.0) * sigma)
+    assert np.abs(gb[0] - dref).max() <= 1e-6 * dref.max()
