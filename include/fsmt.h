@@ -202,6 +202,30 @@ fsmt_status fsmt_forward_plain(const fsmt_compiled* c, int32_t R, float sigma, c
 fsmt_status fsmt_adjoint_plain(const fsmt_compiled* c, int32_t R, float sigma, const float* w, const float* a,
                                const float* b, float* work, float* grad_a, float* grad_b, void* stream);
 
+/* Allocation-free form of the plain pass pair (the paper has no counterpart: this
+ * is a deployment convenience).  Some callers cannot call cudaMalloc at this
+ * point: programs that reserve all device memory at start-up and must keep a
+ * fixed footprint afterwards, and hosts whose device memory is owned by another
+ * allocator (for instance a framework's caching pool) that forbids allocations
+ * outside its own accounting.  For them this entry point runs fsmt_forward_plain
+ * and then fsmt_adjoint_plain with their work memory taken from a fixed 64 MiB
+ * array (16 Mi floats) that lives in the library's device image on every GPU
+ * that loads the library, until the process exits.  It calls no cudaMalloc,
+ * cudaFree or other allocating routine.  Inputs and outputs are as for the two
+ * plain calls (grad_a, grad_b overwritten; cop, obj may be NULL).
+ *  - Size limit: EINVAL, with a message, when fsmt_plain_work_floats(c, R) exceeds
+ *    16 Mi floats; nothing is launched then.
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - Every call on a device shares the one array and leaves its contents behind;
+ *    the passes write every value they later read, so no clearing is needed.
+ *    Calls that overlap on the GPU (other streams, other threads) race on the
+ *    array: serialise them.
+ * Errors as the plain calls. */
+fsmt_status fsmt_plain_noalloc(const fsmt_compiled* c, int32_t R, float sigma, const float* w, const float* a,
+                               const float* b, float* grad_a, float* grad_b, float* cop, float* obj, void* stream);
+
 /* ------------------------------------------------------------ PGD step --
  * fsmt_weight_sum: wsum[r] = sum over the constraints of C_sigma of w[c][r]
  * (device w[n_cons][R] in, device wsum[R] overwritten) -- alpha of Prop.

@@ -67,6 +67,7 @@ PROTOTYPES = {
     "fsmt_plain_work_floats": [P, i32, C.POINTER(i64)],
     "fsmt_forward_plain": [P, i32, f32, P, P, P, P, P, P, P],
     "fsmt_adjoint_plain": [P, i32, f32, P, P, P, P, P, P, P],
+    "fsmt_plain_noalloc": [P, i32, f32, P, P, P, P, P, P, P, P],
     "fsmt_weight_sum": [P, i32, P, P, P],
     "fsmt_pgd_step": [P, i32, f32, f32, i32, i32, P, P, P, P, P, P, P, P],
     "fsmt_round_check": [P, i32, P, P, P, P, P, P, P, f32, f32, i32, P],

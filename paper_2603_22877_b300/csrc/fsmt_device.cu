@@ -10,6 +10,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
+#include <string>
 
 #include "fsmt_internal.h"
 
@@ -1216,6 +1218,57 @@ fsmt_status fsmt_adjoint_plain(const fsmt_compiled* c, int32_t R, float sigma, c
     FSMT_CUDA(cudaGetLastError(), "plain adjoint launch");
   }
   return FSMT_OK;
+}
+
+// ------------------------------------------------ allocation-free variant --
+// Work memory of fsmt_plain_noalloc: a fixed array in the library's device image,
+// present on every GPU that loads the library until the process exits.  Host
+// code must not use the symbol as a pointer: its device address is looked up once
+// per device with cudaGetSymbolAddress.
+namespace {
+constexpr int64_t kNoAllocWorkFloats = int64_t(1) << 24;  // 16 Mi floats = 64 MiB
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+float* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+}  // namespace
+static __device__ __align__(256) float g_noalloc_work[kNoAllocWorkFloats];
+
+static fsmt_status noalloc_work_ptr(float** out) {
+  int dev = 0;
+  FSMT_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+  if (dev < 0 || dev >= kNoAllocMaxDevices) {
+    set_error("fsmt_plain_noalloc supports device ordinals below 64");
+    return FSMT_EINVAL;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    FSMT_CUDA(cudaGetSymbolAddress(&p, g_noalloc_work), "cudaGetSymbolAddress of the work array");
+    g_noalloc_ptr[dev] = static_cast<float*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return FSMT_OK;
+}
+
+fsmt_status fsmt_plain_noalloc(const fsmt_compiled* c, int32_t R, float sigma, const float* w, const float* a,
+                               const float* b, float* grad_a, float* grad_b, float* cop, float* obj, void* stream) {
+  fsmt_status s = check_ready(c, R);
+  if (s != FSMT_OK) return s;
+  int64_t need = 0;
+  s = fsmt_plain_work_floats(c, R, &need);
+  if (s != FSMT_OK) return s;
+  if (need > kNoAllocWorkFloats) {
+    set_error("fsmt_plain_noalloc: this instance needs " + std::to_string(need) +
+              " work floats at this R, more than the fixed array of " + std::to_string(kNoAllocWorkFloats) +
+              "; use fsmt_forward_plain / fsmt_adjoint_plain with a caller buffer, or fewer restarts");
+    return FSMT_EINVAL;
+  }
+  float* work = nullptr;
+  s = noalloc_work_ptr(&work);
+  if (s != FSMT_OK) return s;
+  s = fsmt_forward_plain(c, R, sigma, w, a, b, work, cop, obj, stream);
+  if (s != FSMT_OK) return s;
+  return fsmt_adjoint_plain(c, R, sigma, w, a, b, work, grad_a, grad_b, stream);
 }
 
 fsmt_status fsmt_weight_sum(const fsmt_compiled* c, int32_t R, const float* w, float* wsum, void* stream) {
