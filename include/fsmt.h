@@ -77,6 +77,8 @@ typedef struct {
   int64_t atom_nnz;      /* nonzero coefficients over all atoms */
   int32_t fused_ok;      /* 1 if the fused kernels accept this instance */
   int32_t n_chunks;      /* chunks of the chunked forward/adjoint kernel (0: warp-per-constraint kernel) */
+  int32_t jit_shapes;    /* diagram shapes given run-time generated code at fsmt_upload (0: none) */
+  int32_t reserved;
 } fsmt_info;
 
 /* ---------------------------------------------------------------- problem --

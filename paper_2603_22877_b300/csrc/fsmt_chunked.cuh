@@ -1,0 +1,321 @@
+// Device code of the chunked forward/adjoint kernel and the helpers it shares
+// with the other kernels.  Written to compile both ahead of time (nvcc, through
+// fsmt_device.cu) and at run time (NVRTC), where per-shape specialisations of the
+// diagram passes are generated from the compiled diagrams (fsmt_jit.cpp).
+#pragma once
+
+namespace fsmt {
+
+constexpr float kTwoOverSqrtPi = 1.1283791670955126f;
+constexpr float kInvSqrt2 = 0.70710678118654752f;
+constexpr int kMaxObjSmemR = 4096;
+constexpr int kChunkThreads = 512;  // 16 warps
+
+// stage parameter slots (device float[16])
+enum { P_SIGMA = 0, P_ETA, P_BSCALE, P_EPS, P_RHO, P_GAMMA, P_UPDATE_W, P_SWEEPS, P_POLISH, P_NORM };
+
+__device__ __forceinline__ float load_param(const float* prm, int slot, float fallback) {
+  return prm ? prm[slot] : fallback;
+}
+
+// ------------------------------------------------------- literal probability --
+// p = P[variable TRUE]; gz = dd/dz for atoms (0 for Booleans).  Eq. rounding and
+// Eq. sampling; sigma = 0 decides the atom exactly.
+__device__ __forceinline__ void literal_prob(const DevView& d, int lab, int R, int r, bool ok, float s_inv,
+                                             const float* __restrict__ a, const float* __restrict__ b, float& p,
+                                             float& gz) {
+  if (lab < d.n_bool) {
+    float av = ok ? __ldg(a + (size_t)lab * R + r) : 0.f;
+    p = 0.5f * (1.f - av);
+    gz = 0.f;
+    return;
+  }
+  const int i = lab - d.n_bool;
+  const int k0 = __ldg(d.atom_ptr + i), k1 = __ldg(d.atom_ptr + i + 1);
+  if (s_inv > 0.f) {
+    float z = -__ldg(d.atom_q0f + i);
+    for (int k = k0; k < k1; ++k) {
+      float bv = ok ? __ldg(b + (size_t)__ldg(d.atom_var + k) * R + r) : 0.f;
+      z = fmaf(__ldg(d.atom_coef + k), bv, z);
+    }
+    const float si = __ldg(d.atom_inv_norm + i) * s_inv;  // 1 / (sqrt(2) sigma ||q||)
+    const float u = z * si;
+    p = 0.5f * erfcf(u);
+    gz = kTwoOverSqrtPi * __expf(-u * u) * si;
+  } else {
+    Fixed320 acc;
+    acc.clear();
+    for (int k = k0; k < k1; ++k) {
+      float bv = ok ? __ldg(b + (size_t)__ldg(d.atom_var + k) * R + r) : 0.f;
+      uint32_t m;
+      int e;
+      bool neg;
+      float_parts(bv, m, e, neg);
+      if (m == 0) continue;
+      float c = __ldg(d.atom_coef + k);
+      bool cneg = c < 0.f;
+      acc.add((uint64_t)(cneg ? -c : c) * (uint64_t)m, e + 149, neg != cneg);
+    }
+    double q0 = __ldg(d.atom_q0d + i);
+    if (q0 != 0.0) acc.add((uint64_t)fabs(q0), 149, q0 > 0.0);
+    const int sg = acc.sign();
+    const bool truth = __ldg(d.atom_strict + i) ? sg < 0 : sg <= 0;
+    p = truth ? 1.f : 0.f;
+    gz = 0.f;
+  }
+}
+
+__device__ __forceinline__ void scatter_grad(const DevView& d, int lab, int R, int r, float g, float gz,
+                                             float* __restrict__ grad_a, float* __restrict__ grad_b) {
+  if (lab < d.n_bool) {
+    atomicAdd(grad_a + (size_t)lab * R + r, g);
+  } else {
+    const int i = lab - d.n_bool;
+    const float gg = g * gz;
+    if (gg != 0.f) {
+      const int k0 = __ldg(d.atom_ptr + i), k1 = __ldg(d.atom_ptr + i + 1);
+      for (int k = k0; k < k1; ++k)
+        atomicAdd(grad_b + (size_t)__ldg(d.atom_var + k) * R + r, gg * __ldg(d.atom_coef + k));
+    }
+  }
+}
+
+
+// -------------------------------------------------------- chunked kernel --
+// One CTA per chunk of constraints of C_sigma (grid-stride over chunks), looping
+// over restart tiles of 32*RPL restarts; each lane carries RPL restarts (lane,
+// lane+32, ...), so every global access of a warp is a contiguous 128-byte line.
+// Per tile:
+//  (1) every slot -- a Boolean or an atom used by the chunk -- gets its
+//      TRUE-probability p once (Eq. rounding / Eq. sampling);
+//  (2) each warp runs Alg. 3 then Alg. 4 on its constraints -- through a
+//      routine generated for the constraint's diagram shape when there is one
+//      (shape_dispatch), else the generic form below -- with p read from
+//      shared memory and the messages in the warp's rows: one row per decision
+//      node plus two fixed rows for the terminals (the compiler points terminal
+//      children there), so the passes have no branches -- the forward pass may
+//      push into the terminal rows, which are then set to 1 (TRUE) and 0 (FALSE)
+//      for the backward pass; COP_c = m_bu[root] (Lemma backward).  The
+//      backward pass adds w_c m_td[v] (m_bu[hi] - m_bu[lo]) to the slot's
+//      shared accumulator;
+//  (3) each slot's accumulated derivative reaches the global gradient once (for
+//      atoms through dd/db_j).
+template <int RPL>
+struct __align__(4 * RPL) Pack {
+  float v[RPL];
+};
+
+// erfc(x)/2 for the atom probability, by Abramowitz & Stegun 7.1.26 (Hastings):
+// erf(x) = 1 - (a1 t + ... + a5 t^5) e^{-x^2} + e(x), t = 1/(1 + 0.3275911 x),
+// |e(x)| <= 1.5e-7 for x >= 0; erfc(-x) = 2 - erfc(x).  `ex` is e^{-x^2}.
+__device__ __forceinline__ float half_erfc_as(float x, float ex) {
+  const float ax = fabsf(x);
+  const float t = __frcp_rn(fmaf(0.3275911f, ax, 1.f));
+  float poly = fmaf(t, 1.061405429f, -1.453152027f);
+  poly = fmaf(t, poly, 1.421413741f);
+  poly = fmaf(t, poly, -0.284496736f);
+  poly = fmaf(t, poly, 0.254829592f);
+  const float h = 0.5f * t * poly * ex;  // erfc(|x|) / 2
+  return x >= 0.f ? h : 1.f - h;
+}
+
+// z = q.b - q0 of atom i at restart r (normalised form)
+__device__ __forceinline__ float atom_z(const DevView& d, int i, int R, int r, const float* __restrict__ b) {
+  const int k0 = __ldg(d.atom_ptr + i), k1 = __ldg(d.atom_ptr + i + 1);
+  float z = -__ldg(d.atom_q0f + i);
+  for (int k = k0; k < k1; ++k) z = fmaf(__ldg(d.atom_coef + k), __ldg(b + (size_t)__ldg(d.atom_var + k) * R + r), z);
+  return z;
+}
+
+template <bool ADJ, int RPL>
+__device__ __forceinline__ bool shape_dispatch(int shape, const uint2* nd, const Pack<RPL>* s_p, float* s_g, int lane,
+                                               const Pack<RPL>& wc, Pack<RPL>& cp);
+
+template <bool ADJ, int RPL>
+__device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigma, const float* prm, int vcap,
+                                             const float* __restrict__ w, const float* __restrict__ a,
+                                             const float* __restrict__ b, float* __restrict__ grad_a,
+                                             float* __restrict__ grad_b, float* __restrict__ obj,
+                                             float* __restrict__ cop, const int* ctl) {
+  using PK = Pack<RPL>;
+  if (ctl && ctl[0] == 0) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
+  const int rows = vcap + 2;  // decision nodes, then TRUE (vcap) and FALSE (vcap + 1)
+  uint2* s_node = reinterpret_cast<uint2*>(smem);
+  int4* s_con = reinterpret_cast<int4*>(s_node + kChunkMaxNodes);
+  int* s_lab = reinterpret_cast<int*>(s_con + kChunkMaxCons);
+  PK* s_p = reinterpret_cast<PK*>(s_lab + kChunkMaxSlots);
+  float* s_g = reinterpret_cast<float*>(s_p + kChunkMaxSlots * 32);  // [RPL][slots][32]
+  PK* s_m = reinterpret_cast<PK*>(s_g + RPL * kChunkMaxSlots * 32) + warp * rows * 32 + lane;
+  float* obj_s = (R <= kMaxObjSmemR)
+                     ? reinterpret_cast<float*>(reinterpret_cast<PK*>(s_g + RPL * kChunkMaxSlots * 32) + W * rows * 32)
+                     : nullptr;
+  if (obj_s)
+    for (int r = threadIdx.x; r < R; r += blockDim.x) obj_s[r] = 0.f;
+  sigma = load_param(prm, P_SIGMA, sigma);
+  const float s_inv = sigma > 0.f ? kInvSqrt2 / sigma : 0.f;
+  const int n_tiles = (R + 32 * RPL - 1) / (32 * RPL);
+  for (int q = blockIdx.x; q < d.n_chunks; q += gridDim.x) {
+    const int c0 = __ldg(d.chunk_con_ptr + q), nc = __ldg(d.chunk_con_ptr + q + 1) - c0;
+    const int n0 = __ldg(d.chunk_node_ptr + q), nn = __ldg(d.chunk_node_ptr + q + 1) - n0;
+    const int l0 = __ldg(d.chunk_slot_ptr + q), ns = __ldg(d.chunk_slot_ptr + q + 1) - l0;
+    __syncthreads();  // the previous chunk is done with shared memory
+    for (int i = threadIdx.x; i < nn; i += blockDim.x) s_node[i] = d.cnodes[n0 + i];
+    for (int i = threadIdx.x; i < nc; i += blockDim.x) s_con[i] = d.ccon[c0 + i];
+    for (int i = threadIdx.x; i < ns; i += blockDim.x) s_lab[i] = __ldg(d.slot_label + l0 + i);
+    __syncthreads();
+    for (int t = 0; t < n_tiles; ++t) {
+      int rr[RPL];
+      bool ok[RPL];
+#pragma unroll
+      for (int k = 0; k < RPL; ++k) {
+        rr[k] = (t * RPL + k) * 32 + lane;
+        ok[k] = rr[k] < R;
+      }
+      // (1) slot probabilities, once per slot and restart
+      for (int i = warp; i < ns; i += W) {
+        const int lab = s_lab[i];
+        PK pp;
+        if (lab < d.n_bool) {
+#pragma unroll
+          for (int k = 0; k < RPL; ++k) pp.v[k] = ok[k] ? 0.5f * (1.f - __ldg(a + (size_t)lab * R + rr[k])) : 0.f;
+        } else if (s_inv > 0.f) {
+          const int ia = lab - d.n_bool;
+          const float si = __ldg(d.atom_inv_norm + ia) * s_inv;
+#pragma unroll
+          for (int k = 0; k < RPL; ++k) {
+            const float u = ok[k] ? atom_z(d, ia, R, rr[k], b) * si : 0.f;
+            pp.v[k] = half_erfc_as(u, __expf(-u * u));
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < RPL; ++k) {
+            float gz;
+            literal_prob(d, lab, R, rr[k], ok[k], 0.f, a, b, pp.v[k], gz);
+          }
+        }
+        s_p[i * 32 + lane] = pp;
+        if (ADJ)
+#pragma unroll
+          for (int k = 0; k < RPL; ++k) s_g[(k * kChunkMaxSlots + i) * 32 + lane] = 0.f;
+      }
+      __syncthreads();
+      // (2) Alg. 3 and Alg. 4, one warp per constraint
+      for (int c = warp; c < nc; c += W) {
+        const int4 cn = s_con[c];
+        const uint2* nd = s_node + cn.x;
+        const int V = cn.y & 0xffff;
+        const int shape = cn.y >> 16;
+        PK wc, cp;
+#pragma unroll
+        for (int k = 0; k < RPL; ++k) wc.v[k] = ok[k] ? __ldg(w + (size_t)cn.w * R + rr[k]) : 0.f;
+        if (shape == 0 || !shape_dispatch<ADJ, RPL>(shape, nd, s_p, s_g, lane, wc, cp)) {
+          PK zero, one;
+#pragma unroll
+          for (int k = 0; k < RPL; ++k) {
+            zero.v[k] = 0.f;
+            one.v[k] = 1.f;
+          }
+          if (ADJ && V > 0) {
+            s_m[0] = one;  // the root is node 0
+            for (int v = 1; v < V; ++v) s_m[v * 32] = zero;
+            for (int v = 0; v < V; ++v) {  // Alg. 3, topological order
+              const uint2 e = nd[v];
+              const int hi = (int)(e.y & 0xffffu) * 32, lo = (int)(e.y >> 16) * 32;
+              const PK p = s_p[(e.x & 0x7fffffffu) * 32 + lane];
+              const PK mv = s_m[v * 32];
+              PK mh = s_m[hi], ml = s_m[lo];
+#pragma unroll
+              for (int k = 0; k < RPL; ++k) {
+                mh.v[k] = fmaf(p.v[k], mv.v[k], mh.v[k]);
+                ml.v[k] = fmaf(-p.v[k], mv.v[k], ml.v[k] + mv.v[k]);
+              }
+              s_m[hi] = mh;
+              s_m[lo] = ml;
+            }
+          }
+          s_m[vcap * 32] = one;
+          s_m[(vcap + 1) * 32] = zero;
+          for (int v = V - 1; v >= 0; --v) {  // Alg. 4, reverse topological order
+            const uint2 e = nd[v];
+            const int slot = (int)(e.x & 0x7fffffffu);
+            const PK mh = s_m[(int)(e.y & 0xffffu) * 32], ml = s_m[(int)(e.y >> 16) * 32];
+            const PK p = s_p[slot * 32 + lane];
+            PK nb;
+            if (ADJ) {
+              const PK td = s_m[v * 32];
+              float* gs = s_g + slot * 32 + lane;
+#pragma unroll
+              for (int k = 0; k < RPL; ++k) {
+                const float diff = mh.v[k] - ml.v[k];
+                nb.v[k] = fmaf(p.v[k], diff, ml.v[k]);
+                const float g = wc.v[k] * td.v[k] * diff;
+                if (g != 0.f) atomicAdd(gs + k * kChunkMaxSlots * 32, g);
+              }
+            } else {
+#pragma unroll
+              for (int k = 0; k < RPL; ++k) nb.v[k] = fmaf(p.v[k], mh.v[k] - ml.v[k], ml.v[k]);
+            }
+            s_m[v * 32] = nb;
+          }
+          // COP = m_bu[root]; a constant diagram's root is a terminal row
+          cp = V > 0 ? s_m[0] : s_m[(cn.z == 0 ? vcap : vcap + 1) * 32];
+        }
+#pragma unroll
+        for (int k = 0; k < RPL; ++k) {
+          if (!ok[k]) continue;
+          if (cop) cop[(size_t)cn.w * R + rr[k]] = cp.v[k];
+          if (obj) {
+            const float contrib = wc.v[k] * (1.f - 2.f * cp.v[k]);
+            if (obj_s)
+              atomicAdd(obj_s + rr[k], contrib);
+            else
+              atomicAdd(obj + rr[k], contrib);
+          }
+        }
+      }
+      __syncthreads();
+      // (3) one global update per slot and restart
+      if (ADJ) {
+        for (int i = warp; i < ns; i += W) {
+          const int lab = s_lab[i];
+#pragma unroll
+          for (int k = 0; k < RPL; ++k) {
+            const float g = s_g[(k * kChunkMaxSlots + i) * 32 + lane];
+            if (!ok[k] || g == 0.f) continue;
+            if (lab < d.n_bool) {
+              atomicAdd(grad_a + (size_t)lab * R + rr[k], g);
+            } else if (s_inv > 0.f) {
+              const int ia = lab - d.n_bool;
+              const float si = __ldg(d.atom_inv_norm + ia) * s_inv;
+              const float u = atom_z(d, ia, R, rr[k], b) * si;
+              const float gg = g * kTwoOverSqrtPi * __expf(-u * u) * si;  // dC/dz
+              const int k0 = __ldg(d.atom_ptr + ia), k1 = __ldg(d.atom_ptr + ia + 1);
+              for (int j = k0; j < k1; ++j)
+                atomicAdd(grad_b + (size_t)__ldg(d.atom_var + j) * R + rr[k], gg * __ldg(d.atom_coef + j));
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+  }
+  if (obj_s && obj) {
+    __syncthreads();
+    for (int r = threadIdx.x; r < R; r += blockDim.x)
+      if (obj_s[r] != 0.f) atomicAdd(obj + r, obj_s[r]);
+  }
+}
+
+
+#ifndef FSMT_JIT_SHAPES
+// Ahead-of-time build: no generated routines, every constraint takes the generic path.
+template <bool ADJ, int RPL>
+__device__ __forceinline__ bool shape_dispatch(int, const uint2*, const Pack<RPL>*, float*, int, const Pack<RPL>&,
+                                               Pack<RPL>&) {
+  return false;
+}
+#endif
+
+}  // namespace fsmt

@@ -266,6 +266,16 @@ static bool build_chunks(const Problem& P, Compiled& C) {
   std::unordered_map<int, int> slot_of;
   int chunk_cons = 0, chunk_nodes = 0;
   const int tnode = std::max(1, C.max_nodes);  // row of the TRUE terminal in the kernel's message array
+  // diagram shapes in literal space: a node testing a negated literal has its
+  // children swapped, so diagrams of one kind and size share a shape whatever
+  // the polarities; key = V then (hi, lo) per node, terminals V (TRUE), V+1 (FALSE)
+  C.shape_ptr.assign(1, 0);
+  C.shape_hi.clear();
+  C.shape_lo.clear();
+  C.shape_nodes.clear();
+  std::unordered_map<std::string, int> shape_of;
+  std::vector<int> con_shape;  // per constraint in chunk order
+  std::unordered_map<int, bool> neg_of;
   auto close_chunk = [&]() {
     C.chunk_con_ptr.push_back((int32_t)(C.ccon.size() / 4));
     C.chunk_node_ptr.push_back((int32_t)C.cnode_slot.size());
@@ -288,6 +298,37 @@ static bool build_chunks(const Problem& P, Compiled& C) {
     C.ccon.push_back(V);
     C.ccon.push_back(C.con_root[s]);
     C.ccon.push_back(C.con_id[s]);
+    neg_of.clear();
+    {
+      const int cid = C.con_id[s];
+      for (int64_t t = P.con_ptr[cid]; t < P.con_ptr[cid + 1]; ++t)
+        neg_of[P.con_lits[t] >> 1] = (P.con_lits[t] & 1) != 0;
+    }
+    std::string key(reinterpret_cast<const char*>(&V), sizeof(V));
+    std::vector<uint16_t> shi(V), slo(V);
+    for (int v = b; v < b + V; ++v) {
+      const bool ng = neg_of[(int)C.node_label[v]];
+      uint16_t h = (uint16_t)(C.node_hilo[v] & 0xffffu), l = (uint16_t)(C.node_hilo[v] >> 16);
+      if (ng) std::swap(h, l);
+      shi[v - b] = h;
+      slo[v - b] = l;
+      key.append(reinterpret_cast<const char*>(&h), 2);
+      key.append(reinterpret_cast<const char*>(&l), 2);
+    }
+    auto sh = shape_of.find(key);
+    int sid;
+    if (sh == shape_of.end()) {
+      sid = (int)C.shape_nodes.size();
+      shape_of.emplace(key, sid);
+      C.shape_hi.insert(C.shape_hi.end(), shi.begin(), shi.end());
+      C.shape_lo.insert(C.shape_lo.end(), slo.begin(), slo.end());
+      C.shape_ptr.push_back((int32_t)C.shape_hi.size());
+      C.shape_nodes.push_back(0);
+    } else {
+      sid = sh->second;
+    }
+    C.shape_nodes[sid] += V;
+    con_shape.push_back(sid);
     for (int v = b; v < b + V; ++v) {
       const int lab = (int)C.node_label[v];
       auto it = slot_of.find(lab);
@@ -299,7 +340,7 @@ static bool build_chunks(const Problem& P, Compiled& C) {
       } else {
         slot = it->second;
       }
-      C.cnode_slot.push_back((uint32_t)slot);
+      C.cnode_slot.push_back((uint32_t)slot | (neg_of[lab] ? 0x80000000u : 0u));
       // children: decision nodes keep their index; the TRUE / FALSE terminals become
       // the fixed rows tnode / tnode + 1 after the largest diagram's nodes
       auto child = [&](uint32_t x) {
@@ -312,6 +353,22 @@ static bool build_chunks(const Problem& P, Compiled& C) {
     chunk_nodes += V;
   }
   if (chunk_cons > 0) close_chunk();
+  // the shapes worth a generated routine: the largest node counts, at most
+  // kMaxJitShapes, each of at most kMaxJitShapeNodes nodes; their constraints
+  // carry the shape's 1-based rank in the high half of their V field
+  std::vector<int> order(C.shape_nodes.size());
+  std::iota(order.begin(), order.end(), 0);
+  std::sort(order.begin(), order.end(), [&](int x, int y) { return C.shape_nodes[x] > C.shape_nodes[y]; });
+  C.jit_shape.clear();
+  std::vector<int> rank(C.shape_nodes.size(), 0);
+  for (int x : order) {
+    const int V = C.shape_ptr[x + 1] - C.shape_ptr[x];
+    if ((int)C.jit_shape.size() >= kMaxJitShapes) break;
+    if (V < 1 || V > kMaxJitShapeNodes) continue;
+    C.jit_shape.push_back(x);
+    rank[x] = (int)C.jit_shape.size();
+  }
+  for (size_t k = 0; k < con_shape.size(); ++k) C.ccon[4 * k + 1] |= rank[con_shape[k]] << 16;
   return true;
 }
 
@@ -845,6 +902,7 @@ fsmt_status fsmt_compiled_info(const fsmt_compiled* c, fsmt_info* out) {
   out->atom_nnz = (int64_t)C.atom_var.size();
   out->fused_ok = fsmt_fused_limit_ok(C);
   out->n_chunks = C.chunked_ok ? C.n_chunks : 0;
+  out->jit_shapes = C.jit_shapes;
   return FSMT_OK;
 }
 

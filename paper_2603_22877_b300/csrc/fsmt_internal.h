@@ -6,27 +6,14 @@
 #include <string>
 #include <vector>
 
-#include <vector_types.h>
-
 #include "../../include/fsmt.h"
-
-#ifdef __CUDACC__
-#define FSMT_HD __host__ __device__ __forceinline__
-#else
-#define FSMT_HD inline
-#endif
+#include "fsmt_devview.cuh"
 
 namespace fsmt {
 
-constexpr int kMaxNodesPerDiagram = 65533;  // hi/lo are 16-bit and V, V+1 are the terminals
-constexpr int kMaxCompVars = 32;            // reals per block coupled by half-spaces
-constexpr int kMaxCompHalfspaces = 64;      // half-spaces per block
-// chunks of the chunked forward/adjoint kernel
-constexpr int kChunkMaxCons = 64;    // constraints per chunk
-constexpr int kChunkMaxNodes = 2048; // decision nodes per chunk
-constexpr int kChunkMaxSlots = 192;  // distinct variables / atoms per chunk
-
 void set_error(const std::string& msg);
+struct Compiled;
+bool jit_build(Compiled& C);  // fsmt_jit.cpp
 
 struct Problem {
   int32_t n_bool = 0, n_real = 0;
@@ -42,45 +29,6 @@ struct Problem {
   std::vector<int32_t> con_lits;
   int32_t n_atoms() const { return (int32_t)atom_q0.size(); }
   int32_t n_cons() const { return (int32_t)con_kind.size(); }
-};
-
-// Everything the kernels read, as one POD passed by value.
-struct DevView {
-  int32_t n_bool, n_real, n_atoms, n_cons, n_obj;
-  const int32_t* con_ptr;   // [n_cons + 1] node offsets, schedule order
-  const int32_t* con_id;    // [n_cons] constraint id of each schedule slot
-  const uint8_t* con_root;  // [n_cons] root index (0, or V / V+1 if constant)
-  const uint2* nodes;       // {label, hi | lo << 16}
-  // atoms in normalised form  sum coef_j y_j - q0 (<= | <) 0
-  const int32_t* atom_ptr;  // [n_atoms + 1]
-  const int32_t* atom_var;
-  const float* atom_coef;       // exact integers (|q| < 2^24)
-  const float* atom_q0f;        // q0 rounded to FP32 (relaxation only)
-  const double* atom_q0d;       // q0 exact (|q0| < 2^53), for the exact check
-  const float* atom_inv_norm;   // 1 / ||q||_2
-  const uint8_t* atom_strict;
-  // projection
-  const float* lo;
-  const float* hi;
-  int32_t n_free;
-  const int32_t* free_var;      // reals that only have a box
-  int32_t n_comp;
-  const int32_t* comp_var_ptr;  // [n_comp + 1] into comp_var
-  const int32_t* comp_var;      // global real ids
-  const int32_t* comp_hs_ptr;   // [n_comp + 1] into half-space list
-  const int32_t* hs_ptr;        // [n_hs + 1] into hs_lvar / hs_coef
-  const int32_t* hs_lvar;       // local index of the real inside its block
-  const float* hs_coef;
-  const float* hs_q0;
-  const float* hs_inv_qq;       // 1 / ||q||^2
-  // chunked schedule of the constraints of C_sigma
-  int32_t n_chunks;
-  const int32_t* chunk_con_ptr;   // [n_chunks + 1] into ccon
-  const int4* ccon;               // {node offset in chunk, V, root, constraint id}
-  const int32_t* chunk_node_ptr;  // [n_chunks + 1] into cnodes
-  const uint2* cnodes;            // {slot, hi | lo << 16}
-  const int32_t* chunk_slot_ptr;  // [n_chunks + 1] into slot_label
-  const int32_t* slot_label;      // variable id (< n_bool) or n_bool + atom index
 };
 
 // Host-side compiled form (arrays mirror DevView).
@@ -105,7 +53,15 @@ struct Compiled {
   int32_t n_chunks = 0;
   std::vector<int32_t> chunk_con_ptr{0}, chunk_node_ptr{0}, chunk_slot_ptr{0}, slot_label;
   std::vector<int32_t> ccon;  // 4 ints per constraint
-  std::vector<uint32_t> cnode_slot, cnode_hilo;
+  std::vector<uint32_t> cnode_slot, cnode_hilo;  // slot | negated-literal bit 31; children
+  // diagram shapes in literal space (build_chunks) and those given generated code
+  std::vector<int32_t> shape_ptr{0};
+  std::vector<uint16_t> shape_hi, shape_lo;
+  std::vector<int64_t> shape_nodes;
+  std::vector<int32_t> jit_shape;  // shape index of generated routine k (rank k + 1)
+  // run-time compiled chunked kernels (fsmt_jit.cpp): [adjoint][restarts per lane - 1]
+  void* jit_kernel[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  int32_t jit_shapes = 0;
   // device side
   void* dev_block = nullptr;  // one allocation holding every device array
   DevView view{};
@@ -116,92 +72,6 @@ struct Compiled {
   uint64_t graph_key = 0;
   void* capture_stream = nullptr;  // used when the caller passes the legacy default stream
 };
-
-// Exact sign of  sum_t c_t * y_t - q0  where c_t are integers with |c_t| < 2^24
-// (given as exact floats), y_t are FP32 values and q0 an integer with
-// |q0| < 2^53 (given as an exact double).  Every term is an integer multiple of
-// 2^-149, so the sum is accumulated exactly in a 320-bit two's-complement fixed
-// point with that unit.  Returns -1, 0 or +1.
-struct Fixed320 {
-  uint64_t limb[5];
-  FSMT_HD void clear() {
-    for (int i = 0; i < 5; ++i) limb[i] = 0;
-  }
-  // adds (neg ? -1 : 1) * mag * 2^shift, mag < 2^63, shift < 256
-  FSMT_HD void add(uint64_t mag, int shift, bool neg) {
-    uint64_t part[5] = {0, 0, 0, 0, 0};
-    int w = shift >> 6, s = shift & 63;
-    part[w] = mag << s;
-    if (s && w + 1 < 5) part[w + 1] = mag >> (64 - s);
-    if (neg) {  // two's complement of part
-      uint64_t carry = 1;
-      for (int i = 0; i < 5; ++i) {
-        uint64_t v = ~part[i] + carry;
-        carry = (carry && v == 0) ? 1 : 0;
-        part[i] = v;
-      }
-    }
-    uint64_t carry = 0;
-    for (int i = 0; i < 5; ++i) {
-      uint64_t x = limb[i] + part[i];
-      uint64_t c1 = x < limb[i] ? 1 : 0;
-      uint64_t y = x + carry;
-      uint64_t c2 = y < x ? 1 : 0;
-      limb[i] = y;
-      carry = c1 | c2;
-    }
-  }
-  FSMT_HD int sign() const {
-    if (limb[4] >> 63) return -1;
-    for (int i = 0; i < 5; ++i)
-      if (limb[i]) return 1;
-    return 0;
-  }
-};
-
-// Splits a finite float into (integer mantissa m >= 0, exponent k) with
-// value = m * 2^k, k >= -149.
-FSMT_HD void float_parts(float y, uint32_t& m, int& k, bool& neg) {
-  union {
-    float f;
-    uint32_t u;
-  } v;
-  v.f = y;
-  neg = (v.u >> 31) != 0;
-  uint32_t e = (v.u >> 23) & 0xff;
-  uint32_t f = v.u & 0x7fffff;
-  if (e == 0) {
-    m = f;
-    k = -149;
-  } else {
-    m = f | 0x800000u;
-    k = (int)e - 150;
-  }
-}
-
-// sign(sum_t coef_t * y_t - q0) exactly; coef are exact integers stored as floats.
-FSMT_HD int exact_atom_sign(int nnz, const float* coef, const float* y, double q0) {
-  Fixed320 acc;
-  acc.clear();
-  for (int t = 0; t < nnz; ++t) {
-    uint32_t m;
-    int k;
-    bool neg;
-    float_parts(y[t], m, k, neg);
-    if (m == 0) continue;
-    float c = coef[t];
-    bool cneg = c < 0.f;
-    uint64_t cm = (uint64_t)(cneg ? -c : c);
-    acc.add(cm * (uint64_t)m, k + 149, neg != cneg);
-  }
-  if (q0 != 0.0) {
-    bool qneg = q0 < 0.0;
-    double aq = qneg ? -q0 : q0;
-    uint64_t iq = (uint64_t)aq;
-    acc.add(iq, 149, !qneg);
-  }
-  return acc.sign();
-}
 
 }  // namespace fsmt
 

@@ -95,3 +95,32 @@ def test_atom_probability_within_published_erfc_bound():
     # and the derivative is the exact one: dC/db = -2 dp/db = (2/sqrt(pi)) e^{-u^2} / (sqrt(2) sigma)
     dref = 2.0 / np.sqrt(np.pi) * np.exp(-uu * uu) / (np.sqrt(2.0) * sigma)
     assert np.abs(gb[0] - dref).max() <= 1e-6 * dref.max()
+
+
+@pytest.mark.parametrize("make,R", [(lambda: W.large_scheduling(1005, 16, 30, 6, 4, 5), 70),
+                                    (lambda: W.placement2d(1003, 20), 33), (lambda: W.tiny_random(1001), 64)])
+def test_specialised_and_generic_kernels_agree(make, R, monkeypatch):
+    """Diagram shapes get run-time generated routines at upload; with FSMT_NO_JIT the
+    ahead-of-time kernel runs every constraint through the generic path.  Both agree
+    with the oracle."""
+    from paper_2603_22877_b300.engine import Problem
+    inst = make()
+    P, comp, a, b, w = setup(inst, R)
+    assert comp.upload().info is not None
+    from paper_2603_22877_b300 import _lib as L
+    import ctypes as C
+    info = L.Info()
+    L.call("fsmt_compiled_info", comp.h, C.byref(info))
+    assert info.jit_shapes > 0
+    monkeypatch.setenv("FSMT_NO_JIT", "1")
+    comp2 = Problem.from_instance(inst).compile().upload()
+    L.call("fsmt_compiled_info", comp2.h, C.byref(info))
+    assert info.jit_shapes == 0
+    sigma = float(np.float32(inst.scale))
+    ref = OBJ.evaluate(inst, a.astype(np.float64), b.astype(np.float64), w.astype(np.float64), sigma)
+    oc = OBJ.objective_constraints(inst)
+    for c_ in (comp, comp2):
+        obj, cop, ga, gb = gpu_adjoint(c_, R, sigma, a, b, w)
+        assert np.abs(cop[oc] - ref[1][oc]).max() <= COP_TOL
+        assert_grad_close(ga, ref[2], "grad_a")
+        assert_grad_close(gb, ref[3], "grad_b")
