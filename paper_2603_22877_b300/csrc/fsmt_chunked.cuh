@@ -145,7 +145,12 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
   uint2* s_node = reinterpret_cast<uint2*>(smem);
   int4* s_con = reinterpret_cast<int4*>(s_node + kChunkMaxNodes);
   int* s_lab = reinterpret_cast<int*>(s_con + kChunkMaxCons);
-  PK* s_p = reinterpret_cast<PK*>(s_lab + kChunkMaxSlots);
+  int* s_meta = s_lab + kChunkMaxSlots;                            // atom slots: first term << 16 | count
+  float* s_q0 = reinterpret_cast<float*>(s_meta + kChunkMaxSlots);  // atom slots: q0
+  float* s_si = s_q0 + kChunkMaxSlots;                             // atom slots: 1 / (sqrt(2) sigma ||q||)
+  int* s_tvar = reinterpret_cast<int*>(s_si + kChunkMaxSlots);     // the chunk's atom terms
+  float* s_tcoef = reinterpret_cast<float*>(s_tvar + kChunkMaxTerms);
+  PK* s_p = reinterpret_cast<PK*>(s_tcoef + kChunkMaxTerms);
   float* s_g = reinterpret_cast<float*>(s_p + kChunkMaxSlots * 32);  // [RPL][slots][32]
   PK* s_m = reinterpret_cast<PK*>(s_g + RPL * kChunkMaxSlots * 32) + warp * rows * 32 + lane;
   float* obj_s = (R <= kMaxObjSmemR)
@@ -163,7 +168,20 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
     __syncthreads();  // the previous chunk is done with shared memory
     for (int i = threadIdx.x; i < nn; i += blockDim.x) s_node[i] = d.cnodes[n0 + i];
     for (int i = threadIdx.x; i < nc; i += blockDim.x) s_con[i] = d.ccon[c0 + i];
-    for (int i = threadIdx.x; i < ns; i += blockDim.x) s_lab[i] = __ldg(d.slot_label + l0 + i);
+    const int t0 = __ldg(d.chunk_term_ptr + q), nt = __ldg(d.chunk_term_ptr + q + 1) - t0;
+    for (int i = threadIdx.x; i < ns; i += blockDim.x) {
+      const int lab = __ldg(d.slot_label + l0 + i);
+      s_lab[i] = lab;
+      s_meta[i] = __ldg(d.slot_meta + l0 + i);
+      if (lab >= d.n_bool) {
+        s_q0[i] = __ldg(d.atom_q0f + lab - d.n_bool);
+        s_si[i] = __ldg(d.atom_inv_norm + lab - d.n_bool) * s_inv;
+      }
+    }
+    for (int i = threadIdx.x; i < nt; i += blockDim.x) {
+      s_tvar[i] = __ldg(d.term_var + t0 + i);
+      s_tcoef[i] = __ldg(d.term_coef + t0 + i);
+    }
     __syncthreads();
     for (int t = 0; t < n_tiles; ++t) {
       int rr[RPL];
@@ -181,11 +199,14 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
 #pragma unroll
           for (int k = 0; k < RPL; ++k) pp.v[k] = ok[k] ? 0.5f * (1.f - __ldg(a + (size_t)lab * R + rr[k])) : 0.f;
         } else if (s_inv > 0.f) {
-          const int ia = lab - d.n_bool;
-          const float si = __ldg(d.atom_inv_norm + ia) * s_inv;
+          const int meta = s_meta[i], tb = meta >> 16, tc = meta & 0xffff;
+          const float si = s_si[i];
 #pragma unroll
           for (int k = 0; k < RPL; ++k) {
-            const float u = ok[k] ? atom_z(d, ia, R, rr[k], b) * si : 0.f;
+            float z = -s_q0[i];
+            for (int j = 0; j < tc; ++j)
+              z = fmaf(s_tcoef[tb + j], ok[k] ? __ldg(b + (size_t)s_tvar[tb + j] * R + rr[k]) : 0.f, z);
+            const float u = z * si;
             pp.v[k] = half_erfc_as(u, __expf(-u * u));
           }
         } else {
@@ -202,6 +223,9 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
       }
       __syncthreads();
       // (2) Alg. 3 and Alg. 4, one warp per constraint
+      float objacc[RPL];
+#pragma unroll
+      for (int k = 0; k < RPL; ++k) objacc[k] = 0.f;
       for (int c = warp; c < nc; c += W) {
         const int4 cn = s_con[c];
         const uint2* nd = s_node + cn.x;
@@ -266,15 +290,13 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
         for (int k = 0; k < RPL; ++k) {
           if (!ok[k]) continue;
           if (cop) cop[(size_t)cn.w * R + rr[k]] = cp.v[k];
-          if (obj) {
-            const float contrib = wc.v[k] * (1.f - 2.f * cp.v[k]);
-            if (obj_s)
-              atomicAdd(obj_s + rr[k], contrib);
-            else
-              atomicAdd(obj + rr[k], contrib);
-          }
+          objacc[k] = fmaf(wc.v[k], 1.f - 2.f * cp.v[k], objacc[k]);
         }
       }
+      if (obj)
+#pragma unroll
+        for (int k = 0; k < RPL; ++k)
+          if (ok[k] && objacc[k] != 0.f) atomicAdd(obj_s ? obj_s + rr[k] : obj + rr[k], objacc[k]);
       __syncthreads();
       // (3) one global update per slot and restart
       if (ADJ) {
@@ -287,13 +309,14 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
             if (lab < d.n_bool) {
               atomicAdd(grad_a + (size_t)lab * R + rr[k], g);
             } else if (s_inv > 0.f) {
-              const int ia = lab - d.n_bool;
-              const float si = __ldg(d.atom_inv_norm + ia) * s_inv;
-              const float u = atom_z(d, ia, R, rr[k], b) * si;
+              const int meta = s_meta[i], tb = meta >> 16, tc = meta & 0xffff;
+              const float si = s_si[i];
+              float z = -s_q0[i];
+              for (int j = 0; j < tc; ++j) z = fmaf(s_tcoef[tb + j], __ldg(b + (size_t)s_tvar[tb + j] * R + rr[k]), z);
+              const float u = z * si;
               const float gg = g * kTwoOverSqrtPi * __expf(-u * u) * si;  // dC/dz
-              const int k0 = __ldg(d.atom_ptr + ia), k1 = __ldg(d.atom_ptr + ia + 1);
-              for (int j = k0; j < k1; ++j)
-                atomicAdd(grad_b + (size_t)__ldg(d.atom_var + j) * R + rr[k], gg * __ldg(d.atom_coef + j));
+              for (int j = 0; j < tc; ++j)
+                atomicAdd(grad_b + (size_t)s_tvar[tb + j] * R + rr[k], gg * s_tcoef[tb + j]);
             }
           }
         }

@@ -24,8 +24,8 @@ constexpr int kFusedThreads = 256;  // 8 warps
 constexpr int kSmemBudget = 112 * 1024;
 // shared memory of the chunked kernel without the per-warp message arrays
 inline size_t chunk_fixed_bytes(int rpl) {
-  return (size_t)kChunkMaxNodes * 8 + (size_t)kChunkMaxCons * 16 + (size_t)kChunkMaxSlots * 4 +
-         (size_t)kChunkMaxSlots * 32 * 4 * rpl * 2;
+  return (size_t)kChunkMaxNodes * 8 + (size_t)kChunkMaxCons * 16 + (size_t)kChunkMaxSlots * 4 * 4 +
+         (size_t)kChunkMaxTerms * 8 + (size_t)kChunkMaxSlots * 32 * 4 * rpl * 2;
 }
 constexpr size_t kSmemMax = 227 * 1024;
 
@@ -782,7 +782,9 @@ fsmt_status fsmt_upload(fsmt_compiled* cc, void* stream) {
   for (size_t i = 0; i < cnodes.size(); ++i) cnodes[i] = make_uint2(C.cnode_slot[i], C.cnode_hilo[i]);
   const size_t o_ccp = push_array(blob, C.chunk_con_ptr), o_ccon = push_array(blob, C.ccon),
                o_cnp = push_array(blob, C.chunk_node_ptr), o_cnodes = push_array(blob, cnodes),
-               o_csp = push_array(blob, C.chunk_slot_ptr), o_slab = push_array(blob, C.slot_label);
+               o_csp = push_array(blob, C.chunk_slot_ptr), o_slab = push_array(blob, C.slot_label),
+               o_smeta = push_array(blob, C.slot_meta), o_ctp = push_array(blob, C.chunk_term_ptr),
+               o_tvar = push_array(blob, C.term_var), o_tcoef = push_array(blob, C.term_coef);
   if (C.dev_block) {
     cudaFree(C.dev_block);
     C.dev_block = nullptr;
@@ -832,6 +834,10 @@ fsmt_status fsmt_upload(fsmt_compiled* cc, void* stream) {
   v.cnodes = (const uint2*)(base + o_cnodes);
   v.chunk_slot_ptr = (const int32_t*)(base + o_csp);
   v.slot_label = (const int32_t*)(base + o_slab);
+  v.slot_meta = (const int32_t*)(base + o_smeta);
+  v.chunk_term_ptr = (const int32_t*)(base + o_ctp);
+  v.term_var = (const int32_t*)(base + o_tvar);
+  v.term_coef = (const float*)(base + o_tcoef);
   FSMT_CUDA(cudaFuncSetAttribute(k_fused<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024),
             "smem attribute");
   FSMT_CUDA(cudaFuncSetAttribute(k_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024),

@@ -30,8 +30,9 @@ constexpr int kMaxCompVars = 32;            // reals per block coupled by half-s
 constexpr int kMaxCompHalfspaces = 64;      // half-spaces per block
 // chunks of the chunked forward/adjoint kernel
 constexpr int kChunkMaxCons = 64;    // constraints per chunk
-constexpr int kChunkMaxNodes = 2048; // decision nodes per chunk
+constexpr int kChunkMaxNodes = 1536; // decision nodes per chunk
 constexpr int kChunkMaxSlots = 192;  // distinct variables / atoms per chunk
+constexpr int kChunkMaxTerms = 768;  // nonzeros of the atoms of a chunk
 constexpr int kMaxJitShapes = 16;      // diagram shapes given generated code per instance
 constexpr int kMaxJitShapeNodes = 48;  // largest diagram given generated code
 
@@ -72,6 +73,10 @@ struct DevView {
   const uint2* cnodes;            // {slot, hi | lo << 16}
   const int32_t* chunk_slot_ptr;  // [n_chunks + 1] into slot_label
   const int32_t* slot_label;      // variable id (< n_bool) or n_bool + atom index
+  const int32_t* slot_meta;       // atom slots: (first term << 16) | term count, chunk-relative; else 0
+  const int32_t* chunk_term_ptr;  // [n_chunks + 1] into term_var / term_coef
+  const int32_t* term_var;        // real of each atom nonzero, chunk by chunk
+  const float* term_coef;         // its (normalised) coefficient
 };
 
 // Exact sign of  sum_t c_t * y_t - q0  where c_t are integers with |c_t| < 2^24

@@ -227,6 +227,10 @@ static bool build_chunks(const Problem& P, Compiled& C) {
   C.chunk_node_ptr.assign(1, 0);
   C.chunk_slot_ptr.assign(1, 0);
   C.slot_label.clear();
+  C.slot_meta.clear();
+  C.chunk_term_ptr.assign(1, 0);
+  C.term_var.clear();
+  C.term_coef.clear();
   C.ccon.clear();
   C.cnode_slot.clear();
   C.cnode_hilo.clear();
@@ -264,7 +268,8 @@ static bool build_chunks(const Problem& P, Compiled& C) {
     return x.s < y.s;
   });
   std::unordered_map<int, int> slot_of;
-  int chunk_cons = 0, chunk_nodes = 0;
+  int chunk_cons = 0, chunk_nodes = 0, chunk_terms = 0;
+  auto atom_terms = [&](int lab) { return lab < C.n_bool ? 0 : C.atom_ptr[lab - C.n_bool + 1] - C.atom_ptr[lab - C.n_bool]; };
   const int tnode = std::max(1, C.max_nodes);  // row of the TRUE terminal in the kernel's message array
   // diagram shapes in literal space: a node testing a negated literal has its
   // children swapped, so diagrams of one kind and size share a shape whatever
@@ -279,19 +284,37 @@ static bool build_chunks(const Problem& P, Compiled& C) {
   auto close_chunk = [&]() {
     C.chunk_con_ptr.push_back((int32_t)(C.ccon.size() / 4));
     C.chunk_node_ptr.push_back((int32_t)C.cnode_slot.size());
+    // the chunk's atom terms, in slot order
+    int tb = 0;
+    for (size_t k = C.chunk_slot_ptr.back(); k < C.slot_label.size(); ++k) {
+      const int lab = C.slot_label[k];
+      const int tc = atom_terms(lab);
+      C.slot_meta.push_back(tc ? ((tb << 16) | tc) : 0);
+      for (int j = 0; j < tc; ++j) {
+        const int e = C.atom_ptr[lab - C.n_bool] + j;
+        C.term_var.push_back(C.atom_var[e]);
+        C.term_coef.push_back(C.atom_coef[e]);
+      }
+      tb += tc;
+    }
+    C.chunk_term_ptr.push_back((int32_t)C.term_var.size());
     C.chunk_slot_ptr.push_back((int32_t)C.slot_label.size());
     ++C.n_chunks;
     slot_of.clear();
-    chunk_cons = chunk_nodes = 0;
+    chunk_cons = chunk_nodes = chunk_terms = 0;
   };
   for (const Key& k : keys) {
     const int s = k.s;
     const int b = C.con_ptr[s], V = C.con_ptr[s + 1] - b;
-    int new_slots = 0;
+    int new_slots = 0, new_terms = 0;
     for (int v = b; v < b + V; ++v)
-      if (!slot_of.count((int)C.node_label[v])) ++new_slots;  // may count a repeat twice: conservative
+      if (!slot_of.count((int)C.node_label[v])) {  // may count a repeat twice: conservative
+        ++new_slots;
+        new_terms += atom_terms((int)C.node_label[v]);
+      }
     if (chunk_cons > 0 && (chunk_cons + 1 > kChunkMaxCons || chunk_nodes + V > kChunkMaxNodes ||
-                           (int)slot_of.size() + new_slots > kChunkMaxSlots))
+                           (int)slot_of.size() + new_slots > kChunkMaxSlots ||
+                           chunk_terms + new_terms > kChunkMaxTerms))
       close_chunk();
     if (V > kChunkMaxNodes) return false;
     C.ccon.push_back(chunk_nodes);
@@ -337,6 +360,7 @@ static bool build_chunks(const Problem& P, Compiled& C) {
         slot = (int)slot_of.size();
         slot_of.emplace(lab, slot);
         C.slot_label.push_back(lab);
+        chunk_terms += atom_terms(lab);
       } else {
         slot = it->second;
       }
@@ -348,7 +372,7 @@ static bool build_chunks(const Problem& P, Compiled& C) {
       };
       C.cnode_hilo.push_back(child(C.node_hilo[v] & 0xffffu) | (child(C.node_hilo[v] >> 16) << 16));
     }
-    if ((int)slot_of.size() > kChunkMaxSlots) return false;
+    if ((int)slot_of.size() > kChunkMaxSlots || chunk_terms > kChunkMaxTerms) return false;
     ++chunk_cons;
     chunk_nodes += V;
   }
@@ -457,7 +481,6 @@ static fsmt_status compile(const Problem& P, int policy, Compiled& C) {
   }
   if (C.n_obj == 0) C.n_obj_nodes = 0;
   C.con_ptr[n_cons] = (int32_t)total;
-  C.chunked_ok = build_chunks(P, C);
   // atoms, normalised to  q.y - q0 (<= | <) 0
   const int K = C.n_atoms;
   C.atom_ptr.assign(K + 1, 0);
@@ -483,6 +506,7 @@ static fsmt_status compile(const Problem& P, int policy, Compiled& C) {
     C.atom_q0d[i] = (double)q0;
     C.atom_inv_norm[i] = (float)(1.0 / std::sqrt(nn));
   }
+  C.chunked_ok = build_chunks(P, C);
   // projection: box, single-variable unit atoms, half-spaces in constraint order
   C.lo.resize(C.n_real);
   C.hi.resize(C.n_real);
