@@ -226,7 +226,9 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
       float objacc[RPL];
 #pragma unroll
       for (int k = 0; k < RPL; ++k) objacc[k] = 0.f;
-      for (int c = warp; c < nc; c += W) {
+      // contiguous runs of the chunk's (locality-sorted) constraints per warp, so
+      // that fewer warps update the same slot
+      for (int c = warp * nc / W; c < (warp + 1) * nc / W; ++c) {
         const int4 cn = s_con[c];
         const uint2* nd = s_node + cn.x;
         const int V = cn.y & 0xffff;

@@ -277,6 +277,7 @@ static bool build_chunks(const Problem& P, Compiled& C) {
   C.shape_ptr.assign(1, 0);
   C.shape_hi.clear();
   C.shape_lo.clear();
+  C.shape_grp.clear();
   C.shape_nodes.clear();
   std::unordered_map<std::string, int> shape_of;
   std::vector<int> con_shape;  // per constraint in chunk order
@@ -328,15 +329,23 @@ static bool build_chunks(const Problem& P, Compiled& C) {
         neg_of[P.con_lits[t] >> 1] = (P.con_lits[t] & 1) != 0;
     }
     std::string key(reinterpret_cast<const char*>(&V), sizeof(V));
-    std::vector<uint16_t> shi(V), slo(V);
+    std::vector<uint16_t> shi(V), slo(V), sgrp(V);
     for (int v = b; v < b + V; ++v) {
       const bool ng = neg_of[(int)C.node_label[v]];
       uint16_t h = (uint16_t)(C.node_hilo[v] & 0xffffu), l = (uint16_t)(C.node_hilo[v] >> 16);
       if (ng) std::swap(h, l);
+      uint16_t g = (uint16_t)(v - b);  // first node of the constraint testing the same variable
+      for (int u = b; u < v; ++u)
+        if (C.node_label[u] == C.node_label[v]) {
+          g = (uint16_t)(u - b);
+          break;
+        }
       shi[v - b] = h;
       slo[v - b] = l;
+      sgrp[v - b] = g;
       key.append(reinterpret_cast<const char*>(&h), 2);
       key.append(reinterpret_cast<const char*>(&l), 2);
+      key.append(reinterpret_cast<const char*>(&g), 2);
     }
     auto sh = shape_of.find(key);
     int sid;
@@ -345,6 +354,7 @@ static bool build_chunks(const Problem& P, Compiled& C) {
       shape_of.emplace(key, sid);
       C.shape_hi.insert(C.shape_hi.end(), shi.begin(), shi.end());
       C.shape_lo.insert(C.shape_lo.end(), slo.begin(), slo.end());
+      C.shape_grp.insert(C.shape_grp.end(), sgrp.begin(), sgrp.end());
       C.shape_ptr.push_back((int32_t)C.shape_hi.size());
       C.shape_nodes.push_back(0);
     } else {

@@ -58,7 +58,7 @@ struct Compiled {
   std::vector<uint32_t> cnode_slot, cnode_hilo;  // slot | negated-literal bit 31; children
   // diagram shapes in literal space (build_chunks) and those given generated code
   std::vector<int32_t> shape_ptr{0};
-  std::vector<uint16_t> shape_hi, shape_lo;
+  std::vector<uint16_t> shape_hi, shape_lo, shape_grp;  // grp: first node testing the same variable
   std::vector<int64_t> shape_nodes;
   std::vector<int32_t> jit_shape;  // shape index of generated routine k (rank k + 1)
   // run-time compiled chunked kernels (fsmt_jit.cpp): [adjoint][restarts per lane - 1]

@@ -16,6 +16,7 @@
 #include <mutex>
 #include <sstream>
 #include <unordered_map>
+#include <vector>
 
 #include "fsmt_internal.h"
 #include "fsmt_jit_src.inc"  // kJitDevviewSrc, kJitChunkedSrc (generated by build.py)
@@ -57,14 +58,19 @@ Nvrtc& nvrtc() {
 
 // Alg. 3 / Alg. 4 for one shape, straight-line.  Node v tests literal l_v with
 // probability q_v (= p or 1 - p for a negated literal); its children (hi = l_v
-// true) are nodes, or V (TRUE) / V+1 (FALSE).
-std::string shape_routine(int rank, int V, const uint16_t* hi, const uint16_t* lo) {
+// true) are nodes, or V (TRUE) / V+1 (FALSE).  Nodes testing the same variable
+// (grp = the first of them) add their gradient terms in a register, and the
+// first of them -- the last one the reverse pass reaches -- issues the single
+// shared-memory update of the variable's slot.
+std::string shape_routine(int rank, int V, const uint16_t* hi, const uint16_t* lo, const uint16_t* grp) {
   std::ostringstream o;
   auto bu = [&](int c) -> std::string {  // m_bu of a child
     if (c == V) return "1.f";
     if (c == V + 1) return "0.f";
     return "b" + std::to_string(c);
   };
+  std::vector<int> members(V, 0);
+  for (int v = 0; v < V; ++v) ++members[grp[v]];
   o << "template <bool ADJ, int RPL>\n__device__ __forceinline__ void shape_" << rank
     << "(const uint2* __restrict__ nd, const Pack<RPL>* __restrict__ s_p, float* __restrict__ s_g, int lane,"
        " const Pack<RPL>& wc, Pack<RPL>& cp) {\n";
@@ -82,12 +88,20 @@ std::string shape_routine(int rank, int V, const uint16_t* hi, const uint16_t* l
     if (lo[v] < V) o << "      t" << lo[v] << " = fmaf(1.f - q" << v << ", t" << v << ", t" << lo[v] << ");\n";
   }
   o << "    }\n";
+  for (int v = 0; v < V; ++v)
+    if (grp[v] == v && members[v] > 1) o << "    float acc" << v << " = 0.f;\n";
   for (int v = V - 1; v >= 0; --v) {  // Alg. 4
     o << "    const float d" << v << " = " << bu(hi[v]) << " - " << bu(lo[v]) << ";\n";
     o << "    const float b" << v << " = fmaf(q" << v << ", d" << v << ", " << bu(lo[v]) << ");\n";
-    o << "    if (ADJ) {\n      const float g = wc.v[k] * t" << v << " * d" << v << ";\n"
-      << "      atomicAdd(s_g + (k * kChunkMaxSlots + (int)(r" << v << " & 0x7fffffffu)) * 32 + lane, (r" << v
-      << " >> 31) ? -g : g);\n    }\n";
+    o << "    if (ADJ) {\n      const float g = wc.v[k] * t" << v << " * d" << v << ";\n";
+    if (grp[v] != v) {
+      o << "      acc" << grp[v] << " += g;\n";
+    } else {
+      const std::string tot = members[v] > 1 ? "(g + acc" + std::to_string(v) + ")" : "g";
+      o << "      atomicAdd(s_g + (k * kChunkMaxSlots + (int)(r" << v << " & 0x7fffffffu)) * 32 + lane, (r" << v
+        << " >> 31) ? -" << tot << " : " << tot << ");\n";
+    }
+    o << "    }\n";
   }
   o << "    cp.v[k] = b0;\n  }\n}\n\n";
   return o.str();
@@ -99,7 +113,7 @@ std::string generated_source(const Compiled& C) {
   for (size_t k = 0; k < C.jit_shape.size(); ++k) {
     const int x = C.jit_shape[k];
     const int b = C.shape_ptr[x], V = C.shape_ptr[x + 1] - b;
-    o << shape_routine((int)k + 1, V, C.shape_hi.data() + b, C.shape_lo.data() + b);
+    o << shape_routine((int)k + 1, V, C.shape_hi.data() + b, C.shape_lo.data() + b, C.shape_grp.data() + b);
   }
   o << "template <bool ADJ, int RPL>\n__device__ __forceinline__ bool shape_dispatch(int shape, const uint2* nd,"
        " const Pack<RPL>* s_p, float* s_g, int lane, const Pack<RPL>& wc, Pack<RPL>& cp) {\n  switch (shape) {\n";
