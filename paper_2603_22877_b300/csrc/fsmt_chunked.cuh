@@ -9,7 +9,8 @@ namespace fsmt {
 constexpr float kTwoOverSqrtPi = 1.1283791670955126f;
 constexpr float kInvSqrt2 = 0.70710678118654752f;
 constexpr int kMaxObjSmemR = 4096;
-constexpr int kChunkThreads = 512;  // 16 warps
+constexpr int kChunkThreads = 512;       // 16 warps
+constexpr int kChunkThreadsWide = 1024;  // 32 warps, without the generic path
 
 // stage parameter slots (device float[16])
 enum { P_SIGMA = 0, P_ETA, P_BSCALE, P_EPS, P_RHO, P_GAMMA, P_UPDATE_W, P_SWEEPS, P_POLISH, P_NORM };
@@ -131,7 +132,9 @@ template <bool ADJ, int RPL>
 __device__ __forceinline__ bool shape_dispatch(int shape, const uint2* nd, const Pack<RPL>* s_p, float* s_g, int lane,
                                                const Pack<RPL>& wc, Pack<RPL>& cp);
 
-template <bool ADJ, int RPL>
+// GENERIC = false: every constraint has a generated routine, so the generic
+// path and its per-warp message rows are left out (more warps fit).
+template <bool ADJ, int RPL, bool GENERIC = true>
 __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigma, const float* prm, int vcap,
                                              const float* __restrict__ w, const float* __restrict__ a,
                                              const float* __restrict__ b, float* __restrict__ grad_a,
@@ -153,9 +156,9 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
   PK* s_p = reinterpret_cast<PK*>(s_tcoef + kChunkMaxTerms);
   float* s_g = reinterpret_cast<float*>(s_p + kChunkMaxSlots * 32);  // [RPL][slots][32]
   PK* s_m = reinterpret_cast<PK*>(s_g + RPL * kChunkMaxSlots * 32) + warp * rows * 32 + lane;
-  float* obj_s = (R <= kMaxObjSmemR)
-                     ? reinterpret_cast<float*>(reinterpret_cast<PK*>(s_g + RPL * kChunkMaxSlots * 32) + W * rows * 32)
-                     : nullptr;
+  float* obj_s = (R <= kMaxObjSmemR) ? reinterpret_cast<float*>(reinterpret_cast<PK*>(s_g + RPL * kChunkMaxSlots * 32) +
+                                                                (GENERIC ? W * rows * 32 : 0))
+                                     : nullptr;
   if (obj_s)
     for (int r = threadIdx.x; r < R; r += blockDim.x) obj_s[r] = 0.f;
   sigma = load_param(prm, P_SIGMA, sigma);
@@ -236,7 +239,7 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
         PK wc, cp;
 #pragma unroll
         for (int k = 0; k < RPL; ++k) wc.v[k] = ok[k] ? __ldg(w + (size_t)cn.w * R + rr[k]) : 0.f;
-        if (shape == 0 || !shape_dispatch<ADJ, RPL>(shape, nd, s_p, s_g, lane, wc, cp)) {
+        if ((shape == 0 || !shape_dispatch<ADJ, RPL>(shape, nd, s_p, s_g, lane, wc, cp)) && GENERIC) {
           PK zero, one;
 #pragma unroll
           for (int k = 0; k < RPL; ++k) {

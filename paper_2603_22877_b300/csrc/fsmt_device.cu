@@ -660,6 +660,16 @@ fsmt_status launch_fused(const Compiled& C, bool adj, int R, float sigma, const 
     int vcap = std::max(1, C.max_nodes);
     const int blocks = std::max(1, std::min(C.n_chunks, sm_count()));
     const dim3 g(blocks), t(cs.warps * 32);
+    void* wk = C.jit_wide[adj ? 1 : 0][cs.rpl - 1];
+    if (wk) {  // every constraint has a generated routine: 32 warps, no generic message rows
+      const size_t smem = chunk_fixed_bytes(cs.rpl) + (R <= kMaxObjSmemR ? (size_t)R * 4 : 0);
+      DevView view = C.view;
+      void* args[] = {&view, &R, &sigma, (void*)&prm, &vcap, (void*)&w, (void*)&a, (void*)&b,
+                      &ga, &gb, &obj, &cop, (void*)&ctl};
+      FSMT_CUDA(cudaLaunchKernel((const void*)wk, g, dim3(kChunkThreadsWide), args, smem, st),
+                "specialised kernel launch");
+      return FSMT_OK;
+    }
     void* jk = C.jit_kernel[adj ? 1 : 0][cs.rpl - 1];
     if (jk) {  // run-time specialised kernel
       DevView view = C.view;

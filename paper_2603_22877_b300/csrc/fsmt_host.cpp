@@ -402,7 +402,11 @@ static bool build_chunks(const Problem& P, Compiled& C) {
     C.jit_shape.push_back(x);
     rank[x] = (int)C.jit_shape.size();
   }
-  for (size_t k = 0; k < con_shape.size(); ++k) C.ccon[4 * k + 1] |= rank[con_shape[k]] << 16;
+  C.all_specialized = !con_shape.empty();
+  for (size_t k = 0; k < con_shape.size(); ++k) {
+    C.ccon[4 * k + 1] |= rank[con_shape[k]] << 16;
+    if (rank[con_shape[k]] == 0) C.all_specialized = false;
+  }
   return true;
 }
 

@@ -63,6 +63,8 @@ struct Compiled {
   std::vector<int32_t> jit_shape;  // shape index of generated routine k (rank k + 1)
   // run-time compiled chunked kernels (fsmt_jit.cpp): [adjoint][restarts per lane - 1]
   void* jit_kernel[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  void* jit_wide[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // no generic path: all_specialized only
+  bool all_specialized = false;  // every constraint of C_sigma has a generated routine
   int32_t jit_shapes = 0;
   // device side
   void* dev_block = nullptr;  // one allocation holding every device array

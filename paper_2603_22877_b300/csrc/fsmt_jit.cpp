@@ -74,25 +74,30 @@ std::string shape_routine(int rank, int V, const uint16_t* hi, const uint16_t* l
   o << "template <bool ADJ, int RPL>\n__device__ __forceinline__ void shape_" << rank
     << "(const uint2* __restrict__ nd, const Pack<RPL>* __restrict__ s_p, float* __restrict__ s_g, int lane,"
        " const Pack<RPL>& wc, Pack<RPL>& cp) {\n";
-  for (int v = 0; v < V; ++v) o << "  const unsigned r" << v << " = nd[" << v << "].x;\n";
-  for (int v = 0; v < V; ++v)
-    o << "  const Pack<RPL> p" << v << " = s_p[(r" << v << " & 0x7fffffffu) * 32 + lane];\n";
+  // the slot word and the literal probability are re-read from shared memory at
+  // each use (cheap, off the dependency chain) so that only messages stay live
+  auto q = [&](int v) {
+    return "lit_q(nd[" + std::to_string(v) + "].x, s_p, lane, k)";
+  };
   o << "#pragma unroll\n  for (int k = 0; k < RPL; ++k) {\n";
-  for (int v = 0; v < V; ++v)
-    o << "    const float q" << v << " = (r" << v << " >> 31) ? 1.f - p" << v << ".v[k] : p" << v << ".v[k];\n";
   o << "    float t0 = 1.f";
   for (int v = 1; v < V; ++v) o << ", t" << v << " = 0.f";
   o << ";\n    if (ADJ) {\n";
   for (int v = 0; v < V; ++v) {  // Alg. 3: push to non-terminal children
-    if (hi[v] < V) o << "      t" << hi[v] << " = fmaf(q" << v << ", t" << v << ", t" << hi[v] << ");\n";
-    if (lo[v] < V) o << "      t" << lo[v] << " = fmaf(1.f - q" << v << ", t" << v << ", t" << lo[v] << ");\n";
+    if (hi[v] >= V && lo[v] >= V) continue;
+    o << "      { const float q = " << q(v) << ";\n";
+    if (hi[v] < V) o << "        t" << hi[v] << " = fmaf(q, t" << v << ", t" << hi[v] << ");\n";
+    if (lo[v] < V) o << "        t" << lo[v] << " = fmaf(1.f - q, t" << v << ", t" << lo[v] << "); ";
+    o << "}\n";
   }
   o << "    }\n";
   for (int v = 0; v < V; ++v)
     if (grp[v] == v && members[v] > 1) o << "    float acc" << v << " = 0.f;\n";
   for (int v = V - 1; v >= 0; --v) {  // Alg. 4
+    o << "    const unsigned r" << v << " = nd[" << v << "].x;\n";
     o << "    const float d" << v << " = " << bu(hi[v]) << " - " << bu(lo[v]) << ";\n";
-    o << "    const float b" << v << " = fmaf(q" << v << ", d" << v << ", " << bu(lo[v]) << ");\n";
+    o << "    const float b" << v << " = fmaf(lit_q(r" << v << ", s_p, lane, k), d" << v << ", " << bu(lo[v])
+      << ");\n";
     o << "    if (ADJ) {\n      const float g = wc.v[k] * t" << v << " * d" << v << ";\n";
     if (grp[v] != v) {
       o << "      acc" << grp[v] << " += g;\n";
@@ -107,9 +112,16 @@ std::string shape_routine(int rank, int V, const uint16_t* hi, const uint16_t* l
   return o.str();
 }
 
+std::string kernel_name(int wide, int adj, int rpl) {
+  return std::string("fsmt_jit_") + (wide ? "wide_" : "") + (adj ? "adj_" : "fwd_") + std::to_string(rpl);
+}
+
 std::string generated_source(const Compiled& C) {
   std::ostringstream o;
   o << "#define FSMT_JIT_SHAPES 1\n" << kJitDevviewSrc << "\n" << kJitChunkedSrc << "\nnamespace fsmt {\n\n";
+  o << "// probability of the literal a node tests: p of its slot, or 1 - p when negated (bit 31)\n"
+       "template <int RPL>\n__device__ __forceinline__ float lit_q(unsigned r, const Pack<RPL>* __restrict__ s_p, int lane,"
+       " int k) {\n  const float p = s_p[(r & 0x7fffffffu) * 32 + lane].v[k];\n  return (r >> 31) ? 1.f - p : p;\n}\n\n";
   for (size_t k = 0; k < C.jit_shape.size(); ++k) {
     const int x = C.jit_shape[k];
     const int b = C.shape_ptr[x], V = C.shape_ptr[x + 1] - b;
@@ -120,20 +132,21 @@ std::string generated_source(const Compiled& C) {
   for (size_t k = 0; k < C.jit_shape.size(); ++k)
     o << "    case " << k + 1 << ": shape_" << k + 1 << "<ADJ, RPL>(nd, s_p, s_g, lane, wc, cp); return true;\n";
   o << "    default: return false;\n  }\n}\n\n}  // namespace fsmt\n\n";
-  const char* names[2][2] = {{"fsmt_jit_fwd_1", "fsmt_jit_fwd_2"}, {"fsmt_jit_adj_1", "fsmt_jit_adj_2"}};
-  for (int adj = 0; adj < 2; ++adj)
-    for (int rpl = 1; rpl <= 2; ++rpl)
-      o << "extern \"C\" __global__ void __launch_bounds__(fsmt::kChunkThreads, 1) " << names[adj][rpl - 1]
-        << "(fsmt::DevView d, int R, float sigma, const float* prm, int vcap, const float* __restrict__ w,"
-           " const float* __restrict__ a, const float* __restrict__ b, float* __restrict__ grad_a,"
-           " float* __restrict__ grad_b, float* __restrict__ obj, float* __restrict__ cop, const int* ctl) {\n"
-        << "  fsmt::chunked_body<" << (adj ? "true" : "false") << ", " << rpl
-        << ">(d, R, sigma, prm, vcap, w, a, b, grad_a, grad_b, obj, cop, ctl);\n}\n";
+  for (int wide = 0; wide < 2; ++wide)
+    for (int adj = 0; adj < 2; ++adj)
+      for (int rpl = 1; rpl <= 2; ++rpl)
+        o << "extern \"C\" __global__ void __launch_bounds__(" << (wide ? "fsmt::kChunkThreadsWide" : "fsmt::kChunkThreads")
+          << ", 1) " << kernel_name(wide, adj, rpl)
+          << "(fsmt::DevView d, int R, float sigma, const float* prm, int vcap, const float* __restrict__ w,"
+             " const float* __restrict__ a, const float* __restrict__ b, float* __restrict__ grad_a,"
+             " float* __restrict__ grad_b, float* __restrict__ obj, float* __restrict__ cop, const int* ctl) {\n"
+          << "  fsmt::chunked_body<" << (adj ? "true" : "false") << ", " << rpl << ", " << (wide ? "false" : "true")
+          << ">(d, R, sigma, prm, vcap, w, a, b, grad_a, grad_b, obj, cop, ctl);\n}\n";
   return o.str();
 }
 
 struct Module {
-  void* kernel[2][2];
+  void* kernel[2][2][2];  // [wide][adjoint][restarts per lane - 1]
 };
 std::mutex g_mutex;
 std::unordered_map<std::string, Module> g_modules;  // by source text; kept for the process lifetime
@@ -187,20 +200,23 @@ bool jit_build(Compiled& C) {
       return false;
     }
     Module m{};
-    const char* names[2][2] = {{"fsmt_jit_fwd_1", "fsmt_jit_fwd_2"}, {"fsmt_jit_adj_1", "fsmt_jit_adj_2"}};
-    for (int adj = 0; adj < 2; ++adj)
-      for (int r = 0; r < 2; ++r) {
-        cudaKernel_t k;
-        if (cudaLibraryGetKernel(&k, lib, names[adj][r]) != cudaSuccess) return false;
-        if (cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
-            cudaSuccess)
-          return false;
-        m.kernel[adj][r] = (void*)k;
-      }
+    for (int wide = 0; wide < 2; ++wide)
+      for (int adj = 0; adj < 2; ++adj)
+        for (int r = 0; r < 2; ++r) {
+          cudaKernel_t k;
+          if (cudaLibraryGetKernel(&k, lib, kernel_name(wide, adj, r + 1).c_str()) != cudaSuccess) return false;
+          if (cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
+              cudaSuccess)
+            return false;
+          m.kernel[wide][adj][r] = (void*)k;
+        }
     it = g_modules.emplace(key, m).first;
   }
   for (int adj = 0; adj < 2; ++adj)
-    for (int r = 0; r < 2; ++r) C.jit_kernel[adj][r] = it->second.kernel[adj][r];
+    for (int r = 0; r < 2; ++r) {
+      C.jit_kernel[adj][r] = it->second.kernel[0][adj][r];
+      C.jit_wide[adj][r] = C.all_specialized ? it->second.kernel[1][adj][r] : nullptr;
+    }
   C.jit_shapes = (int32_t)C.jit_shape.size();
   return true;
 }
