@@ -155,10 +155,11 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
   float* s_tcoef = reinterpret_cast<float*>(s_tvar + kChunkMaxTerms);
   PK* s_p = reinterpret_cast<PK*>(s_tcoef + kChunkMaxTerms);
   float* s_g = reinterpret_cast<float*>(s_p + kChunkMaxSlots * 32);  // [RPL][slots][32]
-  PK* s_m = reinterpret_cast<PK*>(s_g + RPL * kChunkMaxSlots * 32) + warp * rows * 32 + lane;
-  float* obj_s = (R <= kMaxObjSmemR) ? reinterpret_cast<float*>(reinterpret_cast<PK*>(s_g + RPL * kChunkMaxSlots * 32) +
-                                                                (GENERIC ? W * rows * 32 : 0))
-                                     : nullptr;
+  float* s_gr = s_g + RPL * kChunkMaxSlots * 32;                      // [RPL][reals][32]: dC/db per chunk real
+  int* s_rid = reinterpret_cast<int*>(s_gr + RPL * kChunkMaxReals * 32);
+  PK* s_rows = reinterpret_cast<PK*>(s_rid + kChunkMaxReals);
+  PK* s_m = s_rows + warp * rows * 32 + lane;
+  float* obj_s = (R <= kMaxObjSmemR) ? reinterpret_cast<float*>(s_rows + (GENERIC ? W * rows * 32 : 0)) : nullptr;
   if (obj_s)
     for (int r = threadIdx.x; r < R; r += blockDim.x) obj_s[r] = 0.f;
   sigma = load_param(prm, P_SIGMA, sigma);
@@ -172,6 +173,8 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
     for (int i = threadIdx.x; i < nn; i += blockDim.x) s_node[i] = d.cnodes[n0 + i];
     for (int i = threadIdx.x; i < nc; i += blockDim.x) s_con[i] = d.ccon[c0 + i];
     const int t0 = __ldg(d.chunk_term_ptr + q), nt = __ldg(d.chunk_term_ptr + q + 1) - t0;
+    const int e0 = __ldg(d.chunk_real_ptr + q), nr = __ldg(d.chunk_real_ptr + q + 1) - e0;
+    for (int i = threadIdx.x; i < nr; i += blockDim.x) s_rid[i] = __ldg(d.real_id + e0 + i);
     for (int i = threadIdx.x; i < ns; i += blockDim.x) {
       const int lab = __ldg(d.slot_label + l0 + i);
       s_lab[i] = lab;
@@ -208,7 +211,7 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
           for (int k = 0; k < RPL; ++k) {
             float z = -s_q0[i];
             for (int j = 0; j < tc; ++j)
-              z = fmaf(s_tcoef[tb + j], ok[k] ? __ldg(b + (size_t)s_tvar[tb + j] * R + rr[k]) : 0.f, z);
+              z = fmaf(s_tcoef[tb + j], ok[k] ? __ldg(b + (size_t)s_rid[s_tvar[tb + j]] * R + rr[k]) : 0.f, z);
             const float u = z * si;
             pp.v[k] = half_erfc_as(u, __expf(-u * u));
           }
@@ -224,6 +227,10 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
 #pragma unroll
           for (int k = 0; k < RPL; ++k) s_g[(k * kChunkMaxSlots + i) * 32 + lane] = 0.f;
       }
+      if (ADJ)
+        for (int i = warp; i < nr; i += W)
+#pragma unroll
+          for (int k = 0; k < RPL; ++k) s_gr[(k * kChunkMaxReals + i) * 32 + lane] = 0.f;
       __syncthreads();
       // (2) Alg. 3 and Alg. 4, one warp per constraint
       float objacc[RPL];
@@ -313,18 +320,26 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
             if (!ok[k] || g == 0.f) continue;
             if (lab < d.n_bool) {
               atomicAdd(grad_a + (size_t)lab * R + rr[k], g);
-            } else if (s_inv > 0.f) {
+            } else if (s_inv > 0.f) {  // dC/dz through dd/db_j into the chunk's real accumulators
               const int meta = s_meta[i], tb = meta >> 16, tc = meta & 0xffff;
               const float si = s_si[i];
               float z = -s_q0[i];
-              for (int j = 0; j < tc; ++j) z = fmaf(s_tcoef[tb + j], __ldg(b + (size_t)s_tvar[tb + j] * R + rr[k]), z);
-              const float u = z * si;
-              const float gg = g * kTwoOverSqrtPi * __expf(-u * u) * si;  // dC/dz
               for (int j = 0; j < tc; ++j)
-                atomicAdd(grad_b + (size_t)s_tvar[tb + j] * R + rr[k], gg * s_tcoef[tb + j]);
+                z = fmaf(s_tcoef[tb + j], __ldg(b + (size_t)s_rid[s_tvar[tb + j]] * R + rr[k]), z);
+              const float u = z * si;
+              const float gg = g * kTwoOverSqrtPi * __expf(-u * u) * si;
+              for (int j = 0; j < tc; ++j)
+                atomicAdd(s_gr + (k * kChunkMaxReals + s_tvar[tb + j]) * 32 + lane, gg * s_tcoef[tb + j]);
             }
           }
         }
+        __syncthreads();
+        for (int i = warp; i < nr; i += W)  // one global update per chunk real and restart
+#pragma unroll
+          for (int k = 0; k < RPL; ++k) {
+            const float g = s_gr[(k * kChunkMaxReals + i) * 32 + lane];
+            if (ok[k] && g != 0.f) atomicAdd(grad_b + (size_t)s_rid[i] * R + rr[k], g);
+          }
         __syncthreads();
       }
     }

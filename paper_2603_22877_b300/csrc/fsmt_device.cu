@@ -25,7 +25,8 @@ constexpr int kSmemBudget = 112 * 1024;
 // shared memory of the chunked kernel without the per-warp message arrays
 inline size_t chunk_fixed_bytes(int rpl) {
   return (size_t)kChunkMaxNodes * 8 + (size_t)kChunkMaxCons * 16 + (size_t)kChunkMaxSlots * 4 * 4 +
-         (size_t)kChunkMaxTerms * 8 + (size_t)kChunkMaxSlots * 32 * 4 * rpl * 2;
+         (size_t)kChunkMaxTerms * 8 + (size_t)kChunkMaxReals * 4 + (size_t)kChunkMaxSlots * 32 * 4 * rpl * 2 +
+         (size_t)kChunkMaxReals * 32 * 4 * rpl;
 }
 constexpr size_t kSmemMax = 227 * 1024;
 
@@ -794,7 +795,8 @@ fsmt_status fsmt_upload(fsmt_compiled* cc, void* stream) {
                o_cnp = push_array(blob, C.chunk_node_ptr), o_cnodes = push_array(blob, cnodes),
                o_csp = push_array(blob, C.chunk_slot_ptr), o_slab = push_array(blob, C.slot_label),
                o_smeta = push_array(blob, C.slot_meta), o_ctp = push_array(blob, C.chunk_term_ptr),
-               o_tvar = push_array(blob, C.term_var), o_tcoef = push_array(blob, C.term_coef);
+               o_tvar = push_array(blob, C.term_var), o_tcoef = push_array(blob, C.term_coef),
+               o_crp = push_array(blob, C.chunk_real_ptr), o_rid = push_array(blob, C.real_id);
   if (C.dev_block) {
     cudaFree(C.dev_block);
     C.dev_block = nullptr;
@@ -848,6 +850,8 @@ fsmt_status fsmt_upload(fsmt_compiled* cc, void* stream) {
   v.chunk_term_ptr = (const int32_t*)(base + o_ctp);
   v.term_var = (const int32_t*)(base + o_tvar);
   v.term_coef = (const float*)(base + o_tcoef);
+  v.chunk_real_ptr = (const int32_t*)(base + o_crp);
+  v.real_id = (const int32_t*)(base + o_rid);
   FSMT_CUDA(cudaFuncSetAttribute(k_fused<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024),
             "smem attribute");
   FSMT_CUDA(cudaFuncSetAttribute(k_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024),

@@ -33,6 +33,7 @@ constexpr int kChunkMaxCons = 64;    // constraints per chunk
 constexpr int kChunkMaxNodes = 1536; // decision nodes per chunk
 constexpr int kChunkMaxSlots = 192;  // distinct variables / atoms per chunk
 constexpr int kChunkMaxTerms = 768;  // nonzeros of the atoms of a chunk
+constexpr int kChunkMaxReals = 64;   // distinct reals of the atoms of a chunk
 constexpr int kMaxJitShapes = 16;      // diagram shapes given generated code per instance
 constexpr int kMaxJitShapeNodes = 48;  // largest diagram given generated code
 
@@ -75,7 +76,9 @@ struct DevView {
   const int32_t* slot_label;      // variable id (< n_bool) or n_bool + atom index
   const int32_t* slot_meta;       // atom slots: (first term << 16) | term count, chunk-relative; else 0
   const int32_t* chunk_term_ptr;  // [n_chunks + 1] into term_var / term_coef
-  const int32_t* term_var;        // real of each atom nonzero, chunk by chunk
+  const int32_t* term_var;        // chunk-local real of each atom nonzero, chunk by chunk
+  const int32_t* chunk_real_ptr;  // [n_chunks + 1] into real_id
+  const int32_t* real_id;         // the chunk's reals
   const float* term_coef;         // its (normalised) coefficient
 };
 

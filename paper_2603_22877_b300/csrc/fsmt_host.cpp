@@ -230,6 +230,8 @@ static bool build_chunks(const Problem& P, Compiled& C) {
   C.slot_meta.clear();
   C.chunk_term_ptr.assign(1, 0);
   C.term_var.clear();
+  C.chunk_real_ptr.assign(1, 0);
+  C.real_id.clear();
   C.term_coef.clear();
   C.ccon.clear();
   C.cnode_slot.clear();
@@ -270,6 +272,17 @@ static bool build_chunks(const Problem& P, Compiled& C) {
   std::unordered_map<int, int> slot_of;
   int chunk_cons = 0, chunk_nodes = 0, chunk_terms = 0;
   auto atom_terms = [&](int lab) { return lab < C.n_bool ? 0 : C.atom_ptr[lab - C.n_bool + 1] - C.atom_ptr[lab - C.n_bool]; };
+  std::unordered_map<int, int> real_of;  // the open chunk's reals
+  auto new_reals = [&](int s) {  // reals constraint s would add to the open chunk (may over-count repeats)
+    int n = 0;
+    for (int v = C.con_ptr[s]; v < C.con_ptr[s + 1]; ++v) {
+      const int lab = (int)C.node_label[v];
+      if (lab < C.n_bool || slot_of.count(lab)) continue;
+      for (int e = C.atom_ptr[lab - C.n_bool]; e < C.atom_ptr[lab - C.n_bool + 1]; ++e)
+        if (!real_of.count(C.atom_var[e])) ++n;
+    }
+    return n;
+  };
   const int tnode = std::max(1, C.max_nodes);  // row of the TRUE terminal in the kernel's message array
   // diagram shapes in literal space: a node testing a negated literal has its
   // children swapped, so diagrams of one kind and size share a shape whatever
@@ -293,13 +306,18 @@ static bool build_chunks(const Problem& P, Compiled& C) {
       C.slot_meta.push_back(tc ? ((tb << 16) | tc) : 0);
       for (int j = 0; j < tc; ++j) {
         const int e = C.atom_ptr[lab - C.n_bool] + j;
-        C.term_var.push_back(C.atom_var[e]);
+        C.term_var.push_back(real_of.at(C.atom_var[e]));
         C.term_coef.push_back(C.atom_coef[e]);
       }
       tb += tc;
     }
     C.chunk_term_ptr.push_back((int32_t)C.term_var.size());
     C.chunk_slot_ptr.push_back((int32_t)C.slot_label.size());
+    std::vector<int> reals(real_of.size());
+    for (auto& kv : real_of) reals[kv.second] = kv.first;
+    C.real_id.insert(C.real_id.end(), reals.begin(), reals.end());
+    C.chunk_real_ptr.push_back((int32_t)C.real_id.size());
+    real_of.clear();
     ++C.n_chunks;
     slot_of.clear();
     chunk_cons = chunk_nodes = chunk_terms = 0;
@@ -315,7 +333,8 @@ static bool build_chunks(const Problem& P, Compiled& C) {
       }
     if (chunk_cons > 0 && (chunk_cons + 1 > kChunkMaxCons || chunk_nodes + V > kChunkMaxNodes ||
                            (int)slot_of.size() + new_slots > kChunkMaxSlots ||
-                           chunk_terms + new_terms > kChunkMaxTerms))
+                           chunk_terms + new_terms > kChunkMaxTerms ||
+                           (int)real_of.size() + new_reals(s) > kChunkMaxReals))
       close_chunk();
     if (V > kChunkMaxNodes) return false;
     C.ccon.push_back(chunk_nodes);
@@ -371,6 +390,12 @@ static bool build_chunks(const Problem& P, Compiled& C) {
         slot_of.emplace(lab, slot);
         C.slot_label.push_back(lab);
         chunk_terms += atom_terms(lab);
+        if (lab >= C.n_bool)
+          for (int e = C.atom_ptr[lab - C.n_bool]; e < C.atom_ptr[lab - C.n_bool + 1]; ++e)
+            if (!real_of.count(C.atom_var[e])) {
+              const int nr = (int)real_of.size();
+              real_of.emplace(C.atom_var[e], nr);
+            }
       } else {
         slot = it->second;
       }
@@ -382,7 +407,8 @@ static bool build_chunks(const Problem& P, Compiled& C) {
       };
       C.cnode_hilo.push_back(child(C.node_hilo[v] & 0xffffu) | (child(C.node_hilo[v] >> 16) << 16));
     }
-    if ((int)slot_of.size() > kChunkMaxSlots || chunk_terms > kChunkMaxTerms) return false;
+    if ((int)slot_of.size() > kChunkMaxSlots || chunk_terms > kChunkMaxTerms || (int)real_of.size() > kChunkMaxReals)
+      return false;
     ++chunk_cons;
     chunk_nodes += V;
   }

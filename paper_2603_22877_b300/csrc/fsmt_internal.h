@@ -52,7 +52,7 @@ struct Compiled {
   bool chunked_ok = false;
   int32_t n_chunks = 0;
   std::vector<int32_t> chunk_con_ptr{0}, chunk_node_ptr{0}, chunk_slot_ptr{0}, slot_label;
-  std::vector<int32_t> slot_meta, chunk_term_ptr{0}, term_var;
+  std::vector<int32_t> slot_meta, chunk_term_ptr{0}, term_var, chunk_real_ptr{0}, real_id;
   std::vector<float> term_coef;
   std::vector<int32_t> ccon;  // 4 ints per constraint
   std::vector<uint32_t> cnode_slot, cnode_hilo;  // slot | negated-literal bit 31; children
