@@ -153,11 +153,11 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
   float* s_si = s_q0 + kChunkMaxSlots;                             // atom slots: 1 / (sqrt(2) sigma ||q||)
   int* s_tvar = reinterpret_cast<int*>(s_si + kChunkMaxSlots);     // the chunk's atom terms
   float* s_tcoef = reinterpret_cast<float*>(s_tvar + kChunkMaxTerms);
-  PK* s_p = reinterpret_cast<PK*>(s_tcoef + kChunkMaxTerms);
-  float* s_g = reinterpret_cast<float*>(s_p + kChunkMaxSlots * 32);  // [RPL][slots][32]
-  float* s_gr = s_g + RPL * kChunkMaxSlots * 32;                      // [RPL][reals][32]: dC/db per chunk real
-  int* s_rid = reinterpret_cast<int*>(s_gr + RPL * kChunkMaxReals * 32);
-  PK* s_rows = reinterpret_cast<PK*>(s_rid + kChunkMaxReals);
+  int* s_rid = reinterpret_cast<int*>(s_tcoef + kChunkMaxTerms);  // the chunk's reals
+  const int cap = d.chunk_slot_cap;
+  PK* s_p = reinterpret_cast<PK*>(s_rid + kChunkMaxReals);   // [slot][32]
+  float* s_g = reinterpret_cast<float*>(s_p + cap * 32);     // [slot][RPL][32]
+  PK* s_rows = reinterpret_cast<PK*>(s_g + cap * RPL * 32);
   PK* s_m = s_rows + warp * rows * 32 + lane;
   float* obj_s = (R <= kMaxObjSmemR) ? reinterpret_cast<float*>(s_rows + (GENERIC ? W * rows * 32 : 0)) : nullptr;
   if (obj_s)
@@ -189,6 +189,57 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
       s_tcoef[i] = __ldg(d.term_coef + t0 + i);
     }
     __syncthreads();
+    // One pass over the slots: the gradient of tile tf leaves for global memory
+    // (one update per slot and restart; an atom's through dd/dz and the chain rule
+    // into its reals), and the slots get the TRUE-probability p of tile tp.
+    auto slot_pass = [&](int tf, int tp) {
+      for (int i = warp; i < ns; i += W) {
+        const int lab = s_lab[i];
+        const bool is_atom = lab >= d.n_bool;
+        const int meta = s_meta[i], tb = meta >> 16, tc = meta & 0xffff;
+        if (ADJ && tf >= 0) {
+#pragma unroll
+          for (int k = 0; k < RPL; ++k) {
+            const int r = (tf * RPL + k) * 32 + lane;
+            const float g = s_g[(i * RPL + k) * 32 + lane];
+            if (r >= R || g == 0.f) continue;
+            if (!is_atom) {
+              atomicAdd(grad_a + (size_t)lab * R + r, g);
+            } else if (s_inv > 0.f) {
+              float z = -s_q0[i];
+              for (int j = 0; j < tc; ++j) z = fmaf(s_tcoef[tb + j], __ldg(b + (size_t)s_rid[s_tvar[tb + j]] * R + r), z);
+              const float si = s_si[i], u = z * si;
+              const float gg = g * kTwoOverSqrtPi * __expf(-u * u) * si;  // dC/dz
+              for (int j = 0; j < tc; ++j)
+                atomicAdd(grad_b + (size_t)s_rid[s_tvar[tb + j]] * R + r, gg * s_tcoef[tb + j]);
+            }
+          }
+        }
+        if (tp < n_tiles) {
+          PK pp;
+#pragma unroll
+          for (int k = 0; k < RPL; ++k) {
+            const int r = (tp * RPL + k) * 32 + lane;
+            const bool ok = r < R;
+            if (!is_atom) {
+              pp.v[k] = ok ? 0.5f * (1.f - __ldg(a + (size_t)lab * R + r)) : 0.f;
+            } else if (s_inv > 0.f) {
+              float z = -s_q0[i];
+              for (int j = 0; j < tc; ++j)
+                z = fmaf(s_tcoef[tb + j], ok ? __ldg(b + (size_t)s_rid[s_tvar[tb + j]] * R + r) : 0.f, z);
+              const float u = z * s_si[i];
+              pp.v[k] = half_erfc_as(u, __expf(-u * u));
+            } else {
+              float gz;
+              literal_prob(d, lab, R, r, ok, 0.f, a, b, pp.v[k], gz);
+            }
+            if (ADJ) s_g[(i * RPL + k) * 32 + lane] = 0.f;
+          }
+          s_p[i * 32 + lane] = pp;
+        }
+      }
+    };
+    slot_pass(-1, 0);
     for (int t = 0; t < n_tiles; ++t) {
       int rr[RPL];
       bool ok[RPL];
@@ -197,47 +248,11 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
         rr[k] = (t * RPL + k) * 32 + lane;
         ok[k] = rr[k] < R;
       }
-      // (1) slot probabilities, once per slot and restart
-      for (int i = warp; i < ns; i += W) {
-        const int lab = s_lab[i];
-        PK pp;
-        if (lab < d.n_bool) {
-#pragma unroll
-          for (int k = 0; k < RPL; ++k) pp.v[k] = ok[k] ? 0.5f * (1.f - __ldg(a + (size_t)lab * R + rr[k])) : 0.f;
-        } else if (s_inv > 0.f) {
-          const int meta = s_meta[i], tb = meta >> 16, tc = meta & 0xffff;
-          const float si = s_si[i];
-#pragma unroll
-          for (int k = 0; k < RPL; ++k) {
-            float z = -s_q0[i];
-            for (int j = 0; j < tc; ++j)
-              z = fmaf(s_tcoef[tb + j], ok[k] ? __ldg(b + (size_t)s_rid[s_tvar[tb + j]] * R + rr[k]) : 0.f, z);
-            const float u = z * si;
-            pp.v[k] = half_erfc_as(u, __expf(-u * u));
-          }
-        } else {
-#pragma unroll
-          for (int k = 0; k < RPL; ++k) {
-            float gz;
-            literal_prob(d, lab, R, rr[k], ok[k], 0.f, a, b, pp.v[k], gz);
-          }
-        }
-        s_p[i * 32 + lane] = pp;
-        if (ADJ)
-#pragma unroll
-          for (int k = 0; k < RPL; ++k) s_g[(k * kChunkMaxSlots + i) * 32 + lane] = 0.f;
-      }
-      if (ADJ)
-        for (int i = warp; i < nr; i += W)
-#pragma unroll
-          for (int k = 0; k < RPL; ++k) s_gr[(k * kChunkMaxReals + i) * 32 + lane] = 0.f;
-      __syncthreads();
-      // (2) Alg. 3 and Alg. 4, one warp per constraint
+      __syncthreads();  // p of tile t is ready, accumulators are zero
+      // Alg. 3 and Alg. 4, one warp per constraint, each warp a contiguous run
       float objacc[RPL];
 #pragma unroll
       for (int k = 0; k < RPL; ++k) objacc[k] = 0.f;
-      // contiguous runs of the chunk's (locality-sorted) constraints per warp, so
-      // that fewer warps update the same slot
       for (int c = warp * nc / W; c < (warp + 1) * nc / W; ++c) {
         const int4 cn = s_con[c];
         const uint2* nd = s_node + cn.x;
@@ -281,13 +296,13 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
             PK nb;
             if (ADJ) {
               const PK td = s_m[v * 32];
-              float* gs = s_g + slot * 32 + lane;
+              float* gs = s_g + slot * RPL * 32 + lane;
 #pragma unroll
               for (int k = 0; k < RPL; ++k) {
                 const float diff = mh.v[k] - ml.v[k];
                 nb.v[k] = fmaf(p.v[k], diff, ml.v[k]);
                 const float g = wc.v[k] * td.v[k] * diff;
-                if (g != 0.f) atomicAdd(gs + k * kChunkMaxSlots * 32, g);
+                if (g != 0.f) atomicAdd(gs + k * 32, g);
               }
             } else {
 #pragma unroll
@@ -309,39 +324,8 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
 #pragma unroll
         for (int k = 0; k < RPL; ++k)
           if (ok[k] && objacc[k] != 0.f) atomicAdd(obj_s ? obj_s + rr[k] : obj + rr[k], objacc[k]);
-      __syncthreads();
-      // (3) one global update per slot and restart
-      if (ADJ) {
-        for (int i = warp; i < ns; i += W) {
-          const int lab = s_lab[i];
-#pragma unroll
-          for (int k = 0; k < RPL; ++k) {
-            const float g = s_g[(k * kChunkMaxSlots + i) * 32 + lane];
-            if (!ok[k] || g == 0.f) continue;
-            if (lab < d.n_bool) {
-              atomicAdd(grad_a + (size_t)lab * R + rr[k], g);
-            } else if (s_inv > 0.f) {  // dC/dz through dd/db_j into the chunk's real accumulators
-              const int meta = s_meta[i], tb = meta >> 16, tc = meta & 0xffff;
-              const float si = s_si[i];
-              float z = -s_q0[i];
-              for (int j = 0; j < tc; ++j)
-                z = fmaf(s_tcoef[tb + j], __ldg(b + (size_t)s_rid[s_tvar[tb + j]] * R + rr[k]), z);
-              const float u = z * si;
-              const float gg = g * kTwoOverSqrtPi * __expf(-u * u) * si;
-              for (int j = 0; j < tc; ++j)
-                atomicAdd(s_gr + (k * kChunkMaxReals + s_tvar[tb + j]) * 32 + lane, gg * s_tcoef[tb + j]);
-            }
-          }
-        }
-        __syncthreads();
-        for (int i = warp; i < nr; i += W)  // one global update per chunk real and restart
-#pragma unroll
-          for (int k = 0; k < RPL; ++k) {
-            const float g = s_gr[(k * kChunkMaxReals + i) * 32 + lane];
-            if (ok[k] && g != 0.f) atomicAdd(grad_b + (size_t)s_rid[i] * R + rr[k], g);
-          }
-        __syncthreads();
-      }
+      __syncthreads();  // the gradient of tile t is complete; p of tile t is no longer read
+        slot_pass(t, t + 1);
     }
   }
   if (obj_s && obj) {

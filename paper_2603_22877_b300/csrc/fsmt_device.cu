@@ -23,10 +23,9 @@ namespace {
 constexpr int kFusedThreads = 256;  // 8 warps
 constexpr int kSmemBudget = 112 * 1024;
 // shared memory of the chunked kernel without the per-warp message arrays
-inline size_t chunk_fixed_bytes(int rpl) {
+inline size_t chunk_fixed_bytes(int rpl, int slot_cap) {
   return (size_t)kChunkMaxNodes * 8 + (size_t)kChunkMaxCons * 16 + (size_t)kChunkMaxSlots * 4 * 4 +
-         (size_t)kChunkMaxTerms * 8 + (size_t)kChunkMaxReals * 4 + (size_t)kChunkMaxSlots * 32 * 4 * rpl * 2 +
-         (size_t)kChunkMaxReals * 32 * 4 * rpl;
+         (size_t)kChunkMaxTerms * 8 + (size_t)kChunkMaxReals * 4 + (size_t)slot_cap * 32 * 4 * rpl * 2;
 }
 constexpr size_t kSmemMax = 227 * 1024;
 
@@ -644,11 +643,16 @@ ChunkShape chunk_shape(const Compiled& C, int R) {
   ChunkShape s{R > 32 ? 2 : 1, 0, 0};
   if (!C.chunked_ok) return s;
   const int vcap = std::max(1, C.max_nodes);
-  const size_t per_warp = (size_t)(vcap + 2) * 32 * 4 * s.rpl;
-  const size_t fixed = chunk_fixed_bytes(s.rpl) + (R <= kMaxObjSmemR ? (size_t)R * 4 : 0);
-  if (fixed + 4 * per_warp > kSmemMax) return s;
-  s.warps = (int)std::min<size_t>(kChunkThreads / 32, (kSmemMax - fixed) / per_warp);
-  s.smem = fixed + (size_t)s.warps * per_warp;
+  const size_t obj_bytes = R <= kMaxObjSmemR ? (size_t)R * 4 : 0;
+  // two restarts per lane while that leaves at least 8 warps, else one
+  for (int rpl = s.rpl; rpl >= 1; --rpl) {
+    const size_t per_warp = (size_t)(vcap + 2) * 32 * 4 * rpl;
+    const size_t fixed = chunk_fixed_bytes(rpl, C.chunk_slot_cap) + obj_bytes;
+    if (fixed + 4 * per_warp > kSmemMax) continue;
+    const int warps = (int)std::min<size_t>(kChunkThreads / 32, (kSmemMax - fixed) / per_warp);
+    if (warps > s.warps) s = {rpl, warps, fixed + (size_t)warps * per_warp};
+    if (s.warps >= 8) break;
+  }
   return s;
 }
 
@@ -656,21 +660,22 @@ fsmt_status launch_fused(const Compiled& C, bool adj, int R, float sigma, const 
                          const float* a, const float* b, float* ga, float* gb, float* obj, float* cop, const int* ctl,
                          cudaStream_t st) {
   if (C.n_obj == 0) return FSMT_OK;
+  int vcap = std::max(1, C.max_nodes);
+  const int blocks = std::max(1, std::min(C.n_chunks, sm_count()));
+  const int wide_rpl = R > 32 ? 2 : 1;
+  void* wk = C.chunked_ok ? C.jit_wide[adj ? 1 : 0][wide_rpl - 1] : nullptr;
+  const size_t wide_smem = chunk_fixed_bytes(wide_rpl, C.chunk_slot_cap) + (R <= kMaxObjSmemR ? (size_t)R * 4 : 0);
+  if (wk && wide_smem <= kSmemMax) {  // every constraint has a generated routine: 32 warps, no generic message rows
+    DevView view = C.view;
+    void* args[] = {&view, &R, &sigma, (void*)&prm, &vcap, (void*)&w, (void*)&a, (void*)&b,
+                    &ga, &gb, &obj, &cop, (void*)&ctl};
+    FSMT_CUDA(cudaLaunchKernel((const void*)wk, dim3(blocks), dim3(kChunkThreadsWide), args, wide_smem, st),
+              "specialised kernel launch");
+    return FSMT_OK;
+  }
   const ChunkShape cs = chunk_shape(C, R);
   if (cs.warps > 0) {
-    int vcap = std::max(1, C.max_nodes);
-    const int blocks = std::max(1, std::min(C.n_chunks, sm_count()));
     const dim3 g(blocks), t(cs.warps * 32);
-    void* wk = C.jit_wide[adj ? 1 : 0][cs.rpl - 1];
-    if (wk) {  // every constraint has a generated routine: 32 warps, no generic message rows
-      const size_t smem = chunk_fixed_bytes(cs.rpl) + (R <= kMaxObjSmemR ? (size_t)R * 4 : 0);
-      DevView view = C.view;
-      void* args[] = {&view, &R, &sigma, (void*)&prm, &vcap, (void*)&w, (void*)&a, (void*)&b,
-                      &ga, &gb, &obj, &cop, (void*)&ctl};
-      FSMT_CUDA(cudaLaunchKernel((const void*)wk, g, dim3(kChunkThreadsWide), args, smem, st),
-                "specialised kernel launch");
-      return FSMT_OK;
-    }
     void* jk = C.jit_kernel[adj ? 1 : 0][cs.rpl - 1];
     if (jk) {  // run-time specialised kernel
       DevView view = C.view;
@@ -840,6 +845,7 @@ fsmt_status fsmt_upload(fsmt_compiled* cc, void* stream) {
   v.hs_q0 = (const float*)(base + o_hsq);
   v.hs_inv_qq = (const float*)(base + o_hsi);
   v.n_chunks = C.n_chunks;
+  v.chunk_slot_cap = C.chunk_slot_cap;
   v.chunk_con_ptr = (const int32_t*)(base + o_ccp);
   v.ccon = (const int4*)(base + o_ccon);
   v.chunk_node_ptr = (const int32_t*)(base + o_cnp);

@@ -30,8 +30,11 @@ constexpr int kMaxCompVars = 32;            // reals per block coupled by half-s
 constexpr int kMaxCompHalfspaces = 64;      // half-spaces per block
 // chunks of the chunked forward/adjoint kernel
 constexpr int kChunkMaxCons = 64;    // constraints per chunk
-constexpr int kChunkMaxNodes = 1536; // decision nodes per chunk
-constexpr int kChunkMaxSlots = 192;  // distinct variables / atoms per chunk
+constexpr int kChunkMaxNodes = 2048; // decision nodes per chunk
+constexpr int kChunkMaxSlots = 320;  // distinct variables / atoms per chunk (hard limit)
+// the slot limit when the generic DP path may run: its per-warp message rows
+// share shared memory with the slot arrays, so smaller chunks keep more warps
+constexpr int kChunkSlotsGeneric = 192;
 constexpr int kChunkMaxTerms = 768;  // nonzeros of the atoms of a chunk
 constexpr int kChunkMaxReals = 64;   // distinct reals of the atoms of a chunk
 constexpr int kMaxJitShapes = 16;      // diagram shapes given generated code per instance
@@ -68,6 +71,7 @@ struct DevView {
   const float* hs_inv_qq;       // 1 / ||q||^2
   // chunked schedule of the constraints of C_sigma
   int32_t n_chunks;
+  int32_t chunk_slot_cap;         // most slots of any chunk: rows of the per-slot shared arrays
   const int32_t* chunk_con_ptr;   // [n_chunks + 1] into ccon
   const int4* ccon;               // {node offset in chunk, V, root, constraint id}
   const int32_t* chunk_node_ptr;  // [n_chunks + 1] into cnodes

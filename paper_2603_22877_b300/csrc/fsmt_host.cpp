@@ -2,9 +2,11 @@
 // verifier.  The device side lives in fsmt_device.cu.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <functional>
 #include <numeric>
+#include <string>
 #include <unordered_map>
 
 #include "fsmt_internal.h"
@@ -215,13 +217,13 @@ static bool build_diagram(int kind, int param, const int32_t* lits, int L, Diagr
 // id of the variables they touch (Booleans by id, reals after them), coarsely
 // then finely -- so that a chunk's constraints share variables.  A chunk then
 // takes constraints in that order until it would exceed kChunkMaxCons
-// constraints, kChunkMaxNodes nodes or kChunkMaxSlots distinct variables/atoms
+// constraints, kChunkMaxNodes nodes or slot_limit distinct variables/atoms
 // ("slots").  Every node's label is rewritten to its chunk-local slot, and a
 // child that is a terminal to the fixed row max_nodes (TRUE) or max_nodes + 1
 // (FALSE).  Returns
 // false if a single constraint does not fit a chunk (the warp-per-constraint
 // kernel then serves the instance).
-static bool build_chunks(const Problem& P, Compiled& C) {
+static bool build_chunks(const Problem& P, Compiled& C, int slot_limit) {
   const int n_obj = C.n_obj;
   C.chunk_con_ptr.assign(1, 0);
   C.chunk_node_ptr.assign(1, 0);
@@ -237,6 +239,7 @@ static bool build_chunks(const Problem& P, Compiled& C) {
   C.cnode_slot.clear();
   C.cnode_hilo.clear();
   C.n_chunks = 0;
+  C.chunk_slot_cap = 0;
   if (n_obj == 0) return true;
   struct Key {
     int64_t k0, k1, k2, k3;
@@ -313,6 +316,7 @@ static bool build_chunks(const Problem& P, Compiled& C) {
     }
     C.chunk_term_ptr.push_back((int32_t)C.term_var.size());
     C.chunk_slot_ptr.push_back((int32_t)C.slot_label.size());
+    C.chunk_slot_cap = std::max<int32_t>(C.chunk_slot_cap, (int32_t)slot_of.size());
     std::vector<int> reals(real_of.size());
     for (auto& kv : real_of) reals[kv.second] = kv.first;
     C.real_id.insert(C.real_id.end(), reals.begin(), reals.end());
@@ -332,7 +336,7 @@ static bool build_chunks(const Problem& P, Compiled& C) {
         new_terms += atom_terms((int)C.node_label[v]);
       }
     if (chunk_cons > 0 && (chunk_cons + 1 > kChunkMaxCons || chunk_nodes + V > kChunkMaxNodes ||
-                           (int)slot_of.size() + new_slots > kChunkMaxSlots ||
+                           (int)slot_of.size() + new_slots > slot_limit ||
                            chunk_terms + new_terms > kChunkMaxTerms ||
                            (int)real_of.size() + new_reals(s) > kChunkMaxReals))
       close_chunk();
@@ -407,7 +411,7 @@ static bool build_chunks(const Problem& P, Compiled& C) {
       };
       C.cnode_hilo.push_back(child(C.node_hilo[v] & 0xffffu) | (child(C.node_hilo[v] >> 16) << 16));
     }
-    if ((int)slot_of.size() > kChunkMaxSlots || chunk_terms > kChunkMaxTerms || (int)real_of.size() > kChunkMaxReals)
+    if ((int)slot_of.size() > slot_limit || chunk_terms > kChunkMaxTerms || (int)real_of.size() > kChunkMaxReals)
       return false;
     ++chunk_cons;
     chunk_nodes += V;
@@ -546,7 +550,13 @@ static fsmt_status compile(const Problem& P, int policy, Compiled& C) {
     C.atom_q0d[i] = (double)q0;
     C.atom_inv_norm[i] = (float)(1.0 / std::sqrt(nn));
   }
-  C.chunked_ok = build_chunks(P, C);
+  // chunks of up to kChunkMaxSlots slots when every constraint gets a generated
+  // routine (the kernel then holds no per-warp message rows); otherwise, or when
+  // run-time compilation is switched off, kChunkSlotsGeneric
+  const char* no_jit = std::getenv("FSMT_NO_JIT");
+  const bool jit_off = no_jit && no_jit[0] && std::string(no_jit) != "0";
+  C.chunked_ok = build_chunks(P, C, jit_off ? kChunkSlotsGeneric : kChunkMaxSlots);
+  if (C.chunked_ok && !C.all_specialized && !jit_off) C.chunked_ok = build_chunks(P, C, kChunkSlotsGeneric);
   // projection: box, single-variable unit atoms, half-spaces in constraint order
   C.lo.resize(C.n_real);
   C.hi.resize(C.n_real);

@@ -103,7 +103,7 @@ std::string shape_routine(int rank, int V, const uint16_t* hi, const uint16_t* l
       o << "      acc" << grp[v] << " += g;\n";
     } else {
       const std::string tot = members[v] > 1 ? "(g + acc" + std::to_string(v) + ")" : "g";
-      o << "      atomicAdd(s_g + (k * kChunkMaxSlots + (int)(r" << v << " & 0x7fffffffu)) * 32 + lane, (r" << v
+      o << "      atomicAdd(s_g + ((int)(r" << v << " & 0x7fffffffu) * RPL + k) * 32 + lane, (r" << v
         << " >> 31) ? -" << tot << " : " << tot << ");\n";
     }
     o << "    }\n";
