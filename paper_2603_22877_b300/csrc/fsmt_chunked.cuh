@@ -157,7 +157,11 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
   const int cap = d.chunk_slot_cap;
   PK* s_p = reinterpret_cast<PK*>(s_rid + kChunkMaxReals);   // [slot][32]
   float* s_g = reinterpret_cast<float*>(s_p + cap * 32);     // [slot][RPL][32]
-  PK* s_rows = reinterpret_cast<PK*>(s_g + cap * RPL * 32);
+  // reals staged per restart tile (0: atoms read b from global memory instead)
+  const int rcap = d.chunk_real_cap;
+  float* s_b = s_g + cap * RPL * 32;            // [tile parity][real][RPL][32]: b of the chunk's reals
+  float* s_gr = s_b + 2 * rcap * RPL * 32;      // [tile parity][real][RPL][32]: dC/db accumulators
+  PK* s_rows = reinterpret_cast<PK*>(s_gr + 2 * rcap * RPL * 32);
   PK* s_m = s_rows + warp * rows * 32 + lane;
   float* obj_s = (R <= kMaxObjSmemR) ? reinterpret_cast<float*>(s_rows + (GENERIC ? W * rows * 32 : 0)) : nullptr;
   if (obj_s)
@@ -188,54 +192,134 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
       s_tvar[i] = __ldg(d.term_var + t0 + i);
       s_tcoef[i] = __ldg(d.term_coef + t0 + i);
     }
+    const bool staged = rcap > 0;
+    const int nre = nr * RPL * 32;  // staged elements per tile
+    // b of tile t for the chunk's reals, into buffer t & 1
+    auto stage_b = [&](int t) {
+      float* dst = s_b + (t & 1) * rcap * RPL * 32;
+      for (int e = threadIdx.x; e < nre; e += blockDim.x) {
+        const int r = (t * RPL + (e >> 5) % RPL) * 32 + (e & 31);
+        dst[e] = r < R ? __ldg(b + (size_t)__ldg(d.real_id + e0 + e / (RPL * 32)) * R + r) : 0.f;
+      }
+    };
+    // dC/db of tile t: one global update per real and restart, then the buffer is cleared
+    auto flush_gr = [&](int t) {
+      float* src = s_gr + (t & 1) * rcap * RPL * 32;
+      for (int e = threadIdx.x; e < nre; e += blockDim.x) {
+        const float g = src[e];
+        const int r = (t * RPL + (e >> 5) % RPL) * 32 + (e & 31);
+        if (g != 0.f && r < R) atomicAdd(grad_b + (size_t)s_rid[e / (RPL * 32)] * R + r, g);
+        src[e] = 0.f;
+      }
+    };
+    if (staged) {
+      stage_b(0);
+      if (ADJ)
+        for (int e = threadIdx.x; e < 2 * nre; e += blockDim.x) s_gr[(e / nre) * rcap * RPL * 32 + e % nre] = 0.f;
+    }
     __syncthreads();
-    // One pass over the slots: the gradient of tile tf leaves for global memory
-    // (one update per slot and restart; an atom's through dd/dz and the chain rule
-    // into its reals), and the slots get the TRUE-probability p of tile tp.
+    // One pass over the slots: the gradient of tile tf leaves the slot
+    // accumulators (a Boolean's for global memory, an atom's through dd/dz and
+    // the chain rule into its reals), and the slots get the TRUE-probability p
+    // of tile tp.
     auto slot_pass = [&](int tf, int tp) {
+      const bool do_f = ADJ && tf >= 0, do_p = tp < n_tiles;
+      const float* sbf = s_b + (tf & 1) * rcap * RPL * 32;
+      const float* sbp = s_b + (tp & 1) * rcap * RPL * 32;
+      float* sgr = s_gr + (tf & 1) * rcap * RPL * 32;
       for (int i = warp; i < ns; i += W) {
         const int lab = s_lab[i];
-        const bool is_atom = lab >= d.n_bool;
-        const int meta = s_meta[i], tb = meta >> 16, tc = meta & 0xffff;
-        if (ADJ && tf >= 0) {
-#pragma unroll
-          for (int k = 0; k < RPL; ++k) {
-            const int r = (tf * RPL + k) * 32 + lane;
-            const float g = s_g[(i * RPL + k) * 32 + lane];
-            if (r >= R || g == 0.f) continue;
-            if (!is_atom) {
-              atomicAdd(grad_a + (size_t)lab * R + r, g);
-            } else if (s_inv > 0.f) {
-              float z = -s_q0[i];
-              for (int j = 0; j < tc; ++j) z = fmaf(s_tcoef[tb + j], __ldg(b + (size_t)s_rid[s_tvar[tb + j]] * R + r), z);
-              const float si = s_si[i], u = z * si;
-              const float gg = g * kTwoOverSqrtPi * __expf(-u * u) * si;  // dC/dz
-              for (int j = 0; j < tc; ++j)
-                atomicAdd(grad_b + (size_t)s_rid[s_tvar[tb + j]] * R + r, gg * s_tcoef[tb + j]);
-            }
-          }
-        }
-        if (tp < n_tiles) {
+        float* gi = s_g + i * RPL * 32 + lane;  // the slot's adjoint, restart k at gi[32 k]
+        if (lab < d.n_bool) {  // a Boolean: p = (1 - a) / 2
           PK pp;
 #pragma unroll
           for (int k = 0; k < RPL; ++k) {
-            const int r = (tp * RPL + k) * 32 + lane;
-            const bool ok = r < R;
-            if (!is_atom) {
-              pp.v[k] = ok ? 0.5f * (1.f - __ldg(a + (size_t)lab * R + r)) : 0.f;
-            } else if (s_inv > 0.f) {
-              float z = -s_q0[i];
-              for (int j = 0; j < tc; ++j)
-                z = fmaf(s_tcoef[tb + j], ok ? __ldg(b + (size_t)s_rid[s_tvar[tb + j]] * R + r) : 0.f, z);
-              const float u = z * s_si[i];
-              pp.v[k] = half_erfc_as(u, __expf(-u * u));
-            } else {
-              float gz;
-              literal_prob(d, lab, R, r, ok, 0.f, a, b, pp.v[k], gz);
+            const int rf = (tf * RPL + k) * 32 + lane, rp = (tp * RPL + k) * 32 + lane;
+            if (do_f) {
+              const float g = gi[32 * k];
+              if (rf < R && g != 0.f) atomicAdd(grad_a + (size_t)lab * R + rf, g);
             }
-            if (ADJ) s_g[(i * RPL + k) * 32 + lane] = 0.f;
+            if (do_p) {
+              pp.v[k] = rp < R ? 0.5f * (1.f - __ldg(a + (size_t)lab * R + rp)) : 0.f;
+              if (ADJ) gi[32 * k] = 0.f;
+            }
           }
-          s_p[i * 32 + lane] = pp;
+          if (do_p) s_p[i * 32 + lane] = pp;
+        } else if (staged && s_inv > 0.f) {
+          // an atom, its reals staged: z = q.y - q0 of both tiles in one sweep
+          // over the terms; past the last restart b reads 0 and the adjoint is 0
+          const int meta = s_meta[i], tb = meta >> 16, tc = meta & 0xffff;
+          const float q0 = s_q0[i], si = s_si[i];
+          float zf[RPL], zp[RPL];
+#pragma unroll
+          for (int k = 0; k < RPL; ++k) zf[k] = zp[k] = -q0;
+          for (int j = 0; j < tc; ++j) {
+            const float cj = s_tcoef[tb + j];
+            const int o = s_tvar[tb + j] * RPL * 32 + lane;
+#pragma unroll
+            for (int k = 0; k < RPL; ++k) {
+              if (do_f) zf[k] = fmaf(cj, sbf[o + 32 * k], zf[k]);
+              if (do_p) zp[k] = fmaf(cj, sbp[o + 32 * k], zp[k]);
+            }
+          }
+          if (do_f) {  // dC/dz = g dd/dz, then dC/db_j = dC/dz q_j into the chunk's reals
+            float gz[RPL];
+#pragma unroll
+            for (int k = 0; k < RPL; ++k) {
+              const float u = zf[k] * si;
+              gz[k] = gi[32 * k] * (kTwoOverSqrtPi * si) * __expf(-u * u);
+            }
+            for (int j = 0; j < tc; ++j) {
+              const float cj = s_tcoef[tb + j];
+              const int o = s_tvar[tb + j] * RPL * 32 + lane;
+#pragma unroll
+              for (int k = 0; k < RPL; ++k) atomicAdd(sgr + o + 32 * k, gz[k] * cj);
+            }
+          }
+          if (do_p) {
+            PK pp;
+#pragma unroll
+            for (int k = 0; k < RPL; ++k) {
+              const float u = zp[k] * si;
+              pp.v[k] = half_erfc_as(u, __expf(-u * u));
+              if (ADJ) gi[32 * k] = 0.f;
+            }
+            s_p[i * 32 + lane] = pp;
+          }
+        } else {  // an atom with b in global memory, or sigma = 0
+          const int meta = s_meta[i], tb = meta >> 16, tc = meta & 0xffff;
+          PK pp;
+#pragma unroll
+          for (int k = 0; k < RPL; ++k) {
+            const int rf = (tf * RPL + k) * 32 + lane, rp = (tp * RPL + k) * 32 + lane;
+            if (do_f && s_inv > 0.f) {
+              const float g = gi[32 * k];
+              if (rf < R && g != 0.f) {
+                float z = -s_q0[i];
+                for (int j = 0; j < tc; ++j)
+                  z = fmaf(s_tcoef[tb + j], __ldg(b + (size_t)s_rid[s_tvar[tb + j]] * R + rf), z);
+                const float si = s_si[i], u = z * si;
+                const float gz = g * kTwoOverSqrtPi * __expf(-u * u) * si;  // dC/dz
+                for (int j = 0; j < tc; ++j)
+                  atomicAdd(grad_b + (size_t)s_rid[s_tvar[tb + j]] * R + rf, gz * s_tcoef[tb + j]);
+              }
+            }
+            if (do_p) {
+              const bool ok = rp < R;
+              if (s_inv > 0.f) {
+                float z = -s_q0[i];
+                for (int j = 0; j < tc; ++j)
+                  z = fmaf(s_tcoef[tb + j], ok ? __ldg(b + (size_t)s_rid[s_tvar[tb + j]] * R + rp) : 0.f, z);
+                const float u = z * s_si[i];
+                pp.v[k] = half_erfc_as(u, __expf(-u * u));
+              } else {
+                float gz;
+                literal_prob(d, lab, R, rp, ok, 0.f, a, b, pp.v[k], gz);
+              }
+              if (ADJ) gi[32 * k] = 0.f;
+            }
+          }
+          if (do_p) s_p[i * 32 + lane] = pp;
         }
       }
     };
@@ -249,6 +333,10 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
         ok[k] = rr[k] < R;
       }
       __syncthreads();  // p of tile t is ready, accumulators are zero
+      if (staged) {  // while the DP runs: b of tile t + 1 in, dC/db of tile t - 1 out
+        if (t + 1 < n_tiles) stage_b(t + 1);
+        if (ADJ && t >= 1) flush_gr(t - 1);
+      }
       // Alg. 3 and Alg. 4, one warp per constraint, each warp a contiguous run
       float objacc[RPL];
 #pragma unroll
@@ -325,7 +413,11 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
         for (int k = 0; k < RPL; ++k)
           if (ok[k] && objacc[k] != 0.f) atomicAdd(obj_s ? obj_s + rr[k] : obj + rr[k], objacc[k]);
       __syncthreads();  // the gradient of tile t is complete; p of tile t is no longer read
-        slot_pass(t, t + 1);
+      slot_pass(t, t + 1);
+    }
+    if (ADJ && staged) {
+      __syncthreads();
+      flush_gr(n_tiles - 1);
     }
   }
   if (obj_s && obj) {

@@ -634,25 +634,30 @@ fsmt_status launch_fused_warp(const Compiled& C, bool adj, int R, float sigma, c
   return FSMT_OK;
 }
 
-// restarts per lane and warps of the chunked kernel for this instance (warps 0: it cannot run it)
+// restarts per lane, warps and staged reals of the chunked kernel for this
+// instance (warps 0: it cannot run it)
 struct ChunkShape {
-  int rpl, warps;
+  int rpl, warps, real_cap;
   size_t smem;
 };
+// shared memory of the staged reals: b and dC/db, two tiles each
+inline size_t staged_bytes(int rpl, int real_cap) { return (size_t)real_cap * rpl * 32 * 4 * 4; }
 ChunkShape chunk_shape(const Compiled& C, int R) {
-  ChunkShape s{R > 32 ? 2 : 1, 0, 0};
+  ChunkShape s{R > 32 ? 2 : 1, 0, 0, 0};
   if (!C.chunked_ok) return s;
   const int vcap = std::max(1, C.max_nodes);
   const size_t obj_bytes = R <= kMaxObjSmemR ? (size_t)R * 4 : 0;
-  // two restarts per lane while that leaves at least 8 warps, else one
-  for (int rpl = s.rpl; rpl >= 1; --rpl) {
-    const size_t per_warp = (size_t)(vcap + 2) * 32 * 4 * rpl;
-    const size_t fixed = chunk_fixed_bytes(rpl, C.chunk_slot_cap) + obj_bytes;
-    if (fixed + 4 * per_warp > kSmemMax) continue;
-    const int warps = (int)std::min<size_t>(kChunkThreads / 32, (kSmemMax - fixed) / per_warp);
-    if (warps > s.warps) s = {rpl, warps, fixed + (size_t)warps * per_warp};
-    if (s.warps >= 8) break;
-  }
+  // two restarts per lane while that leaves at least 8 warps, else one; staged
+  // reals while they leave at least 8 warps
+  for (int rpl = s.rpl; rpl >= 1; --rpl)
+    for (int rc : {C.stage_reals ? C.chunk_real_max : 0, 0}) {
+      const size_t per_warp = (size_t)(vcap + 2) * 32 * 4 * rpl;
+      const size_t fixed = chunk_fixed_bytes(rpl, C.chunk_slot_cap) + staged_bytes(rpl, rc) + obj_bytes;
+      if (fixed + 4 * per_warp > kSmemMax) continue;
+      const int warps = (int)std::min<size_t>(kChunkThreads / 32, (kSmemMax - fixed) / per_warp);
+      if (warps > s.warps) s = {rpl, warps, rc, fixed + (size_t)warps * per_warp};
+      if (s.warps >= 8) return s;
+    }
   return s;
 }
 
@@ -662,38 +667,41 @@ fsmt_status launch_fused(const Compiled& C, bool adj, int R, float sigma, const 
   if (C.n_obj == 0) return FSMT_OK;
   int vcap = std::max(1, C.max_nodes);
   const int blocks = std::max(1, std::min(C.n_chunks, sm_count()));
+  DevView view = C.view;
+  void* args[] = {&view, &R, &sigma, (void*)&prm, &vcap, (void*)&w, (void*)&a, (void*)&b,
+                  &ga, &gb, &obj, &cop, (void*)&ctl};
   const int wide_rpl = R > 32 ? 2 : 1;
   void* wk = C.chunked_ok ? C.jit_wide[adj ? 1 : 0][wide_rpl - 1] : nullptr;
-  const size_t wide_smem = chunk_fixed_bytes(wide_rpl, C.chunk_slot_cap) + (R <= kMaxObjSmemR ? (size_t)R * 4 : 0);
-  if (wk && wide_smem <= kSmemMax) {  // every constraint has a generated routine: 32 warps, no generic message rows
-    DevView view = C.view;
-    void* args[] = {&view, &R, &sigma, (void*)&prm, &vcap, (void*)&w, (void*)&a, (void*)&b,
-                    &ga, &gb, &obj, &cop, (void*)&ctl};
-    FSMT_CUDA(cudaLaunchKernel((const void*)wk, dim3(blocks), dim3(kChunkThreadsWide), args, wide_smem, st),
-              "specialised kernel launch");
-    return FSMT_OK;
+  if (wk) {  // every constraint has a generated routine: 32 warps, no generic message rows
+    const size_t base = chunk_fixed_bytes(wide_rpl, C.chunk_slot_cap) + (R <= kMaxObjSmemR ? (size_t)R * 4 : 0);
+    for (int rc : {C.stage_reals ? C.chunk_real_max : 0, 0}) {
+      const size_t smem = base + staged_bytes(wide_rpl, rc);
+      if (smem > kSmemMax) continue;
+      view.chunk_real_cap = rc;
+      FSMT_CUDA(cudaLaunchKernel((const void*)wk, dim3(blocks), dim3(kChunkThreadsWide), args, smem, st),
+                "specialised kernel launch");
+      return FSMT_OK;
+    }
   }
   const ChunkShape cs = chunk_shape(C, R);
   if (cs.warps > 0) {
+    view.chunk_real_cap = cs.real_cap;
     const dim3 g(blocks), t(cs.warps * 32);
     void* jk = C.jit_kernel[adj ? 1 : 0][cs.rpl - 1];
     if (jk) {  // run-time specialised kernel
-      DevView view = C.view;
-      void* args[] = {&view, &R, &sigma, (void*)&prm, &vcap, (void*)&w, (void*)&a, (void*)&b,
-                      &ga, &gb, &obj, &cop, (void*)&ctl};
       FSMT_CUDA(cudaLaunchKernel((const void*)jk, g, t, args, cs.smem, st), "specialised kernel launch");
       return FSMT_OK;
     }
     if (cs.rpl == 2) {
       if (adj)
-        k_chunked<true, 2><<<g, t, cs.smem, st>>>(C.view, R, sigma, prm, vcap, w, a, b, ga, gb, obj, cop, ctl);
+        k_chunked<true, 2><<<g, t, cs.smem, st>>>(view, R, sigma, prm, vcap, w, a, b, ga, gb, obj, cop, ctl);
       else
-        k_chunked<false, 2><<<g, t, cs.smem, st>>>(C.view, R, sigma, prm, vcap, w, a, b, ga, gb, obj, cop, ctl);
+        k_chunked<false, 2><<<g, t, cs.smem, st>>>(view, R, sigma, prm, vcap, w, a, b, ga, gb, obj, cop, ctl);
     } else {
       if (adj)
-        k_chunked<true, 1><<<g, t, cs.smem, st>>>(C.view, R, sigma, prm, vcap, w, a, b, ga, gb, obj, cop, ctl);
+        k_chunked<true, 1><<<g, t, cs.smem, st>>>(view, R, sigma, prm, vcap, w, a, b, ga, gb, obj, cop, ctl);
       else
-        k_chunked<false, 1><<<g, t, cs.smem, st>>>(C.view, R, sigma, prm, vcap, w, a, b, ga, gb, obj, cop, ctl);
+        k_chunked<false, 1><<<g, t, cs.smem, st>>>(view, R, sigma, prm, vcap, w, a, b, ga, gb, obj, cop, ctl);
     }
     FSMT_CUDA(cudaGetLastError(), "chunked kernel launch");
     return FSMT_OK;
@@ -846,6 +854,7 @@ fsmt_status fsmt_upload(fsmt_compiled* cc, void* stream) {
   v.hs_inv_qq = (const float*)(base + o_hsi);
   v.n_chunks = C.n_chunks;
   v.chunk_slot_cap = C.chunk_slot_cap;
+  v.chunk_real_cap = 0;  // set per launch
   v.chunk_con_ptr = (const int32_t*)(base + o_ccp);
   v.ccon = (const int4*)(base + o_ccon);
   v.chunk_node_ptr = (const int32_t*)(base + o_cnp);
@@ -875,6 +884,8 @@ fsmt_status fsmt_upload(fsmt_compiled* cc, void* stream) {
   cudaGetDevice(&C.device);
   C.uploaded = true;
   jit_build(C);  // optional: falls back to the ahead-of-time chunked kernel
+  const char* no_stage = std::getenv("FSMT_NO_STAGE");
+  C.stage_reals = !(no_stage && no_stage[0] && std::string(no_stage) != "0");
   return FSMT_OK;
 }
 

@@ -72,6 +72,7 @@ struct DevView {
   // chunked schedule of the constraints of C_sigma
   int32_t n_chunks;
   int32_t chunk_slot_cap;         // most slots of any chunk: rows of the per-slot shared arrays
+  int32_t chunk_real_cap;         // most reals of any chunk when their b is staged in shared memory, else 0
   const int32_t* chunk_con_ptr;   // [n_chunks + 1] into ccon
   const int4* ccon;               // {node offset in chunk, V, root, constraint id}
   const int32_t* chunk_node_ptr;  // [n_chunks + 1] into cnodes

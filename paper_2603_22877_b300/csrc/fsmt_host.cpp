@@ -223,6 +223,14 @@ static bool build_diagram(int kind, int param, const int32_t* lits, int L, Diagr
 // (FALSE).  Returns
 // false if a single constraint does not fit a chunk (the warp-per-constraint
 // kernel then serves the instance).
+// Shared memory of the 1024-thread kernel, two restarts per lane, left for the
+// per-slot arrays (512 bytes a slot: probabilities and adjoints) and the staged
+// reals (1024 bytes a real: b and dC/db, double-buffered) once the fixed arrays
+// and the per-restart objective (up to 4096 restarts) are placed.
+constexpr int kChunkWideBytes = 227 * 1024 - (kChunkMaxNodes * 8 + kChunkMaxCons * 16 + kChunkMaxSlots * 16 +
+                                              kChunkMaxTerms * 8 + kChunkMaxReals * 4) - 4096 * 4;
+static_assert(kChunkWideBytes >= kChunkMaxSlots * 512 + 16 * 1024, "wide chunk budget");
+
 static bool build_chunks(const Problem& P, Compiled& C, int slot_limit) {
   const int n_obj = C.n_obj;
   C.chunk_con_ptr.assign(1, 0);
@@ -240,6 +248,7 @@ static bool build_chunks(const Problem& P, Compiled& C, int slot_limit) {
   C.cnode_hilo.clear();
   C.n_chunks = 0;
   C.chunk_slot_cap = 0;
+  C.chunk_real_max = 0;
   if (n_obj == 0) return true;
   struct Key {
     int64_t k0, k1, k2, k3;
@@ -317,6 +326,7 @@ static bool build_chunks(const Problem& P, Compiled& C, int slot_limit) {
     C.chunk_term_ptr.push_back((int32_t)C.term_var.size());
     C.chunk_slot_ptr.push_back((int32_t)C.slot_label.size());
     C.chunk_slot_cap = std::max<int32_t>(C.chunk_slot_cap, (int32_t)slot_of.size());
+    C.chunk_real_max = std::max<int32_t>(C.chunk_real_max, (int32_t)real_of.size());
     std::vector<int> reals(real_of.size());
     for (auto& kv : real_of) reals[kv.second] = kv.first;
     C.real_id.insert(C.real_id.end(), reals.begin(), reals.end());
@@ -338,7 +348,10 @@ static bool build_chunks(const Problem& P, Compiled& C, int slot_limit) {
     if (chunk_cons > 0 && (chunk_cons + 1 > kChunkMaxCons || chunk_nodes + V > kChunkMaxNodes ||
                            (int)slot_of.size() + new_slots > slot_limit ||
                            chunk_terms + new_terms > kChunkMaxTerms ||
-                           (int)real_of.size() + new_reals(s) > kChunkMaxReals))
+                           (int)real_of.size() + new_reals(s) > kChunkMaxReals ||
+                           (slot_limit > kChunkSlotsGeneric &&
+                            ((int)slot_of.size() + new_slots) * 512 + ((int)real_of.size() + new_reals(s)) * 1024 >
+                                kChunkWideBytes)))
       close_chunk();
     if (V > kChunkMaxNodes) return false;
     C.ccon.push_back(chunk_nodes);

@@ -52,6 +52,8 @@ struct Compiled {
   bool chunked_ok = false;
   int32_t n_chunks = 0;
   int32_t chunk_slot_cap = 0;  // most slots of any chunk
+  int32_t chunk_real_max = 0;  // most reals of any chunk
+  bool stage_reals = true;     // stage the chunk's reals in shared memory (FSMT_NO_STAGE=1 turns it off)
   std::vector<int32_t> chunk_con_ptr{0}, chunk_node_ptr{0}, chunk_slot_ptr{0}, slot_label;
   std::vector<int32_t> slot_meta, chunk_term_ptr{0}, term_var, chunk_real_ptr{0}, real_id;
   std::vector<float> term_coef;

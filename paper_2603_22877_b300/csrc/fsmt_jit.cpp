@@ -59,9 +59,13 @@ Nvrtc& nvrtc() {
 // Alg. 3 / Alg. 4 for one shape, straight-line.  Node v tests literal l_v with
 // probability q_v (= p or 1 - p for a negated literal); its children (hi = l_v
 // true) are nodes, or V (TRUE) / V+1 (FALSE).  Nodes testing the same variable
-// (grp = the first of them) add their gradient terms in a register, and the
-// first of them -- the last one the reverse pass reaches -- issues the single
-// shared-memory update of the variable's slot.
+// form a group (grp = its first node), so the shape fixes which nodes read
+// which variable.  Each pass reads a group's slot word and q from shared
+// memory once, at the group's first node in that pass's order; the messages
+// t_v (Alg. 3) and b_v (Alg. 4) live in registers; the reverse pass sums
+// t_v (b_hi - b_lo) over a group and issues the one shared-memory update of
+// its slot at the group's last node.  Short live ranges keep the routine
+// within the 64 registers of the 1024-thread kernel.
 std::string shape_routine(int rank, int V, const uint16_t* hi, const uint16_t* lo, const uint16_t* grp) {
   std::ostringstream o;
   auto bu = [&](int c) -> std::string {  // m_bu of a child
@@ -69,44 +73,33 @@ std::string shape_routine(int rank, int V, const uint16_t* hi, const uint16_t* l
     if (c == V + 1) return "0.f";
     return "b" + std::to_string(c);
   };
-  std::vector<int> members(V, 0);
-  for (int v = 0; v < V; ++v) ++members[grp[v]];
+  std::vector<int> last(V, -1);  // last node of each group, by index
+  for (int v = 0; v < V; ++v) last[grp[v]] = v;
   o << "template <bool ADJ, int RPL>\n__device__ __forceinline__ void shape_" << rank
     << "(const uint2* __restrict__ nd, const Pack<RPL>* __restrict__ s_p, float* __restrict__ s_g, int lane,"
        " const Pack<RPL>& wc, Pack<RPL>& cp) {\n";
-  // the slot word and the literal probability are re-read from shared memory at
-  // each use (cheap, off the dependency chain) so that only messages stay live
-  auto q = [&](int v) {
-    return "lit_q(nd[" + std::to_string(v) + "].x, s_p, lane, k)";
-  };
   o << "#pragma unroll\n  for (int k = 0; k < RPL; ++k) {\n";
   o << "    float t0 = 1.f";
   for (int v = 1; v < V; ++v) o << ", t" << v << " = 0.f";
   o << ";\n    if (ADJ) {\n";
   for (int v = 0; v < V; ++v) {  // Alg. 3: push to non-terminal children
-    if (hi[v] >= V && lo[v] >= V) continue;
-    o << "      { const float q = " << q(v) << ";\n";
-    if (hi[v] < V) o << "        t" << hi[v] << " = fmaf(q, t" << v << ", t" << hi[v] << ");\n";
-    if (lo[v] < V) o << "        t" << lo[v] << " = fmaf(1.f - q, t" << v << ", t" << lo[v] << "); ";
-    o << "}\n";
+    const int g = grp[v];
+    if (g == v) o << "      const float f" << g << " = lit_q(nd[" << g << "].x, s_p, lane, k);\n";
+    if (hi[v] < V) o << "      t" << hi[v] << " = fmaf(f" << g << ", t" << v << ", t" << hi[v] << ");\n";
+    if (lo[v] < V) o << "      t" << lo[v] << " = fmaf(1.f - f" << g << ", t" << v << ", t" << lo[v] << ");\n";
   }
   o << "    }\n";
-  for (int v = 0; v < V; ++v)
-    if (grp[v] == v && members[v] > 1) o << "    float acc" << v << " = 0.f;\n";
-  for (int v = V - 1; v >= 0; --v) {  // Alg. 4
-    o << "    const unsigned r" << v << " = nd[" << v << "].x;\n";
+  for (int v = V - 1; v >= 0; --v) {  // Alg. 4, and the adjoint sum of each group
+    const int g = grp[v];
+    if (last[g] == v)
+      o << "    const float q" << g << " = lit_q(nd[" << g << "].x, s_p, lane, k);\n    float acc" << g << " = 0.f;\n";
     o << "    const float d" << v << " = " << bu(hi[v]) << " - " << bu(lo[v]) << ";\n";
-    o << "    const float b" << v << " = fmaf(lit_q(r" << v << ", s_p, lane, k), d" << v << ", " << bu(lo[v])
-      << ");\n";
-    o << "    if (ADJ) {\n      const float g = wc.v[k] * t" << v << " * d" << v << ";\n";
-    if (grp[v] != v) {
-      o << "      acc" << grp[v] << " += g;\n";
-    } else {
-      const std::string tot = members[v] > 1 ? "(g + acc" + std::to_string(v) + ")" : "g";
-      o << "      atomicAdd(s_g + ((int)(r" << v << " & 0x7fffffffu) * RPL + k) * 32 + lane, (r" << v
-        << " >> 31) ? -" << tot << " : " << tot << ");\n";
-    }
-    o << "    }\n";
+    o << "    const float b" << v << " = fmaf(q" << g << ", d" << v << ", " << bu(lo[v]) << ");\n";
+    o << "    if (ADJ) acc" << g << " = fmaf(t" << v << ", d" << v << ", acc" << g << ");\n";
+    if (g == v)
+      o << "    if (ADJ) {\n      const unsigned r = nd[" << g << "].x;\n"
+        << "      atomicAdd(s_g + ((int)(r & 0x7fffffffu) * RPL + k) * 32 + lane, (r >> 31) ? -wc.v[k] * acc" << g
+        << " : wc.v[k] * acc" << g << ");\n    }\n";
   }
   o << "    cp.v[k] = b0;\n  }\n}\n\n";
   return o.str();
