@@ -129,7 +129,7 @@ __device__ __forceinline__ float atom_z(const DevView& d, int i, int R, int r, c
 }
 
 template <bool ADJ, int RPL>
-__device__ __forceinline__ bool shape_dispatch(int shape, const uint2* nd, const Pack<RPL>* s_p, float* s_g, int lane,
+__device__ __forceinline__ bool shape_dispatch(int shape, const uint2* nd, const float* s_p, float* s_g, int lane,
                                                const Pack<RPL>& wc, Pack<RPL>& cp);
 
 // GENERIC = false: every constraint has a generated routine, so the generic
@@ -155,8 +155,8 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
   float* s_tcoef = reinterpret_cast<float*>(s_tvar + kChunkMaxTerms);
   int* s_rid = reinterpret_cast<int*>(s_tcoef + kChunkMaxTerms);  // the chunk's reals
   const int cap = d.chunk_slot_cap;
-  PK* s_p = reinterpret_cast<PK*>(s_rid + kChunkMaxReals);   // [slot][32]
-  float* s_g = reinterpret_cast<float*>(s_p + cap * 32);     // [slot][RPL][32]
+  float* s_p = reinterpret_cast<float*>(s_rid + kChunkMaxReals);  // [slot][RPL][32]: TRUE-probability
+  float* s_g = s_p + cap * RPL * 32;                               // [slot][RPL][32]: adjoint
   // reals staged per restart tile (0: atoms read b from global memory instead)
   const int rcap = d.chunk_real_cap;
   float* s_b = s_g + cap * RPL * 32;            // [tile parity][real][RPL][32]: b of the chunk's reals
@@ -244,7 +244,9 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
               if (ADJ) gi[32 * k] = 0.f;
             }
           }
-          if (do_p) s_p[i * 32 + lane] = pp;
+          if (do_p)
+#pragma unroll
+            for (int k = 0; k < RPL; ++k) s_p[(i * RPL + k) * 32 + lane] = pp.v[k];
         } else if (staged && s_inv > 0.f) {
           // an atom, its reals staged: z = q.y - q0 of both tiles in one sweep
           // over the terms; past the last restart b reads 0 and the adjoint is 0
@@ -284,7 +286,8 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
               pp.v[k] = half_erfc_as(u, __expf(-u * u));
               if (ADJ) gi[32 * k] = 0.f;
             }
-            s_p[i * 32 + lane] = pp;
+#pragma unroll
+            for (int k = 0; k < RPL; ++k) s_p[(i * RPL + k) * 32 + lane] = pp.v[k];
           }
         } else {  // an atom with b in global memory, or sigma = 0
           const int meta = s_meta[i], tb = meta >> 16, tc = meta & 0xffff;
@@ -319,7 +322,9 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
               if (ADJ) gi[32 * k] = 0.f;
             }
           }
-          if (do_p) s_p[i * 32 + lane] = pp;
+          if (do_p)
+#pragma unroll
+            for (int k = 0; k < RPL; ++k) s_p[(i * RPL + k) * 32 + lane] = pp.v[k];
         }
       }
     };
@@ -341,14 +346,26 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
       float objacc[RPL];
 #pragma unroll
       for (int k = 0; k < RPL; ++k) objacc[k] = 0.f;
-      for (int c = warp * nc / W; c < (warp + 1) * nc / W; ++c) {
+      const int c_end = (warp + 1) * nc / W;
+      PK wn;  // w of the warp's next constraint, loaded one constraint ahead
+      {
+        const int c = warp * nc / W;
+        const int id = c < c_end ? s_con[c].w : 0;
+#pragma unroll
+        for (int k = 0; k < RPL; ++k) wn.v[k] = (c < c_end && ok[k]) ? __ldg(w + (size_t)id * R + rr[k]) : 0.f;
+      }
+      for (int c = warp * nc / W; c < c_end; ++c) {
         const int4 cn = s_con[c];
         const uint2* nd = s_node + cn.x;
         const int V = cn.y & 0xffff;
         const int shape = cn.y >> 16;
-        PK wc, cp;
+        const PK wc = wn;
+        PK cp;
+        if (c + 1 < c_end) {
+          const int id = s_con[c + 1].w;
 #pragma unroll
-        for (int k = 0; k < RPL; ++k) wc.v[k] = ok[k] ? __ldg(w + (size_t)cn.w * R + rr[k]) : 0.f;
+          for (int k = 0; k < RPL; ++k) wn.v[k] = ok[k] ? __ldg(w + (size_t)id * R + rr[k]) : 0.f;
+        }
         if ((shape == 0 || !shape_dispatch<ADJ, RPL>(shape, nd, s_p, s_g, lane, wc, cp)) && GENERIC) {
           PK zero, one;
 #pragma unroll
@@ -362,7 +379,9 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
             for (int v = 0; v < V; ++v) {  // Alg. 3, topological order
               const uint2 e = nd[v];
               const int hi = (int)(e.y & 0xffffu) * 32, lo = (int)(e.y >> 16) * 32;
-              const PK p = s_p[(e.x & 0x7fffffffu) * 32 + lane];
+              PK p;
+#pragma unroll
+              for (int k = 0; k < RPL; ++k) p.v[k] = s_p[((e.x & 0x7fffffffu) * RPL + k) * 32 + lane];
               const PK mv = s_m[v * 32];
               PK mh = s_m[hi], ml = s_m[lo];
 #pragma unroll
@@ -380,7 +399,9 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
             const uint2 e = nd[v];
             const int slot = (int)(e.x & 0x7fffffffu);
             const PK mh = s_m[(int)(e.y & 0xffffu) * 32], ml = s_m[(int)(e.y >> 16) * 32];
-            const PK p = s_p[slot * 32 + lane];
+            PK p;
+#pragma unroll
+            for (int k = 0; k < RPL; ++k) p.v[k] = s_p[(slot * RPL + k) * 32 + lane];
             PK nb;
             if (ADJ) {
               const PK td = s_m[v * 32];
@@ -431,7 +452,7 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
 #ifndef FSMT_JIT_SHAPES
 // Ahead-of-time build: no generated routines, every constraint takes the generic path.
 template <bool ADJ, int RPL>
-__device__ __forceinline__ bool shape_dispatch(int, const uint2*, const Pack<RPL>*, float*, int, const Pack<RPL>&,
+__device__ __forceinline__ bool shape_dispatch(int, const uint2*, const float*, float*, int, const Pack<RPL>&,
                                                Pack<RPL>&) {
   return false;
 }

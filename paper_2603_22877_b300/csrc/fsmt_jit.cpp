@@ -76,7 +76,7 @@ std::string shape_routine(int rank, int V, const uint16_t* hi, const uint16_t* l
   std::vector<int> last(V, -1);  // last node of each group, by index
   for (int v = 0; v < V; ++v) last[grp[v]] = v;
   o << "template <bool ADJ, int RPL>\n__device__ __forceinline__ void shape_" << rank
-    << "(const uint2* __restrict__ nd, const Pack<RPL>* __restrict__ s_p, float* __restrict__ s_g, int lane,"
+    << "(const uint2* __restrict__ nd, const float* __restrict__ s_p, float* __restrict__ s_g, int lane,"
        " const Pack<RPL>& wc, Pack<RPL>& cp) {\n";
   o << "#pragma unroll\n  for (int k = 0; k < RPL; ++k) {\n";
   o << "    float t0 = 1.f";
@@ -84,7 +84,7 @@ std::string shape_routine(int rank, int V, const uint16_t* hi, const uint16_t* l
   o << ";\n    if (ADJ) {\n";
   for (int v = 0; v < V; ++v) {  // Alg. 3: push to non-terminal children
     const int g = grp[v];
-    if (g == v) o << "      const float f" << g << " = lit_q(nd[" << g << "].x, s_p, lane, k);\n";
+    if (g == v) o << "      const float f" << g << " = lit_q<RPL>(nd[" << g << "].x, s_p, lane, k);\n";
     if (hi[v] < V) o << "      t" << hi[v] << " = fmaf(f" << g << ", t" << v << ", t" << hi[v] << ");\n";
     if (lo[v] < V) o << "      t" << lo[v] << " = fmaf(1.f - f" << g << ", t" << v << ", t" << lo[v] << ");\n";
   }
@@ -92,7 +92,7 @@ std::string shape_routine(int rank, int V, const uint16_t* hi, const uint16_t* l
   for (int v = V - 1; v >= 0; --v) {  // Alg. 4, and the adjoint sum of each group
     const int g = grp[v];
     if (last[g] == v)
-      o << "    const float q" << g << " = lit_q(nd[" << g << "].x, s_p, lane, k);\n    float acc" << g << " = 0.f;\n";
+      o << "    const float q" << g << " = lit_q<RPL>(nd[" << g << "].x, s_p, lane, k);\n    float acc" << g << " = 0.f;\n";
     o << "    const float d" << v << " = " << bu(hi[v]) << " - " << bu(lo[v]) << ";\n";
     o << "    const float b" << v << " = fmaf(q" << g << ", d" << v << ", " << bu(lo[v]) << ");\n";
     o << "    if (ADJ) acc" << g << " = fmaf(t" << v << ", d" << v << ", acc" << g << ");\n";
@@ -113,15 +113,15 @@ std::string generated_source(const Compiled& C) {
   std::ostringstream o;
   o << "#define FSMT_JIT_SHAPES 1\n" << kJitDevviewSrc << "\n" << kJitChunkedSrc << "\nnamespace fsmt {\n\n";
   o << "// probability of the literal a node tests: p of its slot, or 1 - p when negated (bit 31)\n"
-       "template <int RPL>\n__device__ __forceinline__ float lit_q(unsigned r, const Pack<RPL>* __restrict__ s_p, int lane,"
-       " int k) {\n  const float p = s_p[(r & 0x7fffffffu) * 32 + lane].v[k];\n  return (r >> 31) ? 1.f - p : p;\n}\n\n";
+       "template <int RPL>\n__device__ __forceinline__ float lit_q(unsigned r, const float* __restrict__ s_p, int lane,"
+       " int k) {\n  const float p = s_p[((r & 0x7fffffffu) * RPL + k) * 32 + lane];\n  return (r >> 31) ? 1.f - p : p;\n}\n\n";
   for (size_t k = 0; k < C.jit_shape.size(); ++k) {
     const int x = C.jit_shape[k];
     const int b = C.shape_ptr[x], V = C.shape_ptr[x + 1] - b;
     o << shape_routine((int)k + 1, V, C.shape_hi.data() + b, C.shape_lo.data() + b, C.shape_grp.data() + b);
   }
   o << "template <bool ADJ, int RPL>\n__device__ __forceinline__ bool shape_dispatch(int shape, const uint2* nd,"
-       " const Pack<RPL>* s_p, float* s_g, int lane, const Pack<RPL>& wc, Pack<RPL>& cp) {\n  switch (shape) {\n";
+       " const float* s_p, float* s_g, int lane, const Pack<RPL>& wc, Pack<RPL>& cp) {\n  switch (shape) {\n";
   for (size_t k = 0; k < C.jit_shape.size(); ++k)
     o << "    case " << k + 1 << ": shape_" << k + 1 << "<ADJ, RPL>(nd, s_p, s_g, lane, wc, cp); return true;\n";
   o << "    default: return false;\n  }\n}\n\n}  // namespace fsmt\n\n";
