@@ -9,7 +9,6 @@ namespace fsmt {
 constexpr float kTwoOverSqrtPi = 1.1283791670955126f;
 constexpr float kInvSqrt2 = 0.70710678118654752f;
 constexpr int kMaxObjSmemR = 4096;
-constexpr int kChunkThreads = 512;       // 16 warps
 constexpr int kChunkThreadsWide = 1024;  // 32 warps, without the generic path
 
 // stage parameter slots (device float[16])
@@ -87,8 +86,11 @@ __device__ __forceinline__ void scatter_grad(const DevView& d, int lab, int R, i
 // over restart tiles of 32*RPL restarts; each lane carries RPL restarts (lane,
 // lane+32, ...), so every global access of a warp is a contiguous 128-byte line.
 // Per tile:
-//  (1) every slot -- a Boolean or an atom used by the chunk -- gets its
-//      TRUE-probability p once (Eq. rounding / Eq. sampling);
+//  (1) every slot -- a literal (a Boolean or an atom, with its polarity) used by
+//      the chunk -- gets its probability q of holding once (Eq. rounding /
+//      Eq. sampling; 1 - p for a negated literal), so the diagram passes work in
+//      literal space (a node's hi child: its literal holds) with no polarity
+//      logic of their own;
 //  (2) each warp runs Alg. 3 then Alg. 4 on its constraints -- through a
 //      routine generated for the constraint's diagram shape when there is one
 //      (shape_dispatch), else the generic form below -- with p read from
@@ -100,11 +102,18 @@ __device__ __forceinline__ void scatter_grad(const DevView& d, int lab, int R, i
 //      backward pass adds w_c m_td[v] (m_bu[hi] - m_bu[lo]) to the slot's
 //      shared accumulator;
 //  (3) each slot's accumulated derivative reaches the global gradient once (for
-//      atoms through dd/db_j).
+//      atoms through dd/db_j; negated literals with the sign flipped).
 template <int RPL>
 struct __align__(4 * RPL) Pack {
   float v[RPL];
 };
+
+// Arithmetic of the generated diagram routines: IEEE single operations, never
+// contracted with one another.
+__device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float vsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
 
 // erfc(x)/2 for the atom probability, by Abramowitz & Stegun 7.1.26 (Hastings):
 // erf(x) = 1 - (a1 t + ... + a5 t^5) e^{-x^2} + e(x), t = 1/(1 + 0.3275911 x),
@@ -155,8 +164,8 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
   float* s_tcoef = reinterpret_cast<float*>(s_tvar + kChunkMaxTerms);
   int* s_rid = reinterpret_cast<int*>(s_tcoef + kChunkMaxTerms);  // the chunk's reals
   const int cap = d.chunk_slot_cap;
-  float* s_p = reinterpret_cast<float*>(s_rid + kChunkMaxReals);  // [slot][RPL][32]: TRUE-probability
-  float* s_g = s_p + cap * RPL * 32;                               // [slot][RPL][32]: adjoint
+  float* s_p = reinterpret_cast<float*>(s_rid + kChunkMaxReals);  // [slot][RPL][32]: probability of the literal
+  float* s_g = s_p + cap * RPL * 32;                               // [slot][RPL][32]: its adjoint
   // reals staged per restart tile (0: atoms read b from global memory instead)
   const int rcap = d.chunk_real_cap;
   float* s_b = s_g + cap * RPL * 32;            // [tile parity][real][RPL][32]: b of the chunk's reals
@@ -180,8 +189,9 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
     const int e0 = __ldg(d.chunk_real_ptr + q), nr = __ldg(d.chunk_real_ptr + q + 1) - e0;
     for (int i = threadIdx.x; i < nr; i += blockDim.x) s_rid[i] = __ldg(d.real_id + e0 + i);
     for (int i = threadIdx.x; i < ns; i += blockDim.x) {
-      const int lab = __ldg(d.slot_label + l0 + i);
-      s_lab[i] = lab;
+      const int raw = __ldg(d.slot_label + l0 + i);  // bit 31: the literal is negated
+      const int lab = raw & 0x7fffffff;
+      s_lab[i] = raw;
       s_meta[i] = __ldg(d.slot_meta + l0 + i);
       if (lab >= d.n_bool) {
         s_q0[i] = __ldg(d.atom_q0f + lab - d.n_bool);
@@ -228,25 +238,20 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
       const float* sbp = s_b + (tp & 1) * rcap * RPL * 32;
       float* sgr = s_gr + (tf & 1) * rcap * RPL * 32;
       for (int i = warp; i < ns; i += W) {
-        const int lab = s_lab[i];
-        float* gi = s_g + i * RPL * 32 + lane;  // the slot's adjoint, restart k at gi[32 k]
+        const int raw = s_lab[i], lab = raw & 0x7fffffff;
+        const float sg = raw < 0 ? -1.f : 1.f;  // dq/dp
+        float* gi = s_g + i * RPL * 32 + lane;  // the slot's adjoint dC/dq, restart k at gi[32 k]
+        PK pp;
         if (lab < d.n_bool) {  // a Boolean: p = (1 - a) / 2
-          PK pp;
 #pragma unroll
           for (int k = 0; k < RPL; ++k) {
             const int rf = (tf * RPL + k) * 32 + lane, rp = (tp * RPL + k) * 32 + lane;
             if (do_f) {
               const float g = gi[32 * k];
-              if (rf < R && g != 0.f) atomicAdd(grad_a + (size_t)lab * R + rf, g);
+              if (rf < R && g != 0.f) atomicAdd(grad_a + (size_t)lab * R + rf, sg * g);
             }
-            if (do_p) {
-              pp.v[k] = rp < R ? 0.5f * (1.f - __ldg(a + (size_t)lab * R + rp)) : 0.f;
-              if (ADJ) gi[32 * k] = 0.f;
-            }
+            if (do_p) pp.v[k] = rp < R ? 0.5f * (1.f - sg * __ldg(a + (size_t)lab * R + rp)) : 0.f;
           }
-          if (do_p)
-#pragma unroll
-            for (int k = 0; k < RPL; ++k) s_p[(i * RPL + k) * 32 + lane] = pp.v[k];
         } else if (staged && s_inv > 0.f) {
           // an atom, its reals staged: z = q.y - q0 of both tiles in one sweep
           // over the terms; past the last restart b reads 0 and the adjoint is 0
@@ -264,12 +269,12 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
               if (do_p) zp[k] = fmaf(cj, sbp[o + 32 * k], zp[k]);
             }
           }
-          if (do_f) {  // dC/dz = g dd/dz, then dC/db_j = dC/dz q_j into the chunk's reals
+          if (do_f) {  // dC/dz = dC/dq dq/dp dp/dz, then dC/db_j = dC/dz q_j into the chunk's reals
             float gz[RPL];
 #pragma unroll
             for (int k = 0; k < RPL; ++k) {
               const float u = zf[k] * si;
-              gz[k] = gi[32 * k] * (kTwoOverSqrtPi * si) * __expf(-u * u);
+              gz[k] = sg * gi[32 * k] * (kTwoOverSqrtPi * si) * __expf(-u * u);
             }
             for (int j = 0; j < tc; ++j) {
               const float cj = s_tcoef[tb + j];
@@ -278,20 +283,14 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
               for (int k = 0; k < RPL; ++k) atomicAdd(sgr + o + 32 * k, gz[k] * cj);
             }
           }
-          if (do_p) {
-            PK pp;
+          if (do_p)
 #pragma unroll
             for (int k = 0; k < RPL; ++k) {
               const float u = zp[k] * si;
-              pp.v[k] = half_erfc_as(u, __expf(-u * u));
-              if (ADJ) gi[32 * k] = 0.f;
+              pp.v[k] = half_erfc_as(sg * u, __expf(-u * u));  // 1 - erfc(u)/2 = erfc(-u)/2
             }
-#pragma unroll
-            for (int k = 0; k < RPL; ++k) s_p[(i * RPL + k) * 32 + lane] = pp.v[k];
-          }
         } else {  // an atom with b in global memory, or sigma = 0
           const int meta = s_meta[i], tb = meta >> 16, tc = meta & 0xffff;
-          PK pp;
 #pragma unroll
           for (int k = 0; k < RPL; ++k) {
             const int rf = (tf * RPL + k) * 32 + lane, rp = (tp * RPL + k) * 32 + lane;
@@ -302,7 +301,7 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
                 for (int j = 0; j < tc; ++j)
                   z = fmaf(s_tcoef[tb + j], __ldg(b + (size_t)s_rid[s_tvar[tb + j]] * R + rf), z);
                 const float si = s_si[i], u = z * si;
-                const float gz = g * kTwoOverSqrtPi * __expf(-u * u) * si;  // dC/dz
+                const float gz = sg * g * kTwoOverSqrtPi * __expf(-u * u) * si;  // dC/dz
                 for (int j = 0; j < tc; ++j)
                   atomicAdd(grad_b + (size_t)s_rid[s_tvar[tb + j]] * R + rf, gz * s_tcoef[tb + j]);
               }
@@ -314,18 +313,21 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
                 for (int j = 0; j < tc; ++j)
                   z = fmaf(s_tcoef[tb + j], ok ? __ldg(b + (size_t)s_rid[s_tvar[tb + j]] * R + rp) : 0.f, z);
                 const float u = z * s_si[i];
-                pp.v[k] = half_erfc_as(u, __expf(-u * u));
+                pp.v[k] = half_erfc_as(sg * u, __expf(-u * u));
               } else {
-                float gz;
-                literal_prob(d, lab, R, rp, ok, 0.f, a, b, pp.v[k], gz);
+                float p, gz;
+                literal_prob(d, lab, R, rp, ok, 0.f, a, b, p, gz);
+                pp.v[k] = raw < 0 ? 1.f - p : p;  // exact: p is 0 or 1
               }
-              if (ADJ) gi[32 * k] = 0.f;
             }
           }
-          if (do_p)
-#pragma unroll
-            for (int k = 0; k < RPL; ++k) s_p[(i * RPL + k) * 32 + lane] = pp.v[k];
         }
+        if (do_p)
+#pragma unroll
+          for (int k = 0; k < RPL; ++k) {
+            s_p[(i * RPL + k) * 32 + lane] = pp.v[k];
+            if (ADJ) gi[32 * k] = 0.f;
+          }
       }
     };
     slot_pass(-1, 0);
@@ -381,7 +383,7 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
               const int hi = (int)(e.y & 0xffffu) * 32, lo = (int)(e.y >> 16) * 32;
               PK p;
 #pragma unroll
-              for (int k = 0; k < RPL; ++k) p.v[k] = s_p[((e.x & 0x7fffffffu) * RPL + k) * 32 + lane];
+              for (int k = 0; k < RPL; ++k) p.v[k] = s_p[(e.x * RPL + k) * 32 + lane];
               const PK mv = s_m[v * 32];
               PK mh = s_m[hi], ml = s_m[lo];
 #pragma unroll
@@ -397,7 +399,7 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
           s_m[(vcap + 1) * 32] = zero;
           for (int v = V - 1; v >= 0; --v) {  // Alg. 4, reverse topological order
             const uint2 e = nd[v];
-            const int slot = (int)(e.x & 0x7fffffffu);
+            const int slot = (int)e.x;
             const PK mh = s_m[(int)(e.y & 0xffffu) * 32], ml = s_m[(int)(e.y >> 16) * 32];
             PK p;
 #pragma unroll

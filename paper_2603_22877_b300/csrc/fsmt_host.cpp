@@ -289,7 +289,7 @@ static bool build_chunks(const Problem& P, Compiled& C, int slot_limit) {
     int n = 0;
     for (int v = C.con_ptr[s]; v < C.con_ptr[s + 1]; ++v) {
       const int lab = (int)C.node_label[v];
-      if (lab < C.n_bool || slot_of.count(lab)) continue;
+      if (lab < C.n_bool) continue;
       for (int e = C.atom_ptr[lab - C.n_bool]; e < C.atom_ptr[lab - C.n_bool + 1]; ++e)
         if (!real_of.count(C.atom_var[e])) ++n;
     }
@@ -313,7 +313,7 @@ static bool build_chunks(const Problem& P, Compiled& C, int slot_limit) {
     // the chunk's atom terms, in slot order
     int tb = 0;
     for (size_t k = C.chunk_slot_ptr.back(); k < C.slot_label.size(); ++k) {
-      const int lab = C.slot_label[k];
+      const int lab = C.slot_label[k] & 0x7fffffff;
       const int tc = atom_terms(lab);
       C.slot_meta.push_back(tc ? ((tb << 16) | tc) : 0);
       for (int j = 0; j < tc; ++j) {
@@ -336,15 +336,25 @@ static bool build_chunks(const Problem& P, Compiled& C, int slot_limit) {
     slot_of.clear();
     chunk_cons = chunk_nodes = chunk_terms = 0;
   };
+  // a slot is a literal: (variable or atom, polarity); key 2 * label + negated
+  auto slot_key = [](int lab, bool ng) { return 2 * lab + (ng ? 1 : 0); };
   for (const Key& k : keys) {
     const int s = k.s;
     const int b = C.con_ptr[s], V = C.con_ptr[s + 1] - b;
+    neg_of.clear();
+    {
+      const int cid = C.con_id[s];
+      for (int64_t t = P.con_ptr[cid]; t < P.con_ptr[cid + 1]; ++t)
+        neg_of[P.con_lits[t] >> 1] = (P.con_lits[t] & 1) != 0;
+    }
     int new_slots = 0, new_terms = 0;
-    for (int v = b; v < b + V; ++v)
-      if (!slot_of.count((int)C.node_label[v])) {  // may count a repeat twice: conservative
+    for (int v = b; v < b + V; ++v) {
+      const int lab = (int)C.node_label[v];
+      if (!slot_of.count(slot_key(lab, neg_of[lab]))) {  // may count a repeat twice: conservative
         ++new_slots;
-        new_terms += atom_terms((int)C.node_label[v]);
+        new_terms += atom_terms(lab);
       }
+    }
     if (chunk_cons > 0 && (chunk_cons + 1 > kChunkMaxCons || chunk_nodes + V > kChunkMaxNodes ||
                            (int)slot_of.size() + new_slots > slot_limit ||
                            chunk_terms + new_terms > kChunkMaxTerms ||
@@ -358,12 +368,6 @@ static bool build_chunks(const Problem& P, Compiled& C, int slot_limit) {
     C.ccon.push_back(V);
     C.ccon.push_back(C.con_root[s]);
     C.ccon.push_back(C.con_id[s]);
-    neg_of.clear();
-    {
-      const int cid = C.con_id[s];
-      for (int64_t t = P.con_ptr[cid]; t < P.con_ptr[cid + 1]; ++t)
-        neg_of[P.con_lits[t] >> 1] = (P.con_lits[t] & 1) != 0;
-    }
     std::string key(reinterpret_cast<const char*>(&V), sizeof(V));
     std::vector<uint16_t> shi(V), slo(V), sgrp(V);
     for (int v = b; v < b + V; ++v) {
@@ -400,12 +404,13 @@ static bool build_chunks(const Problem& P, Compiled& C, int slot_limit) {
     con_shape.push_back(sid);
     for (int v = b; v < b + V; ++v) {
       const int lab = (int)C.node_label[v];
-      auto it = slot_of.find(lab);
+      const bool ng = neg_of[lab];
+      auto it = slot_of.find(slot_key(lab, ng));
       int slot;
       if (it == slot_of.end()) {
         slot = (int)slot_of.size();
-        slot_of.emplace(lab, slot);
-        C.slot_label.push_back(lab);
+        slot_of.emplace(slot_key(lab, ng), slot);
+        C.slot_label.push_back(ng ? (int32_t)((uint32_t)lab | 0x80000000u) : lab);
         chunk_terms += atom_terms(lab);
         if (lab >= C.n_bool)
           for (int e = C.atom_ptr[lab - C.n_bool]; e < C.atom_ptr[lab - C.n_bool + 1]; ++e)
@@ -416,13 +421,16 @@ static bool build_chunks(const Problem& P, Compiled& C, int slot_limit) {
       } else {
         slot = it->second;
       }
-      C.cnode_slot.push_back((uint32_t)slot | (neg_of[lab] ? 0x80000000u : 0u));
-      // children: decision nodes keep their index; the TRUE / FALSE terminals become
-      // the fixed rows tnode / tnode + 1 after the largest diagram's nodes
+      C.cnode_slot.push_back((uint32_t)slot);
+      // children in literal space (hi: the literal holds), so a negated literal's
+      // node has them swapped; decision nodes keep their index, the TRUE / FALSE
+      // terminals become the fixed rows tnode / tnode + 1 after the largest diagram's nodes
       auto child = [&](uint32_t x) {
         return x < (uint32_t)V ? x : (x == (uint32_t)V ? (uint32_t)tnode : (uint32_t)tnode + 1);
       };
-      C.cnode_hilo.push_back(child(C.node_hilo[v] & 0xffffu) | (child(C.node_hilo[v] >> 16) << 16));
+      uint32_t h = child(C.node_hilo[v] & 0xffffu), l = child(C.node_hilo[v] >> 16);
+      if (ng) std::swap(h, l);
+      C.cnode_hilo.push_back(h | (l << 16));
     }
     if ((int)slot_of.size() > slot_limit || chunk_terms > kChunkMaxTerms || (int)real_of.size() > kChunkMaxReals)
       return false;

@@ -56,52 +56,131 @@ Nvrtc& nvrtc() {
   return n;
 }
 
-// Alg. 3 / Alg. 4 for one shape, straight-line.  Node v tests literal l_v with
-// probability q_v (= p or 1 - p for a negated literal); its children (hi = l_v
-// true) are nodes, or V (TRUE) / V+1 (FALSE).  Nodes testing the same variable
-// form a group (grp = its first node), so the shape fixes which nodes read
-// which variable.  Each pass reads a group's slot word and q from shared
-// memory once, at the group's first node in that pass's order; the messages
-// t_v (Alg. 3) and b_v (Alg. 4) live in registers; the reverse pass sums
-// t_v (b_hi - b_lo) over a group and issues the one shared-memory update of
-// its slot at the group's last node.  Short live ranges keep the routine
-// within the 64 registers of the 1024-thread kernel.
+// Alg. 3 / Alg. 4 for one shape, straight-line, one restart of the lane at a
+// time (the RPL restarts in turn).  Node v tests a literal whose probability q
+// comes from its slot; its children (hi: the literal holds) are nodes, or V
+// (TRUE) / V+1 (FALSE).  Nodes testing the same literal form a group (grp = its
+// first node); each pass reads a group's slot word and q from shared memory
+// once, at the group's first node in that pass's order.  The messages t_v
+// (Alg. 3) and b_v (Alg. 4) live in registers, and the reverse pass sums
+// t_v (b_hi - b_lo) over a group and issues the group's one shared-memory
+// update at its last node.  The terminals' messages are constants, and every
+// operation with a constant operand is folded as the code is generated.
+namespace {
+struct Ex {  // a message: 0, 1, -1 or a named value
+  enum Kind { ZERO, ONE, MONE, VAR } k;
+  std::string n;
+};
+struct Emitter {
+  std::ostringstream& o;
+  int tmp = 0;
+  std::string name(const Ex& e) const {
+    return e.k == Ex::ZERO ? "zero" : e.k == Ex::ONE ? "one" : e.k == Ex::MONE ? "mone" : e.n;
+  }
+  Ex emit(const std::string& expr) {
+    const std::string n = "e" + std::to_string(tmp++);
+    o << "    const V " << n << " = " << expr << ";\n";
+    return {Ex::VAR, n};
+  }
+  Ex neg(const Ex& x) {
+    if (x.k == Ex::ZERO) return x;
+    if (x.k == Ex::ONE) return {Ex::MONE, ""};
+    if (x.k == Ex::MONE) return {Ex::ONE, ""};
+    return emit("vsub(zero, " + x.n + ")");
+  }
+  Ex add(const Ex& a, const Ex& x) {
+    if (x.k == Ex::ZERO) return a;
+    if (a.k == Ex::ZERO) return x;
+    if (x.k == Ex::MONE) return emit("vsub(" + name(a) + ", one)");
+    return emit("vadd(" + name(a) + ", " + name(x) + ")");
+  }
+  Ex sub(const Ex& a, const Ex& x) {
+    if (x.k == Ex::ZERO) return a;
+    if (a.k == Ex::ZERO) return neg(x);
+    if (a.k == Ex::ONE && x.k == Ex::ONE) return {Ex::ZERO, ""};
+    return emit("vsub(" + name(a) + ", " + name(x) + ")");
+  }
+  Ex mul(const Ex& x, const Ex& y) {
+    if (x.k == Ex::ZERO || y.k == Ex::ZERO) return {Ex::ZERO, ""};
+    if (x.k == Ex::ONE) return y;
+    if (y.k == Ex::ONE) return x;
+    if (x.k == Ex::MONE) return neg(y);
+    if (y.k == Ex::MONE) return neg(x);
+    return emit("vmul(" + x.n + ", " + y.n + ")");
+  }
+  Ex fma(const Ex& x, const Ex& y, const Ex& a) {  // a + x y
+    if (x.k != Ex::VAR || y.k != Ex::VAR) {
+      if (x.k == Ex::ONE) return add(a, y);
+      if (y.k == Ex::ONE) return add(a, x);
+      if (x.k == Ex::MONE) return sub(a, y);
+      if (y.k == Ex::MONE) return sub(a, x);
+      return a;  // a zero factor
+    }
+    if (a.k == Ex::ZERO) return mul(x, y);
+    return emit("vfma(" + x.n + ", " + y.n + ", " + name(a) + ")");
+  }
+};
+}  // namespace
+
 std::string shape_routine(int rank, int V, const uint16_t* hi, const uint16_t* lo, const uint16_t* grp) {
   std::ostringstream o;
-  auto bu = [&](int c) -> std::string {  // m_bu of a child
-    if (c == V) return "1.f";
-    if (c == V + 1) return "0.f";
-    return "b" + std::to_string(c);
-  };
   std::vector<int> last(V, -1);  // last node of each group, by index
   for (int v = 0; v < V; ++v) last[grp[v]] = v;
+  auto load = [&](int g) { return "s_p[(nd[" + std::to_string(g) + "].x * RPL + k) * 32 + lane]"; };
   o << "template <bool ADJ, int RPL>\n__device__ __forceinline__ void shape_" << rank
     << "(const uint2* __restrict__ nd, const float* __restrict__ s_p, float* __restrict__ s_g, int lane,"
-       " const Pack<RPL>& wc, Pack<RPL>& cp) {\n";
-  o << "#pragma unroll\n  for (int k = 0; k < RPL; ++k) {\n";
-  o << "    float t0 = 1.f";
-  for (int v = 1; v < V; ++v) o << ", t" << v << " = 0.f";
-  o << ";\n    if (ADJ) {\n";
-  for (int v = 0; v < V; ++v) {  // Alg. 3: push to non-terminal children
-    const int g = grp[v];
-    if (g == v) o << "      const float f" << g << " = lit_q<RPL>(nd[" << g << "].x, s_p, lane, k);\n";
-    if (hi[v] < V) o << "      t" << hi[v] << " = fmaf(f" << g << ", t" << v << ", t" << hi[v] << ");\n";
-    if (lo[v] < V) o << "      t" << lo[v] << " = fmaf(1.f - f" << g << ", t" << v << ", t" << lo[v] << ");\n";
+       " const Pack<RPL>& wc, Pack<RPL>& cp) {\n"
+       "  using V = float;\n  const V zero = 0.f, one = 1.f, mone = -1.f;\n#pragma unroll\n"
+       "  for (int k = 0; k < RPL; ++k) {\n";
+  for (int adj = 1; adj >= 0; --adj) {
+    o << (adj ? "  if (ADJ) {\n" : "  } else {\n");
+    Emitter E{o};
+    std::vector<Ex> t(V, Ex{Ex::ZERO, ""});
+    if (adj) {
+      o << "    const V wv = wc.v[k];\n";
+      t[0] = {Ex::ONE, ""};
+      std::vector<int> loaded(V, 0);
+      for (int v = 0; v < V; ++v) {  // Alg. 3: push to non-terminal children
+        const int g = grp[v];
+        if (hi[v] >= V && lo[v] >= V) continue;
+        if (!(loaded[g] & 1)) {
+          o << "    const V f" << g << " = " << load(g) << ";\n";
+          loaded[g] |= 1;
+        }
+        const Ex q{Ex::VAR, "f" + std::to_string(g)};
+        if (hi[v] < V) t[hi[v]] = E.fma(q, t[v], t[hi[v]]);
+        if (lo[v] < V) {
+          if (!(loaded[g] & 2)) {
+            o << "    const V nf" << g << " = vsub(one, f" << g << ");\n";
+            loaded[g] |= 2;
+          }
+          t[lo[v]] = E.fma({Ex::VAR, "nf" + std::to_string(g)}, t[v], t[lo[v]]);
+        }
+      }
+    }
+    std::vector<Ex> bm(V), acc(V, Ex{Ex::ZERO, ""});
+    auto bu = [&](int ch) -> Ex {
+      if (ch == V) return {Ex::ONE, ""};
+      if (ch == V + 1) return {Ex::ZERO, ""};
+      return bm[ch];
+    };
+    for (int v = V - 1; v >= 0; --v) {  // Alg. 4, and the adjoint sum of each group
+      const int g = grp[v];
+      if (last[g] == v) o << "    const V q" << g << " = " << load(g) << ";\n";
+      const Ex q{Ex::VAR, "q" + std::to_string(g)};
+      const Ex d = E.sub(bu(hi[v]), bu(lo[v]));
+      bm[v] = E.fma(q, d, bu(lo[v]));
+      if (adj) {
+        acc[g] = E.fma(t[v], d, acc[g]);
+        if (g == v && acc[g].k != Ex::ZERO) {
+          const Ex gw = E.mul({Ex::VAR, "wv"}, acc[g]);  // emitted before the line that uses it
+          o << "    atomicAdd(s_g + (nd[" << g << "].x * RPL + k) * 32 + lane, " << E.name(gw) << ");\n";
+        }
+      }
+    }
+    o << "    cp.v[k] = " << E.name(bm[0]) << ";\n";
   }
-  o << "    }\n";
-  for (int v = V - 1; v >= 0; --v) {  // Alg. 4, and the adjoint sum of each group
-    const int g = grp[v];
-    if (last[g] == v)
-      o << "    const float q" << g << " = lit_q<RPL>(nd[" << g << "].x, s_p, lane, k);\n    float acc" << g << " = 0.f;\n";
-    o << "    const float d" << v << " = " << bu(hi[v]) << " - " << bu(lo[v]) << ";\n";
-    o << "    const float b" << v << " = fmaf(q" << g << ", d" << v << ", " << bu(lo[v]) << ");\n";
-    o << "    if (ADJ) acc" << g << " = fmaf(t" << v << ", d" << v << ", acc" << g << ");\n";
-    if (g == v)
-      o << "    if (ADJ) {\n      const unsigned r = nd[" << g << "].x;\n"
-        << "      atomicAdd(s_g + ((int)(r & 0x7fffffffu) * RPL + k) * 32 + lane, (r >> 31) ? -wc.v[k] * acc" << g
-        << " : wc.v[k] * acc" << g << ");\n    }\n";
-  }
-  o << "    cp.v[k] = b0;\n  }\n}\n\n";
+  o << "  }\n  }\n}\n\n";
   return o.str();
 }
 
@@ -112,9 +191,6 @@ std::string kernel_name(int wide, int adj, int rpl) {
 std::string generated_source(const Compiled& C) {
   std::ostringstream o;
   o << "#define FSMT_JIT_SHAPES 1\n" << kJitDevviewSrc << "\n" << kJitChunkedSrc << "\nnamespace fsmt {\n\n";
-  o << "// probability of the literal a node tests: p of its slot, or 1 - p when negated (bit 31)\n"
-       "template <int RPL>\n__device__ __forceinline__ float lit_q(unsigned r, const float* __restrict__ s_p, int lane,"
-       " int k) {\n  const float p = s_p[((r & 0x7fffffffu) * RPL + k) * 32 + lane];\n  return (r >> 31) ? 1.f - p : p;\n}\n\n";
   for (size_t k = 0; k < C.jit_shape.size(); ++k) {
     const int x = C.jit_shape[k];
     const int b = C.shape_ptr[x], V = C.shape_ptr[x + 1] - b;
@@ -152,6 +228,7 @@ std::unordered_map<std::string, Module> g_modules;  // by source text; kept for 
 // error message).
 bool jit_build(Compiled& C) {
   for (auto& r : C.jit_kernel) r[0] = r[1] = nullptr;
+  for (auto& r : C.jit_wide) r[0] = r[1] = nullptr;
   C.jit_shapes = 0;
   const char* off = std::getenv("FSMT_NO_JIT");
   if ((off && *off && *off != '0') || C.jit_shape.empty() || !C.chunked_ok) return false;
