@@ -51,7 +51,11 @@ def parse():
     p.add_argument("--workload", default="large_scheduling", choices=list(WORKLOADS))
     p.add_argument("--iters", type=int, default=20, help="PGD iterations per stage (step)")
     p.add_argument("--eta", type=float, default=None)
-    p.add_argument("--tts", type=float, default=0.0, help="time-to-SAT budget in seconds per form (0 = skip)")
+    p.add_argument("--tts", type=float, default=150.0,
+                   help="time-to-SAT budget in seconds per form (0 = skip)")
+    p.add_argument("--tts-plain", action="store_true", help="also time-to-SAT in the plain (unfused) form")
+    p.add_argument("--tts-eta", type=float, default=0.2)
+    p.add_argument("--tts-iters", type=int, default=100, help="PGD iterations per stage in the time-to-SAT runs")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--roofline-launches", type=int, default=10)
     return p.parse_args()
@@ -62,6 +66,27 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def replica_seed(rank):
+    """Restart seed of a replica: every rank draws its own initial points."""
+    return 7 + 1000 * rank
+
+
+def max_over_ranks(x, device="cpu"):
+    """Max of a number over the ranks of the default process group (x itself without one)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, ws, ms):
+    """Units of all ranks per second over the slowest rank's time (weak scaling)."""
+    return units_per_rank * ws / (ms / 1000.0)
 
 
 class Clocks:
@@ -218,7 +243,7 @@ def our_arm(args):
     comp.upload()
     info = comp.info
     eta = args.eta if args.eta is not None else 0.02
-    a0, b0 = W.initial_point(inst, R, seed=7 + 1000 * rank)
+    a0, b0 = W.initial_point(inst, R, seed=replica_seed(rank))
     S = Solver(P, comp, R, eta=eta, b_scale=inst.scale, t_max=args.iters, sweeps=20, use_graph=True)
     S.reset(a0, b0)
     sched = [inst.scale / (0.1 * t) for t in range(1, 21)]
@@ -245,13 +270,9 @@ def our_arm(args):
     ms = e0.elapsed_time(e1)
     # a stage stops early only when every restart has converged: count what ran
     iters_per_step = int(S.iters.max().item())
-    if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dev)
     clk = clocks.stop()
-    visits = nodes * R * iters_per_step * args.steps * ws
-    value = visits / (ms / 1000.0)
+    value = whole_job_rate(nodes * R * iters_per_step * args.steps, ws, ms)
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     a_h = torch.from_numpy(a0).pin_memory()
@@ -262,8 +283,8 @@ def our_arm(args):
     t0 = time.perf_counter()
     for k in range(args.steps):
         S.stage_host(sched[k % len(sched)], k + 1, a_h.numpy(), b_h.numpy(), nu_h.numpy(), ob_h.numpy())
-    e2e_s = time.perf_counter() - t0
-    e2e_value = nodes * R * args.iters * args.steps * ws / e2e_s
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dev)
+    e2e_value = whole_job_rate(nodes * R * iters_per_step * args.steps, ws, 1000.0 * e2e_s)
     h2d = (inst.n_bool + inst.n_real) * R * 4
     d2h = R * 8
 
@@ -330,14 +351,25 @@ def our_arm(args):
     except Exception as e:  # report, never hide
         plain = {"error": str(e)}
 
+    # time to the first exactly verified SAT: Alg. 2 from the same initial points,
+    # the schedule 1/sigma = 0.1, 0.2, ... in units of the instance scale,
+    # continued past 2.0 until SAT or the time limit
     tts = None
     if args.tts > 0:
-        S.reset(a0, b0)
-        S.t_max = 200
-        res = S.anneal(sched, time_limit=args.tts)
-        tts = {"fused": {"sat": res["sat"], "seconds": res["seconds"], "stage": res["stage"],
-                         "restart": res["restart"]}}
-        S.t_max = args.iters
+        tts = {"eta": args.tts_eta, "iters_per_stage": args.tts_iters, "limit_s": args.tts}
+        sched_tts = [inst.scale / (0.1 * t) for t in range(1, 1001)]
+        for form in ("fused", "plain") if args.tts_plain else ("fused",):
+            S2 = Solver(P, comp, R, eta=args.tts_eta, b_scale=inst.scale, t_max=args.tts_iters, sweeps=20,
+                        use_graph=True, form=form)
+            S2.reset(a0, b0)
+            torch.cuda.synchronize()
+            res = S2.anneal(sched_tts, time_limit=args.tts)
+            rec = {"sat": res["sat"], "seconds": res["seconds"], "stage": res["stage"], "restart": res["restart"]}
+            if res["sat"]:
+                rec["inv_sigma_over_scale"] = round(0.1 * res["stage"], 1)
+            tts[form] = rec
+            del S2
+            torch.cuda.empty_cache()
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

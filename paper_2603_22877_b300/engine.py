@@ -272,11 +272,20 @@ class Solver:
     Each sigma stage is one fsmt_solve_stage call (a CUDA graph when use_graph);
     restarts whose check reports #Unsat = 0 are re-verified exactly on the host
     before SAT is reported.
+
+    form="plain" runs the same stage as separate library calls issued from
+    Python per iteration (plain forward and adjoint kernels with the top-down
+    messages in device memory, the PGD step, the convergence test), no graph:
+    the unfused form, for comparison.
     """
 
     def __init__(self, problem, compiled, R, eta, b_scale, eps=1e-2, t_max=200, sweeps=20, rho=0.5, gamma=2.0,
-                 tau=1, use_graph=True, polish=32, normalize_eta=True, device="cuda"):
+                 tau=1, use_graph=True, polish=32, normalize_eta=True, device="cuda", form="fused"):
         import torch
+        if form not in ("fused", "plain"):
+            raise ValueError("form is 'fused' or 'plain'")
+        self.form = form
+        self._work = None
         self.problem, self.comp, self.R = problem, compiled, int(R)
         if not compiled.uploaded:
             compiled.upload()
@@ -317,8 +326,36 @@ class Solver:
                              int(bool(self.use_graph)), int(self.polish), int(bool(self.normalize_eta)))
 
     def stage(self, sigma, t, stream=None):
+        if self.form == "plain":
+            return self._stage_plain(sigma, t, stream)
         cfg = self.config(sigma, t)
         L.call("fsmt_solve_stage", self.comp.h, C.byref(cfg), C.byref(self._state), _stream(stream))
+
+    def _stage_plain(self, sigma, t, stream=None):
+        """One stage of Alg. 2 in the plain form; the same steps as fsmt_solve_stage."""
+        import torch
+        comp, R = self.comp, self.R
+        if self._work is None:
+            self._work = torch.empty(comp.plain_work(R), device=self.a.device, dtype=torch.float32)
+        comp.weight_sum(R, self.w, self.wsum, stream)
+        self.active.fill_(1)
+        self.iters.zero_()
+        eps2 = float(self.eps) ** 2
+        for _ in range(int(self.t_max)):
+            comp.forward_plain(R, sigma, self.w, self.a, self.b, self._work, obj=self.obj, stream=stream)
+            comp.adjoint_plain(R, sigma, self.w, self.a, self.b, self._work, self.grad_a, self.grad_b, stream=stream)
+            self.gnorm2.zero_()
+            comp.pgd_step(R, self.eta, self.b_scale, self.sweeps, self.a, self.b, self.grad_a, self.grad_b,
+                          self.gnorm2, active=self.active, wsum=self.wsum if self.normalize_eta else None,
+                          polish=self.polish, stream=stream)
+            act = self.active.bool()
+            self.iters += act.to(torch.int32)
+            done = act & ((self.gnorm2 <= eps2) | torch.isnan(self.gnorm2))
+            self.active.masked_fill_(done, 0)
+            if not bool(self.active.any()):
+                break
+        comp.round_check(R, self.a, self.b, self.n_unsat, w=self.w, h=self.h, rho=self.rho, gamma=self.gamma,
+                         update_w=(t % self.tau == 0), stream=stream)
 
     def stage_host(self, sigma, t, a_host, b_host, n_unsat_host, obj_host, stream=None):
         """The same stage with host input/output buffers (copies inside the call)."""

@@ -106,15 +106,16 @@ def _solver(inst, R, comp, P, **kw):
     return Solver(P, comp, R, **kw)
 
 
-@pytest.mark.parametrize("use_graph", [True, False])
-def test_stage_matches_oracle_first_iterations(use_graph):
-    """A stage of 5 PGD iterations then round/check/ERWA: GPU vs oracle run_stage."""
+@pytest.mark.parametrize("use_graph,form", [(True, "fused"), (False, "fused"), (False, "plain")])
+def test_stage_matches_oracle_first_iterations(use_graph, form):
+    """A stage of 5 PGD iterations then round/check/ERWA: GPU vs oracle run_stage,
+    for the fused stage (graph or not) and the plain form driven call by call."""
     inst = W.jobshop(1002, 10, 5)
     R = 40
     P, comp, a, b, _ = setup(inst, R)
     eta = 0.02
     cfg = pgd.Config(eta=eta, t_max=5, sweeps=20, polish=32)
-    S = _solver(inst, R, comp, P, eta=eta, b_scale=inst.scale, t_max=5, sweeps=20, use_graph=use_graph)
+    S = _solver(inst, R, comp, P, eta=eta, b_scale=inst.scale, t_max=5, sweeps=20, use_graph=use_graph, form=form)
     S.reset(a, b)
     sigma = sigmas_for(inst)[0]
     S.stage(sigma, 1)
@@ -132,16 +133,18 @@ def test_stage_matches_oracle_first_iterations(use_graph):
     assert (S.h.cpu().numpy() == 1.0).all()
 
 
-def test_stage_epsilon_rule_stops_restarts():
+@pytest.mark.parametrize("form", ["fused", "plain"])
+def test_stage_epsilon_rule_stops_restarts(form):
     """With eps large every restart stops after its first iteration (Eq. critical)."""
     inst = W.tiny_random(1001)
     R = 50
     P, comp, a, b, _ = setup(inst, R)
-    S = _solver(inst, R, comp, P, eta=0.01, b_scale=inst.scale, t_max=7, eps=1e6)
+    S = _solver(inst, R, comp, P, eta=0.01, b_scale=inst.scale, t_max=7, eps=1e6, form=form)
     S.reset(a, b)
     S.stage(sigmas_for(inst)[0], 1)
     assert (S.iters.cpu().numpy() == 1).all()
-    assert int(S.ctl[0].item()) == 0 and int(S.ctl[1].item()) == 0
+    if form == "fused":
+        assert int(S.ctl[0].item()) == 0 and int(S.ctl[1].item()) == 0
 
 
 def test_stage_host_buffers_match_device():
