@@ -107,6 +107,10 @@ template <int RPL>
 struct __align__(4 * RPL) Pack {
   float v[RPL];
 };
+template <int N>
+struct IntC {
+  static constexpr int value = N;
+};
 
 // Arithmetic of the generated diagram routines: IEEE single operations, never
 // contracted with one another.
@@ -120,7 +124,7 @@ __device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b)
 // |e(x)| <= 1.5e-7 for x >= 0; erfc(-x) = 2 - erfc(x).  `ex` is e^{-x^2}.
 __device__ __forceinline__ float half_erfc_as(float x, float ex) {
   const float ax = fabsf(x);
-  const float t = __frcp_rn(fmaf(0.3275911f, ax, 1.f));
+  const float t = __fdividef(1.f, fmaf(0.3275911f, ax, 1.f));  // approximate reciprocal, 1 + 0.33|x| >= 1
   float poly = fmaf(t, 1.061405429f, -1.453152027f);
   poly = fmaf(t, poly, 1.421413741f);
   poly = fmaf(t, poly, -0.284496736f);
@@ -257,38 +261,49 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
           // over the terms; past the last restart b reads 0 and the adjoint is 0
           const int meta = s_meta[i], tb = meta >> 16, tc = meta & 0xffff;
           const float q0 = s_q0[i], si = s_si[i];
-          float zf[RPL], zp[RPL];
+          // NT terms known at compile time (2, the common case), or tc when NT = 0
+          auto atom = [&](auto ntc) {
+            constexpr int NT = decltype(ntc)::value;
+            const int nt = NT ? NT : tc;
+            float zf[RPL], zp[RPL];
 #pragma unroll
-          for (int k = 0; k < RPL; ++k) zf[k] = zp[k] = -q0;
-          for (int j = 0; j < tc; ++j) {
-            const float cj = s_tcoef[tb + j];
-            const int o = s_tvar[tb + j] * RPL * 32 + lane;
+            for (int k = 0; k < RPL; ++k) zf[k] = zp[k] = -q0;
 #pragma unroll
-            for (int k = 0; k < RPL; ++k) {
-              if (do_f) zf[k] = fmaf(cj, sbf[o + 32 * k], zf[k]);
-              if (do_p) zp[k] = fmaf(cj, sbp[o + 32 * k], zp[k]);
-            }
-          }
-          if (do_f) {  // dC/dz = dC/dq dq/dp dp/dz, then dC/db_j = dC/dz q_j into the chunk's reals
-            float gz[RPL];
-#pragma unroll
-            for (int k = 0; k < RPL; ++k) {
-              const float u = zf[k] * si;
-              gz[k] = sg * gi[32 * k] * (kTwoOverSqrtPi * si) * __expf(-u * u);
-            }
-            for (int j = 0; j < tc; ++j) {
+            for (int j = 0; j < nt; ++j) {
               const float cj = s_tcoef[tb + j];
               const int o = s_tvar[tb + j] * RPL * 32 + lane;
 #pragma unroll
-              for (int k = 0; k < RPL; ++k) atomicAdd(sgr + o + 32 * k, gz[k] * cj);
+              for (int k = 0; k < RPL; ++k) {
+                if (do_f) zf[k] = fmaf(cj, sbf[o + 32 * k], zf[k]);
+                if (do_p) zp[k] = fmaf(cj, sbp[o + 32 * k], zp[k]);
+              }
             }
-          }
-          if (do_p)
+            if (do_f) {  // dC/dz = dC/dq dq/dp dp/dz, then dC/db_j = dC/dz q_j into the chunk's reals
+              float gz[RPL];
 #pragma unroll
-            for (int k = 0; k < RPL; ++k) {
-              const float u = zp[k] * si;
-              pp.v[k] = half_erfc_as(sg * u, __expf(-u * u));  // 1 - erfc(u)/2 = erfc(-u)/2
+              for (int k = 0; k < RPL; ++k) {
+                const float u = zf[k] * si;
+                gz[k] = sg * gi[32 * k] * (kTwoOverSqrtPi * si) * __expf(-u * u);
+              }
+#pragma unroll
+              for (int j = 0; j < nt; ++j) {
+                const float cj = s_tcoef[tb + j];
+                const int o = s_tvar[tb + j] * RPL * 32 + lane;
+#pragma unroll
+                for (int k = 0; k < RPL; ++k) atomicAdd(sgr + o + 32 * k, gz[k] * cj);
+              }
             }
+            if (do_p)
+#pragma unroll
+              for (int k = 0; k < RPL; ++k) {
+                const float u = zp[k] * si;
+                pp.v[k] = half_erfc_as(sg * u, __expf(-u * u));  // 1 - erfc(u)/2 = erfc(-u)/2
+              }
+          };
+          if (tc == 2)
+            atom(IntC<2>{});
+          else
+            atom(IntC<0>{});
         } else {  // an atom with b in global memory, or sigma = 0
           const int meta = s_meta[i], tb = meta >> 16, tc = meta & 0xffff;
 #pragma unroll

@@ -247,8 +247,9 @@ bool jit_build(Compiled& C) {
     nvrtcProgram prog;
     if (N.create(&prog, src.c_str(), "fsmt_jit.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS) return false;
     const bool verbose = std::getenv("FSMT_JIT_VERBOSE") != nullptr;
-    const char* opts[] = {arch.c_str(), "-std=c++17", "-lineinfo", "--ptxas-options=-v"};
-    const nvrtcResult rc = N.compile(prog, verbose ? 4 : 3, opts);
+    // -default-device: the kernel body's generic lambdas are device code
+    const char* opts[] = {arch.c_str(), "-std=c++17", "-default-device", "-lineinfo", "--ptxas-options=-v"};
+    const nvrtcResult rc = N.compile(prog, verbose ? 5 : 4, opts);
     size_t ls = 0;
     N.log_size(prog, &ls);
     std::string log(ls, '\0');
