@@ -168,11 +168,13 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
   float* s_tcoef = reinterpret_cast<float*>(s_tvar + kChunkMaxTerms);
   int* s_rid = reinterpret_cast<int*>(s_tcoef + kChunkMaxTerms);  // the chunk's reals
   const int cap = d.chunk_slot_cap;
-  float* s_p = reinterpret_cast<float*>(s_rid + kChunkMaxReals);  // [slot][RPL][32]: probability of the literal
-  float* s_g = s_p + cap * RPL * 32;                               // [slot][RPL][32]: its adjoint
+  // per-slot rows of kSlotStride floats, restart k of lane l at 32 k + l; a node's
+  // slot word is the row's byte offset (slot * 4 * kSlotStride)
+  float* s_p = reinterpret_cast<float*>(s_rid + kChunkMaxReals);  // probability of the literal
+  float* s_g = s_p + cap * kSlotStride;                            // its adjoint
   // reals staged per restart tile (0: atoms read b from global memory instead)
   const int rcap = d.chunk_real_cap;
-  float* s_b = s_g + cap * RPL * 32;            // [tile parity][real][RPL][32]: b of the chunk's reals
+  float* s_b = s_g + cap * kSlotStride;         // [tile parity][real][RPL][32]: b of the chunk's reals
   float* s_gr = s_b + 2 * rcap * RPL * 32;      // [tile parity][real][RPL][32]: dC/db accumulators
   PK* s_rows = reinterpret_cast<PK*>(s_gr + 2 * rcap * RPL * 32);
   PK* s_m = s_rows + warp * rows * 32 + lane;
@@ -244,7 +246,7 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
       for (int i = warp; i < ns; i += W) {
         const int raw = s_lab[i], lab = raw & 0x7fffffff;
         const float sg = raw < 0 ? -1.f : 1.f;  // dq/dp
-        float* gi = s_g + i * RPL * 32 + lane;  // the slot's adjoint dC/dq, restart k at gi[32 k]
+        float* gi = s_g + i * kSlotStride + lane;  // the slot's adjoint dC/dq, restart k at gi[32 k]
         PK pp;
         if (lab < d.n_bool) {  // a Boolean: p = (1 - a) / 2
 #pragma unroll
@@ -340,7 +342,7 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
         if (do_p)
 #pragma unroll
           for (int k = 0; k < RPL; ++k) {
-            s_p[(i * RPL + k) * 32 + lane] = pp.v[k];
+            s_p[i * kSlotStride + 32 * k + lane] = pp.v[k];
             if (ADJ) gi[32 * k] = 0.f;
           }
       }
@@ -398,7 +400,7 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
               const int hi = (int)(e.y & 0xffffu) * 32, lo = (int)(e.y >> 16) * 32;
               PK p;
 #pragma unroll
-              for (int k = 0; k < RPL; ++k) p.v[k] = s_p[(e.x * RPL + k) * 32 + lane];
+              for (int k = 0; k < RPL; ++k) p.v[k] = s_p[(e.x >> 8) * kSlotStride + 32 * k + lane];
               const PK mv = s_m[v * 32];
               PK mh = s_m[hi], ml = s_m[lo];
 #pragma unroll
@@ -414,15 +416,15 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
           s_m[(vcap + 1) * 32] = zero;
           for (int v = V - 1; v >= 0; --v) {  // Alg. 4, reverse topological order
             const uint2 e = nd[v];
-            const int slot = (int)e.x;
+            const int slot = (int)(e.x >> 8);
             const PK mh = s_m[(int)(e.y & 0xffffu) * 32], ml = s_m[(int)(e.y >> 16) * 32];
             PK p;
 #pragma unroll
-            for (int k = 0; k < RPL; ++k) p.v[k] = s_p[(slot * RPL + k) * 32 + lane];
+            for (int k = 0; k < RPL; ++k) p.v[k] = s_p[slot * kSlotStride + 32 * k + lane];
             PK nb;
             if (ADJ) {
               const PK td = s_m[v * 32];
-              float* gs = s_g + slot * RPL * 32 + lane;
+              float* gs = s_g + slot * kSlotStride + lane;
 #pragma unroll
               for (int k = 0; k < RPL; ++k) {
                 const float diff = mh.v[k] - ml.v[k];

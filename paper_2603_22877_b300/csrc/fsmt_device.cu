@@ -25,7 +25,7 @@ constexpr int kSmemBudget = 112 * 1024;
 // shared memory of the chunked kernel without the per-warp message arrays
 inline size_t chunk_fixed_bytes(int rpl, int slot_cap) {
   return (size_t)kChunkMaxNodes * 8 + (size_t)kChunkMaxCons * 16 + (size_t)kChunkMaxSlots * 4 * 4 +
-         (size_t)kChunkMaxTerms * 8 + (size_t)kChunkMaxReals * 4 + (size_t)slot_cap * 32 * 4 * rpl * 2;
+         (size_t)kChunkMaxTerms * 8 + (size_t)kChunkMaxReals * 4 + (size_t)slot_cap * kSlotStride * 4 * 2;
 }
 constexpr size_t kSmemMax = 227 * 1024;
 

@@ -35,6 +35,7 @@ constexpr int kChunkMaxSlots = 320;  // distinct variables / atoms per chunk (ha
 // the slot limit when the generic DP path may run: its per-warp message rows
 // share shared memory with the slot arrays, so smaller chunks keep more warps
 constexpr int kChunkSlotsGeneric = 192;
+constexpr int kSlotStride = 64;  // floats per slot row of the per-slot shared arrays (two restarts x 32 lanes)
 constexpr int kChunkThreads = 512;  // threads of the chunked kernel with the generic path (16 warps)
 constexpr int kChunkMaxTerms = 768;  // nonzeros of the atoms of a chunk
 constexpr int kChunkMaxReals = 64;   // distinct reals of the atoms of a chunk

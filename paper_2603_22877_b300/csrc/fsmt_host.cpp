@@ -421,7 +421,7 @@ static bool build_chunks(const Problem& P, Compiled& C, int slot_limit) {
       } else {
         slot = it->second;
       }
-      C.cnode_slot.push_back((uint32_t)slot);
+      C.cnode_slot.push_back((uint32_t)slot * 4u * kSlotStride);  // the slot row's byte offset
       // children in literal space (hi: the literal holds), so a negated literal's
       // node has them swapped; decision nodes keep their index, the TRUE / FALSE
       // terminals become the fixed rows tnode / tnode + 1 after the largest diagram's nodes

@@ -126,11 +126,17 @@ std::string shape_routine(int rank, int V, const uint16_t* hi, const uint16_t* l
   std::ostringstream o;
   std::vector<int> last(V, -1);  // last node of each group, by index
   for (int v = 0; v < V; ++v) last[grp[v]] = v;
-  auto load = [&](int g) { return "s_p[(nd[" + std::to_string(g) + "].x * RPL + k) * 32 + lane]"; };
+  // a slot word is the byte offset of the slot's row; pb and gb point at the lane's
+  // first restart in the probability and adjoint rows of slot 0
+  auto load = [&](int g) {
+    return "*reinterpret_cast<const float*>(pb + nd[" + std::to_string(g) + "].x + 128 * k)";
+  };
   o << "template <bool ADJ, int RPL>\n__device__ __forceinline__ void shape_" << rank
     << "(const uint2* __restrict__ nd, const float* __restrict__ s_p, float* __restrict__ s_g, int lane,"
        " const Pack<RPL>& wc, Pack<RPL>& cp) {\n"
-       "  using V = float;\n  const V zero = 0.f, one = 1.f, mone = -1.f;\n#pragma unroll\n"
+       "  using V = float;\n  const V zero = 0.f, one = 1.f, mone = -1.f;\n"
+       "  const char* pb = reinterpret_cast<const char*>(s_p + lane);\n"
+       "  char* gb = reinterpret_cast<char*>(s_g + lane);\n#pragma unroll\n"
        "  for (int k = 0; k < RPL; ++k) {\n";
   for (int adj = 1; adj >= 0; --adj) {
     o << (adj ? "  if (ADJ) {\n" : "  } else {\n");
@@ -174,7 +180,7 @@ std::string shape_routine(int rank, int V, const uint16_t* hi, const uint16_t* l
         acc[g] = E.fma(t[v], d, acc[g]);
         if (g == v && acc[g].k != Ex::ZERO) {
           const Ex gw = E.mul({Ex::VAR, "wv"}, acc[g]);  // emitted before the line that uses it
-          o << "    atomicAdd(s_g + (nd[" << g << "].x * RPL + k) * 32 + lane, " << E.name(gw) << ");\n";
+          o << "    atomicAdd(reinterpret_cast<float*>(gb + nd[" << g << "].x + 128 * k), " << E.name(gw) << ");\n";
         }
       }
     }
