@@ -63,6 +63,23 @@ FusedShape fused_shape(const Compiled& C, int R) {
 __device__ __forceinline__ bool literal_truth_exact(const DevView& d, int lab, int R, int r,
                                                     const float* __restrict__ a, const float* __restrict__ b) {
   if (lab < d.n_bool) return __ldg(a + (size_t)lab * R + r) < 0.f;
+  // Floating-point filter: z = sum_t c_t y_t - q0 in FP32 (c_t exact, q0 rounded
+  // once) carries an error of at most (n + 2) u (sum_t |c_t y_t| + |q0|), u = 2^-24
+  // (Higham, Accuracy and Stability of Numerical Algorithms, 2nd ed., Sec. 3.1, for
+  // the n fused multiply-adds), plus 2^-149 per operation below the normal range.
+  // Outside that band the sign of z is certain and z != 0, so the atom holds iff
+  // z < 0 whatever its strictness; inside it the exact path decides.
+  const int i = lab - d.n_bool;
+  const int k0 = __ldg(d.atom_ptr + i), k1 = __ldg(d.atom_ptr + i + 1);
+  const float q0 = __ldg(d.atom_q0f + i);
+  float z = -q0, mag = fabsf(q0);
+  for (int k = k0; k < k1; ++k) {
+    const float c = __ldg(d.atom_coef + k), y = __ldg(b + (size_t)__ldg(d.atom_var + k) * R + r);
+    z = fmaf(c, y, z);
+    mag = fmaf(fabsf(c), fabsf(y), mag);
+  }
+  const float n = (float)(k1 - k0 + 4);  // two more terms than the bound for the rounding of mag itself
+  if (fabsf(z) > n * (5.9604645e-8f * mag + 1e-38f)) return z < 0.f;
   float p, gz;
   literal_prob(d, lab, R, r, true, 0.f, a, b, p, gz);
   return p > 0.5f;

@@ -145,3 +145,41 @@ def test_unstaged_and_generic_paths_agree(no_jit, no_stage, monkeypatch):
     np.testing.assert_allclose(obj, ref[0], rtol=1e-5, atol=1e-4)
     assert_grad_close(ga, ref[2], "grad_a")
     assert_grad_close(gb, ref[3], "grad_b")
+
+
+def test_round_check_filter_keeps_boundary_cases_exact():
+    """The check decides each atom with an FP32 filter and falls back to exact
+    arithmetic inside the filter's error band.  Points on an atom's boundary
+    (z = 0) and one float step to either side, with large integer coefficients,
+    strict and non-strict: the GPU's #Unsat and violations equal the oracle's
+    exact check restart by restart."""
+    import torch
+    from oracle import pgd
+    from paper_2603_22877_b300.engine import Problem
+    rng = np.random.default_rng(5)
+    B = W._Builder(0, 3)
+    # c0 y0 + c1 y1 + c2 y2 (rel) q0 with q0 the value at an integer point Y
+    Y = np.array([1234567.0, 89.0, 4097.0])
+    coefs = [[3, -7, 0], [1_000_003, 0, -2], [5, 11, -13], [-8_388_607, 1, 0]]
+    for cf in coefs:
+        var = [j for j in range(3) if cf[j] != 0]
+        c = [cf[j] for j in var]
+        q0 = int(sum(cf[j] * int(Y[j]) for j in var))
+        for rel in (W.LE, W.LT):
+            B.con(W.OR, [W.lit(B.atom(var, c, q0, rel))])
+    inst = B.freeze("boundary", np.full(3, -1e8), np.full(3, 1e8), [], Y, 1.0)
+    R = 96
+    b = np.repeat(Y.astype(np.float32)[:, None], R, axis=1)
+    for r in range(R):  # each restart moves some reals by -1, 0 or +1 float steps
+        steps = rng.integers(-1, 2, 3) if r else np.zeros(3, int)
+        for j in range(3):
+            for _ in range(abs(int(steps[j]))):
+                b[j, r] = np.nextafter(b[j, r], np.float32(np.inf) if steps[j] > 0 else np.float32(-np.inf))
+    comp = Problem.from_instance(inst).compile().upload()
+    nu = torch.zeros(R, dtype=torch.int32, device="cuda")
+    viol = torch.zeros((inst.n_cons, R), dtype=torch.uint8, device="cuda")
+    comp.round_check(R, torch.zeros((0, R), device="cuda"), torch.from_numpy(b).cuda(), nu, violated=viol)
+    _, ref = pgd.round_check(inst, np.zeros((0, R)), b.astype(np.float64))
+    np.testing.assert_array_equal(viol.cpu().numpy().astype(bool), ref)
+    np.testing.assert_array_equal(nu.cpu().numpy(), ref.sum(0))
+    assert ref[:, 0].sum() == len(coefs)  # at Y itself every strict atom fails and every non-strict holds
