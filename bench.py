@@ -247,6 +247,7 @@ def our_arm(args):
     S = Solver(P, comp, R, eta=eta, b_scale=inst.scale, t_max=args.iters, sweeps=20, use_graph=True)
     S.reset(a0, b0)
     sched = [inst.scale / (0.1 * t) for t in range(1, 21)]
+    launch = S.tune(sched[0]).as_dict()  # autotuned kernel configuration (fsmt_autotune)
     stream = torch.cuda.current_stream()
     nodes = info["n_obj_nodes"]
 
@@ -391,7 +392,7 @@ def our_arm(args):
                            "n_obj_cons": info["n_obj_cons"], "n_obj_nodes": nodes, "atoms": inst.n_atoms,
                            "iters_per_step": iters_per_step, "eta": eta, "form": "fused + CUDA graph",
                            "l2": "inputs larger than L2 (diagrams + weights > 126 MB)",
-                           "compile_s": compile_s, "parallelism": f"replicas x{ws}"},
+                           "compile_s": compile_s, "parallelism": f"replicas x{ws}", "launch": launch},
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches_per_step * args.steps, "clocks": clk, "plain": plain,

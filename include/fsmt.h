@@ -81,6 +81,25 @@ typedef struct {
   int32_t reserved;
 } fsmt_info;
 
+/* One way to run the forward (+ adjoint) pass of C_sigma on an instance at R
+ * restarts (fsmt_launch_configs, fsmt_select_config, fsmt_autotune).  The
+ * paper fixes none of this: it is the kernel's tile (restarts per lane) and
+ * work split (warps per CTA, which kernel, whether a chunk's reals are staged
+ * in shared memory). */
+enum { FSMT_VARIANT_WARP = 0,     /* one warp per constraint */
+       FSMT_VARIANT_CHUNKED = 1,  /* chunked kernel compiled ahead of time (generic diagram pass) */
+       FSMT_VARIANT_JIT = 2,      /* chunked kernel with run-time generated per-shape routines */
+       FSMT_VARIANT_WIDE = 3 };   /* the same without the generic pass: every constraint has a routine */
+typedef struct {
+  int32_t variant;         /* FSMT_VARIANT_* */
+  int32_t restarts_per_lane;
+  int32_t staged_reals;    /* reals of a chunk staged in shared memory per restart tile (0: none) */
+  int32_t warps;           /* per CTA */
+  int64_t smem_bytes;      /* dynamic shared memory per CTA */
+  float ms;                /* fsmt_autotune: measured time of one forward + adjoint (else 0) */
+  int32_t reserved;
+} fsmt_launch_config;
+
 /* ---------------------------------------------------------------- problem --
  * Builds the constraint set C of Alg. 1 / Alg. 2 (Results "Satisfiability
  * Modulo Theories": F is the conjunction of constraints over Booleans x and
@@ -191,6 +210,29 @@ fsmt_status fsmt_forward(const fsmt_compiled* c, int32_t R, float sigma, const f
  * cop[n_cons][R] as in fsmt_forward (may be NULL).  Errors as fsmt_forward. */
 fsmt_status fsmt_adjoint(const fsmt_compiled* c, int32_t R, float sigma, const float* w, const float* a,
                          const float* b, float* grad_a, float* grad_b, float* obj, float* cop, void* stream);
+
+/* The configurations that can run this instance at R restarts, the default
+ * first.  Writes min(cap, count) of them to out (device-free; out may be NULL
+ * with cap 0 to count) and the count to *n.  ESTATE before fsmt_upload (the
+ * run-time compiled kernels are known only then), EINVAL on R < 1. */
+fsmt_status fsmt_launch_configs(const fsmt_compiled* c, int32_t R, fsmt_launch_config* out, int32_t cap,
+                                int32_t* n);
+
+/* Pins one of fsmt_launch_configs' configurations (matched on variant,
+ * restarts_per_lane and staged_reals) for later fsmt_forward, fsmt_adjoint and
+ * stages at this R; cfg NULL returns to the default.  EINVAL if it is not one
+ * of them.  A stage graph captured before is re-captured. */
+fsmt_status fsmt_select_config(fsmt_compiled* c, int32_t R, const fsmt_launch_config* cfg);
+
+/* Autotuner: times every configuration of fsmt_launch_configs on the caller's
+ * inputs (one warm-up and three timed forward + adjoint passes each, CUDA
+ * events on `stream`) and pins the fastest as fsmt_select_config does.
+ * grad_a, grad_b and obj are scratch of fsmt_adjoint's shapes, zero on return.
+ * The chosen configuration, with its time, goes to *best (may be NULL).
+ * Synchronises the stream.  Errors as fsmt_adjoint. */
+fsmt_status fsmt_autotune(fsmt_compiled* c, int32_t R, float sigma, const float* w, const float* a,
+                          const float* b, float* grad_a, float* grad_b, float* obj, fsmt_launch_config* best,
+                          void* stream);
 
 /* Plain (unfused) form of the same two passes, for comparison: separate
  * kernels for the atom probabilities, the forward pass (which stores every

@@ -47,6 +47,18 @@ class StageConfig(C.Structure):
 P = C.c_void_p
 i32, i64, f32, f64 = C.c_int32, C.c_int64, C.c_float, C.c_double
 
+class LaunchConfig(C.Structure):
+    _fields_ = [("variant", C.c_int32), ("restarts_per_lane", C.c_int32), ("staged_reals", C.c_int32),
+                ("warps", C.c_int32), ("smem_bytes", C.c_int64), ("ms", C.c_float), ("reserved", C.c_int32)]
+
+    VARIANTS = {0: "warp", 1: "chunked", 2: "jit", 3: "wide"}
+
+    def as_dict(self):
+        return {"variant": self.VARIANTS.get(self.variant, str(self.variant)),
+                "restarts_per_lane": self.restarts_per_lane, "staged_reals": self.staged_reals,
+                "warps": self.warps, "smem_bytes": self.smem_bytes, "ms": self.ms}
+
+
 PROTOTYPES = {
     "fsmt_problem_create": [i32, i32, C.POINTER(P)],
     "fsmt_set_real_bounds": [P, i32, f64, f64],
@@ -64,6 +76,9 @@ PROTOTYPES = {
     "fsmt_free_compiled": [P],
     "fsmt_forward": [P, i32, f32, P, P, P, P, P, P],
     "fsmt_adjoint": [P, i32, f32, P, P, P, P, P, P, P, P],
+    "fsmt_launch_configs": [P, i32, C.POINTER(LaunchConfig), i32, C.POINTER(i32)],
+    "fsmt_select_config": [P, i32, C.POINTER(LaunchConfig)],
+    "fsmt_autotune": [P, i32, f32, P, P, P, P, P, P, C.POINTER(LaunchConfig), P],
     "fsmt_plain_work_floats": [P, i32, C.POINTER(i64)],
     "fsmt_forward_plain": [P, i32, f32, P, P, P, P, P, P, P],
     "fsmt_adjoint_plain": [P, i32, f32, P, P, P, P, P, P, P],

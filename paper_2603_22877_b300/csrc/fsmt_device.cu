@@ -16,6 +16,8 @@
 #include "fsmt_internal.h"
 #include "fsmt_chunked.cuh"
 
+int fsmt_fused_limit_ok(const fsmt::Compiled& C);  // below
+
 namespace fsmt {
 
 namespace {
@@ -35,6 +37,7 @@ fsmt_status cuda_fail(cudaError_t e, const char* what) {
   set_error(std::string(what) + ": " + cudaGetErrorString(e));
   return FSMT_ECUDA;
 }
+fsmt_status cuda_ok(cudaError_t e, const char* what) { return e == cudaSuccess ? FSMT_OK : cuda_fail(e, what); }
 
 #define FSMT_CUDA(call, what)                      \
   do {                                             \
@@ -651,79 +654,114 @@ fsmt_status launch_fused_warp(const Compiled& C, bool adj, int R, float sigma, c
   return FSMT_OK;
 }
 
-// restarts per lane, warps and staged reals of the chunked kernel for this
-// instance (warps 0: it cannot run it)
-struct ChunkShape {
-  int rpl, warps, real_cap;
-  size_t smem;
-};
 // shared memory of the staged reals: b and dC/db, two tiles each
 inline size_t staged_bytes(int rpl, int real_cap) { return (size_t)real_cap * rpl * 32 * 4 * 4; }
-ChunkShape chunk_shape(const Compiled& C, int R) {
-  ChunkShape s{R > 32 ? 2 : 1, 0, 0, 0};
-  if (!C.chunked_ok) return s;
-  const int vcap = std::max(1, C.max_nodes);
+
+// The ways to run the forward (+ adjoint) pass on an instance at R restarts
+// (the autotuner's candidates), in the order of the default choice.
+std::vector<LaunchCfg> launch_candidates(const Compiled& C, int R) {
+  std::vector<LaunchCfg> out;
+  if (C.n_obj == 0) return out;
   const size_t obj_bytes = R <= kMaxObjSmemR ? (size_t)R * 4 : 0;
-  // two restarts per lane while that leaves at least 8 warps, else one; staged
-  // reals while they leave at least 8 warps
-  for (int rpl = s.rpl; rpl >= 1; --rpl)
-    for (int rc : {C.stage_reals ? C.chunk_real_max : 0, 0}) {
-      const size_t per_warp = (size_t)(vcap + 2) * 32 * 4 * rpl;
-      const size_t fixed = chunk_fixed_bytes(rpl, C.chunk_slot_cap) + staged_bytes(rpl, rc) + obj_bytes;
-      if (fixed + 4 * per_warp > kSmemMax) continue;
-      const int warps = (int)std::min<size_t>(kChunkThreads / 32, (kSmemMax - fixed) / per_warp);
-      if (warps > s.warps) s = {rpl, warps, rc, fixed + (size_t)warps * per_warp};
-      if (s.warps >= 8) return s;
+  const int vcap = std::max(1, C.max_nodes);
+  const int rmax = C.stage_reals ? C.chunk_real_max : 0;
+  if (C.chunked_ok) {
+    for (int rpl = R > 32 ? 2 : 1; rpl >= 1; --rpl)  // generated routines, no generic path: 32 warps
+      if (C.jit_wide[1][rpl - 1])
+        for (int rc : {rmax, 0}) {
+          const size_t smem = chunk_fixed_bytes(rpl, C.chunk_slot_cap) + staged_bytes(rpl, rc) + obj_bytes;
+          if (smem <= kSmemMax) out.push_back({kVariantWide, rpl, rc, kChunkThreadsWide / 32, smem});
+          if (rc == 0) break;
+        }
+    for (int rpl = R > 32 ? 2 : 1; rpl >= 1; --rpl)  // with the generic path's per-warp message rows
+      for (int rc : {rmax, 0}) {
+        const size_t per_warp = (size_t)(vcap + 2) * 32 * 4 * rpl;
+        const size_t fixed = chunk_fixed_bytes(rpl, C.chunk_slot_cap) + staged_bytes(rpl, rc) + obj_bytes;
+        if (fixed + 4 * per_warp <= kSmemMax) {
+          const int warps = (int)std::min<size_t>(kChunkThreads / 32, (kSmemMax - fixed) / per_warp);
+          const LaunchCfg g{kVariantGeneric, rpl, rc, warps, fixed + (size_t)warps * per_warp};
+          if (C.jit_kernel[1][rpl - 1]) out.push_back({kVariantJit, rpl, rc, warps, g.smem});
+          out.push_back(g);
+        }
+        if (rc == 0) break;
+      }
+  }
+  if (fsmt_fused_limit_ok(C)) {
+    const FusedShape f = fused_shape(C, R);
+    out.push_back({kVariantWarp, 1, 0, f.warps, f.smem});
+  }
+  return out;
+}
+
+// The default among the candidates: generated routines without the generic
+// path when every constraint has one; else the chunked kernel with two restarts
+// per lane while that leaves at least 8 warps (staged reals likewise); else one
+// warp per constraint.
+LaunchCfg default_config(const Compiled& C, int R) {
+  const std::vector<LaunchCfg> all = launch_candidates(C, R);
+  LaunchCfg best{-1, 0, 0, 0, 0};
+  for (const LaunchCfg& x : all) {
+    if (x.variant == kVariantWide) return x;
+    if (x.variant == kVariantJit || x.variant == kVariantGeneric) {
+      if (best.variant < 0 || (best.warps < 8 && x.warps > best.warps)) best = x;
+      continue;
     }
-  return s;
+    if (best.variant < 0) best = x;
+  }
+  return best;
+}
+
+const LaunchCfg& chosen_config(const Compiled& C, int R, LaunchCfg& scratch) {
+  if (C.tuned_R == R && C.tuned.variant >= 0) return C.tuned;
+  scratch = default_config(C, R);
+  return scratch;
+}
+
+fsmt_status launch_cfg(const Compiled& C, const LaunchCfg& x, bool adj, int R, float sigma, const float* prm,
+                       const float* w, const float* a, const float* b, float* ga, float* gb, float* obj, float* cop,
+                       const int* ctl, cudaStream_t st) {
+  if (x.variant == kVariantWarp) return launch_fused_warp(C, adj, R, sigma, prm, w, a, b, ga, gb, obj, cop, ctl, st);
+  int vcap = std::max(1, C.max_nodes);
+  const dim3 g(std::max(1, std::min(C.n_chunks, sm_count()))), t(x.warps * 32);
+  DevView view = C.view;
+  view.chunk_real_cap = x.real_cap;
+  void* args[] = {&view, &R, &sigma, (void*)&prm, &vcap, (void*)&w, (void*)&a, (void*)&b,
+                  &ga, &gb, &obj, &cop, (void*)&ctl};
+  if (x.variant == kVariantWide || x.variant == kVariantJit) {
+    void* k = x.variant == kVariantWide ? C.jit_wide[adj ? 1 : 0][x.rpl - 1] : C.jit_kernel[adj ? 1 : 0][x.rpl - 1];
+    if (!k) {
+      set_error("run-time compiled kernel missing for the selected configuration");
+      return FSMT_EINVAL;
+    }
+    FSMT_CUDA(cudaLaunchKernel((const void*)k, g, t, args, x.smem, st), "specialised kernel launch");
+    return FSMT_OK;
+  }
+  if (x.rpl == 2) {
+    if (adj)
+      k_chunked<true, 2><<<g, t, x.smem, st>>>(view, R, sigma, prm, vcap, w, a, b, ga, gb, obj, cop, ctl);
+    else
+      k_chunked<false, 2><<<g, t, x.smem, st>>>(view, R, sigma, prm, vcap, w, a, b, ga, gb, obj, cop, ctl);
+  } else {
+    if (adj)
+      k_chunked<true, 1><<<g, t, x.smem, st>>>(view, R, sigma, prm, vcap, w, a, b, ga, gb, obj, cop, ctl);
+    else
+      k_chunked<false, 1><<<g, t, x.smem, st>>>(view, R, sigma, prm, vcap, w, a, b, ga, gb, obj, cop, ctl);
+  }
+  FSMT_CUDA(cudaGetLastError(), "chunked kernel launch");
+  return FSMT_OK;
 }
 
 fsmt_status launch_fused(const Compiled& C, bool adj, int R, float sigma, const float* prm, const float* w,
                          const float* a, const float* b, float* ga, float* gb, float* obj, float* cop, const int* ctl,
                          cudaStream_t st) {
   if (C.n_obj == 0) return FSMT_OK;
-  int vcap = std::max(1, C.max_nodes);
-  const int blocks = std::max(1, std::min(C.n_chunks, sm_count()));
-  DevView view = C.view;
-  void* args[] = {&view, &R, &sigma, (void*)&prm, &vcap, (void*)&w, (void*)&a, (void*)&b,
-                  &ga, &gb, &obj, &cop, (void*)&ctl};
-  const int wide_rpl = R > 32 ? 2 : 1;
-  void* wk = C.chunked_ok ? C.jit_wide[adj ? 1 : 0][wide_rpl - 1] : nullptr;
-  if (wk) {  // every constraint has a generated routine: 32 warps, no generic message rows
-    const size_t base = chunk_fixed_bytes(wide_rpl, C.chunk_slot_cap) + (R <= kMaxObjSmemR ? (size_t)R * 4 : 0);
-    for (int rc : {C.stage_reals ? C.chunk_real_max : 0, 0}) {
-      const size_t smem = base + staged_bytes(wide_rpl, rc);
-      if (smem > kSmemMax) continue;
-      view.chunk_real_cap = rc;
-      FSMT_CUDA(cudaLaunchKernel((const void*)wk, dim3(blocks), dim3(kChunkThreadsWide), args, smem, st),
-                "specialised kernel launch");
-      return FSMT_OK;
-    }
+  LaunchCfg scratch;
+  const LaunchCfg& x = chosen_config(C, R, scratch);
+  if (x.variant < 0) {
+    set_error("no kernel configuration fits this instance; use the plain form");
+    return FSMT_EINVAL;
   }
-  const ChunkShape cs = chunk_shape(C, R);
-  if (cs.warps > 0) {
-    view.chunk_real_cap = cs.real_cap;
-    const dim3 g(blocks), t(cs.warps * 32);
-    void* jk = C.jit_kernel[adj ? 1 : 0][cs.rpl - 1];
-    if (jk) {  // run-time specialised kernel
-      FSMT_CUDA(cudaLaunchKernel((const void*)jk, g, t, args, cs.smem, st), "specialised kernel launch");
-      return FSMT_OK;
-    }
-    if (cs.rpl == 2) {
-      if (adj)
-        k_chunked<true, 2><<<g, t, cs.smem, st>>>(view, R, sigma, prm, vcap, w, a, b, ga, gb, obj, cop, ctl);
-      else
-        k_chunked<false, 2><<<g, t, cs.smem, st>>>(view, R, sigma, prm, vcap, w, a, b, ga, gb, obj, cop, ctl);
-    } else {
-      if (adj)
-        k_chunked<true, 1><<<g, t, cs.smem, st>>>(view, R, sigma, prm, vcap, w, a, b, ga, gb, obj, cop, ctl);
-      else
-        k_chunked<false, 1><<<g, t, cs.smem, st>>>(view, R, sigma, prm, vcap, w, a, b, ga, gb, obj, cop, ctl);
-    }
-    FSMT_CUDA(cudaGetLastError(), "chunked kernel launch");
-    return FSMT_OK;
-  }
-  return launch_fused_warp(C, adj, R, sigma, prm, w, a, b, ga, gb, obj, cop, ctl, st);
+  return launch_cfg(C, x, adj, R, sigma, prm, w, a, b, ga, gb, obj, cop, ctl, st);
 }
 
 fsmt_status launch_pgd(const Compiled& C, int R, float eta, float bscale, int sweeps, int polish, const float* prm,
@@ -943,6 +981,109 @@ fsmt_status fsmt_adjoint(const fsmt_compiled* c, int32_t R, float sigma, const f
   return launch_fused(C, true, R, sigma, nullptr, w, a, b, grad_a, grad_b, obj, cop, nullptr, st);
 }
 
+static fsmt_launch_config to_public(const LaunchCfg& x, float ms) {
+  fsmt_launch_config o{};
+  o.variant = x.variant;
+  o.restarts_per_lane = x.rpl;
+  o.staged_reals = x.real_cap;
+  o.warps = x.warps;
+  o.smem_bytes = (int64_t)x.smem;
+  o.ms = ms;
+  return o;
+}
+
+fsmt_status fsmt_launch_configs(const fsmt_compiled* c, int32_t R, fsmt_launch_config* out, int32_t cap,
+                                int32_t* n) {
+  fsmt_status s = check_ready(c, R);
+  if (s != FSMT_OK) return s;
+  if (!n || cap < 0 || (cap > 0 && !out)) {
+    set_error("invalid output arguments");
+    return FSMT_EINVAL;
+  }
+  const std::vector<LaunchCfg> all = launch_candidates(c->c, R);
+  // the default first, then the rest in enumeration order
+  const LaunchCfg d = default_config(c->c, R);
+  std::vector<LaunchCfg> ordered;
+  if (d.variant >= 0) ordered.push_back(d);
+  for (const LaunchCfg& x : all)
+    if (!(x.variant == d.variant && x.rpl == d.rpl && x.real_cap == d.real_cap)) ordered.push_back(x);
+  for (int i = 0; i < (int)ordered.size() && i < cap; ++i) out[i] = to_public(ordered[i], 0.f);
+  *n = (int32_t)ordered.size();
+  return FSMT_OK;
+}
+
+fsmt_status fsmt_select_config(fsmt_compiled* c, int32_t R, const fsmt_launch_config* cfg) {
+  fsmt_status s = check_ready(c, R);
+  if (s != FSMT_OK) return s;
+  Compiled& C = c->c;
+  if (!cfg) {
+    C.tuned_R = -1;
+    C.tuned.variant = -1;
+    return FSMT_OK;
+  }
+  for (const LaunchCfg& x : launch_candidates(C, R))
+    if (x.variant == cfg->variant && x.rpl == cfg->restarts_per_lane && x.real_cap == cfg->staged_reals) {
+      C.tuned = x;
+      C.tuned_R = R;
+      return FSMT_OK;
+    }
+  set_error("not a configuration of this instance at this R (see fsmt_launch_configs)");
+  return FSMT_EINVAL;
+}
+
+fsmt_status fsmt_autotune(fsmt_compiled* c, int32_t R, float sigma, const float* w, const float* a,
+                          const float* b, float* grad_a, float* grad_b, float* obj, fsmt_launch_config* best,
+                          void* stream) {
+  fsmt_status s = check_ready(c, R);
+  if (s != FSMT_OK) return s;
+  Compiled& C = c->c;
+  if (!(sigma >= 0.f) || !w || (C.n_bool && (!a || !grad_a)) || (C.n_real && (!b || !grad_b))) {
+    set_error("invalid sigma or NULL argument");
+    return FSMT_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const std::vector<LaunchCfg> all = launch_candidates(C, R);
+  if (all.empty()) {
+    if (best) *best = to_public(LaunchCfg{-1, 0, 0, 0, 0}, 0.f);
+    return FSMT_OK;
+  }
+  cudaEvent_t e0, e1;
+  FSMT_CUDA(cudaEventCreate(&e0), "event");
+  FSMT_CUDA(cudaEventCreate(&e1), "event");
+  float best_ms = 0.f;
+  int best_i = -1;
+  for (int i = 0; i < (int)all.size(); ++i) {
+    fsmt_status e = launch_cfg(C, all[i], true, R, sigma, nullptr, w, a, b, grad_a, grad_b, obj, nullptr, nullptr, st);
+    if (e == FSMT_OK) e = cuda_ok(cudaEventRecord(e0, st), "event");
+    for (int k = 0; k < 3 && e == FSMT_OK; ++k)
+      e = launch_cfg(C, all[i], true, R, sigma, nullptr, w, a, b, grad_a, grad_b, obj, nullptr, nullptr, st);
+    if (e == FSMT_OK) e = cuda_ok(cudaEventRecord(e1, st), "event");
+    if (e == FSMT_OK) e = cuda_ok(cudaEventSynchronize(e1), "event");
+    float ms = 0.f;
+    if (e == FSMT_OK) e = cuda_ok(cudaEventElapsedTime(&ms, e0, e1), "event");
+    if (e != FSMT_OK) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return e;
+    }
+    ms /= 3.f;
+    if (best_i < 0 || ms < best_ms) {
+      best_ms = ms;
+      best_i = i;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  C.tuned = all[best_i];
+  C.tuned_R = R;
+  if (C.n_bool) FSMT_CUDA(cudaMemsetAsync(grad_a, 0, sizeof(float) * (size_t)C.n_bool * R, st), "memset grad_a");
+  if (C.n_real) FSMT_CUDA(cudaMemsetAsync(grad_b, 0, sizeof(float) * (size_t)C.n_real * R, st), "memset grad_b");
+  if (obj) FSMT_CUDA(cudaMemsetAsync(obj, 0, sizeof(float) * (size_t)R, st), "memset obj");
+  FSMT_CUDA(cudaStreamSynchronize(st), "synchronise");
+  if (best) *best = to_public(C.tuned, best_ms);
+  return FSMT_OK;
+}
+
 fsmt_status fsmt_plain_work_floats(const fsmt_compiled* c, int32_t R, int64_t* n_floats) {
   if (!c || !n_floats || R < 1) {
     set_error("invalid argument");
@@ -1160,6 +1301,7 @@ fsmt_status fsmt_solve_stage(fsmt_compiled* cc, const fsmt_stage_config* cfg, fs
   for (const void* p : ptrs) mix((uint64_t)(uintptr_t)p);
   mix((uint64_t)s->R);
   mix((uint64_t)cfg->t_max);
+  mix((uint64_t)(C.tuned_R == s->R ? 1 + C.tuned.variant * 64 + C.tuned.rpl * 8 + (C.tuned.real_cap > 0) : 0));
   if (!C.graph_exec || C.graph_key != key) {
     if (C.graph_exec) {
       cudaGraphExecDestroy((cudaGraphExec_t)C.graph_exec);

@@ -32,6 +32,16 @@ struct Problem {
 };
 
 // Host-side compiled form (arrays mirror DevView).
+// One way to run the forward (+ adjoint) pass (fsmt_device.cu; the autotuner's unit).
+enum { kVariantWarp = 0, kVariantGeneric = 1, kVariantJit = 2, kVariantWide = 3 };
+struct LaunchCfg {
+  int variant;   // kVariant*: warp per constraint, ahead-of-time chunked, generated with / without the generic path
+  int rpl;       // restarts per lane
+  int real_cap;  // reals staged in shared memory per chunk (0: b read from global memory)
+  int warps;     // per CTA
+  size_t smem;   // dynamic shared memory per CTA
+};
+
 struct Compiled {
   int32_t n_bool = 0, n_real = 0, n_atoms = 0, n_cons = 0, n_obj = 0;
   int32_t max_nodes = 0;
@@ -54,6 +64,8 @@ struct Compiled {
   int32_t chunk_slot_cap = 0;  // most slots of any chunk
   int32_t chunk_real_max = 0;  // most reals of any chunk
   bool stage_reals = true;     // stage the chunk's reals in shared memory (FSMT_NO_STAGE=1 turns it off)
+  int tuned_R = -1;            // restarts the configuration below was chosen for (fsmt_autotune / fsmt_select_config)
+  LaunchCfg tuned{-1, 0, 0, 0, 0};
   std::vector<int32_t> chunk_con_ptr{0}, chunk_node_ptr{0}, chunk_slot_ptr{0}, slot_label;
   std::vector<int32_t> slot_meta, chunk_term_ptr{0}, term_var, chunk_real_ptr{0}, real_id;
   std::vector<float> term_coef;

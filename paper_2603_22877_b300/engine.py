@@ -158,6 +158,29 @@ class Compiled:
                _dptr(grad_a, torch.float32, sa, "grad_a"), _dptr(grad_b, torch.float32, sb, "grad_b"),
                _dptr(obj, torch.float32, (R,), "obj"), _dptr(cop, torch.float32, sw, "cop"), _stream(stream))
 
+    def launch_configs(self, R):
+        """The kernel configurations that can run this instance at R restarts, default first."""
+        n = C.c_int32()
+        L.call("fsmt_launch_configs", self.h, int(R), None, 0, C.byref(n))
+        arr = (L.LaunchConfig * max(1, n.value))()
+        L.call("fsmt_launch_configs", self.h, int(R), arr, n.value, C.byref(n))
+        return [arr[i] for i in range(n.value)]
+
+    def select_config(self, R, cfg=None):
+        """Pins one of launch_configs(R) for later passes and stages (None: the default)."""
+        L.call("fsmt_select_config", self.h, int(R), C.byref(cfg) if cfg is not None else None)
+
+    def autotune(self, R, sigma, w, a, b, grad_a, grad_b, obj=None, stream=None):
+        """Times every configuration on these inputs and pins the fastest; returns it."""
+        import torch
+        sa, sb, sw = self._shapes(R)
+        best = L.LaunchConfig()
+        L.call("fsmt_autotune", self.h, int(R), float(sigma), _dptr(w, torch.float32, sw, "w"),
+               _dptr(a, torch.float32, sa, "a"), _dptr(b, torch.float32, sb, "b"),
+               _dptr(grad_a, torch.float32, sa, "grad_a"), _dptr(grad_b, torch.float32, sb, "grad_b"),
+               _dptr(obj, torch.float32, (R,), "obj"), C.byref(best), _stream(stream))
+        return best
+
     def plain_work(self, R):
         n = C.c_int64()
         L.call("fsmt_plain_work_floats", self.h, int(R), C.byref(n))
@@ -319,6 +342,11 @@ class Solver:
         self.b.copy_(torch.as_tensor(b0))
         self.w.fill_(1.0)
         self.h.zero_()
+
+    def tune(self, sigma):
+        """Autotunes the forward + adjoint kernel configuration on the current state
+        (fsmt_autotune; the gradient buffers are scratch and left zero)."""
+        return self.comp.autotune(self.R, sigma, self.w, self.a, self.b, self.grad_a, self.grad_b, self.obj)
 
     def config(self, sigma, t):
         return L.StageConfig(float(sigma), float(self.eta), float(self.b_scale), float(self.eps), int(self.t_max),

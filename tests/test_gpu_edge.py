@@ -183,3 +183,36 @@ def test_round_check_filter_keeps_boundary_cases_exact():
     np.testing.assert_array_equal(viol.cpu().numpy().astype(bool), ref)
     np.testing.assert_array_equal(nu.cpu().numpy(), ref.sum(0))
     assert ref[:, 0].sum() == len(coefs)  # at Y itself every strict atom fails and every non-strict holds
+
+
+@pytest.mark.parametrize("make,R", [(lambda: W.large_scheduling(1005, 16, 30, 6, 4, 5), 70),
+                                    (lambda: mixed_instance(False), 33)])
+def test_every_launch_configuration_and_the_autotuner(make, R):
+    """Each kernel configuration the library offers for an instance (kernel
+    variant, restarts per lane, staged reals) agrees with the oracle; the
+    autotuner times them all and pins one of them."""
+    import torch
+    inst = make()
+    P, comp, a, b, w = setup(inst, R)
+    cfgs = comp.launch_configs(R)
+    assert len(cfgs) >= 2
+    keys = {(c.variant, c.restarts_per_lane, c.staged_reals) for c in cfgs}
+    assert len(keys) == len(cfgs)
+    sigma = float(np.float32(inst.scale))
+    ref = OBJ.evaluate(inst, a.astype(np.float64), b.astype(np.float64), w.astype(np.float64), sigma)
+    oc = OBJ.objective_constraints(inst)
+    for cfg in cfgs:
+        comp.select_config(R, cfg)
+        obj, cop, ga, gb = gpu_adjoint(comp, R, sigma, a, b, w)
+        what = cfg.as_dict()
+        assert np.abs(cop[oc] - ref[1][oc]).max() <= COP_TOL, what
+        assert_grad_close(ga, ref[2], f"grad_a {what}")
+        assert_grad_close(gb, ref[3], f"grad_b {what}")
+    comp.select_config(R, None)
+    da, db, dw = (torch.from_numpy(x).cuda() for x in (a, b, w))
+    ga, gb, ob = torch.ones_like(da), torch.ones_like(db), torch.ones(R, device="cuda")
+    best = comp.autotune(R, sigma, dw, da, db, ga, gb, ob)
+    assert best.ms > 0 and (best.variant, best.restarts_per_lane, best.staged_reals) in keys
+    assert not ga.any() and not gb.any() and not ob.any()  # scratch left zero
+    obj, cop, ga2, gb2 = gpu_adjoint(comp, R, sigma, a, b, w)
+    assert_grad_close(ga2, ref[2], "grad_a after autotune")
