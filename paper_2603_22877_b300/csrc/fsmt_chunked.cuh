@@ -142,7 +142,7 @@ __device__ __forceinline__ float atom_z(const DevView& d, int i, int R, int r, c
 }
 
 template <bool ADJ, int RPL>
-__device__ __forceinline__ bool shape_dispatch(int shape, const uint2* nd, const float* s_p, float* s_g, int lane,
+__device__ __forceinline__ bool shape_dispatch(int shape, const unsigned* sl, const float* s_p, float* s_g, int lane,
                                                const Pack<RPL>& wc, Pack<RPL>& cp);
 
 // GENERIC = false: every constraint has a generated routine, so the generic
@@ -160,7 +160,8 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
   const int rows = vcap + 2;  // decision nodes, then TRUE (vcap) and FALSE (vcap + 1)
   uint2* s_node = reinterpret_cast<uint2*>(smem);
   int4* s_con = reinterpret_cast<int4*>(s_node + kChunkMaxNodes);
-  int* s_lab = reinterpret_cast<int*>(s_con + kChunkMaxCons);
+  unsigned* s_list = reinterpret_cast<unsigned*>(s_con + kChunkMaxCons);  // the constraints' literal lists
+  int* s_lab = reinterpret_cast<int*>(s_list + kChunkMaxList);
   int* s_meta = s_lab + kChunkMaxSlots;                            // atom slots: first term << 16 | count
   float* s_q0 = reinterpret_cast<float*>(s_meta + kChunkMaxSlots);  // atom slots: q0
   float* s_si = s_q0 + kChunkMaxSlots;                             // atom slots: 1 / (sqrt(2) sigma ||q||)
@@ -191,6 +192,10 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
     __syncthreads();  // the previous chunk is done with shared memory
     for (int i = threadIdx.x; i < nn; i += blockDim.x) s_node[i] = d.cnodes[n0 + i];
     for (int i = threadIdx.x; i < nc; i += blockDim.x) s_con[i] = d.ccon[c0 + i];
+    {
+      const int q0l = __ldg(d.chunk_list_ptr + q), nl = __ldg(d.chunk_list_ptr + q + 1) - q0l;
+      for (int i = threadIdx.x; i < nl; i += blockDim.x) s_list[i] = __ldg(d.clist + q0l + i);
+    }
     const int t0 = __ldg(d.chunk_term_ptr + q), nt = __ldg(d.chunk_term_ptr + q + 1) - t0;
     const int e0 = __ldg(d.chunk_real_ptr + q), nr = __ldg(d.chunk_real_ptr + q + 1) - e0;
     for (int i = threadIdx.x; i < nr; i += blockDim.x) s_rid[i] = __ldg(d.real_id + e0 + i);
@@ -385,7 +390,7 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
 #pragma unroll
           for (int k = 0; k < RPL; ++k) wn.v[k] = ok[k] ? __ldg(w + (size_t)id * R + rr[k]) : 0.f;
         }
-        if ((shape == 0 || !shape_dispatch<ADJ, RPL>(shape, nd, s_p, s_g, lane, wc, cp)) && GENERIC) {
+        if ((shape == 0 || !shape_dispatch<ADJ, RPL>(shape, s_list + cn.z, s_p, s_g, lane, wc, cp)) && GENERIC) {
           PK zero, one;
 #pragma unroll
           for (int k = 0; k < RPL; ++k) {
@@ -471,7 +476,7 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
 #ifndef FSMT_JIT_SHAPES
 // Ahead-of-time build: no generated routines, every constraint takes the generic path.
 template <bool ADJ, int RPL>
-__device__ __forceinline__ bool shape_dispatch(int, const uint2*, const float*, float*, int, const Pack<RPL>&,
+__device__ __forceinline__ bool shape_dispatch(int, const unsigned*, const float*, float*, int, const Pack<RPL>&,
                                                Pack<RPL>&) {
   return false;
 }

@@ -27,7 +27,8 @@ constexpr int kSmemBudget = 112 * 1024;
 // shared memory of the chunked kernel without the per-warp message arrays
 inline size_t chunk_fixed_bytes(int rpl, int slot_cap) {
   return (size_t)kChunkMaxNodes * 8 + (size_t)kChunkMaxCons * 16 + (size_t)kChunkMaxSlots * 4 * 4 +
-         (size_t)kChunkMaxTerms * 8 + (size_t)kChunkMaxReals * 4 + (size_t)slot_cap * kSlotStride * 4 * 2;
+         (size_t)kChunkMaxTerms * 8 + (size_t)kChunkMaxReals * 4 + (size_t)kChunkMaxList * 4 +
+         (size_t)slot_cap * kSlotStride * 4 * 2;
 }
 constexpr size_t kSmemMax = 227 * 1024;
 
@@ -864,7 +865,8 @@ fsmt_status fsmt_upload(fsmt_compiled* cc, void* stream) {
                o_csp = push_array(blob, C.chunk_slot_ptr), o_slab = push_array(blob, C.slot_label),
                o_smeta = push_array(blob, C.slot_meta), o_ctp = push_array(blob, C.chunk_term_ptr),
                o_tvar = push_array(blob, C.term_var), o_tcoef = push_array(blob, C.term_coef),
-               o_crp = push_array(blob, C.chunk_real_ptr), o_rid = push_array(blob, C.real_id);
+               o_crp = push_array(blob, C.chunk_real_ptr), o_rid = push_array(blob, C.real_id),
+               o_clp = push_array(blob, C.chunk_list_ptr), o_clist = push_array(blob, C.clist);
   if (C.dev_block) {
     cudaFree(C.dev_block);
     C.dev_block = nullptr;
@@ -922,6 +924,8 @@ fsmt_status fsmt_upload(fsmt_compiled* cc, void* stream) {
   v.term_coef = (const float*)(base + o_tcoef);
   v.chunk_real_ptr = (const int32_t*)(base + o_crp);
   v.real_id = (const int32_t*)(base + o_rid);
+  v.chunk_list_ptr = (const int32_t*)(base + o_clp);
+  v.clist = (const uint32_t*)(base + o_clist);
   FSMT_CUDA(cudaFuncSetAttribute(k_fused<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024),
             "smem attribute");
   FSMT_CUDA(cudaFuncSetAttribute(k_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024),

@@ -35,6 +35,7 @@ constexpr int kChunkMaxSlots = 320;  // distinct variables / atoms per chunk (ha
 // the slot limit when the generic DP path may run: its per-warp message rows
 // share shared memory with the slot arrays, so smaller chunks keep more warps
 constexpr int kChunkSlotsGeneric = 192;
+constexpr int kChunkMaxList = 2304;  // words of a chunk's per-constraint literal lists (nodes + padding)
 constexpr int kSlotStride = 64;  // floats per slot row of the per-slot shared arrays (two restarts x 32 lanes)
 constexpr int kChunkThreads = 512;  // threads of the chunked kernel with the generic path (16 warps)
 constexpr int kChunkMaxTerms = 768;  // nonzeros of the atoms of a chunk
@@ -86,6 +87,9 @@ struct DevView {
   const int32_t* term_var;        // chunk-local real of each atom nonzero, chunk by chunk
   const int32_t* chunk_real_ptr;  // [n_chunks + 1] into real_id
   const int32_t* real_id;         // the chunk's reals
+  const int32_t* chunk_list_ptr;  // [n_chunks + 1] into clist
+  const uint32_t* clist;          // per constraint (16-byte aligned, at ccon.z words into the chunk's
+                                  // part): the slot words of its distinct literals in order of first node
   const float* term_coef;         // its (normalised) coefficient
 };
 

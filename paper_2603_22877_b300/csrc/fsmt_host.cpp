@@ -228,13 +228,15 @@ static bool build_diagram(int kind, int param, const int32_t* lits, int L, Diagr
 // reals (1024 bytes a real: b and dC/db, double-buffered) once the fixed arrays
 // and the per-restart objective (up to 4096 restarts) are placed.
 constexpr int kChunkWideBytes = 227 * 1024 - (kChunkMaxNodes * 8 + kChunkMaxCons * 16 + kChunkMaxSlots * 16 +
-                                              kChunkMaxTerms * 8 + kChunkMaxReals * 4) - 4096 * 4;
-static_assert(kChunkWideBytes >= kChunkMaxSlots * 512 + 16 * 1024, "wide chunk budget");
+                                              kChunkMaxTerms * 8 + kChunkMaxReals * 4 + kChunkMaxList * 4) - 4096 * 4;
+static_assert(kChunkWideBytes >= kChunkMaxSlots * 512 + 8 * 1024, "wide chunk budget");
 
 static bool build_chunks(const Problem& P, Compiled& C, int slot_limit) {
   const int n_obj = C.n_obj;
   C.chunk_con_ptr.assign(1, 0);
   C.chunk_node_ptr.assign(1, 0);
+  C.chunk_list_ptr.assign(1, 0);
+  C.clist.clear();
   C.chunk_slot_ptr.assign(1, 0);
   C.slot_label.clear();
   C.slot_meta.clear();
@@ -310,6 +312,7 @@ static bool build_chunks(const Problem& P, Compiled& C, int slot_limit) {
   auto close_chunk = [&]() {
     C.chunk_con_ptr.push_back((int32_t)(C.ccon.size() / 4));
     C.chunk_node_ptr.push_back((int32_t)C.cnode_slot.size());
+    C.chunk_list_ptr.push_back((int32_t)C.clist.size());
     // the chunk's atom terms, in slot order
     int tb = 0;
     for (size_t k = C.chunk_slot_ptr.back(); k < C.slot_label.size(); ++k) {
@@ -358,6 +361,7 @@ static bool build_chunks(const Problem& P, Compiled& C, int slot_limit) {
     if (chunk_cons > 0 && (chunk_cons + 1 > kChunkMaxCons || chunk_nodes + V > kChunkMaxNodes ||
                            (int)slot_of.size() + new_slots > slot_limit ||
                            chunk_terms + new_terms > kChunkMaxTerms ||
+                           (int)(C.clist.size() - C.chunk_list_ptr.back()) + V + 3 > kChunkMaxList ||
                            (int)real_of.size() + new_reals(s) > kChunkMaxReals ||
                            (slot_limit > kChunkSlotsGeneric &&
                             ((int)slot_of.size() + new_slots) * 512 + ((int)real_of.size() + new_reals(s)) * 1024 >
@@ -366,7 +370,8 @@ static bool build_chunks(const Problem& P, Compiled& C, int slot_limit) {
     if (V > kChunkMaxNodes) return false;
     C.ccon.push_back(chunk_nodes);
     C.ccon.push_back(V);
-    C.ccon.push_back(C.con_root[s]);
+    // z: the root flag of a constant diagram, else where its literal list starts
+    C.ccon.push_back(V == 0 ? C.con_root[s] : (int32_t)(C.clist.size() - C.chunk_list_ptr.back()));
     C.ccon.push_back(C.con_id[s]);
     std::string key(reinterpret_cast<const char*>(&V), sizeof(V));
     std::vector<uint16_t> shi(V), slo(V), sgrp(V);
@@ -432,7 +437,16 @@ static bool build_chunks(const Problem& P, Compiled& C, int slot_limit) {
       if (ng) std::swap(h, l);
       C.cnode_hilo.push_back(h | (l << 16));
     }
-    if ((int)slot_of.size() > slot_limit || chunk_terms > kChunkMaxTerms || (int)real_of.size() > kChunkMaxReals)
+    {  // the constraint's literal list: slot words of its distinct literals, in order of first node
+      const size_t n0 = C.cnode_slot.size() - (size_t)V;
+      std::vector<uint32_t> seen;
+      for (size_t v = n0; v < C.cnode_slot.size(); ++v)
+        if (std::find(seen.begin(), seen.end(), C.cnode_slot[v]) == seen.end()) seen.push_back(C.cnode_slot[v]);
+      while (seen.size() % 4) seen.push_back(0);
+      C.clist.insert(C.clist.end(), seen.begin(), seen.end());
+    }
+    if ((int)slot_of.size() > slot_limit || chunk_terms > kChunkMaxTerms || (int)real_of.size() > kChunkMaxReals ||
+        (int)(C.clist.size() - C.chunk_list_ptr.back()) > kChunkMaxList)
       return false;
     ++chunk_cons;
     chunk_nodes += V;

@@ -70,6 +70,8 @@ struct Compiled {
   std::vector<int32_t> slot_meta, chunk_term_ptr{0}, term_var, chunk_real_ptr{0}, real_id;
   std::vector<float> term_coef;
   std::vector<int32_t> ccon;  // 4 ints per constraint
+  std::vector<int32_t> chunk_list_ptr{0};
+  std::vector<uint32_t> clist;  // per constraint: slot words of its distinct literals (padded to 4)
   std::vector<uint32_t> cnode_slot, cnode_hilo;  // slot | negated-literal bit 31; children
   // diagram shapes in literal space (build_chunks) and those given generated code
   std::vector<int32_t> shape_ptr{0};

@@ -124,15 +124,34 @@ struct Emitter {
 
 std::string shape_routine(int rank, int V, const uint16_t* hi, const uint16_t* lo, const uint16_t* grp) {
   std::ostringstream o;
-  std::vector<int> last(V, -1);  // last node of each group, by index
-  for (int v = 0; v < V; ++v) last[grp[v]] = v;
+  std::vector<int> last(V, -1), pos(V, -1);  // last node of each group; the group's place in the literal list
+  int n_groups = 0;
+  for (int v = 0; v < V; ++v) {
+    last[grp[v]] = v;
+    if (grp[v] == v) pos[v] = n_groups++;
+  }
+  // sl: the constraint's literal list, 16-byte aligned; each pass fetches it four
+  // slot words at a time (F<b> forward, B<b> reverse); word of group g: <block>.<x|y|z|w>
+  static const char* comp = "xyzw";
+  std::vector<char> fetched_f((n_groups + 3) / 4, 0), fetched_b((n_groups + 3) / 4, 0);
+  auto word = [&](int g, bool fwd) {
+    const int j = pos[g], blk = j / 4;
+    std::string name = std::string(fwd ? "F" : "B") + std::to_string(blk);
+    std::vector<char>& f = fwd ? fetched_f : fetched_b;
+    if (!f[blk]) {
+      o << "    const uint4 " << name << " = *reinterpret_cast<const uint4*>(sl + " << 4 * blk << ");\n";
+      f[blk] = 1;
+    }
+    return name + "." + comp[j % 4];
+  };
   // a slot word is the byte offset of the slot's row; pb and gb point at the lane's
   // first restart in the probability and adjoint rows of slot 0
-  auto load = [&](int g) {
-    return "*reinterpret_cast<const float*>(pb + nd[" + std::to_string(g) + "].x + 128 * k)";
+  auto load = [&](int g, bool fwd) {
+    const std::string w = word(g, fwd);
+    return "*reinterpret_cast<const float*>(pb + " + w + " + 128 * k)";
   };
   o << "template <bool ADJ, int RPL>\n__device__ __forceinline__ void shape_" << rank
-    << "(const uint2* __restrict__ nd, const float* __restrict__ s_p, float* __restrict__ s_g, int lane,"
+    << "(const unsigned* __restrict__ sl, const float* __restrict__ s_p, float* __restrict__ s_g, int lane,"
        " const Pack<RPL>& wc, Pack<RPL>& cp) {\n"
        "  using V = float;\n  const V zero = 0.f, one = 1.f, mone = -1.f;\n"
        "  const char* pb = reinterpret_cast<const char*>(s_p + lane);\n"
@@ -140,6 +159,8 @@ std::string shape_routine(int rank, int V, const uint16_t* hi, const uint16_t* l
        "  for (int k = 0; k < RPL; ++k) {\n";
   for (int adj = 1; adj >= 0; --adj) {
     o << (adj ? "  if (ADJ) {\n" : "  } else {\n");
+    std::fill(fetched_f.begin(), fetched_f.end(), 0);
+    std::fill(fetched_b.begin(), fetched_b.end(), 0);
     Emitter E{o};
     std::vector<Ex> t(V, Ex{Ex::ZERO, ""});
     if (adj) {
@@ -150,7 +171,8 @@ std::string shape_routine(int rank, int V, const uint16_t* hi, const uint16_t* l
         const int g = grp[v];
         if (hi[v] >= V && lo[v] >= V) continue;
         if (!(loaded[g] & 1)) {
-          o << "    const V f" << g << " = " << load(g) << ";\n";
+          const std::string ld = load(g, true);  // may emit the block fetch first
+          o << "    const V f" << g << " = " << ld << ";\n";
           loaded[g] |= 1;
         }
         const Ex q{Ex::VAR, "f" + std::to_string(g)};
@@ -172,7 +194,10 @@ std::string shape_routine(int rank, int V, const uint16_t* hi, const uint16_t* l
     };
     for (int v = V - 1; v >= 0; --v) {  // Alg. 4, and the adjoint sum of each group
       const int g = grp[v];
-      if (last[g] == v) o << "    const V q" << g << " = " << load(g) << ";\n";
+      if (last[g] == v) {
+        const std::string ld = load(g, false);
+        o << "    const V q" << g << " = " << ld << ";\n";
+      }
       const Ex q{Ex::VAR, "q" + std::to_string(g)};
       const Ex d = E.sub(bu(hi[v]), bu(lo[v]));
       bm[v] = E.fma(q, d, bu(lo[v]));
@@ -180,7 +205,8 @@ std::string shape_routine(int rank, int V, const uint16_t* hi, const uint16_t* l
         acc[g] = E.fma(t[v], d, acc[g]);
         if (g == v && acc[g].k != Ex::ZERO) {
           const Ex gw = E.mul({Ex::VAR, "wv"}, acc[g]);  // emitted before the line that uses it
-          o << "    atomicAdd(reinterpret_cast<float*>(gb + nd[" << g << "].x + 128 * k), " << E.name(gw) << ");\n";
+          const std::string wd = word(g, false);  // fetched at the group's last node already
+          o << "    atomicAdd(reinterpret_cast<float*>(gb + " << wd << " + 128 * k), " << E.name(gw) << ");\n";
         }
       }
     }
@@ -202,10 +228,10 @@ std::string generated_source(const Compiled& C) {
     const int b = C.shape_ptr[x], V = C.shape_ptr[x + 1] - b;
     o << shape_routine((int)k + 1, V, C.shape_hi.data() + b, C.shape_lo.data() + b, C.shape_grp.data() + b);
   }
-  o << "template <bool ADJ, int RPL>\n__device__ __forceinline__ bool shape_dispatch(int shape, const uint2* nd,"
+  o << "template <bool ADJ, int RPL>\n__device__ __forceinline__ bool shape_dispatch(int shape, const unsigned* sl,"
        " const float* s_p, float* s_g, int lane, const Pack<RPL>& wc, Pack<RPL>& cp) {\n  switch (shape) {\n";
   for (size_t k = 0; k < C.jit_shape.size(); ++k)
-    o << "    case " << k + 1 << ": shape_" << k + 1 << "<ADJ, RPL>(nd, s_p, s_g, lane, wc, cp); return true;\n";
+    o << "    case " << k + 1 << ": shape_" << k + 1 << "<ADJ, RPL>(sl, s_p, s_g, lane, wc, cp); return true;\n";
   o << "    default: return false;\n  }\n}\n\n}  // namespace fsmt\n\n";
   for (int wide = 0; wide < 2; ++wide)
     for (int adj = 0; adj < 2; ++adj)
