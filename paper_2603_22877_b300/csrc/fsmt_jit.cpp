@@ -163,10 +163,10 @@ std::string shape_routine(int rank, int V, const uint16_t* hi, const uint16_t* l
     std::fill(fetched_b.begin(), fetched_b.end(), 0);
     Emitter E{o};
     std::vector<Ex> t(V, Ex{Ex::ZERO, ""});
+    std::vector<int> loaded(V, 0);  // bit 0: the forward pass holds q of the group in f<g>
     if (adj) {
       o << "    const V wv = wc.v[k];\n";
       t[0] = {Ex::ONE, ""};
-      std::vector<int> loaded(V, 0);
       for (int v = 0; v < V; ++v) {  // Alg. 3: push to non-terminal children
         const int g = grp[v];
         if (hi[v] >= V && lo[v] >= V) continue;
@@ -194,11 +194,12 @@ std::string shape_routine(int rank, int V, const uint16_t* hi, const uint16_t* l
     };
     for (int v = V - 1; v >= 0; --v) {  // Alg. 4, and the adjoint sum of each group
       const int g = grp[v];
-      if (last[g] == v) {
+      const bool kept = loaded[g] & 1;  // q from the forward pass, still in a register
+      if (last[g] == v && !kept) {
         const std::string ld = load(g, false);
         o << "    const V q" << g << " = " << ld << ";\n";
       }
-      const Ex q{Ex::VAR, "q" + std::to_string(g)};
+      const Ex q{Ex::VAR, (kept ? "f" : "q") + std::to_string(g)};
       const Ex d = E.sub(bu(hi[v]), bu(lo[v]));
       bm[v] = E.fma(q, d, bu(lo[v]));
       if (adj) {
