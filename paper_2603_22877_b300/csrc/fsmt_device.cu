@@ -64,15 +64,31 @@ FusedShape fused_shape(const Compiled& C, int R) {
   return f;
 }
 
+// The floating-point filter of the exact atom test: with z = sum_t c_t y_t - q0 and
+// mag = sum_t |c_t y_t| + |q0| accumulated in FP32 over n terms (fused
+// multiply-adds, c_t exact, q0 rounded once), sign(z) is certain when |z| exceeds
+// (n + 4) (u mag + 2^-126-ish), u = 2^-24 (Higham, Accuracy and Stability of
+// Numerical Algorithms, 2nd ed., Sec. 3.1, with two terms for the rounding of
+// mag itself and an absolute term for results below the normal range).  Returns
+// -1 (z < 0), +1 (z > 0) or 0 (inside the band: the exact test decides).
+__device__ __forceinline__ int atom_filter(float z, float mag, int n) {
+  if (fabsf(z) > (float)(n + 4) * (5.9604645e-8f * mag + 1e-38f)) return z < 0.f ? -1 : 1;
+  return 0;
+}
+
+// the exact test itself, kept out of line: rare, and register-hungry (320-bit accumulator)
+__device__ __noinline__ bool atom_truth_exact_slow(const DevView& d, int lab, int R, int r,
+                                                   const float* __restrict__ a, const float* __restrict__ b) {
+  float p, gz;
+  literal_prob(d, lab, R, r, true, 0.f, a, b, p, gz);
+  return p > 0.5f;
+}
+
 __device__ __forceinline__ bool literal_truth_exact(const DevView& d, int lab, int R, int r,
                                                     const float* __restrict__ a, const float* __restrict__ b) {
   if (lab < d.n_bool) return __ldg(a + (size_t)lab * R + r) < 0.f;
-  // Floating-point filter: z = sum_t c_t y_t - q0 in FP32 (c_t exact, q0 rounded
-  // once) carries an error of at most (n + 2) u (sum_t |c_t y_t| + |q0|), u = 2^-24
-  // (Higham, Accuracy and Stability of Numerical Algorithms, 2nd ed., Sec. 3.1, for
-  // the n fused multiply-adds), plus 2^-149 per operation below the normal range.
-  // Outside that band the sign of z is certain and z != 0, so the atom holds iff
-  // z < 0 whatever its strictness; inside it the exact path decides.
+  // filtered first; outside the filter's band z != 0, so the atom holds iff z < 0
+  // whatever its strictness; inside it the exact path decides
   const int i = lab - d.n_bool;
   const int k0 = __ldg(d.atom_ptr + i), k1 = __ldg(d.atom_ptr + i + 1);
   const float q0 = __ldg(d.atom_q0f + i);
@@ -82,11 +98,9 @@ __device__ __forceinline__ bool literal_truth_exact(const DevView& d, int lab, i
     z = fmaf(c, y, z);
     mag = fmaf(fabsf(c), fabsf(y), mag);
   }
-  const float n = (float)(k1 - k0 + 4);  // two more terms than the bound for the rounding of mag itself
-  if (fabsf(z) > n * (5.9604645e-8f * mag + 1e-38f)) return z < 0.f;
-  float p, gz;
-  literal_prob(d, lab, R, r, true, 0.f, a, b, p, gz);
-  return p > 0.5f;
+  const int f = atom_filter(z, mag, k1 - k0);
+  if (f != 0) return f < 0;
+  return atom_truth_exact_slow(d, lab, R, r, a, b);
 }
 
 // ---------------------------------------------------------- fused kernel --
@@ -551,7 +565,8 @@ __global__ void k_converge(int R, const float* prm, const float* gn2, uint8_t* a
 // Alg. 2's u_c, h_c, #Unsat and weight update.  One warp per constraint.
 __global__ void k_round_check(DevView d, int R, const float* __restrict__ a, const float* __restrict__ b,
                               uint8_t* __restrict__ viol, int* __restrict__ n_unsat, float* __restrict__ w,
-                              float* __restrict__ h, float rho, float gamma, int update_w, const float* prm) {
+                              float* __restrict__ h, float rho, float gamma, int update_w, const float* prm,
+                              int s_begin) {
   extern __shared__ int cnt_s[];
   for (int r = threadIdx.x; r < R; r += blockDim.x) cnt_s[r] = 0;
   __syncthreads();
@@ -563,7 +578,7 @@ __global__ void k_round_check(DevView d, int R, const float* __restrict__ a, con
   const float lg = log2f(gamma);
   const int lane = threadIdx.x & 31, W = blockDim.x >> 5;
   const int n_tiles = (R + 31) >> 5;
-  for (int s = blockIdx.x * W + (threadIdx.x >> 5); s < d.n_cons; s += gridDim.x * W) {
+  for (int s = s_begin + blockIdx.x * W + (threadIdx.x >> 5); s < d.n_cons; s += gridDim.x * W) {
     const int nb = __ldg(d.con_ptr + s);
     const int V = __ldg(d.con_ptr + s + 1) - nb;
     const int cid = __ldg(d.con_id + s);
@@ -587,6 +602,149 @@ __global__ void k_round_check(DevView d, int R, const float* __restrict__ a, con
           hh = 1.f;
         }
         h[k] = hh;
+      }
+    }
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < R; r += blockDim.x)
+    if (cnt_s[r]) atomicAdd(n_unsat + r, cnt_s[r]);
+}
+
+// Round + check of the constraints of C_sigma over the chunk schedule, per chunk
+// and tile of 32 restarts: (A) every literal slot's truth at the rounded point
+// (x = sgn(a), exact atoms) once, as one 32-bit word over the tile's restarts;
+// (B) one thread per constraint evaluates its diagram bottom up on those words
+// (node value = (holds & value(hi)) | (~holds & value(lo)), literal space), all
+// 32 restarts at once; (C) one warp per constraint applies the ERWA update as
+// k_round_check does.
+constexpr int kCheckThreads = 512;
+__global__ void __launch_bounds__(kCheckThreads, 3)
+    k_check_chunked(DevView d, int R, int vcap, const float* __restrict__ a, const float* __restrict__ b,
+                    uint8_t* __restrict__ viol, int* __restrict__ n_unsat, float* __restrict__ w,
+                    float* __restrict__ h, float rho, float gamma, int update_w, const float* prm) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint2* s_node = reinterpret_cast<uint2*>(smem);
+  int4* s_con = reinterpret_cast<int4*>(s_node + kChunkMaxNodes);
+  int* s_lab = reinterpret_cast<int*>(s_con + kChunkMaxCons);
+  int* s_meta = s_lab + kChunkMaxSlots;                               // atoms: first term << 16 | count
+  float* s_q0 = reinterpret_cast<float*>(s_meta + kChunkMaxSlots);    // atoms: q0 (FP32)
+  int* s_tvar = reinterpret_cast<int*>(s_q0 + kChunkMaxSlots);        // the chunk's atom terms
+  float* s_tcoef = reinterpret_cast<float*>(s_tvar + kChunkMaxTerms);
+  float* s_b = s_tcoef + kChunkMaxTerms;                              // [real][32]: b of the tile
+  unsigned* s_t = reinterpret_cast<unsigned*>(s_b + kChunkMaxReals * 32);  // [slot]: the literal holds, bit per restart
+  unsigned* s_val = s_t + kChunkMaxSlots;                                   // [node]: the node's value, bit per restart
+  unsigned* s_u = s_val + kChunkMaxNodes;                                   // [constraint]: violated, bit per restart
+  int* cnt_s = reinterpret_cast<int*>(s_u + kChunkMaxCons);
+  for (int r = threadIdx.x; r < R; r += blockDim.x) cnt_s[r] = 0;
+  if (prm) {
+    rho = prm[P_RHO];
+    gamma = prm[P_GAMMA];
+    update_w = prm[P_UPDATE_W] != 0.f;
+  }
+  const float lg = log2f(gamma);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
+  const int n_tiles = (R + 31) >> 5;
+  for (int q = blockIdx.x; q < d.n_chunks; q += gridDim.x) {
+    const int c0 = __ldg(d.chunk_con_ptr + q), nc = __ldg(d.chunk_con_ptr + q + 1) - c0;
+    const int n0 = __ldg(d.chunk_node_ptr + q), nn = __ldg(d.chunk_node_ptr + q + 1) - n0;
+    const int l0 = __ldg(d.chunk_slot_ptr + q), ns = __ldg(d.chunk_slot_ptr + q + 1) - l0;
+    __syncthreads();  // the previous chunk is done with shared memory
+    for (int i = threadIdx.x; i < nn; i += blockDim.x) s_node[i] = d.cnodes[n0 + i];
+    for (int i = threadIdx.x; i < nc; i += blockDim.x) s_con[i] = d.ccon[c0 + i];
+    for (int i = threadIdx.x; i < ns; i += blockDim.x) {
+      const int raw = __ldg(d.slot_label + l0 + i), lab = raw & 0x7fffffff;
+      s_lab[i] = raw;
+      s_meta[i] = __ldg(d.slot_meta + l0 + i);
+      if (lab >= d.n_bool) s_q0[i] = __ldg(d.atom_q0f + lab - d.n_bool);
+    }
+    const int t0 = __ldg(d.chunk_term_ptr + q), nt = __ldg(d.chunk_term_ptr + q + 1) - t0;
+    for (int i = threadIdx.x; i < nt; i += blockDim.x) {
+      s_tvar[i] = __ldg(d.term_var + t0 + i);
+      s_tcoef[i] = __ldg(d.term_coef + t0 + i);
+    }
+    const int e0 = __ldg(d.chunk_real_ptr + q), nr = __ldg(d.chunk_real_ptr + q + 1) - e0;
+    for (int t = 0; t < n_tiles; ++t) {
+      const int r = t * 32 + lane;
+      const bool ok = r < R;
+      __syncthreads();  // chunk loaded / the previous tile's walks are done
+      for (int e = threadIdx.x; e < nr * 32; e += blockDim.x) {
+        const int rr = t * 32 + (e & 31);
+        s_b[e] = rr < R ? __ldg(b + (size_t)__ldg(d.real_id + e0 + (e >> 5)) * R + rr) : 0.f;
+      }
+      __syncthreads();
+      for (int i = warp; i < ns; i += W) {
+        const int raw = s_lab[i], lab = raw & 0x7fffffff;
+        bool holds = false;
+        if (ok) {
+          if (lab < d.n_bool) {
+            holds = __ldg(a + (size_t)lab * R + r) < 0.f;
+          } else {  // the filter on the staged reals, else the exact test
+            const int meta = s_meta[i], tb = meta >> 16, tc = meta & 0xffff;
+            const float q0 = s_q0[i];
+            float z = -q0, mag = fabsf(q0);
+            for (int j = 0; j < tc; ++j) {
+              const float cj = s_tcoef[tb + j], y = s_b[s_tvar[tb + j] * 32 + lane];
+              z = fmaf(cj, y, z);
+              mag = fmaf(fabsf(cj), fabsf(y), mag);
+            }
+            const int f = atom_filter(z, mag, tc);
+            holds = f != 0 ? f < 0 : atom_truth_exact_slow(d, lab, R, r, a, b);
+          }
+        }
+        const unsigned word = __ballot_sync(0xffffffffu, holds != (raw < 0));
+        if (lane == 0) s_t[i] = word;
+      }
+      __syncthreads();
+      const unsigned valid = t * 32 + 32 <= R ? 0xffffffffu : (1u << (R - t * 32)) - 1u;
+      for (int c = threadIdx.x; c < nc; c += blockDim.x) {  // (B)
+        const int4 cn = s_con[c];
+        const int V = cn.y & 0xffff;
+        unsigned holds_c;
+        if (V == 0) {
+          holds_c = cn.z == 0 ? 0xffffffffu : 0u;  // constant diagram: 0 TRUE, 1 FALSE
+        } else {
+          const uint2* nd = s_node + cn.x;
+          unsigned* val = s_val + cn.x;
+          auto value = [&](unsigned ch) -> unsigned {  // the TRUE terminal's row is vcap, FALSE vcap + 1
+            return ch < (unsigned)V ? val[ch] : (ch == (unsigned)vcap ? 0xffffffffu : 0u);
+          };
+          for (int v = V - 1; v >= 0; --v) {
+            const uint2 e = nd[v];
+            const unsigned m = s_t[e.x >> 8];
+            val[v] = (m & value(e.y & 0xffffu)) | (~m & value(e.y >> 16));
+          }
+          holds_c = val[0];
+        }
+        s_u[c] = ~holds_c & valid;
+      }
+      __syncthreads();
+      for (int c0 = warp; c0 < nc; c0 += 4 * W) {  // (C), four constraints' loads in flight together
+        size_t k[4];
+        float h0[4], w0[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int c = c0 + j * W;
+          const bool live = ok && c < nc;
+          k[j] = live ? (size_t)s_con[c].w * R + r : 0;
+          h0[j] = (h && live) ? h[k[j]] : 0.f;
+          w0[j] = (h && live && update_w) ? w[k[j]] : 0.f;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int c = c0 + j * W;
+          if (!ok || c >= nc) continue;
+          const int u = (int)((s_u[c] >> lane) & 1u);
+          if (viol) viol[k[j]] = (uint8_t)u;
+          if (u) atomicAdd(cnt_s + r, 1);
+          if (h) {
+            float hh = fmaf(rho, h0[j], (float)u);
+            if (update_w) {
+              w[k[j]] = w0[j] * exp2f(hh * lg);
+              hh = 1.f;
+            }
+            h[k[j]] = hh;
+          }
+        }
       }
     }
   }
@@ -811,9 +969,25 @@ fsmt_status launch_round_check(const Compiled& C, int R, const float* a, const f
     set_error("R too large for round_check");
     return FSMT_EINVAL;
   }
-  const int blocks = (int)std::max<long>(1, std::min<long>((C.n_cons + 7) / 8, (long)sm_count() * 4));
-  k_round_check<<<blocks, threads, smem, st>>>(C.view, R, a, b, viol, n_unsat, w, h, rho, gamma, update_w, prm);
-  FSMT_CUDA(cudaGetLastError(), "round_check launch");
+  // constraints of C_sigma over the chunk schedule (when it exists), the rest one warp each
+  int s_begin = 0;
+  const size_t csmem = (size_t)kChunkMaxNodes * (8 + 4) + (size_t)kChunkMaxCons * (16 + 4) +
+                       (size_t)kChunkMaxSlots * (12 + 4) + (size_t)kChunkMaxTerms * 8 +
+                       (size_t)kChunkMaxReals * 32 * 4 + (size_t)R * sizeof(int);
+  if (C.chunked_ok && C.n_chunks > 0 && csmem <= kSmemMax) {
+    const int cblocks = std::max(1, std::min(C.n_chunks, sm_count() * 3));
+    k_check_chunked<<<cblocks, kCheckThreads, csmem, st>>>(C.view, R, std::max(1, C.max_nodes), a, b, viol, n_unsat,
+                                                            w, h, rho, gamma, update_w, prm);
+    FSMT_CUDA(cudaGetLastError(), "chunked check launch");
+    s_begin = C.n_obj;
+  }
+  if (s_begin < C.n_cons) {
+    const int blocks =
+        (int)std::max<long>(1, std::min<long>((C.n_cons - s_begin + 7) / 8, (long)sm_count() * 4));
+    k_round_check<<<blocks, threads, smem, st>>>(C.view, R, a, b, viol, n_unsat, w, h, rho, gamma, update_w, prm,
+                                                 s_begin);
+    FSMT_CUDA(cudaGetLastError(), "round_check launch");
+  }
   return FSMT_OK;
 }
 
@@ -931,6 +1105,8 @@ fsmt_status fsmt_upload(fsmt_compiled* cc, void* stream) {
   FSMT_CUDA(cudaFuncSetAttribute(k_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024),
             "smem attribute");
   FSMT_CUDA(cudaFuncSetAttribute(k_round_check, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024),
+            "smem attribute");
+  FSMT_CUDA(cudaFuncSetAttribute(k_check_chunked, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024),
             "smem attribute");
   FSMT_CUDA(cudaFuncSetAttribute(k_chunked<true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024),
             "smem attribute");

@@ -147,7 +147,8 @@ def test_unstaged_and_generic_paths_agree(no_jit, no_stage, monkeypatch):
     assert_grad_close(gb, ref[3], "grad_b")
 
 
-def test_round_check_filter_keeps_boundary_cases_exact():
+@pytest.mark.parametrize("policy", [0, 1])  # unit atoms projected (one warp per constraint) or in C_sigma (chunks)
+def test_round_check_filter_keeps_boundary_cases_exact(policy):
     """The check decides each atom with an FP32 filter and falls back to exact
     arithmetic inside the filter's error band.  Points on an atom's boundary
     (z = 0) and one float step to either side, with large integer coefficients,
@@ -175,7 +176,8 @@ def test_round_check_filter_keeps_boundary_cases_exact():
         for j in range(3):
             for _ in range(abs(int(steps[j]))):
                 b[j, r] = np.nextafter(b[j, r], np.float32(np.inf) if steps[j] > 0 else np.float32(-np.inf))
-    comp = Problem.from_instance(inst).compile().upload()
+    comp = Problem.from_instance(inst).compile(policy).upload()
+    assert (comp.info["n_chunks"] > 0) == (policy == 1)
     nu = torch.zeros(R, dtype=torch.int32, device="cuda")
     viol = torch.zeros((inst.n_cons, R), dtype=torch.uint8, device="cuda")
     comp.round_check(R, torch.zeros((0, R), device="cuda"), torch.from_numpy(b).cuda(), nu, violated=viol)
