@@ -16,6 +16,7 @@ the data path; rank 0 prints the max-over-ranks time.
 """
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -33,6 +34,7 @@ METRIC = "fwd+adjoint xBDD nodes/s"
 UNIT = "nodes/s"
 
 WORKLOADS = {
+    "random_hybrid": (lambda: W.random_hybrid(1006, 1000), 100),
     "large_scheduling": (lambda: W.large_scheduling(1005), 512),
     "large_scheduling_400": (lambda: W.large_scheduling(1005, n_jobs=400), 512),
     "placement2d": (lambda: W.placement2d(1003), 1024),
@@ -58,6 +60,9 @@ def parse():
     p.add_argument("--tts-iters", type=int, default=50, help="PGD iterations per stage in the time-to-SAT runs")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--roofline-launches", type=int, default=10)
+    p.add_argument("--gradient-time", action="store_true",
+                   help="the paper's gradient-time experiment on the random hybrid benchmark instead of the bench")
+    p.add_argument("--gt-instances", type=int, default=10, help="instances per n in --gradient-time")
     return p.parse_args()
 
 
@@ -402,8 +407,96 @@ def our_arm(args):
         torch.distributed.destroy_process_group()
 
 
+# Per-instance average gradient time of the paper's own solver on the random
+# hybrid benchmark, averaged over the 10 instances of each n: (CPU, dual EPYC 9654
+# at 64 threads; GPU, one L40S), ms (Suppl. Note "Gradient Computation Time",
+# Table gradient-time).  Context from other hardware, not a target of this line.
+PAPER_GRADIENT_MS = {100: (4.98, 12.70), 200: (21.78, 13.64), 300: (34.15, 12.77), 400: (43.14, 12.80),
+                     500: (48.40, 12.60), 600: (56.27, 12.79), 700: (62.40, 12.76), 800: (69.08, 12.84),
+                     900: (77.37, 12.87), 1000: (84.35, 12.65)}
+
+
+def gradient_time(args):
+    """The gradient-time experiment (Suppl. Note "Gradient Computation Time") on
+    the random hybrid benchmark: per instance, gradients at 10,000 random points in
+    100 groups of 100 points, one sigma per group with 1/sigma = 0.00, 0.01, ...,
+    0.99 (in units of the reals' [0, 1] range).  One group is one batched forward +
+    adjoint call at R = 100 (fused kernel when one fits the instance, else the plain
+    form); the 100 calls of an instance are timed together with CUDA events.  The
+    oracle (FP64 numpy, one core) is timed on one group per n."""
+    import torch
+    from paper_2603_22877_b300 import build
+    from paper_2603_22877_b300.engine import Problem
+    build.build()
+    R, groups = 100, 100
+    inv = [0.01 * g for g in range(groups)]
+    sig = [math.inf if x == 0 else 1.0 / x for x in inv]
+    per_n = {}
+    for n in range(100, 1001, 100):
+        times, forms = [], set()
+        for k in range(args.gt_instances):
+            inst = W.random_hybrid(1006 + 10 * k, n)
+            comp = Problem.from_instance(inst).compile().upload()
+            fused_ok = bool(comp.info["fused_ok"]) or comp.info["n_chunks"] > 0
+            rng = np.random.default_rng(7 + k)
+            a = torch.from_numpy(rng.uniform(-1, 1, (groups, n, R)).astype(np.float32)).cuda()
+            b = torch.from_numpy(rng.uniform(0, 1, (groups, n, R)).astype(np.float32)).cuda()
+            w = torch.ones((inst.n_cons, R), device="cuda")
+            ga, gb = torch.zeros((n, R), device="cuda"), torch.zeros((n, R), device="cuda")
+            obj = torch.zeros(R, device="cuda")
+            work = torch.empty(comp.plain_work(R), device="cuda")
+            if fused_ok:  # the autotuned fused configuration
+                comp.autotune(R, sig[50], w, a[50], b[50], ga, gb, obj)
+
+            def grad(g, fused):
+                if fused:
+                    comp.adjoint(R, sig[g], w, a[g], b[g], ga, gb, obj=obj)
+                else:
+                    comp.forward_plain(R, sig[g], w, a[g], b[g], work, obj=obj)
+                    comp.adjoint_plain(R, sig[g], w, a[g], b[g], work, ga, gb)
+
+            best = None
+            for fused in ((True, False) if fused_ok else (False,)):  # the faster form counts
+                for g in range(3):
+                    grad(g, fused)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for g in range(groups):
+                    grad(g, fused)
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / groups
+                if best is None or ms < best[0]:
+                    best = (ms, "fused" if fused else "plain")
+            times.append(best[0])
+            forms.add(best[1])
+            del work
+            if k == 0:  # the oracle on one group of this n
+                from oracle import objective as OBJ
+                a64 = a[50].double().cpu().numpy()
+                b64 = b[50].double().cpu().numpy()
+                D = OBJ.Diagrams(inst)  # compiled once, outside the timed call
+                t0 = time.perf_counter()
+                OBJ.evaluate(inst, a64, b64, np.ones((inst.n_cons, R)), sig[50], diagrams=D)
+                oracle_ms = 1000 * (time.perf_counter() - t0)
+        gpu = float(np.mean(times))
+        per_n[n] = {"gpu_ms_per_group": gpu, "gpu_us_per_point": 1000 * gpu / R, "form": "/".join(sorted(forms)),
+                    "oracle_ms_per_group": oracle_ms, "instances": args.gt_instances,
+                    "paper_cpu_ms": PAPER_GRADIENT_MS[n][0], "paper_gpu_ms": PAPER_GRADIENT_MS[n][1]}
+        print(json.dumps({"n": n, **per_n[n]}), flush=True)
+    line = {"metric": "gradient time (forward + adjoint of 100 points)", "unit": "ms", "higher_is_better": False,
+            "data": "synthetic", "dtype": "f32", "config": {"workload": "random_hybrid", "points_per_group": R,
+                                                            "groups": groups, "inv_sigma": "0.00..0.99"},
+            "per_n": per_n}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.gradient_time:
+        gradient_time(args)
+        return
     if args.impl == "reference":
         reference_arm(args)
     else:

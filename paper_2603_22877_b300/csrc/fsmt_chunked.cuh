@@ -20,7 +20,8 @@ __device__ __forceinline__ float load_param(const float* prm, int slot, float fa
 
 // ------------------------------------------------------- literal probability --
 // p = P[variable TRUE]; gz = dd/dz for atoms (0 for Booleans).  Eq. rounding and
-// Eq. sampling; sigma = 0 decides the atom exactly.
+// Eq. sampling.  s_inv = 1 / (sqrt 2 sigma); s_inv < 0 stands for sigma = 0, which
+// decides the atom exactly; s_inv = 0 for sigma = infinity gives p = 1/2, gz = 0.
 __device__ __forceinline__ void literal_prob(const DevView& d, int lab, int R, int r, bool ok, float s_inv,
                                              const float* __restrict__ a, const float* __restrict__ b, float& p,
                                              float& gz) {
@@ -32,7 +33,7 @@ __device__ __forceinline__ void literal_prob(const DevView& d, int lab, int R, i
   }
   const int i = lab - d.n_bool;
   const int k0 = __ldg(d.atom_ptr + i), k1 = __ldg(d.atom_ptr + i + 1);
-  if (s_inv > 0.f) {
+  if (s_inv >= 0.f) {
     float z = -__ldg(d.atom_q0f + i);
     for (int k = k0; k < k1; ++k) {
       float bv = ok ? __ldg(b + (size_t)__ldg(d.atom_var + k) * R + r) : 0.f;
@@ -183,7 +184,7 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
   if (obj_s)
     for (int r = threadIdx.x; r < R; r += blockDim.x) obj_s[r] = 0.f;
   sigma = load_param(prm, P_SIGMA, sigma);
-  const float s_inv = sigma > 0.f ? kInvSqrt2 / sigma : 0.f;
+  const float s_inv = sigma > 0.f ? kInvSqrt2 / sigma : -1.f;  // < 0: sigma = 0, exact; 0: sigma = inf
   const int n_tiles = (R + 32 * RPL - 1) / (32 * RPL);
   for (int q = blockIdx.x; q < d.n_chunks; q += gridDim.x) {
     const int c0 = __ldg(d.chunk_con_ptr + q), nc = __ldg(d.chunk_con_ptr + q + 1) - c0;
@@ -263,7 +264,7 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
             }
             if (do_p) pp.v[k] = rp < R ? 0.5f * (1.f - sg * __ldg(a + (size_t)lab * R + rp)) : 0.f;
           }
-        } else if (staged && s_inv > 0.f) {
+        } else if (staged && s_inv >= 0.f) {
           // an atom, its reals staged: z = q.y - q0 of both tiles in one sweep
           // over the terms; past the last restart b reads 0 and the adjoint is 0
           const int meta = s_meta[i], tb = meta >> 16, tc = meta & 0xffff;
@@ -316,7 +317,7 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
 #pragma unroll
           for (int k = 0; k < RPL; ++k) {
             const int rf = (tf * RPL + k) * 32 + lane, rp = (tp * RPL + k) * 32 + lane;
-            if (do_f && s_inv > 0.f) {
+            if (do_f && s_inv >= 0.f) {
               const float g = gi[32 * k];
               if (rf < R && g != 0.f) {
                 float z = -s_q0[i];
@@ -330,7 +331,7 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
             }
             if (do_p) {
               const bool ok = rp < R;
-              if (s_inv > 0.f) {
+              if (s_inv >= 0.f) {
                 float z = -s_q0[i];
                 for (int j = 0; j < tc; ++j)
                   z = fmaf(s_tcoef[tb + j], ok ? __ldg(b + (size_t)s_rid[s_tvar[tb + j]] * R + rp) : 0.f, z);
@@ -338,7 +339,7 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
                 pp.v[k] = half_erfc_as(sg * u, __expf(-u * u));
               } else {
                 float p, gz;
-                literal_prob(d, lab, R, rp, ok, 0.f, a, b, p, gz);
+                literal_prob(d, lab, R, rp, ok, -1.f, a, b, p, gz);
                 pp.v[k] = raw < 0 ? 1.f - p : p;  // exact: p is 0 or 1
               }
             }

@@ -80,7 +80,7 @@ __device__ __forceinline__ int atom_filter(float z, float mag, int n) {
 __device__ __noinline__ bool atom_truth_exact_slow(const DevView& d, int lab, int R, int r,
                                                    const float* __restrict__ a, const float* __restrict__ b) {
   float p, gz;
-  literal_prob(d, lab, R, r, true, 0.f, a, b, p, gz);
+  literal_prob(d, lab, R, r, true, -1.f, a, b, p, gz);
   return p > 0.5f;
 }
 
@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_fused(DevView d, int R, float
     __syncthreads();
   }
   sigma = load_param(prm, P_SIGMA, sigma);
-  const float s_inv = sigma > 0.f ? kInvSqrt2 / sigma : 0.f;
+  const float s_inv = sigma > 0.f ? kInvSqrt2 / sigma : -1.f;  // < 0: sigma = 0, exact; 0: sigma = inf
   const int n_tiles = (R + 31) >> 5;
   for (int s = blockIdx.x * W + warp; s < d.n_obj; s += gridDim.x * W) {
     const int nb = __ldg(d.con_ptr + s);
@@ -207,7 +207,7 @@ __global__ void k_atoms_plain(DevView d, int R, float sigma, const float* __rest
                               float* __restrict__ gz_atom) {
   const int r = blockIdx.x * 32 + threadIdx.x;
   const bool ok = r < R;
-  const float s_inv = sigma > 0.f ? kInvSqrt2 / sigma : 0.f;
+  const float s_inv = sigma > 0.f ? kInvSqrt2 / sigma : -1.f;  // < 0: sigma = 0, exact; 0: sigma = inf
   for (int i = blockIdx.y * blockDim.y + threadIdx.y; i < d.n_atoms; i += gridDim.y * blockDim.y) {
     float p, gz;
     literal_prob(d, d.n_bool + i, R, r, ok, s_inv, nullptr, b, p, gz);

@@ -128,3 +128,28 @@ def test_autograd_function_and_finite_differences():
         assert np.abs(fd - fd_ref).max() <= 10 * noise + 1e-3 * np.abs(fd_ref).max(), j
         # the oracle's own central difference is close to its adjoint gradient (O(h^2))
         assert np.abs(fd_ref - gb_ref[j]).max() <= 1e-2 * np.abs(gb_ref[j]).max() + 1e-6
+
+
+@pytest.mark.parametrize("n,R,forms", [(100, 40, ("fused", "plain")), (300, 24, ("plain",))])
+def test_random_hybrid_against_oracle(n, R, forms):
+    """The random hybrid benchmark (cardinality, NAE and parity constraints of up
+    to 50 literals over Booleans and atoms; diagrams of up to 650 nodes) at the
+    gradient-time grid's extremes and between: sigma = 0 (exact), 1/sigma = 0.5,
+    1/sigma = 0 (every atom a fair coin).  Instances whose diagrams fit no fused
+    kernel run in the plain form."""
+    import math
+    inst = W.random_hybrid(1006, n)
+    P, comp, a, b, w = setup(inst, R)
+    if "fused" in forms:
+        assert comp.info["fused_ok"] or comp.info["n_chunks"] > 0
+    D = OBJ.Diagrams(inst)
+    oc = OBJ.objective_constraints(inst)
+    for sigma in (0.0, 2.0, math.inf):
+        ref = OBJ.evaluate(inst, a.astype(np.float64), b.astype(np.float64), w.astype(np.float64), sigma,
+                           diagrams=D)
+        for form in forms:
+            obj, cop, ga, gb = gpu_adjoint(comp, R, np.float32(sigma), a, b, w, plain=form == "plain")
+            assert np.abs(cop[oc] - ref[1][oc]).max() <= COP_TOL, (form, sigma)
+            np.testing.assert_allclose(obj, ref[0], rtol=1e-5, atol=1e-3)
+            assert_grad_close(ga, ref[2], f"grad_a {form} sigma={sigma}")
+            assert_grad_close(gb, ref[3], f"grad_b {form} sigma={sigma}")

@@ -72,6 +72,39 @@ def test_sigma_zero_is_the_indicator():
     assert all((g == 0).all() for _, g in t_le)
 
 
+def test_sigma_infinity_is_a_fair_coin():
+    """1/sigma = 0 (the first point of the gradient-time grid): every atom holds with
+    probability 1/2 whatever b, and the objective does not depend on b."""
+    B = W._Builder(1, 2)
+    a0 = B.atom([0, 1], [3, -2], 1, W.LE)
+    a1 = B.atom([1], [5], 2, W.LT)
+    B.con(W.NAE, [W.lit(0), W.lit(a0)])  # P(not all equal) = 1/2 when the atom is a fair coin
+    B.con(W.XOR, [W.lit(0), W.lit(a0, True), W.lit(a1)])
+    inst = B.freeze("t", np.zeros(2), np.ones(2), [1], np.zeros(2), 1.0)
+    b = np.array([[0.0, 0.3, 1.0], [0.9, 0.2, 0.0]])
+    for i in range(2):
+        p, terms = relax.atom_terms(inst, i, b, math.inf)
+        assert (p == 0.5).all() and all((g == 0).all() for _, g in terms)
+    a = np.array([[-0.4, 0.0, 0.7]])
+    w = np.ones((2, 3))
+    obj, cop, ga, gb = OBJ.evaluate(inst, a, b, w, math.inf)
+    assert np.allclose(cop[0], 0.5) and np.allclose(cop[1], 0.5)  # each has a fair literal
+    assert (gb == 0).all() and np.allclose(obj, 0.0)
+
+
+@pytest.mark.parametrize("n", [100, 300])
+def test_random_hybrid_planted_assignment_satisfies_everything(n):
+    """The random hybrid generator's plant satisfies every cardinality, NAE and
+    parity constraint exactly, with the sizes of the paper's benchmark."""
+    from oracle import semantics as Sm
+    inst = W.random_hybrid(1006, n)
+    assert inst.n_bool == n and inst.n_real == n and inst.n_atoms == n
+    assert inst.n_cons == 2 * (n // 5) + max(1, n // 50)
+    lengths = np.diff(inst.con_ptr)
+    assert (lengths[: 2 * (n // 5)] == min(50, n // 5)).all() and (lengths[2 * (n // 5):] == 50).all()
+    assert Sm.unsat_constraints(inst, inst.planted_x, inst.planted_y) == []
+
+
 def test_gradient_central_differences():
     inst = small_instance()
     R = 3

@@ -445,10 +445,68 @@ def initial_point(inst: Instance, R: int, seed: int = 7):
     return a, b
 
 
+# ---------------------------------------------------------------------------
+# Random hybrid constraints (cardinality, not-all-equal, parity) over Booleans
+# and LRA atoms: the random benchmark of the paper's Results and Methods
+# ---------------------------------------------------------------------------
+def random_hybrid(seed: int = 1006, n: int = 100) -> Instance:
+    """n Booleans, n reals in [0, 1] and n LRA atoms; n/5 cardinality constraints
+    (sum of literals <= k) and n/5 not-all-equal constraints of min(50, n/5)
+    literals each, and n/50 parity constraints of 50 literals.  A literal is a
+    Boolean or an atom, negated at random; literals of one constraint are
+    distinct variables.  An atom has 2-4 reals with integer coefficients in
+    [-10, 10] \\ {0} and q0 one of round(q.y*) - 1, +0, +1 at a planted point y*, so
+    atoms hold or fail there at random.  A planted (x*, y*) satisfies every
+    constraint: k is at least the number of true literals (and at least half
+    the length), and a not-all-equal or parity constraint that fails at the
+    plant has its first literal's polarity flipped."""
+    rng = np.random.default_rng(seed)
+    px = rng.choice(np.array([-1, 1], np.int8), n)
+    py = rng.uniform(0.0, 1.0, n)
+    B = _Builder(n, n)
+    atom_true = []
+    for _ in range(n):
+        nnz = int(rng.integers(2, 5))
+        var = rng.choice(n, nnz, replace=False)
+        coef = rng.integers(1, 11, nnz) * rng.choice([-1, 1], nnz)
+        exact = sum(Fraction(int(cf)) * Fraction(float(py[v])) for cf, v in zip(coef, var))
+        q0 = int(round(exact)) + int(rng.integers(-1, 2))
+        B.atom(var, coef, q0, LE)
+        atom_true.append(exact <= q0)
+
+    def literals(length):
+        ids = rng.choice(2 * n, length, replace=False)  # 0..n-1 Booleans, n..2n-1 atoms
+        lits, truth = [], []
+        for v in ids:
+            v = int(v)
+            neg = bool(rng.integers(2))
+            lits.append(lit(v, neg))
+            val = (px[v] == -1) if v < n else atom_true[v - n]
+            truth.append(bool(val) != neg)
+        return lits, truth
+
+    l_cn = min(50, n // 5)
+    for _ in range(n // 5):  # cardinality
+        lits, truth = literals(l_cn)
+        B.con(CARD_LE, lits, param=max(sum(truth), l_cn // 2))
+    for _ in range(n // 5):  # not-all-equal
+        lits, truth = literals(l_cn)
+        if all(truth) or not any(truth):
+            lits[0] ^= 1
+        B.con(NAE, lits)
+    for _ in range(max(1, n // 50)):  # parity
+        lits, truth = literals(min(50, 2 * n))
+        if sum(truth) % 2 == 0:
+            lits[0] ^= 1
+        B.con(XOR, lits)
+    return B.freeze("random_hybrid", np.zeros(n), np.ones(n), px, py, 1.0, seed=seed, n=n)
+
+
 CONFIGS = {
     "tiny_random": dict(make=lambda: tiny_random(1001), R=64),
     "jobshop": dict(make=lambda: jobshop(1002), R=256),
     "placement2d": dict(make=lambda: placement2d(1003), R=1024),
     "uneven_batch": dict(make=lambda: concat(uneven_batch(1004), "uneven_batch"), R=32),
     "large_scheduling": dict(make=lambda: large_scheduling(1005), R=512),
+    "random_hybrid": dict(make=lambda: random_hybrid(1006, 1000), R=100),
 }
