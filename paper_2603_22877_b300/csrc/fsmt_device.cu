@@ -836,7 +836,7 @@ std::vector<LaunchCfg> launch_candidates(const Compiled& C, int R) {
       for (int rc : {rmax, 0}) {
         const size_t per_warp = (size_t)(vcap + 2) * 32 * 4 * rpl;
         const size_t fixed = chunk_fixed_bytes(rpl, C.chunk_slot_cap) + staged_bytes(rpl, rc) + obj_bytes;
-        if (fixed + 4 * per_warp <= kSmemMax) {
+        if (fixed + per_warp <= kSmemMax) {  // down to one warp: large diagrams' messages still in shared memory
           const int warps = (int)std::min<size_t>(kChunkThreads / 32, (kSmemMax - fixed) / per_warp);
           const LaunchCfg g{kVariantGeneric, rpl, rc, warps, fixed + (size_t)warps * per_warp};
           if (C.jit_kernel[1][rpl - 1]) out.push_back({kVariantJit, rpl, rc, warps, g.smem});

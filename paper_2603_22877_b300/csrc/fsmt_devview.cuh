@@ -39,7 +39,7 @@ constexpr int kChunkMaxList = 2304;  // words of a chunk's per-constraint litera
 constexpr int kSlotStride = 64;  // floats per slot row of the per-slot shared arrays (two restarts x 32 lanes)
 constexpr int kChunkThreads = 512;  // threads of the chunked kernel with the generic path (16 warps)
 constexpr int kChunkMaxTerms = 768;  // nonzeros of the atoms of a chunk
-constexpr int kChunkMaxReals = 64;   // distinct reals of the atoms of a chunk
+constexpr int kChunkMaxReals = 128;   // reals touched by a chunk's atoms
 constexpr int kMaxJitShapes = 16;      // diagram shapes given generated code per instance
 constexpr int kMaxJitShapeNodes = 48;  // largest diagram given generated code
 

@@ -339,6 +339,11 @@ static bool build_chunks(const Problem& P, Compiled& C, int slot_limit) {
     slot_of.clear();
     chunk_cons = chunk_nodes = chunk_terms = 0;
   };
+  // small instances: chunks of fewer constraints, so that they still spread over
+  // the SMs (148 on B300); large ones fill chunks to kChunkMaxCons
+  constexpr int kTargetChunks = 148;
+  const int cons_limit = n_obj < kTargetChunks * 16 ? std::max(1, (n_obj + kTargetChunks - 1) / kTargetChunks)
+                                                    : kChunkMaxCons;
   // a slot is a literal: (variable or atom, polarity); key 2 * label + negated
   auto slot_key = [](int lab, bool ng) { return 2 * lab + (ng ? 1 : 0); };
   for (const Key& k : keys) {
@@ -358,7 +363,7 @@ static bool build_chunks(const Problem& P, Compiled& C, int slot_limit) {
         new_terms += atom_terms(lab);
       }
     }
-    if (chunk_cons > 0 && (chunk_cons + 1 > kChunkMaxCons || chunk_nodes + V > kChunkMaxNodes ||
+    if (chunk_cons > 0 && (chunk_cons + 1 > cons_limit || chunk_nodes + V > kChunkMaxNodes ||
                            (int)slot_of.size() + new_slots > slot_limit ||
                            chunk_terms + new_terms > kChunkMaxTerms ||
                            (int)(C.clist.size() - C.chunk_list_ptr.back()) + V + 3 > kChunkMaxList ||
