@@ -343,6 +343,22 @@ class Solver:
         self.w.fill_(1.0)
         self.h.zero_()
 
+    def state_dict(self):
+        """A checkpoint of the search: points, ERWA weights and histories, and the
+        per-restart outcome of the last stage (host copies; Alg. 2 resumes from it)."""
+        return {k: getattr(self, k).detach().cpu().clone()
+                for k in ("a", "b", "w", "h", "n_unsat", "iters", "obj")}
+
+    def load_state_dict(self, state):
+        """Restores a checkpoint taken by state_dict (same instance and R)."""
+        for k, v in state.items():
+            t = getattr(self, k)
+            if tuple(t.shape) != tuple(v.shape):
+                raise ValueError(f"checkpoint {k} has shape {tuple(v.shape)}, expected {tuple(t.shape)}")
+            t.copy_(v)
+        self.grad_a.zero_()
+        self.grad_b.zero_()
+
     def tune(self, sigma):
         """Autotunes the forward + adjoint kernel configuration on the current state
         (fsmt_autotune; the gradient buffers are scratch and left zero)."""
