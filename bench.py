@@ -57,7 +57,7 @@ def parse():
                    help="time-to-SAT budget in seconds per form (0 = skip)")
     p.add_argument("--tts-plain", action="store_true", help="also time-to-SAT in the plain (unfused) form")
     p.add_argument("--tts-eta", type=float, default=0.2)
-    p.add_argument("--tts-iters", type=int, default=50, help="PGD iterations per stage in the time-to-SAT runs")
+    p.add_argument("--tts-iters", type=int, default=20, help="PGD iterations per stage in the time-to-SAT runs")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--roofline-launches", type=int, default=10)
     p.add_argument("--gradient-time", action="store_true",
