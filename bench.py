@@ -385,9 +385,11 @@ def our_arm(args):
                          f"{dt:.1f} s on the host"}
     # per stage: parameters, stage start, weight sums; per iteration: iteration
     # start, fused forward+adjoint, one PGD kernel per variable class, convergence
-    # test; then round + check (graph iterations past convergence still launch)
+    # test; then round + check: over the chunks for C_sigma, one warp per constraint
+    # for the rest (graph iterations past convergence still launch)
+    checks = (info["n_chunks"] > 0) + (info["n_chunks"] == 0 or inst.n_cons > info["n_obj_cons"])
     launches_per_step = 3 + args.iters * (3 + (inst.n_bool > 0) + (info["n_free_reals"] > 0) +
-                                          (info["n_components"] > 0)) + 1
+                                          (info["n_components"] > 0)) + checks
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,

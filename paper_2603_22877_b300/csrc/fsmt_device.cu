@@ -379,10 +379,13 @@ __global__ void k_pgd_free(DevView d, int R, float eta, float bscale, const floa
 // pinned at the bound the step would cross, then the box is clamped; the thread
 // stops at the first pass that moves nothing, so the point it returns satisfies
 // every half-space exactly whenever the passes settle.
+// The iterate, Dykstra's box corrections and half-space multipliers of each
+// (block, restart) live in shared memory, one column per thread ([var][thread]:
+// conflict-free), sized by the instance's largest block.
 __global__ void k_pgd_comp(DevView d, int R, float eta, float bscale, int sweeps, int polish, const float* prm,
                            const float* __restrict__ wsum, float* __restrict__ b, float* __restrict__ gb,
                            float* __restrict__ gn2, const uint8_t* __restrict__ active, int clear_grad,
-                           const int* ctl) {
+                           const int* ctl, int maxv, int maxh) {
   if (ctl && ctl[0] == 0) return;
   const int r = blockIdx.x * 32 + threadIdx.x;
   const bool ok = r < R;
@@ -396,43 +399,49 @@ __global__ void k_pgd_comp(DevView d, int R, float eta, float bscale, int sweeps
   const float step = eta * bscale * bscale, inv = 1.f / (bscale * eta);
   float part = 0.f;
   if (ok) {
+    extern __shared__ float s_col[];
+    const int T = blockDim.x * blockDim.y, tid = threadIdx.y * blockDim.x + threadIdx.x;
+    float* xs = s_col + tid;           // x(t) at xs[t * T]
+    float* ps = xs + maxv * T;         // pbox(t)
+    float* hs = ps + maxv * T;         // th(q)
+#define x(t) xs[(t) * T]
+#define pbox(t) ps[(t) * T]
+#define th(q) hs[(q) * T]
     for (int c = blockIdx.y * blockDim.y + threadIdx.y; c < d.n_comp; c += gridDim.y * blockDim.y) {
-      float x[kMaxCompVars], old[kMaxCompVars], pbox[kMaxCompVars], th[kMaxCompHalfspaces];
       const int v0 = d.comp_var_ptr[c], nv = d.comp_var_ptr[c + 1] - v0;
       const int h0 = d.comp_hs_ptr[c], nh = d.comp_hs_ptr[c + 1] - h0;
       for (int t = 0; t < nv; ++t) {
         const size_t k = (size_t)d.comp_var[v0 + t] * R + r;
-        old[t] = b[k];
-        x[t] = old[t] - step * gb[k];
-        pbox[t] = 0.f;
+        x(t) = b[k] - step * gb[k];
+        pbox(t) = 0.f;
         if (clear_grad) gb[k] = 0.f;
       }
-      for (int q = 0; q < nh; ++q) th[q] = 0.f;
+      for (int q = 0; q < nh; ++q) th(q) = 0.f;
       for (int sw = 0; sw < sweeps; ++sw) {
         for (int q = 0; q < nh; ++q) {
           const int e0 = d.hs_ptr[h0 + q], e1 = d.hs_ptr[h0 + q + 1];
           float dot = -d.hs_q0[h0 + q];
           for (int e = e0; e < e1; ++e) {
             const float cf = d.hs_coef[e];
-            dot = fmaf(cf, x[d.hs_lvar[e]] + th[q] * cf, dot);
+            dot = fmaf(cf, x(d.hs_lvar[e]) + th(q) * cf, dot);
           }
           const float tn = fmaxf(dot, 0.f) * d.hs_inv_qq[h0 + q];
-          const float delta = th[q] - tn;
-          for (int e = e0; e < e1; ++e) x[d.hs_lvar[e]] = fmaf(delta, d.hs_coef[e], x[d.hs_lvar[e]]);
-          th[q] = tn;
+          const float delta = th(q) - tn;
+          for (int e = e0; e < e1; ++e) x(d.hs_lvar[e]) = fmaf(delta, d.hs_coef[e], x(d.hs_lvar[e]));
+          th(q) = tn;
         }
         for (int t = 0; t < nv; ++t) {
           const int j = d.comp_var[v0 + t];
-          const float yv = x[t] + pbox[t];
+          const float yv = x(t) + pbox(t);
           const float xn = fminf(fmaxf(yv, d.lo[j]), d.hi[j]);
-          pbox[t] = yv - xn;
-          x[t] = xn;
+          pbox(t) = yv - xn;
+          x(t) = xn;
         }
       }
       if (sweeps == 0)
         for (int t = 0; t < nv; ++t) {
           const int j = d.comp_var[v0 + t];
-          x[t] = fminf(fmaxf(x[t], d.lo[j]), d.hi[j]);
+          x(t) = fminf(fmaxf(x(t), d.lo[j]), d.hi[j]);
         }
       for (int pass = 0; pass < polish; ++pass) {
         bool moved = false;
@@ -441,7 +450,7 @@ __global__ void k_pgd_comp(DevView d, int R, float eta, float bscale, int sweeps
           const float q0 = d.hs_q0[h0 + q];
           float v = -q0, mag = fabsf(q0);
           for (int e = e0; e < e1; ++e) {
-            const float term = d.hs_coef[e] * x[d.hs_lvar[e]];
+            const float term = d.hs_coef[e] * x(d.hs_lvar[e]);
             v += term;
             mag += fabsf(term);
           }
@@ -452,7 +461,7 @@ __global__ void k_pgd_comp(DevView d, int R, float eta, float bscale, int sweeps
             for (int e = e0; e < e1; ++e) {
               const float cf = d.hs_coef[e];
               const int t = d.hs_lvar[e], j = d.comp_var[v0 + t];
-              const bool pinned = (cf > 0.f && x[t] <= d.lo[j]) || (cf < 0.f && x[t] >= d.hi[j]);
+              const bool pinned = (cf > 0.f && x(t) <= d.lo[j]) || (cf < 0.f && x(t) >= d.hi[j]);
               if (!pinned) qq = fmaf(cf, cf, qq);
             }
             if (qq > 0.f) {
@@ -460,8 +469,8 @@ __global__ void k_pgd_comp(DevView d, int R, float eta, float bscale, int sweeps
               for (int e = e0; e < e1; ++e) {
                 const float cf = d.hs_coef[e];
                 const int t = d.hs_lvar[e], j = d.comp_var[v0 + t];
-                const bool pinned = (cf > 0.f && x[t] <= d.lo[j]) || (cf < 0.f && x[t] >= d.hi[j]);
-                if (!pinned) x[t] = fmaf(-tq, cf, x[t]);
+                const bool pinned = (cf > 0.f && x(t) <= d.lo[j]) || (cf < 0.f && x(t) >= d.hi[j]);
+                if (!pinned) x(t) = fmaf(-tq, cf, x(t));
               }
               moved = true;
             }
@@ -469,17 +478,21 @@ __global__ void k_pgd_comp(DevView d, int R, float eta, float bscale, int sweeps
         }
         for (int t = 0; t < nv; ++t) {
           const int j = d.comp_var[v0 + t];
-          x[t] = fminf(fmaxf(x[t], d.lo[j]), d.hi[j]);
+          x(t) = fminf(fmaxf(x(t), d.lo[j]), d.hi[j]);
         }
         if (!moved) break;
       }
       for (int t = 0; t < nv; ++t) {
-        const float q = (old[t] - x[t]) * inv;
+        const size_t k = (size_t)d.comp_var[v0 + t] * R + r;
+        const float q = (b[k] - x(t)) * inv;  // b still holds the step's starting point
         part = fmaf(q, q, part);
-        if (act) b[(size_t)d.comp_var[v0 + t] * R + r] = x[t];
+        if (act) b[k] = x(t);
       }
     }
   }
+#undef x
+#undef pbox
+#undef th
   reduce_rows_add(part, gn2, r, ok);
 }
 
@@ -940,9 +953,11 @@ fsmt_status launch_pgd(const Compiled& C, int R, float eta, float bscale, int sw
     k_pgd_free<<<dim3(tiles, rows((long)C.free_var.size())), blk, 0, st>>>(C.view, R, eta, bscale, prm, wsum, b, gb,
                                                                            gn2, active, clear, ctl);
   const int ncomp = (int)C.comp_var_ptr.size() - 1;
-  if (ncomp > 0)
-    k_pgd_comp<<<dim3(tiles, rows(ncomp)), blk, 0, st>>>(C.view, R, eta, bscale, sweeps, polish, prm, wsum, b, gb,
-                                                         gn2, active, clear, ctl);
+  if (ncomp > 0) {
+    const size_t smem = (size_t)(2 * C.comp_max_vars + C.comp_max_hs) * blk.x * blk.y * sizeof(float);
+    k_pgd_comp<<<dim3(tiles, rows(ncomp)), blk, smem, st>>>(C.view, R, eta, bscale, sweeps, polish, prm, wsum, b, gb,
+                                                             gn2, active, clear, ctl, C.comp_max_vars, C.comp_max_hs);
+  }
   FSMT_CUDA(cudaGetLastError(), "pgd kernel launch");
   return FSMT_OK;
 }
@@ -1105,6 +1120,10 @@ fsmt_status fsmt_upload(fsmt_compiled* cc, void* stream) {
   FSMT_CUDA(cudaFuncSetAttribute(k_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024),
             "smem attribute");
   FSMT_CUDA(cudaFuncSetAttribute(k_round_check, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024),
+            "smem attribute");
+  // the largest block (32 reals, 64 half-spaces) needs (2 * 32 + 64) * 256 floats = 128 KB
+  FSMT_CUDA(cudaFuncSetAttribute(k_pgd_comp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (2 * kMaxCompVars + kMaxCompHalfspaces) * 256 * (int)sizeof(float)),
             "smem attribute");
   FSMT_CUDA(cudaFuncSetAttribute(k_check_chunked, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024),
             "smem attribute");

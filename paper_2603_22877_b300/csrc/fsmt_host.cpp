@@ -682,9 +682,12 @@ static fsmt_status compile(const Problem& P, int policy, Compiled& C) {
   C.hs_coef.clear();
   C.hs_q0.clear();
   C.hs_inv_qq.clear();
+  C.comp_max_vars = C.comp_max_hs = 0;
   for (size_t k = 0; k < comp_vars.size(); ++k) {
     if ((int)comp_vars[k].size() > kMaxCompVars || (int)comp_hs[k].size() > kMaxCompHalfspaces)
       return fail(FSMT_EINVAL, "a block of reals coupled by unit atoms has more than 32 reals or 64 half-spaces");
+    C.comp_max_vars = std::max<int32_t>(C.comp_max_vars, (int32_t)comp_vars[k].size());
+    C.comp_max_hs = std::max<int32_t>(C.comp_max_hs, (int32_t)comp_hs[k].size());
     std::unordered_map<int, int> local;
     for (size_t t = 0; t < comp_vars[k].size(); ++t) {
       local[comp_vars[k][t]] = (int)t;
