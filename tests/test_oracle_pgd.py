@@ -157,7 +157,8 @@ def test_descent_lemma():
 
 @pytest.mark.parametrize("make", [lambda: W.tiny_random(1001), lambda: W.jobshop(1002, 8, 4),
                                   lambda: W.placement2d(1003, 12), lambda: W.placement2d(1003, 12, selectors=False),
-                                  lambda: W.large_scheduling(1005, 16, 20, 6, 3, 5)])
+                                  lambda: W.large_scheduling(1005, 16, 20, 6, 3, 5),
+                                  lambda: W.large_scheduling(1005, 5, 20, 6, 3, 5)])
 def test_exact_check_planted_and_flip(make):
     inst = make()
     a = inst.planted_x.astype(np.float64)[:, None] * 0.5
@@ -219,3 +220,24 @@ def test_fig2_toy_annealing_reaches_global_minimum():
     b = np.array([[-0.2]])
     sat, a_end, b_end = pgd.anneal(inst, a, b, cfg)
     assert sat[0] > 0 and a_end[0, 0] < 0 and b_end[0, 0] > 0
+
+
+@pytest.mark.parametrize("n_workers", [3, 5, 6, 7, 12, 20])
+def test_scheduling_worker_index_in_range(n_workers):
+    """Generator sanity for a worker count that is not a power of two: at the plant,
+    re-coding one job's worker index to each of the 2**bits codes leaves every
+    constraint that does not involve another job's time satisfied exactly iff the code
+    names a worker (< n_workers), checked by brute force over all codes."""
+    inst = W.large_scheduling(1005, n_workers, 6, 6, 0, 5)
+    bits = (n_workers - 1).bit_length()
+    assert inst.n_bool == bits * 6
+    assert S.unsat_constraints(inst, inst.planted_x, inst.planted_y) == []
+    lits_of = [inst.lits(c) for c in range(inst.n_cons)]
+    mine = [c for c in range(inst.n_cons)                 # only job 0's bits, no atom
+            if all(l // 2 < bits for l in lits_of[c])]
+    for code in range(1 << bits):
+        x = inst.planted_x.copy()
+        for i in range(bits):
+            x[i] = -1 if (code >> i) & 1 else 1
+        ok = all(S.constraint_holds(inst, c, x, inst.planted_y) for c in mine)
+        assert ok == (code < n_workers), code

@@ -334,10 +334,16 @@ def large_scheduling(seed: int = 1005, n_workers=256, n_jobs=1111, dur_max=20,
     OR (y_j' - y_j >= t_j); precedence y_j >= y_j' + t_j' inside short job chains;
     release/deadline unit atoms 0 <= y_j, y_j + t_j <= T; and, for each of ``n_late``
     workers that start late at d_w, per job: (X_j != w) OR (y_j >= d_w).
+
+    When n_workers is not a power of two the index takes ceil(log2 n_workers) bits and
+    each job also gets clauses that keep X_j below n_workers: the unused codes
+    [n_workers, 2**bits) are covered by aligned blocks (one per set bit of
+    2**bits - n_workers, as in a binary range split), and each block forbids its prefix
+    with one OR clause over the prefix bits.
     """
     rng = np.random.default_rng(seed)
-    bits = int(round(math.log2(n_workers)))
-    assert 1 << bits == n_workers
+    bits = max(1, (n_workers - 1).bit_length())
+    assert n_workers >= 2 and n_late <= n_workers
     n_bool = bits * n_jobs
     n_real = n_jobs
     t = rng.integers(1, dur_max + 1, n_jobs)
@@ -387,6 +393,18 @@ def large_scheduling(seed: int = 1005, n_workers=256, n_jobs=1111, dur_max=20,
     for j in range(n_jobs):
         B.con(OR, [lit(B.atom([j], [-1], 0, LE))])
         B.con(OR, [lit(B.atom([j], [1], T - int(t[j]), LE))])
+    # worker index in range: for each aligned block [lo, lo + 2**k) of unused codes,
+    # NOT(bits >= k of X_j equal those of lo)
+    blocks, lo_code = [], n_workers
+    while lo_code < (1 << bits):
+        k = (lo_code & -lo_code).bit_length() - 1  # largest aligned block starting here
+        while lo_code + (1 << k) > (1 << bits):
+            k -= 1
+        blocks.append((lo_code, k))
+        lo_code += 1 << k
+    for j in range(n_jobs):
+        for code, k in blocks:
+            B.con(OR, [lit(xb(i, j), neg=bool((code >> i) & 1)) for i in range(k, bits)])
     # late workers: (X_j != w) OR (y_j >= d_w)
     for w in late:
         for j in range(n_jobs):
@@ -508,5 +526,6 @@ CONFIGS = {
     "placement2d": dict(make=lambda: placement2d(1003), R=1024),
     "uneven_batch": dict(make=lambda: concat(uneven_batch(1004), "uneven_batch"), R=32),
     "large_scheduling": dict(make=lambda: large_scheduling(1005), R=512),
+    "large_scheduling_lit": dict(make=lambda: large_scheduling(1005, n_workers=20, n_jobs=1000, n_late=6), R=512),
     "random_hybrid": dict(make=lambda: random_hybrid(1006, 1000), R=100),
 }
