@@ -380,7 +380,7 @@ def our_arm(args):
                 torch.cuda.synchronize()
                 res = S2.anneal(sched_tts, time_limit=args.tts)
                 rec = {"sat": res["sat"], "seconds": res["seconds"], "stage": res["stage"],
-                       "restart": res["restart"]}
+                       "restart": res["restart"], "stages_run": res["stages_run"], "best_unsat": res["best_unsat"]}
                 if res["sat"]:
                     rec["inv_sigma_over_scale"] = round(0.1 * res["stage"], 1)
                 runs.append(rec)

@@ -305,10 +305,16 @@ fsmt_status fsmt_pgd_step(const fsmt_compiled* c, int32_t R, float eta, float b_
  * n_unsat[r] = sum_c u_c, and if update_w != 0: w_c <- w_c gamma^h_c, h_c <- 1.
  * Device arrays: a, b inputs; n_unsat[R] output (overwritten); x[n_bool][R] (int8,
  * may be NULL), violated[n_cons][R] (uint8, may be NULL), w and h [n_cons][R]
- * (may both be NULL to skip ERWA).  Errors as above. */
+ * (may both be NULL to skip ERWA); wsum[R] (may be NULL): the restarts' total
+ * weights over C_sigma as fsmt_weight_sum gave them for the stage.  With wsum, a
+ * restart whose mean weight wsum[r] / |C_sigma| exceeds 2^32 has its updated
+ * weights multiplied by 2^-32 (exact): ERWA grows every weight geometrically and a
+ * step normalised by the total weight (fsmt_pgd_step with wsum) does not see a
+ * common factor, so this keeps long schedules inside FP32 (NULL: Alg. 2 as
+ * printed).  Errors as above. */
 fsmt_status fsmt_round_check(const fsmt_compiled* c, int32_t R, const float* a, const float* b, int8_t* x,
                              uint8_t* violated, int32_t* n_unsat, float* w, float* h, float rho, float gamma,
-                             int32_t update_w, void* stream);
+                             int32_t update_w, const float* wsum, void* stream);
 
 /* ------------------------------------------------------- one sigma stage --
  * One stage of Alg. 2 for all restarts: wsum from fsmt_weight_sum, then up to
@@ -316,7 +322,8 @@ fsmt_status fsmt_round_check(const fsmt_compiled* c, int32_t R, const float* a, 
  * [fused forward + adjoint -> PGD step + projection -> ||g||^2 test] with the
  * epsilon rule of Eq. critical applied per restart (an iteration's update is
  * applied, then a restart with ||g||^2 <= eps^2 stops for the rest of the
- * stage), then round + check + ERWA as fsmt_round_check.  All buffers are caller
+ * stage), then round + check + ERWA as fsmt_round_check (with the stage's wsum
+ * when the step is normalised).  All buffers are caller
  * owned device memory; grad_a/grad_b are work buffers that the stage leaves at
  * zero.  ctl is a device int32[4] control block (ctl[0] = restarts still
  * iterating, ctl[1] = error bits: 1 = non-finite ||g||^2 seen).  With use_graph

@@ -25,6 +25,12 @@ Follows, in the paper's order:
   * Alg. 2: per sigma stage, PGD to a critical point, round, u_c = [c violated],
     h_c <- rho h_c + u_c, and every tau stages w_c <- w_c gamma^h_c, h_c <- 1;
     SAT when #Unsat = 0.  rho = 0.5, gamma = 2, tau = 1 (Methods).
+  * Weight rescale (a documented reading for schedules longer than the paper's
+    20 stages): with the normalised step, a restart whose mean weight over
+    C_sigma exceeded 2^32 during the stage has its updated weights multiplied by
+    2^-32.  Alg. 2 grows every weight by at least gamma^rho per stage (h_c is
+    reset to 1), so FP32 weights would overflow after some 90 stages; the
+    normalised step does not see a common factor of the weights.
 
 Pins (tests/test_oracle_pgd.py): projection idempotent and non-expansive;
 Dykstra against an exact active-set enumeration of the QP on small blocks;
@@ -218,14 +224,28 @@ def round_check(inst, a, b, constraints=None):
     return x, viol
 
 
-def erwa(w, h, u, t, rho, gamma, tau):
-    """Alg. 2's history and weight update for stage index t (1-based); returns (w, h, #Unsat)."""
+W_RESCALE_AT = 2.0 ** 32
+
+
+def erwa(w, h, u, t, rho, gamma, tau, mean_w=None):
+    """Alg. 2's history and weight update for stage index t (1-based); returns (w, h, #Unsat).
+
+    mean_w [R] (optional): each restart's mean weight over C_sigma during the stage;
+    restarts above W_RESCALE_AT get their updated weights times 1 / W_RESCALE_AT."""
     h = rho * h + u
     n_unsat = u.sum(0)
     if t % tau == 0:
         w = w * np.power(gamma, h)
+        if mean_w is not None:
+            w = w * np.where(np.asarray(mean_w) > W_RESCALE_AT, 1.0 / W_RESCALE_AT, 1.0)
         h = np.ones_like(h)
     return w, h, n_unsat
+
+
+def mean_weight(inst, w, policy):
+    """Per-restart mean weight over the constraints of C_sigma (None when there are none)."""
+    oc = OBJ.objective_constraints(inst, policy)
+    return w[oc].sum(0) / len(oc) if oc else None
 
 
 # ---------------------------------------------------------------------------
@@ -245,6 +265,7 @@ def run_stage(inst, a, b, w, h, sigma, t, cfg: Config, dom=None, diagrams=None, 
     its = np.zeros(R, np.int64)
     obj = np.zeros(R)
     etas = step_sizes(inst, w, cfg)
+    mean_w = mean_weight(inst, w, cfg.policy) if cfg.normalize_eta else None
     for _ in range(cfg.t_max if iters is None else iters):
         obj, _, ga, gb = OBJ.evaluate(inst, a, b, w, sigma, cfg.policy, diagrams)
         a_new, b_new, gn2 = pgd_step(a, b, ga, gb, etas, inst.scale, dom, cfg.sweeps, cfg.polish)
@@ -255,7 +276,7 @@ def run_stage(inst, a, b, w, h, sigma, t, cfg: Config, dom=None, diagrams=None, 
         if not active.any():
             break
     _, viol = round_check(inst, a, b)
-    w, h, n_unsat = erwa(w, h, viol.astype(np.float64), t, cfg.rho, cfg.gamma, cfg.tau)
+    w, h, n_unsat = erwa(w, h, viol.astype(np.float64), t, cfg.rho, cfg.gamma, cfg.tau, mean_w)
     return a, b, w, h, n_unsat, its, obj
 
 

@@ -574,12 +574,25 @@ __global__ void k_converge(int R, const float* prm, const float* gn2, uint8_t* a
 }
 
 // --------------------------------------------------- round + check + ERWA --
+// Weight rescale of a restart at the ERWA update: Alg. 2 multiplies every weight by
+// gamma^h_c >= gamma^(rho h) each stage, so a long schedule overflows FP32 after some
+// 90 stages.  The step is normalised by the restart's total weight, so a common
+// factor of the weights leaves the iteration unchanged except for the scale of the
+// epsilon test; when the restart's mean weight over C_sigma exceeded 2^32 during the
+// stage (wsum, taken at its start), the updated weights are multiplied by 2^-32
+// (exact).  No rescale without wsum or when the step is not normalised.
+constexpr float kWRescaleAt = 0x1p32f, kWRescale = 0x1p-32f;
+__device__ __forceinline__ float erwa_scale(const DevView& d, const float* wsum, const float* prm, int r, bool ok) {
+  if (!wsum || !ok || (prm && prm[P_NORM] == 0.f)) return 1.f;
+  return wsum[r] > kWRescaleAt * (float)d.n_obj ? kWRescale : 1.f;
+}
+
 // Alg. 1 rounding and an exact walk of every constraint's diagram per restart;
 // Alg. 2's u_c, h_c, #Unsat and weight update.  One warp per constraint.
 __global__ void k_round_check(DevView d, int R, const float* __restrict__ a, const float* __restrict__ b,
                               uint8_t* __restrict__ viol, int* __restrict__ n_unsat, float* __restrict__ w,
                               float* __restrict__ h, float rho, float gamma, int update_w, const float* prm,
-                              int s_begin) {
+                              const float* __restrict__ wsum, int s_begin) {
   extern __shared__ int cnt_s[];
   for (int r = threadIdx.x; r < R; r += blockDim.x) cnt_s[r] = 0;
   __syncthreads();
@@ -611,7 +624,7 @@ __global__ void k_round_check(DevView d, int R, const float* __restrict__ a, con
         const size_t k = (size_t)cid * R + r;
         float hh = fmaf(rho, h[k], (float)u);
         if (update_w) {
-          w[k] = w[k] * exp2f(hh * lg);
+          w[k] = w[k] * exp2f(hh * lg) * erwa_scale(d, wsum, prm, r, true);
           hh = 1.f;
         }
         h[k] = hh;
@@ -634,7 +647,8 @@ constexpr int kCheckThreads = 512;
 __global__ void __launch_bounds__(kCheckThreads, 3)
     k_check_chunked(DevView d, int R, int vcap, const float* __restrict__ a, const float* __restrict__ b,
                     uint8_t* __restrict__ viol, int* __restrict__ n_unsat, float* __restrict__ w,
-                    float* __restrict__ h, float rho, float gamma, int update_w, const float* prm) {
+                    float* __restrict__ h, float rho, float gamma, int update_w, const float* prm,
+                    const float* __restrict__ wsum) {
   extern __shared__ __align__(16) unsigned char smem[];
   uint2* s_node = reinterpret_cast<uint2*>(smem);
   int4* s_con = reinterpret_cast<int4*>(s_node + kChunkMaxNodes);
@@ -752,7 +766,7 @@ __global__ void __launch_bounds__(kCheckThreads, 3)
           if (h) {
             float hh = fmaf(rho, h0[j], (float)u);
             if (update_w) {
-              w[k[j]] = w0[j] * exp2f(hh * lg);
+              w[k[j]] = w0[j] * exp2f(hh * lg) * erwa_scale(d, wsum, prm, r, true);
               hh = 1.f;
             }
             h[k[j]] = hh;
@@ -975,7 +989,7 @@ fsmt_status launch_weight_sum(const Compiled& C, int R, const float* w, float* w
 
 fsmt_status launch_round_check(const Compiled& C, int R, const float* a, const float* b, uint8_t* viol, int* n_unsat,
                                float* w, float* h, float rho, float gamma, int update_w, const float* prm,
-                               cudaStream_t st) {
+                               const float* wsum, cudaStream_t st) {
   FSMT_CUDA(cudaMemsetAsync(n_unsat, 0, sizeof(int) * (size_t)R, st), "memset n_unsat");
   if (C.n_cons == 0) return FSMT_OK;
   const int threads = 256;
@@ -992,7 +1006,7 @@ fsmt_status launch_round_check(const Compiled& C, int R, const float* a, const f
   if (C.chunked_ok && C.n_chunks > 0 && csmem <= kSmemMax) {
     const int cblocks = std::max(1, std::min(C.n_chunks, sm_count() * 3));
     k_check_chunked<<<cblocks, kCheckThreads, csmem, st>>>(C.view, R, std::max(1, C.max_nodes), a, b, viol, n_unsat,
-                                                            w, h, rho, gamma, update_w, prm);
+                                                            w, h, rho, gamma, update_w, prm, wsum);
     FSMT_CUDA(cudaGetLastError(), "chunked check launch");
     s_begin = C.n_obj;
   }
@@ -1000,7 +1014,7 @@ fsmt_status launch_round_check(const Compiled& C, int R, const float* a, const f
     const int blocks =
         (int)std::max<long>(1, std::min<long>((C.n_cons - s_begin + 7) / 8, (long)sm_count() * 4));
     k_round_check<<<blocks, threads, smem, st>>>(C.view, R, a, b, viol, n_unsat, w, h, rho, gamma, update_w, prm,
-                                                 s_begin);
+                                                 wsum, s_begin);
     FSMT_CUDA(cudaGetLastError(), "round_check launch");
   }
   return FSMT_OK;
@@ -1425,7 +1439,7 @@ fsmt_status fsmt_pgd_step(const fsmt_compiled* c, int32_t R, float eta, float b_
 
 fsmt_status fsmt_round_check(const fsmt_compiled* c, int32_t R, const float* a, const float* b, int8_t* x,
                              uint8_t* violated, int32_t* n_unsat, float* w, float* h, float rho, float gamma,
-                             int32_t update_w, void* stream) {
+                             int32_t update_w, const float* wsum, void* stream) {
   fsmt_status s = check_ready(c, R);
   if (s != FSMT_OK) return s;
   const Compiled& C = c->c;
@@ -1439,7 +1453,7 @@ fsmt_status fsmt_round_check(const fsmt_compiled* c, int32_t R, const float* a, 
     k_sign<<<std::min<long>(((long)C.n_bool * R + 255) / 256, 65535L), 256, 0, st>>>(C.n_bool, R, a, x);
     FSMT_CUDA(cudaGetLastError(), "sign launch");
   }
-  return launch_round_check(C, R, a, b, violated, n_unsat, w, h, rho, gamma, update_w, nullptr, st);
+  return launch_round_check(C, R, a, b, violated, n_unsat, w, h, rho, gamma, update_w, nullptr, wsum, st);
 }
 
 static fsmt_status enqueue_stage(const Compiled& C, int t_max, fsmt_state* s, cudaStream_t st) {
@@ -1459,7 +1473,7 @@ static fsmt_status enqueue_stage(const Compiled& C, int t_max, fsmt_state* s, cu
     k_converge<<<1, 1024, 0, st>>>(R, s->params, s->gnorm2, s->active, s->iters, s->ctl);
     FSMT_CUDA(cudaGetLastError(), "converge");
   }
-  return launch_round_check(C, R, s->a, s->b, nullptr, s->n_unsat, s->w, s->h, 0.f, 2.f, 0, s->params, st);
+  return launch_round_check(C, R, s->a, s->b, nullptr, s->n_unsat, s->w, s->h, 0.f, 2.f, 0, s->params, s->wsum, st);
 }
 
 fsmt_status fsmt_solve_stage(fsmt_compiled* cc, const fsmt_stage_config* cfg, fsmt_state* s, void* stream) {

@@ -218,14 +218,14 @@ class Compiled:
                _dptr(active, torch.uint8, (R,), "active"), _stream(stream))
 
     def round_check(self, R, a, b, n_unsat, x=None, violated=None, w=None, h=None, rho=0.5, gamma=2.0,
-                    update_w=True, stream=None):
+                    update_w=True, wsum=None, stream=None):
         import torch
         sa, sb, sw = self._shapes(R)
         L.call("fsmt_round_check", self.h, int(R), _dptr(a, torch.float32, sa, "a"),
                _dptr(b, torch.float32, sb, "b"), _dptr(x, torch.int8, sa, "x"),
                _dptr(violated, torch.uint8, sw, "violated"), _dptr(n_unsat, torch.int32, (R,), "n_unsat"),
                _dptr(w, torch.float32, sw, "w"), _dptr(h, torch.float32, sw, "h"), float(rho), float(gamma),
-               int(bool(update_w)), _stream(stream))
+               int(bool(update_w)), _dptr(wsum, torch.float32, (R,), "wsum"), _stream(stream))
 
 
 def relaxed_objective(compiled, sigma, w, a, b, plain=False):
@@ -399,7 +399,8 @@ class Solver:
             if not bool(self.active.any()):
                 break
         comp.round_check(R, self.a, self.b, self.n_unsat, w=self.w, h=self.h, rho=self.rho, gamma=self.gamma,
-                         update_w=(t % self.tau == 0), stream=stream)
+                         update_w=(t % self.tau == 0), wsum=self.wsum if self.normalize_eta else None,
+                         stream=stream)
 
     def stage_host(self, sigma, t, a_host, b_host, n_unsat_host, obj_host, stream=None):
         """The same stage with host input/output buffers (copies inside the call)."""
@@ -414,17 +415,24 @@ class Solver:
         return sat, x, y
 
     def anneal(self, schedule, time_limit=None):
-        """Runs the sigma schedule; returns dict with the first exactly verified SAT restart (or None)."""
+        """Runs the sigma schedule; returns dict with the first exactly verified SAT restart
+        (or None), the stages run and the fewest unsatisfied constraints any restart had
+        at a rounding."""
         import torch
         t0 = time.perf_counter()
+        best, t = None, 0
         for t, sigma in enumerate(schedule, start=1):
             self.stage(sigma, t)
-            cand = torch.nonzero(self.n_unsat == 0).flatten().tolist()
+            lo = int(self.n_unsat.min())
+            best = lo if best is None else min(best, lo)
+            cand = torch.nonzero(self.n_unsat == 0).flatten().tolist() if lo == 0 else []
             for r in cand:
                 sat, x, y = self.verify_restart(r)
                 if sat:
-                    return dict(sat=True, restart=r, stage=t, seconds=time.perf_counter() - t0, x=x, y=y)
+                    return dict(sat=True, restart=r, stage=t, stages_run=t, best_unsat=0,
+                                seconds=time.perf_counter() - t0, x=x, y=y)
             if time_limit is not None and time.perf_counter() - t0 > time_limit:
                 break
         torch.cuda.synchronize()
-        return dict(sat=False, restart=None, stage=None, seconds=time.perf_counter() - t0)
+        return dict(sat=False, restart=None, stage=None, stages_run=t, best_unsat=best,
+                    seconds=time.perf_counter() - t0)

@@ -99,6 +99,21 @@ def test_round_check_erwa_parity(make, R):
         np.testing.assert_allclose(dw.cpu().numpy(), w_ref, rtol=2e-6)
         np.testing.assert_allclose(dh.cpu().numpy(), h_ref, rtol=1e-6, atol=1e-6)
     assert (nu_ref[::3] == 0).all()
+    # the weight rescale: restarts whose mean weight over C_sigma passed 2^32 (every
+    # fourth, weights times 2^33) get their updated weights times 2^-32, the rest not
+    big = w.copy()
+    big[:, ::4] *= 2.0 ** 33
+    mean = pgd.mean_weight(inst, big.astype(np.float64), OBJ.PROJECT)
+    assert mean is not None and (mean[::4] > pgd.W_RESCALE_AT).all() and (mean[1::4] < 2.0 ** 8).all()
+    w_ref, h_ref, _ = pgd.erwa(big.astype(np.float64), h0.astype(np.float64), viol_ref.astype(np.float64),
+                               1, 0.5, 2.0, 1, mean_w=mean)
+    da, db, dw, dh = to_dev(a, b, big, h0)
+    wsum = torch.zeros(R, dtype=torch.float32, device="cuda")
+    comp.weight_sum(R, dw, wsum)
+    nu = torch.zeros(R, dtype=torch.int32, device="cuda")
+    comp.round_check(R, da, db, nu, w=dw, h=dh, rho=0.5, gamma=2.0, update_w=True, wsum=wsum)
+    np.testing.assert_allclose(dw.cpu().numpy(), w_ref, rtol=2e-6)
+    np.testing.assert_allclose(dh.cpu().numpy(), h_ref, rtol=1e-6, atol=1e-6)
 
 
 def _solver(inst, R, comp, P, **kw):
@@ -205,3 +220,31 @@ def test_checkpoint_resume_reproduces_the_run():
     np.testing.assert_allclose(S2.b.cpu().numpy(), S.b.cpu().numpy(), atol=1e-4 * inst.scale)
     same = (S2.n_unsat.cpu().numpy() == S.n_unsat.cpu().numpy()).mean()
     assert same >= 0.95, same
+
+
+@pytest.mark.parametrize("form", ["fused", "plain"])
+def test_long_schedule_keeps_weights_finite(form):
+    """200 stages of Alg. 2 on an unsatisfiable instance (x0 and not x0): as printed the
+    weights of the failing clauses pass the FP32 range near stage 90; with the rescale
+    of a restart whose mean weight passed 2^32 they stay finite, no step is non-finite
+    and the largest weight stays far below the range."""
+    import torch
+    B = W._Builder(3, 1)
+    A = B.atom([0], [1], 5, W.LE)
+    B.con(W.OR, [W.lit(0)])
+    B.con(W.OR, [W.lit(0, True)])
+    B.con(W.OR, [W.lit(1), W.lit(2), W.lit(A)])
+    inst = B.freeze("unsat", [0.0], [10.0], np.ones(3, np.int8), np.zeros(1), 10.0)
+    R = 40
+    P, comp, a, b, _ = setup(inst, R)
+    S = _solver(inst, R, comp, P, eta=0.05, b_scale=inst.scale, t_max=2, form=form)
+    S.reset(a, b)
+    for t in range(1, 201):
+        S.stage(inst.scale / (0.1 * t), t)
+    w = S.w.cpu().numpy()
+    assert np.isfinite(w).all() and (w >= 0).all()
+    assert w.max() < 2.0 ** 64
+    assert (S.n_unsat.cpu().numpy() >= 1).all()
+    assert np.isfinite(S.gnorm2.cpu().numpy()).all() and np.isfinite(S.obj.cpu().numpy()).all()
+    if form == "fused":
+        assert int(S.ctl[1].item()) == 0

@@ -241,3 +241,49 @@ def test_scheduling_worker_index_in_range(n_workers):
             x[i] = -1 if (code >> i) & 1 else 1
         ok = all(S.constraint_holds(inst, c, x, inst.planted_y) for c in mine)
         assert ok == (code < n_workers), code
+
+
+def test_common_weight_factor_leaves_the_normalised_step_unchanged():
+    """The weight rescale relies on this: with eta_r = eta |C_sigma| / sum_c w_c (Thm.
+    max_step with L proportional to the total weight), scaling every weight of a restart
+    by 2^-32 leaves the PGD iterates bit for bit unchanged (the epsilon test is off)."""
+    inst = W.jobshop(1002, 6, 3)
+    R = 8
+    a, b = W.initial_point(inst, R, seed=4)
+    w = np.random.default_rng(5).uniform(1.0, 9.0, (inst.n_cons, R))
+    cfg = pgd.Config(eta=0.05, eps=0.0, t_max=3)
+    sigma = inst.scale / 0.7
+    out1 = pgd.run_stage(inst, a, b, w, np.zeros_like(w), sigma, 2, cfg)
+    out2 = pgd.run_stage(inst, a, b, w * 2.0 ** -32, np.zeros_like(w), sigma, 2, cfg)
+    np.testing.assert_array_equal(out1[0], out2[0])
+    np.testing.assert_array_equal(out1[1], out2[1])
+    np.testing.assert_array_equal(out1[4], out2[4])         # the same rounding outcome
+    np.testing.assert_array_equal(out1[2] * 2.0 ** -32, out2[2])
+
+
+def test_erwa_weight_rescale_keeps_long_schedules_finite():
+    """Alg. 2 as printed grows every weight by at least gamma^rho per stage (h_c is reset
+    to 1): after 300 stages the weights of a constraint that keeps failing exceed the FP32
+    range.  With the rescale of a restart whose mean weight passed 2^32 the largest stays
+    within it, the ratios between weights are those of Alg. 2 (so the weights of the
+    constraints that hold fall towards zero, as they do relative to the others in
+    Alg. 2), and restarts below the threshold are untouched."""
+    n_c, R, T = 3, 2, 300
+    u = np.zeros((n_c, R))
+    u[0, :] = 1                                           # one constraint fails every stage
+    w0, h0 = np.ones((n_c, R)), np.zeros((n_c, R))
+    w, h, wr, hr = w0, h0, w0, h0
+    for t in range(1, T + 1):
+        w, h, _ = pgd.erwa(w, h, u, t, 0.5, 2.0, 1)
+        wr, hr, _ = pgd.erwa(wr, hr, u, t, 0.5, 2.0, 1, mean_w=wr.mean(0))
+    f32_max = float(np.finfo(np.float32).max)
+    assert w.max() > f32_max
+    assert wr.max() < 2.0 ** 40 and wr.min() > 0
+    np.testing.assert_allclose(wr / wr[1:2], w / w[1:2], rtol=1e-12)
+    # below the threshold nothing changes
+    wa, _, _ = pgd.erwa(w0 * 3, h0, u, 1, 0.5, 2.0, 1, mean_w=np.full(R, 2.0 ** 32))
+    wb, _, _ = pgd.erwa(w0 * 3, h0, u, 1, 0.5, 2.0, 1)
+    np.testing.assert_array_equal(wa, wb)
+    wc, _, _ = pgd.erwa(w0 * 3, h0, u, 1, 0.5, 2.0, 1, mean_w=np.array([2.0 ** 33, 1.0]))
+    np.testing.assert_array_equal(wc[:, 0], wb[:, 0] * 2.0 ** -32)
+    np.testing.assert_array_equal(wc[:, 1], wb[:, 1])
