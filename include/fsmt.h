@@ -311,7 +311,10 @@ fsmt_status fsmt_pgd_step(const fsmt_compiled* c, int32_t R, float eta, float b_
  * weights multiplied by 2^-32 (exact): ERWA grows every weight geometrically and a
  * step normalised by the total weight (fsmt_pgd_step with wsum) does not see a
  * common factor, so this keeps long schedules inside FP32 (NULL: Alg. 2 as
- * printed).  Errors as above. */
+ * printed).  A restart whose point has a non-finite coordinate that the check
+ * reads gets bit 31 of n_unsat[r] set (the value is negative; the low bits still
+ * count its violated constraints); the call itself does not synchronise and
+ * returns FSMT_OK.  Errors as above. */
 fsmt_status fsmt_round_check(const fsmt_compiled* c, int32_t R, const float* a, const float* b, int8_t* x,
                              uint8_t* violated, int32_t* n_unsat, float* w, float* h, float rho, float gamma,
                              int32_t update_w, const float* wsum, void* stream);
@@ -363,7 +366,9 @@ fsmt_status fsmt_solve_stage(fsmt_compiled* c, const fsmt_stage_config* cfg, fsm
 /* The same stage driven from HOST buffers: copies a[n_bool*R] and b[n_real*R]
  * (host, ideally pinned) into the device state, runs fsmt_solve_stage, and
  * copies n_unsat[R] and obj[R] back to host buffers (may be NULL).  Synchronises
- * the stream before returning.  Errors as fsmt_solve_stage. */
+ * the stream before returning.  Errors as fsmt_solve_stage, and FSMT_ENAN when
+ * n_unsat is copied back and some restart's point is non-finite (bit 31 of its
+ * n_unsat, as fsmt_round_check marks it; the outputs are still written). */
 fsmt_status fsmt_solve_stage_host(fsmt_compiled* c, const fsmt_stage_config* cfg, fsmt_state* s,
                                   const float* a_host, const float* b_host, int32_t* n_unsat_host,
                                   float* obj_host, void* stream);

@@ -84,9 +84,19 @@ __device__ __noinline__ bool atom_truth_exact_slow(const DevView& d, int lab, in
   return p > 0.5f;
 }
 
+// bit 31 of n_unsat[r]: restart r's point has a non-finite coordinate that the check
+// read (the count in the low bits stays valid; ordering against the counts' atomic
+// additions does not matter)
+constexpr int kUnsatNonFinite = (int)0x80000000u;
+
 __device__ __forceinline__ bool literal_truth_exact(const DevView& d, int lab, int R, int r,
-                                                    const float* __restrict__ a, const float* __restrict__ b) {
-  if (lab < d.n_bool) return __ldg(a + (size_t)lab * R + r) < 0.f;
+                                                    const float* __restrict__ a, const float* __restrict__ b,
+                                                    bool& bad) {
+  if (lab < d.n_bool) {
+    const float av = __ldg(a + (size_t)lab * R + r);
+    bad |= !isfinite(av);
+    return av < 0.f;
+  }
   // filtered first; outside the filter's band z != 0, so the atom holds iff z < 0
   // whatever its strictness; inside it the exact path decides
   const int i = lab - d.n_bool;
@@ -95,6 +105,7 @@ __device__ __forceinline__ bool literal_truth_exact(const DevView& d, int lab, i
   float z = -q0, mag = fabsf(q0);
   for (int k = k0; k < k1; ++k) {
     const float c = __ldg(d.atom_coef + k), y = __ldg(b + (size_t)__ldg(d.atom_var + k) * R + r);
+    bad |= !isfinite(y);
     z = fmaf(c, y, z);
     mag = fmaf(fabsf(c), fabsf(y), mag);
   }
@@ -613,10 +624,12 @@ __global__ void k_round_check(DevView d, int R, const float* __restrict__ a, con
       const int r = t * 32 + lane;
       if (r >= R) continue;
       int v = root;
+      bool bad = false;
       while (v < V) {
         const uint2 nd = d.nodes[nb + v];
-        v = literal_truth_exact(d, (int)nd.x, R, r, a, b) ? (int)(nd.y & 0xffff) : (int)(nd.y >> 16);
+        v = literal_truth_exact(d, (int)nd.x, R, r, a, b, bad) ? (int)(nd.y & 0xffff) : (int)(nd.y >> 16);
       }
+      if (bad) atomicOr(n_unsat + r, kUnsatNonFinite);
       const int u = v != V ? 1 : 0;
       if (viol) viol[(size_t)cid * R + r] = (uint8_t)u;
       if (u) atomicAdd(cnt_s + r, 1);
@@ -696,7 +709,9 @@ __global__ void __launch_bounds__(kCheckThreads, 3)
       __syncthreads();  // chunk loaded / the previous tile's walks are done
       for (int e = threadIdx.x; e < nr * 32; e += blockDim.x) {
         const int rr = t * 32 + (e & 31);
-        s_b[e] = rr < R ? __ldg(b + (size_t)__ldg(d.real_id + e0 + (e >> 5)) * R + rr) : 0.f;
+        const float y = rr < R ? __ldg(b + (size_t)__ldg(d.real_id + e0 + (e >> 5)) * R + rr) : 0.f;
+        if (!isfinite(y)) atomicOr(n_unsat + rr, kUnsatNonFinite);
+        s_b[e] = y;
       }
       __syncthreads();
       for (int i = warp; i < ns; i += W) {
@@ -704,7 +719,9 @@ __global__ void __launch_bounds__(kCheckThreads, 3)
         bool holds = false;
         if (ok) {
           if (lab < d.n_bool) {
-            holds = __ldg(a + (size_t)lab * R + r) < 0.f;
+            const float av = __ldg(a + (size_t)lab * R + r);
+            if (!isfinite(av)) atomicOr(n_unsat + r, kUnsatNonFinite);
+            holds = av < 0.f;
           } else {  // the filter on the staged reals, else the exact test
             const int meta = s_meta[i], tb = meta >> 16, tc = meta & 0xffff;
             const float q0 = s_q0[i];
@@ -1557,6 +1574,12 @@ fsmt_status fsmt_solve_stage_host(fsmt_compiled* cc, const fsmt_stage_config* cf
     FSMT_CUDA(cudaMemcpyAsync(n_unsat_host, s->n_unsat, sizeof(int32_t) * R, cudaMemcpyDeviceToHost, st), "copy n_unsat");
   if (obj_host) FSMT_CUDA(cudaMemcpyAsync(obj_host, s->obj, sizeof(float) * R, cudaMemcpyDeviceToHost, st), "copy obj");
   FSMT_CUDA(cudaStreamSynchronize(st), "stage sync");
+  if (n_unsat_host)
+    for (size_t r = 0; r < R; ++r)
+      if (n_unsat_host[r] < 0) {
+        set_error("non-finite point in restart " + std::to_string(r));
+        return FSMT_ENAN;
+      }
   return FSMT_OK;
 }
 

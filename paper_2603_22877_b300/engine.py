@@ -416,23 +416,28 @@ class Solver:
 
     def anneal(self, schedule, time_limit=None):
         """Runs the sigma schedule; returns dict with the first exactly verified SAT restart
-        (or None), the stages run and the fewest unsatisfied constraints any restart had
-        at a rounding."""
+        (or None), the stages run, the fewest unsatisfied constraints any restart had at a
+        rounding, and how many restarts ended on a non-finite point (n_unsat < 0; they
+        are never SAT candidates).  Stops early when every restart is non-finite."""
         import torch
         t0 = time.perf_counter()
-        best, t = None, 0
+        best, t, nonfinite = None, 0, 0
         for t, sigma in enumerate(schedule, start=1):
             self.stage(sigma, t)
-            lo = int(self.n_unsat.min())
+            nu = self.n_unsat
+            nonfinite = int((nu < 0).sum())
+            if nonfinite == self.R:
+                break
+            lo = int(torch.where(nu < 0, torch.iinfo(torch.int32).max, nu).min())
             best = lo if best is None else min(best, lo)
-            cand = torch.nonzero(self.n_unsat == 0).flatten().tolist() if lo == 0 else []
+            cand = torch.nonzero(nu == 0).flatten().tolist() if lo == 0 else []
             for r in cand:
                 sat, x, y = self.verify_restart(r)
                 if sat:
-                    return dict(sat=True, restart=r, stage=t, stages_run=t, best_unsat=0,
+                    return dict(sat=True, restart=r, stage=t, stages_run=t, best_unsat=0, nonfinite=nonfinite,
                                 seconds=time.perf_counter() - t0, x=x, y=y)
             if time_limit is not None and time.perf_counter() - t0 > time_limit:
                 break
         torch.cuda.synchronize()
-        return dict(sat=False, restart=None, stage=None, stages_run=t, best_unsat=best,
+        return dict(sat=False, restart=None, stage=None, stages_run=t, best_unsat=best, nonfinite=nonfinite,
                     seconds=time.perf_counter() - t0)

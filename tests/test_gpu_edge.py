@@ -219,3 +219,38 @@ def test_every_launch_configuration_and_the_autotuner(make, R):
     assert not ga.any() and not gb.any() and not ob.any()  # scratch left zero
     obj, cop, ga2, gb2 = gpu_adjoint(comp, R, sigma, a, b, w)
     assert_grad_close(ga2, ref[2], "grad_a after autotune")
+
+
+@pytest.mark.parametrize("policy", [OBJ.PROJECT, OBJ.SOFT])
+def test_nonfinite_points_are_marked(policy):
+    """A restart whose point has a NaN or infinite coordinate that the check reads gets
+    bit 31 of its #Unsat set (chunked check and warp-per-constraint check alike); the
+    other restarts' counts are the oracle's.  The host-buffer stage reports FSMT_ENAN."""
+    import torch
+    from oracle import pgd
+    from paper_2603_22877_b300 import Solver, _lib as L
+    inst = W.jobshop(1002, 10, 5)
+    R = 40
+    P, comp, a, b, _ = setup(inst, R, policy)
+    a, b = a.copy(), b.copy()
+    bad = {3, 5, 7, 33}
+    a[0, 3] = np.nan
+    b[0, 5] = np.inf
+    b[1, 7] = np.nan
+    a[:, 33] = -np.inf
+    nu = torch.zeros(R, dtype=torch.int32, device="cuda")
+    comp.round_check(R, torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda(), nu)
+    nu = nu.cpu().numpy()
+    good = [r for r in range(R) if r not in bad]
+    _, viol = pgd.round_check(inst, a[:, good].astype(np.float64), b[:, good].astype(np.float64))
+    np.testing.assert_array_equal(nu[good], viol.sum(0))
+    assert (nu[sorted(bad)] < 0).all()
+    # the fused stage from host buffers: FSMT_ENAN, the finite restarts still iterate
+    S = Solver(P, comp, R, eta=0.02, b_scale=inst.scale, t_max=3)
+    nuh = np.zeros(R, np.int32)
+    ob = np.zeros(R, np.float32)
+    with pytest.raises(L.FsmtError) as err:
+        S.stage_host(inst.scale / 0.5, 1, np.ascontiguousarray(a), np.ascontiguousarray(b), nuh, ob)
+    assert err.value.status == L.ENAN
+    assert (nuh[sorted(bad)] < 0).all() and (nuh[good] >= 0).all()
+    assert np.isfinite(ob[good]).all()
