@@ -290,7 +290,8 @@ fsmt_status fsmt_plain_noalloc(const fsmt_compiled* c, int32_t R, float sigma, c
  * passes settle); then
  * gnorm2[r] += sum ((a - a_new)/eta_r)^2 + sum ((b - b_new)/(b_scale eta_r))^2.
  * a, b (device, [n][R], [m][R]) are updated in place for restarts with
- * active[r] != 0 (active may be NULL = all); gnorm2[R] (device) is accumulated,
+ * active[r] == 1 (active may be NULL = all; 0 and 2 are stopped restarts, as
+ * fsmt_solve_stage writes them); gnorm2[R] (device) is accumulated,
  * so the caller zeroes it first.  eta > 0, sweeps >= 0, polish >= 0; wsum (device
  * [R]) may be NULL.  Errors as above. */
 fsmt_status fsmt_weight_sum(const fsmt_compiled* c, int32_t R, const float* w, float* wsum, void* stream);
@@ -343,7 +344,8 @@ typedef struct {
   float* grad_b;   /* [n_real][R] work, zero on entry */
   float* obj;      /* [R] C_sigma at the start of the last iteration run */
   float* gnorm2;   /* [R] ||g||^2 of the last iteration run */
-  uint8_t* active; /* [R] */
+  uint8_t* active; /* [R] 1 iterating, 0 stopped by the epsilon test, 2 stopped on a
+                      non-finite ||g||^2 (its n_unsat gets bit 31 at the check) */
   int32_t* iters;  /* [R] iterations run in this stage */
   int32_t* n_unsat;/* [R] */
   int32_t* ctl;    /* [4] */

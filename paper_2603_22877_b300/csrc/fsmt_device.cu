@@ -335,7 +335,7 @@ __global__ void k_pgd_bool(DevView d, int R, float eta, const float* prm, const 
   if (ctl && ctl[0] == 0) return;
   const int r = blockIdx.x * 32 + threadIdx.x;
   const bool ok = r < R;
-  const bool act = ok && (!active || active[r]);
+  const bool act = ok && (!active || active[r] == 1);
   eta = restart_eta(d, eta, prm, wsum, r, ok);
   const float inv = 1.f / eta;
   float part = 0.f;
@@ -361,7 +361,7 @@ __global__ void k_pgd_free(DevView d, int R, float eta, float bscale, const floa
   if (ctl && ctl[0] == 0) return;
   const int r = blockIdx.x * 32 + threadIdx.x;
   const bool ok = r < R;
-  const bool act = ok && (!active || active[r]);
+  const bool act = ok && (!active || active[r] == 1);
   eta = restart_eta(d, eta, prm, wsum, r, ok);
   bscale = load_param(prm, P_BSCALE, bscale);
   const float step = eta * bscale * bscale, inv = 1.f / (bscale * eta);
@@ -400,7 +400,7 @@ __global__ void k_pgd_comp(DevView d, int R, float eta, float bscale, int sweeps
   if (ctl && ctl[0] == 0) return;
   const int r = blockIdx.x * 32 + threadIdx.x;
   const bool ok = r < R;
-  const bool act = ok && (!active || active[r]);
+  const bool act = ok && (!active || active[r] == 1);
   eta = restart_eta(d, eta, prm, wsum, r, ok);
   bscale = load_param(prm, P_BSCALE, bscale);
   if (prm) {
@@ -553,7 +553,10 @@ __global__ void k_iter_begin(int R, float* obj, float* gn2, const int* ctl) {
 }
 
 // Eq. critical per restart: the iteration just run is counted, and a restart
-// whose ||g||^2 <= eps^2 stops.  One block; ctl[0] = restarts still iterating.
+// whose ||g||^2 <= eps^2 stops (active 0); one whose ||g||^2 is not finite stops
+// with active 2 and error bit 1 in ctl[1] (its point may already have been clamped
+// back into the box, so the round check marks it from active).  One block;
+// ctl[0] = restarts still iterating.
 __global__ void k_converge(int R, const float* prm, const float* gn2, uint8_t* active, int* iters, int* ctl) {
   if (ctl[0] == 0) return;
   __syncthreads();
@@ -561,11 +564,11 @@ __global__ void k_converge(int R, const float* prm, const float* gn2, uint8_t* a
   const float eps2 = eps * eps;
   int cnt = 0;
   for (int r = threadIdx.x; r < R; r += blockDim.x) {
-    if (!active[r]) continue;
+    if (active[r] != 1) continue;
     iters[r] += 1;
     const float g = gn2[r];
-    if (isnan(g)) {
-      active[r] = 0;
+    if (!isfinite(g)) {
+      active[r] = 2;
       atomicOr(ctl + 1, 1);
     } else if (g <= eps2) {
       active[r] = 0;
@@ -603,7 +606,7 @@ __device__ __forceinline__ float erwa_scale(const DevView& d, const float* wsum,
 __global__ void k_round_check(DevView d, int R, const float* __restrict__ a, const float* __restrict__ b,
                               uint8_t* __restrict__ viol, int* __restrict__ n_unsat, float* __restrict__ w,
                               float* __restrict__ h, float rho, float gamma, int update_w, const float* prm,
-                              const float* __restrict__ wsum, int s_begin) {
+                              const float* __restrict__ wsum, const uint8_t* __restrict__ active, int s_begin) {
   extern __shared__ int cnt_s[];
   for (int r = threadIdx.x; r < R; r += blockDim.x) cnt_s[r] = 0;
   __syncthreads();
@@ -645,8 +648,10 @@ __global__ void k_round_check(DevView d, int R, const float* __restrict__ a, con
     }
   }
   __syncthreads();
-  for (int r = threadIdx.x; r < R; r += blockDim.x)
+  for (int r = threadIdx.x; r < R; r += blockDim.x) {
     if (cnt_s[r]) atomicAdd(n_unsat + r, cnt_s[r]);
+    if (active && blockIdx.x == 0 && active[r] == 2) atomicOr(n_unsat + r, kUnsatNonFinite);
+  }
 }
 
 // Round + check of the constraints of C_sigma over the chunk schedule, per chunk
@@ -661,7 +666,7 @@ __global__ void __launch_bounds__(kCheckThreads, 3)
     k_check_chunked(DevView d, int R, int vcap, const float* __restrict__ a, const float* __restrict__ b,
                     uint8_t* __restrict__ viol, int* __restrict__ n_unsat, float* __restrict__ w,
                     float* __restrict__ h, float rho, float gamma, int update_w, const float* prm,
-                    const float* __restrict__ wsum) {
+                    const float* __restrict__ wsum, const uint8_t* __restrict__ active) {
   extern __shared__ __align__(16) unsigned char smem[];
   uint2* s_node = reinterpret_cast<uint2*>(smem);
   int4* s_con = reinterpret_cast<int4*>(s_node + kChunkMaxNodes);
@@ -793,8 +798,10 @@ __global__ void __launch_bounds__(kCheckThreads, 3)
     }
   }
   __syncthreads();
-  for (int r = threadIdx.x; r < R; r += blockDim.x)
+  for (int r = threadIdx.x; r < R; r += blockDim.x) {
     if (cnt_s[r]) atomicAdd(n_unsat + r, cnt_s[r]);
+    if (active && blockIdx.x == 0 && active[r] == 2) atomicOr(n_unsat + r, kUnsatNonFinite);
+  }
 }
 
 __global__ void k_sign(int n, int R, const float* __restrict__ a, int8_t* __restrict__ x) {
@@ -1006,7 +1013,7 @@ fsmt_status launch_weight_sum(const Compiled& C, int R, const float* w, float* w
 
 fsmt_status launch_round_check(const Compiled& C, int R, const float* a, const float* b, uint8_t* viol, int* n_unsat,
                                float* w, float* h, float rho, float gamma, int update_w, const float* prm,
-                               const float* wsum, cudaStream_t st) {
+                               const float* wsum, const uint8_t* active, cudaStream_t st) {
   FSMT_CUDA(cudaMemsetAsync(n_unsat, 0, sizeof(int) * (size_t)R, st), "memset n_unsat");
   if (C.n_cons == 0) return FSMT_OK;
   const int threads = 256;
@@ -1023,7 +1030,7 @@ fsmt_status launch_round_check(const Compiled& C, int R, const float* a, const f
   if (C.chunked_ok && C.n_chunks > 0 && csmem <= kSmemMax) {
     const int cblocks = std::max(1, std::min(C.n_chunks, sm_count() * 3));
     k_check_chunked<<<cblocks, kCheckThreads, csmem, st>>>(C.view, R, std::max(1, C.max_nodes), a, b, viol, n_unsat,
-                                                            w, h, rho, gamma, update_w, prm, wsum);
+                                                            w, h, rho, gamma, update_w, prm, wsum, active);
     FSMT_CUDA(cudaGetLastError(), "chunked check launch");
     s_begin = C.n_obj;
   }
@@ -1031,7 +1038,7 @@ fsmt_status launch_round_check(const Compiled& C, int R, const float* a, const f
     const int blocks =
         (int)std::max<long>(1, std::min<long>((C.n_cons - s_begin + 7) / 8, (long)sm_count() * 4));
     k_round_check<<<blocks, threads, smem, st>>>(C.view, R, a, b, viol, n_unsat, w, h, rho, gamma, update_w, prm,
-                                                 wsum, s_begin);
+                                                 wsum, active, s_begin);
     FSMT_CUDA(cudaGetLastError(), "round_check launch");
   }
   return FSMT_OK;
@@ -1470,7 +1477,7 @@ fsmt_status fsmt_round_check(const fsmt_compiled* c, int32_t R, const float* a, 
     k_sign<<<std::min<long>(((long)C.n_bool * R + 255) / 256, 65535L), 256, 0, st>>>(C.n_bool, R, a, x);
     FSMT_CUDA(cudaGetLastError(), "sign launch");
   }
-  return launch_round_check(C, R, a, b, violated, n_unsat, w, h, rho, gamma, update_w, nullptr, wsum, st);
+  return launch_round_check(C, R, a, b, violated, n_unsat, w, h, rho, gamma, update_w, nullptr, wsum, nullptr, st);
 }
 
 static fsmt_status enqueue_stage(const Compiled& C, int t_max, fsmt_state* s, cudaStream_t st) {
@@ -1490,7 +1497,8 @@ static fsmt_status enqueue_stage(const Compiled& C, int t_max, fsmt_state* s, cu
     k_converge<<<1, 1024, 0, st>>>(R, s->params, s->gnorm2, s->active, s->iters, s->ctl);
     FSMT_CUDA(cudaGetLastError(), "converge");
   }
-  return launch_round_check(C, R, s->a, s->b, nullptr, s->n_unsat, s->w, s->h, 0.f, 2.f, 0, s->params, s->wsum, st);
+  return launch_round_check(C, R, s->a, s->b, nullptr, s->n_unsat, s->w, s->h, 0.f, 2.f, 0, s->params, s->wsum,
+                            s->active, st);
 }
 
 fsmt_status fsmt_solve_stage(fsmt_compiled* cc, const fsmt_stage_config* cfg, fsmt_state* s, void* stream) {

@@ -392,15 +392,17 @@ class Solver:
             comp.pgd_step(R, self.eta, self.b_scale, self.sweeps, self.a, self.b, self.grad_a, self.grad_b,
                           self.gnorm2, active=self.active, wsum=self.wsum if self.normalize_eta else None,
                           polish=self.polish, stream=stream)
-            act = self.active.bool()
+            act = self.active == 1
             self.iters += act.to(torch.int32)
-            done = act & ((self.gnorm2 <= eps2) | torch.isnan(self.gnorm2))
-            self.active.masked_fill_(done, 0)
-            if not bool(self.active.any()):
+            self.active.masked_fill_(act & ~torch.isfinite(self.gnorm2), 2)
+            self.active.masked_fill_(act & (self.gnorm2 <= eps2), 0)
+            if not bool((self.active == 1).any()):
                 break
         comp.round_check(R, self.a, self.b, self.n_unsat, w=self.w, h=self.h, rho=self.rho, gamma=self.gamma,
                          update_w=(t % self.tau == 0), wsum=self.wsum if self.normalize_eta else None,
                          stream=stream)
+        stopped = self.active == 2                       # as the fused stage marks them
+        self.n_unsat[stopped] |= torch.iinfo(torch.int32).min
 
     def stage_host(self, sigma, t, a_host, b_host, n_unsat_host, obj_host, stream=None):
         """The same stage with host input/output buffers (copies inside the call)."""

@@ -225,7 +225,10 @@ def test_every_launch_configuration_and_the_autotuner(make, R):
 def test_nonfinite_points_are_marked(policy):
     """A restart whose point has a NaN or infinite coordinate that the check reads gets
     bit 31 of its #Unsat set (chunked check and warp-per-constraint check alike); the
-    other restarts' counts are the oracle's.  The host-buffer stage reports FSMT_ENAN."""
+    other restarts' counts are the oracle's.  In a stage the box clamp turns such a
+    point finite after one step, so the restart is marked from its non-finite ||g||^2
+    (active = 2), in the fused and the plain form; the host-buffer stage reports
+    FSMT_ENAN."""
     import torch
     from oracle import pgd
     from paper_2603_22877_b300 import Solver, _lib as L
@@ -254,3 +257,9 @@ def test_nonfinite_points_are_marked(policy):
     assert err.value.status == L.ENAN
     assert (nuh[sorted(bad)] < 0).all() and (nuh[good] >= 0).all()
     assert np.isfinite(ob[good]).all()
+    assert (S.active.cpu().numpy()[sorted(bad)] == 2).all() and int(S.ctl[1].item()) == 1
+    S2 = Solver(P, comp, R, eta=0.02, b_scale=inst.scale, t_max=3, form="plain")
+    S2.reset(a, b)
+    S2.stage(inst.scale / 0.5, 1)
+    nu2 = S2.n_unsat.cpu().numpy()
+    assert (nu2[sorted(bad)] < 0).all() and (nu2[good] >= 0).all()
