@@ -40,6 +40,8 @@ WORKLOADS = {
     # the encoding read literally: 1,000 jobs on 20 workers (5 index bits, 6,000 variables)
     "large_scheduling_lit": (lambda: W.large_scheduling(1005, n_workers=20, n_jobs=1000, n_late=6), 512),
     "placement2d": (lambda: W.placement2d(1003), 1024),
+    # the paper's 3D placement encoding: 64 macros x 8 layers, 896 modules
+    "placement3d": (lambda: W.placement3d(1007), 512),
     "jobshop": (lambda: W.jobshop(1002), 256),
     "uneven_batch": (lambda: W.concat(W.uneven_batch(1004), "uneven_batch"), 32),
     "tiny_random": (lambda: W.tiny_random(1001), 64),

@@ -21,6 +21,7 @@ CASES = {
     "placement_nosel_R40": (lambda: W.placement2d(1003, 16, selectors=False), 40),
     "sched_small_R37": (lambda: W.large_scheduling(1005, 16, 30, 6, 4, 5), 37),
     "sched_5w_R50": (lambda: W.large_scheduling(1005, 5, 30, 6, 4, 5), 50),
+    "placement3d_R36": (lambda: W.placement3d(1007, 4, 2), 36),
     "batch_small_R32": (lambda: W.concat(W.uneven_batch(1004, 4, (3, 8), (2, 5)), "b"), 32),
 }
 

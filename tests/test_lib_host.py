@@ -39,6 +39,7 @@ SMALL = {
     "placement2d_nosel": lambda: W.placement2d(1003, 10, selectors=False),
     "large_scheduling": lambda: W.large_scheduling(1005, 16, 24, 6, 3, 5),
     "large_scheduling_5w": lambda: W.large_scheduling(1005, 5, 24, 6, 3, 5),
+    "placement3d": lambda: W.placement3d(1007, 4, 4),
     "uneven_batch": lambda: W.concat(W.uneven_batch(1004, 3, (3, 6), (2, 4)), "b"),
 }
 

@@ -151,7 +151,8 @@ def test_multilinear_identity():
 
 @pytest.mark.parametrize("make", [lambda: W.tiny_random(1001), lambda: W.jobshop(1002, 8, 4),
                                   lambda: W.placement2d(1003, 12), lambda: W.large_scheduling(1005, 16, 20, 6, 3, 5),
-                                  lambda: W.large_scheduling(1005, 5, 20, 6, 3, 5)])
+                                  lambda: W.large_scheduling(1005, 5, 20, 6, 3, 5),
+                                  lambda: W.placement3d(1007, 4, 2)])
 def test_soundness_at_planted_vertex(make):
     """Thm. Soundness / Cor. cop=wfe at sigma = 0: every COP is 1 and C = -sum w at a model."""
     inst = make()

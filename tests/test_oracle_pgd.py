@@ -287,3 +287,48 @@ def test_erwa_weight_rescale_keeps_long_schedules_finite():
     wc, _, _ = pgd.erwa(w0 * 3, h0, u, 1, 0.5, 2.0, 1, mean_w=np.array([2.0 ** 33, 1.0]))
     np.testing.assert_array_equal(wc[:, 0], wb[:, 0] * 2.0 ** -32)
     np.testing.assert_array_equal(wc[:, 1], wb[:, 1])
+
+
+@pytest.mark.parametrize("n_macros,n_layers", [(2, 2), (4, 2), (4, 4), (8, 2)])
+def test_placement3d_structure_and_plant(n_macros, n_layers):
+    """Generator sanity for the 3D placement encoding: module and constraint counts,
+    the association (every small memory with two small processes, every small process
+    and large module in exactly one pair), the plant satisfies every constraint
+    exactly, and moving one module of a pair to another macro (one macro bit flipped)
+    breaks that bit's equality clause with each of its partners, plus non-overlap
+    constraints with the module now at the same place in the new macro, and nothing
+    that does not involve it."""
+    inst = W.placement3d(1007, n_macros, n_layers)
+    N = 2 * n_macros + n_macros * n_layers + n_macros * n_layers // 2
+    bm, bl = n_macros.bit_length() - 1, n_layers.bit_length() - 1
+    assert inst.meta["n_modules"] == N
+    assert inst.n_bool == N * (bm + bl) and inst.n_real == 2 * N
+    n_pairs = n_macros + n_macros * n_layers
+    assert inst.meta["n_pairs"] == n_pairs
+    assert inst.n_cons == 4 * N + n_pairs * (bm + 4) + N * (N - 1) // 2
+    kinds = inst.meta["kinds"]
+    assert kinds.count("small_proc") == n_macros * n_layers and kinds.count("small_mem") == n_macros * n_layers // 2
+    # pairs from the equality clauses of macro bit 0: (module of first literal, module of second)
+    partners = {j: [] for j in range(N)}
+    for c in range(inst.n_cons):
+        if int(inst.con_kind[c]) == W.XOR:
+            l1, l2 = inst.lits(c)
+            j, k = (l1 // 2) // (bm + bl), (l2 // 2) // (bm + bl)
+            if (l1 // 2) % (bm + bl) == 0:
+                partners[j].append(k)
+                partners[k].append(j)
+    for j in range(N):
+        want = {"small_mem": 2, "small_proc": 1, "large_proc": 1, "large_mem": 1}[kinds[j]]
+        assert len(partners[j]) == want
+        other = {"small_mem": "small_proc", "small_proc": "small_mem", "large_proc": "large_mem",
+                 "large_mem": "large_proc"}[kinds[j]]
+        assert all(kinds[k] == other for k in partners[j])
+    assert S.unsat_constraints(inst, inst.planted_x, inst.planted_y) == []
+    j = kinds.index("small_proc")
+    x = inst.planted_x.copy()
+    x[j * (bm + bl)] *= -1                                   # macro bit 0 of module j
+    bad = S.unsat_constraints(inst, x, inst.planted_y)
+    assert sum(int(inst.con_kind[c]) == W.XOR for c in bad) == len(partners[j])
+    assert any(int(inst.con_kind[c]) == W.NEQ_OR for c in bad)      # it lands on a peer
+    for c in bad:
+        assert j * (bm + bl) in {int(l) // 2 for l in inst.lits(c)}

@@ -323,6 +323,119 @@ def placement2d(seed: int = 1003, n_rect=400, dim_max=30, selectors=True) -> Ins
 
 
 # ---------------------------------------------------------------------------
+# 3D placement (macro and layer index bits, routing-aware adjacency)
+# ---------------------------------------------------------------------------
+P3_MACRO = 20                                  # macro side; every size below is an integer
+P3_SIZES = {"large_proc": (8, 8), "small_proc": (4, 4), "large_mem": (2, 2)}
+
+
+def placement3d(seed: int = 1007, n_macros=64, n_layers=8) -> Instance:
+    """The paper's 3D placement encoding (Methods, "3D Placement").
+
+    Modules: n_macros large processes, n_macros*n_layers small processes, n_macros
+    large memories and n_macros*n_layers/2 small memories.  Lengths are in units of
+    1/20 of the macro side, so that every size is an integer: macro 20 x 20, large
+    process 8 x 8, small process 4 x 4, large memory 2 x 2, small memory 2 x 1 or
+    1 x 2 (its alignment along x or y drawn per element).  Module j has macro-index
+    bits m_{i,j} (log2 n_macros), layer-index bits l_{i,j} (log2 n_layers) and
+    macro-relative coordinates x_j, y_j in [0, 20].
+
+    Constraints:
+      * feasibility: unit atoms 0 <= x_j <= 20 - w_j, 0 <= y_j <= 20 - d_j;
+      * routing-aware, per associated pair (j, j'): for every macro bit i the unit
+        clause (m_{i,j} = m_{i,j'}) (an XOR with one literal negated), and the unit
+        atoms x_j - x_j' <= w_j', x_j' - x_j <= w_j, y_j - y_j' <= d_j',
+        y_j' - y_j <= d_j (the two touch or overlap in both axes; on different
+        layers they may stack);
+      * non-overlap, per pair of modules: some macro bit differs, or some layer bit
+        differs, or one of x_j - x_j' >= w_j', x_j' - x_j >= w_j, y_j - y_j' >= d_j',
+        y_j' - y_j >= d_j holds (one disjunction, as an NEQ_OR).
+    Association: each large process with one large memory, and each small memory
+    with two small processes (n_macros*n_layers small processes and half as many
+    small memories pair up only this way).  Module ids are a random permutation.
+
+    Plant, per macro t: its large pair on layer 0 at (0, 0) and (8, 0); its small
+    process k on layer k at (10, 10); its small memory q on layer 2q at (14, 10),
+    touching process 2q and stacked beside process 2q + 1.
+    """
+    assert n_macros >= 2 and n_macros & (n_macros - 1) == 0
+    assert n_layers >= 2 and n_layers & (n_layers - 1) == 0
+    rng = np.random.default_rng(seed)
+    bm, bl = n_macros.bit_length() - 1, n_layers.bit_length() - 1
+    # modules in plant order: per macro, large process, large memory, small processes, small memories
+    size, macro, layer, X, Y, kind = [], [], [], [], [], []
+    pairs = []                                          # associated (plant index, plant index)
+    for t in range(n_macros):
+        base = len(size)
+        for name, lay, xy in (("large_proc", 0, (0, 0)), ("large_mem", 0, (8, 0))):
+            size.append(P3_SIZES[name]); macro.append(t); layer.append(lay); X.append(xy[0]); Y.append(xy[1])
+            kind.append(name)
+        pairs.append((base, base + 1))
+        procs = []
+        for k in range(n_layers):
+            procs.append(len(size))
+            size.append(P3_SIZES["small_proc"]); macro.append(t); layer.append(k); X.append(10); Y.append(10)
+            kind.append("small_proc")
+        for q in range(n_layers // 2):
+            m = len(size)
+            size.append((2, 1) if rng.random() < 0.5 else (1, 2)); macro.append(t); layer.append(2 * q)
+            X.append(14); Y.append(10); kind.append("small_mem")
+            pairs += [(procs[2 * q], m), (procs[2 * q + 1], m)]
+    N = len(size)
+    perm = rng.permutation(N)                           # plant index -> module id
+    nb = bm + bl
+    mbit = lambda j, i: j * nb + i
+    lbit = lambda j, i: j * nb + bm + i
+    xv = lambda j: 2 * j
+    yv = lambda j: 2 * j + 1
+    B = _Builder(N * nb, 2 * N)
+    px = np.ones(N * nb, np.int8)
+    py = np.zeros(2 * N)
+    w = np.zeros(N, np.int64)
+    d = np.zeros(N, np.int64)
+    for s in range(N):
+        j = int(perm[s])
+        w[j], d[j] = size[s]
+        py[xv(j)], py[yv(j)] = float(X[s]), float(Y[s])
+        for i in range(bm):
+            px[mbit(j, i)] = -1 if (macro[s] >> i) & 1 else 1
+        for i in range(bl):
+            px[lbit(j, i)] = -1 if (layer[s] >> i) & 1 else 1
+    # feasibility
+    for j in range(N):
+        for v, sz in ((xv(j), w[j]), (yv(j), d[j])):
+            B.con(OR, [lit(B.atom([v], [-1], 0, LE))])
+            B.con(OR, [lit(B.atom([v], [1], P3_MACRO - int(sz), LE))])
+    # routing-aware
+    for s, s2 in pairs:
+        j, k = int(perm[s]), int(perm[s2])
+        for i in range(bm):
+            B.con(XOR, [lit(mbit(j, i)), lit(mbit(k, i), neg=True)])
+        B.con(OR, [lit(B.atom([xv(j), xv(k)], [1, -1], int(w[k]), LE))])
+        B.con(OR, [lit(B.atom([xv(k), xv(j)], [1, -1], int(w[j]), LE))])
+        B.con(OR, [lit(B.atom([yv(j), yv(k)], [1, -1], int(d[k]), LE))])
+        B.con(OR, [lit(B.atom([yv(k), yv(j)], [1, -1], int(d[j]), LE))])
+    # non-overlap
+    for j in range(N):
+        for k in range(j + 1, N):
+            lits = []
+            for i in range(bm):
+                lits += [lit(mbit(j, i)), lit(mbit(k, i))]
+            for i in range(bl):
+                lits += [lit(lbit(j, i)), lit(lbit(k, i))]
+            lits += [lit(B.atom([xv(k), xv(j)], [1, -1], -int(w[k]), LE)),   # x_j - x_k >= w_k
+                     lit(B.atom([xv(j), xv(k)], [1, -1], -int(w[j]), LE)),   # x_k - x_j >= w_j
+                     lit(B.atom([yv(k), yv(j)], [1, -1], -int(d[k]), LE)),   # y_j - y_k >= d_k
+                     lit(B.atom([yv(j), yv(k)], [1, -1], -int(d[j]), LE))]   # y_k - y_j >= d_j
+            B.con(NEQ_OR, lits, param=nb)
+    lo = np.zeros(2 * N)
+    hi = np.full(2 * N, float(P3_MACRO))
+    kinds = np.array(kind)[np.argsort(perm)]
+    return B.freeze("placement3d", lo, hi, px, py, float(P3_MACRO), seed=seed, n_macros=n_macros,
+                    n_layers=n_layers, n_modules=N, n_pairs=len(pairs), kinds=kinds.tolist())
+
+
+# ---------------------------------------------------------------------------
 # Large continuous-time scheduling (worker-index bits, pairwise non-overlap)
 # ---------------------------------------------------------------------------
 def large_scheduling(seed: int = 1005, n_workers=256, n_jobs=1111, dur_max=20,
@@ -526,6 +639,7 @@ CONFIGS = {
     "placement2d": dict(make=lambda: placement2d(1003), R=1024),
     "uneven_batch": dict(make=lambda: concat(uneven_batch(1004), "uneven_batch"), R=32),
     "large_scheduling": dict(make=lambda: large_scheduling(1005), R=512),
+    "placement3d": dict(make=lambda: placement3d(1007), R=512),
     "large_scheduling_lit": dict(make=lambda: large_scheduling(1005, n_workers=20, n_jobs=1000, n_late=6), R=512),
     "random_hybrid": dict(make=lambda: random_hybrid(1006, 1000), R=100),
 }
