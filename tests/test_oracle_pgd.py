@@ -332,3 +332,36 @@ def test_placement3d_structure_and_plant(n_macros, n_layers):
     assert any(int(inst.con_kind[c]) == W.NEQ_OR for c in bad)      # it lands on a peer
     for c in bad:
         assert j * (bm + bl) in {int(l) // 2 for l in inst.lits(c)}
+
+
+def test_scheduling_early_closing_windows():
+    """The deadline side of the workers' availability windows: the plant (redone so that
+    no job on an early-closing worker ends after its close) satisfies every constraint
+    exactly; each window clause is (X_j != w) OR (y_j + t_j <= e_w), so re-coding a job
+    to such a worker with its start just past e_w - t_j violates exactly that clause
+    among the constraints that involve only this job; the default instance is unchanged
+    by the option's existence (its own random stream)."""
+    base = W.large_scheduling(1005, 16, 30, 6, 4, 5)
+    inst = W.large_scheduling(1005, 16, 30, 6, 4, 5, n_early=5)
+    bits = 4
+    assert inst.n_cons == base.n_cons + 5 * 30
+    assert S.unsat_constraints(inst, inst.planted_x, inst.planted_y) == []
+    close = inst.meta["close"]
+    # the window clauses are the last 5 * 30 constraints, worker by worker
+    first = inst.n_cons - 5 * 30
+    lits = inst.lits(first)                      # worker w_0, job 0
+    w0 = sum(1 << i for i, l in enumerate(lits[:bits]) if l & 1)
+    var, coef, q0, rel = inst.atom(int(lits[-1]) // 2 - inst.n_bool)
+    assert list(var) == [0] and list(coef) == [1]
+    t0 = close[0] - int(q0)                      # q0 = e_w - t_0
+    assert 1 <= t0 <= 6
+    x = inst.planted_x.copy()
+    y = inst.planted_y.copy()
+    for i in range(bits):
+        x[i] = -1 if (w0 >> i) & 1 else 1
+    y[0] = float(close[0] - t0 + 1)
+    own = [c for c in range(inst.n_cons)
+           if all(l // 2 < bits or (l // 2 >= inst.n_bool and list(inst.atom(l // 2 - inst.n_bool)[0]) == [0])
+                  for l in inst.lits(c))]
+    bad = [c for c in own if not S.constraint_holds(inst, c, x, y)]
+    assert bad == [first]

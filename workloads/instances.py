@@ -439,14 +439,18 @@ def placement3d(seed: int = 1007, n_macros=64, n_layers=8) -> Instance:
 # Large continuous-time scheduling (worker-index bits, pairwise non-overlap)
 # ---------------------------------------------------------------------------
 def large_scheduling(seed: int = 1005, n_workers=256, n_jobs=1111, dur_max=20,
-                     n_late=72, late_max=10, chain_max=3) -> Instance:
+                     n_late=72, late_max=10, chain_max=3, n_early=0, name="large_scheduling") -> Instance:
     """The paper's scheduling encoding at ~10k variables / ~0.7M constraints.
 
     Per job j: worker-index bits x_{i,j} (log2 n_workers of them) and a start time y_j.
     Constraints: per-pair non-overlap  OR_i (x_{i,j} xor x_{i,j'}) OR (y_j - y_j' >= t_j')
     OR (y_j' - y_j >= t_j); precedence y_j >= y_j' + t_j' inside short job chains;
     release/deadline unit atoms 0 <= y_j, y_j + t_j <= T; and, for each of ``n_late``
-    workers that start late at d_w, per job: (X_j != w) OR (y_j >= d_w).
+    workers that start late at d_w, per job: (X_j != w) OR (y_j >= d_w).  With
+    ``n_early`` > 0, as many workers also close early at e_w (the deadline side of a
+    worker's availability window), per job: (X_j != w) OR (y_j + t_j <= e_w); e_w is
+    drawn in [0.5, 0.8] x the makespan of the plain greedy plant, and the plant is then
+    redone so that no job on such a worker ends after e_w.
 
     When n_workers is not a power of two the index takes ceil(log2 n_workers) bits and
     each job also gets clauses that keep X_j below n_workers: the unused codes
@@ -472,15 +476,30 @@ def large_scheduling(seed: int = 1005, n_workers=256, n_jobs=1111, dur_max=20,
             pred[q] = q - 1
         j += ln
     # planted greedy schedule: each job to the worker where it can start earliest
-    free = d.copy()
-    Y = np.zeros(n_jobs, np.int64)
-    W = np.zeros(n_jobs, np.int64)
-    for j in range(n_jobs):
-        ready = 0 if pred[j] < 0 else Y[pred[j]] + t[pred[j]]
-        st = np.maximum(free, ready)
-        w = int(np.argmin(st))
-        Y[j], W[j] = st[w], w
-        free[w] = st[w] + t[j]
+    def greedy(close):
+        free = d.copy()
+        Y = np.zeros(n_jobs, np.int64)
+        W = np.zeros(n_jobs, np.int64)
+        for j in range(n_jobs):
+            ready = 0 if pred[j] < 0 else Y[pred[j]] + t[pred[j]]
+            st = np.maximum(free, ready)
+            if close is not None:
+                st = np.where(st + t[j] <= close, st, np.iinfo(np.int64).max)
+            w = int(np.argmin(st))
+            Y[j], W[j] = st[w], w
+            free[w] = st[w] + t[j]
+        return Y, W
+
+    Y, W = greedy(None)
+    early, e = np.zeros(0, np.int64), None
+    if n_early:
+        assert n_early < n_workers
+        rng2 = np.random.default_rng([seed, 2])   # its own stream: n_early = 0 draws nothing
+        early = rng2.choice(n_workers, n_early, replace=False)
+        M = int((Y + t).max())
+        e = np.full(n_workers, np.iinfo(np.int64).max // 2)
+        e[early] = rng2.integers(int(math.ceil(0.5 * M)), int(math.ceil(0.8 * M)) + 1, n_early)
+        Y, W = greedy(e)
     T = int(math.ceil(1.2 * int((Y + t).max())))
     xb = lambda i, j: j * bits + i  # Boolean id of bit i of job j
     B = _Builder(n_bool, n_real)
@@ -524,10 +543,17 @@ def large_scheduling(seed: int = 1005, n_workers=256, n_jobs=1111, dur_max=20,
             lits = [lit(xb(i, j), neg=bool((int(w) >> i) & 1)) for i in range(bits)]
             lits.append(lit(B.atom([j], [-1], -int(d[w]), LE)))
             B.con(OR, lits)
+    # early-closing workers: (X_j != w) OR (y_j + t_j <= e_w)
+    for w in early:
+        for j in range(n_jobs):
+            lits = [lit(xb(i, j), neg=bool((int(w) >> i) & 1)) for i in range(bits)]
+            lits.append(lit(B.atom([j], [1], int(e[w]) - int(t[j]), LE)))
+            B.con(OR, lits)
     lo = np.zeros(n_real)
     hi = np.full(n_real, float(T))
-    return B.freeze("large_scheduling", lo, hi, px, py, float(dur_max), seed=seed, horizon=T,
-                    n_workers=n_workers, n_jobs=n_jobs, n_late=n_late)
+    return B.freeze(name, lo, hi, px, py, float(dur_max), seed=seed, horizon=T,
+                    n_workers=n_workers, n_jobs=n_jobs, n_late=n_late, n_early=n_early,
+                    close=(e[early].tolist() if n_early else []))
 
 
 def concat(instances, name="batch") -> Instance:
