@@ -367,8 +367,14 @@ def our_arm(args):
     # the schedule 1/sigma = 0.1, 0.2, ... in units of the instance scale,
     # continued past 2.0 until SAT or the time limit
     # (one run per initial-point seed, each from a fresh solver, graph capture included;
-    # the first seed's points are the bench's own)
+    # the first seed's points are the bench's own).  Under torchrun every rank is a
+    # replica with its own seeds; they share a [SAT verified, out of time] flag per stage
+    # and all stop at the first stage where some replica verified SAT.
     tts = None
+    share = None
+    if ws > 1:
+        from paper_2603_22877_b300 import max_over_replicas
+        share = max_over_replicas("cuda" if torch.distributed.get_backend() == "nccl" else "cpu")
     if args.tts > 0:
         tts = {"eta": args.tts_eta, "iters_per_stage": args.tts_iters, "limit_s": args.tts}
         sched_tts = [inst.scale / (0.1 * t) for t in range(1, 1001)]
@@ -380,11 +386,14 @@ def our_arm(args):
                             use_graph=True, form=form)
                 S2.reset(pa, pb)
                 torch.cuda.synchronize()
-                res = S2.anneal(sched_tts, time_limit=args.tts)
-                rec = {"sat": res["sat"], "seconds": res["seconds"], "stage": res["stage"],
+                res = S2.anneal(sched_tts, time_limit=args.tts, share=share)
+                solved = res["sat"] or res["stopped_by_peer"]   # by this replica or another
+                rec = {"sat": solved, "seconds": res["seconds"], "stage": res["stages_run"] if solved else None,
                        "restart": res["restart"], "stages_run": res["stages_run"], "best_unsat": res["best_unsat"]}
-                if res["sat"]:
-                    rec["inv_sigma_over_scale"] = round(0.1 * res["stage"], 1)
+                if ws > 1:
+                    rec["found_here"] = res["sat"]
+                if solved:
+                    rec["inv_sigma_over_scale"] = round(0.1 * res["stages_run"], 1)
                 runs.append(rec)
                 del S2
                 torch.cuda.empty_cache()

@@ -276,6 +276,22 @@ def _autograd_function():
     return _RelaxedObjective
 
 
+def max_over_replicas(device="cpu"):
+    """The `share` function of Solver.anneal over the default torch.distributed process
+    group: an elementwise max all-reduce of a few integer flags (the restart replicas'
+    one exchange; put the tensor on "cuda" under NCCL).  The identity without a group."""
+    import torch
+    import torch.distributed as dist
+
+    def share(flags):
+        if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+            return list(flags)
+        t = torch.tensor([int(f) for f in flags], dtype=torch.int32, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return [int(v) for v in t.tolist()]
+    return share
+
+
 class _Lazy:
     def __init__(self):
         self.fn = None
@@ -416,11 +432,18 @@ class Solver:
         sat, _ = self.problem.verify_exact(x, y)
         return sat, x, y
 
-    def anneal(self, schedule, time_limit=None):
-        """Runs the sigma schedule; returns dict with the first exactly verified SAT restart
-        (or None), the stages run, the fewest unsatisfied constraints any restart had at a
-        rounding, and how many restarts ended on a non-finite point (n_unsat < 0; they
-        are never SAT candidates).  Stops early when every restart is non-finite."""
+    def anneal(self, schedule, time_limit=None, share=None):
+        """Runs the sigma schedule (Alg. 2); returns dict with the first exactly verified
+        SAT restart (or None), the stages run, the fewest unsatisfied constraints any
+        restart had at a rounding, and how many restarts ended on a non-finite point
+        (n_unsat < 0; they are never SAT candidates).  Without `share` it stops early when
+        every restart is non-finite.
+
+        share: for restart replicas (one solver per rank, independent seeds), a function
+        that takes this rank's flags [verified SAT, out of time] and returns their
+        elementwise maximum over the ranks (max_over_replicas).  Every rank calls it once
+        per stage and all stop after the same stage: the first at which some rank
+        verified SAT (the others return stopped_by_peer = True) or ran out of time."""
         import torch
         t0 = time.perf_counter()
         best, t, nonfinite = None, 0, 0
@@ -428,18 +451,31 @@ class Solver:
             self.stage(sigma, t)
             nu = self.n_unsat
             nonfinite = int((nu < 0).sum())
-            if nonfinite == self.R:
+            found = None
+            if nonfinite < self.R:
+                lo = int(torch.where(nu < 0, torch.iinfo(torch.int32).max, nu).min())
+                best = lo if best is None else min(best, lo)
+                cand = torch.nonzero(nu == 0).flatten().tolist() if lo == 0 else []
+                for r in cand:
+                    sat, x, y = self.verify_restart(r)
+                    if sat:
+                        found = dict(sat=True, restart=r, stage=t, x=x, y=y)
+                        break
+            elif share is None:
                 break
-            lo = int(torch.where(nu < 0, torch.iinfo(torch.int32).max, nu).min())
-            best = lo if best is None else min(best, lo)
-            cand = torch.nonzero(nu == 0).flatten().tolist() if lo == 0 else []
-            for r in cand:
-                sat, x, y = self.verify_restart(r)
-                if sat:
-                    return dict(sat=True, restart=r, stage=t, stages_run=t, best_unsat=0, nonfinite=nonfinite,
-                                seconds=time.perf_counter() - t0, x=x, y=y)
-            if time_limit is not None and time.perf_counter() - t0 > time_limit:
+            late = time_limit is not None and time.perf_counter() - t0 > time_limit
+            flags = [int(found is not None), int(late)]
+            if share is not None:
+                flags = [int(v) for v in share(flags)]
+            if found is not None:
+                return dict(found, stages_run=t, best_unsat=0, nonfinite=nonfinite, stopped_by_peer=False,
+                            seconds=time.perf_counter() - t0)
+            if flags[0]:
+                return dict(sat=False, restart=None, stage=None, stages_run=t, best_unsat=best,
+                            nonfinite=nonfinite, stopped_by_peer=True, seconds=time.perf_counter() - t0)
+            if flags[1]:
                 break
-        torch.cuda.synchronize()
+        if self.n_unsat.is_cuda:
+            torch.cuda.synchronize()
         return dict(sat=False, restart=None, stage=None, stages_run=t, best_unsat=best, nonfinite=nonfinite,
-                    seconds=time.perf_counter() - t0)
+                    stopped_by_peer=False, seconds=time.perf_counter() - t0)
