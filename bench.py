@@ -12,7 +12,12 @@ graph (fused form).  value = decision-node visits of the forward+adjoint sweep
 
 Under torchrun (N > 1) every rank runs an independent replica (its own restart
 seeds; the paper runs 8 independent replicas): weak scaling, no collective on
-the data path; rank 0 prints the max-over-ranks time.
+the data path; rank 0 prints the max-over-ranks time.  In the time-to-SAT runs
+the replicas share one [SAT verified, out of time] flag per stage.
+
+Other modes: --workload (any entry of WORKLOADS), --gradient-time (the paper's
+gradient-time experiment on the random hybrid benchmark), --tts-plain (time to
+SAT in the plain form too), --impl reference (the FP64 oracle on the host).
 """
 import argparse
 import json
