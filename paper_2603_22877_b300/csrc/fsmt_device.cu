@@ -1569,6 +1569,8 @@ fsmt_status fsmt_solve_stage_host(fsmt_compiled* cc, const fsmt_stage_config* cf
     set_error("NULL argument");
     return FSMT_EINVAL;
   }
+  fsmt_status ready = check_ready(cc, s->R);  // before any copy into the state
+  if (ready != FSMT_OK) return ready;
   const Compiled& C = cc->c;
   cudaStream_t st = (cudaStream_t)stream;
   const size_t R = (size_t)s->R;

@@ -184,3 +184,57 @@ def test_device_calls_need_upload():
     comp = Problem.from_instance(inst).compile()
     st = L.load().fsmt_forward(comp.h, 4, C.c_float(1.0), None, None, None, None, None, None)
     assert st == L.ESTATE
+
+
+def _header_params():
+    """Parameter count of every function declared in include/fsmt.h."""
+    import re
+    text = open(os.path.join(ROOT, "include", "fsmt.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    out = {}
+    for m in re.finditer(r"\b(fsmt_\w+)\s*\(([^;{]*?)\)\s*;", text, flags=re.S):
+        params = m.group(2).strip()
+        out[m.group(1)] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_prototypes_match_the_header():
+    """The ctypes prototypes have as many arguments as the C declarations (a missing or
+    extra argument would shift every later one)."""
+    declared = _header_params()
+    assert set(declared) == set(L.PROTOTYPES)
+    for name, n in declared.items():
+        assert len(L.PROTOTYPES[name]) == n, name
+
+
+DEVICE_CALLS = ["fsmt_forward", "fsmt_adjoint", "fsmt_launch_configs", "fsmt_select_config", "fsmt_autotune",
+                "fsmt_forward_plain", "fsmt_adjoint_plain", "fsmt_plain_noalloc", "fsmt_weight_sum",
+                "fsmt_pgd_step", "fsmt_round_check", "fsmt_solve_stage", "fsmt_solve_stage_host"]
+
+
+@pytest.mark.parametrize("name", DEVICE_CALLS)
+def test_every_device_call_checks_upload_first(name):
+    """Every entry point that runs on the device answers FSMT_ESTATE for a compiled
+    object that was never uploaded, before touching any buffer or the CUDA runtime
+    (here there is no GPU at all)."""
+    inst = W.tiny_random(5, n_bool=4, n_real=4, n_cons=5)
+    comp = Problem.from_instance(inst).compile()
+    args = [comp.h]
+    for t in L.PROTOTYPES[name][1:]:
+        if t is C.c_int32:
+            args.append(4)
+        elif t is C.c_float:
+            args.append(C.c_float(1.0))
+        elif t is C.c_void_p:
+            args.append(None)
+        elif t == C.POINTER(L.State):
+            args.append(C.byref(L.State(R=4)))
+        elif t == C.POINTER(L.StageConfig):
+            args.append(C.byref(L.StageConfig()))
+        elif t == C.POINTER(L.LaunchConfig):
+            args.append(C.byref(L.LaunchConfig()))
+        elif t == C.POINTER(C.c_int32):
+            args.append(C.byref(C.c_int32()))
+        else:
+            raise AssertionError(f"{name}: unhandled argument type {t}")
+    assert getattr(L.load(), name)(*args) == L.ESTATE
