@@ -365,3 +365,37 @@ def test_scheduling_early_closing_windows():
                   for l in inst.lits(c))]
     bad = [c for c in own if not S.constraint_holds(inst, c, x, y)]
     assert bad == [first]
+
+
+def test_fig2_sigma_above_two_reaches_the_global_minimum():
+    """Fig. 2's trajectories (tests/golden/fig2_sigma.json): from starts in the local
+    minimum's basin, PGD at a fixed sigma above 2 ends at the global minimum (x = -1,
+    y > 0) and takes more iterations than at sigma = 0.5, below 2 it ends at the local
+    one (x = +1, y <= 0).  A sign error in the gradient, a wrong smoothing width or a
+    dropped constraint moves these end points."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "fig2_sigma.json")))
+    B = W._Builder(1, 1)
+    A = B.atom([0], [1], 0, W.GT)
+    B.con(W.XOR, [W.lit(0, True), W.lit(A)])
+    B.con(W.CARD_LE, [W.lit(0, True), W.lit(A, True)], param=0)
+    inst = B.freeze("fig2", np.array([-1.0]), np.array([1.0]), [-1], np.array([0.5]), 1.0)
+    cfg = pgd.Config(eta=0.05, t_max=3000, eps=1e-6)
+
+    def run(sigma, a0, b0):
+        w, h = np.ones((2, 1)), np.zeros((2, 1))
+        a, b, _, _, _, its, _ = pgd.run_stage(inst, np.array([[a0]]), np.array([[b0]]), w, h, sigma, 1, cfg)
+        return a[0, 0], b[0, 0], int(its[0])
+
+    for a0, b0 in g["starts"]:
+        slow = []
+        for sigma in g["sigma_global"]:
+            a, b, its = run(sigma, a0, b0)
+            assert a == -1.0 and b > 0, (sigma, a0, b0, a, b)
+            slow.append(its)
+        for sigma in g["sigma_local"]:
+            a, b, its = run(sigma, a0, b0)
+            assert a == 1.0 and b <= 0, (sigma, a0, b0, a, b)
+            if sigma == g["sigma_fast"]:
+                assert min(slow) > its
