@@ -407,7 +407,7 @@ def our_arm(args):
                          "seeds": len(runs), "runs": runs}
 
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:  # the host baseline runs at N = 1 only
         rate, k, v, dt = oracle_sample_rate(inst, R, a0, b0, np.ones((inst.n_cons, R), np.float32), sigma, 15.0)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"first {k} constraints of C_sigma x {R} restarts, FP64 numpy forward+adjoint, "
