@@ -67,6 +67,8 @@ def parse():
     p.add_argument("--tts-plain", action="store_true", help="also time-to-SAT in the plain (unfused) form")
     p.add_argument("--tts-eta", type=float, default=0.2)
     p.add_argument("--tts-iters", type=int, default=20, help="PGD iterations per stage in the time-to-SAT runs")
+    p.add_argument("--tts-trace", default=None,
+                   help="JSON-lines file for the per-stage records of the time-to-SAT runs (Solver.anneal log)")
     p.add_argument("--tts-seeds", type=int, default=5,
                    help="initial-point seeds per form; the median is PAR-2 (a miss counts twice the limit)")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -391,7 +393,14 @@ def our_arm(args):
                             use_graph=True, form=form)
                 S2.reset(pa, pb)
                 torch.cuda.synchronize()
-                res = S2.anneal(sched_tts, time_limit=args.tts, share=share)
+                log = None
+                if args.tts_trace and rank == 0:
+                    from paper_2603_22877_b300 import jsonl_log
+                    log = jsonl_log(args.tts_trace)
+                    log({"form": form, "seed": s, "workload": args.workload, "restarts": R})
+                res = S2.anneal(sched_tts, time_limit=args.tts, share=share, log=log)
+                if log is not None:
+                    log.close()
                 solved = res["sat"] or res["stopped_by_peer"]   # by this replica or another
                 rec = {"sat": solved, "seconds": res["seconds"], "stage": res["stages_run"] if solved else None,
                        "restart": res["restart"], "stages_run": res["stages_run"], "best_unsat": res["best_unsat"]}

@@ -7,6 +7,7 @@ arguments; importing it does not touch the GPU, and every device entry point
 fails loudly if the library is missing.
 """
 from ._lib import FsmtError, load  # noqa: F401
-from .engine import Compiled, Problem, Solver, max_over_replicas, relaxed_objective  # noqa: F401
+from .engine import Compiled, Problem, Solver, jsonl_log, max_over_replicas, relaxed_objective  # noqa: F401
 
-__all__ = ["FsmtError", "load", "Problem", "Compiled", "Solver", "max_over_replicas", "relaxed_objective"]
+__all__ = ["FsmtError", "load", "Problem", "Compiled", "Solver", "jsonl_log", "max_over_replicas",
+           "relaxed_objective"]

@@ -276,6 +276,19 @@ def _autograd_function():
     return _RelaxedObjective
 
 
+def jsonl_log(path):
+    """A `log` function for Solver.anneal that appends each stage's record to a JSON-lines
+    file (one object per line, flushed per stage)."""
+    import json
+    f = open(path, "a")
+
+    def write(rec):
+        f.write(json.dumps(rec) + "\n")
+        f.flush()
+    write.close = f.close
+    return write
+
+
 def max_over_replicas(device="cpu"):
     """The `share` function of Solver.anneal over the default torch.distributed process
     group: an elementwise max all-reduce of a few integer flags (the restart replicas'
@@ -432,7 +445,7 @@ class Solver:
         sat, _ = self.problem.verify_exact(x, y)
         return sat, x, y
 
-    def anneal(self, schedule, time_limit=None, share=None):
+    def anneal(self, schedule, time_limit=None, share=None, log=None):
         """Runs the sigma schedule (Alg. 2); returns dict with the first exactly verified
         SAT restart (or None), the stages run, the fewest unsatisfied constraints any
         restart had at a rounding, and how many restarts ended on a non-finite point
@@ -443,7 +456,12 @@ class Solver:
         that takes this rank's flags [verified SAT, out of time] and returns their
         elementwise maximum over the ranks (max_over_replicas).  Every rank calls it once
         per stage and all stop after the same stage: the first at which some rank
-        verified SAT (the others return stopped_by_peer = True) or ran out of time."""
+        verified SAT (the others return stopped_by_peer = True) or ran out of time.
+
+        log: called after every stage with one record (a dict: stage, sigma, seconds since
+        the start, fewest and median #Unsat over the finite restarts, restarts at #Unsat
+        0, non-finite restarts, mean PGD iterations, median ||g||^2 of the last iteration,
+        best objective); jsonl_log(path) writes them one JSON line each."""
         import torch
         t0 = time.perf_counter()
         best, t, nonfinite = None, 0, 0
@@ -452,9 +470,20 @@ class Solver:
             nu = self.n_unsat
             nonfinite = int((nu < 0).sum())
             found = None
+            lo = None
             if nonfinite < self.R:
                 lo = int(torch.where(nu < 0, torch.iinfo(torch.int32).max, nu).min())
                 best = lo if best is None else min(best, lo)
+            if log is not None:
+                fin = nu[nu >= 0]
+                obj = self.obj[torch.isfinite(self.obj)]
+                log(dict(stage=t, sigma=float(sigma), seconds=time.perf_counter() - t0, min_unsat=lo,
+                         median_unsat=float(fin.float().median()) if fin.numel() else None,
+                         at_zero=int((nu == 0).sum()), nonfinite=nonfinite,
+                         mean_iters=float(self.iters.float().mean()),
+                         median_gnorm2=float(torch.nanmedian(self.gnorm2.float())),
+                         best_obj=float(obj.min()) if obj.numel() else None))
+            if nonfinite < self.R:
                 cand = torch.nonzero(nu == 0).flatten().tolist() if lo == 0 else []
                 for r in cand:
                     sat, x, y = self.verify_restart(r)

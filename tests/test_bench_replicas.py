@@ -76,10 +76,14 @@ def _fake_solver(sat_stage, R=4):
         def __init__(self):
             self.R = R
             self.n_unsat = torch.full((R,), 3, dtype=torch.int32)
+            self.iters = torch.full((R,), 7, dtype=torch.int32)
+            self.gnorm2 = torch.full((R,), 0.25)
+            self.obj = torch.full((R,), -1.0)
             self.calls = 0
 
         def stage(self, sigma, t):
             self.calls += 1
+            self.obj[0] = -1.0 - t
             if sat_stage is not None and t >= sat_stage:
                 self.n_unsat[1] = 0
 
@@ -128,3 +132,29 @@ def test_anneal_without_share_is_unchanged():
     S = _fake_solver(None)
     res = S.anneal([1.0] * 6)
     assert not res["sat"] and res["stages_run"] == 6 and res["best_unsat"] == 3
+
+
+def test_anneal_log_writes_one_json_line_per_stage(tmp_path):
+    """The per-stage record of Solver.anneal (#Unsat statistics, iterations, ||g||^2,
+    best objective) through jsonl_log; a non-finite restart is left out of the
+    statistics and counted."""
+    import json
+    import sys
+    sys.path.insert(0, ROOT)
+    from paper_2603_22877_b300 import jsonl_log
+    S = _fake_solver(3)
+    S.n_unsat[2] = -2 ** 31 + 4                            # restart 2 marked non-finite
+    S.obj[2] = float("nan")
+    path = tmp_path / "trace.jsonl"
+    log = jsonl_log(str(path))
+    res = S.anneal([2.0, 1.0, 0.5, 0.25], log=log)
+    log.close()
+    assert res["sat"] and res["stage"] == 3
+    recs = [json.loads(line) for line in path.read_text().splitlines()]
+    assert [r["stage"] for r in recs] == [1, 2, 3]
+    assert [r["sigma"] for r in recs] == [2.0, 1.0, 0.5]
+    assert [r["min_unsat"] for r in recs] == [3, 3, 0]
+    assert [r["at_zero"] for r in recs] == [0, 0, 1]
+    assert all(r["nonfinite"] == 1 and r["mean_iters"] == 7.0 and r["median_gnorm2"] == 0.25 for r in recs)
+    assert [r["best_obj"] for r in recs] == [-2.0, -3.0, -4.0]
+    assert recs[0]["median_unsat"] == 3.0
