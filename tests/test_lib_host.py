@@ -65,6 +65,12 @@ def test_compiler_matches_oracle_diagrams(name):
             total += V
             mine = (list(D["label"][b0:b1]), list(D["hi"][b0:b1]), list(D["lo"][b0:b1]),
                     int(D["con_root"][s]))
+            # topological order: every child lies after its node (terminals V, V + 1), so
+            # the device's walk from the root always ends at a terminal
+            for v in range(V):
+                assert D["hi"][b0 + v] > v and D["lo"][b0 + v] > v and D["hi"][b0 + v] <= V + 1
+                assert D["lo"][b0 + v] <= V + 1
+            assert int(D["con_root"][s]) <= V + 1 and (V == 0 or int(D["con_root"][s]) == 0)
             ids = sorted({int(l) >> 1 for l in inst.lits(c)})
             rng = np.random.default_rng(c)
             for _ in range(8):
