@@ -123,7 +123,7 @@ struct Machine {
 };
 
 struct Diagram {
-  std::vector<uint32_t> label;  // variable / atom id per node, topological order
+  std::vector<int32_t> level;   // position in the literal list per node, topological order
   std::vector<uint16_t> hi, lo; // child index, V = TRUE, V+1 = FALSE
   uint8_t root = 0;
 };
@@ -198,12 +198,12 @@ static bool build_diagram(int kind, int param, const int32_t* lits, int L, Diagr
   std::unordered_map<int, int> pos;
   for (int i = 0; i < V; ++i) pos[order[i]] = i;
   auto index = [&](int r) { return r == kTrue ? V : (r == kFalse ? V + 1 : pos.at(r)); };
-  out.label.resize(V);
+  out.level.resize(V);
   out.hi.resize(V);
   out.lo.resize(V);
   for (int i = 0; i < V; ++i) {
     const Node& n = nodes[order[i]];
-    out.label[i] = (uint32_t)(lits[n.level] >> 1);
+    out.level[i] = n.level;
     out.hi[i] = (uint16_t)index(n.hi);
     out.lo[i] = (uint16_t)index(n.lo);
   }
@@ -545,22 +545,43 @@ static fsmt_status compile(const Problem& P, int policy, Compiled& C) {
   C.node_label.clear();
   C.node_hilo.clear();
   int64_t total = 0;
-  Diagram D;
+  // A diagram depends only on the kind, the parameter, the length and which literals
+  // are negated; the variables only label its levels.  Each distinct shape is built
+  // once and relabelled for every constraint that has it.
+  std::unordered_map<std::string, Diagram> shapes;
+  std::string key;
   for (int s = 0; s < n_cons; ++s) {
     int c = sched[s];
     int64_t b = P.con_ptr[c], e = P.con_ptr[c + 1];
-    if (!build_diagram(P.con_kind[c], P.con_param[c], P.con_lits.data() + b, (int)(e - b), D))
-      return fail(FSMT_EINVAL, "a diagram exceeds 65,533 decision nodes");
+    const int32_t* lits = P.con_lits.data() + b;
+    const int L = (int)(e - b);
+    const int32_t head[3] = {P.con_kind[c], P.con_param[c], L};
+    key.assign(reinterpret_cast<const char*>(head), sizeof(head));
+    for (int t = 0; t < L; t += 8) {
+      unsigned char bits = 0;
+      for (int u = t; u < std::min(L, t + 8); ++u) bits |= (unsigned char)((lits[u] & 1) << (u - t));
+      key.push_back((char)bits);
+    }
+    auto it = shapes.find(key);
+    if (it == shapes.end()) {
+      if (shapes.size() >= (1u << 16)) shapes.clear();  // bounded memory on shape-diverse inputs
+      Diagram D;
+      if (!build_diagram(P.con_kind[c], P.con_param[c], lits, L, D))
+        return fail(FSMT_EINVAL, "a diagram exceeds 65,533 decision nodes");
+      it = shapes.emplace(key, std::move(D)).first;
+    }
+    const Diagram& D = it->second;
+    const size_t V = D.level.size();
     C.con_id[s] = c;
     C.con_root[s] = D.root;
     C.con_ptr[s] = (int32_t)total;
-    total += (int64_t)D.label.size();
+    total += (int64_t)V;
     if (total > INT32_MAX) return fail(FSMT_EINVAL, "more than 2^31-1 decision nodes");
-    for (size_t i = 0; i < D.label.size(); ++i) {
-      C.node_label.push_back(D.label[i]);
+    for (size_t i = 0; i < V; ++i) {
+      C.node_label.push_back((uint32_t)(lits[D.level[i]] >> 1));
       C.node_hilo.push_back((uint32_t)D.hi[i] | ((uint32_t)D.lo[i] << 16));
     }
-    if (s < C.n_obj) C.max_nodes = std::max<int32_t>(C.max_nodes, (int32_t)D.label.size());
+    if (s < C.n_obj) C.max_nodes = std::max<int32_t>(C.max_nodes, (int32_t)V);
     if (s == C.n_obj - 1) C.n_obj_nodes = total;
   }
   if (C.n_obj == 0) C.n_obj_nodes = 0;
