@@ -283,20 +283,13 @@ static bool build_chunks(const Problem& P, Compiled& C, int slot_limit) {
     if (x.k3 != y.k3) return x.k3 < y.k3;
     return x.s < y.s;
   });
-  std::unordered_map<int, int> slot_of;
+  // the open chunk's slots and reals: index arrays over all literals / reals (-1 = not
+  // in the chunk) and the keys in insertion order, which is also their numbering
+  const int n_ids = C.n_bool + C.n_atoms;
+  std::vector<int32_t> slot_idx(2 * (size_t)n_ids, -1), real_idx(C.n_real, -1);
+  std::vector<int32_t> chunk_slot_keys, chunk_reals;
   int chunk_cons = 0, chunk_nodes = 0, chunk_terms = 0;
   auto atom_terms = [&](int lab) { return lab < C.n_bool ? 0 : C.atom_ptr[lab - C.n_bool + 1] - C.atom_ptr[lab - C.n_bool]; };
-  std::unordered_map<int, int> real_of;  // the open chunk's reals
-  auto new_reals = [&](int s) {  // reals constraint s would add to the open chunk (may over-count repeats)
-    int n = 0;
-    for (int v = C.con_ptr[s]; v < C.con_ptr[s + 1]; ++v) {
-      const int lab = (int)C.node_label[v];
-      if (lab < C.n_bool) continue;
-      for (int e = C.atom_ptr[lab - C.n_bool]; e < C.atom_ptr[lab - C.n_bool + 1]; ++e)
-        if (!real_of.count(C.atom_var[e])) ++n;
-    }
-    return n;
-  };
   const int tnode = std::max(1, C.max_nodes);  // row of the TRUE terminal in the kernel's message array
   // diagram shapes in literal space: a node testing a negated literal has its
   // children swapped, so diagrams of one kind and size share a shape whatever
@@ -308,7 +301,12 @@ static bool build_chunks(const Problem& P, Compiled& C, int slot_limit) {
   C.shape_nodes.clear();
   std::unordered_map<std::string, int> shape_of;
   std::vector<int> con_shape;  // per constraint in chunk order
-  std::unordered_map<int, bool> neg_of;
+  // per-constraint scratch: polarity of each literal id, and the first node testing it
+  std::vector<int8_t> neg_of(n_ids, 0);
+  std::vector<int32_t> first_stamp(n_ids, -1), first_node(n_ids, 0);
+  std::string key;
+  std::vector<uint16_t> shi, slo, sgrp;
+  std::vector<uint32_t> seen;
   auto close_chunk = [&]() {
     C.chunk_con_ptr.push_back((int32_t)(C.ccon.size() / 4));
     C.chunk_node_ptr.push_back((int32_t)C.cnode_slot.size());
@@ -321,22 +319,22 @@ static bool build_chunks(const Problem& P, Compiled& C, int slot_limit) {
       C.slot_meta.push_back(tc ? ((tb << 16) | tc) : 0);
       for (int j = 0; j < tc; ++j) {
         const int e = C.atom_ptr[lab - C.n_bool] + j;
-        C.term_var.push_back(real_of.at(C.atom_var[e]));
+        C.term_var.push_back(real_idx[C.atom_var[e]]);
         C.term_coef.push_back(C.atom_coef[e]);
       }
       tb += tc;
     }
     C.chunk_term_ptr.push_back((int32_t)C.term_var.size());
     C.chunk_slot_ptr.push_back((int32_t)C.slot_label.size());
-    C.chunk_slot_cap = std::max<int32_t>(C.chunk_slot_cap, (int32_t)slot_of.size());
-    C.chunk_real_max = std::max<int32_t>(C.chunk_real_max, (int32_t)real_of.size());
-    std::vector<int> reals(real_of.size());
-    for (auto& kv : real_of) reals[kv.second] = kv.first;
-    C.real_id.insert(C.real_id.end(), reals.begin(), reals.end());
+    C.chunk_slot_cap = std::max<int32_t>(C.chunk_slot_cap, (int32_t)chunk_slot_keys.size());
+    C.chunk_real_max = std::max<int32_t>(C.chunk_real_max, (int32_t)chunk_reals.size());
+    C.real_id.insert(C.real_id.end(), chunk_reals.begin(), chunk_reals.end());
     C.chunk_real_ptr.push_back((int32_t)C.real_id.size());
-    real_of.clear();
+    for (int r : chunk_reals) real_idx[r] = -1;
+    chunk_reals.clear();
     ++C.n_chunks;
-    slot_of.clear();
+    for (int k : chunk_slot_keys) slot_idx[k] = -1;
+    chunk_slot_keys.clear();
     chunk_cons = chunk_nodes = chunk_terms = 0;
   };
   // small instances: chunks of fewer constraints, so that they still spread over
@@ -349,28 +347,31 @@ static bool build_chunks(const Problem& P, Compiled& C, int slot_limit) {
   for (const Key& k : keys) {
     const int s = k.s;
     const int b = C.con_ptr[s], V = C.con_ptr[s + 1] - b;
-    neg_of.clear();
     {
       const int cid = C.con_id[s];
       for (int64_t t = P.con_ptr[cid]; t < P.con_ptr[cid + 1]; ++t)
-        neg_of[P.con_lits[t] >> 1] = (P.con_lits[t] & 1) != 0;
+        neg_of[P.con_lits[t] >> 1] = (int8_t)(P.con_lits[t] & 1);
     }
-    int new_slots = 0, new_terms = 0;
+    // what the constraint would add to the open chunk; a literal or real tested at
+    // several nodes is counted at each (conservative)
+    int new_slots = 0, new_terms = 0, new_reals = 0;
     for (int v = b; v < b + V; ++v) {
       const int lab = (int)C.node_label[v];
-      if (!slot_of.count(slot_key(lab, neg_of[lab]))) {  // may count a repeat twice: conservative
+      if (slot_idx[slot_key(lab, neg_of[lab] != 0)] < 0) {
         ++new_slots;
         new_terms += atom_terms(lab);
       }
+      if (lab >= C.n_bool)
+        for (int e = C.atom_ptr[lab - C.n_bool]; e < C.atom_ptr[lab - C.n_bool + 1]; ++e)
+          if (real_idx[C.atom_var[e]] < 0) ++new_reals;
     }
+    const int n_slots = (int)chunk_slot_keys.size(), n_reals = (int)chunk_reals.size();
     if (chunk_cons > 0 && (chunk_cons + 1 > cons_limit || chunk_nodes + V > kChunkMaxNodes ||
-                           (int)slot_of.size() + new_slots > slot_limit ||
-                           chunk_terms + new_terms > kChunkMaxTerms ||
+                           n_slots + new_slots > slot_limit || chunk_terms + new_terms > kChunkMaxTerms ||
                            (int)(C.clist.size() - C.chunk_list_ptr.back()) + V + 3 > kChunkMaxList ||
-                           (int)real_of.size() + new_reals(s) > kChunkMaxReals ||
+                           n_reals + new_reals > kChunkMaxReals ||
                            (slot_limit > kChunkSlotsGeneric &&
-                            ((int)slot_of.size() + new_slots) * 512 + ((int)real_of.size() + new_reals(s)) * 1024 >
-                                kChunkWideBytes)))
+                            (n_slots + new_slots) * 512 + (n_reals + new_reals) * 1024 > kChunkWideBytes)))
       close_chunk();
     if (V > kChunkMaxNodes) return false;
     C.ccon.push_back(chunk_nodes);
@@ -378,18 +379,20 @@ static bool build_chunks(const Problem& P, Compiled& C, int slot_limit) {
     // z: the root flag of a constant diagram, else where its literal list starts
     C.ccon.push_back(V == 0 ? C.con_root[s] : (int32_t)(C.clist.size() - C.chunk_list_ptr.back()));
     C.ccon.push_back(C.con_id[s]);
-    std::string key(reinterpret_cast<const char*>(&V), sizeof(V));
-    std::vector<uint16_t> shi(V), slo(V), sgrp(V);
+    key.assign(reinterpret_cast<const char*>(&V), sizeof(V));
+    shi.resize(V);
+    slo.resize(V);
+    sgrp.resize(V);
     for (int v = b; v < b + V; ++v) {
-      const bool ng = neg_of[(int)C.node_label[v]];
+      const int lab = (int)C.node_label[v];
+      const bool ng = neg_of[lab] != 0;
       uint16_t h = (uint16_t)(C.node_hilo[v] & 0xffffu), l = (uint16_t)(C.node_hilo[v] >> 16);
       if (ng) std::swap(h, l);
-      uint16_t g = (uint16_t)(v - b);  // first node of the constraint testing the same variable
-      for (int u = b; u < v; ++u)
-        if (C.node_label[u] == C.node_label[v]) {
-          g = (uint16_t)(u - b);
-          break;
-        }
+      if (first_stamp[lab] != s) {  // first node of the constraint testing this variable
+        first_stamp[lab] = s;
+        first_node[lab] = v - b;
+      }
+      const uint16_t g = (uint16_t)first_node[lab];
       shi[v - b] = h;
       slo[v - b] = l;
       sgrp[v - b] = g;
@@ -414,22 +417,21 @@ static bool build_chunks(const Problem& P, Compiled& C, int slot_limit) {
     con_shape.push_back(sid);
     for (int v = b; v < b + V; ++v) {
       const int lab = (int)C.node_label[v];
-      const bool ng = neg_of[lab];
-      auto it = slot_of.find(slot_key(lab, ng));
-      int slot;
-      if (it == slot_of.end()) {
-        slot = (int)slot_of.size();
-        slot_of.emplace(slot_key(lab, ng), slot);
+      const bool ng = neg_of[lab] != 0;
+      const int sk = slot_key(lab, ng);
+      int slot = slot_idx[sk];
+      if (slot < 0) {
+        slot = (int)chunk_slot_keys.size();
+        slot_idx[sk] = slot;
+        chunk_slot_keys.push_back(sk);
         C.slot_label.push_back(ng ? (int32_t)((uint32_t)lab | 0x80000000u) : lab);
         chunk_terms += atom_terms(lab);
         if (lab >= C.n_bool)
           for (int e = C.atom_ptr[lab - C.n_bool]; e < C.atom_ptr[lab - C.n_bool + 1]; ++e)
-            if (!real_of.count(C.atom_var[e])) {
-              const int nr = (int)real_of.size();
-              real_of.emplace(C.atom_var[e], nr);
+            if (real_idx[C.atom_var[e]] < 0) {
+              real_idx[C.atom_var[e]] = (int32_t)chunk_reals.size();
+              chunk_reals.push_back(C.atom_var[e]);
             }
-      } else {
-        slot = it->second;
       }
       C.cnode_slot.push_back((uint32_t)slot * 4u * kSlotStride);  // the slot row's byte offset
       // children in literal space (hi: the literal holds), so a negated literal's
@@ -444,14 +446,14 @@ static bool build_chunks(const Problem& P, Compiled& C, int slot_limit) {
     }
     {  // the constraint's literal list: slot words of its distinct literals, in order of first node
       const size_t n0 = C.cnode_slot.size() - (size_t)V;
-      std::vector<uint32_t> seen;
+      seen.clear();
       for (size_t v = n0; v < C.cnode_slot.size(); ++v)
         if (std::find(seen.begin(), seen.end(), C.cnode_slot[v]) == seen.end()) seen.push_back(C.cnode_slot[v]);
       while (seen.size() % 4) seen.push_back(0);
       C.clist.insert(C.clist.end(), seen.begin(), seen.end());
     }
-    if ((int)slot_of.size() > slot_limit || chunk_terms > kChunkMaxTerms || (int)real_of.size() > kChunkMaxReals ||
-        (int)(C.clist.size() - C.chunk_list_ptr.back()) > kChunkMaxList)
+    if ((int)chunk_slot_keys.size() > slot_limit || chunk_terms > kChunkMaxTerms ||
+        (int)chunk_reals.size() > kChunkMaxReals || (int)(C.clist.size() - C.chunk_list_ptr.back()) > kChunkMaxList)
       return false;
     ++chunk_cons;
     chunk_nodes += V;
