@@ -258,7 +258,10 @@ def our_arm(args):
     P = Problem.from_instance(inst)
     comp = P.compile()
     compile_s = time.perf_counter() - t_c
-    comp.upload()
+    t_c = time.perf_counter()
+    comp.upload()                       # device copy + run-time generated routines
+    torch.cuda.synchronize()
+    upload_s = time.perf_counter() - t_c
     info = comp.info
     eta = args.eta if args.eta is not None else 0.02
     a0, b0 = W.initial_point(inst, R, seed=replica_seed(rank))
@@ -437,7 +440,8 @@ def our_arm(args):
                            "n_obj_cons": info["n_obj_cons"], "n_obj_nodes": nodes, "atoms": inst.n_atoms,
                            "iters_per_step": iters_per_step, "eta": eta, "form": "fused + CUDA graph",
                            "l2": "inputs larger than L2 (diagrams + weights > 126 MB)",
-                           "compile_s": compile_s, "parallelism": f"replicas x{ws}", "launch": launch},
+                           "compile_s": compile_s, "upload_s": upload_s, "parallelism": f"replicas x{ws}",
+                           "launch": launch},
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches_per_step * args.steps, "clocks": clk, "plain": plain,
