@@ -41,8 +41,10 @@ typedef enum {
   FSMT_EINVAL = -1,   /* invalid argument or unsupported input */
   FSMT_ENOMEM = -2,   /* host or device allocation failed */
   FSMT_ECUDA = -3,    /* a CUDA runtime call or launch failed */
-  FSMT_ETIMEOUT = -4, /* a bounded device wait gave up */
-  FSMT_ENAN = -5,     /* non-finite state detected */
+  FSMT_ETIMEOUT = -4, /* a bounded device wait gave up (reserved: no kernel waits on
+                         another block, a flag or a peer) */
+  FSMT_ENAN = -5,     /* non-finite state detected (fsmt_solve_stage_host; device calls
+                         mark it per restart in n_unsat instead, see fsmt_round_check) */
   FSMT_ESTATE = -6    /* call out of order (e.g. device call before fsmt_upload) */
 } fsmt_status;
 
