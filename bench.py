@@ -102,6 +102,16 @@ def max_over_ranks(x, device="cpu"):
     return float(t.item())
 
 
+def kernel_name(launch):
+    """The forward + adjoint kernel that a launch configuration runs, as the launch list names it."""
+    rpl = launch["restarts_per_lane"]
+    return {"warp": "k_fused<1> (one warp per constraint, forward + adjoint)",
+            "chunked": f"k_chunked<1, {rpl}> (chunked, ahead-of-time generic diagram pass)",
+            "jit": f"fsmt_jit_adj_{rpl} (chunked, run-time generated routines and the generic pass)",
+            "wide": f"fsmt_jit_wide_adj_{rpl} (chunked, run-time generated routines for every shape)",
+            }.get(launch["variant"], str(launch["variant"]))
+
+
 def whole_job_rate(units_per_rank, ws, ms):
     """Units of all ranks per second over the slowest rank's time (weak scaling)."""
     return units_per_rank * ws / (ms / 1000.0)
@@ -343,7 +353,7 @@ def our_arm(args):
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": achieved / alu_peak, "traffic": traffic,
                 "peak_kind": f"derived: 148 SMs x 128 FP32 lanes x 2 flops (FMA) x {sm_mhz:.0f} MHz",
-                "kernel": "fsmt_jit_wide_adj_2 (run-time specialised forward + adjoint, chunked)",
+                "kernel": kernel_name(launch),
                 "kernel_ms": fused_ms, "algorithmic_flops": alg_flops, "traffic_source": traffic_note,
                 "node_visits_per_s": nodes * R / (fused_ms / 1000.0),
                 "hbm": {"algorithmic_bytes": alg_bytes, "achieved_gbs": alg_bytes / (fused_ms / 1000.0) / 1e9,
