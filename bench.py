@@ -45,6 +45,8 @@ WORKLOADS = {
     # the encoding read literally: 1,000 jobs on 20 workers (5 index bits, 6,000 variables)
     "large_scheduling_lit": (lambda: W.large_scheduling(1005, n_workers=20, n_jobs=1000, n_late=6), 512),
     "placement2d": (lambda: W.placement2d(1003), 1024),
+    # the same rectangles with the paper's style of non-overlap: a plain 4-atom OR, no selectors
+    "placement2d_nosel": (lambda: W.placement2d(1003, selectors=False), 1024),
     # the paper's 3D placement encoding: 64 macros x 8 layers, 896 modules
     "placement3d": (lambda: W.placement3d(1007), 512),
     "jobshop": (lambda: W.jobshop(1002), 256),
