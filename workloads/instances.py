@@ -107,6 +107,34 @@ class _Builder:
         self.lits += [int(l) for l in lits]
         self.ptr.append(len(self.lits))
 
+    def atoms_rows(self, var, coef, q0, rel=LE) -> np.ndarray:
+        """Appends one atom per row of var / coef (int arrays [m][nnz]) with right-hand
+        sides q0[m], as m calls of atom() would; returns the atoms' ids."""
+        var = np.asarray(var, np.int64)
+        coef = np.asarray(coef, np.int64)
+        m, nnz = var.shape
+        assert nnz > 0 and (np.sort(var, 1)[:, 1:] != np.sort(var, 1)[:, :-1]).all()
+        first = len(self.atom_q0)
+        end = self.atom_ptr[-1]
+        self.atom_var += var.ravel().tolist()
+        self.atom_coef += coef.ravel().tolist()
+        self.atom_ptr += (end + nnz * np.arange(1, m + 1)).tolist()
+        self.atom_q0 += np.asarray(q0, np.int64).tolist()
+        self.atom_rel += [int(rel)] * m
+        return self.n_bool + first + np.arange(m)
+
+    def cons_rows(self, kind, lits, param=0):
+        """Appends one constraint per row of lits (int array [m][L]), as m calls of con()."""
+        lits = np.asarray(lits, np.int64)
+        m, L = lits.shape
+        ids = np.sort(lits >> 1, 1)
+        assert (ids[:, 1:] != ids[:, :-1]).all(), "a constraint may not repeat a variable"
+        end = self.ptr[-1]
+        self.kind += [kind] * m
+        self.param += [int(param)] * m
+        self.lits += lits.ravel().tolist()
+        self.ptr += (end + L * np.arange(1, m + 1)).tolist()
+
     def freeze(self, name, lo, hi, px, py, scale, **meta) -> Instance:
         return Instance(
             name=name, n_bool=self.n_bool, n_real=self.n_real,
@@ -415,19 +443,16 @@ def placement3d(seed: int = 1007, n_macros=64, n_layers=8) -> Instance:
         B.con(OR, [lit(B.atom([xv(k), xv(j)], [1, -1], int(w[j]), LE))])
         B.con(OR, [lit(B.atom([yv(j), yv(k)], [1, -1], int(d[k]), LE))])
         B.con(OR, [lit(B.atom([yv(k), yv(j)], [1, -1], int(d[j]), LE))])
-    # non-overlap
-    for j in range(N):
-        for k in range(j + 1, N):
-            lits = []
-            for i in range(bm):
-                lits += [lit(mbit(j, i)), lit(mbit(k, i))]
-            for i in range(bl):
-                lits += [lit(lbit(j, i)), lit(lbit(k, i))]
-            lits += [lit(B.atom([xv(k), xv(j)], [1, -1], -int(w[k]), LE)),   # x_j - x_k >= w_k
-                     lit(B.atom([xv(j), xv(k)], [1, -1], -int(w[j]), LE)),   # x_k - x_j >= w_j
-                     lit(B.atom([yv(k), yv(j)], [1, -1], -int(d[k]), LE)),   # y_j - y_k >= d_k
-                     lit(B.atom([yv(j), yv(k)], [1, -1], -int(d[j]), LE))]   # y_k - y_j >= d_j
-            B.con(NEQ_OR, lits, param=nb)
+    # non-overlap for every pair j < k (row-major): the macro-bit and layer-bit XOR
+    # pairs, then x_j - x_k >= w_k, x_k - x_j >= w_j, y_j - y_k >= d_k, y_k - y_j >= d_j
+    J, K = np.triu_indices(N, 1)
+    var = np.stack([2 * K, 2 * J, 2 * J, 2 * K, 2 * K + 1, 2 * J + 1, 2 * J + 1, 2 * K + 1], 1).reshape(-1, 2)
+    q0 = np.stack([-w[K], -w[J], -d[K], -d[J]], 1).ravel()
+    A = B.atoms_rows(var, np.tile([1, -1], (4 * len(J), 1)), q0).reshape(-1, 4)
+    mb = np.stack([J[:, None] * nb + np.arange(bm), K[:, None] * nb + np.arange(bm)], 2).reshape(len(J), 2 * bm)
+    lb = np.stack([J[:, None] * nb + bm + np.arange(bl), K[:, None] * nb + bm + np.arange(bl)],
+                  2).reshape(len(J), 2 * bl)
+    B.cons_rows(NEQ_OR, np.concatenate([2 * mb, 2 * lb, 2 * A], 1), param=nb)
     lo = np.zeros(2 * N)
     hi = np.full(2 * N, float(P3_MACRO))
     kinds = np.array(kind)[np.argsort(perm)]
@@ -508,15 +533,15 @@ def large_scheduling(seed: int = 1005, n_workers=256, n_jobs=1111, dur_max=20,
         for i in range(bits):
             px[xb(i, j)] = -1 if (W[j] >> i) & 1 else 1
     py = Y.astype(np.float64)
-    # non-overlap for every pair
-    for j in range(n_jobs):
-        for k in range(j + 1, n_jobs):
-            A1 = B.atom([k, j], [1, -1], -int(t[k]), LE)  # y_j - y_k >= t_k
-            A2 = B.atom([j, k], [1, -1], -int(t[j]), LE)  # y_k - y_j >= t_j
-            lits = []
-            for i in range(bits):
-                lits += [lit(xb(i, j)), lit(xb(i, k))]
-            B.con(NEQ_OR, lits + [lit(A1), lit(A2)], param=bits)
+    # non-overlap for every pair j < k (row-major, as two nested loops would give):
+    # OR_i (x_ij xor x_ik) OR A1 OR A2 with A1: y_j - y_k >= t_k, A2: y_k - y_j >= t_j
+    J, K = np.triu_indices(n_jobs, 1)
+    atom_pairs = B.atoms_rows(np.stack([K, J, J, K], 1).reshape(-1, 2), np.tile([1, -1], (2 * len(J), 1)),
+                              np.stack([-t[K], -t[J]], 1).ravel())
+    A = atom_pairs.reshape(-1, 2)
+    bit_lits = np.stack([2 * (J[:, None] * bits + np.arange(bits)), 2 * (K[:, None] * bits + np.arange(bits))],
+                        2).reshape(len(J), 2 * bits)
+    B.cons_rows(NEQ_OR, np.concatenate([bit_lits, 2 * A], 1), param=bits)
     # precedence
     for j in range(n_jobs):
         if pred[j] >= 0:
