@@ -113,6 +113,43 @@ def test_all_kinds_random_constraints():
                                                                         int(inst.con_param[c]), t)
 
 
+def test_repeated_shapes_are_relabelled_not_confused():
+    """The compiler builds each (kind, parameter, length, negations) shape once and
+    relabels it: constraints of one shape over different variables, and constraints that
+    differ only in the parameter or in one negation, must each compute their own function
+    (every assignment checked)."""
+    rng = np.random.default_rng(11)
+    Bd = W._Builder(64, 1)
+    specs = []
+    for kind, L_, params in ((W.OR, 4, [0]), (W.XOR, 5, [0]), (W.NAE, 4, [0]), (W.CARD_LE, 5, [0, 1, 2, 3, 5]),
+                             (W.MUX, 6, [2]), (W.NEQ_OR, 6, [0, 1, 2, 3])):
+        negs = rng.integers(0, 2, L_)
+        for param in params:
+            for flip in (None, 0, L_ - 1):
+                n2 = negs.copy()
+                if flip is not None:
+                    n2[flip] ^= 1
+                for _ in range(3):                       # the same shape on other variables
+                    ids = rng.choice(64, L_, replace=False)
+                    specs.append((kind, param, [2 * int(i) + int(n) for i, n in zip(ids, n2)]))
+    for kind, param, lits in specs:
+        Bd.con(kind, lits, param)
+    inst = Bd.freeze("shapes", np.zeros(1), np.ones(1), np.ones(64), np.zeros(1), 1.0)
+    D = Problem.from_instance(inst).compile().diagrams()
+    for s in range(inst.n_cons):
+        c = int(D["con_id"][s])
+        b0, b1 = D["con_ptr"][s], D["con_ptr"][s + 1]
+        mine = (list(D["label"][b0:b1]), list(D["hi"][b0:b1]), list(D["lo"][b0:b1]), int(D["con_root"][s]))
+        ls = inst.lits(c)
+        ids = [int(l) >> 1 for l in ls]
+        assert sorted(set(int(x) for x in mine[0])) == sorted(set(ids)) or b1 == b0
+        for mask in range(1 << len(ids)):
+            vals = {i: bool((mask >> k) & 1) for k, i in enumerate(ids)}
+            t = [vals[int(l) >> 1] != bool(int(l) & 1) for l in ls]
+            assert bdd.evaluate(mine, vals.__getitem__) == S.kind_value(int(inst.con_kind[c]),
+                                                                        int(inst.con_param[c]), t), (c, mask)
+
+
 def test_bounds_rounded_inward_and_match_oracle():
     inst = W.jobshop(1002, 8, 4)
     comp = Problem.from_instance(inst).compile()
