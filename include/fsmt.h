@@ -80,7 +80,9 @@ typedef struct {
   int32_t fused_ok;      /* 1 if the fused kernels accept this instance */
   int32_t n_chunks;      /* chunks of the chunked forward/adjoint kernel (0: warp-per-constraint kernel) */
   int32_t jit_shapes;    /* diagram shapes given run-time generated code at fsmt_upload (0: none) */
-  int32_t reserved;
+  int32_t empty_boxes;   /* reals whose FP32 box is empty after unit-atom tightening (lo > hi): their
+                            unit atoms admit no FP32 value (contradictory, or pinning the real to a
+                            value FP32 cannot represent), so no restart can pass the exact check */
 } fsmt_info;
 
 /* One way to run the forward (+ adjoint) pass of C_sigma on an instance at R

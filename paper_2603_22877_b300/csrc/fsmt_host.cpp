@@ -664,6 +664,8 @@ static fsmt_status compile(const Problem& P, int policy, Compiled& C) {
       hs.push_back(std::move(h));
     }
   }
+  C.empty_boxes = 0;
+  for (int j = 0; j < C.n_real; ++j) C.empty_boxes += C.lo[j] > C.hi[j] ? 1 : 0;
   // blocks of reals coupled by half-spaces (union-find)
   std::vector<int> parent(C.n_real);
   std::iota(parent.begin(), parent.end(), 0);
@@ -1043,6 +1045,7 @@ fsmt_status fsmt_compiled_info(const fsmt_compiled* c, fsmt_info* out) {
   out->fused_ok = fsmt_fused_limit_ok(C);
   out->n_chunks = C.chunked_ok ? C.n_chunks : 0;
   out->jit_shapes = C.jit_shapes;
+  out->empty_boxes = C.empty_boxes;
   return FSMT_OK;
 }
 

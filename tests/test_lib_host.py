@@ -2,6 +2,7 @@
 compiler against the oracle's diagrams, projection bounds, the exact verifier
 and argument validation."""
 import ctypes as C
+import math
 import os
 import re
 
@@ -167,6 +168,65 @@ def test_bounds_rounded_inward_and_match_oracle():
     lo2, hi2 = Problem.from_instance(inst2).compile().bounds()
     assert float(hi2[0]) * 3 <= 7 and float(np.nextafter(hi2[0], np.float32(9))) * 3 > 7
     assert float(lo2[0]) * -3 < -1 and float(np.nextafter(lo2[0], np.float32(-9))) * -3 >= -1
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_unit_atoms_give_the_tightest_exact_fp32_box(seed):
+    """Single-variable unit atoms of every relation, coefficient sign and literal polarity
+    (several per real, all true at a planted point): the compiled FP32 box is the
+    tightest one whose every point satisfies every unit atom exactly -- the clamp of the
+    projection never leaves a unit atom false -- and it agrees with the oracle's exact
+    rational box to FP32 rounding.  Where the atoms pin a real to a value FP32 cannot
+    represent, the box is empty (lo > hi), no float satisfies them, and the compiled
+    information counts it."""
+    from fractions import Fraction
+    rng = np.random.default_rng(seed)
+    m = 12
+    ystar = [Fraction(int(rng.integers(-400, 400)), int(rng.integers(1, 9))) for _ in range(m)]
+    Bd = W._Builder(0, m)
+    atoms = []
+    for _ in range(60):
+        j = int(rng.integers(m))
+        cj = int(rng.integers(1, 8)) * int(rng.choice([-1, 1]))
+        rel = int(rng.integers(4))
+        v = cj * ystar[j]
+        q0 = round(v) + int(rng.integers(-2, 3))          # often right at the boundary
+        z = v - q0
+        truth = {W.LE: z <= 0, W.LT: z < 0, W.GE: z >= 0, W.GT: z > 0}[rel]
+        neg = not truth                                    # the literal holds at y*
+        Bd.con(W.OR, [W.lit(Bd.atom([j], [cj], q0, rel), neg)])
+        atoms.append((j, cj, q0, rel, neg))
+    inst = Bd.freeze("box", np.full(m, -1000.0), np.full(m, 1000.0), [], np.array([float(y) for y in ystar]), 1.0)
+    # every unit literal holds at the plant (by construction), so the box is not empty
+    def lit_holds(j, cj, q0, rel, neg, y):
+        z = cj * Fraction(y) - q0
+        t = {W.LE: z <= 0, W.LT: z < 0, W.GE: z >= 0, W.GT: z > 0}[rel]
+        return t != neg
+    assert all(lit_holds(*a, ystar[a[0]]) for a in atoms)
+    comp = Problem.from_instance(inst).compile()
+    lo, hi = comp.bounds()
+    dom = pgd.Domain(inst)
+    assert comp.info["empty_boxes"] == int((lo > hi).sum())
+    for j in range(m):
+        mine = [a for a in atoms if a[0] == j]
+        if lo[j] > hi[j]:
+            # the unit atoms pin y_j to a value FP32 cannot represent: no float between
+            # the two bounds (inclusive) satisfies them all, and the exact box is a point
+            assert dom.lo[j] == dom.hi[j]
+            f = hi[j]
+            while f <= lo[j]:
+                assert not all(lit_holds(*a, float(f)) for a in mine), (j, f)
+                f = np.nextafter(f, np.float32(np.inf))
+            continue
+        for y in (float(lo[j]), float(hi[j])):
+            assert all(lit_holds(*a, y) for a in mine), (j, y)
+            assert -1000.0 <= y <= 1000.0
+        # tightest: one FP32 step outwards breaks an atom or leaves the original box
+        out_lo, out_hi = float(np.nextafter(lo[j], np.float32(-np.inf))), float(np.nextafter(hi[j], np.float32(np.inf)))
+        assert out_lo < -1000.0 or not all(lit_holds(*a, out_lo) for a in mine), j
+        assert out_hi > 1000.0 or not all(lit_holds(*a, out_hi) for a in mine), j
+        assert abs(float(lo[j]) - dom.lo[j]) <= 1e-6 * max(1.0, abs(dom.lo[j]))
+        assert abs(float(hi[j]) - dom.hi[j]) <= 1e-6 * max(1.0, abs(dom.hi[j]))
 
 
 @pytest.mark.parametrize("name", list(SMALL))
