@@ -259,6 +259,36 @@ def test_verify_exact_boundary_and_tiny_values():
     assert P.verify_exact(np.zeros(0, np.int8), y2) == (True, -1)
 
 
+@pytest.mark.parametrize("seed", range(3))
+def test_verify_exact_on_random_boundaries(seed):
+    """The host's exact atom test against rational arithmetic: sums of up to six terms
+    with coefficients up to 2^24 - 1 and reals spread over 2^-80 .. 2^60 (so that the
+    terms' magnitudes are far apart), right-hand sides on, just below and just above the
+    exact value, every relation, and the reals nudged by one ulp across the boundary."""
+    from fractions import Fraction
+    rng = np.random.default_rng(100 + seed)
+    for _ in range(120):
+        nnz = int(rng.integers(1, 7))
+        var = list(range(nnz))
+        coef = [int(rng.integers(1, 1 << 24)) * int(rng.choice([-1, 1])) for _ in range(nnz)]
+        y = np.array([float(rng.integers(1, 1 << 20)) * 2.0 ** int(rng.integers(-80, 40)) * float(rng.choice([-1, 1]))
+                      for _ in range(nnz)])
+        exact = sum(Fraction(c_) * Fraction(float(v)) for c_, v in zip(coef, y))
+        if abs(exact) >= 2 ** 52:
+            continue
+        base = math.floor(exact)
+        for q0 in (base - 1, base, base + 1):
+            for rel in (W.LE, W.LT, W.GE, W.GT):
+                Bd = W._Builder(0, nnz)
+                Bd.con(W.OR, [W.lit(Bd.atom(var, coef, q0, rel))])
+                inst = Bd.freeze("b", np.full(nnz, -np.inf), np.full(nnz, np.inf), [], y, 1.0)
+                P = Problem.from_instance(inst)
+                for yy in (y, np.nextafter(y, np.inf), np.nextafter(y, -np.inf)):
+                    z = sum(Fraction(c_) * Fraction(float(v)) for c_, v in zip(coef, yy)) - q0
+                    want = {W.LE: z <= 0, W.LT: z < 0, W.GE: z >= 0, W.GT: z > 0}[rel]
+                    assert P.verify_exact(np.zeros(0, np.int8), yy)[0] == want, (coef, list(yy), q0, rel)
+
+
 def test_argument_validation():
     P = Problem(3, 2)
     bad = [
