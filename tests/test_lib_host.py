@@ -289,6 +289,87 @@ def test_verify_exact_on_random_boundaries(seed):
                     assert P.verify_exact(np.zeros(0, np.int8), yy)[0] == want, (coef, list(yy), q0, rel)
 
 
+@pytest.mark.parametrize("seed", range(8))
+def test_projection_blocks_match_the_coupling_graph(seed):
+    """Multi-variable unit atoms couple reals into blocks that the projection handles
+    one by one: the compiled half-space, block and free-real counts equal the connected
+    components of the coupling graph (computed here by a plain graph search), under
+    PROJECT only; SOFT keeps every unit atom in C_sigma."""
+    rng = np.random.default_rng(seed)
+    m = 90
+    Bd = W._Builder(3, m)
+    edges = []
+    for _ in range(int(rng.integers(5, 30))):
+        k = int(rng.integers(2, 4))
+        vs = [int(v) for v in rng.choice(m, k, replace=False)]
+        Bd.con(W.OR, [W.lit(Bd.atom(vs, [1] * (k - 1) + [-1], int(rng.integers(-5, 5)), W.LE))])
+        edges.append(vs)
+    for _ in range(10):                                   # single-variable ones only tighten the box
+        Bd.con(W.OR, [W.lit(Bd.atom([int(rng.integers(m))], [1], 100, W.LE))])
+    Bd.con(W.OR, [W.lit(0), W.lit(Bd.atom([0, 1], [1, 1], 50, W.LE))])   # not unit: has a Boolean
+    inst = Bd.freeze("blocks", np.zeros(m), np.full(m, 100.0), np.ones(3), np.zeros(m), 1.0)
+    adj = {v: set() for v in range(m)}
+    for vs in edges:
+        for v in vs:
+            adj[v] |= set(vs) - {v}
+    seen, blocks, largest = set(), 0, 0
+    for v in range(m):
+        if v in seen or not adj[v]:
+            continue
+        blocks += 1
+        stack, size = [v], 0
+        while stack:
+            u = stack.pop()
+            if u not in seen:
+                seen.add(u)
+                size += 1
+                stack += list(adj[u])
+        largest = max(largest, size)
+    P = Problem.from_instance(inst)
+    if largest > 32:                                      # the projection's per-block limit
+        with pytest.raises(L.FsmtError):
+            P.compile(L.UNIT_PROJECT)
+        return
+    info = P.compile(L.UNIT_PROJECT).info
+    assert info["n_halfspaces"] == len(edges)
+    assert info["n_components"] == blocks
+    assert info["n_free_reals"] == m - len(seen)
+    assert info["n_obj_cons"] == 1
+    soft = P.compile(L.UNIT_SOFT).info
+    assert soft["n_halfspaces"] == 0 and soft["n_obj_cons"] == inst.n_cons
+
+
+def test_projection_block_limits():
+    """A block of 33 coupled reals (a chain of unit atoms) exceeds the projection's
+    per-block limit of 32 reals: compile refuses it with EINVAL under PROJECT, and SOFT
+    (no projection) accepts it; 32 reals, and 64 half-spaces in one block, are accepted,
+    65 half-spaces are not."""
+    Bd = W._Builder(0, 33)
+    for j in range(32):
+        Bd.con(W.OR, [W.lit(Bd.atom([j, j + 1], [1, -1], 0, W.LE))])
+    inst = Bd.freeze("chain", np.zeros(33), np.ones(33), [], np.zeros(33), 1.0)
+    P = Problem.from_instance(inst)
+    with pytest.raises(L.FsmtError) as e:
+        P.compile(L.UNIT_PROJECT)
+    assert e.value.status == L.EINVAL
+    P.compile(L.UNIT_SOFT)
+    Bd = W._Builder(0, 32)                                # 32 reals: accepted
+    for j in range(31):
+        Bd.con(W.OR, [W.lit(Bd.atom([j, j + 1], [1, -1], 0, W.LE))])
+    ok = Problem.from_instance(Bd.freeze("chain32", np.zeros(32), np.ones(32), [], np.zeros(32), 1.0))
+    assert ok.compile(L.UNIT_PROJECT).info["n_components"] == 1
+    for n_hs, fails in ((64, False), (65, True)):         # half-spaces per block: at most 64
+        Bd = W._Builder(0, 4)
+        for t in range(n_hs):
+            Bd.con(W.OR, [W.lit(Bd.atom([t % 4, (t + 1) % 4], [1, -1], t, W.LE))])
+        P = Problem.from_instance(Bd.freeze("hs", np.zeros(4), np.ones(4), [], np.zeros(4), 1.0))
+        if fails:
+            with pytest.raises(L.FsmtError):
+                P.compile(L.UNIT_PROJECT)
+        else:
+            assert P.compile(L.UNIT_PROJECT).info["n_halfspaces"] == n_hs
+
+
 def test_argument_validation():
     P = Problem(3, 2)
     bad = [
