@@ -370,6 +370,23 @@ def test_projection_block_limits():
             assert P.compile(L.UNIT_PROJECT).info["n_halfspaces"] == n_hs
 
 
+def test_diagram_size_limit():
+    """A cardinality constraint 'at most k of L' has (k + 1)(L - k) decision nodes; the
+    node indices of a diagram are 16-bit, so compile accepts 256 x 255 = 65,280 nodes
+    and refuses 256 x 257 = 65,792 (EINVAL)."""
+    for L_, k, ok in ((510, 255, True), (512, 255, False)):
+        Bd = W._Builder(L_, 1)
+        Bd.con(W.CARD_LE, [W.lit(i) for i in range(L_)], k)
+        P = Problem.from_instance(Bd.freeze("card", np.zeros(1), np.ones(1), np.ones(L_), np.zeros(1), 1.0))
+        if ok:
+            info = P.compile().info
+            assert info["n_nodes"] == (k + 1) * (L_ - k) and info["max_nodes"] == info["n_nodes"]
+        else:
+            with pytest.raises(L.FsmtError) as e:
+                P.compile()
+            assert e.value.status == L.EINVAL
+
+
 def test_argument_validation():
     P = Problem(3, 2)
     bad = [
