@@ -336,6 +336,11 @@ class Solver:
         import torch
         if form not in ("fused", "plain"):
             raise ValueError("form is 'fused' or 'plain'")
+        info = compiled.info
+        if form == "fused" and info["n_obj_cons"] > 0 and info["n_chunks"] == 0 and not info["fused_ok"]:
+            # neither the chunked kernel (a constraint exceeds a chunk) nor the warp kernel
+            # (the largest diagram's messages exceed its shared memory) takes this instance
+            raise ValueError(f"no fused kernel takes a diagram of {info['max_nodes']} nodes; use form='plain'")
         self.form = form
         self._work = None
         self.problem, self.comp, self.R = problem, compiled, int(R)

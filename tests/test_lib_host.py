@@ -387,6 +387,35 @@ def test_diagram_size_limit():
             assert e.value.status == L.EINVAL
 
 
+def test_kernel_paths_chosen_by_size():
+    """Which forward + adjoint kernel can take an instance, from its compiled information:
+    the chunked kernel while every constraint fits a chunk (at most 2,048 nodes, and at
+    most 192 distinct literals when it needs the generic pass); the warp-per-constraint
+    kernel while the largest diagram's messages fit its shared memory; neither for a
+    2,102-node diagram, where the fused solver refuses the instance up front (before any
+    device work) and points to the plain form."""
+    from paper_2603_22877_b300 import Solver
+
+    def build(kind, L_, k=0):
+        Bd = W._Builder(L_ + 3, 1)
+        Bd.con(kind, [W.lit(i) for i in range(L_)], k)
+        Bd.con(W.OR, [W.lit(L_), W.lit(L_ + 1)])
+        P = Problem.from_instance(Bd.freeze("x", np.zeros(1), np.ones(1), np.ones(L_ + 3), np.zeros(1), 1.0))
+        return P, P.compile()
+
+    _, c = build(W.OR, 190)                               # fits a chunk of 192 literals
+    assert c.info["n_chunks"] > 0 and c.info["fused_ok"] == 1
+    _, c = build(W.OR, 300)                               # 300 literals: warp kernel only
+    assert c.info["n_chunks"] == 0 and c.info["fused_ok"] == 1
+    _, c = build(W.CARD_LE, 100, 19)                      # 1,620 nodes: chunked only
+    assert c.info["n_chunks"] > 0 and c.info["fused_ok"] == 0
+    P, c = build(W.CARD_LE, 120, 20)                      # 2,100 nodes: neither
+    assert c.info["n_chunks"] == 0 and c.info["fused_ok"] == 0 and c.info["max_nodes"] == 2100
+    with pytest.raises(ValueError, match="plain"):
+        Solver(P, c, 32, eta=0.1, b_scale=1.0)
+    assert not c.uploaded
+
+
 def test_argument_validation():
     P = Problem(3, 2)
     bad = [
