@@ -435,6 +435,17 @@ def test_argument_validation():
             f()
         assert e.value.status == L.EINVAL
     assert P.n_cons == 0
+    # nothing of a failed bulk call was kept: a bulk call mixing a good and a bad row
+    # adds neither, and the next constraint added gets id 0 (verify_exact names it)
+    with pytest.raises(L.FsmtError):
+        P.add_constraints([0, 0], [0, 0], [0, 1, 2], [0, 100])
+    with pytest.raises(L.FsmtError):
+        P.add_atoms([0, 1, 2], [1, 0], [1, 0], [100, 0], [0, 0])   # y1 <= 100 (true), then coef 0
+    P.add_constraints([0], [0], [0, 1], [2])                 # OR(x1): false at x1 = FALSE (+1)
+    assert P.verify_exact(np.array([1, 1, 1], np.int8), np.zeros(2)) == (False, 0)
+    P.add_atoms([0, 1], [0], [1], [5], [0])                  # atom 0: y0 <= 5, literal id 3
+    P.add_constraints([0], [0], [0, 1], [2 * 3])
+    assert P.verify_exact(np.array([1, -1, 1], np.int8), np.array([6.0, 0.0])) == (False, 1)
     with pytest.raises(L.FsmtError):
         P.verify_exact(np.array([0, 1, 1], np.int8), np.zeros(2))
 
