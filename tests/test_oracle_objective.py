@@ -42,6 +42,56 @@ def test_atom_probability_monte_carlo():
     assert abs(est - p[0]) < 4 * math.sqrt(p[0] * (1 - p[0]) / N)
 
 
+def _two_atom_or(shared):
+    """OR(A1, A2): with shared reals the scheduling non-overlap pair A1: y0 - y1 >= 2,
+    A2: y1 - y0 >= 3; without, the same atoms over disjoint reals (y0, y1) and (y2, y3)."""
+    B = W._Builder(0, 4)
+    A1 = B.atom([1, 0], [1, -1], -2, W.LE)               # y0 - y1 >= 2
+    A2 = B.atom([0, 1] if shared else [2, 3], [1, -1], -3, W.LE)   # y1 - y0 >= 3 (or y3 - y2 >= 3)
+    B.con(W.OR, [W.lit(A1), W.lit(A2)])
+    return B.freeze("or2", np.full(4, -50.0), np.full(4, 50.0), [], np.zeros(4), 1.0)
+
+
+def test_cop_equals_gaussian_sampling_when_atoms_are_independent():
+    """Thm. expectation: with y ~ N(b, sigma^2 I) and atoms over disjoint reals, the
+    probability that the constraint holds is exactly the COP of independent atom
+    marginals -- checked by sampling y itself (10^6 draws, 4 standard errors)."""
+    inst = _two_atom_or(shared=False)
+    b = np.array([[0.4], [-1.1], [2.0], [4.2]])
+    sigma = 1.3
+    w = np.ones((1, 1))
+    _, cop, _, _ = OBJ.evaluate(inst, np.zeros((0, 1)), b, w, sigma, with_grad=False)
+    rng = np.random.default_rng(5)
+    N = 1_000_000
+    y = b[:, 0][:, None] + sigma * rng.standard_normal((4, N))
+    est = ((y[0] - y[1] >= 2) | (y[3] - y[2] >= 3)).mean()
+    assert abs(est - cop[0, 0]) < 4 * math.sqrt(cop[0, 0] * (1 - cop[0, 0]) / N)
+
+
+def test_shared_reals_diverge_from_gaussian_sampling_as_documented():
+    """Reading R4: atoms of one constraint that share reals are correlated under
+    y ~ N(b, sigma^2 I), but Alg. 3 (and the oracle) multiplies their marginals.  For
+    the non-overlap pair the two atoms exclude each other, so sampling y gives
+    P[A1] + P[A2] while the COP is 1 - (1 - P[A1])(1 - P[A2]): the COP falls short by the
+    product P[A1] P[A2], far outside the sampling error.  Not a gate on the CUDA path:
+    it records what the method computes."""
+    inst = _two_atom_or(shared=True)
+    b = np.array([[0.3], [0.1], [0.0], [0.0]])
+    sigma = 4.0
+    w = np.ones((1, 1))
+    _, cop, _, _ = OBJ.evaluate(inst, np.zeros((0, 1)), b, w, sigma, with_grad=False)
+    p1, _ = relax.atom_terms(inst, 0, b, sigma)
+    p2, _ = relax.atom_terms(inst, 1, b, sigma)
+    np.testing.assert_allclose(cop[0, 0], 1 - (1 - p1[0]) * (1 - p2[0]), rtol=1e-12)
+    rng = np.random.default_rng(6)
+    N = 1_000_000
+    y = b[:, 0][:, None] + sigma * rng.standard_normal((4, N))
+    est = ((y[0] - y[1] >= 2) | (y[1] - y[0] >= 3)).mean()
+    se = math.sqrt(est * (1 - est) / N)
+    assert abs(est - (p1[0] + p2[0])) < 4 * se
+    assert est - cop[0, 0] > 20 * se and abs((est - cop[0, 0]) - p1[0] * p2[0]) < 4 * se
+
+
 def test_atom_derivative_finite_difference():
     """dd/db_j (Prop. Lipschitz proof form) against central differences of d = 1 - 2p."""
     inst = small_instance()
