@@ -16,8 +16,9 @@ the data path; rank 0 prints the max-over-ranks time.  In the time-to-SAT runs
 the replicas share one [SAT verified, out of time] flag per stage.
 
 Other modes: --workload (any entry of WORKLOADS), --gradient-time (the paper's
-gradient-time experiment on the random hybrid benchmark), --tts-plain (time to
-SAT in the plain form too), --impl reference (the FP64 oracle on the host).
+gradient-time experiment on the random hybrid benchmark), --no-tts-plain (skip
+the plain form's time to SAT, one seed by default), --impl reference (the FP64
+oracle on the host).
 """
 import argparse
 import json
@@ -66,7 +67,10 @@ def parse():
     p.add_argument("--eta", type=float, default=None)
     p.add_argument("--tts", type=float, default=150.0,
                    help="time-to-SAT budget in seconds per form (0 = skip)")
-    p.add_argument("--tts-plain", action="store_true", help="also time-to-SAT in the plain (unfused) form")
+    p.add_argument("--no-tts-plain", dest="tts_plain", action="store_false",
+                   help="skip the time-to-SAT run of the plain (unfused) form")
+    p.add_argument("--tts-plain-seeds", type=int, default=1,
+                   help="initial-point seeds of the plain form's time-to-SAT (the first ones of the fused form's)")
     p.add_argument("--tts-eta", type=float, default=0.2)
     p.add_argument("--tts-iters", type=int, default=20, help="PGD iterations per stage in the time-to-SAT runs")
     p.add_argument("--tts-trace", default=None,
@@ -447,7 +451,7 @@ def our_arm(args):
         sched_tts = [inst.scale / (0.1 * t) for t in range(1, 1001)]
         for form in ("fused", "plain") if args.tts_plain else ("fused",):
             runs = []
-            for s in range(max(1, args.tts_seeds)):
+            for s in range(max(1, args.tts_seeds if form == "fused" else min(args.tts_plain_seeds, args.tts_seeds))):
                 pa, pb = (a0, b0) if s == 0 else W.initial_point(inst, R, seed=replica_seed(rank) + 100000 * s)
                 S2 = Solver(P, comp, R, eta=args.tts_eta, b_scale=inst.scale, t_max=args.tts_iters, sweeps=20,
                             use_graph=True, form=form)
