@@ -478,6 +478,9 @@ def our_arm(args):
             par2 = [r["seconds"] if r["sat"] else 2 * args.tts for r in runs]
             tts[form] = {"median_s_par2": float(np.median(par2)), "solved": sum(r["sat"] for r in runs),
                          "seeds": len(runs), "runs": runs}
+        if "plain" in tts and tts["fused"]["runs"][0]["sat"] and tts["plain"]["runs"][0]["sat"]:
+            # same initial points, same schedule: the batched fused form against the plain one
+            tts["plain_over_fused_seed0"] = tts["plain"]["runs"][0]["seconds"] / tts["fused"]["runs"][0]["seconds"]
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:  # the host baseline runs at N = 1 only
