@@ -33,10 +33,16 @@ Follows, in the paper's order:
     normalised step does not see a common factor of the weights.
 
 Pins (tests/test_oracle_pgd.py): projection idempotent and non-expansive;
-Dykstra against an exact active-set enumeration of the QP on small blocks;
-the descent lemma with eta = 1/L (Lemma descent, Prop. Lipschitz); exact check
-against planted assignments and single-literal flips; Fig. 2's two minima;
-the vectorised kind evaluation against the scalar definition.
+Dykstra against an exact active-set enumeration of the QP on small blocks, and
+the polish within 8 margins of that exact projection (bit for bit unchanged
+where no half-space is within its margin); the descent lemma with eta = 1/L
+(Lemma descent, Prop. Lipschitz) at S = 1 and, in the coordinates y/S, at
+S = 100; the step's covariance under a change of the reals' unit (atoms, boxes,
+sigma and S times 4 give the reals times 4 and the same ||g||^2, bit for bit);
+step_sizes by hand on a three-constraint instance and its independence of the
+projected atoms' weights; exact check against planted assignments and
+single-literal flips; Fig. 2's two minima; the vectorised kind evaluation
+against the scalar definition.
 The annealing trajectory itself is parity unpinned (the paper gives no
 trajectory values for a known step size).
 """

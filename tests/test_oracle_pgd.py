@@ -399,3 +399,181 @@ def test_fig2_sigma_above_two_reaches_the_global_minimum():
             assert a == 1.0 and b <= 0, (sigma, a0, b0, a, b)
             if sigma == g["sigma_fast"]:
                 assert min(slow) > its
+
+
+# --------------------------------------------------------------------------- scaled coordinates
+def rescaled(inst, k):
+    """The same instance with every real measured in units k times smaller: y' = k y.
+    Atoms q.y rel q0 become q.y' rel k q0; boxes, the plant and the length scale
+    scale by k.  k a power of two keeps every value exact."""
+    import dataclasses
+    return dataclasses.replace(inst, atom_q0=inst.atom_q0 * k, lo=inst.lo * k, hi=inst.hi * k,
+                               planted_y=inst.planted_y * k, scale=inst.scale * k)
+
+
+@pytest.mark.parametrize("make", [lambda: W.jobshop(1002, 8, 4), lambda: W.tiny_random(21, 6, 4, 12),
+                                  lambda: W.placement2d(1003, 8)])
+def test_pgd_step_is_covariant_under_a_change_of_units(make):
+    """The reals' step is taken in the coordinates y/S (Eq. pg1, pg2 on the paper's
+    [0, 1]-scaled reals, Methods "Benchmarks").  A step defined that way cannot depend
+    on the unit the reals are written in: measuring every real in units 4 times
+    smaller (atoms, boxes, sigma and S times 4) must give the same Booleans, the reals
+    times 4, the same ||g||^2 (Eq. grad_map in scaled coordinates) and the same
+    objective, bit for bit (powers of two are exact).  An S where S^2 belongs in the
+    b-step, or S^2 where S belongs in ||g||^2, breaks this."""
+    inst = make()
+    k = 4
+    ik = rescaled(inst, k)
+    R = 6
+    a, b = W.initial_point(inst, R, seed=11)
+    a, b = a.astype(np.float64), b.astype(np.float64)
+    w = np.random.default_rng(2).uniform(0.5, 3.0, (inst.n_cons, R))
+    cfg = pgd.Config(eta=0.05)
+    sigma = inst.scale / 0.9
+    dom, domk = pgd.Domain(inst), pgd.Domain(ik)
+    etas = pgd.step_sizes(inst, w, cfg)
+    np.testing.assert_array_equal(etas, pgd.step_sizes(ik, w, cfg))
+    A, Bk = a.copy(), b * k
+    for _ in range(3):
+        obj, _, ga, gb = OBJ.evaluate(inst, a, b, w, sigma)
+        objk, _, gak, gbk = OBJ.evaluate(ik, A, Bk, w, sigma * k)
+        np.testing.assert_array_equal(obj, objk)
+        np.testing.assert_array_equal(ga, gak)
+        a, b, gn2 = pgd.pgd_step(a, b, ga, gb, etas, inst.scale, dom, cfg.sweeps, cfg.polish)
+        A, Bk, gn2k = pgd.pgd_step(A, Bk, gak, gbk, etas, ik.scale, domk, cfg.sweeps, cfg.polish)
+        np.testing.assert_array_equal(a, A)
+        np.testing.assert_array_equal(b * k, Bk)
+        np.testing.assert_array_equal(gn2, gn2k)
+        assert (gn2 > 0).all()
+
+
+def test_descent_lemma_in_scaled_coordinates():
+    """Lemma descent at S != 1.  In u = y/S the objective is F(a, u) = C(a, S u); an
+    atom q.(S u) <= q0 has the same probability as q.y <= q0 with sigma/S in place of
+    sigma, so Prop. Lipschitz gives L of F with sigma/S.  With eta = 1/L the step
+    (b-step eta S^2 dC/db = S times the u-step eta dF/du) must satisfy
+    F(new) <= F - eta/2 ||g||^2 with ||g|| measured in u.  A b-step S times too large
+    (S^3) overshoots and fails; S = 100 here, the reals' native range [0, 100]."""
+    inst = W.tiny_random(21, n_bool=6, n_real=4, n_cons=12)
+    S_ = inst.scale
+    assert S_ == 100.0
+    R = 4
+    a, b = W.initial_point(inst, R, seed=3)
+    a, b = a.astype(np.float64), b.astype(np.float64)
+    w = np.ones((inst.n_cons, R))
+    sigma_u = 0.3
+    sigma = sigma_u * S_
+    n, m = inst.n_bool, inst.n_real
+    alpha = float(inst.n_cons)
+    beta = max(1, max(sum(1 for l in inst.lits(c) if (l >> 1) >= n and j in inst.atom((l >> 1) - n)[0])
+                      for c in range(inst.n_cons) for j in range(m)))
+    gam = math.sqrt(2) * beta / (math.sqrt(math.pi) * sigma_u)
+    rho = alpha * math.sqrt(n + m) * max(1.0, gam)
+    L = math.sqrt(n + m * gam * gam) * rho
+    eta = 1.0 / L
+    dom = pgd.Domain(inst)
+    moved = 0.0
+    for _ in range(5):
+        obj, _, ga, gb = OBJ.evaluate(inst, a, b, w, sigma)
+        a2, b2, gn2 = pgd.pgd_step(a, b, ga, gb, eta, S_, dom, 20)
+        obj2 = OBJ.evaluate(inst, a2, b2, w, sigma, with_grad=False)[0]
+        assert (obj2 - obj <= -eta / 2 * gn2 + 1e-12).all()
+        moved = max(moved, np.abs(b2 - b).max())
+        a, b = a2, b2
+    assert moved > 0
+
+
+# --------------------------------------------------------------------------- step normalisation
+def three_constraint_instance():
+    """x0 OR A, NOT x1 OR B (in C_sigma) and the unit atom y0 + y1 <= 5 (projected)."""
+    B = W._Builder(2, 2)
+    A_ = B.atom([0, 1], [1, -2], 3)
+    B_ = B.atom([1], [3], 4)
+    U = B.atom([0, 1], [1, 1], 5)
+    B.con(W.OR, [W.lit(0), W.lit(A_)])
+    B.con(W.OR, [W.lit(1, True), W.lit(B_)])
+    B.con(W.OR, [W.lit(U)])
+    return B.freeze("three", np.zeros(2), np.full(2, 9.0), [-1, 1], np.array([1.0, 1.0]), 1.0)
+
+
+def test_step_sizes_hand_derived():
+    """eta_r = eta |C_sigma| / sum_{c in C_sigma} w_c (Thm. max_step with L proportional to
+    the total weight alpha of Prop. Lipschitz).  By hand for the three-constraint
+    instance, C_sigma = {0, 1} (constraint 2 is a projected unit atom):
+      restart 0, w = (2, 3, 100): 0.1 * 2 / 5 = 0.04
+      restart 1, w = (5, 1, 7):   0.1 * 2 / 6 = 1/30
+      restart 2, w = (1, 1, 1):   0.1 (unit weights give the configured step)
+    Summing over every constraint gives 0.1*2/105, 0.1*2/13 and 0.1*2/3; dropping
+    |C_sigma| gives 0.02, 1/60 and 0.05.  With the unit atom kept in the objective
+    (SOFT), |C_sigma| = 3 and the sums include it."""
+    inst = three_constraint_instance()
+    assert OBJ.objective_constraints(inst, OBJ.PROJECT) == [0, 1]
+    w = np.array([[2.0, 5.0, 1.0], [3.0, 1.0, 1.0], [100.0, 7.0, 1.0]])
+    cfg = pgd.Config(eta=0.1)
+    got = pgd.step_sizes(inst, w, cfg)
+    np.testing.assert_allclose(got, [0.04, 1.0 / 30.0, 0.1], rtol=1e-15)
+    soft = pgd.step_sizes(inst, w, cfg, policy=OBJ.SOFT)
+    np.testing.assert_allclose(soft, [0.1 * 3 / 105, 0.1 * 3 / 13, 0.1], rtol=1e-15)
+    off = pgd.step_sizes(inst, w, pgd.Config(eta=0.1, normalize_eta=False))
+    np.testing.assert_array_equal(off, [0.1, 0.1, 0.1])
+
+
+def test_step_sizes_ignore_the_weights_of_projected_atoms():
+    """A projected unit atom is not part of C_sigma, so its ERWA weight cannot change L
+    and must not change the step: the whole PGD trajectory is the same whatever its
+    weight (fails if the normalisation sums over every constraint)."""
+    inst = W.jobshop(1002, 6, 3)
+    R = 4
+    a, b = W.initial_point(inst, R, seed=6)
+    unit = [c for c in range(inst.n_cons) if OBJ.is_unit_atomic(inst, c)]
+    assert unit
+    w = np.random.default_rng(8).uniform(1.0, 4.0, (inst.n_cons, R))
+    w2 = w.copy()
+    w2[unit] *= 1000.0
+    cfg = pgd.Config(eta=0.05, eps=0.0, t_max=3)
+    sigma = inst.scale / 0.5
+    o1 = pgd.run_stage(inst, a, b, w, np.zeros_like(w), sigma, 1, cfg)
+    o2 = pgd.run_stage(inst, a, b, w2, np.zeros_like(w), sigma, 1, cfg)
+    np.testing.assert_array_equal(o1[0], o2[0])
+    np.testing.assert_array_equal(o1[1], o2[1])
+
+
+# --------------------------------------------------------------------------- polish at a converged point
+def test_polish_stays_within_its_margin_of_the_exact_projection():
+    """Prop. QP's projection, computed exactly by active-set enumeration, against
+    Dykstra run to convergence (3,000 sweeps) followed by the polish.  The polish only
+    moves a half-space whose value is within its margin m = 2^-16 (|q0| + sum |q_j y_j|)
+    of the boundary, onto q.y <= q0 - 2m, so:
+      * where the exact projection keeps every half-space more than 4 margins inside,
+        the polished point is Dykstra's point bit for bit (nothing moves);
+      * elsewhere, where the polish settles in D exactly, it stays within 8 margins
+        (max over the half-spaces) of the exact projection in every coordinate.
+    The bound is 2x the largest distance seen over 1,500 random blocks of 2-4 reals and
+    1-3 half-spaces (4.1 margins, at narrow corners where two moves of 2m add up).  A
+    polish that overshoots (a target 10 margins inside, a step not divided by ||q||^2)
+    or that moves points which need no move fails it."""
+    rng = np.random.default_rng(0)
+    interior = near = 0
+    for _ in range(30):
+        inst, lo, hi, A, c = halfspace_instance(rng, n_real=int(rng.integers(2, 5)), n_half=int(rng.integers(1, 4)))
+        dom = pgd.Domain(inst)
+        Y = rng.uniform(-6, 6, (inst.n_real, 8))            # 8 points per block, one call
+        XD = dom.project_b(Y, sweeps=3000, polish=0)
+        XP = dom.project_b(Y, sweeps=3000, polish=32)
+        for r in range(Y.shape[1]):
+            x_ex = exact_projection(Y[:, r], lo, hi, A, c)
+            if x_ex is None:
+                break
+            xd, xp = XD[:, r], XP[:, r]
+            M = max(pgd.POLISH_MARGIN * (abs(q0) + np.abs(q * x_ex[var]).sum()) for var, q, q0 in dom.halfspaces)
+            slack = min(q0 - (q * x_ex[var]).sum() for var, q, q0 in dom.halfspaces)
+            if slack > 4 * M:
+                np.testing.assert_array_equal(xp, xd)
+                interior += 1
+                continue
+            feasible = all(sum(Fraction(float(A[k, j])) * Fraction(float(xp[j])) for j in range(len(xp)))
+                           <= Fraction(float(c[k])) for k in range(len(c)))
+            if feasible:
+                assert np.abs(xp - x_ex).max() <= 8 * M, (np.abs(xp - x_ex).max() / M)
+                near += 1
+    assert interior > 20 and near > 60
