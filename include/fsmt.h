@@ -324,6 +324,27 @@ fsmt_status fsmt_round_check(const fsmt_compiled* c, int32_t R, const float* a, 
                              uint8_t* violated, int32_t* n_unsat, float* w, float* h, float rho, float gamma,
                              int32_t update_w, const float* wsum, void* stream);
 
+/* Alg. 1's rounding alone: x[i][r] = -1 (TRUE) if a[i][r] < 0, else +1, for every
+ * Boolean and restart (device a[n_bool][R] in, device int8 x[n_bool][R] out).  The
+ * values fsmt_round_check writes to its x.  Errors as above. */
+fsmt_status fsmt_round(const fsmt_compiled* c, int32_t R, const float* a, int8_t* x, void* stream);
+
+/* The epsilon rule of Eq. critical after one PGD iteration, per restart, as the
+ * stage applies it: for every restart with active[r] == 1, iters[r] += 1; then a
+ * non-finite gnorm2[r] stops it with active[r] = 2 and sets bit 0 of ctl[1];
+ * gnorm2[r] <= eps^2 stops it with active[r] = 0.  ctl[0] is overwritten with the
+ * number of restarts still active (1).  Device arrays gnorm2[R], active[R],
+ * iters[R], ctl[2]; eps >= 0.  For callers that drive the iterations themselves
+ * (the plain form); fsmt_solve_stage does this inside its graph.  Errors as above. */
+fsmt_status fsmt_converge(const fsmt_compiled* c, int32_t R, float eps, const float* gnorm2, uint8_t* active,
+                          int32_t* iters, int32_t* ctl, void* stream);
+
+/* Sets bit 31 of n_unsat[r] (device int32[R]) for every restart with active[r] == 2
+ * (device uint8[R]): a restart stopped on a non-finite ||g||^2, marked at the check
+ * as fsmt_solve_stage marks it.  Call it after fsmt_round_check.  Errors as above. */
+fsmt_status fsmt_mark_nonfinite(const fsmt_compiled* c, int32_t R, const uint8_t* active, int32_t* n_unsat,
+                                void* stream);
+
 /* ------------------------------------------------------- one sigma stage --
  * One stage of Alg. 2 for all restarts: wsum from fsmt_weight_sum, then up to
  * t_max iterations of

@@ -86,6 +86,9 @@ PROTOTYPES = {
     "fsmt_weight_sum": [P, i32, P, P, P],
     "fsmt_pgd_step": [P, i32, f32, f32, i32, i32, P, P, P, P, P, P, P, P],
     "fsmt_round_check": [P, i32, P, P, P, P, P, P, P, f32, f32, i32, P, P],
+    "fsmt_round": [P, i32, P, P, P],
+    "fsmt_converge": [P, i32, f32, P, P, P, P, P],
+    "fsmt_mark_nonfinite": [P, i32, P, P, P],
     "fsmt_solve_stage": [P, C.POINTER(StageConfig), C.POINTER(State), P],
     "fsmt_solve_stage_host": [P, C.POINTER(StageConfig), C.POINTER(State), P, P, P, P, P],
     "fsmt_last_error": [],

@@ -556,11 +556,13 @@ __global__ void k_iter_begin(int R, float* obj, float* gn2, const int* ctl) {
 // whose ||g||^2 <= eps^2 stops (active 0); one whose ||g||^2 is not finite stops
 // with active 2 and error bit 1 in ctl[1] (its point may already have been clamped
 // back into the box, so the round check marks it from active).  One block;
-// ctl[0] = restarts still iterating.
-__global__ void k_converge(int R, const float* prm, const float* gn2, uint8_t* active, int* iters, int* ctl) {
-  if (ctl[0] == 0) return;
+// ctl[0] = restarts still iterating.  gate: return at once when ctl[0] is already 0
+// (the graph's iterations past convergence); eps comes from prm when it is given.
+__global__ void k_converge(int R, const float* prm, float eps_arg, const float* gn2, uint8_t* active, int* iters,
+                           int* ctl, int gate) {
+  if (gate && ctl[0] == 0) return;
   __syncthreads();
-  const float eps = prm[P_EPS];
+  const float eps = load_param(prm, P_EPS, eps_arg);
   const float eps2 = eps * eps;
   int cnt = 0;
   for (int r = threadIdx.x; r < R; r += blockDim.x) {
@@ -802,6 +804,12 @@ __global__ void __launch_bounds__(kCheckThreads, 3)
     if (cnt_s[r]) atomicAdd(n_unsat + r, cnt_s[r]);
     if (active && blockIdx.x == 0 && active[r] == 2) atomicOr(n_unsat + r, kUnsatNonFinite);
   }
+}
+
+// bit 31 of n_unsat[r] for every restart stopped on a non-finite ||g||^2 (active 2)
+__global__ void k_mark_nonfinite(int R, const uint8_t* __restrict__ active, int* __restrict__ n_unsat) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < R; r += gridDim.x * blockDim.x)
+    if (active[r] == 2) n_unsat[r] |= kUnsatNonFinite;
 }
 
 __global__ void k_sign(int n, int R, const float* __restrict__ a, int8_t* __restrict__ x) {
@@ -1480,6 +1488,47 @@ fsmt_status fsmt_round_check(const fsmt_compiled* c, int32_t R, const float* a, 
   return launch_round_check(C, R, a, b, violated, n_unsat, w, h, rho, gamma, update_w, nullptr, wsum, nullptr, st);
 }
 
+fsmt_status fsmt_round(const fsmt_compiled* c, int32_t R, const float* a, int8_t* x, void* stream) {
+  fsmt_status s = check_ready(c, R);
+  if (s != FSMT_OK) return s;
+  const Compiled& C = c->c;
+  if (C.n_bool == 0) return FSMT_OK;
+  if (!a || !x) {
+    set_error("NULL argument");
+    return FSMT_EINVAL;
+  }
+  k_sign<<<std::min<long>(((long)C.n_bool * R + 255) / 256, 65535L), 256, 0, (cudaStream_t)stream>>>(C.n_bool, R,
+                                                                                                        a, x);
+  FSMT_CUDA(cudaGetLastError(), "sign launch");
+  return FSMT_OK;
+}
+
+fsmt_status fsmt_converge(const fsmt_compiled* c, int32_t R, float eps, const float* gnorm2, uint8_t* active,
+                          int32_t* iters, int32_t* ctl, void* stream) {
+  fsmt_status s = check_ready(c, R);
+  if (s != FSMT_OK) return s;
+  if (!gnorm2 || !active || !iters || !ctl || !(eps >= 0.f)) {
+    set_error("NULL argument or invalid eps");
+    return FSMT_EINVAL;
+  }
+  k_converge<<<1, 1024, 0, (cudaStream_t)stream>>>(R, nullptr, eps, gnorm2, active, iters, ctl, 0);
+  FSMT_CUDA(cudaGetLastError(), "converge launch");
+  return FSMT_OK;
+}
+
+fsmt_status fsmt_mark_nonfinite(const fsmt_compiled* c, int32_t R, const uint8_t* active, int32_t* n_unsat,
+                                void* stream) {
+  fsmt_status s = check_ready(c, R);
+  if (s != FSMT_OK) return s;
+  if (!active || !n_unsat) {
+    set_error("NULL argument");
+    return FSMT_EINVAL;
+  }
+  k_mark_nonfinite<<<(R + 255) / 256, 256, 0, (cudaStream_t)stream>>>(R, active, n_unsat);
+  FSMT_CUDA(cudaGetLastError(), "mark launch");
+  return FSMT_OK;
+}
+
 static fsmt_status enqueue_stage(const Compiled& C, int t_max, fsmt_state* s, cudaStream_t st) {
   const int R = s->R;
   k_stage_begin<<<(R + 255) / 256, 256, 0, st>>>(R, s->active, s->iters, s->ctl);
@@ -1494,7 +1543,7 @@ static fsmt_status enqueue_stage(const Compiled& C, int t_max, fsmt_state* s, cu
     e = launch_pgd(C, R, 1.f, 1.f, 0, 0, s->params, s->wsum, s->a, s->b, s->grad_a, s->grad_b, s->gnorm2, s->active, 1,
                    s->ctl, st);
     if (e != FSMT_OK) return e;
-    k_converge<<<1, 1024, 0, st>>>(R, s->params, s->gnorm2, s->active, s->iters, s->ctl);
+    k_converge<<<1, 1024, 0, st>>>(R, s->params, 0.f, s->gnorm2, s->active, s->iters, s->ctl, 1);
     FSMT_CUDA(cudaGetLastError(), "converge");
   }
   return launch_round_check(C, R, s->a, s->b, nullptr, s->n_unsat, s->w, s->h, 0.f, 2.f, 0, s->params, s->wsum,

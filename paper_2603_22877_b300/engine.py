@@ -228,6 +228,27 @@ class Compiled:
                int(bool(update_w)), _dptr(wsum, torch.float32, (R,), "wsum"), _stream(stream))
 
 
+    def round(self, R, a, x, stream=None):
+        """Alg. 1's rounding of every Boolean and restart into x (int8 [n_bool][R])."""
+        import torch
+        sa, _, _ = self._shapes(R)
+        L.call("fsmt_round", self.h, int(R), _dptr(a, torch.float32, sa, "a"), _dptr(x, torch.int8, sa, "x"),
+               _stream(stream))
+
+    def converge(self, R, eps, gnorm2, active, iters, ctl, stream=None):
+        """Eq. critical after one iteration (fsmt_converge): updates active, iters and ctl."""
+        import torch
+        L.call("fsmt_converge", self.h, int(R), float(eps), _dptr(gnorm2, torch.float32, (R,), "gnorm2"),
+               _dptr(active, torch.uint8, (R,), "active"), _dptr(iters, torch.int32, (R,), "iters"),
+               _dptr(ctl, torch.int32, None, "ctl"), _stream(stream))
+
+    def mark_nonfinite(self, R, active, n_unsat, stream=None):
+        """Bit 31 of n_unsat for the restarts stopped on a non-finite ||g||^2."""
+        import torch
+        L.call("fsmt_mark_nonfinite", self.h, int(R), _dptr(active, torch.uint8, (R,), "active"),
+               _dptr(n_unsat, torch.int32, (R,), "n_unsat"), _stream(stream))
+
+
 def relaxed_objective(compiled, sigma, w, a, b, plain=False):
     """C_sigma per restart as a differentiable torch function of (a, b)."""
     return RelaxedObjective.apply(a, b, compiled, w, float(sigma), bool(plain))
@@ -305,6 +326,28 @@ def max_over_replicas(device="cpu"):
     return share
 
 
+def gather_replicas(record):
+    """Every replica's `record` (any picklable object), in rank order, on every rank of
+    the default torch.distributed process group (all_gather_object; [record] without a
+    group).  The host-side exchange of the independent-replica protocol, run once after
+    the replicas have finished: nothing on the data path waits on it."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [record]
+    out = [None] * dist.get_world_size()
+    dist.all_gather_object(out, record)
+    return out
+
+
+def replica_median(runs, limit):
+    """The paper's replica protocol (Methods, experimental setup: independent replicas,
+    the median reported) scored as PAR-2 (a replica that found no exactly verified SAT
+    counts twice the time limit): runs are dicts with "sat" and "seconds"."""
+    if not runs:
+        raise ValueError("no replica runs")
+    return float(np.median([r["seconds"] if r["sat"] else 2.0 * float(limit) for r in runs]))
+
+
 class _Lazy:
     def __init__(self):
         self.fn = None
@@ -343,6 +386,7 @@ class Solver:
             raise ValueError(f"no fused kernel takes a diagram of {info['max_nodes']} nodes; use form='plain'")
         self.form = form
         self._work = None
+        self._x = None  # rounded Booleans of the candidates verified on the host
         self.problem, self.comp, self.R = problem, compiled, int(R)
         if not compiled.uploaded:
             compiled.upload()
@@ -410,7 +454,11 @@ class Solver:
         L.call("fsmt_solve_stage", self.comp.h, C.byref(cfg), C.byref(self._state), _stream(stream))
 
     def _stage_plain(self, sigma, t, stream=None):
-        """One stage of Alg. 2 in the plain form; the same steps as fsmt_solve_stage."""
+        """One stage of Alg. 2 in the plain form; the same steps as fsmt_solve_stage,
+        each a library call issued from here: weight sums, then per iteration the
+        plain forward and adjoint passes, the PGD step and the epsilon test
+        (fsmt_converge, which also counts the restarts still iterating into ctl[0]),
+        then round + check + ERWA and the marking of non-finite restarts."""
         import torch
         comp, R = self.comp, self.R
         if self._work is None:
@@ -418,7 +466,7 @@ class Solver:
         comp.weight_sum(R, self.w, self.wsum, stream)
         self.active.fill_(1)
         self.iters.zero_()
-        eps2 = float(self.eps) ** 2
+        self.ctl.zero_()
         for _ in range(int(self.t_max)):
             comp.forward_plain(R, sigma, self.w, self.a, self.b, self._work, obj=self.obj, stream=stream)
             comp.adjoint_plain(R, sigma, self.w, self.a, self.b, self._work, self.grad_a, self.grad_b, stream=stream)
@@ -426,17 +474,13 @@ class Solver:
             comp.pgd_step(R, self.eta, self.b_scale, self.sweeps, self.a, self.b, self.grad_a, self.grad_b,
                           self.gnorm2, active=self.active, wsum=self.wsum if self.normalize_eta else None,
                           polish=self.polish, stream=stream)
-            act = self.active == 1
-            self.iters += act.to(torch.int32)
-            self.active.masked_fill_(act & ~torch.isfinite(self.gnorm2), 2)
-            self.active.masked_fill_(act & (self.gnorm2 <= eps2), 0)
-            if not bool((self.active == 1).any()):
+            comp.converge(R, self.eps, self.gnorm2, self.active, self.iters, self.ctl, stream=stream)
+            if int(self.ctl[0].item()) == 0:
                 break
         comp.round_check(R, self.a, self.b, self.n_unsat, w=self.w, h=self.h, rho=self.rho, gamma=self.gamma,
                          update_w=(t % self.tau == 0), wsum=self.wsum if self.normalize_eta else None,
                          stream=stream)
-        stopped = self.active == 2                       # as the fused stage marks them
-        self.n_unsat[stopped] |= torch.iinfo(torch.int32).min
+        comp.mark_nonfinite(R, self.active, self.n_unsat, stream=stream)
 
     def stage_host(self, sigma, t, a_host, b_host, n_unsat_host, obj_host, stream=None):
         """The same stage with host input/output buffers (copies inside the call)."""
@@ -445,7 +489,13 @@ class Solver:
                _np_ptr(b_host), _np_ptr(n_unsat_host), _np_ptr(obj_host), _stream(stream))
 
     def verify_restart(self, r):
-        x = np.where(self.a[:, r].cpu().numpy() < 0, -1, 1).astype(np.int8)
+        """Restart r's rounded point (fsmt_round) checked exactly on the host
+        (fsmt_verify_exact); y is the restart's reals, widened to float64 exactly."""
+        import torch
+        if self._x is None:
+            self._x = torch.empty((self.comp.n_bool, self.R), device=self.a.device, dtype=torch.int8)
+        self.comp.round(self.R, self.a, self._x)
+        x = self._x[:, r].cpu().numpy()
         y = self.b[:, r].cpu().numpy().astype(np.float64)
         sat, _ = self.problem.verify_exact(x, y)
         return sat, x, y
@@ -466,12 +516,24 @@ class Solver:
         log: called after every stage with one record (a dict: stage, sigma, seconds since
         the start, fewest and median #Unsat over the finite restarts, restarts at #Unsat
         0, non-finite restarts, mean PGD iterations, median ||g||^2 of the last iteration,
-        best objective); jsonl_log(path) writes them one JSON line each."""
+        best objective, and the stage's device time from CUDA events around it, gpu_ms);
+        jsonl_log(path) writes them one JSON line each.
+
+        The result also counts rejected_candidates: restarts whose device check reported
+        #Unsat = 0 but whose rounded point failed the exact host verification (a
+        disagreement between the two checks; 0 is expected)."""
         import torch
         t0 = time.perf_counter()
-        best, t, nonfinite = None, 0, 0
+        best, t, nonfinite, rejected = None, 0, 0, 0
+        ev = None
+        if log is not None and self.n_unsat.is_cuda:
+            ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
         for t, sigma in enumerate(schedule, start=1):
+            if ev is not None:
+                ev[0].record()
             self.stage(sigma, t)
+            if ev is not None:
+                ev[1].record()
             nu = self.n_unsat
             nonfinite = int((nu < 0).sum())
             found = None
@@ -487,7 +549,8 @@ class Solver:
                          at_zero=int((nu == 0).sum()), nonfinite=nonfinite,
                          mean_iters=float(self.iters.float().mean()),
                          median_gnorm2=float(torch.nanmedian(self.gnorm2.float())),
-                         best_obj=float(obj.min()) if obj.numel() else None))
+                         best_obj=float(obj.min()) if obj.numel() else None,
+                         gpu_ms=(ev[1].synchronize(), ev[0].elapsed_time(ev[1]))[1] if ev is not None else None))
             if nonfinite < self.R:
                 cand = torch.nonzero(nu == 0).flatten().tolist() if lo == 0 else []
                 for r in cand:
@@ -495,6 +558,7 @@ class Solver:
                     if sat:
                         found = dict(sat=True, restart=r, stage=t, x=x, y=y)
                         break
+                    rejected += 1
             elif share is None:
                 break
             late = time_limit is not None and time.perf_counter() - t0 > time_limit
@@ -503,13 +567,14 @@ class Solver:
                 flags = [int(v) for v in share(flags)]
             if found is not None:
                 return dict(found, stages_run=t, best_unsat=0, nonfinite=nonfinite, stopped_by_peer=False,
-                            seconds=time.perf_counter() - t0)
+                            seconds=time.perf_counter() - t0, rejected_candidates=rejected)
             if flags[0]:
                 return dict(sat=False, restart=None, stage=None, stages_run=t, best_unsat=best,
-                            nonfinite=nonfinite, stopped_by_peer=True, seconds=time.perf_counter() - t0)
+                            nonfinite=nonfinite, stopped_by_peer=True, seconds=time.perf_counter() - t0,
+                            rejected_candidates=rejected)
             if flags[1]:
                 break
         if self.n_unsat.is_cuda:
             torch.cuda.synchronize()
         return dict(sat=False, restart=None, stage=None, stages_run=t, best_unsat=best, nonfinite=nonfinite,
-                    stopped_by_peer=False, seconds=time.perf_counter() - t0)
+                    stopped_by_peer=False, seconds=time.perf_counter() - t0, rejected_candidates=rejected)

@@ -193,6 +193,7 @@ def test_anneal_finds_exactly_verified_sat():
     res = S.anneal(sched)
     assert res["sat"], res
     assert Sm.unsat_constraints(inst, res["x"], res["y"]) == []
+    assert res["rejected_candidates"] == 0   # the device check and the host verifier agree
 
 
 def test_checkpoint_resume_reproduces_the_run():
@@ -248,3 +249,48 @@ def test_long_schedule_keeps_weights_finite(form):
     assert np.isfinite(S.gnorm2.cpu().numpy()).all() and np.isfinite(S.obj.cpu().numpy()).all()
     if form == "fused":
         assert int(S.ctl[1].item()) == 0
+
+
+def test_round_matches_the_oracle_rounding():
+    """fsmt_round (Alg. 1: x = TRUE (-1) iff a < 0) against the oracle's rounding, on
+    points that include exact zeros of both signs and the box ends."""
+    import torch
+    inst = W.jobshop(1002, 10, 5)
+    R = 70
+    P, comp, a, b, _ = setup(inst, R)
+    a = a.copy()
+    a[0, :4] = [0.0, -0.0, -1.0, 1.0]
+    a[1, :3] = [np.float32(-1e-30), np.float32(1e-30), np.float32(-np.finfo(np.float32).tiny)]
+    da, = to_dev(a)
+    x = torch.zeros((inst.n_bool, R), dtype=torch.int8, device="cuda")
+    comp.round(R, da, x)
+    x_ref, _ = pgd.round_check(inst, a.astype(np.float64), b.astype(np.float64), constraints=[])
+    np.testing.assert_array_equal(x.cpu().numpy(), x_ref)
+
+
+def test_converge_and_nonfinite_marks():
+    """fsmt_converge applies Eq. critical to restarts still iterating (active 1):
+    ||g||^2 <= eps^2 stops one (active 0), a non-finite ||g||^2 stops it with active 2
+    and ctl[1] bit 0, the others keep iterating and are counted in ctl[0]; every
+    iterating restart's iteration count grows by one.  fsmt_mark_nonfinite then sets
+    bit 31 of #Unsat exactly for the restarts with active 2."""
+    import torch
+    inst = W.tiny_random(1001)
+    R = 8
+    P, comp, _, _, _ = setup(inst, R)
+    eps = 0.01
+    g = np.array([0.5, 1e-5, np.nan, np.inf, 2.0, 1e-4, -np.inf, 3e-4], np.float32)
+    act = np.array([1, 1, 1, 1, 0, 1, 1, 1], np.uint8)
+    dg = torch.from_numpy(g).cuda()
+    da = torch.from_numpy(act).cuda()
+    it = torch.full((R,), 3, dtype=torch.int32, device="cuda")
+    ctl = torch.tensor([R, 0, 0, 0], dtype=torch.int32, device="cuda")
+    comp.converge(R, eps, dg, da, it, ctl)
+    assert da.cpu().numpy().tolist() == [1, 0, 2, 2, 0, 0, 2, 1]
+    assert it.cpu().numpy().tolist() == [4, 4, 4, 4, 3, 4, 4, 4]
+    assert ctl.cpu().numpy().tolist()[:2] == [2, 1]
+    nu = torch.tensor([3, 0, 5, 1, 0, 0, 7, 2], dtype=torch.int32, device="cuda")
+    comp.mark_nonfinite(R, da, nu)
+    bit = np.int32(-2 ** 31)
+    want = np.array([3, 0, 5 | bit, 1 | bit, 0, 0, 7 | bit, 2], np.int32)
+    np.testing.assert_array_equal(nu.cpu().numpy(), want)
