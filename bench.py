@@ -69,12 +69,16 @@ def parse():
                    help="time-to-SAT budget in seconds per form (0 = skip)")
     p.add_argument("--no-tts-plain", dest="tts_plain", action="store_false",
                    help="skip the time-to-SAT run of the plain (unfused) form")
-    p.add_argument("--tts-plain-seeds", type=int, default=1,
+    p.add_argument("--tts-plain-seeds", type=int, default=5,
                    help="initial-point seeds of the plain form's time-to-SAT (the first ones of the fused form's)")
     p.add_argument("--tts-eta", type=float, default=0.2)
     p.add_argument("--tts-iters", type=int, default=20, help="PGD iterations per stage in the time-to-SAT runs")
     p.add_argument("--tts-trace", default=None,
                    help="JSON-lines file for the per-stage records of the time-to-SAT runs (Solver.anneal log)")
+    p.add_argument("--tts-protocol", default="median", choices=["median", "first"],
+                   help="under torchrun: 'median' runs every replica independently to its own SAT and reports "
+                        "the median over replicas and seeds (the paper's protocol); 'first' stops all replicas "
+                        "at the first stage where one of them verified SAT")
     p.add_argument("--tts-seeds", type=int, default=5,
                    help="initial-point seeds per form; the median is PAR-2 (a miss counts twice the limit)")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -239,55 +243,238 @@ def profiled_traffic(workload, R):
 
 
 # ---------------------------------------------------------------------------- oracle timing
-def oracle_sample_rate(inst, R, a, b, w, sigma, budget_s):
-    """The FP64 oracle (as it stands) over a bounded prefix of the constraints of C_sigma.
+def host_cpu():
+    """(usable cores, CPU model) of this host."""
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count() or 1
+    model = "unknown"
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return cores, model
 
-    Returns (nodes/s, constraints sampled, node-restart visits, seconds)."""
+
+def oracle_sample_rate(inst, R, a, b, sigma, budget_s, cons=None, cycle=False):
+    """The FP64 oracle (as it stands, unit weights) over the constraints `cons` (default:
+    C_sigma in id order), one after another until budget_s has passed, on this core
+    (with cycle, starting again at the first when all are done).
+
+    Returns (nodes/s, constraint evaluations, node-restart visits, seconds)."""
     from oracle import objective as OBJ
     D = OBJ.Diagrams(inst)
-    a64, b64, w64 = a.astype(np.float64), b.astype(np.float64), w.astype(np.float64)
-    oc = OBJ.objective_constraints(inst)
+    a64, b64 = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    ones = np.ones(R)
+    oc = OBJ.objective_constraints(inst) if cons is None else cons
     t0 = time.perf_counter()
     visits, k = 0, 0
-    while k < len(oc) and time.perf_counter() - t0 < budget_s:
-        c = oc[k]
-        OBJ.constraint_contrib(inst, D, c, a64, b64, w64[c], sigma)
+    while (cycle or k < len(oc)) and oc and time.perf_counter() - t0 < budget_s:
+        c = oc[k % len(oc)]
+        OBJ.constraint_contrib(inst, D, c, a64, b64, ones, sigma)
         visits += len(D[c][0]) * R
         k += 1
     dt = time.perf_counter() - t0
     return visits / dt, k, visits, dt
 
 
+def constraint_slice(inst, cons):
+    """The instance restricted to the constraints `cons` and the atoms they name (atoms
+    renumbered in order of first use; Booleans and reals unchanged), so that a worker
+    process receives only its share of the input."""
+    import dataclasses
+    amap, ptr, var, coef, q0, rel = {}, [0], [], [], [], []
+    kinds, params, cptr, lits = [], [], [0], []
+    for c in cons:
+        for l in inst.lits(c):
+            vid = int(l) >> 1
+            if vid >= inst.n_bool:
+                i = vid - inst.n_bool
+                if i not in amap:
+                    amap[i] = len(amap)
+                    v, cf, q, r = inst.atom(i)
+                    var += list(v)
+                    coef += list(cf)
+                    ptr.append(len(var))
+                    q0.append(q)
+                    rel.append(r)
+                vid = inst.n_bool + amap[i]
+            lits.append(2 * vid + (int(l) & 1))
+        kinds.append(int(inst.con_kind[c]))
+        params.append(int(inst.con_param[c]))
+        cptr.append(len(lits))
+    return dataclasses.replace(
+        inst, atom_ptr=np.asarray(ptr, np.int64), atom_var=np.asarray(var, np.int32),
+        atom_coef=np.asarray(coef, np.int64), atom_q0=np.asarray(q0, np.int64), atom_rel=np.asarray(rel, np.int8),
+        con_kind=np.asarray(kinds, np.int8), con_param=np.asarray(params, np.int32),
+        con_ptr=np.asarray(cptr, np.int64), con_lits=np.asarray(lits, np.int32))
+
+
+_W = {}
+
+
+def _oracle_worker_init(shm_a, shape_a, shm_b, shape_b, R, sigma):
+    from multiprocessing import shared_memory
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    sa = shared_memory.SharedMemory(name=shm_a) if shm_a else None
+    sb = shared_memory.SharedMemory(name=shm_b) if shm_b else None
+    _W.update(sa=sa, sb=sb, R=R, sigma=sigma,
+              a=np.ndarray(shape_a, np.float64, buffer=sa.buf) if sa else np.zeros(shape_a),
+              b=np.ndarray(shape_b, np.float64, buffer=sb.buf) if sb else np.zeros(shape_b))
+
+
+def _oracle_worker(job):
+    sub, start_at, budget_s = job
+    while time.time() < start_at:   # every worker starts together
+        time.sleep(0.001)
+    _, k, v, dt = oracle_sample_rate(sub, _W["R"], _W["a"], _W["b"], _W["sigma"], budget_s,
+                                     cons=list(range(sub.n_cons)), cycle=True)
+    return v, dt, k
+
+
+class OraclePool:
+    """The FP64 oracle on `workers` processes at once (spawn context; the points shared
+    through shared memory), each over its own block of `per_worker` consecutive
+    constraints of C_sigma; run(budget) times one round of all of them together and
+    returns (nodes/s = the sum of the workers' rates, constraints done, seconds)."""
+
+    def __init__(self, inst, R, a, b, sigma, workers, per_worker):
+        import multiprocessing as mp
+        from multiprocessing import shared_memory
+        from oracle import objective as OBJ
+        oc = OBJ.objective_constraints(inst)
+        a64, b64 = np.ascontiguousarray(a, np.float64), np.ascontiguousarray(b, np.float64)
+        self.shms, names = [], []
+        for x in (a64, b64):
+            if x.size:
+                m = shared_memory.SharedMemory(create=True, size=x.nbytes)
+                np.ndarray(x.shape, np.float64, buffer=m.buf)[...] = x
+                self.shms.append(m)
+                names.append(m.name)
+            else:
+                names.append(None)
+        n = min(per_worker, len(oc))
+        self.jobs = [constraint_slice(inst, [oc[(i * per_worker + j) % len(oc)] for j in range(n)])
+                     for i in range(workers)]
+        self.workers, self.per_worker = workers, per_worker
+        self.pool = mp.get_context("spawn").Pool(workers, initializer=_oracle_worker_init,
+                                                 initargs=(names[0], a64.shape, names[1], b64.shape, R, sigma))
+
+    def run(self, budget_s):
+        start_at = time.time() + 1.0 + 0.01 * self.workers
+        res = self.pool.map(_oracle_worker, [(j, start_at, budget_s) for j in self.jobs], chunksize=1)
+        return sum(v / dt for v, dt, _ in res), sum(k for _, _, k in res), max(dt for _, dt, _ in res)
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+        for m in self.shms:
+            m.close()
+            m.unlink()
+
+
+def cpu_baseline(inst, R, a, b, sigma, budget_s=10.0):
+    """The FP64 oracle on this host: one core over C_sigma in order, then every usable
+    core at once, each process over its own block of C_sigma (twice what one core got
+    through in the same time); both in node visits per second."""
+    cores, model = host_cpu()
+    r1, k1, _, dt1 = oracle_sample_rate(inst, R, a, b, sigma, budget_s)
+    per = max(64, 2 * k1)
+    pool = OraclePool(inst, R, a, b, sigma, cores, per)
+    try:
+        rn, kn, dtn = pool.run(budget_s)
+    finally:
+        pool.close()
+    return {"value": rn, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"FP64 numpy forward+adjoint, {R} restarts: one core over the first {k1} constraints of "
+                       f"C_sigma ({dt1:.1f} s); {cores} processes at once, each over its own block of {per} "
+                       f"constraints of C_sigma ({dtn:.1f} s, {kn} constraints in all)"),
+            "value_1core": r1, "value_allcores": rn, "cores_used": cores, "nproc": cores, "cpu_model": model}
+
+
 def reference_arm(args):
+    """The reference arm: the paper publishes no code, so the FP64 oracle as it stands
+    runs on every usable host core (one process per core, each over its own block of
+    C_sigma) on the same workload, restarts and initial points; a step is one round of
+    all processes at once (~3 s each)."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
     make, R = WORKLOADS[args.workload]
     inst = make()
-    a, b = W.initial_point(inst, R, seed=7)
-    w = np.ones((inst.n_cons, R), np.float32)
+    a, b = W.initial_point(inst, R, seed=replica_seed(0))
     sigma = inst.scale / (0.1 * 10)
+    cores, model = host_cpu()
     budget = 3.0
-    for _ in range(args.warmup):
-        oracle_sample_rate(inst, R, a, b, w, sigma, budget)
-    visits, secs, ks = 0, 0.0, []
-    for _ in range(args.steps):
-        _, k, v, dt = oracle_sample_rate(inst, R, a, b, w, sigma, budget)
-        visits += v
-        secs += dt
-        ks.append(k)
-    value = visits / secs
-    sample = (f"first {max(ks)} constraints of C_sigma x {R} restarts per step (~{budget:.0f} s of FP64 numpy "
-              f"forward+adjoint each), {inst.name}")
+    _, k1, _, _ = oracle_sample_rate(inst, R, a, b, sigma, budget)
+    per = max(64, 2 * k1)
+    pool = OraclePool(inst, R, a, b, sigma, cores, per)
+    try:
+        for _ in range(args.warmup):
+            pool.run(1.0)
+        rates, ks, secs = [], [], 0.0
+        for _ in range(args.steps):
+            r, k, dt = pool.run(budget)
+            rates.append(r)
+            ks.append(k)
+            secs += dt
+    finally:
+        pool.close()
+    value = float(np.mean(rates))
+    sample = (f"{cores} processes, each over its own block of {per} constraints of C_sigma x {R} restarts, "
+              f"~{budget:.0f} s of FP64 numpy forward+adjoint per step ({int(np.mean(ks))} constraints per step), "
+              f"{inst.name}")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * secs / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": inst.name, "restarts": R, "n_vars": inst.n_bool + inst.n_real,
                        "n_cons": inst.n_cons},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                             "cpu_model": model},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def fused_roofline(info, inst, R, nodes, fused_ms, launch, workload, peaks, peak_kind, n_sm):
+    """Roofline of the fused forward + adjoint kernel against both roofs it could hit.
+
+    Work per launch: 10 FP32 flops per decision-node visit (Alg. 3: two FMA; Alg. 4:
+    one subtract, one FMA; the adjoint sum: one FMA), against n_sm x 128 FP32 lanes x
+    2 flops x the maximum SM clock; and the algorithmic bytes (structure once: 8 B per
+    node, 17 B per atom, 8 B per nonzero, 9 B per constraint; state once: w, a and b
+    in, the gradients out, the objective) against the measured HBM bandwidth.  The
+    reported bound is the roof the kernel is nearer to (the larger fraction).  At the
+    FP32 roof the same launch would move its bytes at alg_bytes / (alg_flops /
+    alu_peak): the fraction of HBM a fused form of this work can reach at most."""
+    sm_mhz = float(peaks.get("sm_max_mhz", 2032.0))
+    alu_peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
+    alg_flops = 10.0 * nodes * R
+    structure = nodes * 8 + info["n_atoms"] * 17 + info["atom_nnz"] * 8 + info["n_obj_cons"] * 9
+    state = 4 * R * (info["n_obj_cons"] + 2 * (inst.n_bool + inst.n_real) + 1)
+    alg_bytes = structure + state
+    sec = fused_ms / 1000.0
+    alu = {"achieved": alg_flops / sec / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
+           "frac": alg_flops / sec / 1e12 / alu_peak,
+           "peak_kind": f"derived: {n_sm} SMs x 128 FP32 lanes x 2 flops (FMA) x {sm_mhz:.0f} MHz"}
+    hbm = {"achieved": alg_bytes / sec / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+           "frac": alg_bytes / sec / 1e9 / peaks["hbm_gbs"], "peak_kind": f"{peak_kind} (copy bandwidth)"}
+    cap = alg_bytes / (alg_flops / (alu_peak * 1e12)) / 1e9 / peaks["hbm_gbs"]
+    top, bound = (alu, "alu") if alu["frac"] >= hbm["frac"] else (hbm, "hbm")
+    traffic, traffic_note = profiled_traffic(workload, R)
+    return {"bound": bound, "achieved": top["achieved"], "peak": top["peak"], "unit": top["unit"],
+            "frac": top["frac"], "traffic": traffic, "peak_kind": top["peak_kind"],
+            "kernel": kernel_name(launch), "kernel_ms": fused_ms, "algorithmic_flops": alg_flops,
+            "algorithmic_bytes": alg_bytes, "traffic_source": traffic_note,
+            "node_visits_per_s": nodes * R / sec, "alu": alu, "hbm": hbm,
+            "hbm_target": {"frac": 0.5, "met": hbm["frac"] >= 0.5, "hbm_frac_at_fp32_roof": cap,
+                           "note": "at 10 FP32 flops per node visit the FP32 roof caps a fused form of this "
+                                   "work at hbm_frac_at_fp32_roof of HBM bandwidth"}}
 
 
 # ---------------------------------------------------------------------------- our arm
@@ -376,29 +563,8 @@ def our_arm(args):
     torch.cuda.synchronize()
     fused_ms = f0.elapsed_time(f1) / args.roofline_launches  # includes the three small memsets
     peaks, peak_kind = load_peaks()
-    # The fused kernel is bound by instruction issue, not by DRAM: its DRAM
-    # traffic is the algorithmic minimum (structure once, w and the state once)
-    # and runs at a few percent of HBM bandwidth.  Its roofline is FP32 ALU:
-    # 10 flops per decision-node visit (Alg. 3: two FMA; Alg. 4: one subtract,
-    # one FMA; adjoint: one FMA, counted as in DESIGN) against 148 SMs x 128 FP32
-    # lanes x 2 flops x the maximum SM clock.
-    sm_mhz = float(peaks.get("sm_max_mhz", 2032.0))
-    alu_peak = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
-    alg_flops = 10.0 * nodes * R
-    structure = nodes * 8 + info["n_atoms"] * 17 + info["atom_nnz"] * 8 + info["n_obj_cons"] * 9
-    state = 4 * R * (info["n_obj_cons"] + 2 * (inst.n_bool + inst.n_real) + 1)
-    alg_bytes = structure + state
-    achieved = alg_flops / (fused_ms / 1000.0) / 1e12
-    traffic, traffic_note = profiled_traffic(args.workload, R)
-    roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": achieved / alu_peak, "traffic": traffic,
-                "peak_kind": f"derived: 148 SMs x 128 FP32 lanes x 2 flops (FMA) x {sm_mhz:.0f} MHz",
-                "kernel": kernel_name(launch),
-                "kernel_ms": fused_ms, "algorithmic_flops": alg_flops, "traffic_source": traffic_note,
-                "node_visits_per_s": nodes * R / (fused_ms / 1000.0),
-                "hbm": {"algorithmic_bytes": alg_bytes, "achieved_gbs": alg_bytes / (fused_ms / 1000.0) / 1e9,
-                        "peak_gbs": peaks["hbm_gbs"], "frac": alg_bytes / (fused_ms / 1000.0) / 1e9 / peaks["hbm_gbs"],
-                        "peak_kind": peak_kind}}
+    roofline = fused_roofline(info, inst, R, nodes, fused_ms, launch, args.workload, peaks, peak_kind,
+                              torch.cuda.get_device_properties(dev).multi_processor_count)
 
     # plain (unfused) form of the same forward+adjoint, for comparison
     plain = None
@@ -443,7 +609,7 @@ def our_arm(args):
     # and all stop at the first stage where some replica verified SAT.
     tts = None
     share = None
-    if ws > 1:
+    if ws > 1 and args.tts_protocol == "first":
         from paper_2603_22877_b300 import max_over_replicas
         share = max_over_replicas("cuda" if torch.distributed.get_backend() == "nccl" else "cpu")
     if args.tts > 0:
@@ -467,7 +633,8 @@ def our_arm(args):
                     log.close()
                 solved = res["sat"] or res["stopped_by_peer"]   # by this replica or another
                 rec = {"sat": solved, "seconds": res["seconds"], "stage": res["stages_run"] if solved else None,
-                       "restart": res["restart"], "stages_run": res["stages_run"], "best_unsat": res["best_unsat"]}
+                       "restart": res["restart"], "stages_run": res["stages_run"], "best_unsat": res["best_unsat"],
+                       "rejected_candidates": res["rejected_candidates"], "seed": s}
                 if ws > 1:
                     rec["found_here"] = res["sat"]
                 if solved:
@@ -475,19 +642,25 @@ def our_arm(args):
                 runs.append(rec)
                 del S2
                 torch.cuda.empty_cache()
-            par2 = [r["seconds"] if r["sat"] else 2 * args.tts for r in runs]
-            tts[form] = {"median_s_par2": float(np.median(par2)), "solved": sum(r["sat"] for r in runs),
-                         "seeds": len(runs), "runs": runs}
-        if "plain" in tts and tts["fused"]["runs"][0]["sat"] and tts["plain"]["runs"][0]["sat"]:
-            # same initial points, same schedule: the batched fused form against the plain one
-            tts["plain_over_fused_seed0"] = tts["plain"]["runs"][0]["seconds"] / tts["fused"]["runs"][0]["seconds"]
+            from paper_2603_22877_b300 import gather_replicas, replica_median
+            if ws > 1 and args.tts_protocol == "median":   # every replica's runs, for the median over all
+                runs = [dict(r, rank=k) for k, rr in enumerate(gather_replicas(runs)) for r in rr]
+            tts[form] = {"median_s_par2": replica_median(runs, args.tts), "solved": sum(r["sat"] for r in runs),
+                         "seeds": len(runs), "runs": runs,
+                         "protocol": args.tts_protocol if ws > 1 else "median over seeds"}
+        if "plain" in tts:
+            # same initial points, same schedule: the batched fused form against the plain one,
+            # as the ratio of the PAR-2 medians over the (replica, seed) runs both forms made
+            par2 = {f: {(r.get("rank", 0), r["seed"]): (r["seconds"] if r["sat"] else 2 * args.tts)
+                        for r in tts[f]["runs"]} for f in ("fused", "plain")}
+            both = sorted(set(par2["fused"]) & set(par2["plain"]))
+            tts["plain_over_fused_median"] = float(np.median([par2["plain"][k] for k in both]) /
+                                                   np.median([par2["fused"][k] for k in both]))
+            tts["plain_over_fused_per_seed"] = [par2["plain"][k] / par2["fused"][k] for k in both]
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:  # the host baseline runs at N = 1 only
-        rate, k, v, dt = oracle_sample_rate(inst, R, a0, b0, np.ones((inst.n_cons, R), np.float32), sigma, 15.0)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"first {k} constraints of C_sigma x {R} restarts, FP64 numpy forward+adjoint, "
-                         f"{dt:.1f} s on the host"}
+        cpu = cpu_baseline(inst, R, a0, b0, sigma)
     # per stage: parameters, stage start, weight sums; per iteration: iteration
     # start, fused forward+adjoint, one PGD kernel per variable class, convergence
     # test; then round + check: over the chunks for C_sigma, one warp per constraint

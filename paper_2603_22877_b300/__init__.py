@@ -7,7 +7,8 @@ arguments; importing it does not touch the GPU, and every device entry point
 fails loudly if the library is missing.
 """
 from ._lib import FsmtError, load  # noqa: F401
-from .engine import Compiled, Problem, Solver, jsonl_log, max_over_replicas, relaxed_objective  # noqa: F401
+from .engine import (Compiled, Problem, Solver, gather_replicas, jsonl_log, max_over_replicas,  # noqa: F401
+                     relaxed_objective, replica_median)
 
 __all__ = ["FsmtError", "load", "Problem", "Compiled", "Solver", "jsonl_log", "max_over_replicas",
-           "relaxed_objective"]
+           "gather_replicas", "replica_median", "relaxed_objective"]

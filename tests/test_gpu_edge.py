@@ -189,7 +189,8 @@ def test_round_check_filter_keeps_boundary_cases_exact(policy):
 
 @pytest.mark.parametrize("make,R", [(lambda: W.large_scheduling(1005, 16, 30, 6, 4, 5), 70),
                                     (lambda: mixed_instance(False), 33),
-                                    (lambda: W.placement2d(1003, 20), 40)])  # 7-node diagrams: odd row counts
+                                    (lambda: W.placement2d(1003, 20), 40),   # 7-node diagrams: odd row counts
+                                    (lambda: W.random_hybrid(1006, 300), 24)])  # diagrams of up to 650 nodes
 def test_every_launch_configuration_and_the_autotuner(make, R):
     """Each kernel configuration the library offers for an instance (kernel
     variant, restarts per lane, staged reals) agrees with the oracle; the

@@ -132,18 +132,23 @@ def test_autograd_function_and_finite_differences():
         assert np.abs(fd_ref - gb_ref[j]).max() <= 1e-2 * np.abs(gb_ref[j]).max() + 1e-6
 
 
-@pytest.mark.parametrize("n,R,forms", [(100, 40, ("fused", "plain")), (300, 24, ("plain",))])
+@pytest.mark.parametrize("n,R,forms", [(100, 40, ("fused", "plain")), (300, 24, ("fused", "plain")),
+                                       (1000, 100, ("fused",))])
 def test_random_hybrid_against_oracle(n, R, forms):
     """The random hybrid benchmark (cardinality, NAE and parity constraints of up
     to 50 literals over Booleans and atoms; diagrams of up to 650 nodes) at the
     gradient-time grid's extremes and between: sigma = 0 (exact), 1/sigma = 0.5,
-    1/sigma = 0 (every atom a fair coin).  Instances whose diagrams fit no fused
-    kernel run in the plain form."""
+    1/sigma = 0 (every atom a fair coin).  At n = 300 and 1,000 the fused form is
+    the chunked kernel that the gradient-time experiment times there (650-node
+    diagrams through its generic pass, up to 128 staged reals); n = 1,000 at
+    R = 100 is that experiment's own group size."""
     import math
     inst = W.random_hybrid(1006, n)
     P, comp, a, b, w = setup(inst, R)
     if "fused" in forms:
         assert comp.info["fused_ok"] or comp.info["n_chunks"] > 0
+    if n >= 300:
+        assert comp.info["n_chunks"] > 0 and comp.info["max_nodes"] > 48   # the chunked kernel, generic pass
     D = OBJ.Diagrams(inst)
     oc = OBJ.objective_constraints(inst)
     for sigma in (0.0, 2.0, math.inf):
