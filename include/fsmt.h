@@ -168,7 +168,9 @@ fsmt_status fsmt_verify_exact(const fsmt_problem* p, const int8_t* x, const doub
  * multi-variable ones become half-spaces of the projection (Prop. QP).  The
  * problem may be freed afterwards.  EINVAL if a diagram has more than 65,533
  * decision nodes, the total exceeds 2^31 - 1 nodes, or a block of reals coupled
- * by half-spaces has more than 32 reals or 64 half-spaces. */
+ * by half-spaces needs more than one CTA's shared memory in the projection:
+ * 4 * ((2 nv + nh) * 32 + (nh + 1) + 2 nnz + 2 nh + 2 nv) bytes > 225 KB for a block of
+ * nv reals, nh half-spaces and nnz nonzeros (a chain of some 500 reals fits). */
 fsmt_status fsmt_compile(const fsmt_problem* p, int32_t unit_policy, fsmt_compiled** out);
 
 fsmt_status fsmt_compiled_info(const fsmt_compiled* c, fsmt_info* out);

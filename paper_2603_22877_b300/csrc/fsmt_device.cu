@@ -382,23 +382,27 @@ __global__ void k_pgd_free(DevView d, int R, float eta, float bscale, const floa
 }
 
 // Dykstra's alternating projections on one block of coupled reals, one thread
-// per (block, restart); the block's reals and the half-space increments stay in
-// thread-local arrays.  Per sweep: every half-space in constraint order, then
-// the box.  Then up to `polish` passes: each half-space q.y <= q0 whose value is
-// above -margin, margin = 2^-16 (|q0| + sum |q_j y_j|) (far above the FP32
-// rounding of q.y), is projected onto q.y <= q0 - 2 margin along the reals not
-// pinned at the bound the step would cross, then the box is clamped; the thread
-// stops at the first pass that moves nothing, so the point it returns satisfies
-// every half-space exactly whenever the passes settle.
-// The iterate, Dykstra's box corrections and half-space multipliers of each
-// (block, restart) live in shared memory, one column per thread ([var][thread]:
-// conflict-free), sized by the instance's largest block.
+// per (block, restart); a warp serves one block for 32 restarts.  Per sweep:
+// every half-space in constraint order, then the box.  Then up to `polish`
+// passes: each half-space q.y <= q0 whose value is above -margin, margin = 2^-16
+// (|q0| + sum |q_j y_j|) (far above the FP32 rounding of q.y), is projected onto
+// q.y <= q0 - 2 margin along the reals not pinned at the bound the step would
+// cross, then the box is clamped; the thread stops at the first pass that moves
+// nothing, so the point it returns satisfies every half-space exactly whenever
+// the passes settle.
+// Shared memory: the iterate, Dykstra's box corrections and half-space
+// multipliers of each (block, restart), one column per thread ([var][thread]:
+// conflict-free), sized by the instance's largest block; and per warp the block
+// itself (half-space offsets, local reals, coefficients, right-hand sides,
+// 1/||q||^2, the box), staged once by the warp's lanes together so that the
+// sweeps read it by broadcast instead of through dependent global loads.
 __global__ void k_pgd_comp(DevView d, int R, float eta, float bscale, int sweeps, int polish, const float* prm,
                            const float* __restrict__ wsum, float* __restrict__ b, float* __restrict__ gb,
                            float* __restrict__ gn2, const uint8_t* __restrict__ active, int clear_grad,
-                           const int* ctl, int maxv, int maxh) {
+                           const int* ctl, int maxv, int maxh, int maxnz) {
   if (ctl && ctl[0] == 0) return;
-  const int r = blockIdx.x * 32 + threadIdx.x;
+  const int lane = threadIdx.x;
+  const int r = blockIdx.x * 32 + lane;
   const bool ok = r < R;
   const bool act = ok && (!active || active[r] == 1);
   eta = restart_eta(d, eta, prm, wsum, r, ok);
@@ -409,96 +413,115 @@ __global__ void k_pgd_comp(DevView d, int R, float eta, float bscale, int sweeps
   }
   const float step = eta * bscale * bscale, inv = 1.f / (bscale * eta);
   float part = 0.f;
-  if (ok) {
-    extern __shared__ float s_col[];
-    const int T = blockDim.x * blockDim.y, tid = threadIdx.y * blockDim.x + threadIdx.x;
-    float* xs = s_col + tid;           // x(t) at xs[t * T]
-    float* ps = xs + maxv * T;         // pbox(t)
-    float* hs = ps + maxv * T;         // th(q)
+  extern __shared__ float s_col[];
+  const int T = blockDim.x * blockDim.y, tid = threadIdx.y * blockDim.x + lane;
+  float* xs = s_col + tid;           // x(t) at xs[t * T]
+  float* ps = xs + maxv * T;         // pbox(t)
+  float* hs = ps + maxv * T;         // th(q)
+  // the warp's staged block
+  const int wwords = (maxh + 1) + 2 * maxnz + 2 * maxh + 2 * maxv;
+  int* s_hp = reinterpret_cast<int*>(s_col + (2 * maxv + maxh) * T) + threadIdx.y * wwords;  // offsets [nh + 1]
+  int* s_lv = s_hp + maxh + 1;                                   // local real of each term
+  float* s_cf = reinterpret_cast<float*>(s_lv + maxnz);          // coefficient of each term
+  float* s_q0 = s_cf + maxnz;                                    // right-hand sides
+  float* s_iq = s_q0 + maxh;                                     // 1 / ||q||^2
+  float* s_lo = s_iq + maxh;                                     // the box of each local real
+  float* s_hi = s_lo + maxv;
 #define x(t) xs[(t) * T]
 #define pbox(t) ps[(t) * T]
 #define th(q) hs[(q) * T]
-    for (int c = blockIdx.y * blockDim.y + threadIdx.y; c < d.n_comp; c += gridDim.y * blockDim.y) {
-      const int v0 = d.comp_var_ptr[c], nv = d.comp_var_ptr[c + 1] - v0;
-      const int h0 = d.comp_hs_ptr[c], nh = d.comp_hs_ptr[c + 1] - h0;
+  for (int c = blockIdx.y * blockDim.y + threadIdx.y; c < d.n_comp; c += gridDim.y * blockDim.y) {
+    const int v0 = d.comp_var_ptr[c], nv = d.comp_var_ptr[c + 1] - v0;
+    const int h0 = d.comp_hs_ptr[c], nh = d.comp_hs_ptr[c + 1] - h0;
+    const int e_base = d.hs_ptr[h0], nz = d.hs_ptr[h0 + nh] - e_base;
+    __syncwarp();  // the previous block's reads are done
+    for (int i = lane; i <= nh; i += 32) s_hp[i] = d.hs_ptr[h0 + i] - e_base;
+    for (int i = lane; i < nz; i += 32) {
+      s_lv[i] = d.hs_lvar[e_base + i];
+      s_cf[i] = d.hs_coef[e_base + i];
+    }
+    for (int i = lane; i < nh; i += 32) {
+      s_q0[i] = d.hs_q0[h0 + i];
+      s_iq[i] = d.hs_inv_qq[h0 + i];
+    }
+    for (int i = lane; i < nv; i += 32) {
+      const int j = d.comp_var[v0 + i];
+      s_lo[i] = d.lo[j];
+      s_hi[i] = d.hi[j];
+    }
+    __syncwarp();
+    if (!ok) continue;
+    for (int t = 0; t < nv; ++t) {
+      const size_t k = (size_t)d.comp_var[v0 + t] * R + r;
+      x(t) = b[k] - step * gb[k];
+      pbox(t) = 0.f;
+      if (clear_grad) gb[k] = 0.f;
+    }
+    for (int q = 0; q < nh; ++q) th(q) = 0.f;
+    for (int sw = 0; sw < sweeps; ++sw) {
+      for (int q = 0; q < nh; ++q) {
+        const int e0 = s_hp[q], e1 = s_hp[q + 1];
+        const float thq = th(q);
+        float dot = -s_q0[q];
+        for (int e = e0; e < e1; ++e) {
+          const float cf = s_cf[e];
+          dot = fmaf(cf, x(s_lv[e]) + thq * cf, dot);
+        }
+        const float tn = fmaxf(dot, 0.f) * s_iq[q];
+        const float delta = thq - tn;
+        for (int e = e0; e < e1; ++e) x(s_lv[e]) = fmaf(delta, s_cf[e], x(s_lv[e]));
+        th(q) = tn;
+      }
       for (int t = 0; t < nv; ++t) {
-        const size_t k = (size_t)d.comp_var[v0 + t] * R + r;
-        x(t) = b[k] - step * gb[k];
-        pbox(t) = 0.f;
-        if (clear_grad) gb[k] = 0.f;
+        const float yv = x(t) + pbox(t);
+        const float xn = fminf(fmaxf(yv, s_lo[t]), s_hi[t]);
+        pbox(t) = yv - xn;
+        x(t) = xn;
       }
-      for (int q = 0; q < nh; ++q) th(q) = 0.f;
-      for (int sw = 0; sw < sweeps; ++sw) {
-        for (int q = 0; q < nh; ++q) {
-          const int e0 = d.hs_ptr[h0 + q], e1 = d.hs_ptr[h0 + q + 1];
-          float dot = -d.hs_q0[h0 + q];
+    }
+    if (sweeps == 0)
+      for (int t = 0; t < nv; ++t) x(t) = fminf(fmaxf(x(t), s_lo[t]), s_hi[t]);
+    for (int pass = 0; pass < polish; ++pass) {
+      bool moved = false;
+      for (int q = 0; q < nh; ++q) {
+        const int e0 = s_hp[q], e1 = s_hp[q + 1];
+        const float q0 = s_q0[q];
+        float v = -q0, mag = fabsf(q0);
+        for (int e = e0; e < e1; ++e) {
+          const float term = s_cf[e] * x(s_lv[e]);
+          v += term;
+          mag += fabsf(term);
+        }
+        const float margin = kPolishMargin * mag;
+        if (v > -margin) {
+          // move along the reals that are not pinned at the bound the step would cross
+          float qq = 0.f;
           for (int e = e0; e < e1; ++e) {
-            const float cf = d.hs_coef[e];
-            dot = fmaf(cf, x(d.hs_lvar[e]) + th(q) * cf, dot);
+            const float cf = s_cf[e];
+            const int t = s_lv[e];
+            const bool pinned = (cf > 0.f && x(t) <= s_lo[t]) || (cf < 0.f && x(t) >= s_hi[t]);
+            if (!pinned) qq = fmaf(cf, cf, qq);
           }
-          const float tn = fmaxf(dot, 0.f) * d.hs_inv_qq[h0 + q];
-          const float delta = th(q) - tn;
-          for (int e = e0; e < e1; ++e) x(d.hs_lvar[e]) = fmaf(delta, d.hs_coef[e], x(d.hs_lvar[e]));
-          th(q) = tn;
-        }
-        for (int t = 0; t < nv; ++t) {
-          const int j = d.comp_var[v0 + t];
-          const float yv = x(t) + pbox(t);
-          const float xn = fminf(fmaxf(yv, d.lo[j]), d.hi[j]);
-          pbox(t) = yv - xn;
-          x(t) = xn;
-        }
-      }
-      if (sweeps == 0)
-        for (int t = 0; t < nv; ++t) {
-          const int j = d.comp_var[v0 + t];
-          x(t) = fminf(fmaxf(x(t), d.lo[j]), d.hi[j]);
-        }
-      for (int pass = 0; pass < polish; ++pass) {
-        bool moved = false;
-        for (int q = 0; q < nh; ++q) {
-          const int e0 = d.hs_ptr[h0 + q], e1 = d.hs_ptr[h0 + q + 1];
-          const float q0 = d.hs_q0[h0 + q];
-          float v = -q0, mag = fabsf(q0);
-          for (int e = e0; e < e1; ++e) {
-            const float term = d.hs_coef[e] * x(d.hs_lvar[e]);
-            v += term;
-            mag += fabsf(term);
-          }
-          const float margin = kPolishMargin * mag;
-          if (v > -margin) {
-            // move along the reals that are not pinned at the bound the step would cross
-            float qq = 0.f;
+          if (qq > 0.f) {
+            const float tq = (v + 2.f * margin) / qq;
             for (int e = e0; e < e1; ++e) {
-              const float cf = d.hs_coef[e];
-              const int t = d.hs_lvar[e], j = d.comp_var[v0 + t];
-              const bool pinned = (cf > 0.f && x(t) <= d.lo[j]) || (cf < 0.f && x(t) >= d.hi[j]);
-              if (!pinned) qq = fmaf(cf, cf, qq);
+              const float cf = s_cf[e];
+              const int t = s_lv[e];
+              const bool pinned = (cf > 0.f && x(t) <= s_lo[t]) || (cf < 0.f && x(t) >= s_hi[t]);
+              if (!pinned) x(t) = fmaf(-tq, cf, x(t));
             }
-            if (qq > 0.f) {
-              const float tq = (v + 2.f * margin) / qq;
-              for (int e = e0; e < e1; ++e) {
-                const float cf = d.hs_coef[e];
-                const int t = d.hs_lvar[e], j = d.comp_var[v0 + t];
-                const bool pinned = (cf > 0.f && x(t) <= d.lo[j]) || (cf < 0.f && x(t) >= d.hi[j]);
-                if (!pinned) x(t) = fmaf(-tq, cf, x(t));
-              }
-              moved = true;
-            }
+            moved = true;
           }
         }
-        for (int t = 0; t < nv; ++t) {
-          const int j = d.comp_var[v0 + t];
-          x(t) = fminf(fmaxf(x(t), d.lo[j]), d.hi[j]);
-        }
-        if (!moved) break;
       }
-      for (int t = 0; t < nv; ++t) {
-        const size_t k = (size_t)d.comp_var[v0 + t] * R + r;
-        const float q = (b[k] - x(t)) * inv;  // b still holds the step's starting point
-        part = fmaf(q, q, part);
-        if (act) b[k] = x(t);
-      }
+      for (int t = 0; t < nv; ++t) x(t) = fminf(fmaxf(x(t), s_lo[t]), s_hi[t]);
+      if (!moved) break;
+    }
+    for (int t = 0; t < nv; ++t) {
+      const size_t k = (size_t)d.comp_var[v0 + t] * R + r;
+      const float q = (b[k] - x(t)) * inv;  // b still holds the step's starting point
+      part = fmaf(q, q, part);
+      if (act) b[k] = x(t);
     }
   }
 #undef x
@@ -1000,9 +1023,16 @@ fsmt_status launch_pgd(const Compiled& C, int R, float eta, float bscale, int sw
                                                                            gn2, active, clear, ctl);
   const int ncomp = (int)C.comp_var_ptr.size() - 1;
   if (ncomp > 0) {
-    const size_t smem = (size_t)(2 * C.comp_max_vars + C.comp_max_hs) * blk.x * blk.y * sizeof(float);
-    k_pgd_comp<<<dim3(tiles, rows(ncomp)), blk, smem, st>>>(C.view, R, eta, bscale, sweeps, polish, prm, wsum, b, gb,
-                                                             gn2, active, clear, ctl, C.comp_max_vars, C.comp_max_hs);
+    // as many warps per CTA (at most 8) as the largest block's shared memory allows
+    auto words = [&](int wy) { return (size_t)proj_block_words(C.comp_max_vars, C.comp_max_hs, C.comp_max_nnz, wy); };
+    int wy = 8;
+    while (wy > 1 && words(wy) > (size_t)kProjSmemWords) wy /= 2;
+    const dim3 cblk(32, wy);
+    const long cap = std::max<long>(1, 4L * sm_count() * 8 / tiles);
+    const int gy = (int)std::max<long>(1, std::min<long>(std::min<long>((ncomp + wy - 1) / wy, cap), 65535L));
+    k_pgd_comp<<<dim3(tiles, gy), cblk, words(wy) * sizeof(float), st>>>(
+        C.view, R, eta, bscale, sweeps, polish, prm, wsum, b, gb, gn2, active, clear, ctl, C.comp_max_vars,
+        C.comp_max_hs, C.comp_max_nnz);
   }
   FSMT_CUDA(cudaGetLastError(), "pgd kernel launch");
   return FSMT_OK;
@@ -1167,9 +1197,9 @@ fsmt_status fsmt_upload(fsmt_compiled* cc, void* stream) {
             "smem attribute");
   FSMT_CUDA(cudaFuncSetAttribute(k_round_check, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024),
             "smem attribute");
-  // the largest block (32 reals, 64 half-spaces) needs (2 * 32 + 64) * 256 floats = 128 KB
+  // the block columns and the staged blocks (launch_pgd narrows the CTA when they need more)
   FSMT_CUDA(cudaFuncSetAttribute(k_pgd_comp, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (2 * kMaxCompVars + kMaxCompHalfspaces) * 256 * (int)sizeof(float)),
+                                 (int)(kProjSmemWords * sizeof(float))),
             "smem attribute");
   FSMT_CUDA(cudaFuncSetAttribute(k_check_chunked, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024),
             "smem attribute");

@@ -26,8 +26,15 @@ typedef signed char int8_t;
 namespace fsmt {
 
 constexpr int kMaxNodesPerDiagram = 65533;  // hi/lo are 16-bit and V, V+1 are the terminals
-constexpr int kMaxCompVars = 32;            // reals per block coupled by half-spaces
-constexpr int kMaxCompHalfspaces = 64;      // half-spaces per block
+// Shared memory (4-byte words) of the projection kernel for blocks of coupled reals of
+// at most nv reals, nh half-spaces and nnz nonzeros over a block's half-spaces, wy
+// warps per CTA: per thread the block's iterate, box corrections and half-space
+// multipliers; per warp the staged block (offsets, local reals, coefficients,
+// right-hand sides, 1/||q||^2, the box).  A block is accepted when one warp's CTA fits.
+FSMT_HD long proj_block_words(long nv, long nh, long nnz, long wy) {
+  return (2 * nv + nh) * 32 * wy + wy * ((nh + 1) + 2 * nnz + 2 * nh + 2 * nv);
+}
+constexpr long kProjSmemWords = (227 * 1024 - 2048) / 4;  // a CTA's dynamic shared memory, 2 KB left for static
 // chunks of the chunked forward/adjoint kernel
 constexpr int kChunkMaxCons = 64;    // constraints per chunk
 constexpr int kChunkMaxNodes = 2048; // decision nodes per chunk

@@ -707,10 +707,14 @@ static fsmt_status compile(const Problem& P, int policy, Compiled& C) {
   C.hs_coef.clear();
   C.hs_q0.clear();
   C.hs_inv_qq.clear();
-  C.comp_max_vars = C.comp_max_hs = 0;
+  C.comp_max_vars = C.comp_max_hs = C.comp_max_nnz = 0;
   for (size_t k = 0; k < comp_vars.size(); ++k) {
-    if ((int)comp_vars[k].size() > kMaxCompVars || (int)comp_hs[k].size() > kMaxCompHalfspaces)
-      return fail(FSMT_EINVAL, "a block of reals coupled by unit atoms has more than 32 reals or 64 half-spaces");
+    long nnz = 0;
+    for (int x : comp_hs[k]) nnz += (long)hs[x].var.size();
+    if (proj_block_words((long)comp_vars[k].size(), (long)comp_hs[k].size(), nnz, 1) > kProjSmemWords)
+      return fail(FSMT_EINVAL, "a block of reals coupled by unit atoms (" + std::to_string(comp_vars[k].size()) +
+                                   " reals, " + std::to_string(comp_hs[k].size()) + " half-spaces, " +
+                                   std::to_string(nnz) + " nonzeros) exceeds the projection kernel's shared memory");
     C.comp_max_vars = std::max<int32_t>(C.comp_max_vars, (int32_t)comp_vars[k].size());
     C.comp_max_hs = std::max<int32_t>(C.comp_max_hs, (int32_t)comp_hs[k].size());
     std::unordered_map<int, int> local;
@@ -732,6 +736,7 @@ static fsmt_status compile(const Problem& P, int policy, Compiled& C) {
       C.hs_inv_qq.push_back((float)(1.0 / qq));
     }
     C.comp_hs_ptr.push_back((int32_t)(C.hs_ptr.size() - 1));
+    C.comp_max_nnz = std::max<int32_t>(C.comp_max_nnz, C.hs_ptr.back() - C.hs_ptr[C.comp_hs_ptr[C.comp_hs_ptr.size() - 2]]);
   }
   return FSMT_OK;
 }

@@ -59,6 +59,7 @@ struct Compiled {
   std::vector<int32_t> comp_var_ptr{0}, comp_var, comp_hs_ptr{0}, hs_ptr{0}, hs_lvar;
   std::vector<float> hs_coef, hs_q0, hs_inv_qq;
   int32_t comp_max_vars = 0, comp_max_hs = 0;  // the largest block's reals and half-spaces
+  int32_t comp_max_nnz = 0;  // the most nonzeros over one block's half-spaces
   int32_t empty_boxes = 0;  // reals with lo > hi after unit-atom tightening (no FP32 point)
   // chunked schedule of C_sigma (see build_chunks in fsmt_host.cpp)
   bool chunked_ok = false;

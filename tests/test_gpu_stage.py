@@ -12,7 +12,9 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("make,R", [(lambda: W.jobshop(1002, 10, 5), 70), (lambda: W.tiny_random(1001), 45),
-                                    (lambda: W.large_scheduling(1005, 16, 30, 6, 4, 5), 40)])
+                                    (lambda: W.large_scheduling(1005, 16, 30, 6, 4, 5), 40),
+                                    # two jobs through 100 machines: blocks of 100 coupled reals
+                                    (lambda: W.jobshop(1002, 2, 100), 64)])
 def test_pgd_step_parity(make, R):
     import torch
     inst = make()

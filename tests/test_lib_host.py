@@ -340,34 +340,28 @@ def test_projection_blocks_match_the_coupling_graph(seed):
 
 
 def test_projection_block_limits():
-    """A block of 33 coupled reals (a chain of unit atoms) exceeds the projection's
-    per-block limit of 32 reals: compile refuses it with EINVAL under PROJECT, and SOFT
-    (no projection) accepts it; 32 reals, and 64 half-spaces in one block, are accepted,
-    65 half-spaces are not."""
-    Bd = W._Builder(0, 33)
-    for j in range(32):
-        Bd.con(W.OR, [W.lit(Bd.atom([j, j + 1], [1, -1], 0, W.LE))])
-    inst = Bd.freeze("chain", np.zeros(33), np.ones(33), [], np.zeros(33), 1.0)
-    P = Problem.from_instance(inst)
+    """A block of reals coupled by unit atoms is accepted while one warp's CTA of the
+    projection kernel holds it in shared memory: per thread the block's iterate, box
+    corrections and multipliers, 4 (2 nv + nh) 32 bytes, plus the staged block, within
+    225 KB (227 KB less the kernel's static shared memory).  A chain of 500 reals (499 half-spaces) fits, one of 600 does not (EINVAL
+    under PROJECT; SOFT, with no projection, accepts it); 65 half-spaces over 4 reals fit."""
+    def chain(n):
+        Bd = W._Builder(0, n)
+        for j in range(n - 1):
+            Bd.con(W.OR, [W.lit(Bd.atom([j, j + 1], [1, -1], 0, W.LE))])
+        return Problem.from_instance(Bd.freeze("chain", np.zeros(n), np.ones(n), [], np.zeros(n), 1.0))
+    for n in (33, 100, 500):
+        assert chain(n).compile(L.UNIT_PROJECT).info["n_components"] == 1
+    P = chain(600)
     with pytest.raises(L.FsmtError) as e:
         P.compile(L.UNIT_PROJECT)
-    assert e.value.status == L.EINVAL
+    assert e.value.status == L.EINVAL and "shared memory" in str(e.value)
     P.compile(L.UNIT_SOFT)
-    Bd = W._Builder(0, 32)                                # 32 reals: accepted
-    for j in range(31):
-        Bd.con(W.OR, [W.lit(Bd.atom([j, j + 1], [1, -1], 0, W.LE))])
-    ok = Problem.from_instance(Bd.freeze("chain32", np.zeros(32), np.ones(32), [], np.zeros(32), 1.0))
-    assert ok.compile(L.UNIT_PROJECT).info["n_components"] == 1
-    for n_hs, fails in ((64, False), (65, True)):         # half-spaces per block: at most 64
-        Bd = W._Builder(0, 4)
-        for t in range(n_hs):
-            Bd.con(W.OR, [W.lit(Bd.atom([t % 4, (t + 1) % 4], [1, -1], t, W.LE))])
-        P = Problem.from_instance(Bd.freeze("hs", np.zeros(4), np.ones(4), [], np.zeros(4), 1.0))
-        if fails:
-            with pytest.raises(L.FsmtError):
-                P.compile(L.UNIT_PROJECT)
-        else:
-            assert P.compile(L.UNIT_PROJECT).info["n_halfspaces"] == n_hs
+    Bd = W._Builder(0, 4)
+    for t in range(65):
+        Bd.con(W.OR, [W.lit(Bd.atom([t % 4, (t + 1) % 4], [1, -1], t, W.LE))])
+    P = Problem.from_instance(Bd.freeze("hs", np.zeros(4), np.ones(4), [], np.zeros(4), 1.0))
+    assert P.compile(L.UNIT_PROJECT).info["n_halfspaces"] == 65
 
 
 def test_diagram_size_limit():
