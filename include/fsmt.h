@@ -83,6 +83,8 @@ typedef struct {
   int32_t empty_boxes;   /* reals whose FP32 box is empty after unit-atom tightening (lo > hi): their
                             unit atoms admit no FP32 value (contradictory, or pinning the real to a
                             value FP32 cannot represent), so no restart can pass the exact check */
+  int32_t proj_shapes;   /* shapes of blocks of coupled reals given run-time generated projection routines at
+                            fsmt_upload (0: none; the generic projection loop serves every block) */
 } fsmt_info;
 
 /* One way to run the forward (+ adjoint) pass of C_sigma on an instance at R

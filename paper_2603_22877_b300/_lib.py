@@ -27,7 +27,8 @@ class Info(C.Structure):
                 ("n_obj_cons", C.c_int32), ("n_nodes", C.c_int64), ("n_obj_nodes", C.c_int64),
                 ("max_nodes", C.c_int32), ("n_halfspaces", C.c_int32), ("n_components", C.c_int32),
                 ("n_free_reals", C.c_int32), ("atom_nnz", C.c_int64), ("fused_ok", C.c_int32),
-                ("n_chunks", C.c_int32), ("jit_shapes", C.c_int32), ("empty_boxes", C.c_int32)]
+                ("n_chunks", C.c_int32), ("jit_shapes", C.c_int32), ("empty_boxes", C.c_int32),
+                ("proj_shapes", C.c_int32)]
 
 
 class State(C.Structure):

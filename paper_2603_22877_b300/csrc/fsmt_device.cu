@@ -15,6 +15,7 @@
 
 #include "fsmt_internal.h"
 #include "fsmt_chunked.cuh"
+#include "fsmt_proj.cuh"
 
 int fsmt_fused_limit_ok(const fsmt::Compiled& C);  // below
 
@@ -32,7 +33,6 @@ inline size_t chunk_fixed_bytes(int rpl, int slot_cap) {
 }
 constexpr size_t kSmemMax = 227 * 1024;
 
-constexpr float kPolishMargin = 1.52587890625e-05f;  // 2^-16
 
 fsmt_status cuda_fail(cudaError_t e, const char* what) {
   set_error(std::string(what) + ": " + cudaGetErrorString(e));
@@ -307,27 +307,7 @@ __global__ void k_adj_plain(DevView d, int R, const float* __restrict__ w, const
 // With wsum (per-restart total weight of C_sigma) the step of restart r is
 // eta * n_obj / wsum[r] (Thm. max_step: eta = 1/L with L proportional to the
 // total weight, Prop. Lipschitz).
-__device__ __forceinline__ void reduce_rows_add(float part, float* gn2, int r, bool ok) {
-  __shared__ float red[8][33];
-  red[threadIdx.y][threadIdx.x] = part;
-  __syncthreads();
-  if (threadIdx.y == 0) {
-    float s = 0.f;
-    for (int y = 0; y < (int)blockDim.y; ++y) s += red[y][threadIdx.x];
-    if (ok && s != 0.f) atomicAdd(gn2 + r, s);
-  }
-}
-
-__device__ __forceinline__ float restart_eta(const DevView& d, float eta, const float* prm, const float* wsum,
-                                             int r, bool ok) {
-  eta = load_param(prm, P_ETA, eta);
-  if (prm && prm[P_NORM] == 0.f) wsum = nullptr;
-  if (wsum && ok && d.n_obj > 0) {
-    const float ws = wsum[r];
-    if (ws > 0.f) eta *= (float)d.n_obj / ws;
-  }
-  return eta;
-}
+// reduce_rows_add and restart_eta: fsmt_proj.cuh
 
 __global__ void k_pgd_bool(DevView d, int R, float eta, const float* prm, const float* __restrict__ wsum,
                            float* __restrict__ a, float* __restrict__ ga, float* __restrict__ gn2,
@@ -381,153 +361,13 @@ __global__ void k_pgd_free(DevView d, int R, float eta, float bscale, const floa
   reduce_rows_add(part, gn2, r, ok);
 }
 
-// Dykstra's alternating projections on one block of coupled reals, one thread
-// per (block, restart); a warp serves one block for 32 restarts.  Per sweep:
-// every half-space in constraint order, then the box.  Then up to `polish`
-// passes: each half-space q.y <= q0 whose value is above -margin, margin = 2^-16
-// (|q0| + sum |q_j y_j|) (far above the FP32 rounding of q.y), is projected onto
-// q.y <= q0 - 2 margin along the reals not pinned at the bound the step would
-// cross, then the box is clamped; the thread stops at the first pass that moves
-// nothing, so the point it returns satisfies every half-space exactly whenever
-// the passes settle.
-// Shared memory: the iterate, Dykstra's box corrections and half-space
-// multipliers of each (block, restart), one column per thread ([var][thread]:
-// conflict-free), sized by the instance's largest block; and per warp the block
-// itself (half-space offsets, local reals, coefficients, right-hand sides,
-// 1/||q||^2, the box), staged once by the warp's lanes together so that the
-// sweeps read it by broadcast instead of through dependent global loads.
+// The projection of the blocks of coupled reals (fsmt_proj.cuh), compiled ahead of
+// time: every block takes the generic loop.
 __global__ void k_pgd_comp(DevView d, int R, float eta, float bscale, int sweeps, int polish, const float* prm,
                            const float* __restrict__ wsum, float* __restrict__ b, float* __restrict__ gb,
                            float* __restrict__ gn2, const uint8_t* __restrict__ active, int clear_grad,
                            const int* ctl, int maxv, int maxh, int maxnz) {
-  if (ctl && ctl[0] == 0) return;
-  const int lane = threadIdx.x;
-  const int r = blockIdx.x * 32 + lane;
-  const bool ok = r < R;
-  const bool act = ok && (!active || active[r] == 1);
-  eta = restart_eta(d, eta, prm, wsum, r, ok);
-  bscale = load_param(prm, P_BSCALE, bscale);
-  if (prm) {
-    sweeps = (int)prm[P_SWEEPS];
-    polish = (int)prm[P_POLISH];
-  }
-  const float step = eta * bscale * bscale, inv = 1.f / (bscale * eta);
-  float part = 0.f;
-  extern __shared__ float s_col[];
-  const int T = blockDim.x * blockDim.y, tid = threadIdx.y * blockDim.x + lane;
-  float* xs = s_col + tid;           // x(t) at xs[t * T]
-  float* ps = xs + maxv * T;         // pbox(t)
-  float* hs = ps + maxv * T;         // th(q)
-  // the warp's staged block
-  const int wwords = (maxh + 1) + 2 * maxnz + 2 * maxh + 2 * maxv;
-  int* s_hp = reinterpret_cast<int*>(s_col + (2 * maxv + maxh) * T) + threadIdx.y * wwords;  // offsets [nh + 1]
-  int* s_lv = s_hp + maxh + 1;                                   // local real of each term
-  float* s_cf = reinterpret_cast<float*>(s_lv + maxnz);          // coefficient of each term
-  float* s_q0 = s_cf + maxnz;                                    // right-hand sides
-  float* s_iq = s_q0 + maxh;                                     // 1 / ||q||^2
-  float* s_lo = s_iq + maxh;                                     // the box of each local real
-  float* s_hi = s_lo + maxv;
-#define x(t) xs[(t) * T]
-#define pbox(t) ps[(t) * T]
-#define th(q) hs[(q) * T]
-  for (int c = blockIdx.y * blockDim.y + threadIdx.y; c < d.n_comp; c += gridDim.y * blockDim.y) {
-    const int v0 = d.comp_var_ptr[c], nv = d.comp_var_ptr[c + 1] - v0;
-    const int h0 = d.comp_hs_ptr[c], nh = d.comp_hs_ptr[c + 1] - h0;
-    const int e_base = d.hs_ptr[h0], nz = d.hs_ptr[h0 + nh] - e_base;
-    __syncwarp();  // the previous block's reads are done
-    for (int i = lane; i <= nh; i += 32) s_hp[i] = d.hs_ptr[h0 + i] - e_base;
-    for (int i = lane; i < nz; i += 32) {
-      s_lv[i] = d.hs_lvar[e_base + i];
-      s_cf[i] = d.hs_coef[e_base + i];
-    }
-    for (int i = lane; i < nh; i += 32) {
-      s_q0[i] = d.hs_q0[h0 + i];
-      s_iq[i] = d.hs_inv_qq[h0 + i];
-    }
-    for (int i = lane; i < nv; i += 32) {
-      const int j = d.comp_var[v0 + i];
-      s_lo[i] = d.lo[j];
-      s_hi[i] = d.hi[j];
-    }
-    __syncwarp();
-    if (!ok) continue;
-    for (int t = 0; t < nv; ++t) {
-      const size_t k = (size_t)d.comp_var[v0 + t] * R + r;
-      x(t) = b[k] - step * gb[k];
-      pbox(t) = 0.f;
-      if (clear_grad) gb[k] = 0.f;
-    }
-    for (int q = 0; q < nh; ++q) th(q) = 0.f;
-    for (int sw = 0; sw < sweeps; ++sw) {
-      for (int q = 0; q < nh; ++q) {
-        const int e0 = s_hp[q], e1 = s_hp[q + 1];
-        const float thq = th(q);
-        float dot = -s_q0[q];
-        for (int e = e0; e < e1; ++e) {
-          const float cf = s_cf[e];
-          dot = fmaf(cf, x(s_lv[e]) + thq * cf, dot);
-        }
-        const float tn = fmaxf(dot, 0.f) * s_iq[q];
-        const float delta = thq - tn;
-        for (int e = e0; e < e1; ++e) x(s_lv[e]) = fmaf(delta, s_cf[e], x(s_lv[e]));
-        th(q) = tn;
-      }
-      for (int t = 0; t < nv; ++t) {
-        const float yv = x(t) + pbox(t);
-        const float xn = fminf(fmaxf(yv, s_lo[t]), s_hi[t]);
-        pbox(t) = yv - xn;
-        x(t) = xn;
-      }
-    }
-    if (sweeps == 0)
-      for (int t = 0; t < nv; ++t) x(t) = fminf(fmaxf(x(t), s_lo[t]), s_hi[t]);
-    for (int pass = 0; pass < polish; ++pass) {
-      bool moved = false;
-      for (int q = 0; q < nh; ++q) {
-        const int e0 = s_hp[q], e1 = s_hp[q + 1];
-        const float q0 = s_q0[q];
-        float v = -q0, mag = fabsf(q0);
-        for (int e = e0; e < e1; ++e) {
-          const float term = s_cf[e] * x(s_lv[e]);
-          v += term;
-          mag += fabsf(term);
-        }
-        const float margin = kPolishMargin * mag;
-        if (v > -margin) {
-          // move along the reals that are not pinned at the bound the step would cross
-          float qq = 0.f;
-          for (int e = e0; e < e1; ++e) {
-            const float cf = s_cf[e];
-            const int t = s_lv[e];
-            const bool pinned = (cf > 0.f && x(t) <= s_lo[t]) || (cf < 0.f && x(t) >= s_hi[t]);
-            if (!pinned) qq = fmaf(cf, cf, qq);
-          }
-          if (qq > 0.f) {
-            const float tq = (v + 2.f * margin) / qq;
-            for (int e = e0; e < e1; ++e) {
-              const float cf = s_cf[e];
-              const int t = s_lv[e];
-              const bool pinned = (cf > 0.f && x(t) <= s_lo[t]) || (cf < 0.f && x(t) >= s_hi[t]);
-              if (!pinned) x(t) = fmaf(-tq, cf, x(t));
-            }
-            moved = true;
-          }
-        }
-      }
-      for (int t = 0; t < nv; ++t) x(t) = fminf(fmaxf(x(t), s_lo[t]), s_hi[t]);
-      if (!moved) break;
-    }
-    for (int t = 0; t < nv; ++t) {
-      const size_t k = (size_t)d.comp_var[v0 + t] * R + r;
-      const float q = (b[k] - x(t)) * inv;  // b still holds the step's starting point
-      part = fmaf(q, q, part);
-      if (act) b[k] = x(t);
-    }
-  }
-#undef x
-#undef pbox
-#undef th
-  reduce_rows_add(part, gn2, r, ok);
+  pgd_comp_body(d, R, eta, bscale, sweeps, polish, prm, wsum, b, gb, gn2, active, clear_grad, ctl, maxv, maxh, maxnz);
 }
 
 // wsum[r] += sum over the constraints of C_sigma of w[c][r] (caller zeroes wsum).
@@ -1030,9 +870,18 @@ fsmt_status launch_pgd(const Compiled& C, int R, float eta, float bscale, int sw
     const dim3 cblk(32, wy);
     const long cap = std::max<long>(1, 4L * sm_count() * 8 / tiles);
     const int gy = (int)std::max<long>(1, std::min<long>(std::min<long>((ncomp + wy - 1) / wy, cap), 65535L));
-    k_pgd_comp<<<dim3(tiles, gy), cblk, words(wy) * sizeof(float), st>>>(
-        C.view, R, eta, bscale, sweeps, polish, prm, wsum, b, gb, gn2, active, clear, ctl, C.comp_max_vars,
-        C.comp_max_hs, C.comp_max_nnz);
+    if (C.jit_proj) {  // generated routines for the frequent block shapes, the generic loop for the rest
+      DevView view = C.view;
+      int maxv = C.comp_max_vars, maxh = C.comp_max_hs, maxnz = C.comp_max_nnz;
+      void* args[] = {&view, &R, &eta, &bscale, &sweeps, &polish, (void*)&prm, (void*)&wsum, &b, &gb, &gn2,
+                      (void*)&active, &clear, (void*)&ctl, &maxv, &maxh, &maxnz};
+      FSMT_CUDA(cudaLaunchKernel((const void*)C.jit_proj, dim3(tiles, gy), cblk, args, words(wy) * sizeof(float), st),
+                "projection kernel launch");
+    } else {
+      k_pgd_comp<<<dim3(tiles, gy), cblk, words(wy) * sizeof(float), st>>>(
+          C.view, R, eta, bscale, sweeps, polish, prm, wsum, b, gb, gn2, active, clear, ctl, C.comp_max_vars,
+          C.comp_max_hs, C.comp_max_nnz);
+    }
   }
   FSMT_CUDA(cudaGetLastError(), "pgd kernel launch");
   return FSMT_OK;
@@ -1122,7 +971,7 @@ fsmt_status fsmt_upload(fsmt_compiled* cc, void* stream) {
                o_cv = push_array(blob, C.comp_var), o_chp = push_array(blob, C.comp_hs_ptr),
                o_hsp = push_array(blob, C.hs_ptr), o_hsl = push_array(blob, C.hs_lvar),
                o_hsc = push_array(blob, C.hs_coef), o_hsq = push_array(blob, C.hs_q0),
-               o_hsi = push_array(blob, C.hs_inv_qq);
+               o_hsi = push_array(blob, C.hs_inv_qq), o_csh = push_array(blob, C.comp_shape);
   std::vector<uint2> cnodes(C.cnode_slot.size());
   for (size_t i = 0; i < cnodes.size(); ++i) cnodes[i] = make_uint2(C.cnode_slot[i], C.cnode_hilo[i]);
   const size_t o_ccp = push_array(blob, C.chunk_con_ptr), o_ccon = push_array(blob, C.ccon),
@@ -1174,6 +1023,7 @@ fsmt_status fsmt_upload(fsmt_compiled* cc, void* stream) {
   v.hs_coef = (const float*)(base + o_hsc);
   v.hs_q0 = (const float*)(base + o_hsq);
   v.hs_inv_qq = (const float*)(base + o_hsi);
+  v.comp_shape = (const int32_t*)(base + o_csh);
   v.n_chunks = C.n_chunks;
   v.chunk_slot_cap = C.chunk_slot_cap;
   v.chunk_real_cap = 0;  // set per launch

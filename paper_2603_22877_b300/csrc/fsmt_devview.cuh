@@ -49,6 +49,10 @@ constexpr int kChunkMaxTerms = 768;  // nonzeros of the atoms of a chunk
 constexpr int kChunkMaxReals = 128;   // reals touched by a chunk's atoms
 constexpr int kMaxJitShapes = 16;      // diagram shapes given generated code per instance
 constexpr int kMaxJitShapeNodes = 48;  // largest diagram given generated code
+constexpr int kMaxProjShapes = 16;     // block shapes given generated projection routines per instance
+constexpr int kMaxProjShapeVars = 24;  // largest block given one: reals,
+constexpr int kMaxProjShapeHs = 32;    // half-spaces
+constexpr int kMaxProjShapeNnz = 96;   // and nonzeros
 
 // Everything the kernels read, as one POD passed by value.
 struct DevView {
@@ -79,6 +83,7 @@ struct DevView {
   const float* hs_coef;
   const float* hs_q0;
   const float* hs_inv_qq;       // 1 / ||q||^2
+  const int32_t* comp_shape;    // [n_comp] rank of the block's generated projection routine (0: none)
   // chunked schedule of the constraints of C_sigma
   int32_t n_chunks;
   int32_t chunk_slot_cap;         // most slots of any chunk: rows of the per-slot shared arrays

@@ -482,6 +482,57 @@ static bool build_chunks(const Problem& P, Compiled& C, int slot_limit) {
   return true;
 }
 
+// ------------------------------------------------ projection block shapes ---
+// A block's shape: its local real count, and per half-space (in constraint order)
+// the local reals and integer coefficients; the right-hand sides and the box are
+// data.  The most frequent shapes (at most kMaxProjShapes, each of at most
+// kMaxProjShapeVars reals, kMaxProjShapeHs half-spaces and kMaxProjShapeNnz
+// nonzeros) get run-time generated projection routines (fsmt_jit.cpp); every block
+// records its shape's 1-based rank, 0 for the generic path.
+static void select_proj_shapes(Compiled& C) {
+  const int ncomp = (int)C.comp_var_ptr.size() - 1;
+  C.comp_shape.assign(ncomp, 0);
+  C.proj_shape_comp.clear();
+  std::unordered_map<std::string, int> id_of;
+  std::vector<int> first_comp, count;
+  std::vector<int> sid(ncomp, -1);
+  std::string key;
+  for (int c = 0; c < ncomp; ++c) {
+    const int nv = C.comp_var_ptr[c + 1] - C.comp_var_ptr[c];
+    const int h0 = C.comp_hs_ptr[c], nh = C.comp_hs_ptr[c + 1] - h0;
+    const int nz = C.hs_ptr[h0 + nh] - C.hs_ptr[h0];
+    if (nv > kMaxProjShapeVars || nh > kMaxProjShapeHs || nz > kMaxProjShapeNnz) continue;
+    key.assign(reinterpret_cast<const char*>(&nv), sizeof(nv));
+    for (int q = h0; q < h0 + nh; ++q) {
+      const int32_t n = C.hs_ptr[q + 1] - C.hs_ptr[q];
+      key.append(reinterpret_cast<const char*>(&n), sizeof(n));
+      for (int e = C.hs_ptr[q]; e < C.hs_ptr[q + 1]; ++e) {
+        key.append(reinterpret_cast<const char*>(&C.hs_lvar[e]), sizeof(int32_t));
+        key.append(reinterpret_cast<const char*>(&C.hs_coef[e]), sizeof(float));
+      }
+    }
+    auto it = id_of.find(key);
+    if (it == id_of.end()) {
+      it = id_of.emplace(key, (int)first_comp.size()).first;
+      first_comp.push_back(c);
+      count.push_back(0);
+    }
+    sid[c] = it->second;
+    ++count[it->second];
+  }
+  std::vector<int> order(first_comp.size());
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return count[a] > count[b]; });
+  std::vector<int> rank(first_comp.size(), 0);
+  for (int x : order) {
+    if ((int)C.proj_shape_comp.size() >= kMaxProjShapes) break;
+    C.proj_shape_comp.push_back(first_comp[x]);
+    rank[x] = (int)C.proj_shape_comp.size();
+  }
+  for (int c = 0; c < ncomp; ++c)
+    if (sid[c] >= 0) C.comp_shape[c] = rank[sid[c]];
+}
+
 // ------------------------------------------------- FP32 bound rounding ------
 // Largest (upper) or smallest (lower) float f with  f * c <= d  (f * c < d when
 // strict), c a nonzero integer below 2^24 in magnitude and d an integer below
@@ -717,11 +768,13 @@ static fsmt_status compile(const Problem& P, int policy, Compiled& C) {
                                    std::to_string(nnz) + " nonzeros) exceeds the projection kernel's shared memory");
     C.comp_max_vars = std::max<int32_t>(C.comp_max_vars, (int32_t)comp_vars[k].size());
     C.comp_max_hs = std::max<int32_t>(C.comp_max_hs, (int32_t)comp_hs[k].size());
+    // local reals numbered in order of first appearance in the block's half-spaces
+    // (constraint order), so that blocks of one structure -- a precedence chain of a
+    // given length, whatever its reals -- share one shape
     std::unordered_map<int, int> local;
-    for (size_t t = 0; t < comp_vars[k].size(); ++t) {
-      local[comp_vars[k][t]] = (int)t;
-      C.comp_var.push_back(comp_vars[k][t]);
-    }
+    for (int x : comp_hs[k])
+      for (int j : hs[x].var)
+        if (local.emplace(j, (int)local.size()).second) C.comp_var.push_back(j);
     C.comp_var_ptr.push_back((int32_t)C.comp_var.size());
     for (int x : comp_hs[k]) {
       const HS& h = hs[x];
@@ -738,6 +791,7 @@ static fsmt_status compile(const Problem& P, int policy, Compiled& C) {
     C.comp_hs_ptr.push_back((int32_t)(C.hs_ptr.size() - 1));
     C.comp_max_nnz = std::max<int32_t>(C.comp_max_nnz, C.hs_ptr.back() - C.hs_ptr[C.comp_hs_ptr[C.comp_hs_ptr.size() - 2]]);
   }
+  select_proj_shapes(C);
   return FSMT_OK;
 }
 
@@ -1050,6 +1104,7 @@ fsmt_status fsmt_compiled_info(const fsmt_compiled* c, fsmt_info* out) {
   out->fused_ok = fsmt_fused_limit_ok(C);
   out->n_chunks = C.chunked_ok ? C.n_chunks : 0;
   out->jit_shapes = C.jit_shapes;
+  out->proj_shapes = C.proj_shapes;
   out->empty_boxes = C.empty_boxes;
   return FSMT_OK;
 }

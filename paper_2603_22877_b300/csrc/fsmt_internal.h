@@ -60,6 +60,10 @@ struct Compiled {
   std::vector<float> hs_coef, hs_q0, hs_inv_qq;
   int32_t comp_max_vars = 0, comp_max_hs = 0;  // the largest block's reals and half-spaces
   int32_t comp_max_nnz = 0;  // the most nonzeros over one block's half-spaces
+  std::vector<int32_t> comp_shape;       // per block: rank of its generated projection routine (0: generic)
+  std::vector<int32_t> proj_shape_comp;  // per generated routine: a block of that shape
+  void* jit_proj = nullptr;              // run-time compiled projection kernel (fsmt_jit.cpp), or none
+  int32_t proj_shapes = 0;               // projection routines in it
   int32_t empty_boxes = 0;  // reals with lo > hi after unit-atom tightening (no FP32 point)
   // chunked schedule of C_sigma (see build_chunks in fsmt_host.cpp)
   bool chunked_ok = false;

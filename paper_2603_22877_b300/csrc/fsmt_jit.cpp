@@ -19,7 +19,7 @@
 #include <vector>
 
 #include "fsmt_internal.h"
-#include "fsmt_jit_src.inc"  // kJitDevviewSrc, kJitChunkedSrc (generated by build.py)
+#include "fsmt_jit_src.inc"  // kJitDevviewSrc, kJitChunkedSrc, kJitProjSrc (generated by build.py)
 
 namespace fsmt {
 
@@ -217,13 +217,95 @@ std::string shape_routine(int rank, int V, const uint16_t* hi, const uint16_t* l
   return o.str();
 }
 
+// A float as an exact hexadecimal literal.
+std::string flit(float f) {
+  char buf[64];
+  std::snprintf(buf, sizeof(buf), "%af", (double)f);
+  return buf;
+}
+
+// The projection of one (block, restart) for one block shape (fsmt_proj.cuh's
+// pgd_comp_body, the same operations in the same order): the block's iterate x<t>,
+// box corrections p<t> and half-space multipliers h<q> in registers, the
+// coefficients and 1/||q||^2 as constants, the right-hand sides and the box read
+// from the warp's staged block.  Representative block c of the shape.
+std::string proj_routine(int rank, const Compiled& C, int c) {
+  std::ostringstream o;
+  const int v0 = C.comp_var_ptr[c], nv = C.comp_var_ptr[c + 1] - v0;
+  const int h0 = C.comp_hs_ptr[c], nh = C.comp_hs_ptr[c + 1] - h0;
+  auto X = [](int t) { return "x" + std::to_string(t); };
+  o << "__device__ __forceinline__ void proj_" << rank
+    << "(const float* __restrict__ s_q0, const float* __restrict__ s_lo, const float* __restrict__ s_hi,"
+       " float* __restrict__ b, float* __restrict__ gb, const int* __restrict__ cvar, int R, int r, float step,"
+       " float inv, int sweeps, int polish, int clear_grad, bool act, float& part) {\n";
+  for (int t = 0; t < nv; ++t) o << "  float x" << t << ", p" << t << " = 0.f;\n";
+  for (int t = 0; t < nv; ++t)
+    o << "  {\n    const size_t k = (size_t)cvar[" << t << "] * R + r;\n    x" << t
+      << " = fmaf(-step, gb[k], b[k]);\n    if (clear_grad) gb[k] = 0.f;\n  }\n";
+  for (int q = 0; q < nh; ++q) o << "  float h" << q << " = 0.f;\n";
+  o << "  for (int sw = 0; sw < sweeps; ++sw) {\n";
+  for (int q = 0; q < nh; ++q) {
+    const int e0 = C.hs_ptr[h0 + q], e1 = C.hs_ptr[h0 + q + 1];
+    o << "    {\n      float dot = -s_q0[" << q << "];\n";
+    for (int e = e0; e < e1; ++e)
+      o << "      dot = proj_dot(" << flit(C.hs_coef[e]) << ", " << X(C.hs_lvar[e]) << ", h" << q << ", dot);\n";
+    o << "      const float tn = proj_tn(dot, " << flit(C.hs_inv_qq[h0 + q]) << ");\n";
+    o << "      const float dl = __fsub_rn(h" << q << ", tn);\n";
+    for (int e = e0; e < e1; ++e)
+      o << "      " << X(C.hs_lvar[e]) << " = fmaf(dl, " << flit(C.hs_coef[e]) << ", " << X(C.hs_lvar[e]) << ");\n";
+    o << "      h" << q << " = tn;\n    }\n";
+  }
+  for (int t = 0; t < nv; ++t)
+    o << "    p" << t << " = proj_box(x" << t << ", p" << t << ", s_lo[" << t << "], s_hi[" << t << "]);\n";
+  o << "  }\n  if (sweeps == 0) {\n";
+  for (int t = 0; t < nv; ++t)
+    o << "    x" << t << " = fminf(fmaxf(x" << t << ", s_lo[" << t << "]), s_hi[" << t << "]);\n";
+  o << "  }\n  for (int pass = 0; pass < polish; ++pass) {\n    bool moved = false;\n";
+  for (int q = 0; q < nh; ++q) {
+    const int e0 = C.hs_ptr[h0 + q], e1 = C.hs_ptr[h0 + q + 1];
+    o << "    {\n      const float q0 = s_q0[" << q << "];\n      float v = -q0, mag = fabsf(q0);\n";
+    for (int e = e0; e < e1; ++e)
+      o << "      { const float tm = __fmul_rn(" << flit(C.hs_coef[e]) << ", " << X(C.hs_lvar[e])
+        << "); v = __fadd_rn(v, tm); mag = __fadd_rn(mag, fabsf(tm)); }\n";
+    o << "      const float mg = __fmul_rn(kPolishMargin, mag);\n      if (v > -mg) {\n        float qq = 0.f;\n";
+    for (int e = e0; e < e1; ++e) {
+      const int t = C.hs_lvar[e];
+      const float cf = C.hs_coef[e];
+      o << "        const bool n" << e - e0 << " = !(" << (cf > 0.f ? X(t) + " <= s_lo[" : X(t) + " >= s_hi[") << t
+        << "]);\n        if (n" << e - e0 << ") qq = fmaf(" << flit(cf) << ", " << flit(cf) << ", qq);\n";
+    }
+    o << "        if (qq > 0.f) {\n          const float tq = __fdiv_rn(__fadd_rn(v, __fmul_rn(2.f, mg)), qq);\n";
+    for (int e = e0; e < e1; ++e)
+      o << "          if (n" << e - e0 << ") " << X(C.hs_lvar[e]) << " = fmaf(-tq, " << flit(C.hs_coef[e]) << ", "
+        << X(C.hs_lvar[e]) << ");\n";
+    o << "          moved = true;\n        }\n      }\n    }\n";
+  }
+  for (int t = 0; t < nv; ++t)
+    o << "    x" << t << " = fminf(fmaxf(x" << t << ", s_lo[" << t << "]), s_hi[" << t << "]);\n";
+  o << "    if (!moved) break;\n  }\n";
+  for (int t = 0; t < nv; ++t)
+    o << "  {\n    const size_t k = (size_t)cvar[" << t << "] * R + r;\n    const float q = __fmul_rn(__fsub_rn(b[k], x"
+      << t << "), inv);\n    part = fmaf(q, q, part);\n    if (act) b[k] = x" << t << ";\n  }\n";
+  o << "}\n\n";
+  return o.str();
+}
+
 std::string kernel_name(int wide, int adj, int rpl) {
   return std::string("fsmt_jit_") + (wide ? "wide_" : "") + (adj ? "adj_" : "fwd_") + std::to_string(rpl);
 }
 
 std::string generated_source(const Compiled& C) {
   std::ostringstream o;
-  o << "#define FSMT_JIT_SHAPES 1\n" << kJitDevviewSrc << "\n" << kJitChunkedSrc << "\nnamespace fsmt {\n\n";
+  o << "#define FSMT_JIT_SHAPES 1\n#define FSMT_JIT_PROJ 1\n" << kJitDevviewSrc << "\n" << kJitChunkedSrc << "\n"
+    << kJitProjSrc << "\nnamespace fsmt {\n\n";
+  for (size_t k = 0; k < C.proj_shape_comp.size(); ++k) o << proj_routine((int)k + 1, C, C.proj_shape_comp[k]);
+  o << "__device__ __forceinline__ bool proj_dispatch(int shape, const float* s_q0, const float* s_lo,"
+       " const float* s_hi, float* b, float* gb, const int* cvar, int R, int r, float step, float inv, int sweeps,"
+       " int polish, int clear_grad, bool act, float& part) {\n  switch (shape) {\n";
+  for (size_t k = 0; k < C.proj_shape_comp.size(); ++k)
+    o << "    case " << k + 1 << ": proj_" << k + 1
+      << "(s_q0, s_lo, s_hi, b, gb, cvar, R, r, step, inv, sweeps, polish, clear_grad, act, part); return true;\n";
+  o << "    default: return false;\n  }\n}\n\n";
   for (size_t k = 0; k < C.jit_shape.size(); ++k) {
     const int x = C.jit_shape[k];
     const int b = C.shape_ptr[x], V = C.shape_ptr[x + 1] - b;
@@ -244,11 +326,18 @@ std::string generated_source(const Compiled& C) {
              " float* __restrict__ grad_b, float* __restrict__ obj, float* __restrict__ cop, const int* ctl) {\n"
           << "  fsmt::chunked_body<" << (adj ? "true" : "false") << ", " << rpl << ", " << (wide ? "false" : "true")
           << ">(d, R, sigma, prm, vcap, w, a, b, grad_a, grad_b, obj, cop, ctl);\n}\n";
+  o << "extern \"C\" __global__ void __launch_bounds__(256) fsmt_jit_proj(fsmt::DevView d, int R, float eta,"
+       " float bscale, int sweeps, int polish, const float* prm, const float* __restrict__ wsum,"
+       " float* __restrict__ b, float* __restrict__ gb, float* __restrict__ gn2,"
+       " const uint8_t* __restrict__ active, int clear_grad, const int* ctl, int maxv, int maxh, int maxnz) {\n"
+       "  fsmt::pgd_comp_body(d, R, eta, bscale, sweeps, polish, prm, wsum, b, gb, gn2, active, clear_grad, ctl,"
+       " maxv, maxh, maxnz);\n}\n";
   return o.str();
 }
 
 struct Module {
   void* kernel[2][2][2];  // [wide][adjoint][restarts per lane - 1]
+  void* proj;             // the projection kernel with generated block routines
 };
 std::mutex g_mutex;
 std::unordered_map<std::string, Module> g_modules;  // by source text; kept for the process lifetime
@@ -263,8 +352,11 @@ bool jit_build(Compiled& C) {
   for (auto& r : C.jit_kernel) r[0] = r[1] = nullptr;
   for (auto& r : C.jit_wide) r[0] = r[1] = nullptr;
   C.jit_shapes = 0;
+  C.jit_proj = nullptr;
+  C.proj_shapes = 0;
   const char* off = std::getenv("FSMT_NO_JIT");
-  if ((off && *off && *off != '0') || C.jit_shape.empty() || !C.chunked_ok) return false;
+  const bool diagrams = !C.jit_shape.empty() && C.chunked_ok, blocks = !C.proj_shape_comp.empty();
+  if ((off && *off && *off != '0') || !(diagrams || blocks)) return false;
   Nvrtc& N = nvrtc();
   if (!N.ok) return false;
   int dev = 0, major = 0, minor = 0;
@@ -314,14 +406,28 @@ bool jit_build(Compiled& C) {
             return false;
           m.kernel[wide][adj][r] = (void*)k;
         }
+    {
+      cudaKernel_t k;
+      if (cudaLibraryGetKernel(&k, lib, "fsmt_jit_proj") != cudaSuccess) return false;
+      if (cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(kProjSmemWords * sizeof(float))) != cudaSuccess)
+        return false;
+      m.proj = (void*)k;
+    }
     it = g_modules.emplace(key, m).first;
   }
-  for (int adj = 0; adj < 2; ++adj)
-    for (int r = 0; r < 2; ++r) {
-      C.jit_kernel[adj][r] = it->second.kernel[0][adj][r];
-      C.jit_wide[adj][r] = C.all_specialized ? it->second.kernel[1][adj][r] : nullptr;
-    }
-  C.jit_shapes = (int32_t)C.jit_shape.size();
+  if (diagrams) {
+    for (int adj = 0; adj < 2; ++adj)
+      for (int r = 0; r < 2; ++r) {
+        C.jit_kernel[adj][r] = it->second.kernel[0][adj][r];
+        C.jit_wide[adj][r] = C.all_specialized ? it->second.kernel[1][adj][r] : nullptr;
+      }
+    C.jit_shapes = (int32_t)C.jit_shape.size();
+  }
+  if (blocks) {
+    C.jit_proj = it->second.proj;
+    C.proj_shapes = (int32_t)C.proj_shape_comp.size();
+  }
   return true;
 }
 

@@ -1,0 +1,218 @@
+// Device code of the projection of the reals onto D (Def. Projection, Prop. QP):
+// Dykstra's alternating projections on each block of reals coupled by
+// multi-variable unit atoms, then the feasibility polish, with the per-restart
+// ||g||^2 of Eq. grad_map.  Compiled both ahead of time (through fsmt_device.cu)
+// and at run time (NVRTC, fsmt_jit.cpp), where straight-line routines with the
+// block's iterate in registers are generated for the most frequent block shapes.
+//
+// The arithmetic is written out with explicit fused multiply-adds and correctly
+// rounded operations (no contraction left to the compiler), so that a generated
+// routine, which repeats it with the coefficients as constants, gives the same
+// bits as the generic loop.
+#pragma once
+
+namespace fsmt {
+
+constexpr float kPolishMargin = 1.52587890625e-05f;  // 2^-16
+
+// Sum over the blockDim.y rows of a (32 restarts x rows) block, added to gn2[r].
+__device__ __forceinline__ void reduce_rows_add(float part, float* gn2, int r, bool ok) {
+  __shared__ float red[8][33];
+  red[threadIdx.y][threadIdx.x] = part;
+  __syncthreads();
+  if (threadIdx.y == 0) {
+    float s = 0.f;
+    for (int y = 0; y < (int)blockDim.y; ++y) s += red[y][threadIdx.x];
+    if (ok && s != 0.f) atomicAdd(gn2 + r, s);
+  }
+}
+
+// The step of restart r: eta, or eta * n_obj / wsum[r] when the step is normalised
+// by the total weight (Thm. max_step with L proportional to the weight, Prop. Lipschitz).
+__device__ __forceinline__ float restart_eta(const DevView& d, float eta, const float* prm, const float* wsum,
+                                             int r, bool ok) {
+  eta = load_param(prm, P_ETA, eta);
+  if (prm && prm[P_NORM] == 0.f) wsum = nullptr;
+  if (wsum && ok && d.n_obj > 0) {
+    const float ws = wsum[r];
+    if (ws > 0.f) eta *= (float)d.n_obj / ws;
+  }
+  return eta;
+}
+
+// The arithmetic of one Dykstra half-space term, one box step and one polish term,
+// shared by the generic loop and the generated routines.
+__device__ __forceinline__ float proj_dot(float cf, float x, float th, float dot) { return fmaf(cf, fmaf(th, cf, x), dot); }
+__device__ __forceinline__ float proj_tn(float dot, float iq) { return __fmul_rn(fmaxf(dot, 0.f), iq); }
+__device__ __forceinline__ float proj_box(float& x, float p, float lo, float hi) {  // returns the new correction
+  const float yv = __fadd_rn(x, p);
+  const float xn = fminf(fmaxf(yv, lo), hi);
+  x = xn;
+  return __fsub_rn(yv, xn);
+}
+
+// A block shape's generated routine (rank shape >= 1) runs the whole projection of
+// one (block, restart) and returns true; false leaves it to the generic loop.
+__device__ __forceinline__ bool proj_dispatch(int shape, const float* s_q0, const float* s_lo, const float* s_hi,
+                                              float* b, float* gb, const int* cvar, int R, int r, float step,
+                                              float inv, int sweeps, int polish, int clear_grad, bool act,
+                                              float& part);
+
+// One thread per (block, restart); a warp serves one block for 32 restarts.  Per
+// sweep: every half-space in constraint order, then the box.  Then up to `polish`
+// passes: each half-space q.y <= q0 whose value is above -margin, margin = 2^-16
+// (|q0| + sum |q_j y_j|) (far above the FP32 rounding of q.y), is projected onto
+// q.y <= q0 - 2 margin along the reals not pinned at the bound the step would
+// cross, then the box is clamped; the thread stops at the first pass that moves
+// nothing, so the point it returns satisfies every half-space exactly whenever
+// the passes settle.
+// Shared memory: the iterate, Dykstra's box corrections and half-space
+// multipliers of each (block, restart), one column per thread ([var][thread]:
+// conflict-free), sized by the instance's largest block; and per warp the block
+// itself (half-space offsets, local reals, coefficients, right-hand sides,
+// 1/||q||^2, the box), staged once by the warp's lanes together so that the
+// sweeps read it by broadcast instead of through dependent global loads.
+__device__ __forceinline__ void pgd_comp_body(const DevView& d, int R, float eta, float bscale, int sweeps,
+                                              int polish, const float* prm, const float* __restrict__ wsum,
+                                              float* __restrict__ b, float* __restrict__ gb,
+                                              float* __restrict__ gn2, const uint8_t* __restrict__ active,
+                                              int clear_grad, const int* ctl, int maxv, int maxh, int maxnz) {
+  if (ctl && ctl[0] == 0) return;
+  const int lane = threadIdx.x;
+  const int r = blockIdx.x * 32 + lane;
+  const bool ok = r < R;
+  const bool act = ok && (!active || active[r] == 1);
+  eta = restart_eta(d, eta, prm, wsum, r, ok);
+  bscale = load_param(prm, P_BSCALE, bscale);
+  if (prm) {
+    sweeps = (int)prm[P_SWEEPS];
+    polish = (int)prm[P_POLISH];
+  }
+  const float step = eta * bscale * bscale, inv = 1.f / (bscale * eta);
+  float part = 0.f;
+  extern __shared__ float s_col[];
+  const int T = blockDim.x * blockDim.y, tid = threadIdx.y * blockDim.x + lane;
+  float* xs = s_col + tid;           // x(t) at xs[t * T]
+  float* ps = xs + maxv * T;         // pbox(t)
+  float* hs = ps + maxv * T;         // th(q)
+  // the warp's staged block
+  const int wwords = (maxh + 1) + 2 * maxnz + 2 * maxh + 2 * maxv;
+  int* s_hp = reinterpret_cast<int*>(s_col + (2 * maxv + maxh) * T) + threadIdx.y * wwords;  // offsets [nh + 1]
+  int* s_lv = s_hp + maxh + 1;                                   // local real of each term
+  float* s_cf = reinterpret_cast<float*>(s_lv + maxnz);          // coefficient of each term
+  float* s_q0 = s_cf + maxnz;                                    // right-hand sides
+  float* s_iq = s_q0 + maxh;                                     // 1 / ||q||^2
+  float* s_lo = s_iq + maxh;                                     // the box of each local real
+  float* s_hi = s_lo + maxv;
+#define x(t) xs[(t) * T]
+#define pbox(t) ps[(t) * T]
+#define th(q) hs[(q) * T]
+  for (int c = blockIdx.y * blockDim.y + threadIdx.y; c < d.n_comp; c += gridDim.y * blockDim.y) {
+    const int v0 = d.comp_var_ptr[c], nv = d.comp_var_ptr[c + 1] - v0;
+    const int h0 = d.comp_hs_ptr[c], nh = d.comp_hs_ptr[c + 1] - h0;
+    const int e_base = d.hs_ptr[h0], nz = d.hs_ptr[h0 + nh] - e_base;
+    __syncwarp();  // the previous block's reads are done
+    for (int i = lane; i <= nh; i += 32) s_hp[i] = d.hs_ptr[h0 + i] - e_base;
+    for (int i = lane; i < nz; i += 32) {
+      s_lv[i] = d.hs_lvar[e_base + i];
+      s_cf[i] = d.hs_coef[e_base + i];
+    }
+    for (int i = lane; i < nh; i += 32) {
+      s_q0[i] = d.hs_q0[h0 + i];
+      s_iq[i] = d.hs_inv_qq[h0 + i];
+    }
+    for (int i = lane; i < nv; i += 32) {
+      const int j = d.comp_var[v0 + i];
+      s_lo[i] = d.lo[j];
+      s_hi[i] = d.hi[j];
+    }
+    __syncwarp();
+    if (!ok) continue;
+    const int shape = d.comp_shape[c];
+    if (shape > 0 && proj_dispatch(shape, s_q0, s_lo, s_hi, b, gb, d.comp_var + v0, R, r, step, inv, sweeps, polish,
+                                   clear_grad, act, part))
+      continue;
+    for (int t = 0; t < nv; ++t) {
+      const size_t k = (size_t)d.comp_var[v0 + t] * R + r;
+      x(t) = fmaf(-step, gb[k], b[k]);
+      pbox(t) = 0.f;
+      if (clear_grad) gb[k] = 0.f;
+    }
+    for (int q = 0; q < nh; ++q) th(q) = 0.f;
+    for (int sw = 0; sw < sweeps; ++sw) {
+      for (int q = 0; q < nh; ++q) {
+        const int e0 = s_hp[q], e1 = s_hp[q + 1];
+        const float thq = th(q);
+        float dot = -s_q0[q];
+        for (int e = e0; e < e1; ++e) dot = proj_dot(s_cf[e], x(s_lv[e]), thq, dot);
+        const float tn = proj_tn(dot, s_iq[q]);
+        const float delta = __fsub_rn(thq, tn);
+        for (int e = e0; e < e1; ++e) x(s_lv[e]) = fmaf(delta, s_cf[e], x(s_lv[e]));
+        th(q) = tn;
+      }
+      for (int t = 0; t < nv; ++t) {
+        float xt = x(t);
+        pbox(t) = proj_box(xt, pbox(t), s_lo[t], s_hi[t]);
+        x(t) = xt;
+      }
+    }
+    if (sweeps == 0)
+      for (int t = 0; t < nv; ++t) x(t) = fminf(fmaxf(x(t), s_lo[t]), s_hi[t]);
+    for (int pass = 0; pass < polish; ++pass) {
+      bool moved = false;
+      for (int q = 0; q < nh; ++q) {
+        const int e0 = s_hp[q], e1 = s_hp[q + 1];
+        const float q0 = s_q0[q];
+        float v = -q0, mag = fabsf(q0);
+        for (int e = e0; e < e1; ++e) {
+          const float term = __fmul_rn(s_cf[e], x(s_lv[e]));
+          v = __fadd_rn(v, term);
+          mag = __fadd_rn(mag, fabsf(term));
+        }
+        const float margin = __fmul_rn(kPolishMargin, mag);
+        if (v > -margin) {
+          // move along the reals that are not pinned at the bound the step would cross
+          float qq = 0.f;
+          for (int e = e0; e < e1; ++e) {
+            const float cf = s_cf[e];
+            const int t = s_lv[e];
+            const bool pinned = (cf > 0.f && x(t) <= s_lo[t]) || (cf < 0.f && x(t) >= s_hi[t]);
+            if (!pinned) qq = fmaf(cf, cf, qq);
+          }
+          if (qq > 0.f) {
+            const float tq = __fdiv_rn(__fadd_rn(v, __fmul_rn(2.f, margin)), qq);
+            for (int e = e0; e < e1; ++e) {
+              const float cf = s_cf[e];
+              const int t = s_lv[e];
+              const bool pinned = (cf > 0.f && x(t) <= s_lo[t]) || (cf < 0.f && x(t) >= s_hi[t]);
+              if (!pinned) x(t) = fmaf(-tq, cf, x(t));
+            }
+            moved = true;
+          }
+        }
+      }
+      for (int t = 0; t < nv; ++t) x(t) = fminf(fmaxf(x(t), s_lo[t]), s_hi[t]);
+      if (!moved) break;
+    }
+    for (int t = 0; t < nv; ++t) {
+      const size_t k = (size_t)d.comp_var[v0 + t] * R + r;
+      const float q = __fmul_rn(__fsub_rn(b[k], x(t)), inv);  // b still holds the step's starting point
+      part = fmaf(q, q, part);
+      if (act) b[k] = x(t);
+    }
+  }
+#undef x
+#undef pbox
+#undef th
+  reduce_rows_add(part, gn2, r, ok);
+}
+
+#ifndef FSMT_JIT_PROJ
+// Ahead-of-time build: no generated projection routines, every block takes the generic loop.
+__device__ __forceinline__ bool proj_dispatch(int, const float*, const float*, const float*, float*, float*,
+                                              const int*, int, int, float, float, int, int, int, bool, float&) {
+  return false;
+}
+#endif
+
+}  // namespace fsmt

@@ -495,8 +495,9 @@ class Solver:
         if self._x is None:
             self._x = torch.empty((self.comp.n_bool, self.R), device=self.a.device, dtype=torch.int8)
         self.comp.round(self.R, self.a, self._x)
-        x = self._x[:, r].cpu().numpy()
-        y = self.b[:, r].cpu().numpy().astype(np.float64)
+        # whole arrays to the host (one copy each), then restart r's column
+        x = np.ascontiguousarray(self._x.cpu().numpy()[:, r])
+        y = self.b.cpu().numpy()[:, r].astype(np.float64)
         sat, _ = self.problem.verify_exact(x, y)
         return sat, x, y
 
@@ -534,25 +535,29 @@ class Solver:
             self.stage(sigma, t)
             if ev is not None:
                 ev[1].record()
-            nu = self.n_unsat
+            # the stage's outcome reaches the host as one small copy; the statistics are
+            # taken there (no device kernels beyond the library's own in the loop)
+            nu = self.n_unsat.cpu().numpy()
             nonfinite = int((nu < 0).sum())
             found = None
             lo = None
             if nonfinite < self.R:
-                lo = int(torch.where(nu < 0, torch.iinfo(torch.int32).max, nu).min())
+                lo = int(nu[nu >= 0].min())
                 best = lo if best is None else min(best, lo)
             if log is not None:
                 fin = nu[nu >= 0]
-                obj = self.obj[torch.isfinite(self.obj)]
+                ob = self.obj.cpu().numpy()
+                ob = ob[np.isfinite(ob)]
+                gn = self.gnorm2.cpu().numpy().astype(np.float64)
                 log(dict(stage=t, sigma=float(sigma), seconds=time.perf_counter() - t0, min_unsat=lo,
-                         median_unsat=float(fin.float().median()) if fin.numel() else None,
+                         median_unsat=float(np.median(fin)) if fin.size else None,
                          at_zero=int((nu == 0).sum()), nonfinite=nonfinite,
-                         mean_iters=float(self.iters.float().mean()),
-                         median_gnorm2=float(torch.nanmedian(self.gnorm2.float())),
-                         best_obj=float(obj.min()) if obj.numel() else None,
+                         mean_iters=float(self.iters.cpu().numpy().astype(np.float64).mean()),
+                         median_gnorm2=float(np.nanmedian(gn)) if not np.isnan(gn).all() else None,
+                         best_obj=float(ob.min()) if ob.size else None,
                          gpu_ms=(ev[1].synchronize(), ev[0].elapsed_time(ev[1]))[1] if ev is not None else None))
             if nonfinite < self.R:
-                cand = torch.nonzero(nu == 0).flatten().tolist() if lo == 0 else []
+                cand = np.nonzero(nu == 0)[0].tolist() if lo == 0 else []
                 for r in cand:
                     sat, x, y = self.verify_restart(r)
                     if sat:

@@ -296,3 +296,40 @@ def test_converge_and_nonfinite_marks():
     bit = np.int32(-2 ** 31)
     want = np.array([3, 0, 5 | bit, 1 | bit, 0, 0, 7 | bit, 2], np.int32)
     np.testing.assert_array_equal(nu.cpu().numpy(), want)
+
+
+@pytest.mark.parametrize("make,R", [(lambda: W.jobshop(1002, 10, 5), 70),
+                                    (lambda: W.concat(W.uneven_batch(1004, 6, (3, 12), (3, 9)), "b"), 32)])
+def test_generated_projection_matches_the_generic_loop(make, R, monkeypatch):
+    """Blocks of coupled reals whose shape got a run-time generated projection routine
+    (fsmt_info.proj_shapes > 0: the iterate in registers, the coefficients as
+    constants) end at the same points with the same ||g||^2, bit for bit, as the
+    generic loop that FSMT_NO_JIT leaves every block to: the routines repeat its
+    operations in its order."""
+    import ctypes as C
+    import torch
+    from paper_2603_22877_b300 import _lib as L
+    from paper_2603_22877_b300.engine import Problem
+    inst = make()
+    P, comp, a, b, w = setup(inst, R)
+    info = L.Info()
+    L.call("fsmt_compiled_info", comp.h, C.byref(info))
+    assert info.proj_shapes > 0
+    monkeypatch.setenv("FSMT_NO_JIT", "1")
+    comp2 = Problem.from_instance(inst).compile().upload()
+    L.call("fsmt_compiled_info", comp2.h, C.byref(info))
+    assert info.proj_shapes == 0
+    sigma = sigmas_for(inst)[1]
+    _, _, ga, gb = OBJ.evaluate(inst, a.astype(np.float64), b.astype(np.float64), w.astype(np.float64), sigma)
+    wsum = torch.zeros(R, device="cuda")   # one set of weight sums (their float atomics order varies by run)
+    comp.weight_sum(R, to_dev(w)[0], wsum)
+    outs = []
+    for c_ in (comp, comp2):
+        da, db, dga, dgb = to_dev(a, b, ga.astype(np.float32), gb.astype(np.float32))
+        gn = torch.zeros(R, device="cuda")
+        c_.pgd_step(R, 0.05, inst.scale, 20, da, db, dga, dgb, gn, wsum=wsum, polish=32)
+        outs.append((da.cpu().numpy(), db.cpu().numpy(), gn.cpu().numpy()))
+    np.testing.assert_array_equal(outs[0][0], outs[1][0])
+    np.testing.assert_array_equal(outs[0][1], outs[1][1])
+    # ||g||^2 adds the blocks' shares with float atomics, in an order that varies by run
+    np.testing.assert_allclose(outs[0][2], outs[1][2], rtol=1e-6)

@@ -31,6 +31,20 @@ HARNESS = r'''
 #include <cstring>
 #include "fsmt_jit.cpp"
 namespace fsmt { void set_error(const std::string&) {} }
+extern "C" long proj_src(int rank, int nv, int nh, const int32_t* hs_ptr, const int32_t* lvar, const float* coef,
+                         const float* inv_qq, char* out, long cap) {
+  fsmt::Compiled C;
+  C.comp_var_ptr = {0, nv};
+  C.comp_hs_ptr = {0, nh};
+  C.hs_ptr.assign(hs_ptr, hs_ptr + nh + 1);
+  C.hs_lvar.assign(lvar, lvar + hs_ptr[nh]);
+  C.hs_coef.assign(coef, coef + hs_ptr[nh]);
+  C.hs_inv_qq.assign(inv_qq, inv_qq + nh);
+  const std::string s = fsmt::proj_routine(rank, C, 0);
+  if ((long)s.size() + 1 > cap) return -1;
+  std::memcpy(out, s.c_str(), s.size() + 1);
+  return (long)s.size();
+}
 extern "C" long shape_src(int rank, int V, const uint16_t* hi, const uint16_t* lo, const uint16_t* grp,
                           char* out, long cap) {
   const std::string s = fsmt::shape_routine(rank, V, hi, lo, grp);
@@ -77,6 +91,7 @@ def generator(tmp_path_factory):
     assert r.returncode == 0, r.stderr
     lib = C.CDLL(str(so))
     lib.shape_src.restype = C.c_long
+    lib.proj_src.restype = C.c_long
 
     def source(rank, hi, lo, grp):
         buf = C.create_string_buffer(1 << 20)
@@ -84,6 +99,7 @@ def generator(tmp_path_factory):
         n = lib.shape_src(rank, len(hi), *[a.ctypes.data_as(C.c_void_p) for a in arrs], buf, 1 << 20)
         assert n > 0
         return buf.value.decode()
+    source.lib = lib
     return source, d
 
 
@@ -172,3 +188,102 @@ def test_generated_routines_match_the_definition(generator):
                 for r_ in range(2):
                     g = float(dwant[i][r_]) * (-1.0 if neg[i] else 1.0) * float(w[r_])
                     assert abs(s_g[j * SLOT_FLOATS + 32 * r_] - g) <= 2e-5 * max(1.0, abs(g)), (kind, lits, i, r_)
+
+
+PROJ_SHIM = r'''
+#include <cmath>
+#include <cstddef>
+#define __device__
+#define __forceinline__ inline
+#define __restrict__
+static inline float fmaf_(float a, float b, float c) { return std::fma(a, b, c); }
+#define fmaf fmaf_
+static inline float __fmul_rn(float a, float b) { return a * b; }
+static inline float __fadd_rn(float a, float b) { return a + b; }
+static inline float __fsub_rn(float a, float b) { return a - b; }
+static inline float __fdiv_rn(float a, float b) { return a / b; }
+static const float kPolishMargin = 1.52587890625e-05f;
+static inline float proj_dot(float cf, float x, float th, float dot) { return fmaf(cf, fmaf(th, cf, x), dot); }
+static inline float proj_tn(float dot, float iq) { return __fmul_rn(std::fmax(dot, 0.f), iq); }
+static inline float proj_box(float& x, float p, float lo, float hi) {
+  const float yv = __fadd_rn(x, p); const float xn = std::fmin(std::fmax(yv, lo), hi); x = xn; return __fsub_rn(yv, xn);
+}
+static inline float fminf_(float a, float b) { return std::fmin(a, b); }
+static inline float fmaxf_(float a, float b) { return std::fmax(a, b); }
+static inline float fabsf_(float a) { return std::fabs(a); }
+#define fminf fminf_
+#define fmaxf fmaxf_
+#define fabsf fabsf_
+'''
+
+
+def test_generated_projection_routines_match_the_oracle(generator):
+    """The projection routines generated for frequent block shapes (fsmt_jit.cpp,
+    proj_routine: Dykstra's sweeps and the feasibility polish of Prop. QP's reading,
+    straight-line over registers) compiled for the host and run on precedence chains
+    of job-shop instances (blocks of 3, 5 and 9 reals), against the oracle's
+    Domain.project_b in FP64: the same end points up to FP32 rounding, and the
+    squared step lengths summed as ||g||^2 (Eq. grad_map)."""
+    from oracle import pgd
+    source, d = generator
+    lib = source.lib
+    rng = np.random.default_rng(8)
+    body = [PROJ_SHIM]
+    cases = []
+    for k, (jobs, machines) in enumerate(((4, 3), (5, 5), (3, 9)), start=1):
+        inst = W.jobshop(1002, jobs, machines)
+        dom = pgd.Domain(inst)
+        hs = dom.halfspaces[:machines - 1]                  # the first job's chain
+        order = []
+        for var, q, q0 in hs:
+            for j in var:
+                if int(j) not in order:
+                    order.append(int(j))
+        loc = {j: t for t, j in enumerate(order)}
+        ptr, lv, cf, iq = [0], [], [], []
+        for var, q, q0 in hs:
+            lv += [loc[int(j)] for j in var]
+            cf += [float(c) for c in q]
+            ptr.append(len(lv))
+            iq.append(np.float32(1.0 / float((np.asarray(q) ** 2).sum())))
+        arrs = [np.asarray(ptr, np.int32), np.asarray(lv, np.int32), np.asarray(cf, np.float32), np.asarray(iq, np.float32)]
+        buf = C.create_string_buffer(1 << 20)
+        assert lib.proj_src(k, len(order), len(hs), *[a.ctypes.data_as(C.c_void_p) for a in arrs], buf, 1 << 20) > 0
+        body.append(buf.value.decode())
+        body.append(f'extern "C" void run_{k}(const float* q0, const float* lo, const float* hi, float* b, float* gb,'
+                    f' const int* cvar, float step, float inv, float* part) {{\n'
+                    f'  float p = 0.f;\n  proj_{k}(q0, lo, hi, b, gb, cvar, 1, 0, step, inv, 20, 32, 1, true, p);\n'
+                    f'  *part = p;\n}}\n')
+        cases.append((k, inst, dom, hs, order))
+    src = d / "proj.cpp"
+    src.write_text("\n".join(body))
+    so = d / "proj.so"
+    r = subprocess.run([_gxx(), "-std=c++17", "-O1", "-ffp-contract=off", "-shared", "-fPIC", str(src), "-o", str(so)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[:4000]
+    rl = C.CDLL(str(so))
+    for k, inst, dom, hs, order in cases:
+        n = len(order)
+        q0 = np.asarray([h[2] for h in hs], np.float32)
+        lo = np.asarray([dom.lo[j] for j in order], np.float32)
+        hi = np.asarray([dom.hi[j] for j in order], np.float32)
+        cvar = np.arange(n, dtype=np.int32)                  # restart 0 of R = 1: b[t]
+        for trial in range(6):
+            y0 = (inst.planted_y[order] + rng.normal(0, 4.0, n)).astype(np.float32)
+            g = rng.normal(0, 1.0, n).astype(np.float32)
+            step, inv = np.float32(0.5), np.float32(1.0)
+            b = y0.copy()
+            gb = g.copy()
+            part = np.zeros(1, np.float32)
+            getattr(rl, f"run_{k}")(*[a.ctypes.data_as(C.c_void_p) for a in (q0, lo, hi, b, gb, cvar)],
+                                    C.c_float(step), C.c_float(inv), part.ctypes.data_as(C.c_void_p))
+            assert not gb.any()                              # the gradient is cleared
+            full = np.zeros((inst.n_real, 1))
+            full[:, 0] = inst.planted_y
+            full[order, 0] = y0.astype(np.float64) - 0.5 * g.astype(np.float64)
+            # the other reals of the instance do not interact with this chain's block
+            ref = dom.project_b(full, 20, 32)[order, 0]
+            scale = float(np.abs(ref).max()) + 1.0
+            np.testing.assert_allclose(b, ref, atol=2e-5 * scale, err_msg=f"shape {k} trial {trial}")
+            want = float(((y0.astype(np.float64) - ref) ** 2).sum())
+            assert abs(part[0] - want) <= 1e-4 * want + 1e-3, (part[0], want)
