@@ -8,7 +8,10 @@ Follows, in the paper's order:
     projection of the reals unchanged.
   * Def. Projection / Prop. QP: D = [-1, 1]^n x (box of the reals) x (unit
     atomic constraints).  Single-variable unit atoms tighten the box (exact
-    clamp).  Multi-variable unit atoms are half-spaces; the projection onto
+    clamp); a single-variable equality pins the real.  A multi-variable equality
+    is a hyperplane: its Dykstra multiplier is not clamped (the projection onto
+    an affine set), the polish returns points to it within the FP32 band, and
+    repair_equalities makes it hold exactly before the exact check (a reading).  Multi-variable unit atoms are half-spaces; the projection onto
     box n half-spaces uses Dykstra's alternating projections (Boyle & Dykstra
     1986) with a fixed number of sweeps, half-spaces in constraint order and
     the box last in each sweep, followed by a short feasibility polish so that
@@ -42,7 +45,9 @@ sigma and S times 4 give the reals times 4 and the same ||g||^2, bit for bit);
 step_sizes by hand on a three-constraint instance and its independence of the
 projected atoms' weights; exact check against planted assignments and
 single-literal flips; Fig. 2's two minima; the vectorised kind evaluation
-against the scalar definition.
+against the scalar definition; with equalities, Dykstra against the active-set QP
+with the equality rows always active, the polish back onto the hyperplanes within
+their band, and the repair's cases by hand.
 The annealing trajectory itself is parity unpinned (the paper gives no
 trajectory values for a known step size).
 """
@@ -73,6 +78,14 @@ class Config:
 POLISH_MARGIN = 2.0 ** -16
 
 
+def eq_band(n, mag):
+    """The band within which an equality's residual q.y - q0 is taken as zero in FP32:
+    (n + 4) (u mag + 2^-126-ish), u = 2^-24, mag = |q0| + sum |q_j y_j| over its n
+    terms (Higham, Accuracy and Stability of Numerical Algorithms, 2nd ed., Sec. 3.1,
+    the bound of an n-term FP32 dot product, with two terms for the rounding of mag)."""
+    return (n + 4) * (2.0 ** -24 * mag + 1e-38)
+
+
 def step_sizes(inst, w, cfg, policy=None):
     """Per-restart step size.  With normalize_eta, eta_r = eta |C_sigma| / sum_c w_c[r]:
     Thm. max_step takes eta = 1/L with L proportional to alpha = sum_c w_c (Prop.
@@ -96,6 +109,7 @@ class Domain:
         self.lo = np.array(inst.lo, np.float64)
         self.hi = np.array(inst.hi, np.float64)
         self.halfspaces = []  # (vars, coefs float64, q0 float64)
+        self.eq = []          # per entry of halfspaces: an equality's hyperplane q.y = q0
         if policy != OBJ.PROJECT:
             return
         for c in range(inst.n_cons):
@@ -103,6 +117,17 @@ class Domain:
                 continue
             l = int(inst.lits(c)[0])
             var, coef, q0, rel = inst.atom((l >> 1) - inst.n_bool)
+            if rel == S.EQ:  # an equality unit atom: a pinned real, or a hyperplane
+                if l & 1:
+                    raise ValueError("a negated equality is not a convex set")
+                if len(var) == 1:
+                    v = float(Fraction(int(q0), int(coef[0])))
+                    j = int(var[0])
+                    self.lo[j], self.hi[j] = max(self.lo[j], v), min(self.hi[j], v)
+                else:
+                    self.halfspaces.append((np.asarray(var, np.int64), np.asarray(coef, np.float64), float(q0)))
+                    self.eq.append(True)
+                continue
             coef, q0, strict = S.normalized_atom(coef, q0, rel)
             if l & 1:  # not (q.y <= q0)  ->  -q.y <= -q0 (closure of the open half-space)
                 coef, q0 = [-c_ for c_ in coef], -q0
@@ -115,6 +140,7 @@ class Domain:
                     self.lo[j] = max(self.lo[j], bound)
             else:
                 self.halfspaces.append((np.asarray(var, np.int64), np.asarray(coef, np.float64), float(q0)))
+                self.eq.append(False)
 
     def project_b(self, bp, sweeps, polish=32):
         """proj onto box n half-spaces of points bp [m][R] (Dykstra; exact clamp if no half-space).
@@ -125,7 +151,13 @@ class Domain:
         projected onto q.y <= q0 - 2 margin along the reals that are not pinned
         at the bound the step would cross, then the box is clamped; a restart
         stops when a pass moves nothing.  The result satisfies every half-space exactly
-        whenever the passes settle."""
+        whenever the passes settle.
+
+        An equality is a hyperplane: in Dykstra's sweeps its multiplier is not clamped
+        at zero (the projection onto an affine set), and in the polish a hyperplane whose
+        residual exceeds eq_band is projected back onto it along the reals not pinned at
+        the bound the move would cross (FP32 cannot hold most hyperplanes exactly; the
+        exact repair on the host, repair_equalities, finishes them)."""
         x = np.clip(bp, self.lo[:, None], self.hi[:, None])
         if not self.halfspaces:
             return x
@@ -138,7 +170,7 @@ class Domain:
             for k, (var, q, q0) in enumerate(self.halfspaces):
                 yv = x[var] + t_h[k][None, :] * q[:, None]
                 viol = (q[:, None] * yv).sum(0) - q0
-                t_h[k] = np.maximum(viol, 0.0) / float((q * q).sum())
+                t_h[k] = (viol if self.eq[k] else np.maximum(viol, 0.0)) / float((q * q).sum())
                 x[var] = yv - t_h[k][None, :] * q[:, None]
             yv = x[J] + p_box
             xn = np.clip(yv, self.lo[J][:, None], self.hi[J][:, None])
@@ -146,9 +178,20 @@ class Domain:
             x[J] = xn
         for _ in range(polish):
             moved = np.zeros(R, bool)
-            for var, q, q0 in self.halfspaces:
+            for k, (var, q, q0) in enumerate(self.halfspaces):
                 xv = x[var]
                 v = (q[:, None] * xv).sum(0) - q0
+                if self.eq[k]:  # back onto the hyperplane when off it by more than the FP32 band
+                    need = np.abs(v) > eq_band(len(var), abs(q0) + (np.abs(q[:, None] * xv)).sum(0))
+                    lo, hi = self.lo[var][:, None], self.hi[var][:, None]
+                    dirn = np.sign(v)[None, :] * q[:, None]  # the move is -t q_j, t of the sign of v
+                    free = ~(((dirn > 0) & (xv <= lo)) | ((dirn < 0) & (xv >= hi)))
+                    qq = ((q * q)[:, None] * free).sum(0)
+                    need &= qq > 0
+                    step = np.where(need, v / np.where(qq > 0, qq, 1.0), 0.0)
+                    x[var] = xv - step[None, :] * q[:, None] * free
+                    moved |= need
+                    continue
                 margin = POLISH_MARGIN * (abs(q0) + (np.abs(q[:, None] * xv)).sum(0))
                 need = v > -margin
                 # the step moves y_j by -t q_j; a real on the bound it would cross stays put
@@ -163,6 +206,42 @@ class Domain:
             if not moved.any():
                 break
         return x
+
+
+def repair_equalities(inst, y):
+    """Exact repair of the reals y ([m] floats) so that every projected equality unit
+    atom holds exactly, before the exact check (the projection leaves a hyperplane only
+    within FP32 rounding).  In constraint order, an equality that does not already hold
+    is solved for its pivot: the last of its reals with coefficient +-1 that no earlier
+    equality used as pivot; y_p = (q0 - sum_{j != p} q_j y_j) / q_p exactly.  Returns the
+    reals as Fractions, or None when an equality has no such real or a later pivot broke
+    an earlier equality.  (A reading: the paper's exact check has no equalities to hold.)"""
+    yv = [Fraction(float(v)) for v in y]
+    eqs = []
+    for c in range(inst.n_cons):
+        if OBJ.is_unit_atomic(inst, c):
+            l = int(inst.lits(c)[0])
+            var, coef, q0, rel = inst.atom((l >> 1) - inst.n_bool)
+            if rel == S.EQ and not l & 1:
+                eqs.append(([int(v) for v in var], [int(q) for q in coef], int(q0)))
+    pivots = set()
+
+    def residual(var, coef, q0):
+        return sum(Fraction(q) * yv[v] for v, q in zip(var, coef)) - q0
+
+    for var, coef, q0 in eqs:
+        if residual(var, coef, q0) == 0:
+            continue
+        cand = [t for t in range(len(var)) if abs(coef[t]) == 1 and var[t] not in pivots]
+        if not cand:
+            return None
+        t = cand[-1]
+        rest = sum(Fraction(coef[u]) * yv[var[u]] for u in range(len(var)) if u != t)
+        yv[var[t]] = (q0 - rest) / coef[t]
+        pivots.add(var[t])
+    if any(residual(*e) != 0 for e in eqs):
+        return None
+    return yv
 
 
 def pgd_step(a, b, ga, gb, eta, scale, dom, sweeps, polish=32):

@@ -3,8 +3,9 @@
 A constraint c is a Boolean function of its literals' truth values (Results,
 "Satisfiability Modulo Theories"; Methods, "Benchmark Problem Descriptions"
 for cardinality, not-all-equal and parity).  An atom is the linear relation
-sum_j q_ij y_j - q_i0 (rel) 0 (Results, "Walsh-Fourier Expansions"); its
-indicator delta_i(y) is -1 when it holds.
+sum_j q_ij y_j - q_i0 (rel) 0 (Results, "Walsh-Fourier Expansions"; rel one of
+<=, <, >=, >, = as in Results, "Satisfiability Modulo Theories"); its indicator
+delta_i(y) is -1 when it holds.
 
 Pins: each kind is checked in the tests against hand-written truth tables and
 the planted assignments of the input generators; atom truth is exact rational
@@ -15,7 +16,7 @@ from fractions import Fraction
 import numpy as np
 
 OR, XOR, CARD_LE, NAE, MUX, NEQ_OR = 0, 1, 2, 3, 4, 5
-LE, LT, GE, GT = 0, 1, 2, 3
+LE, LT, GE, GT, EQ = 0, 1, 2, 3, 4
 
 
 def kind_value(kind: int, param: int, t) -> bool:
@@ -49,11 +50,17 @@ def atom_holds_exact(coef, var, q0, rel, y) -> bool:
         return s >= 0
     if rel == GT:
         return s > 0
+    if rel == EQ:
+        return s == 0
     raise ValueError(rel)
 
 
 def normalized_atom(coef, q0, rel):
-    """Rewrites GE/GT as LE/LT by negating both sides: returns (coef, q0, strict)."""
+    """Rewrites GE/GT as LE/LT by negating both sides: returns (coef, q0, strict).
+    An equality has no such form (its smoothed probability is 0: it may only be a
+    projected unit constraint), so it raises."""
+    if rel == EQ:
+        raise ValueError("an equality atom has no relaxed (<=) form")
     if rel in (GE, GT):
         return [-int(c) for c in coef], -int(q0), rel == GT
     return [int(c) for c in coef], int(q0), rel == LT
@@ -101,4 +108,6 @@ def atom_truth_batch(inst, i, y):
         return s < 0
     if rel == GE:
         return s >= 0
+    if rel == EQ:
+        return s == 0
     return s > 0

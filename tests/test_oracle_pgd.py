@@ -577,3 +577,138 @@ def test_polish_stays_within_its_margin_of_the_exact_projection():
                 assert np.abs(xp - x_ex).max() <= 8 * M, (np.abs(xp - x_ex).max() / M)
                 near += 1
     assert interior > 20 and near > 60
+
+
+# --------------------------------------------------------------------------- equalities
+def exact_projection_eq(y, lo, hi, A, c, eq):
+    """argmin ||x - y||^2 s.t. lo <= x <= hi, A_k x <= c_k, and A_k x = c_k where eq[k]:
+    active-set enumeration (KKT) with the equality rows always active and their
+    multipliers of either sign."""
+    n = len(y)
+    rows = []
+    for i in range(n):
+        e = np.zeros(n)
+        e[i] = 1
+        rows.append((e, hi[i], False))
+        rows.append((-e, -lo[i], False))
+    for k in range(len(c)):
+        rows.append((A[k], c[k], bool(eq[k])))
+    always = [k for k, r in enumerate(rows) if r[2]]
+    optional = [k for k, r in enumerate(rows) if not r[2]]
+    best, best_d = None, np.inf
+    for r in range(0, n + 1 - len(always)):
+        for extra in itertools.combinations(optional, r):
+            act = list(always) + list(extra)
+            G = np.array([rows[k][0] for k in act]).reshape(len(act), n)
+            h = np.array([rows[k][1] for k in act])
+            M = G @ G.T
+            if abs(np.linalg.det(M)) < 1e-12:
+                continue
+            lam = np.linalg.solve(M, G @ y - h)
+            if any(lam[t] < -1e-12 for t in range(len(always), len(act))):
+                continue
+            x = y - G.T @ lam
+            ok = all((abs(rows[k][0] @ x - rows[k][1]) <= 1e-9) if rows[k][2] else (rows[k][0] @ x <= rows[k][1] + 1e-9)
+                     for k in range(len(rows)))
+            if ok and np.linalg.norm(x - y) < best_d:
+                best, best_d = x, np.linalg.norm(x - y)
+    return best
+
+
+def test_dykstra_with_hyperplanes_matches_exact_qp():
+    """Prop. QP with equality unit atoms: Dykstra's sweeps treat an equality as a
+    hyperplane (its multiplier not clamped at zero) and converge to the Euclidean
+    projection onto box, half-spaces and hyperplanes, against an active-set
+    enumeration in which the equality rows are always active."""
+    rng = np.random.default_rng(3)
+    checked = 0
+    for _ in range(30):
+        n = 4
+        B = W._Builder(0, n)
+        A, c, eq = [], [], []
+        for k in range(3):
+            var = rng.choice(n, 2, replace=False)
+            coef = rng.integers(1, 3, 2) * rng.choice([-1, 1], 2)
+            q0 = int(rng.integers(-2, 3))
+            rel = W.EQ if k == 0 else W.LE
+            B.con(W.OR, [W.lit(B.atom(var, coef, q0, rel))])
+            row = np.zeros(n)
+            row[var] = coef
+            A.append(row)
+            c.append(q0)
+            eq.append(rel == W.EQ)
+        lo, hi = np.full(n, -5.0), np.full(n, 5.0)
+        inst = B.freeze("eq", lo, hi, [], np.zeros(n), 1.0)
+        dom = pgd.Domain(inst)
+        assert dom.eq == [True, False, False]
+        Y = rng.uniform(-7, 7, (n, 4))
+        X = dom.project_b(Y, sweeps=4000, polish=0)
+        for r in range(Y.shape[1]):
+            x_ex = exact_projection_eq(Y[:, r], lo, hi, np.array(A), np.array(c, float), eq)
+            if x_ex is None:
+                continue
+            np.testing.assert_allclose(X[:, r], x_ex, atol=1e-7)
+            checked += 1
+    assert checked > 60
+
+
+def test_polish_returns_points_to_the_hyperplanes():
+    """No-wait jobs (each precedence an equality) from points near the plant: after the
+    projection every equality's residual is within its FP32 band (eq_band), every
+    inequality unit atom holds exactly, and the repair then makes the equalities hold
+    exactly while moving no real by more than a few bands."""
+    inst = W.jobshop(1002, 8, 5, no_wait=3)
+    dom = pgd.Domain(inst)
+    rng = np.random.default_rng(9)
+    y = (inst.planted_y[:, None] + rng.normal(0, 0.5, (inst.n_real, 16))).astype(np.float32).astype(np.float64)
+    x = dom.project_b(y, 20, 32).astype(np.float32).astype(np.float64)
+    unit = [c for c in range(inst.n_cons) if OBJ.is_unit_atomic(inst, c)]
+    for r in range(16):
+        for (var, q, q0), e in zip(dom.halfspaces, dom.eq):
+            v = float((q * x[var, r]).sum() - q0)
+            mag = abs(q0) + float(np.abs(q * x[var, r]).sum())
+            if e:
+                assert abs(v) <= 4 * pgd.eq_band(len(var), mag), (r, v)
+        ineq = [c for c in unit if inst.atom((int(inst.lits(c)[0]) >> 1) - inst.n_bool)[3] != W.EQ]
+        _, viol = pgd.round_check(inst, np.zeros((inst.n_bool, 1)), x[:, r:r + 1], constraints=ineq)
+        assert not viol[ineq].any()
+        rep = pgd.repair_equalities(inst, x[:, r])
+        assert rep is not None
+        for c in unit:
+            var, coef, q0, rel = inst.atom((int(inst.lits(c)[0]) >> 1) - inst.n_bool)
+            if rel == W.EQ:
+                assert sum(Fraction(int(q)) * rep[int(v)] for v, q in zip(var, coef)) == q0
+        assert max(abs(float(a_) - b_) for a_, b_ in zip(rep, x[:, r])) <= 1e-3
+
+
+def test_repair_equalities_cases():
+    """The repair solves each equality that does not hold for its last real with
+    coefficient +-1 not yet used: chains are solved in order; an equality with no such
+    real, or a later pivot that breaks an earlier equality, gives None."""
+    def inst_of(eqs, n=3):
+        B = W._Builder(0, n)
+        for var, coef, q0 in eqs:
+            B.con(W.OR, [W.lit(B.atom(var, coef, q0, W.EQ))])
+        return B.freeze("r", np.full(n, -9.0), np.full(n, 9.0), [], np.zeros(n), 1.0)
+    chain = inst_of([([0, 1], [1, -1], -2), ([1, 2], [1, -1], -3)])     # y1 = y0 + 2, y2 = y1 + 3
+    rep = pgd.repair_equalities(chain, [0.5, 2.4999999, 0.0])
+    assert rep == [Fraction(1, 2), Fraction(5, 2), Fraction(11, 2)]
+    assert pgd.repair_equalities(inst_of([([0, 1], [2, 3], 5)]), [1.0, 0.9, 0.0]) is None   # no +-1 real
+    assert pgd.repair_equalities(inst_of([([0, 1], [2, 3], 5)]), [1.0, 1.0, 0.0]) == [1, 1, 0]  # holds: kept
+    broken = inst_of([([0, 1], [1, 1], 1), ([1, 2], [1, 1], 2), ([0, 1], [-1, 1], 0)])
+    assert pgd.repair_equalities(broken, [0.0, 0.3, 0.1]) is None
+    one = inst_of([([0], [3], 7)])                                        # 3 y0 = 7: pinned, no float fits
+    dom = pgd.Domain(one)
+    assert dom.lo[0] == dom.hi[0] == 7 / 3
+
+
+def test_equalities_only_as_projected_unit_atoms():
+    """A negated equality (a disequality) is not a convex set and cannot be projected
+    onto; an equality has no relaxed form for C_sigma (its smoothed probability is 0)."""
+    B = W._Builder(0, 2)
+    B.con(W.OR, [W.lit(B.atom([0, 1], [1, -1], 0, W.EQ), True)])
+    inst = B.freeze("ne", np.zeros(2), np.ones(2), [], np.zeros(2), 1.0)
+    with pytest.raises(ValueError):
+        pgd.Domain(inst)
+    with pytest.raises(ValueError):
+        S.normalized_atom([1, -1], 0, S.EQ)

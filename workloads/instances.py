@@ -11,7 +11,7 @@ Conventions (shared by every consumer):
     true and neg == 0, or when it is false and neg == 1.
   * A Boolean value x is +-1 with -1 meaning TRUE (the paper's convention, Cor. 1).
   * An atom is ``sum_j coef_j * y_j  rel  q0`` with integer coefficients and
-    rel in {LE, LT, GE, GT}.
+    rel in {LE, LT, GE, GT, EQ}; an EQ atom appears only as a unit constraint.
   * Constraint kinds (the Boolean function of the literal truth values):
       OR      at least one literal true
       XOR     an odd number of literals true
@@ -35,7 +35,7 @@ import numpy as np
 OR, XOR, CARD_LE, NAE, MUX, NEQ_OR = 0, 1, 2, 3, 4, 5
 KIND_NAMES = {OR: "OR", XOR: "XOR", CARD_LE: "CARD_LE", NAE: "NAE", MUX: "MUX", NEQ_OR: "NEQ_OR"}
 # atom relations
-LE, LT, GE, GT = 0, 1, 2, 3
+LE, LT, GE, GT, EQ = 0, 1, 2, 3, 4
 
 
 @dataclass
@@ -201,8 +201,12 @@ def tiny_random(seed: int = 1001, n_bool=20, n_real=10, n_cons=200, width=3) -> 
 # ---------------------------------------------------------------------------
 # Job-shop scheduling with Boolean order selectors
 # ---------------------------------------------------------------------------
-def _jobshop_into(B: _Builder, rng, n_jobs, n_mach, dur_max, bool_base, real_base, px, py):
-    """Adds one job-shop instance to builder B.  Returns (horizon, n_bool_used, n_real_used)."""
+def _jobshop_into(B: _Builder, rng, n_jobs, n_mach, dur_max, bool_base, real_base, px, py, no_wait=0):
+    """Adds one job-shop instance to builder B.  Returns (horizon, n_bool_used, n_real_used).
+
+    no_wait: the last no_wait jobs run without waits between their operations (each
+    precedence an equality s_k + d_k = s_{k+1}); the plant then runs them one after
+    another after every other job."""
     order = [rng.permutation(n_mach) for _ in range(n_jobs)]
     dur = rng.integers(1, dur_max + 1, (n_jobs, n_mach))
     sidx = lambda j, k: real_base + j * n_mach + k  # real var of the k-th operation of job j
@@ -216,6 +220,13 @@ def _jobshop_into(B: _Builder, rng, n_jobs, n_mach, dur_max, bool_base, real_bas
             s = max(job_ready[j], mach_ready[mch])
             start[j, k] = s
             job_ready[j] = mach_ready[mch] = s + dur[j, k]
+    if no_wait:
+        t = int(job_ready[:n_jobs - no_wait].max()) if n_jobs > no_wait else 0
+        for j in range(n_jobs - no_wait, n_jobs):
+            for k in range(n_mach):
+                start[j, k] = t
+                t += int(dur[j, k])
+            job_ready[j] = t
     H = int(math.ceil(1.2 * int(job_ready.max())))
     for j in range(n_jobs):
         for k in range(n_mach):
@@ -227,10 +238,11 @@ def _jobshop_into(B: _Builder, rng, n_jobs, n_mach, dur_max, bool_base, real_bas
             B.con(OR, [lit(a0)])
             a1 = B.atom([sidx(j, k)], [1], H - int(dur[j, k]), LE)
             B.con(OR, [lit(a1)])
-    # precedence along each job: s_k + d_k <= s_{k+1}
+    # precedence along each job: s_k + d_k <= s_{k+1} (= for the no-wait jobs)
     for j in range(n_jobs):
         for k in range(n_mach - 1):
-            a = B.atom([sidx(j, k), sidx(j, k + 1)], [1, -1], -int(dur[j, k]), LE)
+            rel = EQ if j >= n_jobs - no_wait else LE
+            a = B.atom([sidx(j, k), sidx(j, k + 1)], [1, -1], -int(dur[j, k]), rel)
             B.con(OR, [lit(a)])
     # same-machine pairs with an order selector o: o -> (i before j), not o -> (j before i)
     ops_on = [[] for _ in range(n_mach)]
@@ -255,14 +267,14 @@ def _jobshop_into(B: _Builder, rng, n_jobs, n_mach, dur_max, bool_base, real_bas
     return H, nb, n_jobs * n_mach
 
 
-def jobshop(seed: int = 1002, n_jobs=40, n_mach=10, dur_max=20) -> Instance:
+def jobshop(seed: int = 1002, n_jobs=40, n_mach=10, dur_max=20, no_wait=0) -> Instance:
     rng = np.random.default_rng(seed)
     n_bool = n_mach * n_jobs * (n_jobs - 1) // 2
     n_real = n_jobs * n_mach
     B = _Builder(n_bool, n_real)
     px = np.ones(n_bool, np.int8)
     py = np.zeros(n_real)
-    H, nb, nr = _jobshop_into(B, rng, n_jobs, n_mach, dur_max, 0, 0, px, py)
+    H, nb, nr = _jobshop_into(B, rng, n_jobs, n_mach, dur_max, 0, 0, px, py, no_wait)
     assert nb == n_bool and nr == n_real
     lo = np.zeros(n_real)
     hi = np.full(n_real, float(H))
