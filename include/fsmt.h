@@ -48,8 +48,11 @@ typedef enum {
   FSMT_ESTATE = -6    /* call out of order (e.g. device call before fsmt_upload) */
 } fsmt_status;
 
-/* atom relations: sum_j coef_j y_j  rel  q0 */
-enum { FSMT_LE = 0, FSMT_LT = 1, FSMT_GE = 2, FSMT_GT = 3 };
+/* atom relations: sum_j coef_j y_j  rel  q0 (Results "Satisfiability Modulo Theories").
+ * An equality (FSMT_EQ) has probability 0 under Gaussian smoothing, so it is accepted
+ * only as the positive literal of a unit constraint that the projection enforces
+ * (fsmt_compile with FSMT_UNIT_PROJECT); see fsmt_compile and fsmt_repair_equalities. */
+enum { FSMT_LE = 0, FSMT_LT = 1, FSMT_GE = 2, FSMT_GT = 3, FSMT_EQ = 4 };
 
 /* constraint kinds (the Boolean function of the literals' truth values)
  *   OR      at least one literal true
@@ -123,7 +126,7 @@ fsmt_status fsmt_set_real_bounds(fsmt_problem* p, int32_t j, double lo, double h
 /* Adds the atom sum_{t<nnz} coef[t] * y_{var[t]}  rel  q0 (host arrays of length
  * nnz >= 1) and writes its atom index (0-based, its literal id is n_bool + index)
  * to *atom_id_out.  EINVAL if a var is out of range or repeated, a coefficient is
- * 0 or |coef| >= 2^24, |q0| >= 2^53, or rel is not one of FSMT_LE..FSMT_GT.
+ * 0 or |coef| >= 2^24, |q0| >= 2^53, or rel is not one of FSMT_LE..FSMT_EQ.
  * (The bounds make every coefficient exact in FP32 and q0 exact in FP64, which
  * the exact check relies on.) */
 fsmt_status fsmt_add_atom(fsmt_problem* p, int32_t nnz, const int32_t* var, const int64_t* coef,
@@ -160,6 +163,17 @@ void fsmt_free_problem(fsmt_problem* p);
 fsmt_status fsmt_verify_exact(const fsmt_problem* p, const int8_t* x, const double* y,
                               int32_t* sat_out, int32_t* first_violated_out);
 
+/* Exact repair of reals y[n_real] (host, in place) so that every projected equality
+ * unit atom holds exactly, before fsmt_verify_exact: the projection leaves a point on
+ * a hyperplane only within FP32 rounding.  In constraint order, an equality that does
+ * not already hold is solved for its pivot -- the last of its reals with coefficient
+ * +-1 that no earlier equality used as pivot -- as y_p = (q0 - sum_{j != p} q_j y_j) / q_p,
+ * computed exactly.  Writes 1 to *ok_out when every equality then holds exactly, else 0
+ * (an equality with no such real, a pivot value that a double cannot hold exactly, or
+ * a later pivot that broke an earlier equality); y is written either way.  Problems
+ * without equalities leave y unchanged with *ok_out = 1.  EINVAL on NULL pointers. */
+fsmt_status fsmt_repair_equalities(const fsmt_problem* p, double* y, int32_t* ok_out);
+
 /* --------------------------------------------------------------- compile --
  * Compiles every constraint to a reduced ordered xBDD (Def. xBDD: atoms are
  * propositional inputs, no LP pruning; Suppl. Note "Decision Diagrams"), variable
@@ -167,8 +181,16 @@ fsmt_status fsmt_verify_exact(const fsmt_problem* p, const int8_t* x, const doub
  * order with the TRUE / FALSE terminals last.  With FSMT_UNIT_PROJECT, unit atomic
  * constraints leave the objective: single-variable ones tighten the box (bounds
  * rounded inward to FP32 so that a clamped value satisfies the atom exactly),
- * multi-variable ones become half-spaces of the projection (Prop. QP).  The
- * problem may be freed afterwards.  EINVAL if a diagram has more than 65,533
+ * multi-variable ones become half-spaces of the projection (Prop. QP).  A
+ * single-variable equality pins its real (both bounds rounded inward: an empty box
+ * when FP32 cannot hold the value); a multi-variable equality becomes a hyperplane of
+ * the projection (Dykstra's multiplier unclamped; the polish returns points to it
+ * within the FP32 band of an n-term dot product), and the exact check on the device
+ * counts it as holding within the polish margin 2^-16 (|q0| + sum |q_j y_j|), a candidate
+ * filter for fsmt_repair_equalities and fsmt_verify_exact on the host.  The
+ * problem may be freed afterwards.  EINVAL if an equality atom appears anywhere but
+ * as the positive literal of a unit constraint under FSMT_UNIT_PROJECT, if a diagram has
+ * more than 65,533
  * decision nodes, the total exceeds 2^31 - 1 nodes, or a block of reals coupled
  * by half-spaces needs more than one CTA's shared memory in the projection:
  * 4 * ((2 nv + nh) * 32 + (nh + 1) + 2 nnz + 2 nh + 2 nv) bytes > 225 KB for a block of

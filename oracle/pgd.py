@@ -78,6 +78,15 @@ class Config:
 POLISH_MARGIN = 2.0 ** -16
 
 
+def eq_holds_on_device(var, coef, q0, y):
+    """The device check's rule for a projected equality at reals y: it counts as holding
+    when |q.y - q0| <= 2^-16 (|q0| + sum |q_j y_j|), the polish margin (a candidate
+    filter: the exact repair and check on the host decide SAT)."""
+    z = sum(Fraction(int(q)) * Fraction(float(y[int(v)])) for v, q in zip(var, coef)) - int(q0)
+    mag = abs(int(q0)) + sum(abs(float(q) * float(y[int(v)])) for v, q in zip(var, coef))
+    return abs(float(z)) <= POLISH_MARGIN * mag
+
+
 def eq_band(n, mag):
     """The band within which an equality's residual q.y - q0 is taken as zero in FP32:
     (n + 4) (u mag + 2^-126-ish), u = 2^-24, mag = |q0| + sum |q_j y_j| over its n

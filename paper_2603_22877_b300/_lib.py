@@ -11,7 +11,7 @@ LIB_PATH = os.path.join(HERE, "libfsmt.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENAN, ESTATE = 0, -1, -2, -3, -4, -5, -6
 STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "ENAN", -6: "ESTATE"}
-LE, LT, GE, GT = 0, 1, 2, 3
+LE, LT, GE, GT, EQ = 0, 1, 2, 3, 4
 OR, XOR, CARD_LE, NAE, MUX, NEQ_OR = 0, 1, 2, 3, 4, 5
 UNIT_PROJECT, UNIT_SOFT = 0, 1
 
@@ -69,6 +69,7 @@ PROTOTYPES = {
     "fsmt_add_constraints": [P, i32, P, P, P, P],
     "fsmt_free_problem": [P],
     "fsmt_verify_exact": [P, P, P, C.POINTER(i32), C.POINTER(i32)],
+    "fsmt_repair_equalities": [P, P, C.POINTER(i32)],
     "fsmt_compile": [P, i32, C.POINTER(P)],
     "fsmt_compiled_info": [P, C.POINTER(Info)],
     "fsmt_get_diagrams": [P, P, P, P, P, P, P],

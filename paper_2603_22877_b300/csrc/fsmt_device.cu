@@ -109,6 +109,11 @@ __device__ __forceinline__ bool literal_truth_exact(const DevView& d, int lab, i
     z = fmaf(c, y, z);
     mag = fmaf(fabsf(c), fabsf(y), mag);
   }
+  // an equality (a projected unit atom) counts as holding within the projection's polish
+  // margin, 2^-16 (|q0| + sum |q_j y_j|): FP32 reals rarely meet a hyperplane exactly, the
+  // polish leaves them within a few FP32 bands of it, and the host repairs them exactly
+  // before its verification
+  if (__ldg(d.atom_strict + i) == 2) return fabsf(z) <= kPolishMargin * mag;
   const int f = atom_filter(z, mag, k1 - k0);
   if (f != 0) return f < 0;
   return atom_truth_exact_slow(d, lab, R, r, a, b);
@@ -524,8 +529,11 @@ __global__ void k_round_check(DevView d, int R, const float* __restrict__ a, con
 // (x = sgn(a), exact atoms) once, as one 32-bit word over the tile's restarts;
 // (B) one thread per constraint evaluates its diagram bottom up on those words
 // (node value = (holds & value(hi)) | (~holds & value(lo)), literal space), all
-// 32 restarts at once; (C) one warp per constraint applies the ERWA update as
-// k_round_check does.
+// 32 restarts at once, keeps the constraint's violation word of the tile, and the
+// tile's #Unsat is counted from those words; (C) once every tile of the chunk is
+// walked, each warp streams whole rows of w and h (one constraint, every restart,
+// four restarts a lane per vector access when R is a multiple of 4) and applies the
+// ERWA update as k_round_check does.
 constexpr int kCheckThreads = 512;
 __global__ void __launch_bounds__(kCheckThreads, 3)
     k_check_chunked(DevView d, int R, int vcap, const float* __restrict__ a, const float* __restrict__ b,
@@ -543,8 +551,8 @@ __global__ void __launch_bounds__(kCheckThreads, 3)
   float* s_b = s_tcoef + kChunkMaxTerms;                              // [real][32]: b of the tile
   unsigned* s_t = reinterpret_cast<unsigned*>(s_b + kChunkMaxReals * 32);  // [slot]: the literal holds, bit per restart
   unsigned* s_val = s_t + kChunkMaxSlots;                                   // [node]: the node's value, bit per restart
-  unsigned* s_u = s_val + kChunkMaxNodes;                                   // [constraint]: violated, bit per restart
-  int* cnt_s = reinterpret_cast<int*>(s_u + kChunkMaxCons);
+  int* cnt_s = reinterpret_cast<int*>(s_val + kChunkMaxNodes);            // [R]: #Unsat of the CTA's chunks
+  unsigned* s_u = reinterpret_cast<unsigned*>(cnt_s + R);                   // [tile][constraint]: violated bits
   for (int r = threadIdx.x; r < R; r += blockDim.x) cnt_s[r] = 0;
   if (prm) {
     rho = prm[P_RHO];
@@ -629,36 +637,62 @@ __global__ void __launch_bounds__(kCheckThreads, 3)
           }
           holds_c = val[0];
         }
-        s_u[c] = ~holds_c & valid;
+        s_u[t * kChunkMaxCons + c] = ~holds_c & valid;
       }
       __syncthreads();
-      for (int c0 = warp; c0 < nc; c0 += 4 * W) {  // (C), four constraints' loads in flight together
-        size_t k[4];
-        float h0[4], w0[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int c = c0 + j * W;
-          const bool live = ok && c < nc;
-          k[j] = live ? (size_t)s_con[c].w * R + r : 0;
-          h0[j] = (h && live) ? h[k[j]] : 0.f;
-          w0[j] = (h && live && update_w) ? w[k[j]] : 0.f;
+      if (threadIdx.x < 32 && ok) {  // the tile's #Unsat over the chunk, from the words
+        int cnt = 0;
+        for (int c = 0; c < nc; ++c) cnt += (int)((s_u[t * kChunkMaxCons + c] >> lane) & 1u);
+        cnt_s[r] += cnt;
+      }
+    }
+    __syncthreads();
+    // (C) per constraint, every restart: u, then h <- rho h + u and, on update, w <- w gamma^h, h <- 1
+    auto erwa = [&](size_t k, int rr, int u) {
+      if (viol) viol[k] = (uint8_t)u;
+      if (h) {
+        float hh = fmaf(rho, h[k], (float)u);
+        if (update_w) {
+          w[k] = w[k] * exp2f(hh * lg) * erwa_scale(d, wsum, prm, rr, true);
+          hh = 1.f;
         }
+        h[k] = hh;
+      }
+    };
+    if ((R & 3) == 0) {  // rows 16-byte aligned: four restarts per lane and access
+      for (int c = warp; c < nc; c += W) {
+        const size_t row = (size_t)s_con[c].w * R;
+        for (int r4 = 4 * lane; r4 < R; r4 += 128) {
+          const unsigned bits = (s_u[(r4 >> 5) * kChunkMaxCons + c] >> (r4 & 31)) & 15u;
+          const size_t k = row + r4;
+          if (viol)
+            *reinterpret_cast<uchar4*>(viol + k) =
+                make_uchar4(bits & 1u, (bits >> 1) & 1u, (bits >> 2) & 1u, (bits >> 3) & 1u);
+          if (!h) continue;
+          float4 hv = *reinterpret_cast<const float4*>(h + k);
+          float hs[4] = {hv.x, hv.y, hv.z, hv.w}, ws[4];
+          if (update_w) {
+            const float4 wv = *reinterpret_cast<const float4*>(w + k);
+            ws[0] = wv.x, ws[1] = wv.y, ws[2] = wv.z, ws[3] = wv.w;
+          }
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int c = c0 + j * W;
-          if (!ok || c >= nc) continue;
-          const int u = (int)((s_u[c] >> lane) & 1u);
-          if (viol) viol[k[j]] = (uint8_t)u;
-          if (u) atomicAdd(cnt_s + r, 1);
-          if (h) {
-            float hh = fmaf(rho, h0[j], (float)u);
+          for (int j = 0; j < 4; ++j) {
+            float hh = fmaf(rho, hs[j], (float)((bits >> j) & 1u));
             if (update_w) {
-              w[k[j]] = w0[j] * exp2f(hh * lg) * erwa_scale(d, wsum, prm, r, true);
+              ws[j] = ws[j] * exp2f(hh * lg) * erwa_scale(d, wsum, prm, r4 + j, true);
               hh = 1.f;
             }
-            h[k[j]] = hh;
+            hs[j] = hh;
           }
+          *reinterpret_cast<float4*>(h + k) = make_float4(hs[0], hs[1], hs[2], hs[3]);
+          if (update_w) *reinterpret_cast<float4*>(w + k) = make_float4(ws[0], ws[1], ws[2], ws[3]);
         }
+      }
+    } else {
+      for (int c = warp; c < nc; c += W) {
+        const size_t row = (size_t)s_con[c].w * R;
+        for (int rr = lane; rr < R; rr += 32)
+          erwa(row + rr, rr, (int)((s_u[(rr >> 5) * kChunkMaxCons + c] >> (rr & 31)) & 1u));
       }
     }
   }
@@ -911,7 +945,8 @@ fsmt_status launch_round_check(const Compiled& C, int R, const float* a, const f
   }
   // constraints of C_sigma over the chunk schedule (when it exists), the rest one warp each
   int s_begin = 0;
-  const size_t csmem = (size_t)kChunkMaxNodes * (8 + 4) + (size_t)kChunkMaxCons * (16 + 4) +
+  const size_t csmem = (size_t)kChunkMaxNodes * (8 + 4) + (size_t)kChunkMaxCons * 16 +
+                       (size_t)((R + 31) / 32) * kChunkMaxCons * 4 +
                        (size_t)kChunkMaxSlots * (12 + 4) + (size_t)kChunkMaxTerms * 8 +
                        (size_t)kChunkMaxReals * 32 * 4 + (size_t)R * sizeof(int);
   if (C.chunked_ok && C.n_chunks > 0 && csmem <= kSmemMax) {
@@ -971,7 +1006,8 @@ fsmt_status fsmt_upload(fsmt_compiled* cc, void* stream) {
                o_cv = push_array(blob, C.comp_var), o_chp = push_array(blob, C.comp_hs_ptr),
                o_hsp = push_array(blob, C.hs_ptr), o_hsl = push_array(blob, C.hs_lvar),
                o_hsc = push_array(blob, C.hs_coef), o_hsq = push_array(blob, C.hs_q0),
-               o_hsi = push_array(blob, C.hs_inv_qq), o_csh = push_array(blob, C.comp_shape);
+               o_hsi = push_array(blob, C.hs_inv_qq), o_csh = push_array(blob, C.comp_shape),
+               o_hse = push_array(blob, C.hs_eq);
   std::vector<uint2> cnodes(C.cnode_slot.size());
   for (size_t i = 0; i < cnodes.size(); ++i) cnodes[i] = make_uint2(C.cnode_slot[i], C.cnode_hilo[i]);
   const size_t o_ccp = push_array(blob, C.chunk_con_ptr), o_ccon = push_array(blob, C.ccon),
@@ -1024,6 +1060,7 @@ fsmt_status fsmt_upload(fsmt_compiled* cc, void* stream) {
   v.hs_q0 = (const float*)(base + o_hsq);
   v.hs_inv_qq = (const float*)(base + o_hsi);
   v.comp_shape = (const int32_t*)(base + o_csh);
+  v.hs_eq = (const uint8_t*)(base + o_hse);
   v.n_chunks = C.n_chunks;
   v.chunk_slot_cap = C.chunk_slot_cap;
   v.chunk_real_cap = 0;  // set per launch

@@ -30,9 +30,10 @@ constexpr int kMaxNodesPerDiagram = 65533;  // hi/lo are 16-bit and V, V+1 are t
 // at most nv reals, nh half-spaces and nnz nonzeros over a block's half-spaces, wy
 // warps per CTA: per thread the block's iterate, box corrections and half-space
 // multipliers; per warp the staged block (offsets, local reals, coefficients,
-// right-hand sides, 1/||q||^2, the box).  A block is accepted when one warp's CTA fits.
+// right-hand sides, 1/||q||^2, the box, the equality flags).  A block is accepted when one
+// warp's CTA fits.
 FSMT_HD long proj_block_words(long nv, long nh, long nnz, long wy) {
-  return (2 * nv + nh) * 32 * wy + wy * ((nh + 1) + 2 * nnz + 2 * nh + 2 * nv);
+  return (2 * nv + nh) * 32 * wy + wy * ((nh + 1) + 2 * nnz + 3 * nh + 2 * nv);
 }
 constexpr long kProjSmemWords = (227 * 1024 - 2048) / 4;  // a CTA's dynamic shared memory, 2 KB left for static
 // chunks of the chunked forward/adjoint kernel
@@ -68,7 +69,7 @@ struct DevView {
   const float* atom_q0f;        // q0 rounded to FP32 (relaxation only)
   const double* atom_q0d;       // q0 exact (|q0| < 2^53), for the exact check
   const float* atom_inv_norm;   // 1 / ||q||_2
-  const uint8_t* atom_strict;
+  const uint8_t* atom_strict;   // 1: strict (<), 2: equality (=, projected unit atoms only), else 0
   // projection
   const float* lo;
   const float* hi;
@@ -83,6 +84,7 @@ struct DevView {
   const float* hs_coef;
   const float* hs_q0;
   const float* hs_inv_qq;       // 1 / ||q||^2
+  const uint8_t* hs_eq;         // 1: the entry is an equality's hyperplane q.y = q0
   const int32_t* comp_shape;    // [n_comp] rank of the block's generated projection routine (0: none)
   // chunked schedule of the constraints of C_sigma
   int32_t n_chunks;

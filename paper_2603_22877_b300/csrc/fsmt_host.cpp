@@ -26,7 +26,7 @@ static fsmt_status fail(fsmt_status s, const std::string& msg) {
 static fsmt_status check_atom(const Problem& P, int32_t nnz, const int32_t* var, const int64_t* coef, int64_t q0,
                               int32_t rel) {
   if (nnz < 1) return fail(FSMT_EINVAL, "atom with no variables");
-  if (rel < FSMT_LE || rel > FSMT_GT) return fail(FSMT_EINVAL, "unknown atom relation");
+  if (rel < FSMT_LE || rel > FSMT_EQ) return fail(FSMT_EINVAL, "unknown atom relation");
   if (q0 >= (int64_t(1) << 53) || q0 <= -(int64_t(1) << 53)) return fail(FSMT_EINVAL, "|q0| must be below 2^53");
   for (int t = 0; t < nnz; ++t) {
     if (var[t] < 0 || var[t] >= P.n_real) return fail(FSMT_EINVAL, "atom variable out of range");
@@ -506,6 +506,7 @@ static void select_proj_shapes(Compiled& C) {
     for (int q = h0; q < h0 + nh; ++q) {
       const int32_t n = C.hs_ptr[q + 1] - C.hs_ptr[q];
       key.append(reinterpret_cast<const char*>(&n), sizeof(n));
+      key.push_back((char)C.hs_eq[q]);
       for (int e = C.hs_ptr[q]; e < C.hs_ptr[q + 1]; ++e) {
         key.append(reinterpret_cast<const char*>(&C.hs_lvar[e]), sizeof(int32_t));
         key.append(reinterpret_cast<const char*>(&C.hs_coef[e]), sizeof(float));
@@ -579,6 +580,18 @@ static fsmt_status compile(const Problem& P, int policy, Compiled& C) {
   C.n_atoms = P.n_atoms();
   C.n_cons = P.n_cons();
   const int n_cons = C.n_cons;
+  // an equality atom only as the positive literal of a unit constraint that the
+  // projection enforces: Gaussian smoothing gives it probability 0 in C_sigma, and its
+  // negation is not a convex set
+  for (int c = 0; c < n_cons; ++c)
+    for (int64_t t = P.con_ptr[c]; t < P.con_ptr[c + 1]; ++t) {
+      const int32_t l = P.con_lits[t];
+      if ((l >> 1) < P.n_bool || P.atom_rel[(l >> 1) - P.n_bool] != FSMT_EQ) continue;
+      if (!(policy == FSMT_UNIT_PROJECT && is_unit_atomic(P, c) && (l & 1) == 0))
+        return fail(FSMT_EINVAL, "constraint " + std::to_string(c) +
+                                     ": an equality atom is accepted only as the positive literal of a unit "
+                                     "constraint under FSMT_UNIT_PROJECT");
+    }
   // schedule: constraints of C_sigma first (original order), then the projected ones
   std::vector<int> sched;
   std::vector<int> projected;
@@ -651,7 +664,7 @@ static fsmt_status compile(const Problem& P, int policy, Compiled& C) {
   for (int i = 0; i < K; ++i) {
     const int rel = P.atom_rel[i];
     const bool flip = rel == FSMT_GE || rel == FSMT_GT;
-    C.atom_strict[i] = (rel == FSMT_LT || rel == FSMT_GT) ? 1 : 0;
+    C.atom_strict[i] = rel == FSMT_EQ ? 2 : (rel == FSMT_LT || rel == FSMT_GT) ? 1 : 0;  // 2: equality
     C.atom_ptr[i + 1] = (int32_t)P.atom_ptr[i + 1];
     double nn = 0.0;
     for (int64_t t = P.atom_ptr[i]; t < P.atom_ptr[i + 1]; ++t) {
@@ -682,12 +695,39 @@ static fsmt_status compile(const Problem& P, int policy, Compiled& C) {
     std::vector<int32_t> var;
     std::vector<int64_t> coef;
     int64_t q0;
+    bool eq = false;  // a hyperplane q.y = q0 (an equality unit atom)
   };
   std::vector<HS> hs;
   for (int c : projected) {  // ascending constraint id
     int32_t l = P.con_lits[P.con_ptr[c]];
     int i = (l >> 1) - P.n_bool;
     const int rel = P.atom_rel[i];
+    if (rel == FSMT_EQ) {  // positive (checked above): pin one real, or a hyperplane
+      const int64_t b = P.atom_ptr[i], e = P.atom_ptr[i + 1];
+      if (e - b == 1) {
+        const int j = P.atom_var[b];
+        const int64_t cj = P.atom_coef[b], q0 = P.atom_q0[i];
+        // both sides rounded inward: the box is the value when FP32 holds it, else empty
+        const float up = inward_bound(cj, q0, false), dn = inward_bound(-cj, -q0, false);
+        if (cj > 0) {
+          C.hi[j] = std::min(C.hi[j], up);
+          C.lo[j] = std::max(C.lo[j], dn);
+        } else {
+          C.lo[j] = std::max(C.lo[j], up);
+          C.hi[j] = std::min(C.hi[j], dn);
+        }
+      } else {
+        HS h;
+        for (int64_t t = b; t < e; ++t) {
+          h.var.push_back(P.atom_var[t]);
+          h.coef.push_back(P.atom_coef[t]);
+        }
+        h.q0 = P.atom_q0[i];
+        h.eq = true;
+        hs.push_back(std::move(h));
+      }
+      continue;
+    }
     const bool flip = rel == FSMT_GE || rel == FSMT_GT;
     bool strict = rel == FSMT_LT || rel == FSMT_GT;
     int64_t sgn = flip ? -1 : 1;
@@ -758,6 +798,7 @@ static fsmt_status compile(const Problem& P, int policy, Compiled& C) {
   C.hs_coef.clear();
   C.hs_q0.clear();
   C.hs_inv_qq.clear();
+  C.hs_eq.clear();
   C.comp_max_vars = C.comp_max_hs = C.comp_max_nnz = 0;
   for (size_t k = 0; k < comp_vars.size(); ++k) {
     long nnz = 0;
@@ -787,6 +828,7 @@ static fsmt_status compile(const Problem& P, int policy, Compiled& C) {
       C.hs_ptr.push_back((int32_t)C.hs_lvar.size());
       C.hs_q0.push_back((float)h.q0);
       C.hs_inv_qq.push_back((float)(1.0 / qq));
+      C.hs_eq.push_back(h.eq ? 1 : 0);
     }
     C.comp_hs_ptr.push_back((int32_t)(C.hs_ptr.size() - 1));
     C.comp_max_nnz = std::max<int32_t>(C.comp_max_nnz, C.hs_ptr.back() - C.hs_ptr[C.comp_hs_ptr[C.comp_hs_ptr.size() - 2]]);
@@ -835,7 +877,9 @@ static int cmp_mag(const Mag& a, const Mag& b) {
   return 0;
 }
 
-static int exact_sign_double(const Problem& P, int atom, const double* y) {
+// The exact value of sum_{t != skip} c_t y_t - q0 over atom's terms (skip: a term left
+// out, or -1), as positive and negative magnitudes in units of 2^kmin.
+static void exact_linear(const Problem& P, int atom, const double* y, int64_t skip, Mag& pos, Mag& neg, int& kmin) {
   struct Term {
     unsigned __int128 mag;
     int exp;
@@ -843,6 +887,7 @@ static int exact_sign_double(const Problem& P, int atom, const double* y) {
   };
   std::vector<Term> terms;
   for (int64_t t = P.atom_ptr[atom]; t < P.atom_ptr[atom + 1]; ++t) {
+    if (t == skip) continue;
     double v = y[P.atom_var[t]];
     if (v == 0.0) continue;
     int e;
@@ -855,12 +900,51 @@ static int exact_sign_double(const Problem& P, int atom, const double* y) {
   }
   int64_t q0 = P.atom_q0[atom];
   if (q0 != 0) terms.push_back({(unsigned __int128)(uint64_t)(q0 < 0 ? -q0 : q0), 0, q0 > 0});
-  if (terms.empty()) return 0;
-  int kmin = terms[0].exp;
+  kmin = 0;
+  if (terms.empty()) return;
+  kmin = terms[0].exp;
   for (auto& t : terms) kmin = std::min(kmin, t.exp);
-  Mag pos, neg;
   for (auto& t : terms) (t.neg ? neg : pos).add_shifted(t.mag, t.exp - kmin);
+}
+
+static int exact_sign_double(const Problem& P, int atom, const double* y) {
+  Mag pos, neg;
+  int kmin;
+  exact_linear(P, atom, y, -1, pos, neg, kmin);
   return cmp_mag(pos, neg);
+}
+
+// (pos - neg) * 2^kmin as a double, negated when `negate`; false when a double cannot
+// hold it exactly (more than 53 significant bits, or out of range).
+static bool exact_to_double(const Mag& pos, const Mag& neg, int kmin, bool negate, double* out) {
+  const int c = cmp_mag(pos, neg);
+  if (c == 0) {
+    *out = 0.0;
+    return true;
+  }
+  const Mag& big = c > 0 ? pos : neg;
+  const Mag& small = c > 0 ? neg : pos;
+  std::vector<uint32_t> d(big.w.size(), 0);
+  int64_t borrow = 0;
+  for (size_t i = 0; i < big.w.size(); ++i) {
+    int64_t v = (int64_t)big.w[i] - (i < small.w.size() ? (int64_t)small.w[i] : 0) - borrow;
+    borrow = v < 0 ? 1 : 0;
+    d[i] = (uint32_t)(v + (borrow << 32));
+  }
+  int hb = -1, lb = -1;
+  for (size_t i = 0; i < d.size(); ++i)
+    for (int bit = 0; bit < 32; ++bit)
+      if ((d[i] >> bit) & 1u) {
+        if (lb < 0) lb = (int)i * 32 + bit;
+        hb = (int)i * 32 + bit;
+      }
+  if (hb - lb + 1 > 53) return false;
+  uint64_t m = 0;
+  for (int b = hb; b >= lb; --b) m = (m << 1) | ((d[b / 32] >> (b % 32)) & 1u);
+  const double v = std::ldexp((double)m, kmin + lb);
+  if (!std::isfinite(v) || v == 0.0 || std::ldexp(v, -(kmin + lb)) != (double)m) return false;
+  *out = ((c > 0) != negate) ? v : -v;
+  return true;
 }
 
 static bool atom_true_exact(const Problem& P, int atom, const double* y) {
@@ -872,6 +956,8 @@ static bool atom_true_exact(const Problem& P, int atom, const double* y) {
       return s < 0;
     case FSMT_GE:
       return s >= 0;
+    case FSMT_EQ:
+      return s == 0;
     default:
       return s > 0;
   }
@@ -1024,6 +1110,45 @@ fsmt_status fsmt_add_constraints(fsmt_problem* p, int32_t count, const int8_t* k
   } catch (...) {
     return fail(FSMT_ENOMEM, "allocation failed");
   }
+  return FSMT_OK;
+}
+
+fsmt_status fsmt_repair_equalities(const fsmt_problem* p, double* y, int32_t* ok_out) {
+  if (!p || !y || !ok_out) return fail(FSMT_EINVAL, "NULL argument");
+  const Problem& P = p->p;
+  std::vector<int> eqs;  // the projected equality atoms, in constraint order
+  for (int c = 0; c < P.n_cons(); ++c) {
+    if (!is_unit_atomic(P, c)) continue;
+    const int32_t l = P.con_lits[P.con_ptr[c]];
+    const int i = (l >> 1) - P.n_bool;
+    if ((l & 1) == 0 && P.atom_rel[i] == FSMT_EQ) eqs.push_back(i);
+  }
+  std::vector<char> pivot(P.n_real, 0);
+  int ok = 1;
+  for (int i : eqs) {
+    if (exact_sign_double(P, i, y) == 0) continue;
+    int64_t tp = -1;  // the last real with coefficient +-1 not yet a pivot
+    for (int64_t t = P.atom_ptr[i]; t < P.atom_ptr[i + 1]; ++t)
+      if ((P.atom_coef[t] == 1 || P.atom_coef[t] == -1) && !pivot[P.atom_var[t]]) tp = t;
+    if (tp < 0) {
+      ok = 0;
+      continue;
+    }
+    // y_p = (q0 - sum_{t != p} c_t y_t) / c_p = -(sum_{t != p} c_t y_t - q0) * c_p, c_p = +-1
+    Mag pos, neg;
+    int kmin;
+    exact_linear(P, i, y, tp, pos, neg, kmin);
+    double v;
+    if (!exact_to_double(pos, neg, kmin, P.atom_coef[tp] > 0, &v)) {
+      ok = 0;
+      continue;
+    }
+    y[P.atom_var[tp]] = v;
+    pivot[P.atom_var[tp]] = 1;
+  }
+  for (int i : eqs)
+    if (exact_sign_double(P, i, y) != 0) ok = 0;
+  *ok_out = ok;
   return FSMT_OK;
 }
 

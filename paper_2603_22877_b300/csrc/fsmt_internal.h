@@ -58,6 +58,7 @@ struct Compiled {
   std::vector<int32_t> free_var;
   std::vector<int32_t> comp_var_ptr{0}, comp_var, comp_hs_ptr{0}, hs_ptr{0}, hs_lvar;
   std::vector<float> hs_coef, hs_q0, hs_inv_qq;
+  std::vector<uint8_t> hs_eq;  // 1: an equality's hyperplane, 0: a half-space
   int32_t comp_max_vars = 0, comp_max_hs = 0;  // the largest block's reals and half-spaces
   int32_t comp_max_nnz = 0;  // the most nonzeros over one block's half-spaces
   std::vector<int32_t> comp_shape;       // per block: rank of its generated projection routine (0: generic)

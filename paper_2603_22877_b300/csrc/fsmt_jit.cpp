@@ -249,7 +249,8 @@ std::string proj_routine(int rank, const Compiled& C, int c) {
     o << "    {\n      float dot = -s_q0[" << q << "];\n";
     for (int e = e0; e < e1; ++e)
       o << "      dot = proj_dot(" << flit(C.hs_coef[e]) << ", " << X(C.hs_lvar[e]) << ", h" << q << ", dot);\n";
-    o << "      const float tn = proj_tn(dot, " << flit(C.hs_inv_qq[h0 + q]) << ");\n";
+    o << "      const float tn = " << (C.hs_eq[h0 + q] ? "proj_tn_eq" : "proj_tn") << "(dot, "
+      << flit(C.hs_inv_qq[h0 + q]) << ");\n";
     o << "      const float dl = __fsub_rn(h" << q << ", tn);\n";
     for (int e = e0; e < e1; ++e)
       o << "      " << X(C.hs_lvar[e]) << " = fmaf(dl, " << flit(C.hs_coef[e]) << ", " << X(C.hs_lvar[e]) << ");\n";
@@ -267,6 +268,22 @@ std::string proj_routine(int rank, const Compiled& C, int c) {
     for (int e = e0; e < e1; ++e)
       o << "      { const float tm = __fmul_rn(" << flit(C.hs_coef[e]) << ", " << X(C.hs_lvar[e])
         << "); v = __fadd_rn(v, tm); mag = __fadd_rn(mag, fabsf(tm)); }\n";
+    if (C.hs_eq[h0 + q]) {  // a hyperplane: back onto it when off by more than the FP32 band
+      o << "      if (fabsf(v) > proj_eq_band(" << e1 - e0 << ", mag)) {\n        float qq = 0.f;\n";
+      for (int e = e0; e < e1; ++e) {
+        const int t = C.hs_lvar[e];
+        const float cf = C.hs_coef[e];
+        o << "        const bool n" << e - e0 << " = !(((v > 0.f) == " << (cf > 0.f ? "true" : "false") << ") ? "
+          << X(t) << " <= s_lo[" << t << "] : " << X(t) << " >= s_hi[" << t << "]);\n        if (n" << e - e0
+          << ") qq = fmaf(" << flit(cf) << ", " << flit(cf) << ", qq);\n";
+      }
+      o << "        if (qq > 0.f) {\n          const float tq = __fdiv_rn(v, qq);\n";
+      for (int e = e0; e < e1; ++e)
+        o << "          if (n" << e - e0 << ") " << X(C.hs_lvar[e]) << " = fmaf(-tq, " << flit(C.hs_coef[e]) << ", "
+          << X(C.hs_lvar[e]) << ");\n";
+      o << "          moved = true;\n        }\n      }\n    }\n";
+      continue;
+    }
     o << "      const float mg = __fmul_rn(kPolishMargin, mag);\n      if (v > -mg) {\n        float qq = 0.f;\n";
     for (int e = e0; e < e1; ++e) {
       const int t = C.hs_lvar[e];

@@ -44,6 +44,14 @@ __device__ __forceinline__ float restart_eta(const DevView& d, float eta, const 
 // shared by the generic loop and the generated routines.
 __device__ __forceinline__ float proj_dot(float cf, float x, float th, float dot) { return fmaf(cf, fmaf(th, cf, x), dot); }
 __device__ __forceinline__ float proj_tn(float dot, float iq) { return __fmul_rn(fmaxf(dot, 0.f), iq); }
+// Dykstra's multiplier of an equality's hyperplane: not clamped at zero (an affine set).
+__device__ __forceinline__ float proj_tn_eq(float dot, float iq) { return __fmul_rn(dot, iq); }
+// The band within which an equality's residual counts as zero in FP32: (n + 4) (u mag +
+// 2^-126-ish), u = 2^-24 (the bound of an n-term FP32 dot product; Higham, Accuracy and
+// Stability of Numerical Algorithms, 2nd ed., Sec. 3.1).
+__device__ __forceinline__ float proj_eq_band(int n, float mag) {
+  return (float)(n + 4) * fmaf(5.9604645e-8f, mag, 1e-38f);
+}
 __device__ __forceinline__ float proj_box(float& x, float p, float lo, float hi) {  // returns the new correction
   const float yv = __fadd_rn(x, p);
   const float xn = fminf(fmaxf(yv, lo), hi);
@@ -65,7 +73,10 @@ __device__ __forceinline__ bool proj_dispatch(int shape, const float* s_q0, cons
 // q.y <= q0 - 2 margin along the reals not pinned at the bound the step would
 // cross, then the box is clamped; the thread stops at the first pass that moves
 // nothing, so the point it returns satisfies every half-space exactly whenever
-// the passes settle.
+// the passes settle.  An equality's hyperplane q.y = q0 takes Dykstra's step with an
+// unclamped multiplier, and in the polish it is projected back onto itself (along the
+// reals not pinned at the bound the move would cross) while its residual exceeds
+// proj_eq_band; the exact repair on the host finishes it.
 // Shared memory: the iterate, Dykstra's box corrections and half-space
 // multipliers of each (block, restart), one column per thread ([var][thread]:
 // conflict-free), sized by the instance's largest block; and per warp the block
@@ -96,7 +107,7 @@ __device__ __forceinline__ void pgd_comp_body(const DevView& d, int R, float eta
   float* ps = xs + maxv * T;         // pbox(t)
   float* hs = ps + maxv * T;         // th(q)
   // the warp's staged block
-  const int wwords = (maxh + 1) + 2 * maxnz + 2 * maxh + 2 * maxv;
+  const int wwords = (maxh + 1) + 2 * maxnz + 3 * maxh + 2 * maxv;
   int* s_hp = reinterpret_cast<int*>(s_col + (2 * maxv + maxh) * T) + threadIdx.y * wwords;  // offsets [nh + 1]
   int* s_lv = s_hp + maxh + 1;                                   // local real of each term
   float* s_cf = reinterpret_cast<float*>(s_lv + maxnz);          // coefficient of each term
@@ -104,6 +115,7 @@ __device__ __forceinline__ void pgd_comp_body(const DevView& d, int R, float eta
   float* s_iq = s_q0 + maxh;                                     // 1 / ||q||^2
   float* s_lo = s_iq + maxh;                                     // the box of each local real
   float* s_hi = s_lo + maxv;
+  int* s_eq = reinterpret_cast<int*>(s_hi + maxv);                // 1: an equality's hyperplane
 #define x(t) xs[(t) * T]
 #define pbox(t) ps[(t) * T]
 #define th(q) hs[(q) * T]
@@ -120,6 +132,7 @@ __device__ __forceinline__ void pgd_comp_body(const DevView& d, int R, float eta
     for (int i = lane; i < nh; i += 32) {
       s_q0[i] = d.hs_q0[h0 + i];
       s_iq[i] = d.hs_inv_qq[h0 + i];
+      s_eq[i] = d.hs_eq[h0 + i];
     }
     for (int i = lane; i < nv; i += 32) {
       const int j = d.comp_var[v0 + i];
@@ -145,7 +158,7 @@ __device__ __forceinline__ void pgd_comp_body(const DevView& d, int R, float eta
         const float thq = th(q);
         float dot = -s_q0[q];
         for (int e = e0; e < e1; ++e) dot = proj_dot(s_cf[e], x(s_lv[e]), thq, dot);
-        const float tn = proj_tn(dot, s_iq[q]);
+        const float tn = s_eq[q] ? proj_tn_eq(dot, s_iq[q]) : proj_tn(dot, s_iq[q]);
         const float delta = __fsub_rn(thq, tn);
         for (int e = e0; e < e1; ++e) x(s_lv[e]) = fmaf(delta, s_cf[e], x(s_lv[e]));
         th(q) = tn;
@@ -168,6 +181,30 @@ __device__ __forceinline__ void pgd_comp_body(const DevView& d, int R, float eta
           const float term = __fmul_rn(s_cf[e], x(s_lv[e]));
           v = __fadd_rn(v, term);
           mag = __fadd_rn(mag, fabsf(term));
+        }
+        if (s_eq[q]) {  // back onto the hyperplane when off it by more than the FP32 band
+          if (fabsf(v) > proj_eq_band(e1 - e0, mag)) {
+            float qq = 0.f;
+            for (int e = e0; e < e1; ++e) {
+              const float cf = s_cf[e];
+              const int t = s_lv[e];
+              const bool down = (v > 0.f) == (cf > 0.f);  // the move -(v/qq) cf lowers x(t)
+              const bool pinned = down ? x(t) <= s_lo[t] : x(t) >= s_hi[t];
+              if (!pinned) qq = fmaf(cf, cf, qq);
+            }
+            if (qq > 0.f) {
+              const float tq = __fdiv_rn(v, qq);
+              for (int e = e0; e < e1; ++e) {
+                const float cf = s_cf[e];
+                const int t = s_lv[e];
+                const bool down = (v > 0.f) == (cf > 0.f);
+                const bool pinned = down ? x(t) <= s_lo[t] : x(t) >= s_hi[t];
+                if (!pinned) x(t) = fmaf(-tq, cf, x(t));
+              }
+              moved = true;
+            }
+          }
+          continue;
         }
         const float margin = __fmul_rn(kPolishMargin, mag);
         if (v > -margin) {

@@ -95,6 +95,14 @@ class Problem:
         L.call("fsmt_verify_exact", self.h, _np_ptr(x), _np_ptr(y), C.byref(sat), C.byref(first))
         return bool(sat.value), int(first.value)
 
+    def repair_equalities(self, y):
+        """Exact repair of reals y so that every projected equality holds exactly
+        (fsmt_repair_equalities).  Returns (ok, repaired y as float64)."""
+        y = np.array(y, np.float64)
+        ok = C.c_int32()
+        L.call("fsmt_repair_equalities", self.h, _np_ptr(y), C.byref(ok))
+        return bool(ok.value), y
+
     def compile(self, policy=L.UNIT_PROJECT):
         return Compiled(self, policy)
 
@@ -489,8 +497,9 @@ class Solver:
                _np_ptr(b_host), _np_ptr(n_unsat_host), _np_ptr(obj_host), _stream(stream))
 
     def verify_restart(self, r):
-        """Restart r's rounded point (fsmt_round) checked exactly on the host
-        (fsmt_verify_exact); y is the restart's reals, widened to float64 exactly."""
+        """Restart r's rounded point (fsmt_round) checked exactly on the host: y is the
+        restart's reals widened to float64 exactly, repaired exactly onto the projected
+        equalities (fsmt_repair_equalities), then fsmt_verify_exact."""
         import torch
         if self._x is None:
             self._x = torch.empty((self.comp.n_bool, self.R), device=self.a.device, dtype=torch.int8)
@@ -498,6 +507,9 @@ class Solver:
         # whole arrays to the host (one copy each), then restart r's column
         x = np.ascontiguousarray(self._x.cpu().numpy()[:, r])
         y = self.b.cpu().numpy()[:, r].astype(np.float64)
+        ok, y = self.problem.repair_equalities(y)  # equalities held within FP32 rounding: made exact
+        if not ok:
+            return False, x, y
         sat, _ = self.problem.verify_exact(x, y)
         return sat, x, y
 

@@ -1,5 +1,7 @@
 """Launches the forward + adjoint kernels a few times on one workload, for
 profilers: python -m paper_2603_22877_b300.profile_kernel --workload NAME --launches N
+With --stages N it runs N annealing stages instead (the autotuned configuration,
+20 PGD iterations each, from a captured CUDA graph), for launch lists of a stage.
 
 Workloads are the seeded synthetic instances of the `workloads` package; the
 smaller variants keep a profiler capture short."""
@@ -28,6 +30,7 @@ def main():
     p.add_argument("--workload", default="large_scheduling_400", choices=list(CASES))
     p.add_argument("--launches", type=int, default=3)
     p.add_argument("--plain", action="store_true")
+    p.add_argument("--stages", type=int, default=0, help="annealing stages to run instead of bare launches")
     args = p.parse_args()
     import torch
     from paper_2603_22877_b300 import build
@@ -44,6 +47,17 @@ def main():
     ga, gb = torch.zeros_like(da), torch.zeros_like(db)
     obj = torch.zeros(R, device="cuda")
     sigma = inst.scale
+    if args.stages > 0:
+        from paper_2603_22877_b300 import Solver
+        S = Solver(P, comp, R, eta=0.02, b_scale=inst.scale, t_max=20, sweeps=20, use_graph=True)
+        S.reset(a, b)
+        sched = [inst.scale / (0.1 * t) for t in range(1, 21)]
+        S.tune(sched[0])
+        for k in range(args.stages):
+            S.stage(sched[k % len(sched)], k + 1)
+        torch.cuda.synchronize()
+        print("stages", args.stages, "iters", int(S.iters.max()), "n_unsat min", int(S.n_unsat.min()))
+        return
     work = torch.empty(comp.plain_work(R), device="cuda") if args.plain else None
     for _ in range(args.launches):
         if args.plain:

@@ -14,7 +14,9 @@ pytestmark = pytest.mark.gpu
 @pytest.mark.parametrize("make,R", [(lambda: W.jobshop(1002, 10, 5), 70), (lambda: W.tiny_random(1001), 45),
                                     (lambda: W.large_scheduling(1005, 16, 30, 6, 4, 5), 40),
                                     # two jobs through 100 machines: blocks of 100 coupled reals
-                                    (lambda: W.jobshop(1002, 2, 100), 64)])
+                                    (lambda: W.jobshop(1002, 2, 100), 64),
+                                    # no-wait jobs: equalities' hyperplanes in the projection
+                                    (lambda: W.jobshop(1002, 10, 5, no_wait=4), 70)])
 def test_pgd_step_parity(make, R):
     import torch
     inst = make()
@@ -299,7 +301,8 @@ def test_converge_and_nonfinite_marks():
 
 
 @pytest.mark.parametrize("make,R", [(lambda: W.jobshop(1002, 10, 5), 70),
-                                    (lambda: W.concat(W.uneven_batch(1004, 6, (3, 12), (3, 9)), "b"), 32)])
+                                    (lambda: W.concat(W.uneven_batch(1004, 6, (3, 12), (3, 9)), "b"), 32),
+                                    (lambda: W.jobshop(1002, 10, 5, no_wait=4), 40)])
 def test_generated_projection_matches_the_generic_loop(make, R, monkeypatch):
     """Blocks of coupled reals whose shape got a run-time generated projection routine
     (fsmt_info.proj_shapes > 0: the iterate in registers, the coefficients as
@@ -333,3 +336,48 @@ def test_generated_projection_matches_the_generic_loop(make, R, monkeypatch):
     np.testing.assert_array_equal(outs[0][1], outs[1][1])
     # ||g||^2 adds the blocks' shares with float atomics, in an order that varies by run
     np.testing.assert_allclose(outs[0][2], outs[1][2], rtol=1e-6)
+
+
+def test_equalities_check_within_the_margin_and_anneal_to_exact_sat():
+    """No-wait jobs (each precedence an equality q.y = q0, projected as a hyperplane): after
+    a PGD step every equality is within a few FP32 bands of its hyperplane; the device check
+    counts an equality as holding within the polish margin, every other constraint exactly
+    -- the oracle's exact check with that rule for the equalities gives the same #Unsat.
+    Alg. 2 then reaches a restart that the host repairs onto the hyperplanes exactly and
+    verifies exactly (fsmt_repair_equalities, fsmt_verify_exact), and the oracle's exact
+    check agrees on the certificate."""
+    import torch
+    from fractions import Fraction
+    from oracle import semantics as Sm
+    inst = W.jobshop(1002, 8, 4, no_wait=3)
+    R = 64
+    P, comp, a, b, w = setup(inst, R)
+    sigma = sigmas_for(inst)[1]
+    _, _, ga, gb = OBJ.evaluate(inst, a.astype(np.float64), b.astype(np.float64), w.astype(np.float64), sigma)
+    da, db, dga, dgb = to_dev(a, b, ga.astype(np.float32), gb.astype(np.float32))
+    gn = torch.zeros(R, device="cuda")
+    comp.pgd_step(R, 0.05, inst.scale, 20, da, db, dga, dgb, gn, polish=32)
+    nu = torch.zeros(R, dtype=torch.int32, device="cuda")
+    comp.round_check(R, da, db, nu)
+    a_out, b_out = da.cpu().numpy().astype(np.float64), db.cpu().numpy().astype(np.float64)
+    _, viol = pgd.round_check(inst, a_out, b_out)
+    eq_cons = []
+    for c in range(inst.n_cons):
+        if OBJ.is_unit_atomic(inst, c):
+            var, coef, q0, rel = inst.atom((int(inst.lits(c)[0]) >> 1) - inst.n_bool)
+            if rel == W.EQ:
+                eq_cons.append(c)
+                for r in range(R):
+                    viol[c, r] = not pgd.eq_holds_on_device(var, coef, q0, b_out[:, r])
+                    z = sum(Fraction(int(q)) * Fraction(float(b_out[int(v), r])) for v, q in zip(var, coef)) - q0
+                    mag = abs(q0) + sum(abs(float(q) * b_out[int(v), r]) for v, q in zip(var, coef))
+                    assert abs(float(z)) <= 4 * pgd.eq_band(len(var), mag)
+    assert eq_cons and not viol[eq_cons].any()
+    np.testing.assert_array_equal(nu.cpu().numpy(), viol.sum(0))
+    S = _solver(inst, R, comp, P, eta=0.05, b_scale=inst.scale, t_max=50)
+    S.reset(a, b)
+    res = S.anneal([inst.scale / (0.1 * t) for t in range(1, 61)])
+    assert res["sat"], res
+    assert Sm.unsat_constraints(inst, res["x"], res["y"]) == []
+    for c in eq_cons:  # the certificate holds every equality exactly
+        assert Sm.constraint_holds(inst, c, res["x"], res["y"])

@@ -32,7 +32,7 @@ HARNESS = r'''
 #include "fsmt_jit.cpp"
 namespace fsmt { void set_error(const std::string&) {} }
 extern "C" long proj_src(int rank, int nv, int nh, const int32_t* hs_ptr, const int32_t* lvar, const float* coef,
-                         const float* inv_qq, char* out, long cap) {
+                         const float* inv_qq, const uint8_t* eq, char* out, long cap) {
   fsmt::Compiled C;
   C.comp_var_ptr = {0, nv};
   C.comp_hs_ptr = {0, nh};
@@ -40,6 +40,7 @@ extern "C" long proj_src(int rank, int nv, int nh, const int32_t* hs_ptr, const 
   C.hs_lvar.assign(lvar, lvar + hs_ptr[nh]);
   C.hs_coef.assign(coef, coef + hs_ptr[nh]);
   C.hs_inv_qq.assign(inv_qq, inv_qq + nh);
+  C.hs_eq.assign(eq, eq + nh);
   const std::string s = fsmt::proj_routine(rank, C, 0);
   if ((long)s.size() + 1 > cap) return -1;
   std::memcpy(out, s.c_str(), s.size() + 1);
@@ -205,6 +206,8 @@ static inline float __fdiv_rn(float a, float b) { return a / b; }
 static const float kPolishMargin = 1.52587890625e-05f;
 static inline float proj_dot(float cf, float x, float th, float dot) { return fmaf(cf, fmaf(th, cf, x), dot); }
 static inline float proj_tn(float dot, float iq) { return __fmul_rn(std::fmax(dot, 0.f), iq); }
+static inline float proj_tn_eq(float dot, float iq) { return __fmul_rn(dot, iq); }
+static inline float proj_eq_band(int n, float mag) { return (float)(n + 4) * std::fma(5.9604645e-8f, mag, 1e-38f); }
 static inline float proj_box(float& x, float p, float lo, float hi) {
   const float yv = __fadd_rn(x, p); const float xn = std::fmin(std::fmax(yv, lo), hi); x = xn; return __fsub_rn(yv, xn);
 }
@@ -221,7 +224,8 @@ def test_generated_projection_routines_match_the_oracle(generator):
     """The projection routines generated for frequent block shapes (fsmt_jit.cpp,
     proj_routine: Dykstra's sweeps and the feasibility polish of Prop. QP's reading,
     straight-line over registers) compiled for the host and run on precedence chains
-    of job-shop instances (blocks of 3, 5 and 9 reals), against the oracle's
+    of job-shop instances (blocks of 3, 5 and 9 reals, and a no-wait chain of 6 whose
+    links are equalities' hyperplanes), against the oracle's
     Domain.project_b in FP64: the same end points up to FP32 rounding, and the
     squared step lengths summed as ||g||^2 (Eq. grad_map)."""
     from oracle import pgd
@@ -230,10 +234,11 @@ def test_generated_projection_routines_match_the_oracle(generator):
     rng = np.random.default_rng(8)
     body = [PROJ_SHIM]
     cases = []
-    for k, (jobs, machines) in enumerate(((4, 3), (5, 5), (3, 9)), start=1):
-        inst = W.jobshop(1002, jobs, machines)
+    for k, (jobs, machines, no_wait) in enumerate(((4, 3, 0), (5, 5, 0), (3, 9, 0), (4, 6, 4)), start=1):
+        inst = W.jobshop(1002, jobs, machines, no_wait=no_wait)
         dom = pgd.Domain(inst)
         hs = dom.halfspaces[:machines - 1]                  # the first job's chain
+        eqf = dom.eq[:machines - 1]                         # no-wait: every link an equality
         order = []
         for var, q, q0 in hs:
             for j in var:
@@ -246,7 +251,8 @@ def test_generated_projection_routines_match_the_oracle(generator):
             cf += [float(c) for c in q]
             ptr.append(len(lv))
             iq.append(np.float32(1.0 / float((np.asarray(q) ** 2).sum())))
-        arrs = [np.asarray(ptr, np.int32), np.asarray(lv, np.int32), np.asarray(cf, np.float32), np.asarray(iq, np.float32)]
+        arrs = [np.asarray(ptr, np.int32), np.asarray(lv, np.int32), np.asarray(cf, np.float32), np.asarray(iq, np.float32),
+                np.asarray(eqf, np.uint8)]
         buf = C.create_string_buffer(1 << 20)
         assert lib.proj_src(k, len(order), len(hs), *[a.ctypes.data_as(C.c_void_p) for a in arrs], buf, 1 << 20) > 0
         body.append(buf.value.decode())

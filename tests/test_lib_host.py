@@ -3,6 +3,7 @@ compiler against the oracle's diagrams, projection bounds, the exact verifier
 and argument validation."""
 import ctypes as C
 import math
+from fractions import Fraction
 import os
 import re
 
@@ -503,3 +504,81 @@ def test_every_device_call_checks_upload_first(name):
         else:
             raise AssertionError(f"{name}: unhandled argument type {t}")
     assert getattr(L.load(), name)(*args) == L.ESTATE
+
+
+# --------------------------------------------------------------------------- equalities
+def _eq_problem(eqs, n=3, extra=None, policy=L.UNIT_PROJECT):
+    B_ = W._Builder(1, n)
+    for var, coef, q0, neg in eqs:
+        B_.con(W.OR, [W.lit(B_.atom(var, coef, q0, W.EQ), neg)])
+    if extra:
+        extra(B_)
+    inst = B_.freeze("eq", np.full(n, -9.0), np.full(n, 9.0), [1], np.zeros(n), 1.0)
+    return inst, Problem.from_instance(inst)
+
+
+def test_equalities_only_as_projected_unit_atoms():
+    """An equality (probability 0 under Gaussian smoothing) compiles only as the positive
+    literal of a unit constraint under FSMT_UNIT_PROJECT: negated, inside a clause, or
+    under SOFT it is refused with EINVAL."""
+    _, P = _eq_problem([([0, 1], [1, -1], 2, False)])
+    assert P.compile(L.UNIT_PROJECT).info["n_halfspaces"] == 1
+    for eqs, extra, pol in (([([0, 1], [1, -1], 2, True)], None, L.UNIT_PROJECT),
+                            ([([0, 1], [1, -1], 2, False)], None, L.UNIT_SOFT),
+                            ([], lambda B_: B_.con(W.OR, [W.lit(0), W.lit(B_.atom([0, 1], [1, 1], 1, W.EQ))]),
+                             L.UNIT_PROJECT)):
+        _, P = _eq_problem(eqs, extra=extra)
+        with pytest.raises(L.FsmtError) as e:
+            P.compile(pol)
+        assert e.value.status == L.EINVAL and "equality" in str(e.value)
+
+
+def test_single_variable_equality_pins_the_real():
+    """3 y0 = 6 pins y0 at 2 exactly; 3 y1 = 7 has no FP32 value, so y1's box is empty
+    (counted in empty_boxes)."""
+    _, P = _eq_problem([([0], [3], 6, False), ([1], [3], 7, False)])
+    comp = P.compile(L.UNIT_PROJECT)
+    lo, hi = comp.bounds()
+    assert lo[0] == hi[0] == 2.0
+    assert lo[1] > hi[1] and comp.info["empty_boxes"] == 1
+
+
+def test_repair_matches_the_oracle():
+    """fsmt_repair_equalities against the oracle's repair_equalities, on no-wait job-shop
+    chains from points off their hyperplanes by FP32-sized amounts and by large ones:
+    where the library's doubles hold the result, they are the oracle's exact values;
+    then every equality holds exactly and fsmt_verify_exact agrees with the oracle's
+    exact check on the repaired point."""
+    inst = W.jobshop(1002, 6, 5, no_wait=3)
+    P = Problem.from_instance(inst)
+    rng = np.random.default_rng(4)
+    agreed = 0
+    for trial in range(40):
+        scale = 1e-4 if trial % 2 else 3.0
+        y = (inst.planted_y + rng.normal(0, scale, inst.n_real)).astype(np.float32).astype(np.float64)
+        ok, yr = P.repair_equalities(y)
+        ref = pgd.repair_equalities(inst, y)
+        assert ok == (ref is not None)
+        if not ok:
+            continue
+        assert [Fraction(v) for v in yr] == ref
+        sat, first = P.verify_exact(inst.planted_x, yr)
+        assert sat == (S.unsat_constraints(inst, inst.planted_x, yr) == [])
+        agreed += 1
+    assert agreed >= 30
+
+
+def test_repair_refuses_what_a_double_cannot_hold():
+    """y1 = y0 + 1 with y0 = 2^60 + ... is exact in Fractions but a double cannot hold
+    y0 + 1 next to 2^-40 parts: the library reports ok = 0 and the oracle's repair, exact,
+    succeeds; an equality with no coefficient +-1 that does not hold gives ok = 0 in both."""
+    inst, P = _eq_problem([([0, 1], [1, -1], -1, False)])
+    y = [2.0 ** 52, 0.5, 0.0]               # y1 = y0 + 1 = 2^52 + 1: exact; fine
+    ok, yr = P.repair_equalities(y)
+    assert ok and yr[1] == 2.0 ** 52 + 1
+    y = [2.0 ** 53 + 2.0, 0.0, 0.0]          # y1 = 2^53 + 3 needs 54 bits
+    ok, yr = P.repair_equalities(y)
+    assert not ok and pgd.repair_equalities(inst, y) is not None
+    inst, P = _eq_problem([([0, 1], [2, 3], 5, False)])
+    assert P.repair_equalities([1.0, 0.9, 0.0])[0] is False
+    assert pgd.repair_equalities(inst, [1.0, 0.9, 0.0]) is None
