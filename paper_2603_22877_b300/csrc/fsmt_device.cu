@@ -71,8 +71,10 @@ FusedShape fused_shape(const Compiled& C, int R) {
 // Numerical Algorithms, 2nd ed., Sec. 3.1, with two terms for the rounding of
 // mag itself and an absolute term for results below the normal range).  Returns
 // -1 (z < 0), +1 (z > 0) or 0 (inside the band: the exact test decides).
+// the filter's bound on |fl(z) - z| for an n-term FP32 dot product, fn = n + 4
+__device__ __forceinline__ float filter_bound(float mag, float fn) { return fn * fmaf(5.9604645e-8f, mag, 1e-38f); }
 __device__ __forceinline__ int atom_filter(float z, float mag, int n) {
-  if (fabsf(z) > (float)(n + 4) * (5.9604645e-8f * mag + 1e-38f)) return z < 0.f ? -1 : 1;
+  if (fabsf(z) > filter_bound(mag, (float)(n + 4))) return z < 0.f ? -1 : 1;
   return 0;
 }
 
@@ -386,6 +388,67 @@ __global__ void k_weight_sum(DevView d, int R, const float* __restrict__ w, floa
   reduce_rows_add(part, wsum, r, ok);
 }
 
+// The same sum for R a multiple of 4, at streaming speed: each warp takes 32 rows of
+// C_sigma at a time (their ids in one load, then broadcast) and reads each row as
+// float4 columns, 512 restarts a pass (column 4 lane + 128 m of the pass, m < 4),
+// two rows in flight; the lane keeps its columns' sums in registers, the CTA's
+// warps meet in shared memory, and the CTA adds its sums to wsum once per pass.
+constexpr int kWsumCols = 512;
+__global__ void __launch_bounds__(256) k_weight_sum_rows(DevView d, int R, const float* __restrict__ w,
+                                                        float* __restrict__ wsum) {
+  __shared__ float s_sum[kWsumCols];
+  const int lane = threadIdx.x & 31, W = blockDim.x >> 5;
+  const int gw = blockIdx.x * W + (threadIdx.x >> 5), nw = gridDim.x * W;
+  for (int c0 = 0; c0 < R; c0 += kWsumCols) {
+    for (int i = threadIdx.x; i < kWsumCols; i += blockDim.x) s_sum[i] = 0.f;
+    __syncthreads();
+    float4 acc[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) acc[m] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int s0 = gw * 32; s0 < d.n_obj; s0 += nw * 32) {
+      const int nrow = min(32, d.n_obj - s0);
+      const int myid = lane < nrow ? __ldg(d.con_id + s0 + lane) : 0;
+      for (int j = 0; j < nrow; j += 2) {
+        float4 v[2][4];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int id = __shfl_sync(0xffffffffu, myid, j + u);
+          const bool rok = j + u < nrow;
+#pragma unroll
+          for (int m = 0; m < 4; ++m) {
+            const int col = c0 + 4 * lane + 128 * m;
+            v[u][m] = rok && col < R ? __ldg(reinterpret_cast<const float4*>(w + (size_t)id * R + col))
+                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+#pragma unroll
+          for (int m = 0; m < 4; ++m) {
+            acc[m].x += v[u][m].x;
+            acc[m].y += v[u][m].y;
+            acc[m].z += v[u][m].z;
+            acc[m].w += v[u][m].w;
+          }
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int cl = 4 * lane + 128 * m;
+      if (c0 + cl < R) {
+        atomicAdd(s_sum + cl, acc[m].x);
+        atomicAdd(s_sum + cl + 1, acc[m].y);
+        atomicAdd(s_sum + cl + 2, acc[m].z);
+        atomicAdd(s_sum + cl + 3, acc[m].w);
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kWsumCols && c0 + i < R; i += blockDim.x)
+      if (s_sum[i] != 0.f) atomicAdd(wsum + c0 + i, s_sum[i]);
+    __syncthreads();
+  }
+}
+
 // ------------------------------------------------------- stage bookkeeping --
 __global__ void k_set_params(float* prm, float sigma, float eta, float bscale, float eps, float rho, float gamma,
                              float update_w, float sweeps, float polish, float norm) {
@@ -524,36 +587,52 @@ __global__ void k_round_check(DevView d, int R, const float* __restrict__ a, con
   }
 }
 
-// Round + check of the constraints of C_sigma over the chunk schedule, per chunk
-// and tile of 32 restarts: (A) every literal slot's truth at the rounded point
-// (x = sgn(a), exact atoms) once, as one 32-bit word over the tile's restarts;
-// (B) one thread per constraint evaluates its diagram bottom up on those words
-// (node value = (holds & value(hi)) | (~holds & value(lo)), literal space), all
-// 32 restarts at once, keeps the constraint's violation word of the tile, and the
-// tile's #Unsat is counted from those words; (C) once every tile of the chunk is
-// walked, each warp streams whole rows of w and h (one constraint, every restart,
-// four restarts a lane per vector access when R is a multiple of 4) and applies the
-// ERWA update as k_round_check does.
+// Round + check of the constraints of C_sigma over the chunk schedule.  Per chunk,
+// the restarts in groups of kCheckTG tiles of 32: (A) every literal slot's truth at
+// the rounded point (x = sgn(a), exact atoms) as one 32-bit word per tile: Boolean
+// slots two a warp, atom slots one a warp (the chunk's slots fall into the two
+// lists as they are staged), the loads of all the group's tiles in flight together,
+// the FP32 filter decided per word and the exact test only where it cannot; (B) one
+// thread per (constraint, tile) evaluates the diagram bottom up on those words
+// (node value = (holds & value(hi)) | (~holds & value(lo)), literal space), all 32
+// restarts of the tile at once, and keeps the constraint's violation word; (C) a
+// warp per tile counts #Unsat from the words.  Once every group is done, each warp
+// streams whole rows of w and h (one constraint, every restart, four restarts a
+// lane per vector access when R is a multiple of 4) and applies the ERWA update as
+// k_round_check does.
 constexpr int kCheckThreads = 512;
-__global__ void __launch_bounds__(kCheckThreads, 3)
+constexpr int kCheckTG = 8;  // tiles of a group: (A) unrolls over them, (B) has one thread per tile
+static_assert(kCheckThreads / 32 >= kCheckTG, "(C) takes a warp per tile of the group");
+static_assert(kCheckTG % 4 == 0, "(A) stores a slot's words four at a time");
+__host__ __device__ constexpr size_t check_smem_bytes(int R) {
+  return (size_t)kChunkMaxNodes * 8 + (size_t)kChunkMaxCons * 16 + (size_t)kChunkMaxSlots * 12 +
+         (size_t)kChunkMaxTerms * 8 + (size_t)kChunkMaxSlots * 4 + (size_t)kChunkMaxSlots * kCheckTG * 4 +
+         (size_t)kChunkMaxNodes * kCheckTG * 4 + (size_t)((R + 31) / 32) * kChunkMaxCons * 4 + (size_t)(R + 2) * 4;
+}
+__global__ void __launch_bounds__(kCheckThreads, 2)
     k_check_chunked(DevView d, int R, int vcap, const float* __restrict__ a, const float* __restrict__ b,
                     uint8_t* __restrict__ viol, int* __restrict__ n_unsat, float* __restrict__ w,
                     float* __restrict__ h, float rho, float gamma, int update_w, const float* prm,
                     const float* __restrict__ wsum, const uint8_t* __restrict__ active) {
+  constexpr int TG = kCheckTG;
   extern __shared__ __align__(16) unsigned char smem[];
   uint2* s_node = reinterpret_cast<uint2*>(smem);
   int4* s_con = reinterpret_cast<int4*>(s_node + kChunkMaxNodes);
   int* s_lab = reinterpret_cast<int*>(s_con + kChunkMaxCons);
   int* s_meta = s_lab + kChunkMaxSlots;                               // atoms: first term << 16 | count
   float* s_q0 = reinterpret_cast<float*>(s_meta + kChunkMaxSlots);    // atoms: q0 (FP32)
-  int* s_tvar = reinterpret_cast<int*>(s_q0 + kChunkMaxSlots);        // the chunk's atom terms
+  int* s_tvar = reinterpret_cast<int*>(s_q0 + kChunkMaxSlots);        // the chunk's atom terms: global real id
   float* s_tcoef = reinterpret_cast<float*>(s_tvar + kChunkMaxTerms);
-  float* s_b = s_tcoef + kChunkMaxTerms;                              // [real][32]: b of the tile
-  unsigned* s_t = reinterpret_cast<unsigned*>(s_b + kChunkMaxReals * 32);  // [slot]: the literal holds, bit per restart
-  unsigned* s_val = s_t + kChunkMaxSlots;                                   // [node]: the node's value, bit per restart
-  int* cnt_s = reinterpret_cast<int*>(s_val + kChunkMaxNodes);            // [R]: #Unsat of the CTA's chunks
-  unsigned* s_u = reinterpret_cast<unsigned*>(cnt_s + R);                   // [tile][constraint]: violated bits
+  int* s_list = reinterpret_cast<int*>(s_tcoef + kChunkMaxTerms);     // Boolean slots from the front, atom slots from the back
+  unsigned* s_t = reinterpret_cast<unsigned*>(s_list + kChunkMaxSlots);  // [slot][tile of group]: holds, bit per restart
+  unsigned* s_val = s_t + kChunkMaxSlots * TG;                          // [node][tile of group]: the node's value
+  unsigned* s_u = s_val + kChunkMaxNodes * TG;                          // [tile][constraint]: violated bits
+  const int n_tiles = (R + 31) >> 5;
+  int* cnt_s = reinterpret_cast<int*>(s_u + n_tiles * kChunkMaxCons);  // [R]: #Unsat of the CTA's chunks
+  int& s_nb = cnt_s[R];      // the chunk's Boolean slots
+  int& s_na = cnt_s[R + 1];  // and atom slots
   for (int r = threadIdx.x; r < R; r += blockDim.x) cnt_s[r] = 0;
+  if (threadIdx.x == 0) s_nb = s_na = 0;
   if (prm) {
     rho = prm[P_RHO];
     gamma = prm[P_GAMMA];
@@ -561,7 +640,10 @@ __global__ void __launch_bounds__(kCheckThreads, 3)
   }
   const float lg = log2f(gamma);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
-  const int n_tiles = (R + 31) >> 5;
+  // (B) pairs a constraint with ts tiles, ts the least power of two >= min(TG, n_tiles)
+  int ts_log = 0;
+  while ((1 << ts_log) < min(TG, n_tiles)) ++ts_log;
+  const int ts = 1 << ts_log;
   for (int q = blockIdx.x; q < d.n_chunks; q += gridDim.x) {
     const int c0 = __ldg(d.chunk_con_ptr + q), nc = __ldg(d.chunk_con_ptr + q + 1) - c0;
     const int n0 = __ldg(d.chunk_node_ptr + q), nn = __ldg(d.chunk_node_ptr + q + 1) - n0;
@@ -573,52 +655,134 @@ __global__ void __launch_bounds__(kCheckThreads, 3)
       const int raw = __ldg(d.slot_label + l0 + i), lab = raw & 0x7fffffff;
       s_lab[i] = raw;
       s_meta[i] = __ldg(d.slot_meta + l0 + i);
-      if (lab >= d.n_bool) s_q0[i] = __ldg(d.atom_q0f + lab - d.n_bool);
+      if (lab >= d.n_bool) {
+        s_q0[i] = __ldg(d.atom_q0f + lab - d.n_bool);
+        s_list[ns - 1 - atomicAdd(&s_na, 1)] = i;
+      } else {
+        s_list[atomicAdd(&s_nb, 1)] = i;
+      }
     }
     const int t0 = __ldg(d.chunk_term_ptr + q), nt = __ldg(d.chunk_term_ptr + q + 1) - t0;
+    const int e0 = __ldg(d.chunk_real_ptr + q);
     for (int i = threadIdx.x; i < nt; i += blockDim.x) {
-      s_tvar[i] = __ldg(d.term_var + t0 + i);
+      s_tvar[i] = __ldg(d.real_id + e0 + __ldg(d.term_var + t0 + i));
       s_tcoef[i] = __ldg(d.term_coef + t0 + i);
     }
-    const int e0 = __ldg(d.chunk_real_ptr + q), nr = __ldg(d.chunk_real_ptr + q + 1) - e0;
-    for (int t = 0; t < n_tiles; ++t) {
-      const int r = t * 32 + lane;
-      const bool ok = r < R;
-      __syncthreads();  // chunk loaded / the previous tile's walks are done
-      for (int e = threadIdx.x; e < nr * 32; e += blockDim.x) {
-        const int rr = t * 32 + (e & 31);
-        const float y = rr < R ? __ldg(b + (size_t)__ldg(d.real_id + e0 + (e >> 5)) * R + rr) : 0.f;
-        if (!isfinite(y)) atomicOr(n_unsat + rr, kUnsatNonFinite);
-        s_b[e] = y;
+    for (int g = 0; g < n_tiles; g += TG) {
+      const int ng = min(TG, n_tiles - g);
+      __syncthreads();  // chunk loaded / the previous group's walks are done with s_t
+      // (A) restart r = (g + k) * 32 + lane of tile k of the group; every restart of
+      // the group exists when `full`, otherwise loads past R read 0 (bits masked in B)
+      const bool full = ng == TG && (R & 31) == 0;
+      auto in_r = [&](int k) { return full || (k < ng && (g + k) * 32 + lane < R); };
+      const int nb = s_nb, na = s_na;
+      // the slot's row of TG words, 16-byte aligned
+      auto store_row = [&](int i, const unsigned* word) {
+        uint4* row = reinterpret_cast<uint4*>(s_t + i * TG);
+#pragma unroll
+        for (int k = 0; k < TG; k += 4) row[k / 4] = make_uint4(word[k], word[k + 1], word[k + 2], word[k + 3]);
+      };
+      // Booleans (holds: a < 0), two slots a warp at a time
+      for (int j = warp; j < nb; j += 2 * W) {
+        const bool two = j + W < nb;
+        const int i0 = s_list[j], i1 = two ? s_list[j + W] : i0;
+        const float* ap0 = a + (size_t)(s_lab[i0] & 0x7fffffff) * R + g * 32 + lane;
+        const float* ap1 = a + (size_t)(s_lab[i1] & 0x7fffffff) * R + g * 32 + lane;
+        float av0[TG], av1[TG];
+#pragma unroll
+        for (int k = 0; k < TG; ++k) {
+          av0[k] = in_r(k) ? __ldg(ap0 + 32 * k) : 0.f;
+          av1[k] = in_r(k) ? __ldg(ap1 + 32 * k) : 0.f;
+        }
+        const unsigned flip0 = s_lab[i0] < 0 ? 0xffffffffu : 0u, flip1 = s_lab[i1] < 0 ? 0xffffffffu : 0u;
+        unsigned w0[TG], w1[TG], badm = 0;  // badm: bit k, this lane's restart of tile k is non-finite
+#pragma unroll
+        for (int k = 0; k < TG; ++k) {
+          w0[k] = __ballot_sync(0xffffffffu, av0[k] < 0.f) ^ flip0;
+          w1[k] = __ballot_sync(0xffffffffu, av1[k] < 0.f) ^ flip1;
+          if (!isfinite(av0[k]) || !isfinite(av1[k])) badm |= 1u << k;
+        }
+        if (badm)
+#pragma unroll
+          for (int k = 0; k < TG; ++k)
+            if ((badm >> k) & 1u) atomicOr(n_unsat + (g + k) * 32 + lane, kUnsatNonFinite);
+        if (lane == 0) store_row(i0, w0);
+        if (lane == 1 && two) store_row(i1, w1);
       }
-      __syncthreads();
-      for (int i = warp; i < ns; i += W) {
+      // atoms: z = q.y - q0 and the filter's magnitude; the exact test where the filter cannot decide
+      for (int j = warp; j < na; j += W) {
+        const int i = s_list[ns - 1 - j];
         const int raw = s_lab[i], lab = raw & 0x7fffffff;
-        bool holds = false;
-        if (ok) {
-          if (lab < d.n_bool) {
-            const float av = __ldg(a + (size_t)lab * R + r);
-            if (!isfinite(av)) atomicOr(n_unsat + r, kUnsatNonFinite);
-            holds = av < 0.f;
-          } else {  // the filter on the staged reals, else the exact test
-            const int meta = s_meta[i], tb = meta >> 16, tc = meta & 0xffff;
-            const float q0 = s_q0[i];
-            float z = -q0, mag = fabsf(q0);
-            for (int j = 0; j < tc; ++j) {
-              const float cj = s_tcoef[tb + j], y = s_b[s_tvar[tb + j] * 32 + lane];
-              z = fmaf(cj, y, z);
-              mag = fmaf(fabsf(cj), fabsf(y), mag);
+        const unsigned flip = raw < 0 ? 0xffffffffu : 0u;
+        const int meta = s_meta[i], tb = meta >> 16, tc = meta & 0xffff;
+        const float q0 = s_q0[i];
+        unsigned word[TG];
+        float z[TG], mag[TG];
+        // term jj's y at tile k (0 past R)
+        auto term_y = [&](int jj, int k) -> float {
+          return in_r(k) ? __ldg(b + (size_t)s_tvar[tb + jj] * R + (g + k) * 32 + lane) : 0.f;
+        };
+        if (tc == 2) {
+          const float c0 = s_tcoef[tb], c1 = s_tcoef[tb + 1];
+          float y0[TG], y1[TG];
+#pragma unroll
+          for (int k = 0; k < TG; ++k) {
+            y0[k] = term_y(0, k);
+            y1[k] = term_y(1, k);
+          }
+#pragma unroll
+          for (int k = 0; k < TG; ++k) {
+            z[k] = fmaf(c1, y1[k], fmaf(c0, y0[k], -q0));
+            mag[k] = fmaf(fabsf(c1), fabsf(y1[k]), fmaf(fabsf(c0), fabsf(y0[k]), fabsf(q0)));
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < TG; ++k) {
+            z[k] = -q0;
+            mag[k] = fabsf(q0);
+          }
+          for (int jj = 0; jj < tc; ++jj) {
+            const float cj = s_tcoef[tb + jj];
+            float y[TG];
+#pragma unroll
+            for (int k = 0; k < TG; ++k) y[k] = term_y(jj, k);
+#pragma unroll
+            for (int k = 0; k < TG; ++k) {
+              z[k] = fmaf(cj, y[k], z[k]);
+              mag[k] = fmaf(fabsf(cj), fabsf(y[k]), mag[k]);
             }
-            const int f = atom_filter(z, mag, tc);
-            holds = f != 0 ? f < 0 : atom_truth_exact_slow(d, lab, R, r, a, b);
           }
         }
-        const unsigned word = __ballot_sync(0xffffffffu, holds != (raw < 0));
-        if (lane == 0) s_t[i] = word;
+        // bit k of uncm: the filter cannot decide this lane's restart of tile k; of badm:
+        // its magnitude is non-finite, which a non-finite y makes it
+        const float fn = (float)(tc + 4);
+        unsigned uncm = 0, badm = 0;
+#pragma unroll
+        for (int k = 0; k < TG; ++k) {
+          word[k] = __ballot_sync(0xffffffffu, z[k] < 0.f) ^ flip;
+          if (!(fabsf(z[k]) > filter_bound(mag[k], fn))) uncm |= 1u << k;
+          if (!isfinite(mag[k])) badm |= 1u << k;
+        }
+        if (__any_sync(0xffffffffu, (uncm | badm) != 0)) {  // rare: exact decisions, and which reals are non-finite
+#pragma unroll
+          for (int k = 0; k < TG; ++k) {
+            const int r = (g + k) * 32 + lane;
+            const bool ok = in_r(k);
+            if (ok && ((badm >> k) & 1u))
+              for (int jj = 0; jj < tc; ++jj)
+                if (!isfinite(__ldg(b + (size_t)s_tvar[tb + jj] * R + r))) atomicOr(n_unsat + r, kUnsatNonFinite);
+            bool holds = ((word[k] ^ flip) >> lane) & 1u;  // z < 0, where the filter decides
+            if (ok && ((uncm >> k) & 1u)) holds = atom_truth_exact_slow(d, lab, R, r, a, b);
+            word[k] = __ballot_sync(0xffffffffu, holds) ^ flip;
+          }
+        }
+        if (lane == 0) store_row(i, word);
       }
       __syncthreads();
-      const unsigned valid = t * 32 + 32 <= R ? 0xffffffffu : (1u << (R - t * 32)) - 1u;
-      for (int c = threadIdx.x; c < nc; c += blockDim.x) {  // (B)
+      // (B) thread per (constraint c, tile k of the group)
+      for (int p = threadIdx.x; p < nc << ts_log; p += blockDim.x) {
+        const int c = p >> ts_log, k = p & (ts - 1), t = g + k;
+        if (k >= ng) continue;
         const int4 cn = s_con[c];
         const int V = cn.y & 0xffff;
         unsigned holds_c;
@@ -626,28 +790,34 @@ __global__ void __launch_bounds__(kCheckThreads, 3)
           holds_c = cn.z == 0 ? 0xffffffffu : 0u;  // constant diagram: 0 TRUE, 1 FALSE
         } else {
           const uint2* nd = s_node + cn.x;
-          unsigned* val = s_val + cn.x;
+          unsigned* val = s_val + cn.x * TG + k;
           auto value = [&](unsigned ch) -> unsigned {  // the TRUE terminal's row is vcap, FALSE vcap + 1
-            return ch < (unsigned)V ? val[ch] : (ch == (unsigned)vcap ? 0xffffffffu : 0u);
+            return ch < (unsigned)V ? val[ch * TG] : (ch == (unsigned)vcap ? 0xffffffffu : 0u);
           };
           for (int v = V - 1; v >= 0; --v) {
             const uint2 e = nd[v];
-            const unsigned m = s_t[e.x >> 8];
-            val[v] = (m & value(e.y & 0xffffu)) | (~m & value(e.y >> 16));
+            const unsigned m = s_t[(e.x >> 8) * TG + k];
+            val[v * TG] = (m & value(e.y & 0xffffu)) | (~m & value(e.y >> 16));
           }
           holds_c = val[0];
         }
+        const unsigned valid = t * 32 + 32 <= R ? 0xffffffffu : (1u << (R - t * 32)) - 1u;
         s_u[t * kChunkMaxCons + c] = ~holds_c & valid;
       }
       __syncthreads();
-      if (threadIdx.x < 32 && ok) {  // the tile's #Unsat over the chunk, from the words
-        int cnt = 0;
-        for (int c = 0; c < nc; ++c) cnt += (int)((s_u[t * kChunkMaxCons + c] >> lane) & 1u);
-        cnt_s[r] += cnt;
+      // (C) the group's #Unsat over the chunk, a warp per tile (W >= TG)
+      if (warp < ng) {
+        const int t = g + warp, r = t * 32 + lane;
+        if (r < R) {
+          int cnt = 0;
+          for (int c = 0; c < nc; ++c) cnt += (int)((s_u[t * kChunkMaxCons + c] >> lane) & 1u);
+          cnt_s[r] += cnt;
+        }
       }
     }
     __syncthreads();
-    // (C) per constraint, every restart: u, then h <- rho h + u and, on update, w <- w gamma^h, h <- 1
+    if (threadIdx.x == 0) s_nb = s_na = 0;  // read last by (A); the next chunk counts after the loop-top barrier
+    // ERWA per constraint, every restart: u, then h <- rho h + u and, on update, w <- w gamma^h, h <- 1
     auto erwa = [&](size_t k, int rr, int u) {
       if (viol) viol[k] = (uint8_t)u;
       if (h) {
@@ -924,6 +1094,12 @@ fsmt_status launch_pgd(const Compiled& C, int R, float eta, float bscale, int sw
 fsmt_status launch_weight_sum(const Compiled& C, int R, const float* w, float* wsum, cudaStream_t st) {
   FSMT_CUDA(cudaMemsetAsync(wsum, 0, sizeof(float) * (size_t)R, st), "memset wsum");
   if (C.n_obj == 0) return FSMT_OK;
+  if (R % 4 == 0) {  // rows 16-byte aligned: whole rows as float4
+    const int blocks = (int)std::max<long>(1, std::min<long>((C.n_obj + 255) / 256, (long)sm_count() * 4));
+    k_weight_sum_rows<<<blocks, 256, 0, st>>>(C.view, R, w, wsum);
+    FSMT_CUDA(cudaGetLastError(), "weight sum launch");
+    return FSMT_OK;
+  }
   const int tiles = (R + 31) / 32;
   const long cap = std::max<long>(1, 4L * sm_count() * 8 / tiles);
   const int gy = (int)std::max<long>(1, std::min<long>(std::min<long>((C.n_obj + 7) / 8, cap), 65535L));
@@ -945,12 +1121,10 @@ fsmt_status launch_round_check(const Compiled& C, int R, const float* a, const f
   }
   // constraints of C_sigma over the chunk schedule (when it exists), the rest one warp each
   int s_begin = 0;
-  const size_t csmem = (size_t)kChunkMaxNodes * (8 + 4) + (size_t)kChunkMaxCons * 16 +
-                       (size_t)((R + 31) / 32) * kChunkMaxCons * 4 +
-                       (size_t)kChunkMaxSlots * (12 + 4) + (size_t)kChunkMaxTerms * 8 +
-                       (size_t)kChunkMaxReals * 32 * 4 + (size_t)R * sizeof(int);
+  const size_t csmem = check_smem_bytes(R);
   if (C.chunked_ok && C.n_chunks > 0 && csmem <= kSmemMax) {
-    const int cblocks = std::max(1, std::min(C.n_chunks, sm_count() * 3));
+    const int per_sm = csmem * 2 + 2048 <= 228 * 1024 ? 2 : 1;
+    const int cblocks = std::max(1, std::min(C.n_chunks, sm_count() * per_sm));
     k_check_chunked<<<cblocks, kCheckThreads, csmem, st>>>(C.view, R, std::max(1, C.max_nodes), a, b, viol, n_unsat,
                                                             w, h, rho, gamma, update_w, prm, wsum, active);
     FSMT_CUDA(cudaGetLastError(), "chunked check launch");

@@ -381,3 +381,18 @@ def test_equalities_check_within_the_margin_and_anneal_to_exact_sat():
     assert Sm.unsat_constraints(inst, res["x"], res["y"]) == []
     for c in eq_cons:  # the certificate holds every equality exactly
         assert Sm.constraint_holds(inst, c, res["x"], res["y"])
+
+
+@pytest.mark.parametrize("R", [4, 100, 512, 1100, 70])
+def test_weight_sum_over_column_passes(R):
+    """wsum[r] = sum of w over C_sigma: the float4 row kernel (R a multiple of 4,
+    one or several 512-restart passes, a ragged last pass) and the general one (R = 70)."""
+    import torch
+    inst = W.jobshop(1002, 10, 5)
+    from paper_2603_22877_b300.engine import Problem
+    comp = Problem.from_instance(inst).compile().upload()
+    w = np.random.default_rng(R).uniform(0.5, 3.0, (inst.n_cons, R)).astype(np.float32)
+    wsum = torch.full((R,), float("nan"), device="cuda")
+    comp.weight_sum(R, to_dev(w)[0], wsum)
+    oc = OBJ.objective_constraints(inst)
+    np.testing.assert_allclose(wsum.cpu().numpy(), w[oc].astype(np.float64).sum(0), rtol=1e-5)
