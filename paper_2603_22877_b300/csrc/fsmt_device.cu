@@ -588,7 +588,8 @@ __global__ void k_round_check(DevView d, int R, const float* __restrict__ a, con
 }
 
 // Round + check of the constraints of C_sigma over the chunk schedule.  Per chunk,
-// the restarts in groups of kCheckTG tiles of 32: (A) every literal slot's truth at
+// the restarts in groups of TG tiles of 32 (TG: the least power of two >= the tile
+// count, at most 8): (A) every literal slot's truth at
 // the rounded point (x = sgn(a), exact atoms) as one 32-bit word per tile: Boolean
 // slots two a warp, atom slots one a warp (the chunk's slots fall into the two
 // lists as they are staged), the loads of all the group's tiles in flight together,
@@ -601,20 +602,23 @@ __global__ void k_round_check(DevView d, int R, const float* __restrict__ a, con
 // lane per vector access when R is a multiple of 4) and applies the ERWA update as
 // k_round_check does.
 constexpr int kCheckThreads = 512;
-constexpr int kCheckTG = 8;  // tiles of a group: (A) unrolls over them, (B) has one thread per tile
+constexpr int kCheckTG = 8;  // the largest group: (A) unrolls over its tiles, (B) has one thread per tile
 static_assert(kCheckThreads / 32 >= kCheckTG, "(C) takes a warp per tile of the group");
-static_assert(kCheckTG % 4 == 0, "(A) stores a slot's words four at a time");
-__host__ __device__ constexpr size_t check_smem_bytes(int R) {
-  return (size_t)kChunkMaxNodes * 8 + (size_t)kChunkMaxCons * 16 + (size_t)kChunkMaxSlots * 12 +
-         (size_t)kChunkMaxTerms * 8 + (size_t)kChunkMaxSlots * 4 + (size_t)kChunkMaxSlots * kCheckTG * 4 +
-         (size_t)kChunkMaxNodes * kCheckTG * 4 + (size_t)((R + 31) / 32) * kChunkMaxCons * 4 + (size_t)(R + 2) * 4;
+inline int check_group(int R) {  // TG for R restarts
+  const int tiles = (R + 31) / 32;
+  return tiles >= 5 ? 8 : tiles >= 3 ? 4 : tiles;
 }
-__global__ void __launch_bounds__(kCheckThreads, 2)
+__host__ __device__ constexpr size_t check_smem_bytes(int R, int TG) {
+  return (size_t)kChunkMaxNodes * 8 + (size_t)kChunkMaxCons * 16 + (size_t)kChunkMaxSlots * 12 +
+         (size_t)kChunkMaxTerms * 8 + (size_t)kChunkMaxSlots * 4 + (size_t)kChunkMaxSlots * TG * 4 +
+         (size_t)kChunkMaxNodes * TG * 4 + (size_t)((R + 31) / 32) * kChunkMaxCons * 4 + (size_t)(R + 2) * 4;
+}
+template <int TG>
+__global__ void __launch_bounds__(kCheckThreads, TG <= 2 ? 3 : 2)
     k_check_chunked(DevView d, int R, int vcap, const float* __restrict__ a, const float* __restrict__ b,
                     uint8_t* __restrict__ viol, int* __restrict__ n_unsat, float* __restrict__ w,
                     float* __restrict__ h, float rho, float gamma, int update_w, const float* prm,
                     const float* __restrict__ wsum, const uint8_t* __restrict__ active) {
-  constexpr int TG = kCheckTG;
   extern __shared__ __align__(16) unsigned char smem[];
   uint2* s_node = reinterpret_cast<uint2*>(smem);
   int4* s_con = reinterpret_cast<int4*>(s_node + kChunkMaxNodes);
@@ -678,9 +682,14 @@ __global__ void __launch_bounds__(kCheckThreads, 2)
       const int nb = s_nb, na = s_na;
       // the slot's row of TG words, 16-byte aligned
       auto store_row = [&](int i, const unsigned* word) {
-        uint4* row = reinterpret_cast<uint4*>(s_t + i * TG);
+        if constexpr (TG % 4 == 0) {
+          uint4* row = reinterpret_cast<uint4*>(s_t + i * TG);
 #pragma unroll
-        for (int k = 0; k < TG; k += 4) row[k / 4] = make_uint4(word[k], word[k + 1], word[k + 2], word[k + 3]);
+          for (int k = 0; k < TG; k += 4) row[k / 4] = make_uint4(word[k], word[k + 1], word[k + 2], word[k + 3]);
+        } else {
+#pragma unroll
+          for (int k = 0; k < TG; ++k) s_t[i * TG + k] = word[k];
+        }
       };
       // Booleans (holds: a < 0), two slots a warp at a time
       for (int j = warp; j < nb; j += 2 * W) {
@@ -1094,7 +1103,7 @@ fsmt_status launch_pgd(const Compiled& C, int R, float eta, float bscale, int sw
 fsmt_status launch_weight_sum(const Compiled& C, int R, const float* w, float* wsum, cudaStream_t st) {
   FSMT_CUDA(cudaMemsetAsync(wsum, 0, sizeof(float) * (size_t)R, st), "memset wsum");
   if (C.n_obj == 0) return FSMT_OK;
-  if (R % 4 == 0) {  // rows 16-byte aligned: whole rows as float4
+  if (R % 4 == 0 && R >= 128) {  // rows 16-byte aligned and at least a warp's float4 width: whole rows
     const int blocks = (int)std::max<long>(1, std::min<long>((C.n_obj + 255) / 256, (long)sm_count() * 4));
     k_weight_sum_rows<<<blocks, 256, 0, st>>>(C.view, R, w, wsum);
     FSMT_CUDA(cudaGetLastError(), "weight sum launch");
@@ -1121,12 +1130,16 @@ fsmt_status launch_round_check(const Compiled& C, int R, const float* a, const f
   }
   // constraints of C_sigma over the chunk schedule (when it exists), the rest one warp each
   int s_begin = 0;
-  const size_t csmem = check_smem_bytes(R);
+  const int tg = check_group(R);
+  const size_t csmem = check_smem_bytes(R, tg);
   if (C.chunked_ok && C.n_chunks > 0 && csmem <= kSmemMax) {
-    const int per_sm = csmem * 2 + 2048 <= 228 * 1024 ? 2 : 1;
+    const int fit = (int)std::max<size_t>(1, 228 * 1024 / (csmem + 1024));
+    const int per_sm = std::min(fit, tg <= 2 ? 3 : 2);
     const int cblocks = std::max(1, std::min(C.n_chunks, sm_count() * per_sm));
-    k_check_chunked<<<cblocks, kCheckThreads, csmem, st>>>(C.view, R, std::max(1, C.max_nodes), a, b, viol, n_unsat,
-                                                            w, h, rho, gamma, update_w, prm, wsum, active);
+    auto kern = tg == 1 ? k_check_chunked<1> : tg == 2 ? k_check_chunked<2> : tg == 4 ? k_check_chunked<4>
+                                                                                      : k_check_chunked<8>;
+    kern<<<cblocks, kCheckThreads, csmem, st>>>(C.view, R, std::max(1, C.max_nodes), a, b, viol, n_unsat, w, h, rho,
+                                                gamma, update_w, prm, wsum, active);
     FSMT_CUDA(cudaGetLastError(), "chunked check launch");
     s_begin = C.n_obj;
   }
@@ -1262,7 +1275,13 @@ fsmt_status fsmt_upload(fsmt_compiled* cc, void* stream) {
   FSMT_CUDA(cudaFuncSetAttribute(k_pgd_comp, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(kProjSmemWords * sizeof(float))),
             "smem attribute");
-  FSMT_CUDA(cudaFuncSetAttribute(k_check_chunked, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024),
+  FSMT_CUDA(cudaFuncSetAttribute(k_check_chunked<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024),
+            "smem attribute");
+  FSMT_CUDA(cudaFuncSetAttribute(k_check_chunked<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024),
+            "smem attribute");
+  FSMT_CUDA(cudaFuncSetAttribute(k_check_chunked<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024),
+            "smem attribute");
+  FSMT_CUDA(cudaFuncSetAttribute(k_check_chunked<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024),
             "smem attribute");
   FSMT_CUDA(cudaFuncSetAttribute(k_chunked<true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024),
             "smem attribute");

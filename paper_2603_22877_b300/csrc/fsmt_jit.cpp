@@ -11,10 +11,13 @@
 #include <dlfcn.h>
 #include <nvrtc.h>
 
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <functional>
 #include <mutex>
 #include <sstream>
+#include <string>
 #include <unordered_map>
 #include <vector>
 
@@ -224,6 +227,33 @@ std::string flit(float f) {
   return buf;
 }
 
+// The polish divides by qq = sum of the free terms' squared coefficients (FP32, fmaf in
+// term order; term e free when flag n<e> is set).  When every nonzero qq that the flags
+// can give is a power of two, the quotient equals the product with the exact reciprocal
+// 2^-k, and the routine multiplies by a reciprocal picked by the flags instead of
+// dividing (bit for bit the same result); returns that selection as an expression, or ""
+// (divide) when some qq is not a power of two or the half-space has more than 4 terms.
+static std::string polish_reciprocal(const std::vector<float>& cf) {
+  const int n = (int)cf.size();
+  if (n == 0 || n > 4) return "";
+  std::vector<float> rq(1u << n, 1.f);
+  for (unsigned m = 1; m < (1u << n); ++m) {
+    float qq = 0.f;
+    for (int e = 0; e < n; ++e)
+      if ((m >> e) & 1u) qq = std::fmaf(cf[e], cf[e], qq);
+    if (!(qq > 0.f)) continue;
+    int ex;
+    if (std::frexp(qq, &ex) != 0.5f || ex - 1 < -126 || ex - 1 > 126) return "";  // qq = 2^(ex-1), normal
+    rq[m] = std::ldexp(1.f, 1 - ex);
+  }
+  // nested selection on n<n-1> ... n0 (mask bit e = flag n<e>)
+  std::function<std::string(int, unsigned)> sel = [&](int e, unsigned m) -> std::string {
+    if (e < 0) return flit(rq[m]);
+    return "(n" + std::to_string(e) + " ? " + sel(e - 1, m | (1u << e)) + " : " + sel(e - 1, m) + ")";
+  };
+  return sel(n - 1, 0u);
+}
+
 // The projection of one (block, restart) for one block shape (fsmt_proj.cuh's
 // pgd_comp_body, the same operations in the same order): the block's iterate x<t>,
 // box corrections p<t> and half-space multipliers h<q> in registers, the
@@ -277,25 +307,43 @@ std::string proj_routine(int rank, const Compiled& C, int c) {
           << X(t) << " <= s_lo[" << t << "] : " << X(t) << " >= s_hi[" << t << "]);\n        if (n" << e - e0
           << ") qq = fmaf(" << flit(cf) << ", " << flit(cf) << ", qq);\n";
       }
-      o << "        if (qq > 0.f) {\n          const float tq = __fdiv_rn(v, qq);\n";
+      std::vector<float> cfs(C.hs_coef.begin() + e0, C.hs_coef.begin() + e1);
+      const std::string rq = polish_reciprocal(cfs);
+      o << "        if (qq > 0.f) {\n          const float tq = "
+        << (rq.empty() ? std::string("__fdiv_rn(v, qq)") : "__fmul_rn(v, " + rq + ")") << ";\n";
       for (int e = e0; e < e1; ++e)
         o << "          if (n" << e - e0 << ") " << X(C.hs_lvar[e]) << " = fmaf(-tq, " << flit(C.hs_coef[e]) << ", "
           << X(C.hs_lvar[e]) << ");\n";
       o << "          moved = true;\n        }\n      }\n    }\n";
       continue;
     }
-    o << "      const float mg = __fmul_rn(kPolishMargin, mag);\n      if (v > -mg) {\n        float qq = 0.f;\n";
+    // with an exact reciprocal the half-space is one straight run of selects (no
+    // branch): a real moves where the half-space is within the margin, some real is
+    // free (qq > 0) and this real is free -- the generic loop's conditions
+    std::vector<float> cfs(C.hs_coef.begin() + e0, C.hs_coef.begin() + e1);
+    const std::string rq = polish_reciprocal(cfs);
+    o << "      const float mg = __fmul_rn(kPolishMargin, mag);\n";
+    o << (rq.empty() ? "      if (v > -mg) {\n" : "      {\n") << "        float qq = 0.f;\n";
     for (int e = e0; e < e1; ++e) {
       const int t = C.hs_lvar[e];
       const float cf = C.hs_coef[e];
       o << "        const bool n" << e - e0 << " = !(" << (cf > 0.f ? X(t) + " <= s_lo[" : X(t) + " >= s_hi[") << t
         << "]);\n        if (n" << e - e0 << ") qq = fmaf(" << flit(cf) << ", " << flit(cf) << ", qq);\n";
     }
-    o << "        if (qq > 0.f) {\n          const float tq = __fdiv_rn(__fadd_rn(v, __fmul_rn(2.f, mg)), qq);\n";
-    for (int e = e0; e < e1; ++e)
-      o << "          if (n" << e - e0 << ") " << X(C.hs_lvar[e]) << " = fmaf(-tq, " << flit(C.hs_coef[e]) << ", "
-        << X(C.hs_lvar[e]) << ");\n";
-    o << "          moved = true;\n        }\n      }\n    }\n";
+    if (rq.empty()) {
+      o << "        if (qq > 0.f) {\n          const float tq = __fdiv_rn(__fadd_rn(v, __fmul_rn(2.f, mg)), qq);\n";
+      for (int e = e0; e < e1; ++e)
+        o << "          if (n" << e - e0 << ") " << X(C.hs_lvar[e]) << " = fmaf(-tq, " << flit(C.hs_coef[e]) << ", "
+          << X(C.hs_lvar[e]) << ");\n";
+      o << "          moved = true;\n        }\n      }\n    }\n";
+    } else {
+      o << "        const bool go = v > -mg && qq > 0.f;\n";
+      o << "        const float tq = __fmul_rn(__fadd_rn(v, __fmul_rn(2.f, mg)), " << rq << ");\n";
+      for (int e = e0; e < e1; ++e)
+        o << "        " << X(C.hs_lvar[e]) << " = go && n" << e - e0 << " ? fmaf(-tq, " << flit(C.hs_coef[e]) << ", "
+          << X(C.hs_lvar[e]) << ") : " << X(C.hs_lvar[e]) << ";\n";
+      o << "        moved |= go;\n      }\n    }\n";
+    }
   }
   for (int t = 0; t < nv; ++t)
     o << "    x" << t << " = fminf(fmaxf(x" << t << ", s_lo[" << t << "]), s_hi[" << t << "]);\n";

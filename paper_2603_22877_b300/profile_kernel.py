@@ -2,6 +2,10 @@
 profilers: python -m paper_2603_22877_b300.profile_kernel --workload NAME --launches N
 With --stages N it runs N annealing stages instead (the autotuned configuration,
 20 PGD iterations each, from a captured CUDA graph), for launch lists of a stage.
+The autotuner's choice is printed as an index into the instance's launch
+configurations; --config INDEX pins that one instead of tuning, so that a run under
+a profiler (where the tuner's timings are distorted) uses the kernels a plain run
+chose.
 
 Workloads are the seeded synthetic instances of the `workloads` package; the
 smaller variants keep a profiler capture short."""
@@ -31,6 +35,7 @@ def main():
     p.add_argument("--launches", type=int, default=3)
     p.add_argument("--plain", action="store_true")
     p.add_argument("--stages", type=int, default=0, help="annealing stages to run instead of bare launches")
+    p.add_argument("--config", type=int, default=-1, help="with --stages: pin this launch configuration (index)")
     args = p.parse_args()
     import torch
     from paper_2603_22877_b300 import build
@@ -52,11 +57,19 @@ def main():
         S = Solver(P, comp, R, eta=0.02, b_scale=inst.scale, t_max=20, sweeps=20, use_graph=True)
         S.reset(a, b)
         sched = [inst.scale / (0.1 * t) for t in range(1, 21)]
-        S.tune(sched[0])
+        cfgs = comp.launch_configs(R)
+        key = lambda c: (c.variant, c.restarts_per_lane, c.staged_reals, c.warps)
+        if args.config >= 0:
+            comp.select_config(R, cfgs[args.config])
+            idx = args.config
+        else:
+            best = S.tune(sched[0])
+            idx = [key(c) for c in cfgs].index(key(best))
         for k in range(args.stages):
             S.stage(sched[k % len(sched)], k + 1)
         torch.cuda.synchronize()
-        print("stages", args.stages, "iters", int(S.iters.max()), "n_unsat min", int(S.n_unsat.min()))
+        print("stages", args.stages, "iters", int(S.iters.max()), "n_unsat min", int(S.n_unsat.min()),
+              "config", idx, cfgs[idx].as_dict())
         return
     work = torch.empty(comp.plain_work(R), device="cuda") if args.plain else None
     for _ in range(args.launches):

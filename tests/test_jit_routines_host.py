@@ -293,3 +293,28 @@ def test_generated_projection_routines_match_the_oracle(generator):
             np.testing.assert_allclose(b, ref, atol=2e-5 * scale, err_msg=f"shape {k} trial {trial}")
             want = float(((y0.astype(np.float64) - ref) ** 2).sum())
             assert abs(part[0] - want) <= 1e-4 * want + 1e-3, (part[0], want)
+
+
+def test_polish_multiplies_only_by_exact_reciprocals(generator):
+    """The generated polish replaces the division by qq (the free terms' squared
+    coefficients) with a product only when every nonzero qq the flags can give is a
+    power of two, where x / 2^k and x * 2^-k round the same real number: unit chains
+    (qq in {1, 2}) and coefficients +-2 (qq in {4, 8}) multiply, coefficients (1, 3)
+    (qq = 10) divide."""
+    source, _ = generator
+    lib = source.lib
+
+    def src(coefs):
+        arrs = [np.asarray([0, len(coefs)], np.int32), np.arange(len(coefs), dtype=np.int32),
+                np.asarray(coefs, np.float32), np.asarray([1.0 / sum(c * c for c in coefs)], np.float32),
+                np.zeros(1, np.uint8)]
+        buf = C.create_string_buffer(1 << 16)
+        assert lib.proj_src(1, len(coefs), 1, *[a.ctypes.data_as(C.c_void_p) for a in arrs], buf, 1 << 16) > 0
+        return buf.value.decode()
+
+    unit = src([1.0, -1.0])
+    assert "__fdiv_rn" not in unit and "(n1 ? (n0 ? 0x1p-1f : 0x1p+0f)" in unit
+    two = src([2.0, -2.0])
+    assert "__fdiv_rn" not in two and "0x1p-3f" in two and "0x1p-2f" in two
+    assert "__fdiv_rn" in src([1.0, 3.0])
+    assert "__fdiv_rn" in src([1.0, 1.0, 1.0, 1.0, 1.0])  # more than four terms: always the division
