@@ -65,8 +65,9 @@ Nvrtc& nvrtc() {
 // (TRUE) / V+1 (FALSE).  Nodes testing the same literal form a group (grp = its
 // first node); each pass reads a group's slot word and q from shared memory
 // once, at the group's first node in that pass's order.  The messages t_v
-// (Alg. 3) and b_v (Alg. 4) live in registers, and the reverse pass sums
-// t_v (b_hi - b_lo) over a group and issues the group's one shared-memory
+// (Alg. 3, started at w_c instead of 1, so that t_v = w_c m_td[v]) and b_v
+// (Alg. 4) live in registers, and the reverse pass sums t_v (b_hi - b_lo) over a
+// group -- the group's w_c dC/dq -- and issues the group's one shared-memory
 // update at its last node.  The terminals' messages are constants, and every
 // operation with a constant operand is folded as the code is generated.
 namespace {
@@ -168,8 +169,10 @@ std::string shape_routine(int rank, int V, const uint16_t* hi, const uint16_t* l
     std::vector<Ex> t(V, Ex{Ex::ZERO, ""});
     std::vector<int> loaded(V, 0);  // bit 0: the forward pass holds q of the group in f<g>
     if (adj) {
+      // the root's top-down message is w_c instead of 1: every m_td, and so every
+      // group's adjoint sum, carries the weight, and no group multiplies by it
       o << "    const V wv = wc.v[k];\n";
-      t[0] = {Ex::ONE, ""};
+      t[0] = {Ex::VAR, "wv"};
       for (int v = 0; v < V; ++v) {  // Alg. 3: push to non-terminal children
         const int g = grp[v];
         if (hi[v] >= V && lo[v] >= V) continue;
@@ -208,9 +211,8 @@ std::string shape_routine(int rank, int V, const uint16_t* hi, const uint16_t* l
       if (adj) {
         acc[g] = E.fma(t[v], d, acc[g]);
         if (g == v && acc[g].k != Ex::ZERO) {
-          const Ex gw = E.mul({Ex::VAR, "wv"}, acc[g]);  // emitted before the line that uses it
           const std::string wd = word(g, false);  // fetched at the group's last node already
-          o << "    atomicAdd(reinterpret_cast<float*>(gb + " << wd << " + 128 * k), " << E.name(gw) << ");\n";
+          o << "    atomicAdd(reinterpret_cast<float*>(gb + " << wd << " + 128 * k), " << E.name(acc[g]) << ");\n";
         }
       }
     }
