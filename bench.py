@@ -4,8 +4,11 @@
 A step is one annealing stage of Alg. 2 over one batch of restarts: `iters`
 iterations of [relax -> forward COP -> adjoint -> PGD + projection -> ||g||^2
 test], then round + exact check + ERWA.  The stage runs from a captured CUDA
-graph (fused form).  value = decision-node visits of the forward+adjoint sweep
-(nodes in C_sigma x restarts x iterations run) per second, whole job.
+graph, its iterations in the stage form the tuner found fastest (separate
+launches, one persistent forward + adjoint + PGD kernel for the stage, or that
+kernel once per iteration; all three timed in stage_forms_ms).  value =
+decision-node visits of the forward+adjoint sweep (nodes in C_sigma x restarts x
+iterations run) per second, whole job.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload large_scheduling] [--iters 20] [--tts SECONDS]
@@ -82,6 +85,10 @@ def parse():
     p.add_argument("--tts-seeds", type=int, default=5,
                    help="initial-point seeds per form; the median is PAR-2 (a miss counts twice the limit)")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--stage-form", default="auto", choices=["auto", "launches", "stage", "iteration"],
+                   help="how a stage runs its PGD iterations: separate launches per iteration, one persistent "
+                        "kernel for the stage, that kernel once per iteration, or auto (the fastest of the three, "
+                        "timed by Solver.tune)")
     p.add_argument("--roofline-launches", type=int, default=10)
     p.add_argument("--gradient-time", action="store_true",
                    help="the paper's gradient-time experiment on the random hybrid benchmark instead of the bench")
@@ -502,10 +509,13 @@ def our_arm(args):
     info = comp.info
     eta = args.eta if args.eta is not None else 0.02
     a0, b0 = W.initial_point(inst, R, seed=replica_seed(rank))
-    S = Solver(P, comp, R, eta=eta, b_scale=inst.scale, t_max=args.iters, sweeps=20, use_graph=True)
+    S = Solver(P, comp, R, eta=eta, b_scale=inst.scale, t_max=args.iters, sweeps=20, use_graph=True,
+               stage_form=args.stage_form)
     S.reset(a0, b0)
     sched = [inst.scale / (0.1 * t) for t in range(1, 21)]
-    launch = S.tune(sched[0]).as_dict()  # autotuned kernel configuration (fsmt_autotune)
+    # autotuned forward + adjoint configuration (fsmt_autotune), then the stage form
+    launch = S.tune(sched[0]).as_dict()
+    stage_form = S.chosen_stage_form
     stream = torch.cuda.current_stream()
     nodes = info["n_obj_nodes"]
 
@@ -515,6 +525,7 @@ def our_arm(args):
     for k in range(args.warmup):
         step(k)
     torch.cuda.synchronize()
+    S.check_stage_status()
     clocks = Clocks(local)
     clocks.start()
     if ws > 1:
@@ -527,11 +538,15 @@ def our_arm(args):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
+    S.check_stage_status()
     # a stage stops early only when every restart has converged: count what ran
     iters_per_step = int(S.iters.max().item())
     ms = max_over_ranks(ms, dev)
     clk = clocks.stop()
     value = whole_job_rate(nodes * R * iters_per_step * args.steps, ws, ms)
+
+    # every stage form timed on the same state: the tuner's own timings (two stages each)
+    stage_forms = dict(S.stage_form_ms or {stage_form: ms / args.steps})
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     a_h = torch.from_numpy(a0).pin_memory()
@@ -545,7 +560,7 @@ def our_arm(args):
     e2e_s = max_over_ranks(time.perf_counter() - t0, dev)
     e2e_value = whole_job_rate(nodes * R * iters_per_step * args.steps, ws, 1000.0 * e2e_s)
     h2d = (inst.n_bool + inst.n_real) * R * 4
-    d2h = R * 8
+    d2h = R * 8 + 4  # #Unsat and the objective per restart, and the stage's error bits
 
     # roofline of the dominant kernel: the fused forward+adjoint, timed alone with events
     da, db, dw = S.a, S.b, S.w
@@ -666,8 +681,13 @@ def our_arm(args):
     # test; then round + check: over the chunks for C_sigma, one warp per constraint
     # for the rest (graph iterations past convergence still launch)
     checks = (info["n_chunks"] > 0) + (info["n_chunks"] == 0 or inst.n_cons > info["n_obj_cons"])
-    launches_per_step = 3 + args.iters * (3 + (inst.n_bool > 0) + (info["n_free_reals"] > 0) +
-                                          (info["n_components"] > 0)) + checks
+    if stage_form == "stage":  # parameters, stage start, weight sums, iteration start, the stage kernel, checks
+        launches_per_step = 5 + checks
+    elif stage_form == "iteration":  # the same with the stage kernel once per iteration
+        launches_per_step = 4 + args.iters + checks
+    else:
+        launches_per_step = 3 + args.iters * (3 + (inst.n_bool > 0) + (info["n_free_reals"] > 0) +
+                                              (info["n_components"] > 0)) + checks
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -675,13 +695,19 @@ def our_arm(args):
                 "config": {"workload": args.workload, "restarts": R, "n_vars": inst.n_bool + inst.n_real,
                            "n_bool": inst.n_bool, "n_real": inst.n_real, "n_cons": inst.n_cons,
                            "n_obj_cons": info["n_obj_cons"], "n_obj_nodes": nodes, "atoms": inst.n_atoms,
-                           "iters_per_step": iters_per_step, "eta": eta, "form": "fused + CUDA graph",
+                           "iters_per_step": iters_per_step, "eta": eta,
+                           "form": {"stage": "fused forward + adjoint + PGD, one persistent kernel per stage",
+                                    "iteration": "fused forward + adjoint + PGD, one persistent kernel per iteration",
+                                    "launches": "fused forward + adjoint, PGD kernels, separate launches per "
+                                                "iteration"}[stage_form] + ", CUDA graph",
+                           "stage_form": stage_form,
                            "l2": "inputs larger than L2 (diagrams + weights > 126 MB)",
                            "compile_s": compile_s, "upload_s": upload_s, "parallelism": f"replicas x{ws}",
                            "launch": launch},
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-                "gpu_launches": launches_per_step * args.steps, "clocks": clk, "plain": plain,
+                "gpu_launches": launches_per_step * args.steps, "clocks": clk, "stage_forms_ms": stage_forms,
+                "plain": plain,
                 "per_instance": per_instance,
                 "time_to_sat": tts}
         print(json.dumps(line), flush=True)

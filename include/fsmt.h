@@ -41,8 +41,8 @@ typedef enum {
   FSMT_EINVAL = -1,   /* invalid argument or unsupported input */
   FSMT_ENOMEM = -2,   /* host or device allocation failed */
   FSMT_ECUDA = -3,    /* a CUDA runtime call or launch failed */
-  FSMT_ETIMEOUT = -4, /* a bounded device wait gave up (reserved: no kernel waits on
-                         another block, a flag or a peer) */
+  FSMT_ETIMEOUT = -4, /* a bounded device wait gave up: the persistent stage kernel's
+                         grid barrier (fsmt_solve_stage_host) */
   FSMT_ENAN = -5,     /* non-finite state detected (fsmt_solve_stage_host; device calls
                          mark it per restart in n_unsat instead, see fsmt_round_check) */
   FSMT_ESTATE = -6    /* call out of order (e.g. device call before fsmt_upload) */
@@ -381,10 +381,28 @@ fsmt_status fsmt_mark_nonfinite(const fsmt_compiled* c, int32_t R, const uint8_t
  * when the step is normalised).  All buffers are caller
  * owned device memory; grad_a/grad_b are work buffers that the stage leaves at
  * zero.  ctl is a device int32[4] control block (ctl[0] = restarts still
- * iterating, ctl[1] = error bits: 1 = non-finite ||g||^2 seen).  With use_graph
- * != 0 the launches of a stage are captured once in a CUDA graph (per compiled
- * object and buffer set) and replayed; the scalar parameters travel in params (a
- * device float[16] buffer), so one graph serves every sigma. */
+ * iterating, ctl[1] = error bits: 1 = non-finite ||g||^2 seen, 4 = the persistent
+ * kernel gave up waiting at a grid barrier; ctl[2..3] = that kernel's grid barrier,
+ * reset by the stage itself).  With use_graph != 0 the launches of a stage are
+ * captured once in a CUDA graph (per compiled object and buffer set) and replayed;
+ * the scalar parameters travel in params (a device float[16] buffer), so one graph
+ * serves every sigma.
+ *
+ * With persistent != 0, and when fsmt_stage_form reports the persistent forms for
+ * R, Alg. 1's loop body runs fused in one persistent cooperative kernel (forward +
+ * adjoint over C_sigma, grid barrier, PGD step + projection of every real and
+ * Boolean, grid barrier whose last CTA applies the epsilon test; the forward +
+ * adjoint phase is the configuration chosen by fsmt_autotune / fsmt_select_config):
+ * persistent = 1 runs all t_max iterations in ONE launch (a stage is five launches
+ * -- parameters, stage start, weight sum, iteration start, the stage kernel -- before
+ * the round check); persistent = 2 launches the same kernel once per iteration (no
+ * loop inside it, so that the forward + adjoint phase is compiled as in its own
+ * kernel).  Each barrier waits at most 5 s
+ * for the slowest CTA (the environment variable FSMT_STAGE_BARRIER_NS, read at
+ * each launch or graph capture, sets another limit in ns); a kernel that gave up
+ * sets bit 4 of ctl[1] and ends, and fsmt_solve_stage_host returns FSMT_ETIMEOUT.  Results equal the separate-launch
+ * form's up to the order of floating-point atomic additions.  One stage at a time
+ * per state (the barrier lives in its ctl). */
 typedef struct {
   int32_t R;
   float* a;        /* [n_bool][R] */
@@ -412,14 +430,36 @@ typedef struct {
   int32_t use_graph;
   int32_t polish;        /* feasibility passes after Dykstra (see fsmt_pgd_step) */
   int32_t normalize_eta; /* 1: eta_r = eta * n_obj / wsum[r] */
+  int32_t persistent;    /* 0: separate launches per iteration; 1: one persistent kernel for the
+                            stage; 2: one persistent kernel per iteration (where available) */
 } fsmt_stage_config;
 
 fsmt_status fsmt_solve_stage(fsmt_compiled* c, const fsmt_stage_config* cfg, fsmt_state* s, void* stream);
 
+/* Whether fsmt_solve_stage with persistent = 1 or 2 runs the persistent kernel at R
+ * restarts (1) or falls back to separate launches per iteration (0): the
+ * persistent form needs the run-time compiled module (NVRTC), a stage kernel for
+ * the chosen forward + adjoint configuration (the chunked kernel of the generated
+ * routines, or the warp-per-constraint kernel), at most 1e11 node visits per
+ * iteration, and the largest block of coupled reals within one CTA's shared memory.
+ * ESTATE before fsmt_upload. */
+fsmt_status fsmt_stage_form(const fsmt_compiled* c, int32_t R, int32_t* persistent_out);
+
+/* Per-phase device timestamps of the persistent stage kernel, for profiling (no
+ * counterpart in the paper).  With trace != NULL every later persistent stage of c
+ * writes global-timer readings (ns) into the caller's device buffer trace, which
+ * holds 1 + 2 t_max uint64: [0] the kernel's start, [1 + 2 i] the moment the last CTA
+ * finished iteration i's forward + adjoint phase, [2 + 2 i] the moment the last CTA
+ * finished its PGD phase and the epsilon test ran; entries of iterations not run keep
+ * their old values.  NULL turns it off.  Stages captured in a CUDA graph keep the
+ * buffer they were captured with (the graph is keyed by it).  EINVAL for a NULL c. */
+fsmt_status fsmt_stage_trace(fsmt_compiled* c, uint64_t* trace);
+
 /* The same stage driven from HOST buffers: copies a[n_bool*R] and b[n_real*R]
  * (host, ideally pinned) into the device state, runs fsmt_solve_stage, and
- * copies n_unsat[R] and obj[R] back to host buffers (may be NULL).  Synchronises
- * the stream before returning.  Errors as fsmt_solve_stage, and FSMT_ENAN when
+ * copies n_unsat[R] and obj[R] back to host buffers (may be NULL), and ctl[1].
+ * Synchronises the stream before returning.  Errors as fsmt_solve_stage,
+ * FSMT_ETIMEOUT when the persistent kernel gave up at a grid barrier, and FSMT_ENAN when
  * n_unsat is copied back and some restart's point is non-finite (bit 31 of its
  * n_unsat, as fsmt_round_check marks it; the outputs are still written). */
 fsmt_status fsmt_solve_stage_host(fsmt_compiled* c, const fsmt_stage_config* cfg, fsmt_state* s,

@@ -42,7 +42,7 @@ class StageConfig(C.Structure):
     _fields_ = [("sigma", C.c_float), ("eta", C.c_float), ("b_scale", C.c_float), ("eps", C.c_float),
                 ("t_max", C.c_int32), ("sweeps", C.c_int32), ("rho", C.c_float), ("gamma", C.c_float),
                 ("update_w", C.c_int32), ("use_graph", C.c_int32), ("polish", C.c_int32),
-                ("normalize_eta", C.c_int32)]
+                ("normalize_eta", C.c_int32), ("persistent", C.c_int32)]
 
 
 P = C.c_void_p
@@ -92,6 +92,8 @@ PROTOTYPES = {
     "fsmt_converge": [P, i32, f32, P, P, P, P, P],
     "fsmt_mark_nonfinite": [P, i32, P, P, P],
     "fsmt_solve_stage": [P, C.POINTER(StageConfig), C.POINTER(State), P],
+    "fsmt_stage_form": [P, i32, C.POINTER(i32)],
+    "fsmt_stage_trace": [P, P],
     "fsmt_solve_stage_host": [P, C.POINTER(StageConfig), C.POINTER(State), P, P, P, P, P],
     "fsmt_last_error": [],
     "fsmt_version": [],

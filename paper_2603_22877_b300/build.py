@@ -11,7 +11,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libfsmt.so")
 SOURCES = ["fsmt_device.cu", "fsmt_host.cpp", "fsmt_jit.cpp"]
-HEADERS = ["fsmt_internal.h", "fsmt_devview.cuh", "fsmt_chunked.cuh", "fsmt_proj.cuh", "fsmt_jit_src.inc",
+HEADERS = ["fsmt_internal.h", "fsmt_devview.cuh", "fsmt_chunked.cuh", "fsmt_proj.cuh", "fsmt_stage.cuh", "fsmt_jit_src.inc",
            os.path.join("..", "..", "include", "fsmt.h")]
 
 
@@ -37,11 +37,12 @@ def write_jit_sources():
     """Embeds the device headers as strings, for the run-time compiler (fsmt_jit.cpp)."""
     parts = []
     for var, name in (("kJitDevviewSrc", "fsmt_devview.cuh"), ("kJitChunkedSrc", "fsmt_chunked.cuh"),
-                      ("kJitProjSrc", "fsmt_proj.cuh")):
+                      ("kJitProjSrc", "fsmt_proj.cuh"), ("kJitStageSrc", "fsmt_stage.cuh")):
         text = open(os.path.join(CSRC, name)).read()
         assert ")FSMTSRC" not in text
         parts.append(f'static const char* {var} = R"FSMTSRC(\n{text})FSMTSRC";\n')
-    body = "// generated by build.py from fsmt_devview.cuh, fsmt_chunked.cuh and fsmt_proj.cuh; do not edit\n" + "".join(parts)
+    body = ("// generated by build.py from fsmt_devview.cuh, fsmt_chunked.cuh, fsmt_proj.cuh and fsmt_stage.cuh;"
+            " do not edit\n" + "".join(parts))
     if not os.path.exists(JIT_INC) or open(JIT_INC).read() != body:
         with open(JIT_INC, "w") as f:
             f.write(body)

@@ -18,15 +18,25 @@ __device__ __forceinline__ float load_param(const float* prm, int slot, float fa
   return prm ? prm[slot] : fallback;
 }
 
+// A read of the restarts' point (a, b).  Kernels that run one pass read it through
+// the read-only path; the persistent stage kernel, whose PGD phase rewrites a and b
+// between its forward + adjoint phases, reads it through L2 (CO = true), because the
+// read-only path is only defined for data that no thread of the kernel writes.
+template <bool CO>
+__device__ __forceinline__ float ld_state(const float* p) {
+  return CO ? __ldcg(p) : __ldg(p);
+}
+
 // ------------------------------------------------------- literal probability --
 // p = P[variable TRUE]; gz = dd/dz for atoms (0 for Booleans).  Eq. rounding and
 // Eq. sampling.  s_inv = 1 / (sqrt 2 sigma); s_inv < 0 stands for sigma = 0, which
 // decides the atom exactly; s_inv = 0 for sigma = infinity gives p = 1/2, gz = 0.
+template <bool CO = false>
 __device__ __forceinline__ void literal_prob(const DevView& d, int lab, int R, int r, bool ok, float s_inv,
                                              const float* __restrict__ a, const float* __restrict__ b, float& p,
                                              float& gz) {
   if (lab < d.n_bool) {
-    float av = ok ? __ldg(a + (size_t)lab * R + r) : 0.f;
+    float av = ok ? ld_state<CO>(a + (size_t)lab * R + r) : 0.f;
     p = 0.5f * (1.f - av);
     gz = 0.f;
     return;
@@ -36,7 +46,7 @@ __device__ __forceinline__ void literal_prob(const DevView& d, int lab, int R, i
   if (s_inv >= 0.f) {
     float z = -__ldg(d.atom_q0f + i);
     for (int k = k0; k < k1; ++k) {
-      float bv = ok ? __ldg(b + (size_t)__ldg(d.atom_var + k) * R + r) : 0.f;
+      float bv = ok ? ld_state<CO>(b + (size_t)__ldg(d.atom_var + k) * R + r) : 0.f;
       z = fmaf(__ldg(d.atom_coef + k), bv, z);
     }
     const float si = __ldg(d.atom_inv_norm + i) * s_inv;  // 1 / (sqrt(2) sigma ||q||)
@@ -47,7 +57,7 @@ __device__ __forceinline__ void literal_prob(const DevView& d, int lab, int R, i
     Fixed320 acc;
     acc.clear();
     for (int k = k0; k < k1; ++k) {
-      float bv = ok ? __ldg(b + (size_t)__ldg(d.atom_var + k) * R + r) : 0.f;
+      float bv = ok ? ld_state<CO>(b + (size_t)__ldg(d.atom_var + k) * R + r) : 0.f;
       uint32_t m;
       int e;
       bool neg;
@@ -148,7 +158,7 @@ __device__ __forceinline__ bool shape_dispatch(int shape, const unsigned* sl, co
 
 // GENERIC = false: every constraint has a generated routine, so the generic
 // path and its per-warp message rows are left out (more warps fit).
-template <bool ADJ, int RPL, bool GENERIC = true>
+template <bool ADJ, int RPL, bool GENERIC = true, bool CO = false>
 __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigma, const float* prm, int vcap,
                                              const float* __restrict__ w, const float* __restrict__ a,
                                              const float* __restrict__ b, float* __restrict__ grad_a,
@@ -221,7 +231,7 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
       float* dst = s_b + (t & 1) * rcap * RPL * 32;
       for (int e = threadIdx.x; e < nre; e += blockDim.x) {
         const int r = (t * RPL + (e >> 5) % RPL) * 32 + (e & 31);
-        dst[e] = r < R ? __ldg(b + (size_t)__ldg(d.real_id + e0 + e / (RPL * 32)) * R + r) : 0.f;
+        dst[e] = r < R ? ld_state<CO>(b + (size_t)__ldg(d.real_id + e0 + e / (RPL * 32)) * R + r) : 0.f;
       }
     };
     // dC/db of tile t: one global update per real and restart, then the buffer is cleared
@@ -262,7 +272,7 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
               const float g = gi[32 * k];
               if (rf < R && g != 0.f) atomicAdd(grad_a + (size_t)lab * R + rf, sg * g);
             }
-            if (do_p) pp.v[k] = rp < R ? 0.5f * (1.f - sg * __ldg(a + (size_t)lab * R + rp)) : 0.f;
+            if (do_p) pp.v[k] = rp < R ? 0.5f * (1.f - sg * ld_state<CO>(a + (size_t)lab * R + rp)) : 0.f;
           }
         } else if (staged && s_inv >= 0.f) {
           // an atom, its reals staged: z = q.y - q0 of both tiles in one sweep
@@ -322,7 +332,7 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
               if (rf < R && g != 0.f) {
                 float z = -s_q0[i];
                 for (int j = 0; j < tc; ++j)
-                  z = fmaf(s_tcoef[tb + j], __ldg(b + (size_t)s_rid[s_tvar[tb + j]] * R + rf), z);
+                  z = fmaf(s_tcoef[tb + j], ld_state<CO>(b + (size_t)s_rid[s_tvar[tb + j]] * R + rf), z);
                 const float si = s_si[i], u = z * si;
                 const float gz = sg * g * kTwoOverSqrtPi * __expf(-u * u) * si;  // dC/dz
                 for (int j = 0; j < tc; ++j)
@@ -334,12 +344,12 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
               if (s_inv >= 0.f) {
                 float z = -s_q0[i];
                 for (int j = 0; j < tc; ++j)
-                  z = fmaf(s_tcoef[tb + j], ok ? __ldg(b + (size_t)s_rid[s_tvar[tb + j]] * R + rp) : 0.f, z);
+                  z = fmaf(s_tcoef[tb + j], ok ? ld_state<CO>(b + (size_t)s_rid[s_tvar[tb + j]] * R + rp) : 0.f, z);
                 const float u = z * s_si[i];
                 pp.v[k] = half_erfc_as(sg * u, __expf(-u * u));
               } else {
                 float p, gz;
-                literal_prob(d, lab, R, rp, ok, -1.f, a, b, p, gz);
+                literal_prob<CO>(d, lab, R, rp, ok, -1.f, a, b, p, gz);
                 pp.v[k] = raw < 0 ? 1.f - p : p;  // exact: p is 0 or 1
               }
             }
@@ -473,6 +483,92 @@ __device__ __forceinline__ void chunked_body(const DevView& d, int R, float sigm
   }
 }
 
+
+// ---------------------------------------------------- warp per constraint --
+// One warp per constraint of C_sigma (grid-stride), looping over restart tiles;
+// the constraint's nodes are staged once in the warp's shared memory and reused
+// for every tile.  Per lane: Alg. 3 (top-down messages m_td), then, if ADJ,
+// Alg. 4 (bottom-up messages m_bu written over m_td in reverse topological
+// order, so one array serves both) with the gradient scattered by atomics.
+template <bool ADJ, bool CO = false>
+__device__ __forceinline__ void fused_warp_body(const DevView& d, int R, float sigma, const float* prm, int vcap,
+                                                const float* __restrict__ w, const float* __restrict__ a,
+                                                const float* __restrict__ b, float* __restrict__ grad_a,
+                                                float* __restrict__ grad_b, float* __restrict__ obj,
+                                                float* __restrict__ cop) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
+  const size_t wb = (size_t)vcap * 8 + (size_t)(3 * vcap + 2) * 128;
+  uint2* snode = reinterpret_cast<uint2*>(smem + warp * wb);
+  float* sp = reinterpret_cast<float*>(snode + vcap);
+  float* sg = sp + vcap * 32;
+  float* sm = sg + vcap * 32;
+  float* obj_s = (R <= kMaxObjSmemR) ? reinterpret_cast<float*>(smem + W * wb) : nullptr;
+  if (obj_s) {
+    for (int r = threadIdx.x; r < R; r += blockDim.x) obj_s[r] = 0.f;
+    __syncthreads();
+  }
+  sigma = load_param(prm, P_SIGMA, sigma);
+  const float s_inv = sigma > 0.f ? kInvSqrt2 / sigma : -1.f;  // < 0: sigma = 0, exact; 0: sigma = inf
+  const int n_tiles = (R + 31) >> 5;
+  for (int s = blockIdx.x * W + warp; s < d.n_obj; s += gridDim.x * W) {
+    const int nb = __ldg(d.con_ptr + s);
+    const int V = __ldg(d.con_ptr + s + 1) - nb;
+    const int cid = __ldg(d.con_id + s);
+    const int root = __ldg(d.con_root + s);
+    for (int i = lane; i < V; i += 32) snode[i] = d.nodes[nb + i];
+    __syncwarp();
+    for (int t = 0; t < n_tiles; ++t) {
+      const int r = t * 32 + lane;
+      const bool ok = r < R;
+      for (int v = 0; v < V + 2; ++v) sm[v * 32 + lane] = 0.f;
+      sm[root * 32 + lane] = 1.f;
+      for (int v = 0; v < V; ++v) {  // Alg. 3, topological order
+        const uint2 nd = snode[v];
+        const int hi = nd.y & 0xffff, lo = nd.y >> 16;
+        float p, gz;
+        literal_prob<CO>(d, (int)nd.x, R, r, ok, s_inv, a, b, p, gz);
+        sp[v * 32 + lane] = p;
+        if (ADJ) sg[v * 32 + lane] = gz;
+        const float mv = sm[v * 32 + lane];
+        sm[hi * 32 + lane] = fmaf(p, mv, sm[hi * 32 + lane]);
+        sm[lo * 32 + lane] = fmaf(1.f - p, mv, sm[lo * 32 + lane]);
+      }
+      const float cp = sm[V * 32 + lane];
+      const float wc = ok ? __ldg(w + (size_t)cid * R + r) : 0.f;
+      if (ok) {
+        if (cop) cop[(size_t)cid * R + r] = cp;
+        const float contrib = wc * (1.f - 2.f * cp);
+        if (obj) {
+          if (obj_s)
+            atomicAdd(obj_s + r, contrib);
+          else
+            atomicAdd(obj + r, contrib);
+        }
+      }
+      if (ADJ) {  // Alg. 4, reverse topological order
+        sm[V * 32 + lane] = 1.f;
+        sm[(V + 1) * 32 + lane] = 0.f;
+        for (int v = V - 1; v >= 0; --v) {
+          const uint2 nd = snode[v];
+          const int hi = nd.y & 0xffff, lo = nd.y >> 16;
+          const float mh = sm[hi * 32 + lane], ml = sm[lo * 32 + lane];
+          const float p = sp[v * 32 + lane];
+          const float td = sm[v * 32 + lane];
+          const float diff = mh - ml;
+          sm[v * 32 + lane] = fmaf(p, diff, ml);
+          if (ok) scatter_grad(d, (int)nd.x, R, r, wc * td * diff, sg[v * 32 + lane], grad_a, grad_b);
+        }
+      }
+    }
+    __syncwarp();
+  }
+  if (obj_s && obj) {
+    __syncthreads();
+    for (int r = threadIdx.x; r < R; r += blockDim.x)
+      if (obj_s[r] != 0.f) atomicAdd(obj + r, obj_s[r]);
+  }
+}
 
 #ifndef FSMT_JIT_SHAPES
 // Ahead-of-time build: no generated routines, every constraint takes the generic path.

@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -16,6 +17,7 @@
 #include "fsmt_internal.h"
 #include "fsmt_chunked.cuh"
 #include "fsmt_proj.cuh"
+#include "fsmt_stage.cuh"
 
 int fsmt_fused_limit_ok(const fsmt::Compiled& C);  // below
 
@@ -23,7 +25,6 @@ namespace fsmt {
 
 namespace {
 
-constexpr int kFusedThreads = 256;  // 8 warps
 constexpr int kSmemBudget = 112 * 1024;
 // shared memory of the chunked kernel without the per-warp message arrays
 inline size_t chunk_fixed_bytes(int rpl, int slot_cap) {
@@ -122,11 +123,7 @@ __device__ __forceinline__ bool literal_truth_exact(const DevView& d, int lab, i
 }
 
 // ---------------------------------------------------------- fused kernel --
-// One warp per constraint of C_sigma (grid-stride), looping over restart tiles;
-// the constraint's nodes are staged once in the warp's shared memory and reused
-// for every tile.  Per lane: Alg. 3 (top-down messages m_td), then, if ADJ,
-// Alg. 4 (bottom-up messages m_bu written over m_td in reverse topological
-// order, so one array serves both) with the gradient scattered by atomics.
+// One warp per constraint of C_sigma (fused_warp_body, fsmt_chunked.cuh).
 template <bool ADJ>
 __global__ void __launch_bounds__(kFusedThreads) k_fused(DevView d, int R, float sigma, const float* prm, int vcap,
                                                          const float* __restrict__ w, const float* __restrict__ a,
@@ -134,78 +131,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_fused(DevView d, int R, float
                                                          float* __restrict__ grad_b, float* __restrict__ obj,
                                                          float* __restrict__ cop, const int* ctl) {
   if (ctl && ctl[0] == 0) return;
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
-  const size_t wb = (size_t)vcap * 8 + (size_t)(3 * vcap + 2) * 128;
-  uint2* snode = reinterpret_cast<uint2*>(smem + warp * wb);
-  float* sp = reinterpret_cast<float*>(snode + vcap);
-  float* sg = sp + vcap * 32;
-  float* sm = sg + vcap * 32;
-  float* obj_s = (R <= kMaxObjSmemR) ? reinterpret_cast<float*>(smem + W * wb) : nullptr;
-  if (obj_s) {
-    for (int r = threadIdx.x; r < R; r += blockDim.x) obj_s[r] = 0.f;
-    __syncthreads();
-  }
-  sigma = load_param(prm, P_SIGMA, sigma);
-  const float s_inv = sigma > 0.f ? kInvSqrt2 / sigma : -1.f;  // < 0: sigma = 0, exact; 0: sigma = inf
-  const int n_tiles = (R + 31) >> 5;
-  for (int s = blockIdx.x * W + warp; s < d.n_obj; s += gridDim.x * W) {
-    const int nb = __ldg(d.con_ptr + s);
-    const int V = __ldg(d.con_ptr + s + 1) - nb;
-    const int cid = __ldg(d.con_id + s);
-    const int root = __ldg(d.con_root + s);
-    for (int i = lane; i < V; i += 32) snode[i] = d.nodes[nb + i];
-    __syncwarp();
-    for (int t = 0; t < n_tiles; ++t) {
-      const int r = t * 32 + lane;
-      const bool ok = r < R;
-      for (int v = 0; v < V + 2; ++v) sm[v * 32 + lane] = 0.f;
-      sm[root * 32 + lane] = 1.f;
-      for (int v = 0; v < V; ++v) {  // Alg. 3, topological order
-        const uint2 nd = snode[v];
-        const int hi = nd.y & 0xffff, lo = nd.y >> 16;
-        float p, gz;
-        literal_prob(d, (int)nd.x, R, r, ok, s_inv, a, b, p, gz);
-        sp[v * 32 + lane] = p;
-        if (ADJ) sg[v * 32 + lane] = gz;
-        const float mv = sm[v * 32 + lane];
-        sm[hi * 32 + lane] = fmaf(p, mv, sm[hi * 32 + lane]);
-        sm[lo * 32 + lane] = fmaf(1.f - p, mv, sm[lo * 32 + lane]);
-      }
-      const float cp = sm[V * 32 + lane];
-      const float wc = ok ? __ldg(w + (size_t)cid * R + r) : 0.f;
-      if (ok) {
-        if (cop) cop[(size_t)cid * R + r] = cp;
-        const float contrib = wc * (1.f - 2.f * cp);
-        if (obj) {
-          if (obj_s)
-            atomicAdd(obj_s + r, contrib);
-          else
-            atomicAdd(obj + r, contrib);
-        }
-      }
-      if (ADJ) {  // Alg. 4, reverse topological order
-        sm[V * 32 + lane] = 1.f;
-        sm[(V + 1) * 32 + lane] = 0.f;
-        for (int v = V - 1; v >= 0; --v) {
-          const uint2 nd = snode[v];
-          const int hi = nd.y & 0xffff, lo = nd.y >> 16;
-          const float mh = sm[hi * 32 + lane], ml = sm[lo * 32 + lane];
-          const float p = sp[v * 32 + lane];
-          const float td = sm[v * 32 + lane];
-          const float diff = mh - ml;
-          sm[v * 32 + lane] = fmaf(p, diff, ml);
-          if (ok) scatter_grad(d, (int)nd.x, R, r, wc * td * diff, sg[v * 32 + lane], grad_a, grad_b);
-        }
-      }
-    }
-    __syncwarp();
-  }
-  if (obj_s && obj) {
-    __syncthreads();
-    for (int r = threadIdx.x; r < R; r += blockDim.x)
-      if (obj_s[r] != 0.f) atomicAdd(obj + r, obj_s[r]);
-  }
+  fused_warp_body<ADJ>(d, R, sigma, prm, vcap, w, a, b, grad_a, grad_b, obj, cop);
 }
 
 // The chunked kernel compiled ahead of time (no per-shape routines: the
@@ -472,6 +398,7 @@ __global__ void k_stage_begin(int R, uint8_t* active, int* iters, int* ctl) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     ctl[0] = R;
     ctl[1] = 0;
+    ctl[2] = 0;  // the persistent stage kernel's barrier: no CTA has arrived
   }
 }
 
@@ -483,41 +410,14 @@ __global__ void k_iter_begin(int R, float* obj, float* gn2, const int* ctl) {
   }
 }
 
-// Eq. critical per restart: the iteration just run is counted, and a restart
-// whose ||g||^2 <= eps^2 stops (active 0); one whose ||g||^2 is not finite stops
-// with active 2 and error bit 1 in ctl[1] (its point may already have been clamped
-// back into the box, so the round check marks it from active).  One block;
-// ctl[0] = restarts still iterating.  gate: return at once when ctl[0] is already 0
-// (the graph's iterations past convergence); eps comes from prm when it is given.
+// Eq. critical per restart (converge_block, fsmt_stage.cuh).  One block.  gate:
+// return at once when ctl[0] is already 0 (the graph's iterations past
+// convergence); eps comes from prm when it is given.
 __global__ void k_converge(int R, const float* prm, float eps_arg, const float* gn2, uint8_t* active, int* iters,
                            int* ctl, int gate) {
   if (gate && ctl[0] == 0) return;
   __syncthreads();
-  const float eps = load_param(prm, P_EPS, eps_arg);
-  const float eps2 = eps * eps;
-  int cnt = 0;
-  for (int r = threadIdx.x; r < R; r += blockDim.x) {
-    if (active[r] != 1) continue;
-    iters[r] += 1;
-    const float g = gn2[r];
-    if (!isfinite(g)) {
-      active[r] = 2;
-      atomicOr(ctl + 1, 1);
-    } else if (g <= eps2) {
-      active[r] = 0;
-    } else {
-      ++cnt;
-    }
-  }
-  __shared__ int red[32];
-  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = cnt;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int s = 0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
-    ctl[0] = s;
-  }
+  converge_block(R, load_param(prm, P_EPS, eps_arg), gn2, active, iters, ctl);
 }
 
 // --------------------------------------------------- round + check + ERWA --
@@ -1153,6 +1053,122 @@ fsmt_status launch_round_check(const Compiled& C, int R, const float* a, const f
   return FSMT_OK;
 }
 
+// ------------------------------------------------- persistent stage kernel --
+// The stage's iterations in one cooperative launch (stage_body, fsmt_stage.cuh),
+// when this instance's run-time compiled module holds a stage kernel for the chosen
+// forward + adjoint configuration.  Phase B's projection runs on the first
+// proj_warps warps of each CTA, as many as fit in the larger of the forward +
+// adjoint phase's shared memory and 32 KB; the grid is every CTA that fits on the
+// GPU at once (a cooperative launch refuses more).
+struct StagePlan {
+  void* kernel = nullptr;
+  bool per_iteration = false;  // kernel runs one iteration a launch (the stage launches it t_max times)
+  int threads = 0, blocks = 0, proj_warps = 0;
+  size_t smem = 0;
+  LaunchCfg cfg{-1, 0, 0, 0, 0};
+};
+// the per-iteration work above which the stage keeps separate launches (a barrier
+// waits at most kStageBarrierNs for the slowest CTA of a phase)
+constexpr double kStageMaxVisits = 1e11;
+constexpr unsigned long long kStageBarrierNs = 5000000000ull;
+
+bool stage_plan(const Compiled& C, int R, bool per_iteration, StagePlan& p) {
+  p.per_iteration = per_iteration;
+  if (C.n_obj == 0 || (double)C.n_obj_nodes * R > kStageMaxVisits) return false;
+  LaunchCfg scratch;
+  const LaunchCfg& x = chosen_config(C, R, scratch);
+  if (x.variant < 0) return false;
+  int warps = 0;
+  size_t smem_a = 0;
+  if (x.variant == kVariantWarp) {
+    const FusedShape f = fused_shape(C, R);
+    p.kernel = p.per_iteration ? C.jit_step_warp : C.jit_stage_warp;
+    warps = f.warps;
+    smem_a = f.smem;
+  } else if ((x.variant == kVariantWide && C.all_specialized) || (x.variant == kVariantJit && !C.all_specialized)) {
+    p.kernel = p.per_iteration ? C.jit_step_chunk[x.rpl - 1] : C.jit_stage_chunk[x.rpl - 1];
+    warps = x.warps;
+    smem_a = x.smem;
+  }
+  if (!p.kernel) return false;
+  const int ncomp = (int)C.comp_var_ptr.size() - 1;
+  p.smem = smem_a;
+  if (ncomp > 0) {
+    auto bytes = [&](int wy) {
+      return (size_t)proj_block_words(C.comp_max_vars, C.comp_max_hs, C.comp_max_nnz, wy) * sizeof(float);
+    };
+    const size_t room = std::max<size_t>(smem_a, 32 * 1024);
+    int wy = warps;
+    while (wy > 1 && bytes(wy) > room) --wy;
+    if (bytes(wy) > kSmemMax) return false;
+    p.proj_warps = wy;
+    p.smem = std::max(smem_a, bytes(wy));
+  }
+  p.threads = warps * 32;
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, (const void*)p.kernel) != cudaSuccess ||
+      p.smem > (size_t)fa.maxDynamicSharedSizeBytes) {
+    cudaGetLastError();
+    return false;
+  }
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)p.kernel, p.threads, p.smem) !=
+          cudaSuccess ||
+      per_sm < 1) {
+    cudaGetLastError();
+    return false;
+  }
+  p.blocks = sm_count() * per_sm;
+  p.cfg = x;
+  return true;
+}
+
+fsmt_status launch_stage_kernel(const Compiled& C, const StagePlan& p, int t_max, int it0, fsmt_state* s,
+                                cudaStream_t st) {
+  StageArgs sa;
+  sa.d = C.view;
+  sa.d.chunk_real_cap = p.cfg.variant == kVariantWarp ? C.view.chunk_real_cap : p.cfg.real_cap;
+  sa.R = s->R;
+  sa.t_max = t_max;
+  sa.vcap = std::max(1, C.max_nodes);
+  sa.proj_warps = p.proj_warps;
+  sa.maxv = C.comp_max_vars;
+  sa.maxh = C.comp_max_hs;
+  sa.maxnz = C.comp_max_nnz;
+  sa.barrier_ns = kStageBarrierNs;
+  if (const char* e = std::getenv("FSMT_STAGE_BARRIER_NS")) {  // tests of the bounded wait
+    const unsigned long long v = std::strtoull(e, nullptr, 10);
+    if (v > 0) sa.barrier_ns = v;
+  }
+  sa.prm = s->params;
+  sa.w = s->w;
+  sa.wsum = s->wsum;
+  sa.a = s->a;
+  sa.b = s->b;
+  sa.ga = s->grad_a;
+  sa.gb = s->grad_b;
+  sa.obj = s->obj;
+  sa.gn2 = s->gnorm2;
+  sa.active = s->active;
+  sa.iters = s->iters;
+  sa.ctl = s->ctl;
+  sa.trace = C.stage_trace;
+  sa.it0 = it0;
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3(p.blocks);
+  lc.blockDim = dim3(p.threads);
+  lc.dynamicSmemBytes = p.smem;
+  lc.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  void* args[] = {&sa};
+  FSMT_CUDA(cudaLaunchKernelExC(&lc, (const void*)p.kernel, args), "persistent stage kernel launch");
+  return FSMT_OK;
+}
+
 template <typename T>
 size_t push_array(std::vector<unsigned char>& blob, const std::vector<T>& v) {
   size_t off = (blob.size() + 255) & ~size_t(255);
@@ -1639,12 +1655,23 @@ fsmt_status fsmt_mark_nonfinite(const fsmt_compiled* c, int32_t R, const uint8_t
   return FSMT_OK;
 }
 
-static fsmt_status enqueue_stage(const Compiled& C, int t_max, fsmt_state* s, cudaStream_t st) {
+// plan: the persistent stage kernel's launch, or NULL for separate launches per iteration
+static fsmt_status enqueue_stage(const Compiled& C, int t_max, fsmt_state* s, const StagePlan* plan,
+                                 cudaStream_t st) {
   const int R = s->R;
   k_stage_begin<<<(R + 255) / 256, 256, 0, st>>>(R, s->active, s->iters, s->ctl);
   FSMT_CUDA(cudaGetLastError(), "stage begin");
   fsmt_status ws = launch_weight_sum(C, R, s->w, s->wsum, st);
   if (ws != FSMT_OK) return ws;
+  if (plan && t_max > 0) {
+    k_iter_begin<<<(R + 255) / 256, 256, 0, st>>>(R, s->obj, s->gnorm2, s->ctl);
+    FSMT_CUDA(cudaGetLastError(), "iteration begin");
+    for (int it = 0; it < (plan->per_iteration ? t_max : 1); ++it) {
+      ws = launch_stage_kernel(C, *plan, t_max, it, s, st);
+      if (ws != FSMT_OK) return ws;
+    }
+    t_max = 0;
+  }
   for (int it = 0; it < t_max; ++it) {
     k_iter_begin<<<(R + 255) / 256, 256, 0, st>>>(R, s->obj, s->gnorm2, s->ctl);
     fsmt_status e = launch_fused(C, true, R, 0.f, s->params, s->w, s->a, s->b, s->grad_a, s->grad_b, s->obj, nullptr,
@@ -1675,11 +1702,13 @@ fsmt_status fsmt_solve_stage(fsmt_compiled* cc, const fsmt_stage_config* cfg, fs
     return FSMT_EINVAL;
   }
   cudaStream_t st = (cudaStream_t)stream;
+  StagePlan plan;
+  const bool persistent = cfg->persistent > 0 && stage_plan(C, s->R, cfg->persistent == 2, plan);
   k_set_params<<<1, 1, 0, st>>>(s->params, cfg->sigma, cfg->eta, cfg->b_scale, cfg->eps, cfg->rho, cfg->gamma,
                                 (float)cfg->update_w, (float)cfg->sweeps, (float)cfg->polish,
                                 (float)cfg->normalize_eta);
   FSMT_CUDA(cudaGetLastError(), "set params");
-  if (!cfg->use_graph) return enqueue_stage(C, cfg->t_max, s, st);
+  if (!cfg->use_graph) return enqueue_stage(C, cfg->t_max, s, persistent ? &plan : nullptr, st);
   // the legacy default stream cannot be captured: use a blocking stream of our own,
   // which the legacy stream's implicit synchronisation orders with the caller's work
   if (st == nullptr || st == cudaStreamLegacy) {
@@ -1699,6 +1728,8 @@ fsmt_status fsmt_solve_stage(fsmt_compiled* cc, const fsmt_stage_config* cfg, fs
   mix((uint64_t)s->R);
   mix((uint64_t)cfg->t_max);
   mix((uint64_t)(C.tuned_R == s->R ? 1 + C.tuned.variant * 64 + C.tuned.rpl * 8 + (C.tuned.real_cap > 0) : 0));
+  mix((uint64_t)persistent + 2 * (uint64_t)(persistent && plan.per_iteration));
+  mix((uint64_t)(uintptr_t)(persistent ? C.stage_trace : nullptr));
   if (!C.graph_exec || C.graph_key != key) {
     if (C.graph_exec) {
       cudaGraphExecDestroy((cudaGraphExec_t)C.graph_exec);
@@ -1706,7 +1737,7 @@ fsmt_status fsmt_solve_stage(fsmt_compiled* cc, const fsmt_stage_config* cfg, fs
     }
     cudaGraph_t g;
     FSMT_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture");
-    fsmt_status q = enqueue_stage(C, cfg->t_max, s, st);
+    fsmt_status q = enqueue_stage(C, cfg->t_max, s, persistent ? &plan : nullptr, st);
     cudaError_t ce = cudaStreamEndCapture(st, &g);
     if (q != FSMT_OK) return q;
     if (ce != cudaSuccess) return cuda_fail(ce, "end capture");
@@ -1718,6 +1749,27 @@ fsmt_status fsmt_solve_stage(fsmt_compiled* cc, const fsmt_stage_config* cfg, fs
     C.graph_key = key;
   }
   FSMT_CUDA(cudaGraphLaunch((cudaGraphExec_t)C.graph_exec, st), "graph launch");
+  return FSMT_OK;
+}
+
+fsmt_status fsmt_stage_trace(fsmt_compiled* c, uint64_t* trace) {
+  if (!c) {
+    set_error("NULL argument");
+    return FSMT_EINVAL;
+  }
+  c->c.stage_trace = reinterpret_cast<unsigned long long*>(trace);
+  return FSMT_OK;
+}
+
+fsmt_status fsmt_stage_form(const fsmt_compiled* c, int32_t R, int32_t* persistent_out) {
+  if (!persistent_out) {
+    set_error("NULL argument");
+    return FSMT_EINVAL;
+  }
+  fsmt_status e = check_ready(c, R);
+  if (e != FSMT_OK) return e;
+  StagePlan plan;
+  *persistent_out = stage_plan(c->c, R, false, plan) && stage_plan(c->c, R, true, plan) ? 1 : 0;
   return FSMT_OK;
 }
 
@@ -1742,7 +1794,13 @@ fsmt_status fsmt_solve_stage_host(fsmt_compiled* cc, const fsmt_stage_config* cf
   if (n_unsat_host)
     FSMT_CUDA(cudaMemcpyAsync(n_unsat_host, s->n_unsat, sizeof(int32_t) * R, cudaMemcpyDeviceToHost, st), "copy n_unsat");
   if (obj_host) FSMT_CUDA(cudaMemcpyAsync(obj_host, s->obj, sizeof(float) * R, cudaMemcpyDeviceToHost, st), "copy obj");
+  int32_t err_bits = 0;
+  FSMT_CUDA(cudaMemcpyAsync(&err_bits, s->ctl + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st), "copy ctl");
   FSMT_CUDA(cudaStreamSynchronize(st), "stage sync");
+  if (err_bits & kCtlBarrierTimeout) {
+    set_error("the persistent stage kernel gave up waiting at a grid barrier");
+    return FSMT_ETIMEOUT;
+  }
   if (n_unsat_host)
     for (size_t r = 0; r < R; ++r)
       if (n_unsat_host[r] < 0) {

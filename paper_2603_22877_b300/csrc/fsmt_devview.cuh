@@ -46,6 +46,7 @@ constexpr int kChunkSlotsGeneric = 192;
 constexpr int kChunkMaxList = 2304;  // words of a chunk's per-constraint literal lists (nodes + padding)
 constexpr int kSlotStride = 64;  // floats per slot row of the per-slot shared arrays (two restarts x 32 lanes)
 constexpr int kChunkThreads = 512;  // threads of the chunked kernel with the generic path (16 warps)
+constexpr int kFusedThreads = 256;  // threads of the warp-per-constraint kernel (8 warps)
 constexpr int kChunkMaxTerms = 768;  // nonzeros of the atoms of a chunk
 constexpr int kChunkMaxReals = 128;   // reals touched by a chunk's atoms
 constexpr int kMaxJitShapes = 16;      // diagram shapes given generated code per instance

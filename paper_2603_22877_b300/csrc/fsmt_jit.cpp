@@ -22,7 +22,7 @@
 #include <vector>
 
 #include "fsmt_internal.h"
-#include "fsmt_jit_src.inc"  // kJitDevviewSrc, kJitChunkedSrc, kJitProjSrc (generated by build.py)
+#include "fsmt_jit_src.inc"  // kJitDevviewSrc, kJitChunkedSrc, kJitProjSrc, kJitStageSrc (generated by build.py)
 
 namespace fsmt {
 
@@ -364,7 +364,7 @@ std::string kernel_name(int wide, int adj, int rpl) {
 std::string generated_source(const Compiled& C) {
   std::ostringstream o;
   o << "#define FSMT_JIT_SHAPES 1\n#define FSMT_JIT_PROJ 1\n" << kJitDevviewSrc << "\n" << kJitChunkedSrc << "\n"
-    << kJitProjSrc << "\nnamespace fsmt {\n\n";
+    << kJitProjSrc << "\n" << kJitStageSrc << "\nnamespace fsmt {\n\n";
   for (size_t k = 0; k < C.proj_shape_comp.size(); ++k) o << proj_routine((int)k + 1, C, C.proj_shape_comp[k]);
   o << "__device__ __forceinline__ bool proj_dispatch(int shape, const float* s_q0, const float* s_lo,"
        " const float* s_hi, float* b, float* gb, const int* cvar, int R, int r, float step, float inv, int sweeps,"
@@ -393,6 +393,30 @@ std::string generated_source(const Compiled& C) {
              " float* __restrict__ grad_b, float* __restrict__ obj, float* __restrict__ cop, const int* ctl) {\n"
           << "  fsmt::chunked_body<" << (adj ? "true" : "false") << ", " << rpl << ", " << (wide ? "false" : "true")
           << ">(d, R, sigma, prm, vcap, w, a, b, grad_a, grad_b, obj, cop, ctl);\n}\n";
+  // the persistent stage kernels (fsmt_stage.cuh): the chunked forward + adjoint
+  // body in the form this instance runs (without the generic path when every
+  // constraint has a routine), and the warp-per-constraint body; both read the point
+  // through L2 (it changes between their phases)
+  const bool wide = C.all_specialized;
+  for (int rpl = 1; rpl <= 2; ++rpl)
+    o << "extern \"C\" __global__ void __launch_bounds__(" << (wide ? "fsmt::kChunkThreadsWide" : "fsmt::kChunkThreads")
+      << ", 1) fsmt_jit_stage_chunk_" << rpl << "(fsmt::StageArgs s) {\n"
+      << "  fsmt::stage_body(s, [&] { fsmt::chunked_body<true, " << rpl << ", " << (wide ? "false" : "true")
+      << ", true>(s.d, s.R, 0.f, s.prm, s.vcap, s.w, s.a, s.b, s.ga, s.gb, s.obj, nullptr, nullptr); });\n}\n";
+  // (at most 51 registers, so that five CTAs of the forward + adjoint phase share an SM,
+  // as they do in the warp kernel of its own)
+  o << "extern \"C\" __global__ void __launch_bounds__(fsmt::kFusedThreads, 5) fsmt_jit_stage_warp(fsmt::StageArgs s) {\n"
+       "  fsmt::stage_body(s, [&] { fsmt::fused_warp_body<true, true>(s.d, s.R, 0.f, s.prm, s.vcap, s.w, s.a, s.b, s.ga,"
+       " s.gb, s.obj, nullptr); });\n}\n";
+  // the same with one iteration per launch
+  for (int rpl = 1; rpl <= 2; ++rpl)
+    o << "extern \"C\" __global__ void __launch_bounds__(" << (wide ? "fsmt::kChunkThreadsWide" : "fsmt::kChunkThreads")
+      << ", 1) fsmt_jit_step_chunk_" << rpl << "(fsmt::StageArgs s) {\n"
+      << "  fsmt::stage_step_body(s, [&] { fsmt::chunked_body<true, " << rpl << ", " << (wide ? "false" : "true")
+      << ", true>(s.d, s.R, 0.f, s.prm, s.vcap, s.w, s.a, s.b, s.ga, s.gb, s.obj, nullptr, nullptr); });\n}\n";
+  o << "extern \"C\" __global__ void __launch_bounds__(fsmt::kFusedThreads, 5) fsmt_jit_step_warp(fsmt::StageArgs s) {\n"
+       "  fsmt::stage_step_body(s, [&] { fsmt::fused_warp_body<true, true>(s.d, s.R, 0.f, s.prm, s.vcap, s.w, s.a, s.b,"
+       " s.ga, s.gb, s.obj, nullptr); });\n}\n";
   o << "extern \"C\" __global__ void __launch_bounds__(256) fsmt_jit_proj(fsmt::DevView d, int R, float eta,"
        " float bscale, int sweeps, int polish, const float* prm, const float* __restrict__ wsum,"
        " float* __restrict__ b, float* __restrict__ gb, float* __restrict__ gn2,"
@@ -405,6 +429,10 @@ std::string generated_source(const Compiled& C) {
 struct Module {
   void* kernel[2][2][2];  // [wide][adjoint][restarts per lane - 1]
   void* proj;             // the projection kernel with generated block routines
+  void* stage_chunk[2];   // persistent stage kernels: chunked [restarts per lane - 1]
+  void* stage_warp;       // and warp per constraint
+  void* step_chunk[2];    // the same, one iteration per launch
+  void* step_warp;
 };
 std::mutex g_mutex;
 std::unordered_map<std::string, Module> g_modules;  // by source text; kept for the process lifetime
@@ -421,6 +449,8 @@ bool jit_build(Compiled& C) {
   C.jit_shapes = 0;
   C.jit_proj = nullptr;
   C.proj_shapes = 0;
+  C.jit_stage_chunk[0] = C.jit_stage_chunk[1] = C.jit_stage_warp = nullptr;
+  C.jit_step_chunk[0] = C.jit_step_chunk[1] = C.jit_step_warp = nullptr;
   const char* off = std::getenv("FSMT_NO_JIT");
   const bool diagrams = !C.jit_shape.empty() && C.chunked_ok, blocks = !C.proj_shape_comp.empty();
   if ((off && *off && *off != '0') || !(diagrams || blocks)) return false;
@@ -458,28 +488,51 @@ bool jit_build(Compiled& C) {
     N.cubin(prog, &cubin[0]);
     N.destroy(&prog);
     cudaLibrary_t lib;
-    if (cudaLibraryLoadData(&lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) != cudaSuccess) {
-      set_error("loading the run-time compiled kernels failed; using the ahead-of-time kernel");
+    // a failure below leaves no error behind for the next launch check to find
+    auto fail = [](const char* what) {
+      cudaGetLastError();
+      set_error(std::string(what) + "; using the ahead-of-time kernel");
       return false;
-    }
+    };
+    if (cudaLibraryLoadData(&lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) != cudaSuccess)
+      return fail("loading the run-time compiled kernels failed");
     Module m{};
     for (int wide = 0; wide < 2; ++wide)
       for (int adj = 0; adj < 2; ++adj)
         for (int r = 0; r < 2; ++r) {
           cudaKernel_t k;
-          if (cudaLibraryGetKernel(&k, lib, kernel_name(wide, adj, r + 1).c_str()) != cudaSuccess) return false;
-          if (cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
-              cudaSuccess)
-            return false;
+          if (cudaLibraryGetKernel(&k, lib, kernel_name(wide, adj, r + 1).c_str()) != cudaSuccess ||
+              cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
+                  cudaSuccess)
+            return fail("preparing a run-time compiled chunked kernel failed");
           m.kernel[wide][adj][r] = (void*)k;
         }
     {
       cudaKernel_t k;
-      if (cudaLibraryGetKernel(&k, lib, "fsmt_jit_proj") != cudaSuccess) return false;
-      if (cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      if (cudaLibraryGetKernel(&k, lib, "fsmt_jit_proj") != cudaSuccess ||
+          cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)(kProjSmemWords * sizeof(float))) != cudaSuccess)
-        return false;
+        return fail("preparing the run-time compiled projection kernel failed");
       m.proj = (void*)k;
+    }
+    // the stage kernels have static shared memory of their own (barrier and epsilon
+    // test): the dynamic part may take what is left of the per-CTA maximum
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    for (int r = 0; r < 6; ++r) {
+      cudaKernel_t k;
+      const std::string kind = r < 3 ? "stage" : "step";
+      const std::string nm = (r % 3) < 2 ? "fsmt_jit_" + kind + "_chunk_" + std::to_string(r % 3 + 1)
+                                         : "fsmt_jit_" + kind + "_warp";
+      cudaFuncAttributes fa;
+      if (cudaLibraryGetKernel(&k, lib, nm.c_str()) != cudaSuccess ||
+          cudaFuncGetAttributes(&fa, (const void*)k) != cudaSuccess ||
+          cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               optin - (int)fa.sharedSizeBytes) != cudaSuccess)
+        return fail("preparing the persistent stage kernels failed");
+      void** slot[6] = {&m.stage_chunk[0], &m.stage_chunk[1], &m.stage_warp,
+                        &m.step_chunk[0], &m.step_chunk[1], &m.step_warp};
+      *slot[r] = (void*)k;
     }
     it = g_modules.emplace(key, m).first;
   }
@@ -490,7 +543,13 @@ bool jit_build(Compiled& C) {
         C.jit_wide[adj][r] = C.all_specialized ? it->second.kernel[1][adj][r] : nullptr;
       }
     C.jit_shapes = (int32_t)C.jit_shape.size();
+    for (int r = 0; r < 2; ++r) {
+      C.jit_stage_chunk[r] = it->second.stage_chunk[r];
+      C.jit_step_chunk[r] = it->second.step_chunk[r];
+    }
   }
+  C.jit_stage_warp = it->second.stage_warp;
+  C.jit_step_warp = it->second.step_warp;
   if (blocks) {
     C.jit_proj = it->second.proj;
     C.proj_shapes = (int32_t)C.proj_shape_comp.size();

@@ -83,14 +83,17 @@ __device__ __forceinline__ bool proj_dispatch(int shape, const float* s_q0, cons
 // itself (half-space offsets, local reals, coefficients, right-hand sides,
 // 1/||q||^2, the box), staged once by the warp's lanes together so that the
 // sweeps read it by broadcast instead of through dependent global loads.
-__device__ __forceinline__ void pgd_comp_body(const DevView& d, int R, float eta, float bscale, int sweeps,
-                                              int polish, const float* prm, const float* __restrict__ wsum,
-                                              float* __restrict__ b, float* __restrict__ gb,
-                                              float* __restrict__ gn2, const uint8_t* __restrict__ active,
-                                              int clear_grad, const int* ctl, int maxv, int maxh, int maxnz) {
-  if (ctl && ctl[0] == 0) return;
-  const int lane = threadIdx.x;
-  const int r = blockIdx.x * 32 + lane;
+// The work of one thread: restart tile `tile`, blocks c0, c0 + cstride, ...; ty is
+// the warp's place among the T / 32 warps that share s_col (the columns' stride is
+// T).  Returns the thread's part of ||g||^2 for its restart.
+__device__ __forceinline__ float pgd_comp_core(const DevView& d, int R, float eta, float bscale, int sweeps,
+                                               int polish, const float* prm, const float* __restrict__ wsum,
+                                               float* __restrict__ b, float* __restrict__ gb,
+                                               const uint8_t* __restrict__ active, int clear_grad, int maxv,
+                                               int maxh, int maxnz, int tile, int c0, int cstride, int ty, int T,
+                                               float* s_col) {
+  const int lane = threadIdx.x & 31;
+  const int r = tile * 32 + lane;
   const bool ok = r < R;
   const bool act = ok && (!active || active[r] == 1);
   eta = restart_eta(d, eta, prm, wsum, r, ok);
@@ -101,14 +104,13 @@ __device__ __forceinline__ void pgd_comp_body(const DevView& d, int R, float eta
   }
   const float step = eta * bscale * bscale, inv = 1.f / (bscale * eta);
   float part = 0.f;
-  extern __shared__ float s_col[];
-  const int T = blockDim.x * blockDim.y, tid = threadIdx.y * blockDim.x + lane;
+  const int tid = ty * 32 + lane;
   float* xs = s_col + tid;           // x(t) at xs[t * T]
   float* ps = xs + maxv * T;         // pbox(t)
   float* hs = ps + maxv * T;         // th(q)
   // the warp's staged block
   const int wwords = (maxh + 1) + 2 * maxnz + 3 * maxh + 2 * maxv;
-  int* s_hp = reinterpret_cast<int*>(s_col + (2 * maxv + maxh) * T) + threadIdx.y * wwords;  // offsets [nh + 1]
+  int* s_hp = reinterpret_cast<int*>(s_col + (2 * maxv + maxh) * T) + ty * wwords;  // offsets [nh + 1]
   int* s_lv = s_hp + maxh + 1;                                   // local real of each term
   float* s_cf = reinterpret_cast<float*>(s_lv + maxnz);          // coefficient of each term
   float* s_q0 = s_cf + maxnz;                                    // right-hand sides
@@ -119,7 +121,7 @@ __device__ __forceinline__ void pgd_comp_body(const DevView& d, int R, float eta
 #define x(t) xs[(t) * T]
 #define pbox(t) ps[(t) * T]
 #define th(q) hs[(q) * T]
-  for (int c = blockIdx.y * blockDim.y + threadIdx.y; c < d.n_comp; c += gridDim.y * blockDim.y) {
+  for (int c = c0; c < d.n_comp; c += cstride) {
     const int v0 = d.comp_var_ptr[c], nv = d.comp_var_ptr[c + 1] - v0;
     const int h0 = d.comp_hs_ptr[c], nh = d.comp_hs_ptr[c + 1] - h0;
     const int e_base = d.hs_ptr[h0], nz = d.hs_ptr[h0 + nh] - e_base;
@@ -241,7 +243,23 @@ __device__ __forceinline__ void pgd_comp_body(const DevView& d, int R, float eta
 #undef x
 #undef pbox
 #undef th
-  reduce_rows_add(part, gn2, r, ok);
+  return part;
+}
+
+// The projection kernel's body: CTA (32 restarts, blockDim.y blocks of reals), grid
+// (restart tiles, groups of blocks); the CTA's ||g||^2 parts summed over its rows.
+__device__ __forceinline__ void pgd_comp_body(const DevView& d, int R, float eta, float bscale, int sweeps,
+                                              int polish, const float* prm, const float* __restrict__ wsum,
+                                              float* __restrict__ b, float* __restrict__ gb,
+                                              float* __restrict__ gn2, const uint8_t* __restrict__ active,
+                                              int clear_grad, const int* ctl, int maxv, int maxh, int maxnz) {
+  if (ctl && ctl[0] == 0) return;
+  extern __shared__ float s_col[];
+  const int r = blockIdx.x * 32 + threadIdx.x;
+  const float part = pgd_comp_core(d, R, eta, bscale, sweeps, polish, prm, wsum, b, gb, active, clear_grad, maxv,
+                                   maxh, maxnz, blockIdx.x, blockIdx.y * blockDim.y + threadIdx.y,
+                                   gridDim.y * blockDim.y, threadIdx.y, blockDim.x * blockDim.y, s_col);
+  reduce_rows_add(part, gn2, r, r < R);
 }
 
 #ifndef FSMT_JIT_PROJ

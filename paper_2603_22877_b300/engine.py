@@ -178,6 +178,27 @@ class Compiled:
         """Pins one of launch_configs(R) for later passes and stages (None: the default)."""
         L.call("fsmt_select_config", self.h, int(R), C.byref(cfg) if cfg is not None else None)
 
+    def stage_form(self, R):
+        """True when the persistent stage forms (one kernel per stage, one per
+        iteration) run at R restarts under the configuration now chosen
+        (fsmt_stage_form); else a stage falls back to separate launches."""
+        v = C.c_int32()
+        L.call("fsmt_stage_form", self.h, int(R), C.byref(v))
+        return bool(v.value)
+
+    def stage_trace(self, trace):
+        """Records per-phase device timestamps of later persistent stages into `trace`
+        (a device uint64 / int64 tensor of 1 + 2 t_max entries; fsmt_stage_trace), or
+        stops recording (None).  The buffer must outlive the stages that use it."""
+        import torch
+        ptr = None
+        if trace is not None:
+            if not (trace.is_cuda and trace.dtype in (torch.int64, torch.uint64) and trace.is_contiguous()):
+                raise ValueError("trace must be a contiguous device int64 tensor")
+            ptr = C.c_void_p(trace.data_ptr())
+        self._trace = trace
+        L.call("fsmt_stage_trace", self.h, ptr)
+
     def autotune(self, R, sigma, w, a, b, grad_a, grad_b, obj=None, stream=None):
         """Times every configuration on these inputs and pins the fastest; returns it."""
         import torch
@@ -369,12 +390,24 @@ class _Lazy:
 RelaxedObjective = _Lazy()
 
 
+# fsmt_stage_config.persistent: how a fused stage runs its PGD iterations
+STAGE_FORMS = {"launches": 0, "stage": 1, "iteration": 2}
+
+
 class Solver:
     """Alg. 2 (annealing + ERWA) over R restarts with device-resident state.
 
     Each sigma stage is one fsmt_solve_stage call (a CUDA graph when use_graph);
     restarts whose check reports #Unsat = 0 are re-verified exactly on the host
     before SAT is reported.
+
+    stage_form: how the fused stage's PGD iterations run -- "launches" (separate
+    launches per iteration: forward + adjoint, the PGD kernels, the epsilon test),
+    "stage" (one persistent kernel runs them all, phases separated by grid
+    barriers), "iteration" (that kernel once per iteration), or "auto": separate
+    launches until tune() has timed the three forms on the current state and pinned
+    the fastest.  The persistent forms need the library's run-time compiled kernels
+    (Compiled.stage_form); without them a stage uses separate launches.
 
     form="plain" runs the same stage as separate library calls issued from
     Python per iteration (plain forward and adjoint kernels with the top-down
@@ -383,7 +416,8 @@ class Solver:
     """
 
     def __init__(self, problem, compiled, R, eta, b_scale, eps=1e-2, t_max=200, sweeps=20, rho=0.5, gamma=2.0,
-                 tau=1, use_graph=True, polish=32, normalize_eta=True, device="cuda", form="fused"):
+                 tau=1, use_graph=True, polish=32, normalize_eta=True, device="cuda", form="fused",
+                 stage_form="auto"):
         import torch
         if form not in ("fused", "plain"):
             raise ValueError("form is 'fused' or 'plain'")
@@ -417,6 +451,11 @@ class Solver:
         self.polish, self.normalize_eta = polish, normalize_eta
         self.eta, self.b_scale, self.eps, self.t_max, self.sweeps = eta, b_scale, eps, t_max, sweeps
         self.rho, self.gamma, self.tau, self.use_graph = rho, gamma, tau, use_graph
+        if stage_form not in ("auto",) + tuple(STAGE_FORMS):
+            raise ValueError(f"stage_form is 'auto' or one of {tuple(STAGE_FORMS)}")
+        self.stage_form = stage_form
+        self._form_code = 0 if stage_form == "auto" else STAGE_FORMS[stage_form]
+        self.stage_form_ms = None  # tune(): ms per stage of each form, when it timed them
         self._state = L.State(self.R, *[C.c_void_p(t.data_ptr()) for t in (
             self.a, self.b, self.w, self.h, self.grad_a, self.grad_b, self.obj, self.gnorm2, self.active,
             self.iters, self.n_unsat, self.ctl, self.params, self.wsum)])
@@ -445,15 +484,42 @@ class Solver:
         self.grad_a.zero_()
         self.grad_b.zero_()
 
-    def tune(self, sigma):
+    def tune(self, sigma, stages=2):
         """Autotunes the forward + adjoint kernel configuration on the current state
-        (fsmt_autotune; the gradient buffers are scratch and left zero)."""
-        return self.comp.autotune(self.R, sigma, self.w, self.a, self.b, self.grad_a, self.grad_b, self.obj)
+        (fsmt_autotune; the gradient buffers are scratch and left zero).  With
+        stage_form "auto" it then times `stages` stages of each stage form (after one
+        untimed stage that captures its graph) from the current state, puts the state
+        back, and pins the fastest form; the times are in stage_form_ms."""
+        import torch
+        best = self.comp.autotune(self.R, sigma, self.w, self.a, self.b, self.grad_a, self.grad_b, self.obj)
+        if self.stage_form != "auto" or self.form != "fused" or not self.comp.stage_form(self.R):
+            return best
+        keep = {k: getattr(self, k).clone() for k in ("a", "b", "w", "h")}
+        ms = {}
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for name, code in STAGE_FORMS.items():
+            self._form_code = code
+            for k, v in keep.items():
+                getattr(self, k).copy_(v)
+            self.stage(sigma, 1)
+            e0.record()
+            for t in range(stages):
+                self.stage(sigma, 2 + t)
+            e1.record()
+            torch.cuda.synchronize()
+            self.check_stage_status()
+            ms[name] = e0.elapsed_time(e1) / stages
+        for k, v in keep.items():
+            getattr(self, k).copy_(v)
+        self._form_code = STAGE_FORMS[min(ms, key=ms.get)]
+        self.stage_form_ms = ms
+        return best
 
     def config(self, sigma, t):
         return L.StageConfig(float(sigma), float(self.eta), float(self.b_scale), float(self.eps), int(self.t_max),
                              int(self.sweeps), float(self.rho), float(self.gamma), int(t % self.tau == 0),
-                             int(bool(self.use_graph)), int(self.polish), int(bool(self.normalize_eta)))
+                             int(bool(self.use_graph)), int(self.polish), int(bool(self.normalize_eta)),
+                             int(self._form_code))
 
     def stage(self, sigma, t, stream=None):
         if self.form == "plain":
@@ -489,6 +555,24 @@ class Solver:
                          update_w=(t % self.tau == 0), wsum=self.wsum if self.normalize_eta else None,
                          stream=stream)
         comp.mark_nonfinite(R, self.active, self.n_unsat, stream=stream)
+
+    @property
+    def persistent(self):
+        """Whether fused stages now ask for a persistent form ("stage" or "iteration")."""
+        return self._form_code > 0
+
+    @property
+    def chosen_stage_form(self):
+        """The stage form fused stages now run: "launches", "stage" or "iteration"."""
+        if self.form != "fused" or (self._form_code > 0 and not self.comp.stage_form(self.R)):
+            return "launches"
+        return {v: k for k, v in STAGE_FORMS.items()}[self._form_code]
+
+    def check_stage_status(self):
+        """Raises FsmtError(ETIMEOUT) when the last fused stage's persistent kernel gave
+        up waiting at a grid barrier (bit 4 of ctl[1]); its outputs are then invalid."""
+        if self.form == "fused" and self.persistent and int(self.ctl[1].item()) & 4:
+            raise L.FsmtError(L.ETIMEOUT, "the persistent stage kernel gave up waiting at a grid barrier")
 
     def stage_host(self, sigma, t, a_host, b_host, n_unsat_host, obj_host, stream=None):
         """The same stage with host input/output buffers (copies inside the call)."""
@@ -550,6 +634,7 @@ class Solver:
             # the stage's outcome reaches the host as one small copy; the statistics are
             # taken there (no device kernels beyond the library's own in the loop)
             nu = self.n_unsat.cpu().numpy()
+            self.check_stage_status()
             nonfinite = int((nu < 0).sum())
             found = None
             lo = None

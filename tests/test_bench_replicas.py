@@ -79,6 +79,8 @@ def _fake_solver(sat_stage, R=4):
             self.iters = torch.full((R,), 7, dtype=torch.int32)
             self.gnorm2 = torch.full((R,), 0.25)
             self.obj = torch.full((R,), -1.0)
+            self.form, self._form_code = "fused", 1  # a persistent stage form
+            self.ctl = torch.zeros(4, dtype=torch.int32)  # no error bits: every stage completed
             self.calls = 0
 
         def stage(self, sigma, t):

@@ -41,3 +41,26 @@ def test_checkpoint_round_trip_and_shape_check():
     U = _cpu_solver(R=8)
     with pytest.raises(ValueError, match="shape"):
         U.load_state_dict(ck)
+
+
+def test_stage_status_reports_a_barrier_timeout():
+    """check_stage_status raises ETIMEOUT exactly when a persistent stage form ran and
+    the stage's control block carries bit 4 of ctl[1] (a grid barrier gave up);
+    the other error bits and the separate-launch form leave it silent."""
+    import torch
+    from paper_2603_22877_b300 import _lib as L
+    from paper_2603_22877_b300.engine import STAGE_FORMS
+    S = _cpu_solver()
+    S.form = "fused"
+    S.ctl = torch.zeros(4, dtype=torch.int32)
+    for name, code in STAGE_FORMS.items():
+        S._form_code = code
+        S.ctl[1] = 1  # a non-finite ||g||^2 only
+        S.check_stage_status()
+        S.ctl[1] = 4 | 1
+        if code == 0:
+            S.check_stage_status()
+        else:
+            with pytest.raises(L.FsmtError) as e:
+                S.check_stage_status()
+            assert e.value.status == L.ETIMEOUT
