@@ -438,9 +438,9 @@ fsmt_status fsmt_solve_stage(fsmt_compiled* c, const fsmt_stage_config* cfg, fsm
 
 /* Whether fsmt_solve_stage with persistent = 1 or 2 runs the persistent kernel at R
  * restarts (1) or falls back to separate launches per iteration (0): the
- * persistent form needs the run-time compiled module (NVRTC), a stage kernel for
- * the chosen forward + adjoint configuration (the chunked kernel of the generated
- * routines, or the warp-per-constraint kernel), at most 1e11 node visits per
+ * persistent forms need the run-time compiled module (NVRTC; it holds a stage kernel
+ * for each run-time compiled chunked configuration and for the warp-per-constraint
+ * one, but none for the ahead-of-time chunked kernel), at most 1e11 node visits per
  * iteration, and the largest block of coupled reals within one CTA's shared memory.
  * ESTATE before fsmt_upload. */
 fsmt_status fsmt_stage_form(const fsmt_compiled* c, int32_t R, int32_t* persistent_out);

@@ -1082,11 +1082,11 @@ bool stage_plan(const Compiled& C, int R, bool per_iteration, StagePlan& p) {
   size_t smem_a = 0;
   if (x.variant == kVariantWarp) {
     const FusedShape f = fused_shape(C, R);
-    p.kernel = p.per_iteration ? C.jit_step_warp : C.jit_stage_warp;
+    p.kernel = C.jit_stage_warp[per_iteration];
     warps = f.warps;
     smem_a = f.smem;
-  } else if ((x.variant == kVariantWide && C.all_specialized) || (x.variant == kVariantJit && !C.all_specialized)) {
-    p.kernel = p.per_iteration ? C.jit_step_chunk[x.rpl - 1] : C.jit_stage_chunk[x.rpl - 1];
+  } else if (x.variant == kVariantWide || x.variant == kVariantJit) {
+    p.kernel = C.jit_stage_chunk[per_iteration][x.variant == kVariantWide][x.rpl - 1];
     warps = x.warps;
     smem_a = x.smem;
   }

@@ -91,13 +91,11 @@ struct Compiled {
   void* jit_wide[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // no generic path: all_specialized only
   bool all_specialized = false;  // every constraint of C_sigma has a generated routine
   int32_t jit_shapes = 0;
-  // run-time compiled persistent stage kernels (fsmt_stage.cuh), by the forward +
-  // adjoint body they run: chunked [restarts per lane - 1] (the form without the
-  // generic path when all_specialized, else the one with it), or warp per constraint
-  void* jit_stage_chunk[2] = {nullptr, nullptr};
-  void* jit_stage_warp = nullptr;
-  void* jit_step_chunk[2] = {nullptr, nullptr};  // the same kernels, one iteration per launch
-  void* jit_step_warp = nullptr;
+  // run-time compiled persistent stage kernels (fsmt_stage.cuh), [one iteration a
+  // launch] and by the forward + adjoint body they run: chunked [without the generic
+  // path (all_specialized only)][restarts per lane - 1], or warp per constraint
+  void* jit_stage_chunk[2][2][2] = {};
+  void* jit_stage_warp[2] = {nullptr, nullptr};
   unsigned long long* stage_trace = nullptr;  // the caller's device buffer for fsmt_stage_trace, or none
   // device side
   void* dev_block = nullptr;  // one allocation holding every device array

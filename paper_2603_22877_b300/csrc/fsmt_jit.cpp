@@ -361,6 +361,13 @@ std::string kernel_name(int wide, int adj, int rpl) {
   return std::string("fsmt_jit_") + (wide ? "wide_" : "") + (adj ? "adj_" : "fwd_") + std::to_string(rpl);
 }
 
+// step: one iteration a launch; wide: chunked without (1) / with (0) the generic
+// path, or -1 for warp per constraint
+std::string stage_kernel_name(int step, int wide, int rpl) {
+  const std::string k = step ? "fsmt_jit_step_" : "fsmt_jit_stage_";
+  return wide < 0 ? k + "warp" : k + (wide ? "wide_" : "gen_") + std::to_string(rpl);
+}
+
 std::string generated_source(const Compiled& C) {
   std::ostringstream o;
   o << "#define FSMT_JIT_SHAPES 1\n#define FSMT_JIT_PROJ 1\n" << kJitDevviewSrc << "\n" << kJitChunkedSrc << "\n"
@@ -393,30 +400,27 @@ std::string generated_source(const Compiled& C) {
              " float* __restrict__ grad_b, float* __restrict__ obj, float* __restrict__ cop, const int* ctl) {\n"
           << "  fsmt::chunked_body<" << (adj ? "true" : "false") << ", " << rpl << ", " << (wide ? "false" : "true")
           << ">(d, R, sigma, prm, vcap, w, a, b, grad_a, grad_b, obj, cop, ctl);\n}\n";
-  // the persistent stage kernels (fsmt_stage.cuh): the chunked forward + adjoint
-  // body in the form this instance runs (without the generic path when every
-  // constraint has a routine), and the warp-per-constraint body; both read the point
-  // through L2 (it changes between their phases)
-  const bool wide = C.all_specialized;
-  for (int rpl = 1; rpl <= 2; ++rpl)
-    o << "extern \"C\" __global__ void __launch_bounds__(" << (wide ? "fsmt::kChunkThreadsWide" : "fsmt::kChunkThreads")
-      << ", 1) fsmt_jit_stage_chunk_" << rpl << "(fsmt::StageArgs s) {\n"
-      << "  fsmt::stage_body(s, [&] { fsmt::chunked_body<true, " << rpl << ", " << (wide ? "false" : "true")
-      << ", true>(s.d, s.R, 0.f, s.prm, s.vcap, s.w, s.a, s.b, s.ga, s.gb, s.obj, nullptr, nullptr); });\n}\n";
-  // (at most 51 registers, so that five CTAs of the forward + adjoint phase share an SM,
-  // as they do in the warp kernel of its own)
-  o << "extern \"C\" __global__ void __launch_bounds__(fsmt::kFusedThreads, 5) fsmt_jit_stage_warp(fsmt::StageArgs s) {\n"
-       "  fsmt::stage_body(s, [&] { fsmt::fused_warp_body<true, true>(s.d, s.R, 0.f, s.prm, s.vcap, s.w, s.a, s.b, s.ga,"
-       " s.gb, s.obj, nullptr); });\n}\n";
-  // the same with one iteration per launch
-  for (int rpl = 1; rpl <= 2; ++rpl)
-    o << "extern \"C\" __global__ void __launch_bounds__(" << (wide ? "fsmt::kChunkThreadsWide" : "fsmt::kChunkThreads")
-      << ", 1) fsmt_jit_step_chunk_" << rpl << "(fsmt::StageArgs s) {\n"
-      << "  fsmt::stage_step_body(s, [&] { fsmt::chunked_body<true, " << rpl << ", " << (wide ? "false" : "true")
-      << ", true>(s.d, s.R, 0.f, s.prm, s.vcap, s.w, s.a, s.b, s.ga, s.gb, s.obj, nullptr, nullptr); });\n}\n";
-  o << "extern \"C\" __global__ void __launch_bounds__(fsmt::kFusedThreads, 5) fsmt_jit_step_warp(fsmt::StageArgs s) {\n"
-       "  fsmt::stage_step_body(s, [&] { fsmt::fused_warp_body<true, true>(s.d, s.R, 0.f, s.prm, s.vcap, s.w, s.a, s.b,"
-       " s.ga, s.gb, s.obj, nullptr); });\n}\n";
+  // the persistent stage kernels (fsmt_stage.cuh) around each forward + adjoint body
+  // the tuner can choose: chunked with and without the generic path (the latter run
+  // only when every constraint has a routine), and warp per constraint; each once for
+  // the stage (stage_body) and once per iteration (stage_step_body).  They read the
+  // point through L2 (it changes between their phases).  The warp form is held to at
+  // most 51 registers, so that five CTAs of its forward + adjoint phase share an SM, as
+  // in the warp kernel of its own.
+  for (int step = 0; step < 2; ++step) {
+    const char* body = step ? "stage_step_body" : "stage_body";
+    for (int wide = 0; wide < 2; ++wide)
+      for (int rpl = 1; rpl <= 2; ++rpl)
+        o << "extern \"C\" __global__ void __launch_bounds__("
+          << (wide ? "fsmt::kChunkThreadsWide" : "fsmt::kChunkThreads") << ", 1) "
+          << stage_kernel_name(step, wide, rpl) << "(fsmt::StageArgs s) {\n  fsmt::" << body
+          << "(s, [&] { fsmt::chunked_body<true, " << rpl << ", " << (wide ? "false" : "true")
+          << ", true>(s.d, s.R, 0.f, s.prm, s.vcap, s.w, s.a, s.b, s.ga, s.gb, s.obj, nullptr, nullptr); });\n}\n";
+    o << "extern \"C\" __global__ void __launch_bounds__(fsmt::kFusedThreads, 5) " << stage_kernel_name(step, -1, 0)
+      << "(fsmt::StageArgs s) {\n  fsmt::" << body
+      << "(s, [&] { fsmt::fused_warp_body<true, true>(s.d, s.R, 0.f, s.prm, s.vcap, s.w, s.a, s.b, s.ga, s.gb, s.obj,"
+         " nullptr); });\n}\n";
+  }
   o << "extern \"C\" __global__ void __launch_bounds__(256) fsmt_jit_proj(fsmt::DevView d, int R, float eta,"
        " float bscale, int sweeps, int polish, const float* prm, const float* __restrict__ wsum,"
        " float* __restrict__ b, float* __restrict__ gb, float* __restrict__ gn2,"
@@ -429,10 +433,8 @@ std::string generated_source(const Compiled& C) {
 struct Module {
   void* kernel[2][2][2];  // [wide][adjoint][restarts per lane - 1]
   void* proj;             // the projection kernel with generated block routines
-  void* stage_chunk[2];   // persistent stage kernels: chunked [restarts per lane - 1]
-  void* stage_warp;       // and warp per constraint
-  void* step_chunk[2];    // the same, one iteration per launch
-  void* step_warp;
+  void* stage_chunk[2][2][2];  // persistent stage kernels: chunked [per iteration][wide][restarts per lane - 1]
+  void* stage_warp[2];         // and warp per constraint [per iteration]
 };
 std::mutex g_mutex;
 std::unordered_map<std::string, Module> g_modules;  // by source text; kept for the process lifetime
@@ -449,8 +451,10 @@ bool jit_build(Compiled& C) {
   C.jit_shapes = 0;
   C.jit_proj = nullptr;
   C.proj_shapes = 0;
-  C.jit_stage_chunk[0] = C.jit_stage_chunk[1] = C.jit_stage_warp = nullptr;
-  C.jit_step_chunk[0] = C.jit_step_chunk[1] = C.jit_step_warp = nullptr;
+  for (int step = 0; step < 2; ++step) {
+    C.jit_stage_warp[step] = nullptr;
+    for (int w = 0; w < 2; ++w) C.jit_stage_chunk[step][w][0] = C.jit_stage_chunk[step][w][1] = nullptr;
+  }
   const char* off = std::getenv("FSMT_NO_JIT");
   const bool diagrams = !C.jit_shape.empty() && C.chunked_ok, blocks = !C.proj_shape_comp.empty();
   if ((off && *off && *off != '0') || !(diagrams || blocks)) return false;
@@ -519,20 +523,23 @@ bool jit_build(Compiled& C) {
     // test): the dynamic part may take what is left of the per-CTA maximum
     int optin = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    for (int r = 0; r < 6; ++r) {
+    auto stage_kernel = [&](int step, int wide, int rpl, void*& out) {
       cudaKernel_t k;
-      const std::string kind = r < 3 ? "stage" : "step";
-      const std::string nm = (r % 3) < 2 ? "fsmt_jit_" + kind + "_chunk_" + std::to_string(r % 3 + 1)
-                                         : "fsmt_jit_" + kind + "_warp";
       cudaFuncAttributes fa;
-      if (cudaLibraryGetKernel(&k, lib, nm.c_str()) != cudaSuccess ||
+      if (cudaLibraryGetKernel(&k, lib, stage_kernel_name(step, wide, rpl).c_str()) != cudaSuccess ||
           cudaFuncGetAttributes(&fa, (const void*)k) != cudaSuccess ||
           cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                optin - (int)fa.sharedSizeBytes) != cudaSuccess)
-        return fail("preparing the persistent stage kernels failed");
-      void** slot[6] = {&m.stage_chunk[0], &m.stage_chunk[1], &m.stage_warp,
-                        &m.step_chunk[0], &m.step_chunk[1], &m.step_warp};
-      *slot[r] = (void*)k;
+        return false;
+      out = (void*)k;
+      return true;
+    };
+    for (int step = 0; step < 2; ++step) {
+      for (int wide = 0; wide < 2; ++wide)
+        for (int r = 0; r < 2; ++r)
+          if (!stage_kernel(step, wide, r + 1, m.stage_chunk[step][wide][r]))
+            return fail("preparing the persistent stage kernels failed");
+      if (!stage_kernel(step, -1, 0, m.stage_warp[step])) return fail("preparing the persistent stage kernels failed");
     }
     it = g_modules.emplace(key, m).first;
   }
@@ -543,13 +550,13 @@ bool jit_build(Compiled& C) {
         C.jit_wide[adj][r] = C.all_specialized ? it->second.kernel[1][adj][r] : nullptr;
       }
     C.jit_shapes = (int32_t)C.jit_shape.size();
-    for (int r = 0; r < 2; ++r) {
-      C.jit_stage_chunk[r] = it->second.stage_chunk[r];
-      C.jit_step_chunk[r] = it->second.step_chunk[r];
-    }
+    for (int step = 0; step < 2; ++step)
+      for (int r = 0; r < 2; ++r) {
+        C.jit_stage_chunk[step][0][r] = it->second.stage_chunk[step][0][r];
+        C.jit_stage_chunk[step][1][r] = C.all_specialized ? it->second.stage_chunk[step][1][r] : nullptr;
+      }
   }
-  C.jit_stage_warp = it->second.stage_warp;
-  C.jit_step_warp = it->second.step_warp;
+  for (int step = 0; step < 2; ++step) C.jit_stage_warp[step] = it->second.stage_warp[step];
   if (blocks) {
     C.jit_proj = it->second.proj;
     C.proj_shapes = (int32_t)C.proj_shape_comp.size();

@@ -484,14 +484,18 @@ class Solver:
         self.grad_a.zero_()
         self.grad_b.zero_()
 
-    def tune(self, sigma, stages=2):
+    def tune(self, sigma, stages=2, kernels=True):
         """Autotunes the forward + adjoint kernel configuration on the current state
-        (fsmt_autotune; the gradient buffers are scratch and left zero).  With
-        stage_form "auto" it then times `stages` stages of each stage form (after one
-        untimed stage that captures its graph) from the current state, puts the state
-        back, and pins the fastest form; the times are in stage_form_ms."""
+        (fsmt_autotune; the gradient buffers are scratch and left zero; kernels=False
+        keeps the configuration already chosen).  With stage_form "auto" it then times
+        `stages` stages of each stage form (after one untimed stage that captures its
+        graph) from the current state, puts the state back, and pins the fastest form;
+        the times are in stage_form_ms (None when the configuration has no persistent
+        form).  Returns the forward + adjoint configuration (None with kernels=False)."""
         import torch
-        best = self.comp.autotune(self.R, sigma, self.w, self.a, self.b, self.grad_a, self.grad_b, self.obj)
+        best = None
+        if kernels:
+            best = self.comp.autotune(self.R, sigma, self.w, self.a, self.b, self.grad_a, self.grad_b, self.obj)
         if self.stage_form != "auto" or self.form != "fused" or not self.comp.stage_form(self.R):
             return best
         keep = {k: getattr(self, k).clone() for k in ("a", "b", "w", "h")}

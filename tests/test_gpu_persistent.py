@@ -149,15 +149,18 @@ def test_barrier_wait_is_bounded(monkeypatch):
     np.testing.assert_array_equal(S.iters.cpu().numpy(), ref.iters.cpu().numpy())
 
 
-def test_tune_times_every_stage_form_and_keeps_the_state():
-    """Solver.tune with stage_form "auto" times the three stage forms from the current
-    state, pins the fastest, and leaves the state as it found it."""
+@pytest.mark.parametrize("variant", ["chunk", "warp"])
+def test_tune_times_every_stage_form_and_keeps_the_state(variant):
+    """Solver.tune with stage_form "auto" (the kernel configuration pinned) times the
+    three stage forms from the current state, pins the fastest, and leaves the state
+    as it found it."""
     inst = W.jobshop(1002, 10, 5)
     R = 64
     P, comp, a, b, _ = setup(inst, R)
+    _pick(comp, R, variant)
     S = _solver(P, comp, R, eta=0.02, b_scale=inst.scale, t_max=4)
     S.reset(a, b)
-    S.tune(sigmas_for(inst)[0])
+    S.tune(sigmas_for(inst)[0], kernels=False)
     assert set(S.stage_form_ms) == {"launches", "stage", "iteration"}
     assert S.chosen_stage_form == min(S.stage_form_ms, key=S.stage_form_ms.get)
     np.testing.assert_array_equal(S.a.cpu().numpy(), a)
