@@ -442,8 +442,10 @@ fsmt_status fsmt_solve_stage(fsmt_compiled* c, const fsmt_stage_config* cfg, fsm
  * for each run-time compiled chunked configuration and for the warp-per-constraint
  * one, but none for the ahead-of-time chunked kernel), at most 1e11 node visits per
  * iteration, and the largest block of coupled reals within one CTA's shared memory.
- * ESTATE before fsmt_upload. */
-fsmt_status fsmt_stage_form(const fsmt_compiled* c, int32_t R, int32_t* persistent_out);
+ * The stage kernels are compiled at the first call that needs them (this one, or the
+ * first persistent fsmt_solve_stage), not at fsmt_upload: make that call before any
+ * stream capture of your own.  ESTATE before fsmt_upload. */
+fsmt_status fsmt_stage_form(fsmt_compiled* c, int32_t R, int32_t* persistent_out);
 
 /* Per-phase device timestamps of the persistent stage kernel, for profiling (no
  * counterpart in the paper).  With trace != NULL every later persistent stage of c

@@ -1072,9 +1072,12 @@ struct StagePlan {
 constexpr double kStageMaxVisits = 1e11;
 constexpr unsigned long long kStageBarrierNs = 5000000000ull;
 
-bool stage_plan(const Compiled& C, int R, bool per_iteration, StagePlan& p) {
+// Compiles the stage kernels on first use (outside any stream capture: fsmt_solve_stage
+// plans before it captures).
+bool stage_plan(Compiled& C, int R, bool per_iteration, StagePlan& p) {
   p.per_iteration = per_iteration;
   if (C.n_obj == 0 || (double)C.n_obj_nodes * R > kStageMaxVisits) return false;
+  if (!jit_build_stage(C)) return false;
   LaunchCfg scratch;
   const LaunchCfg& x = chosen_config(C, R, scratch);
   if (x.variant < 0) return false;
@@ -1761,7 +1764,7 @@ fsmt_status fsmt_stage_trace(fsmt_compiled* c, uint64_t* trace) {
   return FSMT_OK;
 }
 
-fsmt_status fsmt_stage_form(const fsmt_compiled* c, int32_t R, int32_t* persistent_out) {
+fsmt_status fsmt_stage_form(fsmt_compiled* c, int32_t R, int32_t* persistent_out) {
   if (!persistent_out) {
     set_error("NULL argument");
     return FSMT_EINVAL;

@@ -14,6 +14,7 @@ namespace fsmt {
 void set_error(const std::string& msg);
 struct Compiled;
 bool jit_build(Compiled& C);  // fsmt_jit.cpp
+bool jit_build_stage(Compiled& C);  // fsmt_jit.cpp: the persistent stage kernels, on first use
 
 struct Problem {
   int32_t n_bool = 0, n_real = 0;
@@ -96,6 +97,7 @@ struct Compiled {
   // path (all_specialized only)][restarts per lane - 1], or warp per constraint
   void* jit_stage_chunk[2][2][2] = {};
   void* jit_stage_warp[2] = {nullptr, nullptr};
+  bool jit_stage_tried = false;  // jit_build_stage ran (they are built on first use)
   unsigned long long* stage_trace = nullptr;  // the caller's device buffer for fsmt_stage_trace, or none
   // device side
   void* dev_block = nullptr;  // one allocation holding every device array

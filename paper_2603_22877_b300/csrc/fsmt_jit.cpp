@@ -368,7 +368,8 @@ std::string stage_kernel_name(int step, int wide, int rpl) {
   return wide < 0 ? k + "warp" : k + (wide ? "wide_" : "gen_") + std::to_string(rpl);
 }
 
-std::string generated_source(const Compiled& C) {
+// The device headers and the instance's generated routines, common to both modules.
+std::string routines_source(const Compiled& C) {
   std::ostringstream o;
   o << "#define FSMT_JIT_SHAPES 1\n#define FSMT_JIT_PROJ 1\n" << kJitDevviewSrc << "\n" << kJitChunkedSrc << "\n"
     << kJitProjSrc << "\n" << kJitStageSrc << "\nnamespace fsmt {\n\n";
@@ -390,6 +391,13 @@ std::string generated_source(const Compiled& C) {
   for (size_t k = 0; k < C.jit_shape.size(); ++k)
     o << "    case " << k + 1 << ": shape_" << k + 1 << "<ADJ, RPL>(sl, s_p, s_g, lane, wc, cp); return true;\n";
   o << "    default: return false;\n  }\n}\n\n}  // namespace fsmt\n\n";
+  return o.str();
+}
+
+// The module of the forward / adjoint kernels and the projection kernel.
+std::string generated_source(const Compiled& C) {
+  std::ostringstream o;
+  o << routines_source(C);
   for (int wide = 0; wide < 2; ++wide)
     for (int adj = 0; adj < 2; ++adj)
       for (int rpl = 1; rpl <= 2; ++rpl)
@@ -400,6 +408,19 @@ std::string generated_source(const Compiled& C) {
              " float* __restrict__ grad_b, float* __restrict__ obj, float* __restrict__ cop, const int* ctl) {\n"
           << "  fsmt::chunked_body<" << (adj ? "true" : "false") << ", " << rpl << ", " << (wide ? "false" : "true")
           << ">(d, R, sigma, prm, vcap, w, a, b, grad_a, grad_b, obj, cop, ctl);\n}\n";
+  o << "extern \"C\" __global__ void __launch_bounds__(256) fsmt_jit_proj(fsmt::DevView d, int R, float eta,"
+       " float bscale, int sweeps, int polish, const float* prm, const float* __restrict__ wsum,"
+       " float* __restrict__ b, float* __restrict__ gb, float* __restrict__ gn2,"
+       " const uint8_t* __restrict__ active, int clear_grad, const int* ctl, int maxv, int maxh, int maxnz) {\n"
+       "  fsmt::pgd_comp_body(d, R, eta, bscale, sweeps, polish, prm, wsum, b, gb, gn2, active, clear_grad, ctl,"
+       " maxv, maxh, maxnz);\n}\n";
+  return o.str();
+}
+
+// The module of the persistent stage kernels, compiled on first use (jit_build_stage).
+std::string stage_source(const Compiled& C) {
+  std::ostringstream o;
+  o << routines_source(C);
   // the persistent stage kernels (fsmt_stage.cuh) around each forward + adjoint body
   // the tuner can choose: chunked with and without the generic path (the latter run
   // only when every constraint has a routine), and warp per constraint; each once for
@@ -421,23 +442,61 @@ std::string generated_source(const Compiled& C) {
       << "(s, [&] { fsmt::fused_warp_body<true, true>(s.d, s.R, 0.f, s.prm, s.vcap, s.w, s.a, s.b, s.ga, s.gb, s.obj,"
          " nullptr); });\n}\n";
   }
-  o << "extern \"C\" __global__ void __launch_bounds__(256) fsmt_jit_proj(fsmt::DevView d, int R, float eta,"
-       " float bscale, int sweeps, int polish, const float* prm, const float* __restrict__ wsum,"
-       " float* __restrict__ b, float* __restrict__ gb, float* __restrict__ gn2,"
-       " const uint8_t* __restrict__ active, int clear_grad, const int* ctl, int maxv, int maxh, int maxnz) {\n"
-       "  fsmt::pgd_comp_body(d, R, eta, bscale, sweeps, polish, prm, wsum, b, gb, gn2, active, clear_grad, ctl,"
-       " maxv, maxh, maxnz);\n}\n";
   return o.str();
 }
 
 struct Module {
   void* kernel[2][2][2];  // [wide][adjoint][restarts per lane - 1]
   void* proj;             // the projection kernel with generated block routines
+};
+struct StageModule {
   void* stage_chunk[2][2][2];  // persistent stage kernels: chunked [per iteration][wide][restarts per lane - 1]
   void* stage_warp[2];         // and warp per constraint [per iteration]
 };
 std::mutex g_mutex;
 std::unordered_map<std::string, Module> g_modules;  // by source text; kept for the process lifetime
+std::unordered_map<std::string, StageModule> g_stage_modules;
+
+// The device's "-arch=sm_XYa" option, or "" without a device.
+std::string device_arch(int& dev) {
+  int major = 0, minor = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return "";
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  return "-arch=sm_" + std::to_string(major) + std::to_string(minor) + "a";
+}
+
+// Compiles src with NVRTC and loads it; false (with the error message set) on failure.
+bool compile_and_load(const std::string& src, const std::string& arch, cudaLibrary_t& lib) {
+  Nvrtc& N = nvrtc();
+  nvrtcProgram prog;
+  if (N.create(&prog, src.c_str(), "fsmt_jit.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS) return false;
+  const bool verbose = std::getenv("FSMT_JIT_VERBOSE") != nullptr;
+  // -default-device: the kernel body's generic lambdas are device code
+  const char* opts[] = {arch.c_str(), "-std=c++17", "-default-device", "-lineinfo", "--ptxas-options=-v"};
+  const nvrtcResult rc = N.compile(prog, verbose ? 5 : 4, opts);
+  size_t ls = 0;
+  N.log_size(prog, &ls);
+  std::string log(ls, '\0');
+  if (ls) N.log(prog, &log[0]);
+  if (verbose) std::fprintf(stderr, "%s\n", log.c_str());
+  if (rc != NVRTC_SUCCESS) {
+    set_error("run-time compilation failed; using the ahead-of-time kernel:\n" + log);
+    N.destroy(&prog);
+    return false;
+  }
+  size_t cs = 0;
+  N.cubin_size(prog, &cs);
+  std::string cubin(cs, '\0');
+  N.cubin(prog, &cubin[0]);
+  N.destroy(&prog);
+  if (cudaLibraryLoadData(&lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("loading the run-time compiled kernels failed; using the ahead-of-time kernel");
+    return false;
+  }
+  return true;
+}
 
 }  // namespace
 
@@ -451,6 +510,7 @@ bool jit_build(Compiled& C) {
   C.jit_shapes = 0;
   C.jit_proj = nullptr;
   C.proj_shapes = 0;
+  C.jit_stage_tried = false;
   for (int step = 0; step < 2; ++step) {
     C.jit_stage_warp[step] = nullptr;
     for (int w = 0; w < 2; ++w) C.jit_stage_chunk[step][w][0] = C.jit_stage_chunk[step][w][1] = nullptr;
@@ -458,48 +518,23 @@ bool jit_build(Compiled& C) {
   const char* off = std::getenv("FSMT_NO_JIT");
   const bool diagrams = !C.jit_shape.empty() && C.chunked_ok, blocks = !C.proj_shape_comp.empty();
   if ((off && *off && *off != '0') || !(diagrams || blocks)) return false;
-  Nvrtc& N = nvrtc();
-  if (!N.ok) return false;
-  int dev = 0, major = 0, minor = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return false;
-  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
-  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  if (!nvrtc().ok) return false;
+  int dev = 0;
+  const std::string arch = device_arch(dev);
+  if (arch.empty()) return false;
   const std::string src = generated_source(C);
-  const std::string arch = "-arch=sm_" + std::to_string(major) + std::to_string(minor) + "a";
   std::lock_guard<std::mutex> lock(g_mutex);
   const std::string key = arch + src;
   auto it = g_modules.find(key);
   if (it == g_modules.end()) {
-    nvrtcProgram prog;
-    if (N.create(&prog, src.c_str(), "fsmt_jit.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS) return false;
-    const bool verbose = std::getenv("FSMT_JIT_VERBOSE") != nullptr;
-    // -default-device: the kernel body's generic lambdas are device code
-    const char* opts[] = {arch.c_str(), "-std=c++17", "-default-device", "-lineinfo", "--ptxas-options=-v"};
-    const nvrtcResult rc = N.compile(prog, verbose ? 5 : 4, opts);
-    size_t ls = 0;
-    N.log_size(prog, &ls);
-    std::string log(ls, '\0');
-    if (ls) N.log(prog, &log[0]);
-    if (verbose) std::fprintf(stderr, "%s\n", log.c_str());
-    if (rc != NVRTC_SUCCESS) {
-      set_error("run-time compilation failed; using the ahead-of-time kernel:\n" + log);
-      N.destroy(&prog);
-      return false;
-    }
-    size_t cs = 0;
-    N.cubin_size(prog, &cs);
-    std::string cubin(cs, '\0');
-    N.cubin(prog, &cubin[0]);
-    N.destroy(&prog);
     cudaLibrary_t lib;
+    if (!compile_and_load(src, arch, lib)) return false;
     // a failure below leaves no error behind for the next launch check to find
     auto fail = [](const char* what) {
       cudaGetLastError();
       set_error(std::string(what) + "; using the ahead-of-time kernel");
       return false;
     };
-    if (cudaLibraryLoadData(&lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) != cudaSuccess)
-      return fail("loading the run-time compiled kernels failed");
     Module m{};
     for (int wide = 0; wide < 2; ++wide)
       for (int adj = 0; adj < 2; ++adj)
@@ -519,6 +554,41 @@ bool jit_build(Compiled& C) {
         return fail("preparing the run-time compiled projection kernel failed");
       m.proj = (void*)k;
     }
+    it = g_modules.emplace(key, m).first;
+  }
+  if (diagrams) {
+    for (int adj = 0; adj < 2; ++adj)
+      for (int r = 0; r < 2; ++r) {
+        C.jit_kernel[adj][r] = it->second.kernel[0][adj][r];
+        C.jit_wide[adj][r] = C.all_specialized ? it->second.kernel[1][adj][r] : nullptr;
+      }
+    C.jit_shapes = (int32_t)C.jit_shape.size();
+  }
+  if (blocks) {
+    C.jit_proj = it->second.proj;
+    C.proj_shapes = (int32_t)C.proj_shape_comp.size();
+  }
+  return true;
+}
+
+// Builds (or reuses) the persistent stage kernels for C, once per compiled object and
+// only when asked for: they double the run-time compilation, which every upload would
+// otherwise pay.  Needs the module of jit_build (the same routines).  Returns whether
+// the kernels are there.
+bool jit_build_stage(Compiled& C) {
+  if (C.jit_stage_tried) return C.jit_stage_warp[0] != nullptr;
+  C.jit_stage_tried = true;
+  if (!C.jit_proj && !C.jit_kernel[1][0]) return false;  // no run-time compiled module
+  int dev = 0;
+  const std::string arch = device_arch(dev);
+  if (arch.empty()) return false;
+  const std::string src = stage_source(C);
+  std::lock_guard<std::mutex> lock(g_mutex);
+  const std::string key = arch + src;
+  auto it = g_stage_modules.find(key);
+  if (it == g_stage_modules.end()) {
+    cudaLibrary_t lib;
+    if (!compile_and_load(src, arch, lib)) return false;
     // the stage kernels have static shared memory of their own (barrier and epsilon
     // test): the dynamic part may take what is left of the per-CTA maximum
     int optin = 0;
@@ -534,32 +604,25 @@ bool jit_build(Compiled& C) {
       out = (void*)k;
       return true;
     };
+    StageModule m{};
     for (int step = 0; step < 2; ++step) {
+      bool ok = stage_kernel(step, -1, 0, m.stage_warp[step]);
       for (int wide = 0; wide < 2; ++wide)
-        for (int r = 0; r < 2; ++r)
-          if (!stage_kernel(step, wide, r + 1, m.stage_chunk[step][wide][r]))
-            return fail("preparing the persistent stage kernels failed");
-      if (!stage_kernel(step, -1, 0, m.stage_warp[step])) return fail("preparing the persistent stage kernels failed");
+        for (int r = 0; r < 2; ++r) ok = ok && stage_kernel(step, wide, r + 1, m.stage_chunk[step][wide][r]);
+      if (!ok) {
+        cudaGetLastError();  // leave no error behind for the next launch check to find
+        set_error("preparing the persistent stage kernels failed; stages use separate launches");
+        return false;
+      }
     }
-    it = g_modules.emplace(key, m).first;
+    it = g_stage_modules.emplace(key, m).first;
   }
-  if (diagrams) {
-    for (int adj = 0; adj < 2; ++adj)
-      for (int r = 0; r < 2; ++r) {
-        C.jit_kernel[adj][r] = it->second.kernel[0][adj][r];
-        C.jit_wide[adj][r] = C.all_specialized ? it->second.kernel[1][adj][r] : nullptr;
-      }
-    C.jit_shapes = (int32_t)C.jit_shape.size();
-    for (int step = 0; step < 2; ++step)
-      for (int r = 0; r < 2; ++r) {
-        C.jit_stage_chunk[step][0][r] = it->second.stage_chunk[step][0][r];
-        C.jit_stage_chunk[step][1][r] = C.all_specialized ? it->second.stage_chunk[step][1][r] : nullptr;
-      }
-  }
-  for (int step = 0; step < 2; ++step) C.jit_stage_warp[step] = it->second.stage_warp[step];
-  if (blocks) {
-    C.jit_proj = it->second.proj;
-    C.proj_shapes = (int32_t)C.proj_shape_comp.size();
+  for (int step = 0; step < 2; ++step) {
+    C.jit_stage_warp[step] = it->second.stage_warp[step];
+    for (int r = 0; r < 2; ++r) {
+      C.jit_stage_chunk[step][0][r] = C.jit_kernel[1][0] ? it->second.stage_chunk[step][0][r] : nullptr;
+      C.jit_stage_chunk[step][1][r] = C.jit_wide[1][0] ? it->second.stage_chunk[step][1][r] : nullptr;
+    }
   }
   return true;
 }
