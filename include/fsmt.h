@@ -397,10 +397,10 @@ fsmt_status fsmt_mark_nonfinite(const fsmt_compiled* c, int32_t R, const uint8_t
  * -- parameters, stage start, weight sum, iteration start, the stage kernel -- before
  * the round check); persistent = 2 launches the same kernel once per iteration (no
  * loop inside it, so that the forward + adjoint phase is compiled as in its own
- * kernel).  Each barrier waits at most 5 s
- * for the slowest CTA (the environment variable FSMT_STAGE_BARRIER_NS, read at
- * each launch or graph capture, sets another limit in ns); a kernel that gave up
- * sets bit 4 of ctl[1] and ends, and fsmt_solve_stage_host returns FSMT_ETIMEOUT.  Results equal the separate-launch
+ * kernel).  Each barrier waits at most 5 s for the slowest CTA (the environment
+ * variable FSMT_STAGE_BARRIER_NS, read at each launch or graph capture, sets another
+ * limit in ns); a kernel that gave up sets bit 4 of ctl[1] and ends, and
+ * fsmt_solve_stage_host returns FSMT_ETIMEOUT.  Results equal the separate-launch
  * form's up to the order of floating-point atomic additions.  One stage at a time
  * per state (the barrier lives in its ctl). */
 typedef struct {
