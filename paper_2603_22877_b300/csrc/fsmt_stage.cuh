@@ -52,13 +52,14 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 
 // Grid-wide barrier over the CTAs of a cooperative launch (all co-resident).  ctl[2]
-// counts arrivals, ctl[3] is the generation.  Every thread fences its writes, one
-// thread per CTA arrives; the last CTA to arrive runs serial() with all its threads,
-// resets the count and opens the next generation; the others wait for it.  The wait
-// is bounded: after limit_ns (or 2^31 polls) the CTA sets kCtlBarrierTimeout in
-// ctl[1] and the barrier returns false, and the caller returns at once (a CTA that
-// never arrives -- it cannot, in a cooperative launch -- costs the others one limit
-// each, never a hang).  The release and acquire fences make every write before the
+// counts arrivals, ctl[3] is the generation.  After a CTA barrier, one thread per CTA
+// fences (cumulatively, for the writes its CTA made before the CTA barrier) and
+// arrives; the last CTA to arrive runs serial() with all its threads, resets the
+// count and opens the next generation; the others wait for it and fence again before
+// their CTA barrier.  The wait is bounded: after limit_ns (or 2^31 polls) the CTA sets
+// kCtlBarrierTimeout in ctl[1] and the barrier returns false, and the caller returns at
+// once (a CTA that never arrives -- it cannot, in a cooperative launch -- costs the
+// others one limit each, never a hang).  The fences make every write before the
 // barrier visible to every read after it (weak loads included; the read-only path
 // excluded).
 template <class F>
@@ -66,7 +67,6 @@ __device__ __forceinline__ bool grid_barrier(int* ctl, unsigned long long limit_
   __shared__ int s_role;  // 1: the last CTA to arrive, 0: released, -1: gave up
   unsigned* cnt = reinterpret_cast<unsigned*>(ctl + 2);
   volatile unsigned* gen = reinterpret_cast<volatile unsigned*>(ctl + 3);
-  __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
     const unsigned g0 = *gen;
@@ -84,7 +84,7 @@ __device__ __forceinline__ bool grid_barrier(int* ctl, unsigned long long limit_
           role = -1;
           break;
         }
-        __nanosleep(128);
+        __nanosleep(32);
       }
     }
     __threadfence();
@@ -94,7 +94,6 @@ __device__ __forceinline__ bool grid_barrier(int* ctl, unsigned long long limit_
   const int role = s_role;
   if (role == 1) {
     serial();
-    __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
       atomicExch(cnt, 0u);
