@@ -1054,9 +1054,10 @@ fsmt_status launch_round_check(const Compiled& C, int R, const float* a, const f
 }
 
 // ------------------------------------------------- persistent stage kernel --
-// The stage's iterations in one cooperative launch (stage_body, fsmt_stage.cuh),
-// when this instance's run-time compiled module holds a stage kernel for the chosen
-// forward + adjoint configuration.  Phase B's projection runs on the first
+// The stage's iterations in one cooperative launch (stage_body, fsmt_stage.cuh), or
+// one such launch per iteration (stage_step_body), when the instance's run-time
+// compiled stage module (jit_build_stage) holds a stage kernel for the chosen
+// forward + adjoint configuration.  The PGD phase's projection runs on the first
 // proj_warps warps of each CTA, as many as fit in the larger of the forward +
 // adjoint phase's shared memory and 32 KB; the grid is every CTA that fits on the
 // GPU at once (a cooperative launch refuses more).
