@@ -473,9 +473,39 @@ def test_binding_prototypes_match_the_header():
         assert len(L.PROTOTYPES[name]) == n, name
 
 
+def _header_structs():
+    """Member names, in order, of every `typedef struct { ... } fsmt_x;` in include/fsmt.h."""
+    import re
+    text = open(os.path.join(ROOT, "include", "fsmt.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    out = {}
+    for m in re.finditer(r"typedef struct \{(.*?)\}\s*(fsmt_\w+)\s*;", text, flags=re.S):
+        names = []
+        for decl in m.group(1).split(";"):
+            decl = decl.strip()
+            if not decl:
+                continue
+            # "int32_t a, b" / "float* a" -> the declarator names
+            first, *rest = decl.split(",")
+            names.append(first.replace("*", " ").split()[-1])
+            names += [r.replace("*", " ").strip() for r in rest]
+        out[m.group(2)] = names
+    return out
+
+
+def test_binding_structs_match_the_header():
+    """The ctypes structures list the header's members in the header's order (a member
+    added on one side only would shift every later one)."""
+    declared = _header_structs()
+    for cname, py in (("fsmt_info", L.Info), ("fsmt_launch_config", L.LaunchConfig), ("fsmt_state", L.State),
+                      ("fsmt_stage_config", L.StageConfig)):
+        assert [f for f, _ in py._fields_] == declared[cname], cname
+
+
 DEVICE_CALLS = ["fsmt_forward", "fsmt_adjoint", "fsmt_launch_configs", "fsmt_select_config", "fsmt_autotune",
                 "fsmt_forward_plain", "fsmt_adjoint_plain", "fsmt_plain_noalloc", "fsmt_weight_sum",
-                "fsmt_pgd_step", "fsmt_round_check", "fsmt_solve_stage", "fsmt_solve_stage_host"]
+                "fsmt_pgd_step", "fsmt_round_check", "fsmt_solve_stage", "fsmt_solve_stage_host",
+                "fsmt_stage_form"]
 
 
 @pytest.mark.parametrize("name", DEVICE_CALLS)
